@@ -1,0 +1,67 @@
+"""FP64 oracle for the training side: data generation from a refined lattice,
+restriction to the coarse lattice, and the AdamW update.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Paper passages followed:
+  * Sec. 2.4 -- supervised training on pairs generated by high-resolution
+    standard LBM runs; the loss is Eq. 4 (``oracle.gnn.collide_loss``).
+
+Readings where the paper is silent (also listed in the design doc):
+  * "High resolution" = an m-times refined lattice (m = 4 by default) under
+    acoustic scaling: the same lattice velocity u0, k_f = k_c / m,
+    tau_f = 1/2 + m (tau_c - 1/2), and m fine steps per coarse step.
+  * Coarse node (I, J) coincides with fine node (m I, m J).
+  * Restriction (Dupuis-Chopard rescaling): rho and u are injected from the
+    fine node; the non-equilibrium part of the fine PRE-collision state is
+    recovered from the stored post-collision one,
+        f_neq_f = (f*_f - f^eq) / (1 - 1/tau_f),
+    rescaled to the coarse lattice, f_neq_c = m (tau_c / tau_f) f_neq_f, and
+    the coarse post-collision state is f*_c = f^eq + (1 - 1/tau_c) f_neq_c.
+  * A training pair is (restricted state at coarse step n, at step n+1); the
+    prediction is one GNN-LBM coarse step on the first element.
+  * The optimiser (unnamed in the paper) is AdamW with decoupled weight decay
+    (Loshchilov & Hutter): beta = (0.9, 0.999), eps = 1e-8.
+"""
+import numpy as np
+
+from . import lbm
+
+
+def fine_tau(tau_c, m):
+    """tau of the m-times refined lattice that keeps the physical viscosity."""
+    return 0.5 + m * (tau_c - 0.5)
+
+
+def restrict(f_fine, m, tau_f, tau_c):
+    """Restrict a fine post-collision state (9, m ny, m nx) to the coarse one."""
+    sub = np.asarray(f_fine, np.float64)[:, ::m, ::m]
+    rho, ux, uy = lbm.moments(sub)
+    feq = lbm.equilibrium(rho, ux, uy)
+    fneq_f = (sub - feq) / (1.0 - 1.0 / tau_f)
+    fneq_c = m * (tau_c / tau_f) * fneq_f
+    return feq + (1.0 - 1.0 / tau_c) * fneq_c
+
+
+def tgv_pair(n_c, u0, k_mult, tau_c, n_steps, m=4):
+    """One training pair on an n_c x n_c coarse TGV with wavenumber
+    k = k_mult * 2 pi / n_c: the fine lattice (m n_c)^2 is run m*n_steps and
+    then m more steps; both ends are restricted.  Returns (f_in, f_target)."""
+    n_f = m * n_c
+    k_f = k_mult * 2.0 * np.pi / n_f
+    tau_f = fine_tau(tau_c, m)
+    f = lbm.tgv_init(n_f, n_f, 1.0, u0, k_f, k_f)
+    f = lbm.bgk_run(f, tau_f, m * n_steps)
+    f_in = restrict(f, m, tau_f, tau_c)
+    f = lbm.bgk_run(f, tau_f, m)
+    return f_in, restrict(f, m, tau_f, tau_c)
+
+
+def adamw_step(theta, grad, m, v, t, lr, wd, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One AdamW update at step t (1-based).  Returns (theta, m, v)."""
+    theta = np.asarray(theta, np.float64) * (1.0 - lr * wd)
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return theta - lr * mhat / (np.sqrt(vhat) + eps), m, v

@@ -1,0 +1,200 @@
+"""Pins of the FP64 GNN oracle (no GPU): special cases, brute force on tiny
+lattices, library routines and finite differences."""
+import numpy as np
+import pytest
+
+from oracle import gnn, lbm
+from paper_2504_14494_gb300 import inputs
+
+
+def _state(nx, ny, seed, u0=0.05, amp=2e-2):
+    f = lbm.tgv_init(nx, ny, 1.0, u0, 2 * np.pi / nx, 2 * np.pi / ny)
+    return f * inputs.perturbation(f.shape, seed, amp)
+
+
+def _params(seed, bias=0.1, s_df=1e-2):
+    return inputs.xavier_params(seed, s_df=s_df, bias_scale=bias)
+
+
+def test_layout_matches_inputs_module():
+    """The oracle's parameter layout and the shared input layout agree."""
+    assert gnn.N_TRAINABLE == inputs.N_TRAINABLE == 38922
+    assert gnn.N_TOTAL == inputs.N_PARAMS
+    assert [s for _, s in gnn.SHAPES] == [tuple(s) for s in inputs.PARAM_SHAPES]
+
+
+def test_gelu_matches_torch_tanh_gelu():
+    """The GELU reading (tanh form) equals torch's gelu(approximate='tanh')
+    in FP64, and its derivative equals autograd's."""
+    torch = pytest.importorskip("torch")
+    z = np.linspace(-8, 8, 2001)
+    zt = torch.tensor(z, dtype=torch.float64, requires_grad=True)
+    yt = torch.nn.functional.gelu(zt, approximate="tanh")
+    yt.sum().backward()
+    assert np.allclose(gnn.gelu(z), yt.detach().numpy(), rtol=1e-14, atol=1e-15)
+    assert np.allclose(gnn.gelu_grad(z), zt.grad.numpy(), rtol=1e-13, atol=1e-14)
+
+
+def test_bf16_round_matches_torch():
+    """bfloat16 round-to-nearest-even agrees with torch's float32->bfloat16."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    a = np.concatenate([rng.standard_normal(10000).astype(np.float32),
+                        np.array([1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -1.0 - 2 ** -8, 0.0], np.float32)])
+    ref = torch.tensor(a).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(gnn.bf16_round(a), ref)
+
+
+@pytest.mark.parametrize("nx,ny", [(4, 4), (5, 3), (3, 3)])
+def test_bruteforce_edge_mlp_equals_split_form(nx, ny):
+    """W_e [h_i; h_j; e_k] = W_a h_i + W_b h_j + W_c e_k (linearity): the
+    brute-force per-edge form and the split form agree to FP64 round-off."""
+    p = gnn.unpack(_params(11))
+    f = _state(nx, ny, 5)
+    y, _ = gnn.forward(f, p)
+    ys = gnn.forward_split(f, p)
+    assert np.allclose(y, ys, rtol=1e-12, atol=1e-12)
+
+
+def _loop_forward(f_pre, p):
+    """Independent brute force with explicit coordinates and Python loops
+    over nodes and the 8 neighbours (Sec. 2.2 message passing)."""
+    _, ny, nx = f_pre.shape
+    e = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+    g = lambda z: 0.5 * z * (1.0 + np.tanh(np.sqrt(2 / np.pi) * (z + 0.044715 * z ** 3)))
+    h = {}
+    for y in range(ny):
+        for x in range(nx):
+            fi = f_pre[:, y, x]
+            rho = fi.sum()
+            ux = sum(fi[i] * e[i][0] for i in range(9)) / rho
+            uy = sum(fi[i] * e[i][1] for i in range(9)) / rho
+            xin = (np.concatenate([fi, [rho, ux, uy]]) - p["mu"]) / p["sigma"]
+            h[(x, y)] = g(p["enc2.W"] @ g(p["enc1.W"] @ xin + p["enc1.b"]) + p["enc2.b"])
+    for r in range(2):
+        new = {}
+        for (x, y), hi in h.items():
+            a = np.zeros(64)
+            for k in range(1, 9):
+                hj = h[((x + e[k][0]) % nx, (y + e[k][1]) % ny)]
+                a += g(p[f"r{r}.edge.W"] @ np.concatenate([hi, hj, e[k]]) + p[f"r{r}.edge.b"])
+            new[(x, y)] = hi + g(p[f"r{r}.node.W"] @ np.concatenate([hi, a]) + p[f"r{r}.node.b"])
+        h = new
+    out = np.zeros((ny * nx, 10))
+    for (x, y), hi in h.items():
+        out[y * nx + x] = p["head.W"] @ hi + p["head.b"]
+    return out
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 3), (4, 2)])
+def test_forward_equals_loop_bruteforce(nx, ny):
+    p = gnn.unpack(_params(12))
+    f = _state(nx, ny, 6)
+    y, _ = gnn.forward(f, p)
+    assert np.allclose(y, _loop_forward(f, p), rtol=1e-12, atol=1e-12)
+
+
+def test_zero_network_reduces_to_bgk():
+    """Eq. 3 with all trainable values zero: y = 0, so tau_adj = 0.5 +
+    sigmoid(0) = 1 and Delta f = 0, and the GNN step equals the BGK step
+    (Eq. 1) exactly."""
+    theta = inputs.zero_params()
+    f = _state(6, 5, 8)
+    a = gnn.gnn_step(f, theta, 0.7)
+    b = lbm.bgk_step(f, 0.7)
+    assert np.array_equal(a, b) or np.allclose(a, b, rtol=0, atol=1e-16)
+
+
+def test_tau_adj_range_and_delta_f_scale():
+    """Sec. 2.3.1: the sigmoid-scaled adjustment lies in (0.5, 1.5) and the
+    correction is s_df times the head output."""
+    p = gnn.unpack(_params(13, bias=2.0))
+    y = np.random.default_rng(0).standard_normal((100, 10)) * 3
+    tau_adj, df = gnn.heads(y, p)
+    assert np.all(tau_adj > 0.5) and np.all(tau_adj < 1.5)
+    sat, _ = gnn.heads(np.array([[-800.0] + [0] * 9, [800.0] + [0] * 9, [0.0] * 10]), p)
+    assert np.allclose(sat, [0.5, 1.5, 1.0], rtol=0, atol=1e-15)
+    assert np.allclose(df, p["s_df"] * y[:, 1:].T)
+
+
+def test_translation_invariance():
+    """The lattice graph is periodic and the network is shared over nodes:
+    shifting the input field shifts the output field."""
+    theta = _params(14)
+    f = _state(6, 4, 9)
+    a = gnn.gnn_step(f, theta, 0.9)
+    b = gnn.gnn_step(np.roll(f, (1, 2), axis=(1, 2)), theta, 0.9)
+    assert np.allclose(np.roll(a, (1, 2), axis=(1, 2)), b, rtol=1e-13, atol=1e-15)
+
+
+def _perturbed(p, name, d, h):
+    q = dict(p)
+    q[name] = p[name] + h * d
+    return q
+
+
+def test_backward_matches_central_differences():
+    """Hand-derived reverse mode vs central finite differences in FP64
+    (h = 1e-6): directional derivatives along a random direction of every
+    tensor, plus 40 single entries, and the gradient w.r.t. the inputs."""
+    nx, ny = 4, 4
+    p = gnn.unpack(_params(15, bias=0.2))
+    f = _state(nx, ny, 10, u0=0.08, amp=5e-2)
+    rng = np.random.default_rng(4)
+    dy = rng.standard_normal((nx * ny, 10))
+    J = lambda pp, ff: float(np.sum(dy * gnn.forward(ff, pp)[0]))
+    _, cache = gnn.forward(f, p)
+    g, df = gnn.backward(dy, cache, p)
+    h = 1e-6
+    for name, shape in gnn.SHAPES:
+        d = rng.standard_normal(shape)
+        fd = (J(_perturbed(p, name, d, h), f) - J(_perturbed(p, name, d, -h), f)) / (2 * h)
+        an = float(np.sum(g[name] * d))
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (name, fd, an)
+    names = [n for n, _ in gnn.SHAPES]
+    for _ in range(40):
+        name = names[rng.integers(len(names))]
+        shape = dict(gnn.SHAPES)[name]
+        d = np.zeros(shape)
+        idx = tuple(int(rng.integers(s)) for s in shape)
+        d[idx] = 1.0
+        hs = 1e-4                    # |J| ~ 1e2: keep the round-off eps|J|/h small
+        fd = (J(_perturbed(p, name, d, hs), f) - J(_perturbed(p, name, d, -hs), f)) / (2 * hs)
+        assert abs(fd - g[name][idx]) <= 1e-6 * max(abs(g[name][idx]), 1e-2), (name, idx)
+    # inputs: relative step on the populations
+    d = rng.standard_normal(f.shape) * 1e-2
+    hf = 1e-5
+    fd = (J(p, f + hf * d) - J(p, f - hf * d)) / (2 * hf)
+    an = float(np.sum(df * d.reshape(9, -1)))
+    assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+
+
+def test_collide_loss_gradient_matches_central_differences():
+    """Eq. 3 + Eq. 4: dL/dy from collide_loss vs central differences in y."""
+    nx, ny = 4, 3
+    p = gnn.unpack(_params(16, s_df=1e-3))
+    f = _state(nx, ny, 11)
+    target = _state(nx, ny, 12)
+    rng = np.random.default_rng(5)
+    y = rng.standard_normal((nx * ny, 10))
+    taus = 0.6 + 0.3 * rng.random(nx * ny)
+    loss, dy, _ = gnn.collide_loss(f, y, taus, target, p)
+    h = 1e-6
+    for _ in range(30):
+        n, c = int(rng.integers(nx * ny)), int(rng.integers(10))
+        yp, ym = y.copy(), y.copy()
+        yp[n, c] += h
+        ym[n, c] -= h
+        fd = (gnn.collide_loss(f, yp, taus, target, p)[0] - gnn.collide_loss(f, ym, taus, target, p)[0]) / (2 * h)
+        assert abs(fd - dy[n, c]) <= 1e-6 * abs(dy[n, c]) + 1e-14, (n, c, fd, dy[n, c])
+
+
+def test_collide_loss_reduces_to_mse_of_eq3():
+    """Eq. 4 is the mean over nodes x 9 of the squared difference of the Eq. 3
+    output from the target; with y = 0 Eq. 3 is the BGK collision."""
+    p = gnn.unpack(inputs.zero_params())
+    f = _state(5, 4, 13)
+    target = _state(5, 4, 14)
+    loss, _, f_pred = gnn.collide_loss(f, np.zeros((20, 10)), 0.8, target, p)
+    assert np.allclose(f_pred.reshape(9, 4, 5), lbm.bgk_collide(f, 0.8), rtol=0, atol=1e-16)
+    assert abs(loss - np.mean((lbm.bgk_collide(f, 0.8) - target) ** 2)) < 1e-18
