@@ -1,0 +1,349 @@
+"""Benchmark of the LBM-GNN hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  A "step" is one lattice update of the
+Taylor-Green workload 4096 x 4096 (periodic, FP32 SoA populations, u0 = 0.05,
+k = 2 pi / 4096), timed with CUDA events on the stream the kernels run on;
+`value` is million lattice-node updates per second (MLUPS) over all ranks.
+Each rank advances its own lattice (weak scaling, no collective on the data
+path).  The GNN-LBM step on the 1024 x 1024 TGV (Re = 1000) is measured in
+the same run and reported beside it under "gnn".
+
+`--impl reference` times the FP64 CPU oracle (the slow, obviously-correct
+restatement of the method) on the host cores, one bounded sub-lattice per
+step, and prints the same line with "impl": "reference".
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS, plain BGK vs GNN-LBM on 1 GB300, at stated TGV velocity L2 error"
+N_SIDE = 4096
+U0 = 0.05
+TAU = 0.8
+TAU_SWEEP = (0.8, 0.5614, 0.5005)
+BYTES_PER_NODE = 72  # 9 FP32 loads + 9 FP32 stores
+
+# DRAM bytes per launch from one ncu capture of the kernel, keyed by the
+# SHA-256 of its source file at capture time; ignored once the source changed.
+NCU_TRAFFIC = {}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _src_sha(name):
+    with open(os.path.join(ROOT, "paper_2504_14494_gb300", "csrc", name), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+def _re(tau, n=N_SIDE, u0=U0):
+    return u0 * n / ((tau - 0.5) / 3.0)
+
+
+class ClockSampler:
+    """Samples SM clock and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2504_14494_gb300 import build, lib as L
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    build.build()
+    L.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    n = args.side
+    nodes = n * n
+    s = L.shape(n, n)
+    k = 2 * np.pi / n
+    stream = torch.cuda.current_stream()
+    fa = torch.empty(9 * nodes, dtype=torch.float32, device=dev)
+    fb = torch.empty_like(fa)
+    L.lbm_init_tgv(fa, s, 1.0, U0, k, k, False)
+
+    def steps(count, tau, bufs):
+        for _ in range(count):
+            L.lbm_step_bgk(bufs[0], bufs[1], None, s, tau, nsteps=1)
+            bufs.reverse()
+
+    bufs = [fa, fb]
+    steps(args.warmup, TAU, bufs)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        steps(args.steps, TAU, bufs)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    t_max = ms
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    done_steps = args.warmup + args.steps
+    assert L.lbm_get_status() == 0
+    if args.only == "bgk":
+        if rank == 0:
+            print(json.dumps({"case": f"bgk {n}x{n}", "ms_per_step": ms / args.steps,
+                              "mlups": nodes * args.steps / (ms / 1e3) / 1e6}))
+        return None
+
+    # TGV velocity L2 error of the state after done_steps steps (closed form).
+    rho = torch.empty(nodes, device=dev)
+    ux = torch.empty(nodes, device=dev)
+    uy = torch.empty(nodes, device=dev)
+    L.lbm_moments(bufs[0], s, rho, ux, uy)
+    xs = torch.arange(n, device=dev, dtype=torch.float64)
+    decay = float(np.exp(-((TAU - 0.5) / 3.0) * 2 * k * k * done_steps))
+    uxa = (U0 * decay * torch.cos(k * xs)[None, :] * torch.sin(k * xs)[:, None]).reshape(-1)
+    uya = (-U0 * decay * torch.sin(k * xs)[None, :] * torch.cos(k * xs)[:, None]).reshape(-1)
+    l2 = float(torch.sqrt(((ux.double() - uxa) ** 2 + (uy.double() - uya) ** 2).sum()
+                          / (uxa ** 2 + uya ** 2).sum()).item())
+
+    # tau sweep (same lattice, fresh TGV state each)
+    sweep = []
+    for tau in TAU_SWEEP:
+        L.lbm_init_tgv(fa, s, 1.0, U0, k, k, False)
+        b2 = [fa, fb]
+        steps(max(3, args.warmup), tau, b2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kk = max(10, min(args.steps, 2000))
+        e0.record(stream)
+        steps(kk, tau, b2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sweep.append({"tau": tau, "re": round(_re(tau), 1),
+                      "mlups": round(nodes * kk / (e0.elapsed_time(e1) / 1e3) / 1e6, 1)})
+
+    # end to end through the C ABI with host buffers: per step the state is
+    # copied from pinned host memory, stepped, and its FP64 totals read back.
+    host_in = torch.empty(9 * nodes, dtype=torch.float32, pin_memory=True)
+    host_in.copy_(fa)
+    host_tot = torch.empty(5, dtype=torch.float64, pin_memory=True)
+    tot = torch.empty(5, dtype=torch.float64, device=dev)
+    ke = max(3, min(args.steps, 30))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(ke):
+        fa.copy_(host_in, non_blocking=True)
+        L.lbm_step_bgk(fa, fb, None, s, TAU, nsteps=1, totals=tot)
+        host_tot.copy_(tot, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / ke
+
+    gnn = gnn_bench(args, L, dev, stream)
+
+    if rank != 0:
+        return None
+    peak, peak_kind = _peaks()
+    ms_step = t_max / args.steps
+    achieved = BYTES_PER_NODE * nodes / (ms / args.steps / 1e3) / 1e9
+    sha = _src_sha("bgk.cu")
+    tr = NCU_TRAFFIC.get("bgk_step_x4")
+    traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == sha else None
+    out = {
+        "metric": METRIC,
+        "value": round(world * nodes * args.steps / (t_max / 1e3) / 1e6, 1),
+        "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "tgv_bgk_4096x4096", "nx": n, "ny": n, "tau": TAU,
+                   "re": round(_re(TAU), 1), "u0": U0, "k": "2*pi/4096",
+                   "l2_flush": "inputs larger than L2 (604 MB per population buffer)",
+                   "parallelism": f"replicas x{world}"},
+        "tgv_l2_error": l2, "tgv_steps_run": done_steps,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_kind": peak_kind, "kernel": "bgk_step_x4",
+                     "algorithmic_bytes_per_launch": BYTES_PER_NODE * nodes},
+        "tau_sweep": sweep,
+        "e2e": {"value": round(nodes / (e2e_ms / 1e3) / 1e6, 1), "unit": "MLUPS",
+                "h2d_bytes_per_step": 9 * nodes * 4, "d2h_bytes_per_step": 5 * 8},
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps,
+        "gnn": gnn,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    return out
+
+
+def gnn_bench(args, L, dev, stream):
+    """GNN-LBM MLUPS on the 1024^2 TGV beside BGK on the same lattice."""
+    if not hasattr(L, "lbm_step_gnn"):
+        return {"status": "not built"}
+    return L.bench_gnn_step(args, dev, stream)
+
+
+def cpu_baseline(budget_s=12.0):
+    """The FP64 oracle BGK step, as it stands, on a bounded sample: a periodic
+    TGV sub-lattice of 1024 x 1024 nodes stepped until ~budget_s of CPU time
+    (numpy, one thread)."""
+    from oracle import lbm
+    n = 1024
+    k = 2 * np.pi / n
+    f = lbm.tgv_init(n, n, 1.0, U0, k, k)
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        f = lbm.bgk_step(f, TAU)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(n * n * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": 1,
+            "kind": "oracle",
+            "sample": f"oracle.lbm.bgk_step (numpy FP64) on a 1024x1024 TGV sub-lattice, "
+                      f"{steps} steps, {dt:.1f} s"}
+
+
+def run_reference(args, rank):
+    """The CPU oracle arm: each step is one oracle BGK step on a sub-lattice
+    sized so that the whole run takes about two minutes."""
+    if rank != 0:
+        return None
+    from oracle import lbm
+    total = args.warmup + args.steps
+    # measured oracle throughput on this host, to size the per-step sample
+    probe = lbm.tgv_init(256, 256, 1.0, U0, 2 * np.pi / 256, 2 * np.pi / 256)
+    t0 = time.perf_counter()
+    lbm.bgk_step(probe, TAU)
+    rate = 256 * 256 / max(time.perf_counter() - t0, 1e-6)
+    per_step = 120.0 / total
+    side = int(np.sqrt(rate * per_step) // 64 * 64)
+    side = max(64, min(N_SIDE, side))
+    k = 2 * np.pi / side
+    f = lbm.tgv_init(side, side, 1.0, U0, k, k)
+    for _ in range(args.warmup):
+        f = lbm.bgk_step(f, TAU)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = lbm.bgk_step(f, TAU)
+    dt = time.perf_counter() - t0
+    val = round(side * side * args.steps / dt / 1e6, 3)
+    sample = (f"oracle.lbm.bgk_step (numpy FP64, 1 thread) on a {side}x{side} TGV sub-lattice "
+              f"of the 4096x4096 workload per step")
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "tgv_bgk_4096x4096", "nx": N_SIDE, "ny": N_SIDE,
+                       "tau": TAU, "u0": U0, "sample_side": side},
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["bgk", "gnn"], default=None,
+                    help="time one kernel family only (profiling runs)")
+    ap.add_argument("--side", type=int, default=N_SIDE, help="lattice side for --only runs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.only is None and args.side != N_SIDE:
+        ap.error("--side applies to --only runs")
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+    if out is not None and rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,108 @@
+/* lbmgnn.h -- C ABI of the GB300 (sm_103a) LBM-GNN library, liblbmgnn.so.
+ *
+ * The library advances D2Q9 lattice Boltzmann populations with the BGK
+ * collision (paper Sec. 2.1, Eq. 1-2, Fig. 1) or with the GNN-enhanced
+ * collision (Sec. 2.2-2.3, Eq. 3), and trains that network (Sec. 2.4, Eq. 4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Pointers named f, f_in, f_out, ... are DEVICE pointers to caller-owned
+ *    memory.  The library allocates nothing unless a call says so.
+ *  - Population layout (SoA, q-major): the value of direction q at node (x, y)
+ *    of lattice b is  f[q * plane_stride + (b * ny + y) * nx + x],  with
+ *    0 <= q < 9, 0 <= b < nb.  plane_stride = 0 means nb * ny * nx.
+ *  - D2Q9 order: e_0=(0,0); e_1..4=(1,0),(0,1),(-1,0),(0,-1);
+ *    e_5..8=(1,1),(-1,1),(-1,-1),(1,-1); w = 4/9, 1/9 (x4), 1/36 (x4).
+ *  - Stored state: the POST-collision populations f*(., n).  One step pulls
+ *    f_i(x) = f*_i(x - e_i) with periodic wrap inside each lattice (streaming),
+ *    collides, and stores f*(., n+1) at x.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on it; arguments are checked on the host before any launch.
+ *  - Every call returns an int status: LBM_OK or a negative LBM_ERR_* code.
+ *    Faults detected inside kernels (non-finite values, a device wait that
+ *    gave up, an index that failed a bounds check) raise bits of a per-device
+ *    status word, which lbm_get_status() reports and clears.
+ *  - The library never aborts or prints.
+ */
+#ifndef LBMGNN_H
+#define LBMGNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,        /* NULL pointer, bad enum, nsteps < 0, ... */
+  LBM_ERR_ALIAS = -2,      /* an output buffer aliases an input buffer */
+  LBM_ERR_SIZE = -3,       /* nx, ny, nb or plane_stride out of range */
+  LBM_ERR_TAU = -4,        /* tau <= 1/2 (negative viscosity) or not finite */
+  LBM_ERR_BLOB = -5,       /* parameter blob of the wrong size or version */
+  LBM_ERR_CUDA = -6,       /* a CUDA runtime call failed */
+  LBM_ERR_NONFINITE = -7,  /* a kernel produced a NaN or Inf population */
+  LBM_ERR_TIMEOUT = -8,    /* a device-side wait gave up */
+  LBM_ERR_BOUNDS = -9,     /* a device-side bounds check failed */
+  LBM_ERR_WORKSPACE = -10  /* workspace missing or smaller than required */
+};
+
+typedef struct {
+  int32_t nx, ny;        /* nodes per lattice in x and y, each >= 1 */
+  int32_t nb;            /* number of stacked lattices, >= 1 */
+  int64_t plane_stride;  /* elements between planes; 0 = nb*ny*nx */
+} lbm_shape;
+
+/* Human-readable name of a status code (static string). */
+LBM_API const char* lbm_status_string(int status);
+
+/* Waits for `stream`, then reads and clears the device status word of the
+ * current device.  Returns LBM_OK, or the most severe of LBM_ERR_TIMEOUT,
+ * LBM_ERR_BOUNDS, LBM_ERR_NONFINITE raised since the last call. */
+LBM_API int lbm_get_status(void* stream);
+
+/* Taylor-Green vortex initial state (paper Sec. 3.2; the formula is this
+ * library's reading): u_x = u0 cos(kx x) sin(ky y), u_y = -u0 sin(kx x)
+ * cos(ky y) at integer node coordinates, rho = rho0 or, if
+ * pressure_consistent, rho0 (1 - 3/4 u0^2 (cos 2kx x + cos 2ky y));
+ * f = f^eq(rho, u) (Eq. 2), evaluated in FP64 and stored as FP32 in every
+ * lattice of the stack.  f: device, 9 planes of shape s. */
+LBM_API int lbm_init_tgv(float* f, lbm_shape s, double rho0, double u0, double kx, double ky,
+                 int pressure_consistent, void* stream);
+
+/* nsteps BGK steps (Eq. 1 with the equilibrium of Eq. 2, Fig. 1 loop):
+ * pull-stream with periodic wrap, moments, f^eq, relaxation
+ * f* = f - (f - f^eq)/tau, store.  One fused kernel per step.
+ *   f_in   device, read only; the state after n steps.
+ *   f_out  device; receives the state after n + nsteps steps.  != f_in.
+ *   f_tmp  device ping-pong buffer of the same shape, required when
+ *          nsteps > 1 (else may be NULL); distinct from f_in and f_out.
+ *   tau    relaxation time (> 1/2) of every lattice, used when `taus` is NULL.
+ *   taus   optional device float[nb]: per-lattice relaxation times.
+ *   totals optional device double[5]; if given it is OVERWRITTEN with FP64
+ *          sums over the final state: mass, x-momentum, y-momentum, kinetic
+ *          energy 1/2 sum |rho u|^2/rho, and the number of nodes holding a
+ *          non-finite value (such nodes are left out of the four sums).
+ * nsteps == 0 copies f_in to f_out.  A non-finite output raises
+ * LBM_ERR_NONFINITE in the status word only when totals are requested. */
+LBM_API int lbm_step_bgk(const float* f_in, float* f_out, float* f_tmp, lbm_shape s, float tau,
+                 const float* taus, int nsteps, double* totals, void* stream);
+
+/* Macroscopic variables of a stored state (Fig. 1 'Compute macroscopic
+ * variables'): rho = sum f_i, u = sum f_i e_i / rho per node (FP32 out,
+ * node-major planes of nb*ny*nx values), and optional FP64 totals (as in
+ * lbm_step_bgk).  Any of rho, ux, uy, totals may be NULL. */
+LBM_API int lbm_moments(const float* f, lbm_shape s, float* rho, float* ux, float* uy,
+                double* totals, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBMGNN_H */

@@ -159,14 +159,16 @@ def velocity_l2_error(ux, uy, ux_a, uy_a):
 
 def totals(f):
     """Domain totals in FP64: mass, momentum x, momentum y, kinetic energy
-    E = 1/2 sum rho |u|^2 = 1/2 sum |rho u|^2 / rho, and the count of
-    non-finite population values."""
+    E = 1/2 sum rho |u|^2 = 1/2 sum |rho u|^2 / rho, and the number of nodes
+    holding a non-finite population (those nodes are left out of the sums)."""
     f = np.asarray(f, dtype=np.float64)
+    bad = ~np.all(np.isfinite(f), axis=0)
+    f = np.where(bad[None], 0.0, f)
     rho = f.sum(axis=0)
     jx = sum(E[i, 0] * f[i] for i in range(Q))
     jy = sum(E[i, 1] * f[i] for i in range(Q))
-    energy = 0.5 * np.sum((jx * jx + jy * jy) / rho)
-    nonfinite = int(np.count_nonzero(~np.isfinite(f)))
+    energy = 0.5 * np.sum(np.where(bad, 0.0, (jx * jx + jy * jy) / np.where(bad, 1.0, rho)))
+    nonfinite = int(np.count_nonzero(bad))
     return np.array([rho.sum(), jx.sum(), jy.sum(), energy, float(nonfinite)])
 
 

@@ -1,0 +1,8 @@
+"""GB300-native (sm_103a) LBM-GNN: the D2Q9 BGK step and the GNN-enhanced
+collision of arXiv 2504.14494 behind the C ABI of liblbmgnn.so.
+
+  lib     -- ctypes binding, one Python function per C entry point
+  build   -- in-tree nvcc build of liblbmgnn.so
+  inputs  -- seeded synthetic inputs (weights, perturbations, workloads)
+"""
+from . import lib  # noqa: F401

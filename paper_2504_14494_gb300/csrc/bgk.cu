@@ -1,0 +1,299 @@
+// D2Q9 BGK kernels: Taylor-Green initial state, the fused pull-stream +
+// moments + equilibrium + BGK relaxation step, and the moments/totals pass.
+//
+// Paper: Sec. 2.1 Eq. 1 (BGK), Eq. 2 (equilibrium), Fig. 1 (loop order),
+// Sec. 3.2 (Taylor-Green vortex).
+//
+// The step is HBM-bound: 9 FP32 loads and 9 FP32 stores per node (72 B).
+// The fast kernel gives each warp 128 consecutive nodes of one row (4 per
+// lane, 16-byte vector loads and stores).  The x +- 1 shifted planes reuse
+// the aligned vector of the lane and take the one missing value from the
+// neighbouring lane by a shuffle; the warp's edge lanes fetch it with a
+// scalar load (which also implements the periodic wrap).  Row wrap is a select.
+#include "common.cuh"
+#include "launch.h"
+
+namespace lbmgnn {
+
+__device__ unsigned g_status = 0;
+
+unsigned* status_word() {
+  static unsigned* addr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+    addr[dev] = static_cast<unsigned*>(p);
+  }
+  return addr[dev];
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide FP64 reduction of the five totals into totals[0..4] (atomics).
+template <int NT>
+__device__ __forceinline__ void block_totals(double (&t)[5], double* __restrict__ totals) {
+  __shared__ double red[NT / 32][5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) red[w][k] = t[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) acc += red[i][threadIdx.x];
+    if (acc != 0.0) atomicAdd(totals + threadIdx.x, acc);
+  }
+}
+
+// Totals contribution of one stored node (post-collision values).
+__device__ __forceinline__ void add_node_totals(double (&t)[5], const float (&o)[Q]) {
+  bool finite = true;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) finite &= isfinite(o[i]);
+  if (!finite) {
+    t[4] += 1.0;
+    return;
+  }
+  const Moments m = moments9(o);
+  const double rho = m.rho;
+  const double jx = (double)m.ux * rho, jy = (double)m.uy * rho;
+  t[0] += rho;
+  t[1] += jx;
+  t[2] += jy;
+  t[3] += 0.5 * (jx * jx + jy * jy) / rho;
+}
+
+// BGK collision of one node (Eq. 1 with Eq. 2), in place.
+__device__ __forceinline__ void bgk_collide(float (&f)[Q], float omega) {
+  const Moments m = moments9(f);
+  const float usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i] = f[i] - omega * (f[i] - feq_i(i, m, usq15));
+}
+
+// ---------------------------------------------------------------------------
+// Fast step: nx % 4 == 0, plane stride % 4 == 0, 16-byte aligned buffers.
+template <bool TOTALS>
+__global__ void __launch_bounds__(128) bgk_step_x4(const float* __restrict__ fin,
+                                                   float* __restrict__ fout, Shape s, float tau,
+                                                   const float* __restrict__ taus,
+                                                   double* __restrict__ totals, unsigned* stw) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int nchunk = (s.nx + 127) >> 7;
+  const int64_t rows = (int64_t)s.nb * s.ny;
+  int64_t row = wid / nchunk;
+  const int chunk = (int)(wid - row * nchunk);
+  const bool warp_on = row < rows;
+  if (!warp_on) row = rows - 1;
+  const int x0 = chunk * 128 + lane * 4;
+  const bool on = warp_on && x0 < s.nx;
+  const int xl = on ? x0 : s.nx - 4;  // in-range position for idle lanes
+  const int b = (int)(row / s.ny);
+  const int y = (int)(row - (int64_t)b * s.ny);
+  const int64_t lat = (int64_t)b * s.ny * s.nx;
+  const int ym = (y == 0) ? s.ny - 1 : y - 1;
+  const int yp = (y == s.ny - 1) ? 0 : y + 1;
+  const int64_t r0 = lat + (int64_t)y * s.nx;
+  const int64_t rm = lat + (int64_t)ym * s.nx;  // source row of e_y = +1
+  const int64_t rp = lat + (int64_t)yp * s.nx;  // source row of e_y = -1
+  const int xm = (xl == 0) ? s.nx - 1 : xl - 1;          // source of e_x = +1 (lane edge)
+  const int xr = (xl + 4 >= s.nx) ? xl + 4 - s.nx : xl + 4;  // source of e_x = -1 (lane edge)
+  const bool need_l = (lane == 0);
+  const bool need_r = (lane == 31) || (xl + 4 >= s.nx);
+  const int64_t ps = s.ps;
+
+  auto v4 = [&](int q, int64_t r) {
+    return __ldg(reinterpret_cast<const float4*>(fin + q * ps + r + xl));
+  };
+  const float4 c0 = v4(0, r0), c1 = v4(1, r0), c2 = v4(2, rm), c3 = v4(3, r0), c4 = v4(4, rp);
+  const float4 c5 = v4(5, rm), c6 = v4(6, rm), c7 = v4(7, rp), c8 = v4(8, rp);
+  // lane-edge scalars (predicated loads)
+  float l1 = 0.f, l5 = 0.f, l8 = 0.f, e3 = 0.f, e6 = 0.f, e7 = 0.f;
+  if (need_l) {
+    l1 = __ldg(fin + 1 * ps + r0 + xm);
+    l5 = __ldg(fin + 5 * ps + rm + xm);
+    l8 = __ldg(fin + 8 * ps + rp + xm);
+  }
+  if (need_r) {
+    e3 = __ldg(fin + 3 * ps + r0 + xr);
+    e6 = __ldg(fin + 6 * ps + rm + xr);
+    e7 = __ldg(fin + 7 * ps + rp + xr);
+  }
+  const float s1 = __shfl_up_sync(0xffffffffu, c1.w, 1);
+  const float s5 = __shfl_up_sync(0xffffffffu, c5.w, 1);
+  const float s8 = __shfl_up_sync(0xffffffffu, c8.w, 1);
+  const float s3 = __shfl_down_sync(0xffffffffu, c3.x, 1);
+  const float s6 = __shfl_down_sync(0xffffffffu, c6.x, 1);
+  const float s7 = __shfl_down_sync(0xffffffffu, c7.x, 1);
+  if (!need_l) { l1 = s1; l5 = s5; l8 = s8; }
+  if (!need_r) { e3 = s3; e6 = s6; e7 = s7; }
+
+  float f[4][Q] = {
+      {c0.x, l1, c2.x, c3.y, c4.x, l5, c6.y, c7.y, l8},
+      {c0.y, c1.x, c2.y, c3.z, c4.y, c5.x, c6.z, c7.z, c8.x},
+      {c0.z, c1.y, c2.z, c3.w, c4.z, c5.y, c6.w, c7.w, c8.y},
+      {c0.w, c1.z, c2.w, e3, c4.w, c5.z, e6, e7, c8.z}};
+  const float omega = 1.0f / (taus ? __ldg(taus + b) : tau);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) bgk_collide(f[j], omega);
+  if (on) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      *reinterpret_cast<float4*>(fout + q * ps + r0 + x0) =
+          make_float4(f[0][q], f[1][q], f[2][q], f[3][q]);
+    }
+  }
+  if constexpr (TOTALS) {
+    double t[5] = {0, 0, 0, 0, 0};
+    if (on) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) add_node_totals(t, f[j]);
+    }
+    if (t[4] != 0.0) raise_status(stw, ST_NONFINITE);
+    block_totals<128>(t, totals);
+  }
+}
+
+// General step: any nx, ny, stride, alignment.  One thread per node.
+template <bool TOTALS>
+__global__ void __launch_bounds__(256) bgk_step_any(const float* __restrict__ fin,
+                                                    float* __restrict__ fout, Shape s, float tau,
+                                                    const float* __restrict__ taus,
+                                                    double* __restrict__ totals, unsigned* stw) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool on = n < N;
+  const int64_t nn = on ? n : N - 1;
+  const int x = (int)(nn % s.nx);
+  const int64_t row = nn / s.nx;
+  const int b = (int)(row / s.ny);
+  const int y = (int)(row - (int64_t)b * s.ny);
+  const int64_t lat = (int64_t)b * s.ny * s.nx;
+  float f[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    int xs = x - ex(q), ys = y - ey(q);
+    xs = xs < 0 ? xs + s.nx : (xs >= s.nx ? xs - s.nx : xs);
+    ys = ys < 0 ? ys + s.ny : (ys >= s.ny ? ys - s.ny : ys);
+    f[q] = __ldg(fin + q * s.ps + lat + (int64_t)ys * s.nx + xs);
+  }
+  bgk_collide(f, 1.0f / (taus ? __ldg(taus + b) : tau));
+  if (on) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) fout[q * s.ps + nn] = f[q];
+  }
+  if constexpr (TOTALS) {
+    double t[5] = {0, 0, 0, 0, 0};
+    if (on) add_node_totals(t, f);
+    if (t[4] != 0.0) raise_status(stw, ST_NONFINITE);
+    block_totals<256>(t, totals);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Moments of a stored state and FP64 totals.
+__global__ void __launch_bounds__(256) moments_kernel(const float* __restrict__ f, Shape s,
+                                                      float* __restrict__ rho,
+                                                      float* __restrict__ ux,
+                                                      float* __restrict__ uy,
+                                                      double* __restrict__ totals, unsigned* stw) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool on = n < N;
+  const int64_t nn = on ? n : N - 1;
+  float v[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) v[q] = __ldg(f + q * s.ps + nn);
+  const Moments m = moments9(v);
+  if (on) {
+    if (rho) rho[nn] = m.rho;
+    if (ux) ux[nn] = m.ux;
+    if (uy) uy[nn] = m.uy;
+  }
+  if (totals) {
+    double t[5] = {0, 0, 0, 0, 0};
+    if (on) add_node_totals(t, v);
+    if (t[4] != 0.0) raise_status(stw, ST_NONFINITE);
+    block_totals<256>(t, totals);
+  }
+}
+
+// Taylor-Green initial state, FP64 arithmetic, FP32 store.
+__global__ void __launch_bounds__(256) tgv_init_kernel(float* __restrict__ f, Shape s, double rho0,
+                                                       double u0, double kx, double ky, int pc) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int x = (int)(n % s.nx);
+  const int y = (int)((n / s.nx) % s.ny);
+  double sx, cx, sy, cy;
+  sincos(kx * x, &sx, &cx);
+  sincos(ky * y, &sy, &cy);
+  const double ux = u0 * cx * sy;
+  const double uy = -u0 * sx * cy;
+  double rho = rho0;
+  if (pc) rho = rho0 * (1.0 - 0.75 * u0 * u0 * ((cx * cx - sx * sx) + (cy * cy - sy * sy)));
+  const double usq = ux * ux + uy * uy;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const double eu = ex(q) * ux + ey(q) * uy;
+    const double w = q == 0 ? 4.0 / 9.0 : (q <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    f[q * s.ps + n] = (float)(w * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+static inline bool x4_ok(const float* a, const float* b, const Shape& s) {
+  return (s.nx % 4 == 0) && (s.ps % 4 == 0) && ((uintptr_t)a % 16 == 0) &&
+         ((uintptr_t)b % 16 == 0);
+}
+
+cudaError_t launch_bgk_step(const float* fin, float* fout, const Shape& s, float tau,
+                            const float* taus, double* totals, cudaStream_t st) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  unsigned* stw = status_word();
+  if (totals && !stw) return cudaErrorInvalidDevice;
+  if (x4_ok(fin, fout, s)) {
+    const int64_t warps = (int64_t)s.nb * s.ny * ((s.nx + 127) / 128);
+    const unsigned blocks = (unsigned)((warps + 3) / 4);
+    if (totals)
+      bgk_step_x4<true><<<blocks, 128, 0, st>>>(fin, fout, s, tau, taus, totals, stw);
+    else
+      bgk_step_x4<false><<<blocks, 128, 0, st>>>(fin, fout, s, tau, taus, totals, stw);
+  } else {
+    const unsigned blocks = (unsigned)((N + 255) / 256);
+    if (totals)
+      bgk_step_any<true><<<blocks, 256, 0, st>>>(fin, fout, s, tau, taus, totals, stw);
+    else
+      bgk_step_any<false><<<blocks, 256, 0, st>>>(fin, fout, s, tau, taus, totals, stw);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const float* f, const Shape& s, float* rho, float* ux, float* uy,
+                           double* totals, cudaStream_t st) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  unsigned* stw = status_word();
+  if (totals && !stw) return cudaErrorInvalidDevice;
+  moments_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(f, s, rho, ux, uy, totals, stw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tgv_init(float* f, const Shape& s, double rho0, double u0, double kx,
+                            double ky, int pc, cudaStream_t st) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  tgv_init_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(f, s, rho0, u0, kx, ky, pc);
+  return cudaGetLastError();
+}
+
+}  // namespace lbmgnn

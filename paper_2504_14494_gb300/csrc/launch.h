@@ -1,0 +1,16 @@
+// Internal launchers shared between the kernel files and the C ABI layer.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace lbmgnn {
+
+cudaError_t launch_bgk_step(const float* fin, float* fout, const Shape& s, float tau,
+                            const float* taus, double* totals, cudaStream_t st);
+cudaError_t launch_moments(const float* f, const Shape& s, float* rho, float* ux, float* uy,
+                           double* totals, cudaStream_t st);
+cudaError_t launch_tgv_init(float* f, const Shape& s, double rho0, double u0, double kx,
+                            double ky, int pc, cudaStream_t st);
+
+}  // namespace lbmgnn

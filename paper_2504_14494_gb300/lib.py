@@ -1,0 +1,124 @@
+"""Thin ctypes binding of liblbmgnn.so (argument marshalling only).
+
+Every function here has the name and argument order of the C entry point in
+include/lbmgnn.h.  Buffer arguments accept a torch tensor (its data_ptr() is
+passed), a raw integer address, or None for a NULL pointer.  `stream`
+defaults to torch's current CUDA stream.  A non-zero status raises LbmError.
+
+There is no fallback: if the shared library is missing or cannot be loaded,
+every call raises.
+"""
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbmgnn.so")
+
+_lib = None
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})" if what else
+                         f"{status_string(code)} ({code})")
+
+
+class lbm_shape(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nb", ctypes.c_int32),
+                ("plane_stride", ctypes.c_int64)]
+
+
+def shape(nx, ny, nb=1, plane_stride=0):
+    return lbm_shape(int(nx), int(ny), int(nb), int(plane_stride))
+
+
+_VP = ctypes.c_void_p
+_SIGS = {
+    "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "lbm_get_status": (ctypes.c_int, [_VP]),
+    "lbm_init_tgv": (ctypes.c_int, [_VP, lbm_shape, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_int, _VP]),
+    "lbm_step_bgk": (ctypes.c_int, [_VP, _VP, _VP, lbm_shape, ctypes.c_float, _VP, ctypes.c_int,
+                                    _VP, _VP]),
+    "lbm_moments": (ctypes.c_int, [_VP, lbm_shape, _VP, _VP, _VP, _VP, _VP]),
+}
+
+
+def load(path=None):
+    """Load the shared library (once).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "paper_2504_14494_gb300.build.build() (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names bound by this module (each must be exported by the library)."""
+    return list(_SIGS)
+
+
+def register(name, restype, argtypes):
+    """Declare one more entry point (used by the other binding modules)."""
+    _SIGS[name] = (restype, argtypes)
+    if _lib is not None:
+        fn = getattr(_lib, name)
+        fn.restype = restype
+        fn.argtypes = argtypes
+
+
+def ptr(x):
+    """Device/host address of a tensor, an int, or None (NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def stream_ptr(stream=None):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def check(rc, what=""):
+    if rc != 0:
+        raise LbmError(rc, what)
+    return rc
+
+
+def status_string(code):
+    return load().lbm_status_string(int(code)).decode()
+
+
+# --- BGK path ------------------------------------------------------------------------
+def lbm_get_status(stream=None):
+    """Synchronise the stream and return (not raise) the device status code."""
+    return load().lbm_get_status(stream_ptr(stream))
+
+
+def lbm_init_tgv(f, s, rho0, u0, kx, ky, pressure_consistent=False, stream=None):
+    check(load().lbm_init_tgv(ptr(f), s, rho0, u0, kx, ky, int(bool(pressure_consistent)),
+                              stream_ptr(stream)), "lbm_init_tgv")
+
+
+def lbm_step_bgk(f_in, f_out, f_tmp, s, tau, taus=None, nsteps=1, totals=None, stream=None):
+    check(load().lbm_step_bgk(ptr(f_in), ptr(f_out), ptr(f_tmp), s, float(tau), ptr(taus),
+                              int(nsteps), ptr(totals), stream_ptr(stream)), "lbm_step_bgk")
+
+
+def lbm_moments(f, s, rho=None, ux=None, uy=None, totals=None, stream=None):
+    check(load().lbm_moments(ptr(f), s, ptr(rho), ptr(ux), ptr(uy), ptr(totals),
+                             stream_ptr(stream)), "lbm_moments")

@@ -1,0 +1,68 @@
+"""The C ABI library builds, loads and exports every entry point declared in
+include/*.h; host-side argument checks return their codes without touching a
+GPU (no compute call is made here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2504_14494_gb300 import lib as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        names += re.findall(r"LBM_API\s+[\w\s\*]+?\b(\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lbmlib):
+    names = _declared()
+    assert "lbm_step_bgk" in names and len(names) >= 5
+    so = ctypes.CDLL(L.LIB_PATH)
+    for n in names:
+        assert hasattr(so, n), n
+
+
+def test_binding_covers_every_declared_symbol(lbmlib):
+    assert set(_declared()) <= set(L.exported_symbols())
+
+
+def test_status_strings(lbmlib):
+    for code in range(0, -11, -1):
+        s = L.status_string(code)
+        assert s and s != "unknown status"
+    assert L.status_string(-99) == "unknown status"
+
+
+def test_host_argument_checks(lbmlib):
+    so = L.load()
+    s = L.shape(8, 8)
+    # NULL buffers
+    assert so.lbm_step_bgk(None, 1 << 20, None, s, 0.8, None, 1, None, None) == -1
+    # bad sizes and plane stride
+    assert so.lbm_step_bgk(1 << 20, 1 << 24, None, L.shape(0, 8), 0.8, None, 1, None, None) == -3
+    assert so.lbm_step_bgk(1 << 20, 1 << 24, None, L.shape(8, 8, 1, 10), 0.8, None, 1, None, None) == -3
+    # in == out, overlapping tmp
+    assert so.lbm_step_bgk(1 << 20, 1 << 20, None, s, 0.8, None, 1, None, None) == -2
+    assert so.lbm_step_bgk(1 << 20, 1 << 24, (1 << 20) + 64, s, 0.8, None, 2, None, None) == -2
+    # missing tmp for nsteps > 1, negative steps
+    assert so.lbm_step_bgk(1 << 20, 1 << 24, None, s, 0.8, None, 2, None, None) == -1
+    assert so.lbm_step_bgk(1 << 20, 1 << 24, None, s, 0.8, None, -1, None, None) == -1
+    # tau <= 1/2 or NaN
+    assert so.lbm_step_bgk(1 << 20, 1 << 24, None, s, 0.5, None, 1, None, None) == -4
+    assert so.lbm_step_bgk(1 << 20, 1 << 24, None, s, float("nan"), None, 1, None, None) == -4
+    assert so.lbm_init_tgv(None, s, 1.0, 0.01, 0.1, 0.1, 0, None) == -1
+    assert so.lbm_init_tgv(1 << 20, s, -1.0, 0.01, 0.1, 0.1, 0, None) == -1
+    assert so.lbm_moments(None, s, None, None, None, None, None) == -1
+
+
+def test_binding_raises_on_error(lbmlib):
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_step_bgk(None, None, None, L.shape(4, 4), 0.8, stream=0)
+    assert ei.value.code == -1
