@@ -102,6 +102,73 @@ LBM_API int lbm_step_bgk(const float* f_in, float* f_out, float* f_tmp, lbm_shap
 LBM_API int lbm_moments(const float* f, lbm_shape s, float* rho, float* ux, float* uy,
                 double* totals, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * GNN-enhanced collision (paper Sec. 2.2-2.3, Fig. 2, Eq. 3)
+ *
+ * Network (this library's reading of Sec. 2.2, whose components the paper
+ * names without formulas): features x = [f_0..f_8, rho, u_x, u_y] of the
+ * pre-collision node, normalised (x - mu)/sigma; encoder 12-64-64 (Linear +
+ * GELU twice); two message-passing rounds over the 8 lattice neighbours
+ * j = i + e_k with m_ik = GELU(W_e [h_i; h_j; e_k] + b_e), a_i = sum_k m_ik,
+ * h_i <- h_i + GELU(W_n [h_i; a_i] + b_n) (separate weights per round); head
+ * y = W_h h + b_h (10 outputs); tau_adj = 1/2 + sigmoid(y_0) in (1/2, 3/2)
+ * and Delta f_i = s_df y_{1+i} (Fig. 2 heads); f*_i = f_i - (f_i - f_i^eq) /
+ * (tau tau_adj) + Delta f_i (Eq. 3).  GELU is the tanh form.
+ *
+ * Parameter vector (FP32, `params`), in this order:
+ *   enc1.W[64][12] enc1.b[64] enc2.W[64][64] enc2.b[64]
+ *   round 1: edge.W[64][130] edge.b[64] node.W[64][128] node.b[64]
+ *   round 2: same shapes
+ *   head.W[10][64] head.b[10]                     -> 38,922 trainable values
+ *   mu[12] sigma[12] s_df                         -> 25 fixed values
+ * Row-major W[out][in]; edge.W columns are [h_i (64) | h_j (64) | e_k (2)],
+ * node.W columns are [h_i (64) | a_i (64)].
+ * Weight matrices are used as BF16 (round to nearest even); biases and the
+ * fixed values as FP32.  Dense layers run on the tensor cores with FP32
+ * accumulation; activations are stored as BF16.
+ * ------------------------------------------------------------------------- */
+
+/* Number of floats of the parameter vector (38,947) and of its trainable
+ * prefix (38,922). */
+LBM_API size_t gnn_param_count(void);
+LBM_API size_t gnn_trainable_count(void);
+
+/* Bytes of the packed device image of the parameters. */
+LBM_API size_t gnn_packed_bytes(void);
+
+/* Converts the FP32 parameter vector (device, gnn_param_count() floats) into
+ * the packed image the kernels read (device, gnn_packed_bytes() bytes,
+ * 16-byte aligned).  Re-run after every change of the parameters. */
+LBM_API int gnn_pack(const float* params, void* packed, void* stream);
+
+/* Workspace bytes lbm_step_gnn needs for shape s (768 bytes per node). */
+LBM_API size_t gnn_step_workspace_bytes(lbm_shape s);
+
+/* One GNN-LBM step (Fig. 1 with 'Use GNN?' = yes): pull-stream f_in with
+ * periodic wrap, run the network on the pre-collision state, apply Eq. 3 and
+ * store f*(n+1) in f_out.
+ *   f_in, f_out  device populations of shape s; f_out != f_in.
+ *   tau / taus   as in lbm_step_bgk.
+ *   packed       device image from gnn_pack.
+ *   totals       optional device double[5] (as in lbm_step_bgk), of f_out.
+ *   workspace    device scratch of ws_bytes >= gnn_step_workspace_bytes(s),
+ *                16-byte aligned; contents undefined afterwards. */
+LBM_API int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape s, float tau,
+                         const float* taus, const void* packed, double* totals,
+                         void* workspace, size_t ws_bytes, void* stream);
+
+/* Bytes of the activations gnn_forward saves for gnn_backward
+ * (1,152 bytes per node): BF16 h0, h1, h2 [N][64], a0, a1 [N][64],
+ * AB0, AB1 [N][128] (A = W_a h | B = W_b h of each round). */
+LBM_API size_t gnn_saved_bytes(lbm_shape s);
+
+/* Network forward on PRE-collision populations f_pre (device, shape s):
+ * writes the head output y (device FP32 [10][N], N = nb*ny*nx, plane o holds
+ * output o of every node) and the saved activations (device, 16-byte
+ * aligned, gnn_saved_bytes(s) bytes). */
+LBM_API int gnn_forward(const float* f_pre, lbm_shape s, const void* packed, void* saved,
+                        float* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,153 @@
+// C ABI entry points of the GNN path (forward).  See include/lbmgnn.h.
+#include <cmath>
+
+#include "common.cuh"
+#include "gnn.cuh"
+#include "gnn_launch.h"
+#include "launch.h"
+
+using namespace lbmgnn;
+
+namespace {
+
+int check_shape_g(const lbm_shape& s, Shape* out) {
+  if (s.nx < 1 || s.ny < 1 || s.nb < 1) return LBM_ERR_SIZE;
+  const int64_t n = (int64_t)s.nx * s.ny * s.nb;
+  if (n > (int64_t(1) << 34)) return LBM_ERR_SIZE;
+  const int64_t ps = s.plane_stride == 0 ? n : s.plane_stride;
+  if (ps < n) return LBM_ERR_SIZE;
+  *out = Shape{s.nx, s.ny, s.nb, ps};
+  return LBM_OK;
+}
+
+int64_t nodes(const Shape& s) { return (int64_t)s.nb * s.ny * s.nx; }
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+bool overlap(const void* a, int64_t na, const void* b, int64_t nb) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + nb && pb < pa + na;
+}
+
+int64_t f_bytes(const Shape& s) { return (8 * s.ps + nodes(s)) * (int64_t)sizeof(float); }
+
+}  // namespace
+
+extern "C" {
+
+size_t gnn_param_count(void) { return P::TOTAL; }
+size_t gnn_trainable_count(void) { return P::TRAINABLE; }
+size_t gnn_packed_bytes(void) { return K::TOTAL; }
+
+int gnn_pack(const float* params, void* packed, void* stream) {
+  if (!params || !packed) return LBM_ERR_ARG;
+  if (!aligned(packed, 16)) return LBM_ERR_ARG;
+  if (cudaMemsetAsync(packed, 0, K::TOTAL, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  return launch_gnn_pack(params, static_cast<uint8_t*>(packed),
+                         static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? LBM_OK
+             : LBM_ERR_CUDA;
+}
+
+size_t gnn_step_workspace_bytes(lbm_shape shape) {
+  Shape s;
+  if (check_shape_g(shape, &s)) return 0;
+  return (size_t)nodes(s) * 768;
+}
+
+int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape shape, float tau, const float* taus,
+                 const void* packed, double* totals, void* workspace, size_t ws_bytes,
+                 void* stream) {
+  Shape s;
+  if (!f_in || !f_out || !packed) return LBM_ERR_ARG;
+  if (int r = check_shape_g(shape, &s)) return r;
+  if (!taus && (!std::isfinite(tau) || !(tau > 0.5f))) return LBM_ERR_TAU;
+  if (!aligned(packed, 16)) return LBM_ERR_ARG;
+  const int64_t N = nodes(s);
+  if (!workspace || ws_bytes < (size_t)N * 768) return LBM_ERR_WORKSPACE;
+  if (!aligned(workspace, 16)) return LBM_ERR_WORKSPACE;
+  if (overlap(f_in, f_bytes(s), f_out, f_bytes(s))) return LBM_ERR_ALIAS;
+  if (overlap(workspace, N * 768, f_in, f_bytes(s)) ||
+      overlap(workspace, N * 768, f_out, f_bytes(s)))
+    return LBM_ERR_ALIAS;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint8_t* pk = static_cast<const uint8_t*>(packed);
+  auto* ws = static_cast<__nv_bfloat16*>(workspace);
+  __nv_bfloat16* h0 = ws;
+  __nv_bfloat16* ab0 = h0 + N * 64;
+  __nv_bfloat16* h1 = ab0 + N * 128;
+  __nv_bfloat16* ab1 = h1 + N * 64;
+  if (launch_gnn_encode(f_in, true, s, pk, h0, ab0, st) != cudaSuccess) return LBM_ERR_CUDA;
+  RoundLaunch r0;
+  r0.h_in = h0;
+  r0.ab_in = ab0;
+  r0.h_out = h1;
+  r0.ab_out = ab1;
+  r0.round = 0;
+  if (launch_gnn_round(0, r0, s, pk, st) != cudaSuccess) return LBM_ERR_CUDA;
+  RoundLaunch r1;
+  r1.h_in = h1;
+  r1.ab_in = ab1;
+  r1.f_post = f_in;
+  r1.f_out = f_out;
+  r1.tau = tau;
+  r1.taus = taus;
+  r1.round = 1;
+  if (launch_gnn_round(1, r1, s, pk, st) != cudaSuccess) return LBM_ERR_CUDA;
+  if (totals) {
+    if (cudaMemsetAsync(totals, 0, 5 * sizeof(double), st) != cudaSuccess) return LBM_ERR_CUDA;
+    if (launch_moments(f_out, s, nullptr, nullptr, nullptr, totals, st) != cudaSuccess)
+      return LBM_ERR_CUDA;
+  }
+  return LBM_OK;
+}
+
+size_t gnn_saved_bytes(lbm_shape shape) {
+  Shape s;
+  if (check_shape_g(shape, &s)) return 0;
+  return (size_t)nodes(s) * 1152;
+}
+
+int gnn_forward(const float* f_pre, lbm_shape shape, const void* packed, void* saved, float* y,
+                void* stream) {
+  Shape s;
+  if (!f_pre || !packed || !saved || !y) return LBM_ERR_ARG;
+  if (int r = check_shape_g(shape, &s)) return r;
+  if (!aligned(packed, 16) || !aligned(saved, 16)) return LBM_ERR_ARG;
+  const int64_t N = nodes(s);
+  if (overlap(saved, N * 1152, f_pre, f_bytes(s)) || overlap(y, N * 40, f_pre, f_bytes(s)) ||
+      overlap(saved, N * 1152, y, N * 40))
+    return LBM_ERR_ALIAS;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint8_t* pk = static_cast<const uint8_t*>(packed);
+  auto* sv = static_cast<__nv_bfloat16*>(saved);
+  __nv_bfloat16* h0 = sv;
+  __nv_bfloat16* h1 = h0 + N * 64;
+  __nv_bfloat16* h2 = h1 + N * 64;
+  __nv_bfloat16* a0 = h2 + N * 64;
+  __nv_bfloat16* a1 = a0 + N * 64;
+  __nv_bfloat16* ab0 = a1 + N * 64;
+  __nv_bfloat16* ab1 = ab0 + N * 128;
+  if (launch_gnn_encode(f_pre, false, s, pk, h0, ab0, st) != cudaSuccess) return LBM_ERR_CUDA;
+  RoundLaunch r0;
+  r0.h_in = h0;
+  r0.ab_in = ab0;
+  r0.h_out = h1;
+  r0.a_out = a0;
+  r0.ab_out = ab1;
+  r0.round = 0;
+  if (launch_gnn_round(0, r0, s, pk, st) != cudaSuccess) return LBM_ERR_CUDA;
+  RoundLaunch r1;
+  r1.h_in = h1;
+  r1.ab_in = ab1;
+  r1.h_out = h2;
+  r1.a_out = a1;
+  r1.y_out = y;
+  r1.round = 1;
+  if (launch_gnn_round(2, r1, s, pk, st) != cudaSuccess) return LBM_ERR_CUDA;
+  return LBM_OK;
+}
+
+}  // extern "C"

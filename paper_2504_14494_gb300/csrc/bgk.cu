@@ -53,7 +53,8 @@ __device__ __forceinline__ void block_totals(double (&t)[5], double* __restrict_
   }
 }
 
-// Totals contribution of one stored node (post-collision values).
+// Totals contribution of one stored node (post-collision values), summed in
+// FP64 from the FP32 populations.
 __device__ __forceinline__ void add_node_totals(double (&t)[5], const float (&o)[Q]) {
   bool finite = true;
 #pragma unroll
@@ -62,9 +63,14 @@ __device__ __forceinline__ void add_node_totals(double (&t)[5], const float (&o)
     t[4] += 1.0;
     return;
   }
-  const Moments m = moments9(o);
-  const double rho = m.rho;
-  const double jx = (double)m.ux * rho, jy = (double)m.uy * rho;
+  double rho = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const double v = o[i];
+    rho += v;
+    if (ex(i)) jx += ex(i) * v;
+    if (ey(i)) jy += ey(i) * v;
+  }
   t[0] += rho;
   t[1] += jx;
   t[2] += jy;

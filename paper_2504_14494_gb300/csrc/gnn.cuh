@@ -1,0 +1,175 @@
+// GNN-enhanced collision: shared definitions (paper Sec. 2.2-2.3, Fig. 2,
+// Eq. 3).
+//
+// Network (widths and message form are this library's reading; the paper
+// gives the components, not the formulas):
+//   x_hat = ([f_0..f_8, rho, u_x, u_y] - mu) / sigma                  (12)
+//   h0 = GELU(W2 GELU(W1 x_hat + b1) + b2)                            (64)
+//   round r = 0, 1 over the 8 lattice neighbours j = i + e_k (periodic):
+//     m_ik = GELU(W_e [h_i; h_j; e_k] + b_e)
+//          = GELU(A_i + B_j + c_k), A = W_a h, B = W_b h, c_k = W_c e_k + b_e
+//     a_i = sum_k m_ik;   h_i <- h_i + GELU(W_n [h_i; a_i] + b_n)
+//   y = W_h h2 + b_h                                                  (10)
+//   tau_adj = 1/2 + sigmoid(y_0),  Delta f_i = s_df y_{1+i}
+//   f*_i = f_i - (f_i - f_i^eq) / (tau tau_adj) + Delta f_i            (Eq. 3)
+// GELU is the tanh form.  Weight matrices are used as BF16 (round to nearest
+// even of the FP32 parameters); biases, mu, sigma, s_df as FP32.  Dense
+// contractions over 128-node tiles run on tcgen05 (BF16 in, FP32 accumulate).
+#pragma once
+#include <cstdint>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "umma.cuh"
+
+namespace lbmgnn {
+
+constexpr int HID = 64;
+constexpr int NFEAT = 12;
+constexpr int NOUT = 10;
+constexpr int TILE = 128;  // nodes per MMA tile (M)
+
+// ---- flat FP32 parameter vector (interface, see include/lbmgnn.h) -----------
+namespace P {
+constexpr int ENC1_W = 0, ENC1_B = 768, ENC2_W = 832, ENC2_B = 4928;
+constexpr int ROUND0 = 4992, ROUND_SIZE = 16640;
+constexpr int EDGE_W = 0, EDGE_B = 8320, NODE_W = 8384, NODE_B = 16576;  // within a round
+constexpr int HEAD_W = 38272, HEAD_B = 38912;
+constexpr int TRAINABLE = 38922;
+constexpr int MU = 38922, SIGMA = 38934, S_DF = 38946;
+constexpr int TOTAL = 38947;
+}  // namespace P
+
+// ---- packed device image of the parameters (byte offsets) -------------------
+// SW128 blocks are the exact shared-memory images the MMAs read.
+namespace K {
+constexpr uint32_t W1F = 0;       // fp32 [64][12] (BF16-rounded values)
+constexpr uint32_t B1 = 3072;     // fp32 [64]
+constexpr uint32_t B2 = 3328;     // fp32 [64]
+constexpr uint32_t NORM = 3584;   // fp32 mu[12], sigma[12], s_df, pad -> 32 floats
+constexpr uint32_t BH = 3712;     // fp32 [16] (10 used)
+constexpr uint32_t WHF = 3776;    // fp32 [10][64] (BF16-rounded values)
+constexpr uint32_t W2 = 7168;     // SW128 [64 out x 64 in]
+constexpr uint32_t W2T = 15360;   // SW128 [64 in x 64 out]
+constexpr uint32_t WH = 23552;    // SW128 [16 out (10 used) x 64 in]
+constexpr uint32_t ROUND0 = 25600;
+constexpr uint32_t ROUND_SIZE = 68608;
+// within a round
+constexpr uint32_t WAB = 0;        // SW128 [128 out (a rows, then b rows) x 64 in]
+constexpr uint32_t WABT = 16384;   // 2 SW128 blocks [64 in x 64 out], block kb = W_a / W_b
+constexpr uint32_t WN = 32768;     // 2 SW128 blocks [64 out x 64 in], block 0: h part, 1: a part
+constexpr uint32_t WNT = 49152;    // SW128 [128 in x 64 out]
+constexpr uint32_t CK = 65536;     // fp32 [8][64]: c_k = W_c e_k + b_e, k = 1..8
+constexpr uint32_t BE = 67584;     // fp32 [64]
+constexpr uint32_t BN = 67840;     // fp32 [64]
+constexpr uint32_t TOTAL = ROUND0 + 2 * ROUND_SIZE;  // 162816
+__host__ __device__ constexpr uint32_t round_base(int r) { return ROUND0 + r * ROUND_SIZE; }
+}  // namespace K
+
+// ---- activations ----------------------------------------------------------------
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// GELU, tanh form: 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).
+__device__ __forceinline__ float gelu(float z) {
+  const float u = z * (0.7978845608028654f + 0.0356774081363001f * z * z);
+  const float hz = 0.5f * z;
+  return fmaf(hz, tanh_fast(u), hz);
+}
+// GELU and its derivative.
+__device__ __forceinline__ float gelu_grad(float z) {
+  const float z2 = z * z;
+  const float u = z * (0.7978845608028654f + 0.0356774081363001f * z2);
+  const float t = tanh_fast(u);
+  const float du = 0.7978845608028654f + 0.1070322244089003f * z2;
+  return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * du;
+}
+__device__ __forceinline__ float sigmoid_acc(float y) { return 0.5f * (1.0f + tanhf(0.5f * y)); }
+
+// ---- BF16 vectors ------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ void unpack_bf16x8(const uint4& u, float* out) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    out[2 * i] = __uint_as_float(w[i] << 16);
+    out[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+  }
+}
+__device__ __forceinline__ uint4 pack_bf16x8(const float* v) {
+  return make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                    pack_bf16x2(v[6], v[7]));
+}
+__device__ __forceinline__ float bf16_round(float v) {
+  return __bfloat162float(__float2bfloat16_rn(v));
+}
+
+// Writes 32 values (features f0..f0+31, f0 a multiple of 8) of row `row` of an
+// SW128 block at `blk` as BF16.
+__device__ __forceinline__ void st_row32(uint8_t* blk, int row, int f0, const float* v) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int chunk = (f0 >> 3) + c;
+    *reinterpret_cast<uint4*>(blk + row * 128 + ((chunk ^ (row & 7)) << 4)) = pack_bf16x8(v + 8 * c);
+  }
+}
+// Reads 32 BF16 values (features f0..f0+31) of row `row` of an SW128 block.
+__device__ __forceinline__ void ld_row32(const uint8_t* blk, int row, int f0, float* v) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int chunk = (f0 >> 3) + c;
+    unpack_bf16x8(*reinterpret_cast<const uint4*>(blk + row * 128 + ((chunk ^ (row & 7)) << 4)),
+                  v + 8 * c);
+  }
+}
+// 32 consecutive BF16 values from global memory (64 bytes, 16-byte aligned).
+__device__ __forceinline__ void ld_g32(const __nv_bfloat16* p, float* v) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) unpack_bf16x8(__ldg(q + c), v + 8 * c);
+}
+__device__ __forceinline__ void st_g32(__nv_bfloat16* p, const float* v) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) q[c] = pack_bf16x8(v + 8 * c);
+}
+
+// Node coordinates within the stacked lattices.
+struct NodeXY {
+  int x, y;
+  int64_t lat;  // index of the lattice's first node
+};
+__device__ __forceinline__ NodeXY node_xy(int64_t n, const Shape& s) {
+  const int64_t row = n / s.nx;
+  const int x = (int)(n - row * s.nx);
+  const int64_t b = row / s.ny;
+  const int y = (int)(row - b * s.ny);
+  return {x, y, b * s.ny * s.nx};
+}
+__device__ __forceinline__ int64_t node_at(const NodeXY& p, int dx, int dy, const Shape& s) {
+  int x = p.x + dx, y = p.y + dy;
+  x = x < 0 ? x + s.nx : (x >= s.nx ? x - s.nx : x);
+  y = y < 0 ? y + s.ny : (y >= s.ny ? y - s.ny : y);
+  return p.lat + (int64_t)y * s.nx + x;
+}
+
+// Copies `bytes` (multiple of 16) from global to shared memory with all threads.
+__device__ __forceinline__ void copy_g2s(void* dst, const void* src, uint32_t bytes) {
+  const uint4* s = reinterpret_cast<const uint4*>(src);
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  for (uint32_t i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+// Per-CTA tensor-core context: TMEM base, MMA-completion barrier and phase.
+struct TcCtx {
+  uint32_t tmem;
+  uint64_t* bar;
+  uint32_t phase;
+};
+
+}  // namespace lbmgnn

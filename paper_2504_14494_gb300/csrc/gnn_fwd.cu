@@ -1,0 +1,440 @@
+// GNN-enhanced collision, forward direction (paper Sec. 2.2-2.3, Eq. 3):
+// parameter packing, the encoder kernel, and the message-passing round kernel
+// (inner round, or last round fused with the head and either the Eq. 3
+// collision + store or the raw head output).
+//
+// Work unit: a tile of 128 consecutive nodes (in the stacked-lattice node
+// order).  A CTA of 256 threads owns one tile at a time (persistent loop over
+// tiles); thread t handles node t % 128 and features 32*(t / 128) .. +32, so
+// that warp w reads tensor-memory lanes 32*(w % 4).. of the accumulators.
+// Dense layers are tcgen05 MMAs (M = 128 nodes, BF16 operands in 128-byte
+// swizzled shared memory, FP32 accumulators in tensor memory).  Elementwise
+// work (12->64 input layer, GELUs, the 8 messages per node) runs on the CUDA
+// cores.  Between the kernels, h (BF16 [N][64]) and the per-node edge terms
+// A = W_a h, B = W_b h (BF16 [N][128]) live in HBM; the 8 neighbour reads of B
+// are served mostly from L2.
+#include "gnn.cuh"
+#include "gnn_launch.h"
+
+namespace lbmgnn {
+
+// ---------------------------------------------------------------------------
+// Parameter packing: FP32 flat vector -> packed device image.
+__device__ __forceinline__ void put_sw(uint8_t* blk, int row, int k, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(blk + sw128_off(row, k)) = __float2bfloat16_rn(v);
+}
+
+__global__ void gnn_pack_kernel(const float* __restrict__ p, uint8_t* __restrict__ out) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  float* w1f = reinterpret_cast<float*>(out + K::W1F);
+  for (int e = tid; e < HID * NFEAT; e += nth) w1f[e] = bf16_round(p[P::ENC1_W + e]);
+  for (int e = tid; e < HID; e += nth) {
+    reinterpret_cast<float*>(out + K::B1)[e] = p[P::ENC1_B + e];
+    reinterpret_cast<float*>(out + K::B2)[e] = p[P::ENC2_B + e];
+  }
+  for (int e = tid; e < 32; e += nth)
+    reinterpret_cast<float*>(out + K::NORM)[e] = e < 25 ? p[P::MU + e] : 0.0f;
+  for (int e = tid; e < 16; e += nth)
+    reinterpret_cast<float*>(out + K::BH)[e] = e < NOUT ? p[P::HEAD_B + e] : 0.0f;
+  for (int e = tid; e < NOUT * HID; e += nth)
+    reinterpret_cast<float*>(out + K::WHF)[e] = bf16_round(p[P::HEAD_W + e]);
+  for (int e = tid; e < HID * HID; e += nth) {
+    const int o = e / HID, i = e % HID;
+    const float w = p[P::ENC2_W + o * HID + i];
+    put_sw(out + K::W2, o, i, w);
+    put_sw(out + K::W2T, i, o, w);
+  }
+  for (int e = tid; e < 16 * HID; e += nth) {
+    const int o = e / HID, i = e % HID;
+    put_sw(out + K::WH, o, i, o < NOUT ? p[P::HEAD_W + o * HID + i] : 0.0f);
+  }
+  for (int r = 0; r < 2; ++r) {
+    const float* pr = p + P::ROUND0 + r * P::ROUND_SIZE;
+    uint8_t* kr = out + K::round_base(r);
+    const float* we = pr + P::EDGE_W;  // [64][130]
+    const float* wn = pr + P::NODE_W;  // [64][128]
+    for (int e = tid; e < HID * HID; e += nth) {
+      const int o = e / HID, i = e % HID;
+      const float wa = we[o * 130 + i], wb = we[o * 130 + HID + i];
+      put_sw(kr + K::WAB, o, i, wa);
+      put_sw(kr + K::WAB, HID + o, i, wb);
+      put_sw(kr + K::WABT, i, o, wa);
+      put_sw(kr + K::WABT + 8192, i, o, wb);
+      const float nh = wn[o * 128 + i], na = wn[o * 128 + HID + i];
+      put_sw(kr + K::WN, o, i, nh);
+      put_sw(kr + K::WN + 8192, o, i, na);
+      put_sw(kr + K::WNT, i, o, nh);
+      put_sw(kr + K::WNT, HID + i, o, na);
+    }
+    for (int e = tid; e < 8 * HID; e += nth) {
+      const int k = e / HID + 1, o = e % HID;
+      const float wcx = bf16_round(we[o * 130 + 128]), wcy = bf16_round(we[o * 130 + 129]);
+      reinterpret_cast<float*>(kr + K::CK)[e] =
+          (float(ex(k)) * wcx + float(ey(k)) * wcy) + pr[P::EDGE_B + o];
+    }
+    for (int e = tid; e < HID; e += nth) {
+      reinterpret_cast<float*>(kr + K::BE)[e] = pr[P::EDGE_B + e];
+      reinterpret_cast<float*>(kr + K::BN)[e] = pr[P::NODE_B + e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Shared prologue/epilogue of the tensor-core kernels.
+struct TcShared {
+  uint64_t bar;
+  uint32_t tmem;
+  int abort;
+};
+
+__device__ __forceinline__ void tc_setup(TcShared* sh, TcCtx& tc) {
+  if (threadIdx.x == 0) {
+    mbar_init(&sh->bar, 1);
+    sh->abort = 0;
+  }
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(&sh->tmem, 256);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  tc.tmem = sh->tmem;
+  tc.bar = &sh->bar;
+  tc.phase = 0;
+}
+
+__device__ __forceinline__ void tc_teardown(TcShared* sh, const TcCtx& tc) {
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tc.tmem, 256);
+}
+
+// Issues the MMA chain (thread 0) after all threads wrote their operands,
+// then waits for it.  Returns false if the wait gave up (status raised).
+template <typename Issue>
+__device__ __forceinline__ bool tc_run(TcShared* sh, TcCtx& tc, unsigned* stw, Issue issue) {
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc_fence_after();
+    issue();
+    umma_commit(tc.bar);
+  }
+  const bool ok = mbar_wait(tc.bar, tc.phase);
+  tc.phase ^= 1u;
+  tc_fence_after();
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) raise_status(stw, ST_TIMEOUT);
+    return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ uint32_t lane_base(uint32_t tmem) {
+  return tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16);
+}
+
+// ---------------------------------------------------------------------------
+// Encoder: pre-collision populations -> h0 (BF16) and the round-0 edge terms.
+namespace enc {
+constexpr uint32_t W2 = 0, WAB = 8192, X = 24576, W1F = 40960, B1 = 44032, B2 = 44288,
+                   NORM = 44544, SH = 44672, BYTES = 44800;
+}
+
+template <bool PULL>
+__global__ void __launch_bounds__(256, 2) gnn_encode_kernel(
+    const float* __restrict__ f, Shape s, const uint8_t* __restrict__ packed,
+    __nv_bfloat16* __restrict__ h0_out, __nv_bfloat16* __restrict__ ab_out, unsigned* stw) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  TcShared* sh = reinterpret_cast<TcShared*>(sm + enc::SH);
+  copy_g2s(sm + enc::W2, packed + K::W2, 8192);
+  copy_g2s(sm + enc::WAB, packed + K::round_base(0) + K::WAB, 16384);
+  copy_g2s(sm + enc::W1F, packed + K::W1F, 3072 + 256 + 256 + 128);  // W1F, B1, B2, NORM
+  TcCtx tc;
+  tc_setup(sh, tc);
+  const float* w1 = reinterpret_cast<const float*>(sm + enc::W1F);
+  const float* b1 = reinterpret_cast<const float*>(sm + enc::B1);
+  const float* b2 = reinterpret_cast<const float*>(sm + enc::B2);
+  const float* nrm = reinterpret_cast<const float*>(sm + enc::NORM);
+  uint8_t* X = sm + enc::X;
+  const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
+  const uint32_t lb = lane_base(tc.tmem);
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t ntiles = (N + TILE - 1) / TILE;
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t n = tile * TILE + node;
+    const bool on = n < N;
+    const int64_t nn = on ? n : N - 1;
+    float fv[Q];
+    if (PULL) {
+      const NodeXY p = node_xy(nn, s);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) fv[q] = __ldg(f + q * s.ps + node_at(p, -ex(q), -ey(q), s));
+    } else {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) fv[q] = __ldg(f + q * s.ps + nn);
+    }
+    const Moments m = moments9(fv);
+    float xh[NFEAT];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) xh[q] = (fv[q] - nrm[q]) / nrm[NFEAT + q];
+    xh[9] = (m.rho - nrm[9]) / nrm[NFEAT + 9];
+    xh[10] = (m.ux - nrm[10]) / nrm[NFEAT + 10];
+    xh[11] = (m.uy - nrm[11]) / nrm[NFEAT + 11];
+    float g[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      float z = b1[f0 + c];
+#pragma unroll
+      for (int j = 0; j < NFEAT; ++j) z = fmaf(w1[(f0 + c) * NFEAT + j], xh[j], z);
+      g[c] = gelu(z);
+    }
+    st_row32(X, node, f0, g);
+    if (!tc_run(sh, tc, stw, [&] {
+          umma_128xN(tc.tmem, smem_u32(X), 0, smem_u32(sm + enc::W2), 0, 1, 64, false);
+        }))
+      break;
+    float h[32];
+    tmem_ld32(lb + f0, h);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) h[c] = gelu(h[c] + b2[f0 + c]);
+    if (on && h0_out) st_g32(h0_out + n * HID + f0, h);
+    st_row32(X, node, f0, h);  // the MMA that read X has completed
+    if (!tc_run(sh, tc, stw, [&] {
+          umma_128xN(tc.tmem + 64, smem_u32(X), 0, smem_u32(sm + enc::WAB), 0, 1, 128, false);
+        }))
+      break;
+    float a[32], b[32];
+    tmem_ld32(lb + 64 + f0, a);
+    tmem_ld32(lb + 128 + f0, b);
+    if (on) {
+      st_g32(ab_out + n * 128 + f0, a);
+      st_g32(ab_out + n * 128 + HID + f0, b);
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  tc_teardown(sh, tc);
+}
+
+// ---------------------------------------------------------------------------
+// Message-passing round r.  MODE 0: inner round -> h_out, AB of round r+1.
+// MODE 1: last round + head + Eq. 3 collision -> f_out (pull from f_post).
+// MODE 2: last round + head -> y [10][N] (FP32) and h_out = h2.
+namespace rnd {
+constexpr uint32_t HA = 0, WN = 32768, WX = 49152, CK = 65536, BN = 67584, BH = 67840,
+                   NORM = 67904, SH = 68032, BYTES = 68096;
+}
+
+struct RoundArgs {
+  const __nv_bfloat16* h_in;   // [N][64]
+  const __nv_bfloat16* ab_in;  // [N][128]: A = W_a h, B = W_b h of this round
+  __nv_bfloat16* h_out;        // [N][64] (MODE 0, 2) or NULL
+  __nv_bfloat16* a_out;        // [N][64] aggregated messages (saved for training) or NULL
+  __nv_bfloat16* ab_out;       // [N][128] next round's A, B (MODE 0)
+  float* y_out;                // [10][N] (MODE 2)
+  const float* f_post;         // stored state to pull from (MODE 1)
+  float* f_out;                // MODE 1
+  float tau;
+  const float* taus;           // per-lattice tau or NULL
+  int round;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Shape s,
+                                                           const uint8_t* __restrict__ packed,
+                                                           unsigned* stw) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  TcShared* sh = reinterpret_cast<TcShared*>(sm + rnd::SH);
+  const uint8_t* kr = packed + K::round_base(ra.round);
+  copy_g2s(sm + rnd::WN, kr + K::WN, 16384);
+  if (MODE == 0)
+    copy_g2s(sm + rnd::WX, packed + K::round_base(ra.round + 1) + K::WAB, 16384);
+  else
+    copy_g2s(sm + rnd::WX, packed + K::WH, 2048);
+  copy_g2s(sm + rnd::CK, kr + K::CK, 2048);
+  copy_g2s(sm + rnd::BN, kr + K::BN, 256);
+  copy_g2s(sm + rnd::BH, packed + K::BH, 64);
+  copy_g2s(sm + rnd::NORM, packed + K::NORM, 128);
+  TcCtx tc;
+  tc_setup(sh, tc);
+  const float* ck = reinterpret_cast<const float*>(sm + rnd::CK);
+  const float* bn = reinterpret_cast<const float*>(sm + rnd::BN);
+  const float* bh = reinterpret_cast<const float*>(sm + rnd::BH);
+  const float* nrm = reinterpret_cast<const float*>(sm + rnd::NORM);
+  uint8_t* H = sm + rnd::HA;
+  uint8_t* Ag = sm + rnd::HA + 16384;
+  const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
+  const uint32_t lb = lane_base(tc.tmem);
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t ntiles = (N + TILE - 1) / TILE;
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t n = tile * TILE + node;
+    const bool on = n < N;
+    const int64_t nn = on ? n : N - 1;
+    const NodeXY p = node_xy(nn, s);
+    // messages m_ik = GELU(A_i + B_j + c_k), summed over the 8 neighbours
+    float A[32], acc[32];
+    ld_g32(ra.ab_in + nn * 128 + f0, A);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = 0.0f;
+#pragma unroll 1
+    for (int k = 1; k < Q; ++k) {
+      const int64_t j = node_at(p, ex(k), ey(k), s);
+      float B[32];
+      ld_g32(ra.ab_in + j * 128 + HID + f0, B);
+      const float* c_k = ck + (k - 1) * HID + f0;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc[c] += gelu(A[c] + B[c] + c_k[c]);
+    }
+    st_row32(Ag, node, f0, acc);
+    if (on && ra.a_out) st_g32(ra.a_out + n * HID + f0, acc);
+    float h[32];
+    ld_g32(ra.h_in + nn * HID + f0, h);
+    st_row32(H, node, f0, h);
+    // node update: h <- h + GELU(W_n [h; a] + b_n)
+    if (!tc_run(sh, tc, stw, [&] {
+          umma_128xN(tc.tmem, smem_u32(H), 16384, smem_u32(sm + rnd::WN), 8192, 2, 64, false);
+        }))
+      break;
+    float z[32];
+    tmem_ld32(lb + f0, z);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) h[c] += gelu(z[c] + bn[f0 + c]);
+    if (on && ra.h_out) st_g32(ra.h_out + n * HID + f0, h);
+    st_row32(H, node, f0, h);
+    if (MODE == 0) {
+      if (!tc_run(sh, tc, stw, [&] {
+            umma_128xN(tc.tmem + 64, smem_u32(H), 0, smem_u32(sm + rnd::WX), 0, 1, 128, false);
+          }))
+        break;
+      float a[32], b[32];
+      tmem_ld32(lb + 64 + f0, a);
+      tmem_ld32(lb + 128 + f0, b);
+      if (on) {
+        st_g32(ra.ab_out + n * 128 + f0, a);
+        st_g32(ra.ab_out + n * 128 + HID + f0, b);
+      }
+    } else {
+      if (!tc_run(sh, tc, stw, [&] {
+            umma_128xN(tc.tmem + 64, smem_u32(H), 0, smem_u32(sm + rnd::WX), 0, 1, 16, false);
+          }))
+        break;
+      if (half == 0) {
+        float y[16];
+        tmem_ld16(lb + 64, y);
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) y[o] += bh[o];
+        if (MODE == 2) {
+          if (on) {
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) ra.y_out[(int64_t)o * N + n] = y[o];
+          }
+        } else {
+          // Eq. 3 on the pre-collision populations pulled from the stored state
+          float fv[Q];
+#pragma unroll
+          for (int q = 0; q < Q; ++q)
+            fv[q] = __ldg(ra.f_post + q * s.ps + node_at(p, -ex(q), -ey(q), s));
+          const Moments mm = moments9(fv);
+          const float usq15 = 1.5f * (mm.ux * mm.ux + mm.uy * mm.uy);
+          const int64_t b = p.lat / ((int64_t)s.nx * s.ny);
+          const float tau = ra.taus ? __ldg(ra.taus + b) : ra.tau;
+          const float tadj = 0.5f + sigmoid_acc(y[0]);
+          const float inv = 1.0f / (tau * tadj);
+          const float sdf = nrm[24];
+          if (on) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+              const float fe = feq_i(q, mm, usq15);
+              ra.f_out[q * s.ps + n] = fv[q] - (fv[q] - fe) * inv + sdf * y[1 + q];
+            }
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  tc_teardown(sh, tc);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+static int g_num_sms = 0;
+static int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+static unsigned grid_for(int64_t N, int per_sm) {
+  const int64_t ntiles = (N + TILE - 1) / TILE;
+  const int64_t cap = (int64_t)num_sms() * per_sm;
+  return (unsigned)(ntiles < cap ? ntiles : cap);
+}
+
+cudaError_t launch_gnn_pack(const float* params, uint8_t* packed, cudaStream_t st) {
+  gnn_pack_kernel<<<64, 256, 0, st>>>(params, packed);
+  return cudaGetLastError();
+}
+
+template <typename KernelT>
+static cudaError_t set_smem(KernelT k, uint32_t bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_gnn_encode(const float* f, bool pull, const Shape& s, const uint8_t* packed,
+                              __nv_bfloat16* h0, __nv_bfloat16* ab, cudaStream_t st) {
+  unsigned* stw = status_word();
+  if (!stw) return cudaErrorInvalidDevice;
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const uint32_t bytes = enc::BYTES + 1024;
+  const unsigned grid = grid_for(N, 2);
+  cudaError_t e;
+  if (pull) {
+    if ((e = set_smem(gnn_encode_kernel<true>, bytes)) != cudaSuccess) return e;
+    gnn_encode_kernel<true><<<grid, 256, bytes, st>>>(f, s, packed, h0, ab, stw);
+  } else {
+    if ((e = set_smem(gnn_encode_kernel<false>, bytes)) != cudaSuccess) return e;
+    gnn_encode_kernel<false><<<grid, 256, bytes, st>>>(f, s, packed, h0, ab, stw);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
+                             const uint8_t* packed, cudaStream_t st) {
+  unsigned* stw = status_word();
+  if (!stw) return cudaErrorInvalidDevice;
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const uint32_t bytes = rnd::BYTES + 1024;
+  const unsigned grid = grid_for(N, 2);
+  RoundArgs ra{rl.h_in, rl.ab_in, rl.h_out, rl.a_out, rl.ab_out, rl.y_out, rl.f_post, rl.f_out,
+               rl.tau, rl.taus, rl.round};
+  cudaError_t e;
+  switch (mode) {
+    case 0:
+      if ((e = set_smem(gnn_round_kernel<0>, bytes)) != cudaSuccess) return e;
+      gnn_round_kernel<0><<<grid, 256, bytes, st>>>(ra, s, packed, stw);
+      break;
+    case 1:
+      if ((e = set_smem(gnn_round_kernel<1>, bytes)) != cudaSuccess) return e;
+      gnn_round_kernel<1><<<grid, 256, bytes, st>>>(ra, s, packed, stw);
+      break;
+    default:
+      if ((e = set_smem(gnn_round_kernel<2>, bytes)) != cudaSuccess) return e;
+      gnn_round_kernel<2><<<grid, 256, bytes, st>>>(ra, s, packed, stw);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lbmgnn

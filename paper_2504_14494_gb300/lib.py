@@ -42,6 +42,15 @@ _SIGS = {
     "lbm_step_bgk": (ctypes.c_int, [_VP, _VP, _VP, lbm_shape, ctypes.c_float, _VP, ctypes.c_int,
                                     _VP, _VP]),
     "lbm_moments": (ctypes.c_int, [_VP, lbm_shape, _VP, _VP, _VP, _VP, _VP]),
+    "gnn_param_count": (ctypes.c_size_t, []),
+    "gnn_trainable_count": (ctypes.c_size_t, []),
+    "gnn_packed_bytes": (ctypes.c_size_t, []),
+    "gnn_pack": (ctypes.c_int, [_VP, _VP, _VP]),
+    "gnn_step_workspace_bytes": (ctypes.c_size_t, [lbm_shape]),
+    "lbm_step_gnn": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP, _VP,
+                                    ctypes.c_size_t, _VP]),
+    "gnn_saved_bytes": (ctypes.c_size_t, [lbm_shape]),
+    "gnn_forward": (ctypes.c_int, [_VP, lbm_shape, _VP, _VP, _VP, _VP]),
 }
 
 
@@ -122,3 +131,46 @@ def lbm_step_bgk(f_in, f_out, f_tmp, s, tau, taus=None, nsteps=1, totals=None, s
 def lbm_moments(f, s, rho=None, ux=None, uy=None, totals=None, stream=None):
     check(load().lbm_moments(ptr(f), s, ptr(rho), ptr(ux), ptr(uy), ptr(totals),
                              stream_ptr(stream)), "lbm_moments")
+
+
+# --- GNN path ------------------------------------------------------------------------
+def gnn_param_count():
+    return load().gnn_param_count()
+
+
+def gnn_trainable_count():
+    return load().gnn_trainable_count()
+
+
+def gnn_packed_bytes():
+    return load().gnn_packed_bytes()
+
+
+def gnn_pack(params, packed, stream=None):
+    check(load().gnn_pack(ptr(params), ptr(packed), stream_ptr(stream)), "gnn_pack")
+
+
+def gnn_step_workspace_bytes(s):
+    return load().gnn_step_workspace_bytes(s)
+
+
+def nbytes(t):
+    return 0 if t is None else t.numel() * t.element_size()
+
+
+def lbm_step_gnn(f_in, f_out, s, tau, taus, packed, totals, workspace, ws_bytes=None,
+                 stream=None):
+    if ws_bytes is None:
+        ws_bytes = nbytes(workspace)
+    check(load().lbm_step_gnn(ptr(f_in), ptr(f_out), s, float(tau), ptr(taus), ptr(packed),
+                              ptr(totals), ptr(workspace), int(ws_bytes), stream_ptr(stream)),
+          "lbm_step_gnn")
+
+
+def gnn_saved_bytes(s):
+    return load().gnn_saved_bytes(s)
+
+
+def gnn_forward(f_pre, s, packed, saved, y, stream=None):
+    check(load().gnn_forward(ptr(f_pre), s, ptr(packed), ptr(saved), ptr(y), stream_ptr(stream)),
+          "gnn_forward")

@@ -1,0 +1,200 @@
+"""Parity of the CUDA GNN forward path (through the C ABI) with the FP64
+oracle, on the same parameter vector (weight matrices as BF16 on both sides).
+
+Stated tolerances (BF16 activations and weights, FP32 accumulation, against
+the FP64 oracle):
+  * head output y: relative L2 over all nodes <= 2e-2 per output group
+    (tau part y_0, correction part y_1..9), so Delta f = s_df y_1..9 too;
+  * tau_adj = 1/2 + sigmoid(y_0): max |difference| <= 1e-2;
+  * saved activations h0, h1, h2: relative L2 <= 2e-2;
+  * the Eq. 3 post-collision state: relative L2 of (f* - f*_BGK) <= 3e-2
+    (the part the network changes), and per population
+    |f* - f*_oracle| <= 1e-6 |f*_oracle| + 5e-2 max |f*_oracle - f*_BGK|
+    (FP32 rounding plus the BF16 error of the correction);
+  * an all-zero network reproduces the BGK step to FP32 rounding.
+"""
+import numpy as np
+import pytest
+
+from oracle import gnn, lbm
+from paper_2504_14494_gb300 import inputs
+from gpu_util import bf16_to_np, from_dev, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _state(nb, ny, nx, seed, u0=0.05, amp=2e-2):
+    f = np.stack([lbm.tgv_init(nx, ny, 1.0, u0, 2 * np.pi / nx, 2 * np.pi / ny)] * nb, axis=1)
+    return (f * inputs.perturbation(f.shape, seed, amp)).astype(np.float32)
+
+
+def _packed(L, theta, dev):
+    import torch
+    p = torch.from_numpy(np.asarray(theta, np.float32)).to(dev)
+    pk = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=dev)
+    L.gnn_pack(p, pk)
+    return pk
+
+
+def _oracle_forward(f, theta):
+    """Oracle y (N, 10) and (h0, h1, h2) for every lattice of the stack."""
+    p = gnn.unpack(theta)
+    ys, hs = [], [[], [], []]
+    for b in range(f.shape[1]):
+        y, cache = gnn.forward(f[:, b].astype(np.float64), p)
+        ys.append(y)
+        for r in range(3):
+            hs[r].append(cache["h"][r])
+    return np.concatenate(ys), [np.concatenate(h) for h in hs]
+
+
+SHAPES = [(1, 16, 16), (1, 3, 5), (2, 12, 20), (1, 1, 1), (1, 3, 130), (3, 7, 9)]
+
+
+@pytest.mark.parametrize("nb,ny,nx", SHAPES)
+def test_forward_matches_oracle(lbmlib, cuda, nb, ny, nx):
+    import torch
+    L = lbmlib
+    theta = inputs.xavier_params(21 + nx, s_df=1e-2, bias_scale=0.1)
+    f = _state(nb, ny, nx, seed=ny * 7 + nx)
+    pk = _packed(L, theta, cuda)
+    din, _ = to_dev(f, cuda)
+    s = L.shape(nx, ny, nb)
+    N = nb * ny * nx
+    saved = torch.zeros(L.gnn_saved_bytes(s) // 2, dtype=torch.bfloat16, device=cuda)
+    y = torch.zeros(10 * N, dtype=torch.float32, device=cuda)
+    L.gnn_forward(din, s, pk, saved, y)
+    assert L.lbm_get_status() == 0
+    y_g = y.view(10, N).cpu().numpy().T.astype(np.float64)
+    y_o, h_o = _oracle_forward(f, theta)
+    e_tau = rel_l2(y_g[:, 0], y_o[:, 0])
+    e_df = rel_l2(y_g[:, 1:], y_o[:, 1:])
+    print(f"rel L2 y0 {e_tau:.2e}  y1..9 {e_df:.2e}")
+    assert e_tau <= 2e-2 and e_df <= 2e-2, (e_tau, e_df)
+    ta_g = 0.5 + gnn.sigmoid(y_g[:, 0])
+    ta_o = 0.5 + gnn.sigmoid(y_o[:, 0])
+    assert np.max(np.abs(ta_g - ta_o)) <= 1e-2
+    for r in range(3):
+        h_g = bf16_to_np(saved[r * N * 64:(r + 1) * N * 64].view(N, 64))
+        e = rel_l2(h_g, h_o[r])
+        assert e <= 2e-2, (r, e)
+
+
+@pytest.mark.parametrize("nb,ny,nx", [(1, 16, 16), (2, 5, 7), (1, 64, 64)])
+def test_step_gnn_matches_oracle(lbmlib, cuda, nb, ny, nx):
+    import torch
+    L = lbmlib
+    theta = inputs.xavier_params(31 + nx, s_df=1e-3, bias_scale=0.1)
+    f = _state(nb, ny, nx, seed=nx + 3 * ny)
+    pk = _packed(L, theta, cuda)
+    din, _ = to_dev(f, cuda)
+    dout = torch.full_like(din, float("nan"))
+    s = L.shape(nx, ny, nb)
+    ws = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    tot = torch.zeros(5, dtype=torch.float64, device=cuda)
+    L.lbm_step_gnn(din, dout, s, 0.8, None, pk, tot, ws)
+    assert L.lbm_get_status() == 0
+    got = from_dev(dout, f.shape)
+    ref = np.stack([gnn.gnn_step(f[:, b].astype(np.float64), theta, 0.8) for b in range(nb)], axis=1)
+    bgk = np.stack([lbm.bgk_step(f[:, b].astype(np.float64), 0.8) for b in range(nb)], axis=1)
+    e_corr = rel_l2(got - bgk, ref - bgk)
+    corr = np.max(np.abs(ref - bgk))
+    e_f = np.max(np.abs(got - ref) - 1e-6 * np.abs(ref)) / corr
+    print(f"correction rel L2 {e_corr:.2e}; max err f* / max correction {e_f:.2e}")
+    assert e_corr <= 3e-2, e_corr
+    assert e_f <= 5e-2, e_f
+    t_ref = sum(lbm.totals(got[:, b]) for b in range(nb))
+    assert abs(tot[0].item() - t_ref[0]) <= 1e-12 * t_ref[0]
+
+
+def test_zero_network_equals_bgk(lbmlib, cuda):
+    """All trainable values zero: tau_adj = 1 and Delta f = 0, so Eq. 3 is the
+    BGK relaxation (Eq. 1)."""
+    import torch
+    L = lbmlib
+    f = _state(2, 12, 16, seed=5)
+    pk = _packed(L, inputs.zero_params(), cuda)
+    din, _ = to_dev(f, cuda)
+    a, b = torch.zeros_like(din), torch.zeros_like(din)
+    s = L.shape(16, 12, 2)
+    ws = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    L.lbm_step_gnn(din, a, s, 0.7, None, pk, None, ws)
+    L.lbm_step_bgk(din, b, None, s, 0.7)
+    torch.cuda.synchronize()
+    assert torch.allclose(a, b, rtol=2e-7, atol=0)
+
+
+def test_per_lattice_tau(lbmlib, cuda):
+    import torch
+    L = lbmlib
+    theta = inputs.xavier_params(41, s_df=1e-3, bias_scale=0.1)
+    f = _state(3, 8, 12, seed=9)
+    pk = _packed(L, theta, cuda)
+    din, _ = to_dev(f, cuda)
+    dout = torch.zeros_like(din)
+    taus = np.array([0.6, 0.9, 1.3], np.float32)
+    s = L.shape(12, 8, 3)
+    ws = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    L.lbm_step_gnn(din, dout, s, 5.0, torch.from_numpy(taus).to(cuda), pk, None, ws)
+    got = from_dev(dout, f.shape)
+    ref = np.stack([gnn.gnn_step(f[:, b].astype(np.float64), theta, float(taus[b])) for b in range(3)],
+                   axis=1)
+    bgk = np.stack([lbm.bgk_step(f[:, b].astype(np.float64), float(taus[b])) for b in range(3)], axis=1)
+    assert rel_l2(got - bgk, ref - bgk) <= 3e-2
+
+
+def test_workspace_and_args_are_checked(lbmlib, cuda):
+    import torch
+    L = lbmlib
+    s = L.shape(8, 8)
+    f = torch.zeros(9 * 64, device=cuda)
+    g = torch.zeros(9 * 64, device=cuda)
+    pk = torch.zeros(L.gnn_packed_bytes(), dtype=torch.uint8, device=cuda)
+    small = torch.zeros(L.gnn_step_workspace_bytes(s) - 16, dtype=torch.uint8, device=cuda)
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_step_gnn(f, g, s, 0.8, None, pk, None, small)
+    assert e.value.code == -10
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_step_gnn(f, f, s, 0.8, None, pk, None, torch.zeros(L.gnn_step_workspace_bytes(s),
+                                                                  dtype=torch.uint8, device=cuda))
+    assert e.value.code == -2
+
+
+def test_full_size_1024_sampled(lbmlib, cuda):
+    """At the 1024^2 inference workload, in the launch configuration the
+    benchmark times: y at 48 sampled nodes (and the 4 corners) against the
+    oracle evaluated on the 9x9 periodic patch around each node (the output
+    depends only on the 5x5 neighbourhood: two message-passing hops)."""
+    import torch
+    L = lbmlib
+    n = 1024
+    s = L.shape(n, n)
+    k = 2 * np.pi / n
+    f = torch.empty(9 * n * n, device=cuda)
+    L.lbm_init_tgv(f, s, 1.0, 0.05, k, k, False)
+    g = torch.Generator(device=cuda)
+    g.manual_seed(3)
+    f.mul_(1 + 2e-2 * (2 * torch.rand(f.shape, generator=g, device=cuda) - 1))
+    theta = inputs.xavier_params(51, s_df=1e-2, bias_scale=0.1)
+    pk = _packed(L, theta, cuda)
+    saved = torch.empty(L.gnn_saved_bytes(s) // 2, dtype=torch.bfloat16, device=cuda)
+    y = torch.empty(10 * n * n, device=cuda)
+    L.gnn_forward(f, s, pk, saved, y)
+    assert L.lbm_get_status() == 0
+    F = f.view(9, n, n).cpu().numpy().astype(np.float64)
+    Y = y.view(10, n * n).cpu().numpy()
+    rng = np.random.default_rng(1)
+    pts = [(int(a), int(b)) for a, b in zip(rng.integers(0, n, 48), rng.integers(0, n, 48))]
+    pts += [(0, 0), (0, n - 1), (n - 1, 0), (n - 1, n - 1)]
+    p = gnn.unpack(theta)
+    yg, yo = [], []
+    for (x, yy) in pts:
+        xs = (np.arange(x - 4, x + 5)) % n
+        ys = (np.arange(yy - 4, yy + 5)) % n
+        patch = F[:, ys[:, None], xs[None, :]]
+        yp, _ = gnn.forward(patch, p)
+        yo.append(yp[4 * 9 + 4])
+        yg.append(Y[:, yy * n + x])
+    yg, yo = np.array(yg), np.array(yo)
+    assert rel_l2(yg[:, 0], yo[:, 0]) <= 2e-2
+    assert rel_l2(yg[:, 1:], yo[:, 1:]) <= 2e-2
