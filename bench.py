@@ -130,6 +130,10 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
+    if args.only == "gnn":
+        res = gnn_bench(args, L, dev, torch.cuda.current_stream(), side=args.side, only=True)
+        print(json.dumps({"case": f"gnn {args.side}x{args.side}", **res}))
+        return None
     n = args.side
     nodes = n * n
     s = L.shape(n, n)
@@ -170,16 +174,7 @@ def run_ours(args, rank, world, local_rank):
         return None
 
     # TGV velocity L2 error of the state after done_steps steps (closed form).
-    rho = torch.empty(nodes, device=dev)
-    ux = torch.empty(nodes, device=dev)
-    uy = torch.empty(nodes, device=dev)
-    L.lbm_moments(bufs[0], s, rho, ux, uy)
-    xs = torch.arange(n, device=dev, dtype=torch.float64)
-    decay = float(np.exp(-((TAU - 0.5) / 3.0) * 2 * k * k * done_steps))
-    uxa = (U0 * decay * torch.cos(k * xs)[None, :] * torch.sin(k * xs)[:, None]).reshape(-1)
-    uya = (-U0 * decay * torch.sin(k * xs)[None, :] * torch.cos(k * xs)[:, None]).reshape(-1)
-    l2 = float(torch.sqrt(((ux.double() - uxa) ** 2 + (uy.double() - uya) ** 2).sum()
-                          / (uxa ** 2 + uya ** 2).sum()).item())
+    l2 = tgv_l2(L, bufs[0], s, n, U0, TAU, done_steps, dev)
 
     # tau sweep (same lattice, fresh TGV state each)
     sweep = []
@@ -254,11 +249,79 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-def gnn_bench(args, L, dev, stream):
-    """GNN-LBM MLUPS on the 1024^2 TGV beside BGK on the same lattice."""
-    if not hasattr(L, "lbm_step_gnn"):
-        return {"status": "not built"}
-    return L.bench_gnn_step(args, dev, stream)
+def tgv_l2(L, f, s, n, u0, tau, t, dev):
+    """Relative L2 velocity error of state f (n x n) against the closed-form
+    TGV decay u0 exp(-2 nu k^2 t), k = 2 pi / n (evaluated with torch)."""
+    import torch
+    k = 2 * np.pi / n
+    rho = torch.empty(n * n, device=dev)
+    ux = torch.empty(n * n, device=dev)
+    uy = torch.empty(n * n, device=dev)
+    L.lbm_moments(f, s, rho, ux, uy)
+    xs = torch.arange(n, device=dev, dtype=torch.float64)
+    decay = float(np.exp(-((tau - 0.5) / 3.0) * 2 * k * k * t))
+    uxa = (u0 * decay * torch.cos(k * xs)[None, :] * torch.sin(k * xs)[:, None]).reshape(-1)
+    uya = (-u0 * decay * torch.sin(k * xs)[None, :] * torch.cos(k * xs)[:, None]).reshape(-1)
+    return float(torch.sqrt(((ux.double() - uxa) ** 2 + (uy.double() - uya) ** 2).sum()
+                            / (uxa ** 2 + uya ** 2).sum()).item())
+
+
+GNN_SIDE = 1024
+GNN_RE = 1000.0
+
+
+def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False):
+    """GNN-LBM MLUPS on the 1024^2 TGV (Re = 1000, u0 = 0.05, Xavier weights,
+    seed 0) beside BGK MLUPS on the same lattice, and both TGV velocity L2
+    errors after the same number of steps from the same initial state."""
+    import torch
+    from paper_2504_14494_gb300 import inputs
+    n = side
+    s = L.shape(n, n)
+    k = 2 * np.pi / n
+    tau = 0.5 + 3.0 * U0 * n / GNN_RE
+    theta = torch.from_numpy(inputs.xavier_params(0)).to(dev)
+    packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=dev)
+    L.gnn_pack(theta, packed)
+    ws = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=dev)
+    fa = torch.empty(9 * n * n, device=dev)
+    fb = torch.empty_like(fa)
+
+    def run(kind, count, bufs):
+        for _ in range(count):
+            if kind == "gnn":
+                L.lbm_step_gnn(bufs[0], bufs[1], s, tau, None, packed, None, ws)
+            else:
+                L.lbm_step_bgk(bufs[0], bufs[1], None, s, tau)
+            bufs.reverse()
+
+    kk = max(10, min(args.steps, 200))
+    res = {}
+    for kind in ("gnn", "bgk"):
+        L.lbm_init_tgv(fa, s, 1.0, U0, k, k, False)
+        bufs = [fa, fb]
+        run(kind, args.warmup, bufs)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run(kind, kk, bufs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / kk
+        st = L.lbm_get_status()
+        res[kind] = {"ms_per_step": round(ms, 4), "mlups": round(n * n / (ms / 1e3) / 1e6, 1),
+                     "l2_error": tgv_l2(L, bufs[0], s, n, U0, tau, args.warmup + kk, dev),
+                     "status": st}
+    if only:
+        return res
+    return {"workload": f"tgv_gnn_{n}x{n}", "re": GNN_RE, "tau": round(tau, 5), "u0": U0,
+            "weights": "xavier-uniform seed 0 (untrained), s_df=1e-4",
+            "steps_timed": kk, "steps_run": args.warmup + kk,
+            "mlups_gnn": res["gnn"]["mlups"], "mlups_bgk_same_lattice": res["bgk"]["mlups"],
+            "ms_per_step_gnn": res["gnn"]["ms_per_step"],
+            "l2_error_gnn": res["gnn"]["l2_error"], "l2_error_bgk": res["bgk"]["l2_error"],
+            "gnn_over_bgk_time": round(res["gnn"]["ms_per_step"] / res["bgk"]["ms_per_step"], 2),
+            "status": res["gnn"]["status"]}
 
 
 def cpu_baseline(budget_s=12.0):
@@ -337,6 +400,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.only is None and args.side != N_SIDE:
         ap.error("--side applies to --only runs")
+    if args.only == "gnn" and args.side == N_SIDE:
+        args.side = GNN_SIDE
     if args.impl == "reference":
         out = run_reference(args, rank)
     else:
