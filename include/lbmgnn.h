@@ -169,6 +169,83 @@ LBM_API size_t gnn_saved_bytes(lbm_shape s);
 LBM_API int gnn_forward(const float* f_pre, lbm_shape s, const void* packed, void* saved,
                         float* y, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Auxiliary lattice operations
+ * ------------------------------------------------------------------------- */
+
+/* Streaming alone (Fig. 1 'Streaming Step' with periodic wrap):
+ * f_out_i(x) = f_in_i(x - e_i).  Turns a stored post-collision state into
+ * the pre-collision populations of the next step.  f_out != f_in. */
+LBM_API int lbm_stream(const float* f_in, float* f_out, lbm_shape s, void* stream);
+
+/* Taylor-Green initial states (as lbm_init_tgv) with per-lattice parameters:
+ * params is a device double[nb][4] = (rho0, u0, kx, ky) for every lattice. */
+LBM_API int lbm_init_tgv_batch(float* f, lbm_shape s, const double* params,
+                               int pressure_consistent, void* stream);
+
+/* Restriction of an m-times refined post-collision state to the coarse
+ * lattice (training data of Sec. 2.4, "high-resolution LBM simulations"; the
+ * scheme is this library's reading): coarse node (X, Y) of lattice b takes
+ * rho, u of fine node (m X, m Y); the non-equilibrium part of the fine
+ * pre-collision state, (f*_f - f^eq)/(1 - 1/tau_f), is rescaled by
+ * m tau_c / tau_f (Dupuis-Chopard) and re-relaxed:
+ * f*_c = f^eq + (1 - 1/tau_c) f_neq_c.  fine = (m nx, m ny, nb) of coarse.
+ * tau_f / taus_f and tau_c / taus_c: scalar or per-lattice device arrays. */
+LBM_API int lbm_restrict(const float* f_fine, lbm_shape fine, float* f_coarse, lbm_shape coarse,
+                         int factor, float tau_f, const float* taus_f, float tau_c,
+                         const float* taus_c, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Training (Sec. 2.4, Eq. 4)
+ * ------------------------------------------------------------------------- */
+
+/* Workspace bytes of gnn_collide_loss. */
+LBM_API size_t gnn_loss_workspace_bytes(lbm_shape s);
+
+/* Eq. 3 on the pre-collision populations f_pre with head output y
+ * (gnn_forward), then the loss of Eq. 4 against f_target, read as the mean
+ * over nodes x 9 of (f*_pred - f*_target)^2.  Writes loss (device double[1]),
+ * dL/dy (device FP32 [10][N], nullable) and f*_pred (nullable, populations of
+ * shape s).  Deterministic. */
+LBM_API int gnn_collide_loss(const float* f_pre, const float* y, const float* f_target,
+                             lbm_shape s, float tau, const float* taus, const void* packed,
+                             double* loss, float* dy, float* f_pred, void* workspace,
+                             size_t ws_bytes, void* stream);
+
+/* Workspace bytes of gnn_backward (3 x 256 bytes per node + 80 MB of
+ * per-CTA gradient partials). */
+LBM_API size_t gnn_backward_workspace_bytes(lbm_shape s);
+
+/* Reverse mode of gnn_forward: given dL/dy (device FP32 [10][N]) and the
+ * activations gnn_forward saved, writes dL/dparams (device FP32, the 38,922
+ * trainable values in parameter order; gradients w.r.t. the BF16-rounded
+ * weights as used) and, if df_pre is not NULL, dL/df_pre (populations of
+ * shape s).  Recomputes every edge pre-activation instead of storing it.
+ * Deterministic (no atomics on gradients). */
+LBM_API int gnn_backward(const float* f_pre, lbm_shape s, const void* packed, const void* saved,
+                         const float* dy, float* dparams, float* df_pre, void* workspace,
+                         size_t ws_bytes, void* stream);
+
+/* AdamW (decoupled weight decay) on the 38,922 trainable values, step >= 1:
+ * theta <- theta (1 - lr wd) - lr mhat / (sqrt(vhat) + eps). */
+LBM_API int gnn_adamw(float* params, const float* grads, float* m, float* v, int64_t step,
+                      float lr, float wd, float beta1, float beta2, float eps, void* stream);
+
+/* Workspace bytes of gnn_train_step. */
+LBM_API size_t gnn_train_workspace_bytes(lbm_shape s);
+
+/* One supervised step on nb training pairs (Sec. 2.4): f_in holds the
+ * coarse post-collision states at step n, f_target those at n + 1; the
+ * prediction is one GNN-LBM step (stream, network, Eq. 3) of f_in; loss
+ * (Eq. 4) and its gradient, then AdamW (beta = 0.9, 0.999; eps = 1e-8) on
+ * params (device FP32, updated in place, with adam_m / adam_v) and a repack
+ * of `packed`.  loss: device double[1] (the loss before the update); grads:
+ * optional device FP32 [38922] receiving the gradient. */
+LBM_API int gnn_train_step(const float* f_in, const float* f_target, lbm_shape s, float tau,
+                           const float* taus, float* params, void* packed, float* adam_m,
+                           float* adam_v, int64_t step, float lr, float wd, double* loss,
+                           float* grads, void* workspace, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,236 @@
+// C ABI entry points of the training side and the auxiliary lattice
+// operations (streaming only, restriction, per-lattice TGV initial states).
+// See include/lbmgnn.h.
+#include <cmath>
+
+#include "common.cuh"
+#include "gnn.cuh"
+#include "gnn_launch.h"
+#include "launch.h"
+
+using namespace lbmgnn;
+
+namespace {
+
+int check_shape_t(const lbm_shape& s, Shape* out) {
+  if (s.nx < 1 || s.ny < 1 || s.nb < 1) return LBM_ERR_SIZE;
+  const int64_t n = (int64_t)s.nx * s.ny * s.nb;
+  if (n > (int64_t(1) << 34)) return LBM_ERR_SIZE;
+  const int64_t ps = s.plane_stride == 0 ? n : s.plane_stride;
+  if (ps < n) return LBM_ERR_SIZE;
+  *out = Shape{s.nx, s.ny, s.nb, ps};
+  return LBM_OK;
+}
+
+int64_t nodes(const Shape& s) { return (int64_t)s.nb * s.ny * s.nx; }
+int64_t up16(int64_t b) { return (b + 15) & ~int64_t(15); }
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+int64_t f_bytes(const Shape& s) { return (8 * s.ps + nodes(s)) * (int64_t)sizeof(float); }
+bool overlap(const void* a, int64_t na, const void* b, int64_t nb) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + nb && pb < pa + na;
+}
+
+constexpr int64_t G_BYTES = (int64_t)GRAD_ROWS * P::TRAINABLE * sizeof(float);
+int64_t loss_blocks(int64_t N) { return (N + 255) / 256; }
+int64_t bwd_ws(int64_t N) { return G_BYTES + 3 * N * HID * (int64_t)sizeof(float); }
+int64_t loss_ws(int64_t N) { return up16(loss_blocks(N) * (int64_t)sizeof(double)); }
+// f_pre | saved | y | dy | loss partials | backward workspace | gradients
+int64_t train_ws(const Shape& s) {
+  const int64_t N = nodes(s);
+  return up16(9 * s.ps * (int64_t)sizeof(float)) + N * 1152 + up16(N * 40) * 2 + loss_ws(N) +
+         bwd_ws(N) + up16(P::TRAINABLE * (int64_t)sizeof(float));
+}
+
+// Carves the backward workspace.
+void carve_bwd(uint8_t* ws, int64_t N, BackwardLaunch& bl) {
+  bl.G = reinterpret_cast<float*>(ws);
+  float* p = reinterpret_cast<float*>(ws + G_BYTES);
+  bl.dh[0] = p;
+  bl.dh[1] = p + N * HID;
+  bl.da = p + 2 * N * HID;
+}
+
+void set_saved(const void* saved, int64_t N, BackwardLaunch& bl) {
+  auto* sv = static_cast<const __nv_bfloat16*>(saved);
+  bl.h0 = sv;
+  bl.h1 = sv + N * 64;
+  bl.h2 = sv + 2 * N * 64;
+  bl.a0 = sv + 3 * N * 64;
+  bl.a1 = sv + 4 * N * 64;
+  bl.ab0 = sv + 5 * N * 64;
+  bl.ab1 = sv + 5 * N * 64 + N * 128;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_stream(const float* f_in, float* f_out, lbm_shape shape, void* stream) {
+  Shape s;
+  if (!f_in || !f_out) return LBM_ERR_ARG;
+  if (int r = check_shape_t(shape, &s)) return r;
+  if (overlap(f_in, f_bytes(s), f_out, f_bytes(s))) return LBM_ERR_ALIAS;
+  return launch_stream(f_in, f_out, s, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? LBM_OK
+             : LBM_ERR_CUDA;
+}
+
+int lbm_init_tgv_batch(float* f, lbm_shape shape, const double* params, int pressure_consistent,
+                       void* stream) {
+  Shape s;
+  if (!f || !params) return LBM_ERR_ARG;
+  if (int r = check_shape_t(shape, &s)) return r;
+  return launch_tgv_init_batch(f, s, params, pressure_consistent ? 1 : 0,
+                               static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? LBM_OK
+             : LBM_ERR_CUDA;
+}
+
+int lbm_restrict(const float* f_fine, lbm_shape fine, float* f_coarse, lbm_shape coarse,
+                 int factor, float tau_f, const float* taus_f, float tau_c, const float* taus_c,
+                 void* stream) {
+  Shape fs, cs;
+  if (!f_fine || !f_coarse || factor < 1) return LBM_ERR_ARG;
+  if (int r = check_shape_t(fine, &fs)) return r;
+  if (int r = check_shape_t(coarse, &cs)) return r;
+  if (fs.nb != cs.nb || (int64_t)fs.nx != (int64_t)factor * cs.nx ||
+      (int64_t)fs.ny != (int64_t)factor * cs.ny)
+    return LBM_ERR_SIZE;
+  if (!taus_f && (!std::isfinite(tau_f) || !(tau_f > 0.5f))) return LBM_ERR_TAU;
+  if (!taus_c && (!std::isfinite(tau_c) || !(tau_c > 0.5f))) return LBM_ERR_TAU;
+  if (overlap(f_fine, f_bytes(fs), f_coarse, f_bytes(cs))) return LBM_ERR_ALIAS;
+  return launch_restrict(f_fine, fs, f_coarse, cs, factor, tau_f, taus_f, tau_c, taus_c,
+                         static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? LBM_OK
+             : LBM_ERR_CUDA;
+}
+
+size_t gnn_loss_workspace_bytes(lbm_shape shape) {
+  Shape s;
+  if (check_shape_t(shape, &s)) return 0;
+  return (size_t)loss_ws(nodes(s));
+}
+
+int gnn_collide_loss(const float* f_pre, const float* y, const float* f_target, lbm_shape shape,
+                     float tau, const float* taus, const void* packed, double* loss, float* dy,
+                     float* f_pred, void* workspace, size_t ws_bytes, void* stream) {
+  Shape s;
+  if (!f_pre || !y || !f_target || !packed || !loss) return LBM_ERR_ARG;
+  if (int r = check_shape_t(shape, &s)) return r;
+  if (!taus && (!std::isfinite(tau) || !(tau > 0.5f))) return LBM_ERR_TAU;
+  const int64_t N = nodes(s);
+  if (!workspace || (int64_t)ws_bytes < loss_ws(N) || !aligned16(workspace))
+    return LBM_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int nblk = 0;
+  auto* lossp = static_cast<double*>(workspace);
+  if (launch_collide_loss(f_pre, y, f_target, s, tau, taus, static_cast<const uint8_t*>(packed),
+                          lossp, &nblk, dy, f_pred, st) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  return launch_loss_finish(lossp, nblk, 9.0 * (double)N, loss, st) == cudaSuccess ? LBM_OK
+                                                                                   : LBM_ERR_CUDA;
+}
+
+size_t gnn_backward_workspace_bytes(lbm_shape shape) {
+  Shape s;
+  if (check_shape_t(shape, &s)) return 0;
+  return (size_t)bwd_ws(nodes(s));
+}
+
+int gnn_backward(const float* f_pre, lbm_shape shape, const void* packed, const void* saved,
+                 const float* dy, float* dparams, float* df_pre, void* workspace, size_t ws_bytes,
+                 void* stream) {
+  Shape s;
+  if (!f_pre || !packed || !saved || !dy || !dparams) return LBM_ERR_ARG;
+  if (int r = check_shape_t(shape, &s)) return r;
+  if (!aligned16(packed) || !aligned16(saved) || !aligned16(dy)) return LBM_ERR_ARG;
+  const int64_t N = nodes(s);
+  if (!workspace || (int64_t)ws_bytes < bwd_ws(N) || !aligned16(workspace))
+    return LBM_ERR_WORKSPACE;
+  if (df_pre && overlap(df_pre, f_bytes(s), f_pre, f_bytes(s))) return LBM_ERR_ALIAS;
+  BackwardLaunch bl;
+  bl.f_pre = f_pre;
+  bl.dy = dy;
+  set_saved(saved, N, bl);
+  carve_bwd(static_cast<uint8_t*>(workspace), N, bl);
+  bl.grad = dparams;
+  bl.df = df_pre;
+  return launch_gnn_backward(bl, s, static_cast<const uint8_t*>(packed),
+                             static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? LBM_OK
+             : LBM_ERR_CUDA;
+}
+
+int gnn_adamw(float* params, const float* grads, float* m, float* v, int64_t step, float lr,
+              float wd, float beta1, float beta2, float eps, void* stream) {
+  if (!params || !grads || !m || !v || step < 1) return LBM_ERR_ARG;
+  if (!(lr >= 0.0f) || !(wd >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+      !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+    return LBM_ERR_ARG;
+  const double bc1 = 1.0 / (1.0 - std::pow((double)beta1, (double)step));
+  const double bc2 = 1.0 / (1.0 - std::pow((double)beta2, (double)step));
+  return launch_adamw(params, grads, m, v, lr, wd, beta1, beta2, eps, (float)bc1, (float)bc2,
+                      static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? LBM_OK
+             : LBM_ERR_CUDA;
+}
+
+size_t gnn_train_workspace_bytes(lbm_shape shape) {
+  Shape s;
+  if (check_shape_t(shape, &s)) return 0;
+  return (size_t)train_ws(s);
+}
+
+int gnn_train_step(const float* f_in, const float* f_target, lbm_shape shape, float tau,
+                   const float* taus, float* params, void* packed, float* adam_m, float* adam_v,
+                   int64_t step, float lr, float wd, double* loss, float* grads, void* workspace,
+                   size_t ws_bytes, void* stream) {
+  Shape s;
+  if (!f_in || !f_target || !params || !packed || !adam_m || !adam_v || !loss || step < 1)
+    return LBM_ERR_ARG;
+  if (int r = check_shape_t(shape, &s)) return r;
+  if (!taus && (!std::isfinite(tau) || !(tau > 0.5f))) return LBM_ERR_TAU;
+  if (!aligned16(packed)) return LBM_ERR_ARG;
+  const int64_t N = nodes(s);
+  if (!workspace || (int64_t)ws_bytes < train_ws(s) || !aligned16(workspace))
+    return LBM_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto* pk = static_cast<uint8_t*>(packed);
+  uint8_t* w = static_cast<uint8_t*>(workspace);
+  float* f_pre = reinterpret_cast<float*>(w);
+  w += up16(9 * s.ps * (int64_t)sizeof(float));
+  void* saved = w;
+  w += N * 1152;
+  float* y = reinterpret_cast<float*>(w);
+  w += up16(N * 40);
+  float* dy = reinterpret_cast<float*>(w);
+  w += up16(N * 40);
+  double* lossp = reinterpret_cast<double*>(w);
+  w += loss_ws(N);
+  uint8_t* bws = w;
+  w += bwd_ws(N);
+  float* g = grads ? grads : reinterpret_cast<float*>(w);
+
+  if (launch_stream(f_in, f_pre, s, st) != cudaSuccess) return LBM_ERR_CUDA;
+  if (int r = gnn_forward(f_pre, shape, packed, saved, y, stream)) return r;
+  int nblk = 0;
+  if (launch_collide_loss(f_pre, y, f_target, s, tau, taus, pk, lossp, &nblk, dy, nullptr, st) !=
+      cudaSuccess)
+    return LBM_ERR_CUDA;
+  if (launch_loss_finish(lossp, nblk, 9.0 * (double)N, loss, st) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  BackwardLaunch bl;
+  bl.f_pre = f_pre;
+  bl.dy = dy;
+  set_saved(saved, N, bl);
+  carve_bwd(bws, N, bl);
+  bl.grad = g;
+  if (launch_gnn_backward(bl, s, pk, st) != cudaSuccess) return LBM_ERR_CUDA;
+  if (int r = gnn_adamw(params, g, adam_m, adam_v, step, lr, wd, 0.9f, 0.999f, 1e-8f, stream))
+    return r;
+  return gnn_pack(params, packed, stream);
+}
+
+}  // extern "C"

@@ -302,4 +302,106 @@ cudaError_t launch_tgv_init(float* f, const Shape& s, double rho0, double u0, do
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Streaming only (pull with periodic wrap): f_out_i(x) = f_in_i(x - e_i).
+__global__ void __launch_bounds__(256) stream_kernel(const float* __restrict__ fin,
+                                                     float* __restrict__ fout, Shape s) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int x = (int)(n % s.nx);
+  const int64_t row = n / s.nx;
+  const int b = (int)(row / s.ny);
+  const int y = (int)(row - (int64_t)b * s.ny);
+  const int64_t lat = (int64_t)b * s.ny * s.nx;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    int xs = x - ex(q), ys = y - ey(q);
+    xs = xs < 0 ? xs + s.nx : (xs >= s.nx ? xs - s.nx : xs);
+    ys = ys < 0 ? ys + s.ny : (ys >= s.ny ? ys - s.ny : ys);
+    fout[q * s.ps + n] = __ldg(fin + q * s.ps + lat + (int64_t)ys * s.nx + xs);
+  }
+}
+
+// Restriction of an m-times refined post-collision state to the coarse
+// lattice: inject rho, u of fine node (m X, m Y); rescale the non-equilibrium
+// part, f_neq_c = m (tau_c / tau_f) (f*_f - f^eq) / (1 - 1/tau_f);
+// f*_c = f^eq + (1 - 1/tau_c) f_neq_c.
+__global__ void __launch_bounds__(256) restrict_kernel(const float* __restrict__ ff, Shape fs,
+                                                       float* __restrict__ fc, Shape cs, int m,
+                                                       float tau_f, const float* __restrict__ taus_f,
+                                                       float tau_c, const float* __restrict__ taus_c) {
+  const int64_t N = (int64_t)cs.nb * cs.ny * cs.nx;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int X = (int)(n % cs.nx);
+  const int64_t row = n / cs.nx;
+  const int b = (int)(row / cs.ny);
+  const int Y = (int)(row - (int64_t)b * cs.ny);
+  const int64_t src = ((int64_t)b * fs.ny + (int64_t)m * Y) * fs.nx + (int64_t)m * X;
+  float f[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) f[q] = __ldg(ff + q * fs.ps + src);
+  const float tf = taus_f ? __ldg(taus_f + b) : tau_f;
+  const float tc = taus_c ? __ldg(taus_c + b) : tau_c;
+  const Moments mm = moments9(f);
+  const float usq15 = 1.5f * (mm.ux * mm.ux + mm.uy * mm.uy);
+  const float scale = (1.0f - 1.0f / tc) * (float)m * (tc / tf) / (1.0f - 1.0f / tf);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const float fe = feq_i(q, mm, usq15);
+    fc[q * cs.ps + n] = fe + scale * (f[q] - fe);
+  }
+}
+
+// Taylor-Green initial state with per-lattice parameters p[b] = (rho0, u0, kx, ky).
+__global__ void __launch_bounds__(256) tgv_init_batch_kernel(float* __restrict__ f, Shape s,
+                                                             const double* __restrict__ prm,
+                                                             int pc) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int x = (int)(n % s.nx);
+  const int64_t row = n / s.nx;
+  const int b = (int)(row / s.ny);
+  const int y = (int)(row - (int64_t)b * s.ny);
+  const double rho0 = prm[4 * b], u0 = prm[4 * b + 1], kx = prm[4 * b + 2], ky = prm[4 * b + 3];
+  double sx, cx, sy, cy;
+  sincos(kx * x, &sx, &cx);
+  sincos(ky * y, &sy, &cy);
+  const double ux = u0 * cx * sy;
+  const double uy = -u0 * sx * cy;
+  double rho = rho0;
+  if (pc) rho = rho0 * (1.0 - 0.75 * u0 * u0 * ((cx * cx - sx * sx) + (cy * cy - sy * sy)));
+  const double usq = ux * ux + uy * uy;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const double eu = ex(q) * ux + ey(q) * uy;
+    const double w = q == 0 ? 4.0 / 9.0 : (q <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    f[q * s.ps + n] = (float)(w * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq));
+  }
+}
+
+cudaError_t launch_stream(const float* fin, float* fout, const Shape& s, cudaStream_t st) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  stream_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(fin, fout, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const float* ff, const Shape& fs, float* fc, const Shape& cs, int m,
+                            float tau_f, const float* taus_f, float tau_c, const float* taus_c,
+                            cudaStream_t st) {
+  const int64_t N = (int64_t)cs.nb * cs.ny * cs.nx;
+  restrict_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(ff, fs, fc, cs, m, tau_f, taus_f,
+                                                               tau_c, taus_c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tgv_init_batch(float* f, const Shape& s, const double* prm, int pc,
+                                  cudaStream_t st) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  tgv_init_batch_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(f, s, prm, pc);
+  return cudaGetLastError();
+}
+
 }  // namespace lbmgnn

@@ -172,4 +172,81 @@ struct TcCtx {
   uint32_t phase;
 };
 
+// ---------------------------------------------------------------------------
+// Shared prologue/epilogue of the tensor-core kernels.
+struct TcShared {
+  uint64_t bar;
+  uint32_t tmem;
+  int abort;
+};
+
+__device__ __forceinline__ void tc_setup(TcShared* sh, TcCtx& tc) {
+  if (threadIdx.x == 0) {
+    mbar_init(&sh->bar, 1);
+    sh->abort = 0;
+  }
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(&sh->tmem, 256);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  tc.tmem = sh->tmem;
+  tc.bar = &sh->bar;
+  tc.phase = 0;
+}
+
+__device__ __forceinline__ void tc_teardown(TcShared* sh, const TcCtx& tc) {
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tc.tmem, 256);
+}
+
+// Issues the MMA chain (thread 0) after all threads wrote their operands,
+// then waits for it.  Returns false if the wait gave up (status raised).
+template <typename Issue>
+__device__ __forceinline__ bool tc_run(TcShared* sh, TcCtx& tc, unsigned* stw, Issue issue) {
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc_fence_after();
+    issue();
+    umma_commit(tc.bar);
+  }
+  const bool ok = mbar_wait(tc.bar, tc.phase);
+  tc.phase ^= 1u;
+  tc_fence_after();
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) raise_status(stw, ST_TIMEOUT);
+    return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ uint32_t lane_base(uint32_t tmem) {
+  return tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16);
+}
+
+// ---- launch helpers ----------------------------------------------------------
+inline int num_sms() {
+  static int g_num_sms = 0;
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+inline unsigned grid_for(int64_t N, int per_sm) {
+  const int64_t ntiles = (N + TILE - 1) / TILE;
+  const int64_t cap = (int64_t)num_sms() * per_sm;
+  return (unsigned)(ntiles < cap ? ntiles : cap);
+}
+
+template <typename KernelT>
+inline cudaError_t set_smem(KernelT k, uint32_t bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 }  // namespace lbmgnn

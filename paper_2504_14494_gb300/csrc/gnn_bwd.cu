@@ -1,0 +1,740 @@
+// GNN-enhanced collision, reverse direction and training (paper Sec. 2.4,
+// Eq. 3, Eq. 4): the Eq. 3 + MSE loss kernel, the head backward, the two
+// kernels of each message-passing round's backward, the encoder backward,
+// the deterministic gradient reduction and the AdamW update.
+//
+// Per-round recompute: the forward saves h, the aggregated messages a and
+// the per-node edge terms A = W_a h, B = W_b h (BF16); the backward recomputes
+// the node pre-activation W_n [h; a] + b_n with the same MMA and every edge
+// pre-activation z_ik = A_i + B_j + c_k elementwise, so the 8 per-node edge
+// activations are never stored.
+//
+// The edge terms need gradients scattered to neighbours (dB_j collects from
+// every i with j = i + e_k).  They are gathered instead ("pull" form): node j
+// reads da_i and A_i of its 8 neighbours i = j - e_k, so no atomics are used
+// and the result is deterministic.  This needs da of every node first, hence
+// two kernels per round.
+//
+// Weight gradients are contractions over nodes.  Each CTA accumulates them
+// on the tensor cores over all tiles it owns (operands written transposed,
+// nodes along K, into 128-byte swizzled shared memory; FP32 accumulators in
+// tensor memory) and writes one partial row; a final kernel sums the rows in
+// a fixed order.  Bias gradients (column sums) ride along as an extra MMA
+// column of ones.
+#include "gnn.cuh"
+#include "gnn_launch.h"
+
+namespace lbmgnn {
+
+// ---- transposed operand writes ---------------------------------------------------
+// Writes NV values v[c] to rows row0 + c, column `node` (0..127) of a K = 128
+// operand made of two SW128 blocks of R rows each (nodes 0..63, 64..127).
+template <int NV>
+__device__ __forceinline__ void st_col(uint8_t* op, int R, int row0, int node, const float* v) {
+  uint8_t* blk = op + (node >> 6) * (R * 128);
+  const int k = node & 63;
+#pragma unroll
+  for (int c = 0; c < NV; ++c)
+    *reinterpret_cast<__nv_bfloat16*>(blk + sw128_off(row0 + c, k)) = __float2bfloat16_rn(v[c]);
+}
+
+__device__ __forceinline__ void zero_smem(uint8_t* p, uint32_t bytes) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+  for (uint32_t i = threadIdx.x; i < bytes / 16; i += blockDim.x) q[i] = make_uint4(0, 0, 0, 0);
+}
+
+// Sets row `row` of a two-block K = 128 operand (R rows per block) to 1.
+__device__ __forceinline__ void ones_row(uint8_t* op, int R, int row) {
+  for (int n = threadIdx.x; n < 128; n += blockDim.x) {
+    uint8_t* blk = op + (n >> 6) * (R * 128);
+    *reinterpret_cast<__nv_bfloat16*>(blk + sw128_off(row, n & 63)) = __float2bfloat16_rn(1.0f);
+  }
+}
+
+__device__ __forceinline__ void ld_f32x32(const float* p, float* v) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 t = __ldg(q + i);
+    v[4 * i] = t.x;
+    v[4 * i + 1] = t.y;
+    v[4 * i + 2] = t.z;
+    v[4 * i + 3] = t.w;
+  }
+}
+__device__ __forceinline__ void st_f32x32(float* p, const float* v) {
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) q[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 3 followed by Eq. 4: per node f_pred = f - (f - f_eq)/(tau tau_adj) +
+// s_df y_1..9, squared error against the target, and dL/dy.  The loss is the
+// mean over nodes x 9 of the whole stack.  One thread per node.
+__global__ void __launch_bounds__(256) gnn_collide_loss_kernel(
+    const float* __restrict__ f_pre, const float* __restrict__ y, const float* __restrict__ tgt,
+    Shape s, float tau, const float* __restrict__ taus, const uint8_t* __restrict__ packed,
+    double* __restrict__ lossp, float* __restrict__ dy, float* __restrict__ f_pred) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool on = n < N;
+  const int64_t nn = on ? n : N - 1;
+  const float sdf = reinterpret_cast<const float*>(packed + K::NORM)[24];
+  float fv[Q], yv[NOUT];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) fv[q] = __ldg(f_pre + q * s.ps + nn);
+#pragma unroll
+  for (int o = 0; o < NOUT; ++o) yv[o] = __ldg(y + o * N + nn);
+  const int64_t b = nn / ((int64_t)s.nx * s.ny);
+  const float t = taus ? __ldg(taus + b) : tau;
+  const Moments m = moments9(fv);
+  const float usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy);
+  const float sg = sigmoid_acc(yv[0]);
+  const float teff = t * (0.5f + sg);
+  const float inv = 1.0f / teff;
+  const float scale = 2.0f / (9.0f * (float)N);
+  double lp = 0.0;
+  float dta = 0.0f, dyv[NOUT];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const float fe = feq_i(q, m, usq15);
+    const float fp = fv[q] - (fv[q] - fe) * inv + sdf * yv[1 + q];
+    const float r = fp - __ldg(tgt + q * s.ps + nn);
+    lp += (double)r * (double)r;
+    const float g = scale * r;  // dL/df*
+    dyv[1 + q] = sdf * g;
+    dta += g * (fv[q] - fe);
+    if (on && f_pred) f_pred[q * s.ps + n] = fp;
+  }
+  dyv[0] = dta * t * inv * inv * sg * (1.0f - sg);
+  if (on && dy) {
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) dy[o * N + n] = dyv[o];
+  }
+  // block reduction of the squared error
+  if (!on) lp = 0.0;
+  __shared__ double red[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lp;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int i = 0; i < 8; ++i) acc += red[i];
+    lossp[blockIdx.x] = acc;
+  }
+}
+
+// Sum of the per-block squared errors, divided by 9 N (deterministic order).
+__global__ void loss_finish_kernel(const double* __restrict__ lossp, int nblk, double count,
+                                   double* __restrict__ loss) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += lossp[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = red[0] / count;
+}
+
+// ---------------------------------------------------------------------------
+// Head backward: dh2 = dy W_h (CUDA cores), dW_h and db_h accumulated on the
+// tensor cores: D[o][i] += sum_n dy[n][o] [h2 | 1][n][i].
+namespace hb {
+constexpr uint32_t XT = 0, YT = 32768, WHF = 53248, DYS = 55808, SH = 60928, BYTES = 61056;
+}
+
+__global__ void __launch_bounds__(256, 2) gnn_head_bwd_kernel(
+    const float* __restrict__ dy, const __nv_bfloat16* __restrict__ h2, float* __restrict__ dh,
+    float* __restrict__ G, Shape s, const uint8_t* __restrict__ packed, unsigned* stw) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  TcShared* sh = reinterpret_cast<TcShared*>(sm + hb::SH);
+  zero_smem(sm, hb::WHF);
+  copy_g2s(sm + hb::WHF, packed + K::WHF, 2560);
+  __syncthreads();
+  ones_row(sm + hb::YT, 80, 64);
+  TcCtx tc;
+  tc_setup(sh, tc);
+  const float* whf = reinterpret_cast<const float*>(sm + hb::WHF);
+  float* dys = reinterpret_cast<float*>(sm + hb::DYS);
+  uint8_t* XT = sm + hb::XT;
+  uint8_t* YT = sm + hb::YT;
+  const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
+  const uint32_t lb = lane_base(tc.tmem);
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t ntiles = (N + TILE - 1) / TILE;
+  bool first = true, ok = true;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t n = tile * TILE + node;
+    const bool on = n < N;
+    const int64_t nn = on ? n : N - 1;
+    if (half == 0) {
+      float d[NOUT];
+#pragma unroll
+      for (int o = 0; o < NOUT; ++o) {
+        d[o] = on ? __ldg(dy + o * N + nn) : 0.0f;
+        dys[node * NOUT + o] = d[o];
+      }
+      st_col<NOUT>(XT, 128, 0, node, d);
+    }
+    float hv[32];
+    ld_g32(h2 + nn * HID + f0, hv);
+    st_col<32>(YT, 80, f0, node, hv);
+    __syncthreads();
+    float dv[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) dv[c] = 0.0f;
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) {
+      const float g = dys[node * NOUT + o];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) dv[c] = fmaf(g, whf[o * HID + f0 + c], dv[c]);
+    }
+    if (on) st_f32x32(dh + n * HID + f0, dv);
+    const bool acc = !first;
+    if (!tc_run(sh, tc, stw, [&] {
+          umma_128xN(tc.tmem, smem_u32(XT), 16384, smem_u32(YT), 10240, 2, 80, acc);
+        })) {
+      ok = false;
+      break;
+    }
+    first = false;
+  }
+  if (ok && (threadIdx.x >> 5) == 0) {
+    float v[32], w[32], u[16];
+    tmem_ld32(lb, v);
+    tmem_ld32(lb + 32, w);
+    tmem_ld16(lb + 64, u);
+    const int o = threadIdx.x & 31;
+    if (o < NOUT) {
+      float* g = G + (int64_t)blockIdx.x * P::TRAINABLE;
+      for (int i = 0; i < 32; ++i) {
+        g[P::HEAD_W + o * HID + i] = v[i];
+        g[P::HEAD_W + o * HID + 32 + i] = w[i];
+      }
+      g[P::HEAD_B + o] = u[0];
+    }
+  }
+  tc_teardown(sh, tc);
+}
+
+// ---------------------------------------------------------------------------
+// Round backward, part 1 (per node): recompute z_n = W_n [h; a] + b_n,
+// dz_n = dh_out * GELU'(z_n), d[h; a] = dz_n W_n; accumulate dW_n and db_n.
+// Outputs dh_part = dh_out + d[h; a]_h and da = d[h; a]_a (FP32).
+namespace rb1 {
+constexpr uint32_t HA = 0, HAT = 32768, DZ = 65536, DZT = 81920, ONES = 114688, WN = 118784,
+                   WNT = 135168, BN = 151552, SH = 151808, BYTES = 151936;
+}
+
+__global__ void __launch_bounds__(256, 1) gnn_round_bwd1_kernel(
+    const __nv_bfloat16* __restrict__ h_in, const __nv_bfloat16* __restrict__ a_in,
+    const float* __restrict__ dh_out, float* __restrict__ dh_part, float* __restrict__ da,
+    int round, float* __restrict__ G, Shape s, const uint8_t* __restrict__ packed, unsigned* stw) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  TcShared* sh = reinterpret_cast<TcShared*>(sm + rb1::SH);
+  const uint8_t* kr = packed + K::round_base(round);
+  zero_smem(sm + rb1::DZT, rb1::WN - rb1::DZT);  // DZT (upper rows stay 0) and ONES
+  copy_g2s(sm + rb1::WN, kr + K::WN, 16384);
+  copy_g2s(sm + rb1::WNT, kr + K::WNT, 16384);
+  copy_g2s(sm + rb1::BN, kr + K::BN, 256);
+  __syncthreads();
+  ones_row(sm + rb1::ONES, 16, 0);
+  TcCtx tc;
+  tc_setup(sh, tc);
+  const float* bn = reinterpret_cast<const float*>(sm + rb1::BN);
+  uint8_t* HA = sm + rb1::HA;
+  uint8_t* HAT = sm + rb1::HAT;
+  uint8_t* DZ = sm + rb1::DZ;
+  uint8_t* DZT = sm + rb1::DZT;
+  const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
+  const uint32_t lb = lane_base(tc.tmem);
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t ntiles = (N + TILE - 1) / TILE;
+  bool first = true, ok = true;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t n = tile * TILE + node;
+    const bool on = n < N;
+    const int64_t nn = on ? n : N - 1;
+    {
+      float h[32], a[32];
+      ld_g32(h_in + nn * HID + f0, h);
+      ld_g32(a_in + nn * HID + f0, a);
+      st_row32(HA, node, f0, h);
+      st_row32(HA + 16384, node, f0, a);
+      st_col<32>(HAT, 128, f0, node, h);
+      st_col<32>(HAT, 128, HID + f0, node, a);
+    }
+    if (!tc_run(sh, tc, stw, [&] {
+          umma_128xN(tc.tmem, smem_u32(HA), 16384, smem_u32(sm + rb1::WN), 8192, 2, 64, false);
+        })) {
+      ok = false;
+      break;
+    }
+    float dz[32], dho[32];
+    tmem_ld32(lb + f0, dz);
+    ld_f32x32(dh_out + nn * HID + f0, dho);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) dz[c] = on ? dho[c] * gelu_grad(dz[c] + bn[f0 + c]) : 0.0f;
+    st_row32(DZ, node, f0, dz);
+    st_col<32>(DZT, 128, f0, node, dz);
+    const bool acc = !first;
+    if (!tc_run(sh, tc, stw, [&] {
+          umma_128xN(tc.tmem, smem_u32(DZ), 0, smem_u32(sm + rb1::WNT), 0, 1, 128, false);
+          umma_128xN(tc.tmem + 128, smem_u32(HAT), 16384, smem_u32(DZT), 16384, 2, 64, acc);
+          umma_128xN(tc.tmem + 192, smem_u32(DZT), 16384, smem_u32(sm + rb1::ONES), 2048, 2, 16,
+                     acc);
+        })) {
+      ok = false;
+      break;
+    }
+    first = false;
+    float d[32];
+    tmem_ld32(lb + f0, d);
+    if (on) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) d[c] += dho[c];
+      st_f32x32(dh_part + n * HID + f0, d);
+    }
+    tmem_ld32(lb + HID + f0, d);
+    if (on) st_f32x32(da + n * HID + f0, d);
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (ok) {
+    // D_wn[i][o] at columns 128..191 (row i = input feature of [h; a]);
+    // D_bn[o][0] at column 192.
+    const int row = 32 * ((threadIdx.x >> 5) & 3) + (threadIdx.x & 31);
+    float* g = G + (int64_t)blockIdx.x * P::TRAINABLE + P::ROUND0 + round * P::ROUND_SIZE;
+    float v[32];
+    tmem_ld32(lb + 128 + f0, v);
+    for (int c = 0; c < 32; ++c) g[P::NODE_W + (f0 + c) * 128 + row] = v[c];
+    if (half == 0) {
+      float u[16];
+      tmem_ld16(lb + 192, u);
+      if (row < HID) g[P::NODE_B + row] = u[0];
+    }
+  }
+  tc_teardown(sh, tc);
+}
+
+// ---------------------------------------------------------------------------
+// Round backward, part 2 (pull form): for node j
+//   dA_j = sum_k da_j * GELU'(A_j + B_{j+e_k} + c_k)
+//   dB_j = sum_k da_i * GELU'(A_i + B_j + c_k),  i = j - e_k
+//   dc_x,j / dc_y,j = the e_kx / e_ky weighted sums of the dA_j terms.
+// dh_in = dh_part + [dA | dB] [W_a; W_b]; accumulates [dW_a; dW_b], db_e
+// (= sum dA) and the W_c columns (sum dc_x, sum dc_y).
+namespace rb2 {
+constexpr uint32_t DAB = 0, DABT = 32768, DCT = 65536, HT = 98304, WABT = 118784, CK = 135168,
+                   SH = 137216, BYTES = 137344;
+}
+
+__global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
+    const __nv_bfloat16* __restrict__ ab, const float* __restrict__ da,
+    const float* __restrict__ dh_part, const __nv_bfloat16* __restrict__ h_in,
+    float* __restrict__ dh_in, int round, float* __restrict__ G, Shape s,
+    const uint8_t* __restrict__ packed, unsigned* stw) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  TcShared* sh = reinterpret_cast<TcShared*>(sm + rb2::SH);
+  const uint8_t* kr = packed + K::round_base(round);
+  zero_smem(sm + rb2::HT, rb2::WABT - rb2::HT);
+  copy_g2s(sm + rb2::WABT, kr + K::WABT, 16384);
+  copy_g2s(sm + rb2::CK, kr + K::CK, 2048);
+  __syncthreads();
+  ones_row(sm + rb2::HT, 80, 64);
+  TcCtx tc;
+  tc_setup(sh, tc);
+  const float* ck = reinterpret_cast<const float*>(sm + rb2::CK);
+  uint8_t* DAB = sm + rb2::DAB;
+  uint8_t* DABT = sm + rb2::DABT;
+  uint8_t* DCT = sm + rb2::DCT;
+  uint8_t* HT = sm + rb2::HT;
+  const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
+  const uint32_t lb = lane_base(tc.tmem);
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t ntiles = (N + TILE - 1) / TILE;
+  bool first = true, ok = true;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t n = tile * TILE + node;
+    const bool on = n < N;
+    const int64_t nn = on ? n : N - 1;
+    const NodeXY p = node_xy(nn, s);
+#pragma unroll 1
+    for (int sc = 0; sc < 2; ++sc) {  // two chunks of 16 features
+      const int c0 = f0 + 16 * sc;
+      float Aj[16], daj[16], Bj[16], gA[16], gx[16], gy[16], gB[16];
+      {
+        const uint4* q = reinterpret_cast<const uint4*>(ab + nn * 128 + c0);
+        unpack_bf16x8(__ldg(q), Aj);
+        unpack_bf16x8(__ldg(q + 1), Aj + 8);
+        q = reinterpret_cast<const uint4*>(ab + nn * 128 + HID + c0);
+        unpack_bf16x8(__ldg(q), Bj);
+        unpack_bf16x8(__ldg(q + 1), Bj + 8);
+        const float4* r = reinterpret_cast<const float4*>(da + nn * HID + c0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 t = __ldg(r + i);
+          daj[4 * i] = t.x; daj[4 * i + 1] = t.y; daj[4 * i + 2] = t.z; daj[4 * i + 3] = t.w;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) gA[c] = gx[c] = gy[c] = gB[c] = 0.0f;
+#pragma unroll 1
+      for (int k = 1; k < Q; ++k) {
+        const float* c_k = ck + (k - 1) * HID + c0;
+        {
+          const int64_t j = node_at(p, ex(k), ey(k), s);
+          float Bn[16];
+          const uint4* q = reinterpret_cast<const uint4*>(ab + j * 128 + HID + c0);
+          unpack_bf16x8(__ldg(q), Bn);
+          unpack_bf16x8(__ldg(q + 1), Bn + 8);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const float g = daj[c] * gelu_grad(Aj[c] + Bn[c] + c_k[c]);
+            gA[c] += g;
+            if (ex(k)) gx[c] += float(ex(k)) * g;
+            if (ey(k)) gy[c] += float(ey(k)) * g;
+          }
+        }
+        {
+          const int64_t i = node_at(p, -ex(k), -ey(k), s);
+          float Ai[16], dai[16];
+          const uint4* q = reinterpret_cast<const uint4*>(ab + i * 128 + c0);
+          unpack_bf16x8(__ldg(q), Ai);
+          unpack_bf16x8(__ldg(q + 1), Ai + 8);
+          const float4* r = reinterpret_cast<const float4*>(da + i * HID + c0);
+#pragma unroll
+          for (int t4 = 0; t4 < 4; ++t4) {
+            const float4 t = __ldg(r + t4);
+            dai[4 * t4] = t.x; dai[4 * t4 + 1] = t.y; dai[4 * t4 + 2] = t.z; dai[4 * t4 + 3] = t.w;
+          }
+#pragma unroll
+          for (int c = 0; c < 16; ++c) gB[c] += dai[c] * gelu_grad(Ai[c] + Bj[c] + c_k[c]);
+        }
+      }
+      if (!on) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) gA[c] = gx[c] = gy[c] = gB[c] = 0.0f;
+      }
+      // node-major [dA | dB] (A operand of the dh MMA)
+      {
+        const int ch = c0 >> 3;
+        *reinterpret_cast<uint4*>(DAB + node * 128 + ((ch ^ (node & 7)) << 4)) = pack_bf16x8(gA);
+        *reinterpret_cast<uint4*>(DAB + node * 128 + (((ch + 1) ^ (node & 7)) << 4)) = pack_bf16x8(gA + 8);
+        uint8_t* b1 = DAB + 16384;
+        *reinterpret_cast<uint4*>(b1 + node * 128 + ((ch ^ (node & 7)) << 4)) = pack_bf16x8(gB);
+        *reinterpret_cast<uint4*>(b1 + node * 128 + (((ch + 1) ^ (node & 7)) << 4)) = pack_bf16x8(gB + 8);
+      }
+      st_col<16>(DABT, 128, c0, node, gA);
+      st_col<16>(DABT, 128, HID + c0, node, gB);
+      st_col<16>(DCT, 128, c0, node, gx);
+      st_col<16>(DCT, 128, HID + c0, node, gy);
+    }
+    {
+      float h[32];
+      ld_g32(h_in + nn * HID + f0, h);
+      st_col<32>(HT, 80, f0, node, h);
+    }
+    const bool acc = !first;
+    if (!tc_run(sh, tc, stw, [&] {
+          umma_128xN(tc.tmem, smem_u32(DAB), 16384, smem_u32(sm + rb2::WABT), 8192, 2, 64, false);
+          umma_128xN(tc.tmem + 64, smem_u32(DABT), 16384, smem_u32(HT), 10240, 2, 80, acc);
+          umma_128xN(tc.tmem + 144, smem_u32(DCT), 16384, smem_u32(HT) + 8192, 10240, 2, 16, acc);
+        })) {
+      ok = false;
+      break;
+    }
+    first = false;
+    float d[32], dp[32];
+    tmem_ld32(lb + f0, d);
+    if (on) {
+      ld_f32x32(dh_part + n * HID + f0, dp);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) d[c] += dp[c];
+      st_f32x32(dh_in + n * HID + f0, d);
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (ok) {
+    const int row = 32 * ((threadIdx.x >> 5) & 3) + (threadIdx.x & 31);  // o' (a rows, then b rows)
+    float* g = G + (int64_t)blockIdx.x * P::TRAINABLE + P::ROUND0 + round * P::ROUND_SIZE;
+    const int o = row & 63;
+    const int col_off = row < HID ? 0 : HID;
+    float v[32];
+    tmem_ld32(lb + 64 + f0, v);
+    for (int c = 0; c < 32; ++c) g[P::EDGE_W + o * 130 + col_off + f0 + c] = v[c];
+    float u[16];
+    if (half == 0) {
+      tmem_ld16(lb + 128, u);  // column sum of [dA | dB]
+      if (row < HID) g[P::EDGE_B + o] = u[0];
+    } else {
+      tmem_ld16(lb + 144, u);  // column sum of [dc_x | dc_y]
+      g[P::EDGE_W + o * 130 + 128 + (row < HID ? 0 : 1)] = u[0];
+    }
+  }
+  tc_teardown(sh, tc);
+}
+
+// ---------------------------------------------------------------------------
+// Encoder backward: recompute x_hat, z1, g1, z2; dz2 = dh0 * GELU'(z2),
+// dg1 = dz2 W2, dz1 = dg1 * GELU'(z1); accumulate
+// D[o'][i'] = sum_n [dz2 | dz1][n][o'] [g1 | x_hat | 1][n][i'], which holds
+// dW2, db2 (rows 0..63) and dW1, db1 (rows 64..127).  Optionally the input
+// gradient dL/df_pre through x_hat (f_i, rho and u = j / rho).
+namespace eb {
+constexpr uint32_t G1 = 0, DZ2 = 16384, XT = 32768, YT = 65536, W2 = 86016, W2T = 94208,
+                   W1F = 102400, B1 = 105472, B2 = 105728, NORM = 105984, DXH = 106112,
+                   SH = 118400, BYTES = 118528;
+}
+
+__global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
+    const float* __restrict__ f_pre, const float* __restrict__ dh0, float* __restrict__ df,
+    float* __restrict__ G, Shape s, const uint8_t* __restrict__ packed, unsigned* stw) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  TcShared* sh = reinterpret_cast<TcShared*>(sm + eb::SH);
+  zero_smem(sm + eb::YT, eb::W2 - eb::YT);
+  copy_g2s(sm + eb::W2, packed + K::W2, 8192);
+  copy_g2s(sm + eb::W2T, packed + K::W2T, 8192);
+  copy_g2s(sm + eb::W1F, packed + K::W1F, 3712);
+  __syncthreads();
+  ones_row(sm + eb::YT, 80, 76);
+  TcCtx tc;
+  tc_setup(sh, tc);
+  const float* w1 = reinterpret_cast<const float*>(sm + eb::W1F);
+  const float* b1 = reinterpret_cast<const float*>(sm + eb::B1);
+  const float* b2 = reinterpret_cast<const float*>(sm + eb::B2);
+  const float* nrm = reinterpret_cast<const float*>(sm + eb::NORM);
+  float* dxh = reinterpret_cast<float*>(sm + eb::DXH);
+  uint8_t* G1 = sm + eb::G1;
+  uint8_t* DZ2 = sm + eb::DZ2;
+  uint8_t* XT = sm + eb::XT;
+  uint8_t* YT = sm + eb::YT;
+  const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
+  const uint32_t lb = lane_base(tc.tmem);
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t ntiles = (N + TILE - 1) / TILE;
+  bool first = true, ok = true;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t n = tile * TILE + node;
+    const bool on = n < N;
+    const int64_t nn = on ? n : N - 1;
+    float fv[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) fv[q] = __ldg(f_pre + q * s.ps + nn);
+    const Moments m = moments9(fv);
+    float xh[NFEAT];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) xh[q] = (fv[q] - nrm[q]) / nrm[NFEAT + q];
+    xh[9] = (m.rho - nrm[9]) / nrm[NFEAT + 9];
+    xh[10] = (m.ux - nrm[10]) / nrm[NFEAT + 10];
+    xh[11] = (m.uy - nrm[11]) / nrm[NFEAT + 11];
+    float z1[32];
+    {
+      float g[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        float z = b1[f0 + c];
+#pragma unroll
+        for (int j = 0; j < NFEAT; ++j) z = fmaf(w1[(f0 + c) * NFEAT + j], xh[j], z);
+        z1[c] = z;
+        g[c] = gelu(z);
+      }
+      st_row32(G1, node, f0, g);
+      st_col<32>(YT, 80, f0, node, g);
+    }
+    if (half == 0) st_col<NFEAT>(YT, 80, HID, node, xh);
+    if (!tc_run(sh, tc, stw, [&] {
+          umma_128xN(tc.tmem, smem_u32(G1), 0, smem_u32(sm + eb::W2), 0, 1, 64, false);
+        })) {
+      ok = false;
+      break;
+    }
+    float d[32];
+    {
+      float z2[32], g0[32];
+      tmem_ld32(lb + f0, z2);
+      ld_f32x32(dh0 + nn * HID + f0, g0);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) d[c] = on ? g0[c] * gelu_grad(z2[c] + b2[f0 + c]) : 0.0f;
+    }
+    st_row32(DZ2, node, f0, d);
+    st_col<32>(XT, 128, f0, node, d);
+    if (!tc_run(sh, tc, stw, [&] {
+          umma_128xN(tc.tmem, smem_u32(DZ2), 0, smem_u32(sm + eb::W2T), 0, 1, 64, false);
+        })) {
+      ok = false;
+      break;
+    }
+    tmem_ld32(lb + f0, d);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) d[c] *= gelu_grad(z1[c]);  // dz1 (0 for idle nodes)
+    st_col<32>(XT, 128, HID + f0, node, d);
+    if (df) {
+      float px[NFEAT];
+#pragma unroll
+      for (int j = 0; j < NFEAT; ++j) px[j] = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+#pragma unroll
+        for (int j = 0; j < NFEAT; ++j) px[j] = fmaf(d[c], w1[(f0 + c) * NFEAT + j], px[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < NFEAT; ++j) dxh[(half * 128 + node) * NFEAT + j] = px[j];
+    }
+    const bool acc = !first;
+    if (!tc_run(sh, tc, stw, [&] {
+          umma_128xN(tc.tmem + 64, smem_u32(XT), 16384, smem_u32(YT), 10240, 2, 80, acc);
+        })) {
+      ok = false;
+      break;
+    }
+    first = false;
+    if (df && half == 0 && on) {
+      float dx[NFEAT];
+#pragma unroll
+      for (int j = 0; j < NFEAT; ++j)
+        dx[j] = (dxh[node * NFEAT + j] + dxh[(128 + node) * NFEAT + j]) / nrm[NFEAT + j];
+      const float ir = 1.0f / m.rho;
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        df[q * s.ps + n] =
+            dx[q] + dx[9] + (dx[10] * (float(ex(q)) - m.ux) + dx[11] * (float(ey(q)) - m.uy)) * ir;
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (ok) {
+    const int row = 32 * ((threadIdx.x >> 5) & 3) + (threadIdx.x & 31);
+    float* g = G + (int64_t)blockIdx.x * P::TRAINABLE;
+    float v[32];
+    tmem_ld32(lb + 64 + f0, v);
+    if (row < HID) {
+      for (int c = 0; c < 32; ++c) g[P::ENC2_W + row * HID + f0 + c] = v[c];
+    }
+    if (half == 0) {
+      float u[16];
+      tmem_ld16(lb + 128, u);  // columns 64..79: x_hat (12), ones (1)
+      if (row < HID) {
+        g[P::ENC2_B + row] = u[12];
+      } else {
+        for (int j = 0; j < NFEAT; ++j) g[P::ENC1_W + (row - HID) * NFEAT + j] = u[j];
+        g[P::ENC1_B + row - HID] = u[12];
+      }
+    }
+  }
+  tc_teardown(sh, tc);
+}
+
+// ---------------------------------------------------------------------------
+// Sum of the per-CTA gradient rows in a fixed order.
+__global__ void grad_reduce_kernel(const float* __restrict__ G, int rows,
+                                   float* __restrict__ grad) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P::TRAINABLE) return;
+  float acc = 0.0f;
+  for (int r = 0; r < rows; ++r) acc += G[(int64_t)r * P::TRAINABLE + p];
+  grad[p] = acc;
+}
+
+// AdamW (decoupled weight decay) on the trainable prefix.
+__global__ void adamw_kernel(float* __restrict__ theta, const float* __restrict__ g,
+                             float* __restrict__ m, float* __restrict__ v, float lr, float wd,
+                             float b1, float b2, float eps, float bc1, float bc2) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P::TRAINABLE) return;
+  const float gp = g[p];
+  const float mp = b1 * m[p] + (1.0f - b1) * gp;
+  const float vp = b2 * v[p] + (1.0f - b2) * gp * gp;
+  m[p] = mp;
+  v[p] = vp;
+  const float mh = mp * bc1, vh = vp * bc2;
+  theta[p] = theta[p] * (1.0f - lr * wd) - lr * mh / (sqrtf(vh) + eps);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+cudaError_t launch_collide_loss(const float* f_pre, const float* y, const float* tgt,
+                                const Shape& s, float tau, const float* taus,
+                                const uint8_t* packed, double* lossp, int* nblk, float* dy,
+                                float* f_pred, cudaStream_t st) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const unsigned blocks = (unsigned)((N + 255) / 256);
+  *nblk = (int)blocks;
+  gnn_collide_loss_kernel<<<blocks, 256, 0, st>>>(f_pre, y, tgt, s, tau, taus, packed, lossp, dy,
+                                                   f_pred);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_finish(const double* lossp, int nblk, double count, double* loss,
+                               cudaStream_t st) {
+  loss_finish_kernel<<<1, 256, 0, st>>>(lossp, nblk, count, loss);
+  return cudaGetLastError();
+}
+
+static unsigned grad_grid(int64_t N, int per_sm) {
+  unsigned g = grid_for(N, per_sm);
+  return g > (unsigned)GRAD_ROWS ? (unsigned)GRAD_ROWS : g;
+}
+
+cudaError_t launch_gnn_backward(const BackwardLaunch& bl, const Shape& s, const uint8_t* packed,
+                                cudaStream_t st) {
+  unsigned* stw = status_word();
+  if (!stw) return cudaErrorInvalidDevice;
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(bl.G, 0, (size_t)GRAD_ROWS * P::TRAINABLE * sizeof(float), st)) !=
+      cudaSuccess)
+    return e;
+  // head: dh2 -> dh[0]
+  {
+    const uint32_t bytes = hb::BYTES + 1024;
+    if ((e = set_smem(gnn_head_bwd_kernel, bytes)) != cudaSuccess) return e;
+    gnn_head_bwd_kernel<<<grad_grid(N, 2), 256, bytes, st>>>(bl.dy, bl.h2, bl.dh[0], bl.G, s,
+                                                             packed, stw);
+  }
+  // rounds 2 and 1 (index 1, 0): dh[0] -> dh[1] (part) -> dh[0] (in)
+  const __nv_bfloat16* hs[2] = {bl.h0, bl.h1};
+  const __nv_bfloat16* as[2] = {bl.a0, bl.a1};
+  const __nv_bfloat16* abs_[2] = {bl.ab0, bl.ab1};
+  for (int r = 1; r >= 0; --r) {
+    {
+      const uint32_t bytes = rb1::BYTES + 1024;
+      if ((e = set_smem(gnn_round_bwd1_kernel, bytes)) != cudaSuccess) return e;
+      gnn_round_bwd1_kernel<<<grad_grid(N, 1), 256, bytes, st>>>(hs[r], as[r], bl.dh[0], bl.dh[1],
+                                                                 bl.da, r, bl.G, s, packed, stw);
+    }
+    {
+      const uint32_t bytes = rb2::BYTES + 1024;
+      if ((e = set_smem(gnn_round_bwd2_kernel, bytes)) != cudaSuccess) return e;
+      gnn_round_bwd2_kernel<<<grad_grid(N, 1), 256, bytes, st>>>(abs_[r], bl.da, bl.dh[1], hs[r],
+                                                                 bl.dh[0], r, bl.G, s, packed, stw);
+    }
+  }
+  {
+    const uint32_t bytes = eb::BYTES + 1024;
+    if ((e = set_smem(gnn_encode_bwd_kernel, bytes)) != cudaSuccess) return e;
+    gnn_encode_bwd_kernel<<<grad_grid(N, 1), 256, bytes, st>>>(bl.f_pre, bl.dh[0], bl.df, bl.G, s,
+                                                               packed, stw);
+  }
+  grad_reduce_kernel<<<(P::TRAINABLE + 255) / 256, 256, 0, st>>>(bl.G, GRAD_ROWS, bl.grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adamw(float* theta, const float* g, float* m, float* v, float lr, float wd,
+                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t st) {
+  adamw_kernel<<<(P::TRAINABLE + 255) / 256, 256, 0, st>>>(theta, g, m, v, lr, wd, b1, b2, eps,
+                                                           bc1, bc2);
+  return cudaGetLastError();
+}
+
+}  // namespace lbmgnn

@@ -81,60 +81,6 @@ __global__ void gnn_pack_kernel(const float* __restrict__ p, uint8_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Shared prologue/epilogue of the tensor-core kernels.
-struct TcShared {
-  uint64_t bar;
-  uint32_t tmem;
-  int abort;
-};
-
-__device__ __forceinline__ void tc_setup(TcShared* sh, TcCtx& tc) {
-  if (threadIdx.x == 0) {
-    mbar_init(&sh->bar, 1);
-    sh->abort = 0;
-  }
-  if ((threadIdx.x >> 5) == 0) tmem_alloc(&sh->tmem, 256);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  tc.tmem = sh->tmem;
-  tc.bar = &sh->bar;
-  tc.phase = 0;
-}
-
-__device__ __forceinline__ void tc_teardown(TcShared* sh, const TcCtx& tc) {
-  tc_fence_before();
-  __syncthreads();
-  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tc.tmem, 256);
-}
-
-// Issues the MMA chain (thread 0) after all threads wrote their operands,
-// then waits for it.  Returns false if the wait gave up (status raised).
-template <typename Issue>
-__device__ __forceinline__ bool tc_run(TcShared* sh, TcCtx& tc, unsigned* stw, Issue issue) {
-  fence_async_smem();
-  tc_fence_before();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    tc_fence_after();
-    issue();
-    umma_commit(tc.bar);
-  }
-  const bool ok = mbar_wait(tc.bar, tc.phase);
-  tc.phase ^= 1u;
-  tc_fence_after();
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) raise_status(stw, ST_TIMEOUT);
-    return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ uint32_t lane_base(uint32_t tmem) {
-  return tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16);
-}
-
-// ---------------------------------------------------------------------------
 // Encoder: pre-collision populations -> h0 (BF16) and the round-0 edge terms.
 namespace enc {
 constexpr uint32_t W2 = 0, WAB = 8192, X = 24576, W1F = 40960, B1 = 44032, B2 = 44288,
@@ -365,32 +311,11 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Shape s
 
 // ---------------------------------------------------------------------------
 // Launchers
-static int g_num_sms = 0;
-static int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
-  }
-  return g_num_sms;
-}
-
-static unsigned grid_for(int64_t N, int per_sm) {
-  const int64_t ntiles = (N + TILE - 1) / TILE;
-  const int64_t cap = (int64_t)num_sms() * per_sm;
-  return (unsigned)(ntiles < cap ? ntiles : cap);
-}
-
 cudaError_t launch_gnn_pack(const float* params, uint8_t* packed, cudaStream_t st) {
   gnn_pack_kernel<<<64, 256, 0, st>>>(params, packed);
   return cudaGetLastError();
 }
 
-template <typename KernelT>
-static cudaError_t set_smem(KernelT k, uint32_t bytes) {
-  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
 
 cudaError_t launch_gnn_encode(const float* f, bool pull, const Shape& s, const uint8_t* packed,
                               __nv_bfloat16* h0, __nv_bfloat16* ab, cudaStream_t st) {

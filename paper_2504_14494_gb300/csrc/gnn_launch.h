@@ -28,4 +28,36 @@ cudaError_t launch_gnn_encode(const float* f, bool pull, const Shape& s, const u
 cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
                              const uint8_t* packed, cudaStream_t st);
 
+// Rows of per-CTA partial weight gradients (upper bound of the grid of every
+// gradient kernel).
+constexpr int GRAD_ROWS = 512;
+
+struct BackwardLaunch {
+  const float* f_pre = nullptr;            // [9][ps]
+  const float* dy = nullptr;               // [10][N]
+  const __nv_bfloat16* h0 = nullptr;       // saved activations
+  const __nv_bfloat16* h1 = nullptr;
+  const __nv_bfloat16* h2 = nullptr;
+  const __nv_bfloat16* a0 = nullptr;
+  const __nv_bfloat16* a1 = nullptr;
+  const __nv_bfloat16* ab0 = nullptr;
+  const __nv_bfloat16* ab1 = nullptr;
+  float* dh[2] = {nullptr, nullptr};       // FP32 [N][64] ping-pong
+  float* da = nullptr;                     // FP32 [N][64]
+  float* G = nullptr;                      // FP32 [GRAD_ROWS][38922]
+  float* grad = nullptr;                   // FP32 [38922]
+  float* df = nullptr;                     // optional dL/df_pre [9][ps]
+};
+
+cudaError_t launch_gnn_backward(const BackwardLaunch& bl, const Shape& s, const uint8_t* packed,
+                                cudaStream_t st);
+cudaError_t launch_collide_loss(const float* f_pre, const float* y, const float* tgt,
+                                const Shape& s, float tau, const float* taus,
+                                const uint8_t* packed, double* lossp, int* nblk, float* dy,
+                                float* f_pred, cudaStream_t st);
+cudaError_t launch_loss_finish(const double* lossp, int nblk, double count, double* loss,
+                               cudaStream_t st);
+cudaError_t launch_adamw(float* theta, const float* g, float* m, float* v, float lr, float wd,
+                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t st);
+
 }  // namespace lbmgnn

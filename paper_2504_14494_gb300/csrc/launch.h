@@ -13,4 +13,11 @@ cudaError_t launch_moments(const float* f, const Shape& s, float* rho, float* ux
 cudaError_t launch_tgv_init(float* f, const Shape& s, double rho0, double u0, double kx,
                             double ky, int pc, cudaStream_t st);
 
+cudaError_t launch_stream(const float* fin, float* fout, const Shape& s, cudaStream_t st);
+cudaError_t launch_restrict(const float* ff, const Shape& fs, float* fc, const Shape& cs, int m,
+                            float tau_f, const float* taus_f, float tau_c, const float* taus_c,
+                            cudaStream_t st);
+cudaError_t launch_tgv_init_batch(float* f, const Shape& s, const double* prm, int pc,
+                                  cudaStream_t st);
+
 }  // namespace lbmgnn

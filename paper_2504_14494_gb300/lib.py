@@ -51,6 +51,23 @@ _SIGS = {
                                     ctypes.c_size_t, _VP]),
     "gnn_saved_bytes": (ctypes.c_size_t, [lbm_shape]),
     "gnn_forward": (ctypes.c_int, [_VP, lbm_shape, _VP, _VP, _VP, _VP]),
+    "lbm_stream": (ctypes.c_int, [_VP, _VP, lbm_shape, _VP]),
+    "lbm_init_tgv_batch": (ctypes.c_int, [_VP, lbm_shape, _VP, ctypes.c_int, _VP]),
+    "lbm_restrict": (ctypes.c_int, [_VP, lbm_shape, _VP, lbm_shape, ctypes.c_int, ctypes.c_float,
+                                    _VP, ctypes.c_float, _VP, _VP]),
+    "gnn_loss_workspace_bytes": (ctypes.c_size_t, [lbm_shape]),
+    "gnn_collide_loss": (ctypes.c_int, [_VP, _VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP,
+                                        _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "gnn_backward_workspace_bytes": (ctypes.c_size_t, [lbm_shape]),
+    "gnn_backward": (ctypes.c_int, [_VP, lbm_shape, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t,
+                                    _VP]),
+    "gnn_adamw": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_float,
+                                 ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                 _VP]),
+    "gnn_train_workspace_bytes": (ctypes.c_size_t, [lbm_shape]),
+    "gnn_train_step": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP, _VP, _VP,
+                                      ctypes.c_int64, ctypes.c_float, ctypes.c_float, _VP, _VP,
+                                      _VP, ctypes.c_size_t, _VP]),
 }
 
 
@@ -174,3 +191,63 @@ def gnn_saved_bytes(s):
 def gnn_forward(f_pre, s, packed, saved, y, stream=None):
     check(load().gnn_forward(ptr(f_pre), s, ptr(packed), ptr(saved), ptr(y), stream_ptr(stream)),
           "gnn_forward")
+
+
+# --- auxiliary lattice operations and training ------------------------------------
+def lbm_stream(f_in, f_out, s, stream=None):
+    check(load().lbm_stream(ptr(f_in), ptr(f_out), s, stream_ptr(stream)), "lbm_stream")
+
+
+def lbm_init_tgv_batch(f, s, params, pressure_consistent=False, stream=None):
+    check(load().lbm_init_tgv_batch(ptr(f), s, ptr(params), int(bool(pressure_consistent)),
+                                    stream_ptr(stream)), "lbm_init_tgv_batch")
+
+
+def lbm_restrict(f_fine, fine, f_coarse, coarse, factor, tau_f, taus_f, tau_c, taus_c,
+                 stream=None):
+    check(load().lbm_restrict(ptr(f_fine), fine, ptr(f_coarse), coarse, int(factor), float(tau_f),
+                              ptr(taus_f), float(tau_c), ptr(taus_c), stream_ptr(stream)),
+          "lbm_restrict")
+
+
+def gnn_loss_workspace_bytes(s):
+    return load().gnn_loss_workspace_bytes(s)
+
+
+def gnn_collide_loss(f_pre, y, f_target, s, tau, taus, packed, loss, dy, f_pred, workspace,
+                     ws_bytes=None, stream=None):
+    check(load().gnn_collide_loss(ptr(f_pre), ptr(y), ptr(f_target), s, float(tau), ptr(taus),
+                                  ptr(packed), ptr(loss), ptr(dy), ptr(f_pred), ptr(workspace),
+                                  int(nbytes(workspace) if ws_bytes is None else ws_bytes),
+                                  stream_ptr(stream)), "gnn_collide_loss")
+
+
+def gnn_backward_workspace_bytes(s):
+    return load().gnn_backward_workspace_bytes(s)
+
+
+def gnn_backward(f_pre, s, packed, saved, dy, dparams, df_pre, workspace, ws_bytes=None,
+                 stream=None):
+    check(load().gnn_backward(ptr(f_pre), s, ptr(packed), ptr(saved), ptr(dy), ptr(dparams),
+                              ptr(df_pre), ptr(workspace),
+                              int(nbytes(workspace) if ws_bytes is None else ws_bytes),
+                              stream_ptr(stream)), "gnn_backward")
+
+
+def gnn_adamw(params, grads, m, v, step, lr, wd, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    check(load().gnn_adamw(ptr(params), ptr(grads), ptr(m), ptr(v), int(step), float(lr),
+                           float(wd), float(beta1), float(beta2), float(eps), stream_ptr(stream)),
+          "gnn_adamw")
+
+
+def gnn_train_workspace_bytes(s):
+    return load().gnn_train_workspace_bytes(s)
+
+
+def gnn_train_step(f_in, f_target, s, tau, taus, params, packed, adam_m, adam_v, step, lr, wd,
+                   loss, grads, workspace, ws_bytes=None, stream=None):
+    check(load().gnn_train_step(ptr(f_in), ptr(f_target), s, float(tau), ptr(taus), ptr(params),
+                                ptr(packed), ptr(adam_m), ptr(adam_v), int(step), float(lr),
+                                float(wd), ptr(loss), ptr(grads), ptr(workspace),
+                                int(nbytes(workspace) if ws_bytes is None else ws_bytes),
+                                stream_ptr(stream)), "gnn_train_step")
