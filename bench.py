@@ -210,7 +210,11 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / ke
 
-    gnn = gnn_bench(args, L, dev, stream)
+    trained, train_info = train_bench(args, L, dev, stream)
+    gnn = {"trained": gnn_bench(args, L, dev, stream, theta=trained,
+                                label="trained in this run (see training)"),
+           "xavier": gnn_bench(args, L, dev, stream, label="xavier-uniform seed 0, untrained"),
+           "training": train_info}
 
     if rank != 0:
         return None
@@ -270,17 +274,18 @@ GNN_SIDE = 1024
 GNN_RE = 1000.0
 
 
-def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False):
-    """GNN-LBM MLUPS on the 1024^2 TGV (Re = 1000, u0 = 0.05, Xavier weights,
-    seed 0) beside BGK MLUPS on the same lattice, and both TGV velocity L2
-    errors after the same number of steps from the same initial state."""
+def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False, theta=None, label="xavier"):
+    """GNN-LBM MLUPS on the 1024^2 TGV (Re = 1000, u0 = 0.05) beside BGK MLUPS
+    on the same lattice, and both TGV velocity L2 errors after the same number
+    of steps from the same initial state.  `theta`: parameter vector (default
+    Xavier-uniform, seed 0)."""
     import torch
     from paper_2504_14494_gb300 import inputs
     n = side
     s = L.shape(n, n)
     k = 2 * np.pi / n
     tau = 0.5 + 3.0 * U0 * n / GNN_RE
-    theta = torch.from_numpy(inputs.xavier_params(0)).to(dev)
+    theta = torch.from_numpy(inputs.xavier_params(0) if theta is None else theta).to(dev)
     packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=dev)
     L.gnn_pack(theta, packed)
     ws = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=dev)
@@ -315,13 +320,72 @@ def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False):
     if only:
         return res
     return {"workload": f"tgv_gnn_{n}x{n}", "re": GNN_RE, "tau": round(tau, 5), "u0": U0,
-            "weights": "xavier-uniform seed 0 (untrained), s_df=1e-4",
+            "weights": label,
             "steps_timed": kk, "steps_run": args.warmup + kk,
             "mlups_gnn": res["gnn"]["mlups"], "mlups_bgk_same_lattice": res["bgk"]["mlups"],
             "ms_per_step_gnn": res["gnn"]["ms_per_step"],
             "l2_error_gnn": res["gnn"]["l2_error"], "l2_error_bgk": res["bgk"]["l2_error"],
             "gnn_over_bgk_time": round(res["gnn"]["ms_per_step"] / res["bgk"]["ms_per_step"], 2),
             "status": res["gnn"]["status"]}
+
+
+def train_bench(args, L, dev, stream):
+    """Training throughput on the 64 x 256^2 batch workload (4x refined data
+    generated on the GPU, fused train step) and a short training run on 64^2
+    pairs whose weights the GNN-LBM measurement then uses."""
+    import torch
+    from paper_2504_14494_gb300 import inputs
+    from paper_2504_14494_gb300.train import Evaluator, PairStream, Trainer
+    theta = inputs.xavier_params(0, s_df=1e-4)
+    theta[38272:38922] = 0.0
+    # throughput at the full batch workload
+    tr = Trainer(dev, theta=theta.copy(), lr=1e-4, wd=0.0, seed=1, n=256, batch=64, episode=64)
+    for _ in range(3):
+        tr.step()
+    torch.cuda.synchronize()
+    kk = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(kk):
+        tr.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_full = e0.elapsed_time(e1) / kk
+    # time of the fused gnn_train_step alone (data generation excluded)
+    f_in, f_tg, taus = tr.data.next()
+    e0.record(stream)
+    for i in range(kk):
+        L.gnn_train_step(f_in, f_tg, tr.data.coarse, 1.0, taus, tr.params, tr.packed, tr.m, tr.v,
+                         100 + i, 1e-4, 0.0, tr.loss, None, tr.ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_step = e0.elapsed_time(e1) / kk
+    del tr
+    # short training run on 64^2 pairs (16 per batch), then held-out Eq. 4 loss
+    small = Trainer(dev, theta=theta.copy(), lr=1e-4, wd=0.0, seed=1, n=64, batch=16, episode=64)
+    t0 = time.perf_counter()
+    for _ in range(3000):
+        small.step()
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    held = PairStream(dev, n=64, batch=16, m=4, episode=24, seed=12345)
+    ev = Evaluator(dev, held.coarse)
+    zero = torch.from_numpy(inputs.zero_params(s_df=1e-4)).to(dev)
+    lg = lb = 0.0
+    for _ in range(48):
+        a, b, t = held.next()
+        lg += ev.loss_of(small.params, a, b, t)
+        lb += ev.loss_of(zero, a, b, t)
+    info = {"workload": "train_64x256x256_refined4",
+            "ms_per_train_step_incl_datagen": round(ms_full, 3),
+            "ms_per_fused_train_step": round(ms_step, 3),
+            "samples_per_s": round(64 / (ms_full / 1e3), 1),
+            "node_updates_per_s_M": round(64 * 256 * 256 / (ms_step / 1e3) / 1e6, 1),
+            "short_run": {"pairs": "64^2 coarse, 16 per batch", "steps": 3000, "lr": 1e-4,
+                          "wall_s": round(t_train, 2),
+                          "held_out_eq4_loss_gnn": lg / 48, "held_out_eq4_loss_bgk": lb / 48,
+                          "ratio": round(lg / lb, 4)}}
+    return small.theta(), info
 
 
 def cpu_baseline(budget_s=12.0):

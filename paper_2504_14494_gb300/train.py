@@ -1,0 +1,140 @@
+"""Training of the GNN-enhanced collision on data the library generates
+(paper Sec. 2.4), driven through the C ABI.
+
+Every arithmetic step runs in liblbmgnn.so: the refined-lattice Taylor-Green
+runs (lbm_init_tgv_batch, lbm_step_bgk with per-lattice tau), the restriction
+to the coarse lattice (lbm_restrict), and the fused training step
+(gnn_train_step: stream, network forward, Eq. 3, Eq. 4, backward, AdamW,
+repack).  This module only allocates device buffers, draws the per-instance
+flow parameters (seeded) and sequences the calls.
+
+Data (readings of Sec. 2.4 listed with the restriction in include/lbmgnn.h):
+instances are periodic TGVs on an n x n coarse lattice with k = k_mult 2 pi/n,
+k_mult in {1, 2, 4}, u0 ~ U[0.01, 0.08], Re ~ U[100, 5000] with Re = u0 n / nu.
+The refined lattice is m n (m = 4) with the same u0, k_f = k/m and
+tau_f = 1/2 + m (tau - 1/2); m fine steps make one coarse step.  A training
+pair is (restricted state at coarse step t, restricted state at t + 1).
+The refined runs start from the pressure-consistent TGV density by default,
+so that the pairs carry no start-up acoustic transient.
+"""
+import numpy as np
+
+from . import inputs
+from . import lib as L
+
+
+class PairStream:
+    """Batches of training pairs from `batch` refined-lattice TGV runs.
+
+    Each episode draws fresh instances, initialises the fine lattices at
+    equilibrium and yields `episode` consecutive coarse pairs."""
+
+    def __init__(self, device, n=256, batch=64, m=4, episode=32, seed=0,
+                 pressure_consistent=True):
+        import torch
+        self.dev = device
+        self.n, self.batch, self.m, self.episode = n, batch, m, episode
+        self.rng_seed = seed
+        self.draw = 0
+        nf = m * n
+        self.fine = L.shape(nf, nf, batch)
+        self.coarse = L.shape(n, n, batch)
+        self.ff = [torch.empty(9 * batch * nf * nf, device=device) for _ in range(2)]
+        self.fc = [torch.empty(9 * batch * n * n, device=device) for _ in range(2)]
+        self.tau_c = torch.empty(batch, device=device)
+        self.tau_f = torch.empty(batch, device=device)
+        self.prm = torch.empty(batch * 4, dtype=torch.float64, device=device)
+        self.pc = pressure_consistent
+        self.t = episode  # forces a new episode on the first call
+
+    def _new_episode(self):
+        import torch
+        inst = inputs.training_instances(self.batch, self.rng_seed * 100003 + self.draw, self.n)
+        self.draw += 1
+        nf = self.m * self.n
+        prm = np.zeros((self.batch, 4))
+        tc = np.zeros(self.batch, np.float32)
+        for b, d in enumerate(inst):
+            kf = d["k_mult"] * 2 * np.pi / nf
+            prm[b] = (1.0, d["u0"], kf, kf)
+            tc[b] = 0.5 + 3.0 * d["nu"]
+        tf = (0.5 + self.m * (tc.astype(np.float64) - 0.5)).astype(np.float32)
+        self.instances = inst
+        self.prm.copy_(torch.from_numpy(prm.reshape(-1)))
+        self.tau_c.copy_(torch.from_numpy(tc))
+        self.tau_f.copy_(torch.from_numpy(tf))
+        L.lbm_init_tgv_batch(self.ff[0], self.fine, self.prm, self.pc)
+        L.lbm_restrict(self.ff[0], self.fine, self.fc[0], self.coarse, self.m, 0.0, self.tau_f,
+                       0.0, self.tau_c)
+        self.t = 0
+
+    def next(self):
+        """Advance one coarse step; returns (f_in, f_target, tau_c) device
+        tensors valid until the next call."""
+        if self.t >= self.episode:
+            self._new_episode()
+        # m fine steps: ff[0] -> ff[1] -> ff[0] ... ending in ff[0]
+        for _ in range(self.m):
+            L.lbm_step_bgk(self.ff[0], self.ff[1], None, self.fine, 1.0, taus=self.tau_f, nsteps=1)
+            self.ff.reverse()
+        src, dst = self.fc[0], self.fc[1]
+        L.lbm_restrict(self.ff[0], self.fine, dst, self.coarse, self.m, 0.0, self.tau_f, 0.0,
+                       self.tau_c)
+        self.fc.reverse()
+        self.t += 1
+        return src, dst, self.tau_c
+
+
+class Trainer:
+    """AdamW training of the network on a PairStream (fused C ABI step)."""
+
+    def __init__(self, device, theta=None, lr=1e-3, wd=1e-2, seed=0, **stream_kw):
+        import torch
+        self.data = PairStream(device, seed=seed, **stream_kw)
+        theta = inputs.xavier_params(seed) if theta is None else theta
+        self.params = torch.from_numpy(np.asarray(theta, np.float32)).to(device)
+        self.packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=device)
+        L.gnn_pack(self.params, self.packed)
+        self.m = torch.zeros(L.gnn_trainable_count(), device=device)
+        self.v = torch.zeros_like(self.m)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=device)
+        self.ws = torch.empty(L.gnn_train_workspace_bytes(self.data.coarse), dtype=torch.uint8,
+                              device=device)
+        self.lr, self.wd = lr, wd
+        self.step_count = 0
+
+    def step(self):
+        f_in, f_tg, tau_c = self.data.next()
+        self.step_count += 1
+        L.gnn_train_step(f_in, f_tg, self.data.coarse, 1.0, tau_c, self.params, self.packed,
+                         self.m, self.v, self.step_count, self.lr, self.wd, self.loss, None,
+                         self.ws)
+
+    def theta(self):
+        return self.params.cpu().numpy().copy()
+
+
+class Evaluator:
+    """Eq. 4 loss of a parameter vector on pairs, without training: stream,
+    network forward, Eq. 3 and the loss, all through the C ABI."""
+
+    def __init__(self, device, coarse):
+        import torch
+        self.s = coarse
+        n = coarse.nx * coarse.ny * coarse.nb
+        self.f_pre = torch.empty(9 * n, device=device)
+        self.saved = torch.empty(L.gnn_saved_bytes(coarse), dtype=torch.uint8, device=device)
+        self.y = torch.empty(10 * n, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=device)
+        self.ws = torch.empty(L.gnn_loss_workspace_bytes(coarse), dtype=torch.uint8, device=device)
+        self.packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=device)
+        self.dev = device
+
+    def loss_of(self, params, f_in, f_target, taus):
+        """params: device FP32 parameter vector; returns the Eq. 4 loss."""
+        L.gnn_pack(params, self.packed)
+        L.lbm_stream(f_in, self.f_pre, self.s)
+        L.gnn_forward(self.f_pre, self.s, self.packed, self.saved, self.y)
+        L.gnn_collide_loss(self.f_pre, self.y, f_target, self.s, 1.0, taus, self.packed, self.loss,
+                           None, None, self.ws)
+        return self.loss.item()
