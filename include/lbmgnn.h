@@ -246,6 +246,32 @@ LBM_API int gnn_train_step(const float* f_in, const float* f_target, lbm_shape s
                            float* adam_v, int64_t step, float lr, float wd, double* loss,
                            float* grads, void* workspace, size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * GNN-LBM step without caller-provided scratch
+ *
+ * The paper has no counterpart: this entry point exists for callers of this
+ * library that cannot allocate device memory -- a host application whose own
+ * allocator owns the device memory and forbids further allocations, a
+ * real-time loop that may not allocate once running, or a binding with no way
+ * to hand out a device buffer.  It computes exactly what lbm_step_gnn
+ * computes, taking the 768 bytes of scratch per node from a fixed 24 MiB
+ * array inside the library (held on every GPU that loads the library's device
+ * code, until the process exits) instead of a workspace argument; it calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   - Lattices of more than LBM_STEP_GNN_NOALLOC_MAX_NODES nodes (nb*ny*nx)
+ *     are rejected with LBM_ERR_SIZE before anything is launched.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.  A failed lookup returns LBM_ERR_CUDA.
+ *   - All calls share the array, which keeps the previous call's contents;
+ *     nothing in it needs to start at zero.  Calls that overlap on the GPU
+ *     (different streams, several host threads) race on it: serialise them.
+ * Other arguments, errors and results: as lbm_step_gnn. */
+#define LBM_STEP_GNN_NOALLOC_MAX_NODES 32768
+LBM_API int lbm_step_gnn_noalloc(const float* f_in, float* f_out, lbm_shape s, float tau,
+                                 const float* taus, const void* packed, double* totals,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,7 +68,12 @@ _SIGS = {
     "gnn_train_step": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP, _VP, _VP,
                                       ctypes.c_int64, ctypes.c_float, ctypes.c_float, _VP, _VP,
                                       _VP, ctypes.c_size_t, _VP]),
+    "lbm_step_gnn_noalloc": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP,
+                                            _VP]),
 }
+
+# Largest lattice (nb*ny*nx nodes) lbm_step_gnn_noalloc accepts (include/lbmgnn.h).
+LBM_STEP_GNN_NOALLOC_MAX_NODES = 32768
 
 
 def load(path=None):
@@ -251,3 +256,11 @@ def gnn_train_step(f_in, f_target, s, tau, taus, params, packed, adam_m, adam_v,
                                 float(wd), ptr(loss), ptr(grads), ptr(workspace),
                                 int(nbytes(workspace) if ws_bytes is None else ws_bytes),
                                 stream_ptr(stream)), "gnn_train_step")
+
+
+def lbm_step_gnn_noalloc(f_in, f_out, s, tau, taus, packed, totals, stream=None):
+    """lbm_step_gnn with the library's fixed internal scratch (no workspace
+    argument, nothing allocated; see include/lbmgnn.h)."""
+    check(load().lbm_step_gnn_noalloc(ptr(f_in), ptr(f_out), s, float(tau), ptr(taus),
+                                      ptr(packed), ptr(totals), stream_ptr(stream)),
+          "lbm_step_gnn_noalloc")
