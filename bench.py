@@ -214,7 +214,8 @@ def run_ours(args, rank, world, local_rank):
     gnn = {"trained": gnn_bench(args, L, dev, stream, theta=trained,
                                 label="trained in this run (see training)"),
            "xavier": gnn_bench(args, L, dev, stream, label="xavier-uniform seed 0, untrained"),
-           "training": train_info}
+           "training": train_info,
+           "batch": batch_bench(args, L, dev, stream, trained)}
 
     if rank != 0:
         return None
@@ -386,6 +387,46 @@ def train_bench(args, L, dev, stream):
                           "held_out_eq4_loss_gnn": lg / 48, "held_out_eq4_loss_bgk": lb / 48,
                           "ratio": round(lg / lb, 4)}}
     return small.theta(), info
+
+
+def batch_bench(args, L, dev, stream, theta, n_lat=512, seed=7):
+    """The serving-style batch: 512 TGV lattices, sides log-uniform in
+    [32, 1024], Re ~ U[100, 5000], u0 ~ U[0.01, 0.08], first half plain BGK,
+    second half GNN-corrected (trained weights); every step of all lattices is
+    one replay of a recorded CUDA graph (lbm_batch_run)."""
+    import torch
+    from paper_2504_14494_gb300 import inputs
+    draws = inputs.batch_lattices(n_lat, seed)
+    lat = [(d["side"], d["side"], 1 if d["gnn"] else 0, 0.5 + 3.0 * d["nu"]) for d in draws]
+    plan = L.lbm_batch_plan_create(lat)
+    try:
+        n = L.lbm_batch_nodes(plan)
+        n_gnn = sum(d["side"] ** 2 for d in draws if d["gnn"])
+        prm = np.array([(1.0, d["u0"], 2 * np.pi / d["side"], 2 * np.pi / d["side"])
+                        for d in draws])
+        f0 = torch.empty(9 * n, device=dev)
+        f1, f2 = torch.empty_like(f0), torch.empty_like(f0)
+        L.lbm_batch_init_tgv(plan, f0, prm, True)
+        packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=dev)
+        L.gnn_pack(torch.from_numpy(theta).to(dev), packed)
+        ws = torch.empty(max(L.lbm_batch_workspace_bytes(plan), 16), dtype=torch.uint8,
+                         device=dev)
+        kk = max(2, min(args.steps, 10))
+        L.lbm_batch_run(plan, f0, f1, f2, kk, packed, ws)   # tune + record the graph
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.lbm_batch_run(plan, f0, f1, f2, kk, packed, ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = L.lbm_get_status()
+        return {"workload": f"batch_{n_lat}_lattices_sides_32_1024", "seed": seed,
+                "nodes": int(n), "nodes_gnn": int(n_gnn), "steps": kk,
+                "graph_launches": 1, "ms_per_step": round(ms / kk, 3),
+                "mlups_total": round(n * kk / (ms / 1e3) / 1e6, 1), "status": st}
+    finally:
+        L.lbm_batch_plan_destroy(plan)
 
 
 def cpu_baseline(budget_s=12.0):

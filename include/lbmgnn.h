@@ -247,6 +247,64 @@ LBM_API int gnn_train_step(const float* f_in, const float* f_target, lbm_shape s
                            float* grads, void* workspace, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched runs of many lattices of uneven size (serving-style workload)
+ *
+ * A plan packs n lattices (any sizes, each with its own tau and collision)
+ * into one population buffer: the BGK lattices first, then the GNN ones, in
+ * input order within each group; plane stride = lbm_batch_nodes(plan).
+ * lbm_batch_run advances every lattice `steps` steps (periodic wrap inside
+ * each lattice) as ONE CUDA graph launch on `stream`: per step, a batched BGK
+ * kernel over all BGK lattices and, concurrently on a second branch, the GNN
+ * kernels over all GNN lattices.  The graph is recorded on the first call with
+ * a given (buffers, steps) and replayed afterwards.  Launch shapes are chosen
+ * on first use by the autotuner (timed with CUDA events; cached per kernel,
+ * SM count and size bucket; lbm_autotune_save/load persist the cache as JSON).
+ * lbm_batch_plan_create allocates the plan's device tables (cudaMalloc) and
+ * two streams; lbm_batch_plan_destroy frees them.
+ * ------------------------------------------------------------------------- */
+enum { LBM_COLLIDE_BGK = 0, LBM_COLLIDE_GNN = 1 };
+
+typedef struct {
+  int32_t nx, ny;     /* lattice size, each >= 1 */
+  int32_t collision;  /* LBM_COLLIDE_BGK or LBM_COLLIDE_GNN */
+  float tau;          /* relaxation time, > 1/2 */
+} lbm_lattice_desc;
+
+typedef struct lbm_batch_plan lbm_batch_plan;
+
+/* lattices: host array of n descriptors.  *plan receives the new plan. */
+LBM_API int lbm_batch_plan_create(const lbm_lattice_desc* lattices, int n, lbm_batch_plan** plan);
+LBM_API void lbm_batch_plan_destroy(lbm_batch_plan* plan);
+
+/* Total nodes of the packed buffers (their plane stride); -1 for NULL. */
+LBM_API int64_t lbm_batch_nodes(const lbm_batch_plan* plan);
+
+/* First node of every input lattice in the packed buffers (host int64[n]). */
+LBM_API int lbm_batch_offsets(const lbm_batch_plan* plan, int64_t* offsets);
+
+/* Workspace bytes lbm_batch_run needs (768 per node of the GNN lattices). */
+LBM_API size_t lbm_batch_workspace_bytes(const lbm_batch_plan* plan);
+
+/* Taylor-Green initial state of every lattice (as lbm_init_tgv); params:
+ * host double[n][4] = (rho0, u0, kx, ky) per input lattice.  f: packed. */
+LBM_API int lbm_batch_init_tgv(lbm_batch_plan* plan, float* f, const double* params,
+                               int pressure_consistent, void* stream);
+
+/* `steps` steps of every lattice: f_in (read only) -> f_out, with f_tmp as
+ * the ping-pong buffer when steps > 1 (all packed buffers, distinct).  packed:
+ * gnn_pack image, workspace: lbm_batch_workspace_bytes (both only needed if
+ * a lattice uses the GNN collision).  The first call of a plan runs the
+ * autotuner, whose timing runs write f_out.  Call from the device the plan
+ * was created on. */
+LBM_API int lbm_batch_run(lbm_batch_plan* plan, const float* f_in, float* f_out, float* f_tmp,
+                          int steps, const void* packed, void* workspace, size_t ws_bytes,
+                          void* stream);
+
+/* Write / read the autotuner's cache (JSON object "kernel/smN/n2^b": choice). */
+LBM_API int lbm_autotune_save(const char* path);
+LBM_API int lbm_autotune_load(const char* path);
+
+/* ---------------------------------------------------------------------------
  * GNN-LBM step without caller-provided scratch
  *
  * The paper has no counterpart: this entry point exists for callers of this

@@ -77,14 +77,6 @@ __device__ __forceinline__ void add_node_totals(double (&t)[5], const float (&o)
   t[3] += 0.5 * (jx * jx + jy * jy) / rho;
 }
 
-// BGK collision of one node (Eq. 1 with Eq. 2), in place.
-__device__ __forceinline__ void bgk_collide(float (&f)[Q], float omega) {
-  const Moments m = moments9(f);
-  const float usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) f[i] = f[i] - omega * (f[i] - feq_i(i, m, usq15));
-}
-
 // ---------------------------------------------------------------------------
 // Fast step: nx % 4 == 0, plane stride % 4 == 0, 16-byte aligned buffers.
 template <bool TOTALS>

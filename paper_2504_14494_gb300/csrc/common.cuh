@@ -60,6 +60,14 @@ __device__ __forceinline__ float feq_i(int i, const Moments& m, float usq15) {
   return wq(i) * m.rho * (1.0f + 3.0f * eu + 4.5f * eu * eu - usq15);
 }
 
+// BGK collision of one node (Eq. 1 with Eq. 2), in place; omega = 1/tau.
+__device__ __forceinline__ void bgk_collide(float (&f)[Q], float omega) {
+  const Moments m = moments9(f);
+  const float usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i] = f[i] - omega * (f[i] - feq_i(i, m, usq15));
+}
+
 struct Shape {
   int nx, ny, nb;
   int64_t ps;  // plane stride in elements

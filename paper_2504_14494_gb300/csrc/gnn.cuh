@@ -158,6 +158,73 @@ __device__ __forceinline__ int64_t node_at(const NodeXY& p, int dx, int dy, cons
   return p.lat + (int64_t)y * s.nx + x;
 }
 
+// ---- node geometry -------------------------------------------------------------
+// The forward kernels see a contiguous range of `count()` nodes starting at
+// global node `base()` of the population buffers (plane stride `ps()`), and
+// map a global node to its lattice through one of two geometries: a stack
+// of equal lattices, or a table of lattices of any size (batched runs).
+struct GeoPos {
+  int x, y, nx, ny;
+  int64_t lat;  // global index of the lattice's first node
+  int b;        // lattice index (relaxation-time lookup)
+};
+__device__ __forceinline__ int64_t geo_nbr(const GeoPos& p, int dx, int dy) {
+  int x = p.x + dx, y = p.y + dy;
+  x = x < 0 ? x + p.nx : (x >= p.nx ? x - p.nx : x);
+  y = y < 0 ? y + p.ny : (y >= p.ny ? y - p.ny : y);
+  return p.lat + (int64_t)y * p.nx + x;
+}
+
+struct GeoStack {
+  Shape s;
+  __device__ __forceinline__ int64_t count() const { return (int64_t)s.nb * s.ny * s.nx; }
+  __device__ __forceinline__ int64_t base() const { return 0; }
+  __device__ __forceinline__ int64_t ps() const { return s.ps; }
+  __device__ __forceinline__ GeoPos pos(int64_t g) const {
+    const int64_t row = g / s.nx;
+    const int x = (int)(g - row * s.nx);
+    const int64_t b = row / s.ny;
+    const int y = (int)(row - b * s.ny);
+    return {x, y, s.nx, s.ny, b * s.ny * s.nx, (int)b};
+  }
+  __device__ __forceinline__ float tau(const GeoPos& p, float tau0, const float* taus) const {
+    return taus ? __ldg(taus + p.b) : tau0;
+  }
+};
+
+// One lattice of a batched run: first node in the packed buffers, size and
+// relaxation time.
+struct LatDesc {
+  int64_t offset;
+  int32_t nx, ny;
+  float tau;
+  int32_t pad;
+};
+
+struct GeoTable {
+  const LatDesc* lat;  // device table, sorted by offset
+  int first, n;        // lattices first .. first+n-1 form this range
+  int64_t base_, cnt, ps_;
+  __device__ __forceinline__ int64_t count() const { return cnt; }
+  __device__ __forceinline__ int64_t base() const { return base_; }
+  __device__ __forceinline__ int64_t ps() const { return ps_; }
+  __device__ __forceinline__ GeoPos pos(int64_t g) const {
+    int lo = first, hi = first + n - 1;
+    while (lo < hi) {  // last lattice whose offset <= g
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(&lat[mid].offset) <= g) lo = mid; else hi = mid - 1;
+    }
+    const int64_t off = __ldg(&lat[lo].offset);
+    const int nx = __ldg(&lat[lo].nx), ny = __ldg(&lat[lo].ny);
+    const int64_t r = g - off;
+    const int y = (int)(r / nx);
+    return {(int)(r - (int64_t)y * nx), y, nx, ny, off, lo};
+  }
+  __device__ __forceinline__ float tau(const GeoPos& p, float, const float*) const {
+    return __ldg(&lat[p.b].tau);
+  }
+};
+
 // Copies `bytes` (multiple of 16) from global to shared memory with all threads.
 __device__ __forceinline__ void copy_g2s(void* dst, const void* src, uint32_t bytes) {
   const uint4* s = reinterpret_cast<const uint4*>(src);

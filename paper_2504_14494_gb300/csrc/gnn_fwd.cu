@@ -87,9 +87,9 @@ constexpr uint32_t W2 = 0, WAB = 8192, X = 24576, W1F = 40960, B1 = 44032, B2 = 
                    NORM = 44544, SH = 44672, BYTES = 44800;
 }
 
-template <bool PULL>
+template <bool PULL, class Geo>
 __global__ void __launch_bounds__(256, 2) gnn_encode_kernel(
-    const float* __restrict__ f, Shape s, const uint8_t* __restrict__ packed,
+    const float* __restrict__ f, Geo geo, const uint8_t* __restrict__ packed,
     __nv_bfloat16* __restrict__ h0_out, __nv_bfloat16* __restrict__ ab_out, unsigned* stw) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(256, 2) gnn_encode_kernel(
   uint8_t* X = sm + enc::X;
   const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
   const uint32_t lb = lane_base(tc.tmem);
-  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t N = geo.count();
+  const int64_t base = geo.base(), ps = geo.ps();
   const int64_t ntiles = (N + TILE - 1) / TILE;
 
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -115,12 +116,12 @@ __global__ void __launch_bounds__(256, 2) gnn_encode_kernel(
     const int64_t nn = on ? n : N - 1;
     float fv[Q];
     if (PULL) {
-      const NodeXY p = node_xy(nn, s);
+      const GeoPos p = geo.pos(base + nn);
 #pragma unroll
-      for (int q = 0; q < Q; ++q) fv[q] = __ldg(f + q * s.ps + node_at(p, -ex(q), -ey(q), s));
+      for (int q = 0; q < Q; ++q) fv[q] = __ldg(f + q * ps + geo_nbr(p, -ex(q), -ey(q)));
     } else {
 #pragma unroll
-      for (int q = 0; q < Q; ++q) fv[q] = __ldg(f + q * s.ps + nn);
+      for (int q = 0; q < Q; ++q) fv[q] = __ldg(f + q * ps + base + nn);
     }
     const Moments m = moments9(fv);
     float xh[NFEAT];
@@ -188,8 +189,8 @@ struct RoundArgs {
   int round;
 };
 
-template <int MODE>
-__global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Shape s,
+template <int MODE, class Geo>
+__global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Geo geo,
                                                            const uint8_t* __restrict__ packed,
                                                            unsigned* stw) {
   extern __shared__ uint8_t smem_raw[];
@@ -215,14 +216,15 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Shape s
   uint8_t* Ag = sm + rnd::HA + 16384;
   const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
   const uint32_t lb = lane_base(tc.tmem);
-  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t N = geo.count();
+  const int64_t base = geo.base(), ps = geo.ps();
   const int64_t ntiles = (N + TILE - 1) / TILE;
 
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t n = tile * TILE + node;
     const bool on = n < N;
     const int64_t nn = on ? n : N - 1;
-    const NodeXY p = node_xy(nn, s);
+    const GeoPos p = geo.pos(base + nn);
     // messages m_ik = GELU(A_i + B_j + c_k), summed over the 8 neighbours
     float A[32], acc[32];
     ld_g32(ra.ab_in + nn * 128 + f0, A);
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Shape s
     for (int c = 0; c < 32; ++c) acc[c] = 0.0f;
 #pragma unroll 1
     for (int k = 1; k < Q; ++k) {
-      const int64_t j = node_at(p, ex(k), ey(k), s);
+      const int64_t j = geo_nbr(p, ex(k), ey(k)) - base;
       float B[32];
       ld_g32(ra.ab_in + j * 128 + HID + f0, B);
       const float* c_k = ck + (k - 1) * HID + f0;
@@ -285,11 +287,10 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Shape s
           float fv[Q];
 #pragma unroll
           for (int q = 0; q < Q; ++q)
-            fv[q] = __ldg(ra.f_post + q * s.ps + node_at(p, -ex(q), -ey(q), s));
+            fv[q] = __ldg(ra.f_post + q * ps + geo_nbr(p, -ex(q), -ey(q)));
           const Moments mm = moments9(fv);
           const float usq15 = 1.5f * (mm.ux * mm.ux + mm.uy * mm.uy);
-          const int64_t b = p.lat / ((int64_t)s.nx * s.ny);
-          const float tau = ra.taus ? __ldg(ra.taus + b) : ra.tau;
+          const float tau = geo.tau(p, ra.tau, ra.taus);
           const float tadj = 0.5f + sigmoid_acc(y[0]);
           const float inv = 1.0f / (tau * tadj);
           const float sdf = nrm[24];
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Shape s
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
               const float fe = feq_i(q, mm, usq15);
-              ra.f_out[q * s.ps + n] = fv[q] - (fv[q] - fe) * inv + sdf * y[1 + q];
+              ra.f_out[q * ps + base + n] = fv[q] - (fv[q] - fe) * inv + sdf * y[1 + q];
             }
           }
         }
@@ -317,49 +318,89 @@ cudaError_t launch_gnn_pack(const float* params, uint8_t* packed, cudaStream_t s
 }
 
 
-cudaError_t launch_gnn_encode(const float* f, bool pull, const Shape& s, const uint8_t* packed,
-                              __nv_bfloat16* h0, __nv_bfloat16* ab, cudaStream_t st) {
+template <class Geo>
+static cudaError_t encode_any(const float* f, bool pull, const Geo& geo, int64_t N,
+                              const uint8_t* packed, __nv_bfloat16* h0, __nv_bfloat16* ab,
+                              cudaStream_t st, int per_sm = 2) {
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
-  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
   const uint32_t bytes = enc::BYTES + 1024;
-  const unsigned grid = grid_for(N, 2);
+  const unsigned grid = grid_for(N, per_sm);
   cudaError_t e;
   if (pull) {
-    if ((e = set_smem(gnn_encode_kernel<true>, bytes)) != cudaSuccess) return e;
-    gnn_encode_kernel<true><<<grid, 256, bytes, st>>>(f, s, packed, h0, ab, stw);
+    if ((e = set_smem(gnn_encode_kernel<true, Geo>, bytes)) != cudaSuccess) return e;
+    gnn_encode_kernel<true, Geo><<<grid, 256, bytes, st>>>(f, geo, packed, h0, ab, stw);
   } else {
-    if ((e = set_smem(gnn_encode_kernel<false>, bytes)) != cudaSuccess) return e;
-    gnn_encode_kernel<false><<<grid, 256, bytes, st>>>(f, s, packed, h0, ab, stw);
+    if ((e = set_smem(gnn_encode_kernel<false, Geo>, bytes)) != cudaSuccess) return e;
+    gnn_encode_kernel<false, Geo><<<grid, 256, bytes, st>>>(f, geo, packed, h0, ab, stw);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
-                             const uint8_t* packed, cudaStream_t st) {
+template <class Geo>
+static cudaError_t round_any(int mode, const RoundLaunch& rl, const Geo& geo, int64_t N,
+                             const uint8_t* packed, cudaStream_t st, int per_sm = 2) {
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
-  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
   const uint32_t bytes = rnd::BYTES + 1024;
-  const unsigned grid = grid_for(N, 2);
+  const unsigned grid = grid_for(N, per_sm);
   RoundArgs ra{rl.h_in, rl.ab_in, rl.h_out, rl.a_out, rl.ab_out, rl.y_out, rl.f_post, rl.f_out,
                rl.tau, rl.taus, rl.round};
   cudaError_t e;
   switch (mode) {
     case 0:
-      if ((e = set_smem(gnn_round_kernel<0>, bytes)) != cudaSuccess) return e;
-      gnn_round_kernel<0><<<grid, 256, bytes, st>>>(ra, s, packed, stw);
+      if ((e = set_smem(gnn_round_kernel<0, Geo>, bytes)) != cudaSuccess) return e;
+      gnn_round_kernel<0, Geo><<<grid, 256, bytes, st>>>(ra, geo, packed, stw);
       break;
     case 1:
-      if ((e = set_smem(gnn_round_kernel<1>, bytes)) != cudaSuccess) return e;
-      gnn_round_kernel<1><<<grid, 256, bytes, st>>>(ra, s, packed, stw);
+      if ((e = set_smem(gnn_round_kernel<1, Geo>, bytes)) != cudaSuccess) return e;
+      gnn_round_kernel<1, Geo><<<grid, 256, bytes, st>>>(ra, geo, packed, stw);
       break;
     default:
-      if ((e = set_smem(gnn_round_kernel<2>, bytes)) != cudaSuccess) return e;
-      gnn_round_kernel<2><<<grid, 256, bytes, st>>>(ra, s, packed, stw);
+      if ((e = set_smem(gnn_round_kernel<2, Geo>, bytes)) != cudaSuccess) return e;
+      gnn_round_kernel<2, Geo><<<grid, 256, bytes, st>>>(ra, geo, packed, stw);
       break;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_gnn_encode(const float* f, bool pull, const Shape& s, const uint8_t* packed,
+                              __nv_bfloat16* h0, __nv_bfloat16* ab, cudaStream_t st) {
+  return encode_any(f, pull, GeoStack{s}, (int64_t)s.nb * s.ny * s.nx, packed, h0, ab, st);
+}
+
+cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
+                             const uint8_t* packed, cudaStream_t st) {
+  return round_any(mode, rl, GeoStack{s}, (int64_t)s.nb * s.ny * s.nx, packed, st);
+}
+
+cudaError_t launch_gnn_step_table(const float* f_in, float* f_out, const LatDesc* lat, int first,
+                                  int n, int64_t base, int64_t count, int64_t ps,
+                                  const uint8_t* packed, __nv_bfloat16* ws, cudaStream_t st,
+                                  int per_sm) {
+  if (count <= 0) return cudaSuccess;
+  const GeoTable geo{lat, first, n, base, count, ps};
+  __nv_bfloat16* h0 = ws;
+  __nv_bfloat16* ab0 = h0 + count * 64;
+  __nv_bfloat16* h1 = ab0 + count * 128;
+  __nv_bfloat16* ab1 = h1 + count * 64;
+  cudaError_t e;
+  if ((e = encode_any(f_in, true, geo, count, packed, h0, ab0, st, per_sm)) != cudaSuccess)
+    return e;
+  RoundLaunch r0;
+  r0.h_in = h0;
+  r0.ab_in = ab0;
+  r0.h_out = h1;
+  r0.ab_out = ab1;
+  r0.round = 0;
+  if ((e = round_any(0, r0, geo, count, packed, st, per_sm)) != cudaSuccess) return e;
+  RoundLaunch r1;
+  r1.h_in = h1;
+  r1.ab_in = ab1;
+  r1.f_post = f_in;
+  r1.f_out = f_out;
+  r1.round = 1;
+  return round_any(1, r1, geo, count, packed, st, per_sm);
 }
 
 }  // namespace lbmgnn

@@ -33,6 +33,14 @@ def shape(nx, ny, nb=1, plane_stride=0):
     return lbm_shape(int(nx), int(ny), int(nb), int(plane_stride))
 
 
+class lbm_lattice_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("collision", ctypes.c_int32),
+                ("tau", ctypes.c_float)]
+
+
+LBM_COLLIDE_BGK, LBM_COLLIDE_GNN = 0, 1
+
+
 _VP = ctypes.c_void_p
 _SIGS = {
     "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -70,6 +78,16 @@ _SIGS = {
                                       _VP, ctypes.c_size_t, _VP]),
     "lbm_step_gnn_noalloc": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP,
                                             _VP]),
+    "lbm_batch_plan_create": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "lbm_batch_plan_destroy": (None, [_VP]),
+    "lbm_batch_nodes": (ctypes.c_int64, [_VP]),
+    "lbm_batch_offsets": (ctypes.c_int, [_VP, _VP]),
+    "lbm_batch_workspace_bytes": (ctypes.c_size_t, [_VP]),
+    "lbm_batch_init_tgv": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+    "lbm_batch_run": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_size_t,
+                                     _VP]),
+    "lbm_autotune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "lbm_autotune_load": (ctypes.c_int, [ctypes.c_char_p]),
 }
 
 # Largest lattice (nb*ny*nx nodes) lbm_step_gnn_noalloc accepts (include/lbmgnn.h).
@@ -264,3 +282,57 @@ def lbm_step_gnn_noalloc(f_in, f_out, s, tau, taus, packed, totals, stream=None)
     check(load().lbm_step_gnn_noalloc(ptr(f_in), ptr(f_out), s, float(tau), ptr(taus),
                                       ptr(packed), ptr(totals), stream_ptr(stream)),
           "lbm_step_gnn_noalloc")
+
+
+# --- batched runs -----------------------------------------------------------------------
+def lbm_batch_plan_create(lattices):
+    """lattices: iterable of (nx, ny, collision, tau).  Returns the plan handle."""
+    lat = list(lattices)
+    arr = (lbm_lattice_desc * len(lat))(*[lbm_lattice_desc(int(a), int(b), int(c), float(t))
+                                           for a, b, c, t in lat])
+    out = ctypes.c_void_p()
+    check(load().lbm_batch_plan_create(ctypes.cast(arr, ctypes.c_void_p), len(lat),
+                                       ctypes.byref(out)), "lbm_batch_plan_create")
+    return out.value
+
+
+def lbm_batch_plan_destroy(plan):
+    load().lbm_batch_plan_destroy(plan)
+
+
+def lbm_batch_nodes(plan):
+    return load().lbm_batch_nodes(plan)
+
+
+def lbm_batch_offsets(plan, n):
+    import numpy as np
+    out = np.zeros(n, dtype=np.int64)
+    check(load().lbm_batch_offsets(plan, out.ctypes.data), "lbm_batch_offsets")
+    return out
+
+
+def lbm_batch_workspace_bytes(plan):
+    return load().lbm_batch_workspace_bytes(plan)
+
+
+def lbm_batch_init_tgv(plan, f, params, pressure_consistent=False, stream=None):
+    """params: host float64 array [n][4] = (rho0, u0, kx, ky)."""
+    import numpy as np
+    prm = np.ascontiguousarray(params, dtype=np.float64)
+    check(load().lbm_batch_init_tgv(plan, ptr(f), prm.ctypes.data, int(bool(pressure_consistent)),
+                                    stream_ptr(stream)), "lbm_batch_init_tgv")
+
+
+def lbm_batch_run(plan, f_in, f_out, f_tmp, steps, packed, workspace, ws_bytes=None, stream=None):
+    check(load().lbm_batch_run(plan, ptr(f_in), ptr(f_out), ptr(f_tmp), int(steps), ptr(packed),
+                               ptr(workspace),
+                               int(nbytes(workspace) if ws_bytes is None else ws_bytes),
+                               stream_ptr(stream)), "lbm_batch_run")
+
+
+def lbm_autotune_save(path):
+    check(load().lbm_autotune_save(str(path).encode()), "lbm_autotune_save")
+
+
+def lbm_autotune_load(path):
+    check(load().lbm_autotune_load(str(path).encode()), "lbm_autotune_load")

@@ -1,0 +1,108 @@
+"""Batched run of uneven lattices (one CUDA graph launch per call) against
+per-lattice runs of the same kernels and against the oracle.
+
+The per-node arithmetic of the batched kernels is that of the single-lattice
+kernels (each tensor-core row depends only on its own node), so each lattice
+of the batch must equal its own single-lattice run to FP32 rounding
+(<= 1e-6 relative; identical in practice)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import lbm
+from paper_2504_14494_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+LATTICES = [(8, 8, 0, 0.8), (13, 7, 1, 0.7), (32, 32, 0, 0.55), (5, 9, 1, 0.9),
+            (64, 48, 0, 1.3), (20, 20, 1, 0.62), (1, 1, 0, 0.8), (3, 130, 1, 0.75)]
+
+
+def _prm(i, nx, ny):
+    return (1.0, 0.02 + 0.01 * (i % 5), 2 * np.pi / nx, 2 * np.pi / ny)
+
+
+def test_batched_run_equals_per_lattice_runs(lbmlib, cuda, tmp_path):
+    import torch
+    L = lbmlib
+    theta = inputs.xavier_params(17, s_df=1e-3, bias_scale=0.1)
+    params = torch.from_numpy(theta).to(cuda)
+    packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=cuda)
+    L.gnn_pack(params, packed)
+    plan = L.lbm_batch_plan_create(LATTICES)
+    try:
+        n = L.lbm_batch_nodes(plan)
+        assert n == sum(a * b for a, b, _, _ in LATTICES)
+        off = L.lbm_batch_offsets(plan, len(LATTICES))
+        # BGK group first, then GNN group, input order inside each
+        order = [i for i, l in enumerate(LATTICES) if l[2] == 0] + \
+                [i for i, l in enumerate(LATTICES) if l[2] == 1]
+        acc = 0
+        for i in order:
+            assert off[i] == acc
+            acc += LATTICES[i][0] * LATTICES[i][1]
+        prm = np.array([_prm(i, l[0], l[1]) for i, l in enumerate(LATTICES)])
+        f0 = torch.empty(9 * n, device=cuda)
+        L.lbm_batch_init_tgv(plan, f0, prm, False)
+        f1, f2 = torch.empty_like(f0), torch.empty_like(f0)
+        ws = torch.empty(max(L.lbm_batch_workspace_bytes(plan), 16), dtype=torch.uint8, device=cuda)
+        steps = 3
+        L.lbm_batch_run(plan, f0, f1, f2, steps, packed, ws)
+        # replay of the recorded graph gives the same result
+        again = torch.empty_like(f0)
+        L.lbm_batch_run(plan, f0, again, f2, steps, packed, ws)
+        assert L.lbm_get_status() == 0
+        assert torch.equal(f1, again)
+        F0 = f0.view(9, n)
+        F1 = f1.view(9, n)
+        for i, (nx, ny, col, tau) in enumerate(LATTICES):
+            m = nx * ny
+            init = F0[:, off[i]:off[i] + m].contiguous()
+            ref_tgv = lbm.tgv_init(nx, ny, *prm[i]).reshape(9, -1)
+            assert np.all(np.abs(init.cpu().numpy() - ref_tgv) <= 1.2e-7 * np.abs(ref_tgv))
+            a = init.reshape(-1).clone()
+            b = torch.empty_like(a)
+            s = L.shape(nx, ny)
+            for _ in range(steps):
+                if col == 0:
+                    L.lbm_step_bgk(a, b, None, s, tau)
+                else:
+                    w = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+                    L.lbm_step_gnn(a, b, s, tau, None, packed, None, w)
+                a, b = b, a
+            got = F1[:, off[i]:off[i] + m]
+            ref = a.view(9, m)
+            assert torch.allclose(got, ref, rtol=1e-6, atol=0), (i, nx, ny, col)
+            if col == 0:
+                o = lbm.bgk_run(ref_tgv.reshape(9, ny, nx), tau, steps).reshape(9, -1)
+                assert np.allclose(got.double().cpu().numpy(), o, rtol=3e-6, atol=0)
+        # another step count re-records the graph
+        L.lbm_batch_run(plan, f0, f1, f2, 1, packed, ws)
+        ref1 = torch.empty_like(f0)
+        L.lbm_batch_run(plan, f0, ref1, f2, 2, packed, ws)
+        L.lbm_batch_run(plan, ref1, f2, again, 0, packed, ws)   # steps = 0 copies
+        assert torch.equal(ref1, f2)
+        assert L.lbm_get_status() == 0
+        path = tmp_path / "tune.json"
+        L.lbm_autotune_save(path)
+        tuned = json.loads(path.read_text())
+        assert any(k.startswith("bgk_batch/") for k in tuned)
+        assert any(k.startswith("gnn_step_table/") for k in tuned)
+        L.lbm_autotune_load(path)
+    finally:
+        L.lbm_batch_plan_destroy(plan)
+
+
+def test_batch_plan_argument_checks(lbmlib):
+    L = lbmlib
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_batch_plan_create([(8, 8, 0, 0.5)])
+    assert e.value.code == -4
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_batch_plan_create([(0, 8, 0, 0.8)])
+    assert e.value.code == -3
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_batch_plan_create([(8, 8, 7, 0.8)])
+    assert e.value.code == -1
