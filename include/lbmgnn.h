@@ -158,7 +158,7 @@ LBM_API int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape s, float tau
                          void* workspace, size_t ws_bytes, void* stream);
 
 /* Bytes of the activations gnn_forward saves for gnn_backward
- * (1,152 bytes per node): BF16 h0, h1, h2 [N][64], a0, a1 [N][64],
+ * (1,152 bytes per node): BF16 h0, h1, h2 [N][64], a0, a1 [N][64], FP16
  * AB0, AB1 [N][128] (A = W_a h | B = W_b h of each round). */
 LBM_API size_t gnn_saved_bytes(lbm_shape s);
 

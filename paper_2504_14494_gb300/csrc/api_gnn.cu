@@ -76,9 +76,9 @@ int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape shape, float tau, co
   const uint8_t* pk = static_cast<const uint8_t*>(packed);
   auto* ws = static_cast<__nv_bfloat16*>(workspace);
   __nv_bfloat16* h0 = ws;
-  __nv_bfloat16* ab0 = h0 + N * 64;
-  __nv_bfloat16* h1 = ab0 + N * 128;
-  __nv_bfloat16* ab1 = h1 + N * 64;
+  __half* ab0 = reinterpret_cast<__half*>(h0 + N * 64);
+  __nv_bfloat16* h1 = reinterpret_cast<__nv_bfloat16*>(ab0 + N * 128);
+  __half* ab1 = reinterpret_cast<__half*>(h1 + N * 64);
   if (launch_gnn_encode(f_in, true, s, pk, h0, ab0, st) != cudaSuccess) return LBM_ERR_CUDA;
   RoundLaunch r0;
   r0.h_in = h0;
@@ -128,8 +128,8 @@ int gnn_forward(const float* f_pre, lbm_shape shape, const void* packed, void* s
   __nv_bfloat16* h2 = h1 + N * 64;
   __nv_bfloat16* a0 = h2 + N * 64;
   __nv_bfloat16* a1 = a0 + N * 64;
-  __nv_bfloat16* ab0 = a1 + N * 64;
-  __nv_bfloat16* ab1 = ab0 + N * 128;
+  __half* ab0 = reinterpret_cast<__half*>(a1 + N * 64);
+  __half* ab1 = ab0 + N * 128;
   if (launch_gnn_encode(f_pre, false, s, pk, h0, ab0, st) != cudaSuccess) return LBM_ERR_CUDA;
   RoundLaunch r0;
   r0.h_in = h0;

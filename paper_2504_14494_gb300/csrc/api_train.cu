@@ -59,8 +59,8 @@ void set_saved(const void* saved, int64_t N, BackwardLaunch& bl) {
   bl.h2 = sv + 2 * N * 64;
   bl.a0 = sv + 3 * N * 64;
   bl.a1 = sv + 4 * N * 64;
-  bl.ab0 = sv + 5 * N * 64;
-  bl.ab1 = sv + 5 * N * 64 + N * 128;
+  bl.ab0 = reinterpret_cast<const __half*>(sv + 5 * N * 64);
+  bl.ab1 = reinterpret_cast<const __half*>(sv + 5 * N * 64 + N * 128);
 }
 
 }  // namespace

@@ -18,6 +18,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "umma.cuh"
@@ -62,7 +63,11 @@ constexpr uint32_t WNT = 49152;    // SW128 [128 in x 64 out]
 constexpr uint32_t CK = 65536;     // fp32 [8][64]: c_k = W_c e_k + b_e, k = 1..8
 constexpr uint32_t BE = 67584;     // fp32 [64]
 constexpr uint32_t BN = 67840;     // fp32 [64]
-constexpr uint32_t TOTAL = ROUND0 + 2 * ROUND_SIZE;  // 162816
+// SW128 [64 out x 64]: k 0..11 = W1 (BF16), k 16..27 = W1 again, rest 0; the
+// encoder's first layer multiplies it with [x_hi | x_lo] (x = x_hi + x_lo,
+// both BF16), which keeps ~16 bits of the FP32 features.
+constexpr uint32_t W1X = ROUND0 + 2 * ROUND_SIZE;  // 162816
+constexpr uint32_t TOTAL = W1X + 8192;              // 171008
 __host__ __device__ constexpr uint32_t round_base(int r) { return ROUND0 + r * ROUND_SIZE; }
 }  // namespace K
 
@@ -105,6 +110,48 @@ __device__ __forceinline__ uint4 pack_bf16x8(const float* v) {
   return make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
                     pack_bf16x2(v[6], v[7]));
 }
+// FP16 vectors (the edge terms A | B are stored as FP16: 11-bit significand).
+__device__ __forceinline__ void unpack_h8(const uint4& u, float* out) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
+    out[2 * i] = f.x;
+    out[2 * i + 1] = f.y;
+  }
+}
+__device__ __forceinline__ uint4 pack_h8(const float* v) {
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __half2 h = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+    w[i] = *reinterpret_cast<const uint32_t*>(&h);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+__device__ __forceinline__ void st_h32(__half* p, const float* v) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) q[c] = pack_h8(v + 8 * c);
+}
+__device__ __forceinline__ __half2 u32_as_h2(uint32_t u) {
+  return *reinterpret_cast<const __half2*>(&u);
+}
+__device__ __forceinline__ __half2 tanh_h2(__half2 x) {
+  uint32_t y;
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(y) : "r"(*reinterpret_cast<const uint32_t*>(&x)));
+  return u32_as_h2(y);
+}
+// GELU (tanh form) on two FP16 values: 0.5 z (1 + tanh(z (c0 + c1 z^2))).
+__device__ __forceinline__ __half2 gelu_h2(__half2 z) {
+  const __half2 c0 = __float2half2_rn(0.7978845608028654f);
+  const __half2 c1 = __float2half2_rn(0.0356774081363001f);
+  const __half2 hh = __float2half2_rn(0.5f);
+  const __half2 u = __hmul2(z, __hfma2(c1, __hmul2(z, z), c0));
+  const __half2 hz = __hmul2(hh, z);
+  return __hfma2(hz, tanh_h2(u), hz);
+}
+
 __device__ __forceinline__ float bf16_round(float v) {
   return __bfloat162float(__float2bfloat16_rn(v));
 }
@@ -247,12 +294,12 @@ struct TcShared {
   int abort;
 };
 
-__device__ __forceinline__ void tc_setup(TcShared* sh, TcCtx& tc) {
+__device__ __forceinline__ void tc_setup(TcShared* sh, TcCtx& tc, uint32_t ncols = 256) {
   if (threadIdx.x == 0) {
     mbar_init(&sh->bar, 1);
     sh->abort = 0;
   }
-  if ((threadIdx.x >> 5) == 0) tmem_alloc(&sh->tmem, 256);
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(&sh->tmem, ncols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -261,10 +308,11 @@ __device__ __forceinline__ void tc_setup(TcShared* sh, TcCtx& tc) {
   tc.phase = 0;
 }
 
-__device__ __forceinline__ void tc_teardown(TcShared* sh, const TcCtx& tc) {
+__device__ __forceinline__ void tc_teardown(TcShared* sh, const TcCtx& tc,
+                                            uint32_t ncols = 256) {
   tc_fence_before();
   __syncthreads();
-  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tc.tmem, 256);
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tc.tmem, ncols);
 }
 
 // Issues the MMA chain (thread 0) after all threads wrote their operands,

@@ -4,7 +4,7 @@
 // the deterministic gradient reduction and the AdamW update.
 //
 // Per-round recompute: the forward saves h, the aggregated messages a and
-// the per-node edge terms A = W_a h, B = W_b h (BF16); the backward recomputes
+// the per-node edge terms A = W_a h, B = W_b h (FP16); the backward recomputes
 // the node pre-activation W_n [h; a] + b_n with the same MMA and every edge
 // pre-activation z_ik = A_i + B_j + c_k elementwise, so the 8 per-node edge
 // activations are never stored.
@@ -337,7 +337,7 @@ constexpr uint32_t DAB = 0, DABT = 32768, DCT = 65536, HT = 98304, WABT = 118784
 }
 
 __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
-    const __nv_bfloat16* __restrict__ ab, const float* __restrict__ da,
+    const __half* __restrict__ ab, const float* __restrict__ da,
     const float* __restrict__ dh_part, const __nv_bfloat16* __restrict__ h_in,
     float* __restrict__ dh_in, int round, float* __restrict__ G, Shape s,
     const uint8_t* __restrict__ packed, unsigned* stw) {
@@ -373,11 +373,11 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
       float Aj[16], daj[16], Bj[16], gA[16], gx[16], gy[16], gB[16];
       {
         const uint4* q = reinterpret_cast<const uint4*>(ab + nn * 128 + c0);
-        unpack_bf16x8(__ldg(q), Aj);
-        unpack_bf16x8(__ldg(q + 1), Aj + 8);
+        unpack_h8(__ldg(q), Aj);
+        unpack_h8(__ldg(q + 1), Aj + 8);
         q = reinterpret_cast<const uint4*>(ab + nn * 128 + HID + c0);
-        unpack_bf16x8(__ldg(q), Bj);
-        unpack_bf16x8(__ldg(q + 1), Bj + 8);
+        unpack_h8(__ldg(q), Bj);
+        unpack_h8(__ldg(q + 1), Bj + 8);
         const float4* r = reinterpret_cast<const float4*>(da + nn * HID + c0);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -394,8 +394,8 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
           const int64_t j = node_at(p, ex(k), ey(k), s);
           float Bn[16];
           const uint4* q = reinterpret_cast<const uint4*>(ab + j * 128 + HID + c0);
-          unpack_bf16x8(__ldg(q), Bn);
-          unpack_bf16x8(__ldg(q + 1), Bn + 8);
+          unpack_h8(__ldg(q), Bn);
+          unpack_h8(__ldg(q + 1), Bn + 8);
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
             const float g = daj[c] * gelu_grad(Aj[c] + Bn[c] + c_k[c]);
@@ -408,8 +408,8 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
           const int64_t i = node_at(p, -ex(k), -ey(k), s);
           float Ai[16], dai[16];
           const uint4* q = reinterpret_cast<const uint4*>(ab + i * 128 + c0);
-          unpack_bf16x8(__ldg(q), Ai);
-          unpack_bf16x8(__ldg(q + 1), Ai + 8);
+          unpack_h8(__ldg(q), Ai);
+          unpack_h8(__ldg(q + 1), Ai + 8);
           const float4* r = reinterpret_cast<const float4*>(da + i * HID + c0);
 #pragma unroll
           for (int t4 = 0; t4 < 4; ++t4) {
@@ -705,7 +705,7 @@ cudaError_t launch_gnn_backward(const BackwardLaunch& bl, const Shape& s, const 
   // rounds 2 and 1 (index 1, 0): dh[0] -> dh[1] (part) -> dh[0] (in)
   const __nv_bfloat16* hs[2] = {bl.h0, bl.h1};
   const __nv_bfloat16* as[2] = {bl.a0, bl.a1};
-  const __nv_bfloat16* abs_[2] = {bl.ab0, bl.ab1};
+  const __half* abs_[2] = {bl.ab0, bl.ab1};
   for (int r = 1; r >= 0; --r) {
     {
       const uint32_t bytes = rb1::BYTES + 1024;

@@ -49,6 +49,12 @@ __global__ void gnn_pack_kernel(const float* __restrict__ p, uint8_t* __restrict
     const int o = e / HID, i = e % HID;
     put_sw(out + K::WH, o, i, o < NOUT ? p[P::HEAD_W + o * HID + i] : 0.0f);
   }
+  for (int e = tid; e < HID * HID; e += nth) {
+    const int o = e / HID, k = e % HID;
+    const int j = k < 16 ? k : k - 16;
+    const float w = (k < 32 && j < NFEAT) ? p[P::ENC1_W + o * NFEAT + j] : 0.0f;
+    put_sw(out + K::W1X, o, k, w);
+  }
   for (int r = 0; r < 2; ++r) {
     const float* pr = p + P::ROUND0 + r * P::ROUND_SIZE;
     uint8_t* kr = out + K::round_base(r);
@@ -82,27 +88,36 @@ __global__ void gnn_pack_kernel(const float* __restrict__ p, uint8_t* __restrict
 
 // ---------------------------------------------------------------------------
 // Encoder: pre-collision populations -> h0 (BF16) and the round-0 edge terms.
+// Layer 1 (12 -> 64) runs on the tensor cores on [x_hi | x_lo] (see K::W1X),
+// layer 2 and the round-0 edge terms A | B as BF16 MMAs; 128 TMEM columns are
+// reused by the three products, so up to 3 CTAs share an SM.
 namespace enc {
-constexpr uint32_t W2 = 0, WAB = 8192, X = 24576, W1F = 40960, B1 = 44032, B2 = 44288,
-                   NORM = 44544, SH = 44672, BYTES = 44800;
+constexpr uint32_t W1X = 0, W2 = 8192, WAB = 16384, X1 = 32768, X = 49152, B1 = 65536,
+                   B2 = 65792, NORM = 66048, SH = 66176, BYTES = 66304;
 }
 
 template <bool PULL, class Geo>
-__global__ void __launch_bounds__(256, 2) gnn_encode_kernel(
+__global__ void __launch_bounds__(256, 3) gnn_encode_kernel(
     const float* __restrict__ f, Geo geo, const uint8_t* __restrict__ packed,
-    __nv_bfloat16* __restrict__ h0_out, __nv_bfloat16* __restrict__ ab_out, unsigned* stw) {
+    __nv_bfloat16* __restrict__ h0_out, __half* __restrict__ ab_out, unsigned* stw) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   TcShared* sh = reinterpret_cast<TcShared*>(sm + enc::SH);
+  copy_g2s(sm + enc::W1X, packed + K::W1X, 8192);
   copy_g2s(sm + enc::W2, packed + K::W2, 8192);
   copy_g2s(sm + enc::WAB, packed + K::round_base(0) + K::WAB, 16384);
-  copy_g2s(sm + enc::W1F, packed + K::W1F, 3072 + 256 + 256 + 128);  // W1F, B1, B2, NORM
+  copy_g2s(sm + enc::B1, packed + K::B1, 256 + 256 + 128);  // B1, B2, NORM
+  __syncthreads();
+  if (threadIdx.x < NFEAT) {  // sigma -> 1/sigma
+    float* nrm = reinterpret_cast<float*>(sm + enc::NORM);
+    nrm[NFEAT + threadIdx.x] = 1.0f / nrm[NFEAT + threadIdx.x];
+  }
   TcCtx tc;
-  tc_setup(sh, tc);
-  const float* w1 = reinterpret_cast<const float*>(sm + enc::W1F);
+  tc_setup(sh, tc, 128);
   const float* b1 = reinterpret_cast<const float*>(sm + enc::B1);
   const float* b2 = reinterpret_cast<const float*>(sm + enc::B2);
   const float* nrm = reinterpret_cast<const float*>(sm + enc::NORM);
+  uint8_t* X1 = sm + enc::X1;
   uint8_t* X = sm + enc::X;
   const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
   const uint32_t lb = lane_base(tc.tmem);
@@ -114,56 +129,66 @@ __global__ void __launch_bounds__(256, 2) gnn_encode_kernel(
     const int64_t n = tile * TILE + node;
     const bool on = n < N;
     const int64_t nn = on ? n : N - 1;
-    float fv[Q];
-    if (PULL) {
-      const GeoPos p = geo.pos(base + nn);
+    {
+      float fv[Q];
+      if (PULL) {
+        const GeoPos p = geo.pos(base + nn);
 #pragma unroll
-      for (int q = 0; q < Q; ++q) fv[q] = __ldg(f + q * ps + geo_nbr(p, -ex(q), -ey(q)));
-    } else {
+        for (int q = 0; q < Q; ++q) fv[q] = __ldg(f + q * ps + geo_nbr(p, -ex(q), -ey(q)));
+      } else {
 #pragma unroll
-      for (int q = 0; q < Q; ++q) fv[q] = __ldg(f + q * ps + base + nn);
+        for (int q = 0; q < Q; ++q) fv[q] = __ldg(f + q * ps + base + nn);
+      }
+      const Moments m = moments9(fv);
+      float xh[16];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) xh[q] = (fv[q] - nrm[q]) * nrm[NFEAT + q];
+      xh[9] = (m.rho - nrm[9]) * nrm[NFEAT + 9];
+      xh[10] = (m.ux - nrm[10]) * nrm[NFEAT + 10];
+      xh[11] = (m.uy - nrm[11]) * nrm[NFEAT + 11];
+      xh[12] = xh[13] = xh[14] = xh[15] = 0.0f;
+      // half 0 writes x_hi (k 0..15), half 1 writes x_lo = x - x_hi (k 16..31)
+      float v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float hi = bf16_round(xh[j]);
+        v[j] = half == 0 ? hi : xh[j] - hi;
+      }
+      const int ch = half * 2;
+      *reinterpret_cast<uint4*>(X1 + node * 128 + ((ch ^ (node & 7)) << 4)) = pack_bf16x8(v);
+      *reinterpret_cast<uint4*>(X1 + node * 128 + (((ch + 1) ^ (node & 7)) << 4)) =
+          pack_bf16x8(v + 8);
     }
-    const Moments m = moments9(fv);
-    float xh[NFEAT];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) xh[q] = (fv[q] - nrm[q]) / nrm[NFEAT + q];
-    xh[9] = (m.rho - nrm[9]) / nrm[NFEAT + 9];
-    xh[10] = (m.ux - nrm[10]) / nrm[NFEAT + 10];
-    xh[11] = (m.uy - nrm[11]) / nrm[NFEAT + 11];
+    if (!tc_run(sh, tc, stw, [&] {
+          umma_128xN(tc.tmem, smem_u32(X1), 0, smem_u32(sm + enc::W1X), 0, 1, 64, false, 2);
+        }))
+      break;
     float g[32];
+    tmem_ld32(lb + f0, g);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      float z = b1[f0 + c];
-#pragma unroll
-      for (int j = 0; j < NFEAT; ++j) z = fmaf(w1[(f0 + c) * NFEAT + j], xh[j], z);
-      g[c] = gelu(z);
-    }
+    for (int c = 0; c < 32; ++c) g[c] = gelu(g[c] + b1[f0 + c]);
     st_row32(X, node, f0, g);
     if (!tc_run(sh, tc, stw, [&] {
           umma_128xN(tc.tmem, smem_u32(X), 0, smem_u32(sm + enc::W2), 0, 1, 64, false);
         }))
       break;
-    float h[32];
-    tmem_ld32(lb + f0, h);
+    tmem_ld32(lb + f0, g);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) h[c] = gelu(h[c] + b2[f0 + c]);
-    if (on && h0_out) st_g32(h0_out + n * HID + f0, h);
-    st_row32(X, node, f0, h);  // the MMA that read X has completed
+    for (int c = 0; c < 32; ++c) g[c] = gelu(g[c] + b2[f0 + c]);
+    if (on && h0_out) st_g32(h0_out + n * HID + f0, g);
+    st_row32(X, node, f0, g);  // the MMA that read X has completed
     if (!tc_run(sh, tc, stw, [&] {
-          umma_128xN(tc.tmem + 64, smem_u32(X), 0, smem_u32(sm + enc::WAB), 0, 1, 128, false);
+          umma_128xN(tc.tmem, smem_u32(X), 0, smem_u32(sm + enc::WAB), 0, 1, 128, false);
         }))
       break;
-    float a[32], b[32];
-    tmem_ld32(lb + 64 + f0, a);
-    tmem_ld32(lb + 128 + f0, b);
-    if (on) {
-      st_g32(ab_out + n * 128 + f0, a);
-      st_g32(ab_out + n * 128 + HID + f0, b);
-    }
+    tmem_ld32(lb + f0, g);
+    if (on) st_h32(ab_out + n * 128 + f0, g);
+    tmem_ld32(lb + HID + f0, g);
+    if (on) st_h32(ab_out + n * 128 + HID + f0, g);
     tc_fence_before();
     __syncthreads();
   }
-  tc_teardown(sh, tc);
+  tc_teardown(sh, tc, 128);
 }
 
 // ---------------------------------------------------------------------------
@@ -172,15 +197,15 @@ __global__ void __launch_bounds__(256, 2) gnn_encode_kernel(
 // MODE 2: last round + head -> y [10][N] (FP32) and h_out = h2.
 namespace rnd {
 constexpr uint32_t HA = 0, WN = 32768, WX = 49152, CK = 65536, BN = 67584, BH = 67840,
-                   NORM = 67904, SH = 68032, BYTES = 68096;
+                   NORM = 67904, CKH = 68032, SH = 69056, BYTES = 69120;
 }
 
 struct RoundArgs {
   const __nv_bfloat16* h_in;   // [N][64]
-  const __nv_bfloat16* ab_in;  // [N][128]: A = W_a h, B = W_b h of this round
+  const __half* ab_in;         // [N][128] FP16: A = W_a h, B = W_b h of this round
   __nv_bfloat16* h_out;        // [N][64] (MODE 0, 2) or NULL
   __nv_bfloat16* a_out;        // [N][64] aggregated messages (saved for training) or NULL
-  __nv_bfloat16* ab_out;       // [N][128] next round's A, B (MODE 0)
+  __half* ab_out;              // [N][128] next round's A, B (MODE 0), FP16
   float* y_out;                // [10][N] (MODE 2)
   const float* f_post;         // stored state to pull from (MODE 1)
   float* f_out;                // MODE 1
@@ -206,9 +231,16 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Geo geo
   copy_g2s(sm + rnd::BN, kr + K::BN, 256);
   copy_g2s(sm + rnd::BH, packed + K::BH, 64);
   copy_g2s(sm + rnd::NORM, packed + K::NORM, 128);
+  __syncthreads();
+  {  // c_k as FP16 pairs
+    const float* ckf = reinterpret_cast<const float*>(sm + rnd::CK);
+    __half2* ckw = reinterpret_cast<__half2*>(sm + rnd::CKH);
+    for (int i = threadIdx.x; i < 8 * HID / 2; i += blockDim.x)
+      ckw[i] = __floats2half2_rn(ckf[2 * i], ckf[2 * i + 1]);
+  }
   TcCtx tc;
   tc_setup(sh, tc);
-  const float* ck = reinterpret_cast<const float*>(sm + rnd::CK);
+  const __half2* ckh = reinterpret_cast<const __half2*>(sm + rnd::CKH);
   const float* bn = reinterpret_cast<const float*>(sm + rnd::BN);
   const float* bh = reinterpret_cast<const float*>(sm + rnd::BH);
   const float* nrm = reinterpret_cast<const float*>(sm + rnd::NORM);
@@ -225,22 +257,57 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Geo geo
     const bool on = n < N;
     const int64_t nn = on ? n : N - 1;
     const GeoPos p = geo.pos(base + nn);
-    // messages m_ik = GELU(A_i + B_j + c_k), summed over the 8 neighbours
-    float A[32], acc[32];
-    ld_g32(ra.ab_in + nn * 128 + f0, A);
+    // messages m_ik = GELU(A_i + B_j + c_k), summed over the 8 neighbours, in
+    // packed FP16 pairs; per 16-feature chunk the 8 neighbour loads are
+    // issued together.
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = 0.0f;
-#pragma unroll 1
-    for (int k = 1; k < Q; ++k) {
-      const int64_t j = geo_nbr(p, ex(k), ey(k)) - base;
-      float B[32];
-      ld_g32(ra.ab_in + j * 128 + HID + f0, B);
-      const float* c_k = ck + (k - 1) * HID + f0;
+    for (int sc = 0; sc < 2; ++sc) {
+      const int c0 = f0 + 16 * sc;
+      uint4 braw[8][2];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) acc[c] += gelu(A[c] + B[c] + c_k[c]);
+      for (int k = 0; k < 8; ++k) {
+        const int64_t j = geo_nbr(p, ex(k + 1), ey(k + 1)) - base;
+        const uint4* q = reinterpret_cast<const uint4*>(ra.ab_in + j * 128 + HID + c0);
+        braw[k][0] = __ldg(q);
+        braw[k][1] = __ldg(q + 1);
+      }
+      uint4 araw[2];
+      {
+        const uint4* q = reinterpret_cast<const uint4*>(ra.ab_in + nn * 128 + c0);
+        araw[0] = __ldg(q);
+        araw[1] = __ldg(q + 1);
+      }
+      const uint32_t* aw = reinterpret_cast<const uint32_t*>(araw);
+      __half2 acc[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[c] = __float2half2_rn(0.0f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t* bw = reinterpret_cast<const uint32_t*>(braw[k]);
+        const __half2* c_k = ckh + k * (HID / 2) + c0 / 2;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const __half2 z = __hadd2(__hadd2(u32_as_h2(aw[c]), c_k[c]), u32_as_h2(bw[c]));
+          acc[c] = __hadd2(acc[c], gelu_h2(z));
+        }
+      }
+      float av[16];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float2 t = __half22float2(acc[c]);
+        av[2 * c] = t.x;
+        av[2 * c + 1] = t.y;
+      }
+      const int ch = c0 >> 3;
+      *reinterpret_cast<uint4*>(Ag + node * 128 + ((ch ^ (node & 7)) << 4)) = pack_bf16x8(av);
+      *reinterpret_cast<uint4*>(Ag + node * 128 + (((ch + 1) ^ (node & 7)) << 4)) =
+          pack_bf16x8(av + 8);
+      if (on && ra.a_out) {
+        uint4* q = reinterpret_cast<uint4*>(ra.a_out + n * HID + c0);
+        q[0] = pack_bf16x8(av);
+        q[1] = pack_bf16x8(av + 8);
+      }
     }
-    st_row32(Ag, node, f0, acc);
-    if (on && ra.a_out) st_g32(ra.a_out + n * HID + f0, acc);
     float h[32];
     ld_g32(ra.h_in + nn * HID + f0, h);
     st_row32(H, node, f0, h);
@@ -264,8 +331,8 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Geo geo
       tmem_ld32(lb + 64 + f0, a);
       tmem_ld32(lb + 128 + f0, b);
       if (on) {
-        st_g32(ra.ab_out + n * 128 + f0, a);
-        st_g32(ra.ab_out + n * 128 + HID + f0, b);
+        st_h32(ra.ab_out + n * 128 + f0, a);
+        st_h32(ra.ab_out + n * 128 + HID + f0, b);
       }
     } else {
       if (!tc_run(sh, tc, stw, [&] {
@@ -320,12 +387,12 @@ cudaError_t launch_gnn_pack(const float* params, uint8_t* packed, cudaStream_t s
 
 template <class Geo>
 static cudaError_t encode_any(const float* f, bool pull, const Geo& geo, int64_t N,
-                              const uint8_t* packed, __nv_bfloat16* h0, __nv_bfloat16* ab,
+                              const uint8_t* packed, __nv_bfloat16* h0, __half* ab,
                               cudaStream_t st, int per_sm = 2) {
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
   const uint32_t bytes = enc::BYTES + 1024;
-  const unsigned grid = grid_for(N, per_sm);
+  const unsigned grid = grid_for(N, per_sm + (per_sm >= 2 ? 1 : 0));
   cudaError_t e;
   if (pull) {
     if ((e = set_smem(gnn_encode_kernel<true, Geo>, bytes)) != cudaSuccess) return e;
@@ -365,7 +432,7 @@ static cudaError_t round_any(int mode, const RoundLaunch& rl, const Geo& geo, in
 }
 
 cudaError_t launch_gnn_encode(const float* f, bool pull, const Shape& s, const uint8_t* packed,
-                              __nv_bfloat16* h0, __nv_bfloat16* ab, cudaStream_t st) {
+                              __nv_bfloat16* h0, __half* ab, cudaStream_t st) {
   return encode_any(f, pull, GeoStack{s}, (int64_t)s.nb * s.ny * s.nx, packed, h0, ab, st);
 }
 
@@ -381,9 +448,9 @@ cudaError_t launch_gnn_step_table(const float* f_in, float* f_out, const LatDesc
   if (count <= 0) return cudaSuccess;
   const GeoTable geo{lat, first, n, base, count, ps};
   __nv_bfloat16* h0 = ws;
-  __nv_bfloat16* ab0 = h0 + count * 64;
-  __nv_bfloat16* h1 = ab0 + count * 128;
-  __nv_bfloat16* ab1 = h1 + count * 64;
+  __half* ab0 = reinterpret_cast<__half*>(h0 + count * 64);
+  __nv_bfloat16* h1 = reinterpret_cast<__nv_bfloat16*>(ab0 + count * 128);
+  __half* ab1 = reinterpret_cast<__half*>(h1 + count * 64);
   cudaError_t e;
   if ((e = encode_any(f_in, true, geo, count, packed, h0, ab0, st, per_sm)) != cudaSuccess)
     return e;

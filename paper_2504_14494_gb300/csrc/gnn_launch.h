@@ -1,6 +1,7 @@
 // Internal launchers of the GNN kernels (forward, backward, training).
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -9,10 +10,10 @@ namespace lbmgnn {
 
 struct RoundLaunch {
   const __nv_bfloat16* h_in = nullptr;
-  const __nv_bfloat16* ab_in = nullptr;
+  const __half* ab_in = nullptr;     // A | B, FP16
   __nv_bfloat16* h_out = nullptr;
   __nv_bfloat16* a_out = nullptr;
-  __nv_bfloat16* ab_out = nullptr;
+  __half* ab_out = nullptr;
   float* y_out = nullptr;
   const float* f_post = nullptr;
   float* f_out = nullptr;
@@ -23,7 +24,7 @@ struct RoundLaunch {
 
 cudaError_t launch_gnn_pack(const float* params, uint8_t* packed, cudaStream_t st);
 cudaError_t launch_gnn_encode(const float* f, bool pull, const Shape& s, const uint8_t* packed,
-                              __nv_bfloat16* h0, __nv_bfloat16* ab, cudaStream_t st);
+                              __nv_bfloat16* h0, __half* ab, cudaStream_t st);
 // mode 0: inner round; 1: last round + head + Eq. 3 collision; 2: last round + head -> y
 cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
                              const uint8_t* packed, cudaStream_t st);
@@ -50,8 +51,8 @@ struct BackwardLaunch {
   const __nv_bfloat16* h2 = nullptr;
   const __nv_bfloat16* a0 = nullptr;
   const __nv_bfloat16* a1 = nullptr;
-  const __nv_bfloat16* ab0 = nullptr;
-  const __nv_bfloat16* ab1 = nullptr;
+  const __half* ab0 = nullptr;             // FP16 edge terms
+  const __half* ab1 = nullptr;
   float* dh[2] = {nullptr, nullptr};       // FP32 [N][64] ping-pong
   float* da = nullptr;                     // FP32 [N][64]
   float* G = nullptr;                      // FP32 [GRAD_ROWS][38922]

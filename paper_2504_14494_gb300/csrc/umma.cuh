@@ -120,13 +120,13 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 // D (M=128 rows) = sum over kb < nkb of A_kb * B_kb^T, where A_kb and B_kb are
 // SW128 blocks of 128 and N rows at a_addr + kb*a_stride, b_addr + kb*b_stride
 // (shared-space byte addresses).  Issued by a single thread.
+// `nks` (<= 4) is the number of 16-wide K steps used in each block.
 __device__ __forceinline__ void umma_128xN(uint32_t tmem_d, uint32_t a_addr, uint32_t a_stride,
                                            uint32_t b_addr, uint32_t b_stride, int nkb, int N,
-                                           bool accumulate) {
+                                           bool accumulate, int nks = 4) {
   const uint32_t id = idesc_bf16(128, N);
   for (int kb = 0; kb < nkb; ++kb) {
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
+    for (int ks = 0; ks < nks; ++ks) {
       const uint64_t ad = sw128_desc(a_addr + kb * a_stride + ks * 32);
       const uint64_t bd = sw128_desc(b_addr + kb * b_stride + ks * 32);
       umma_bf16(tmem_d, ad, bd, id, (accumulate || kb > 0 || ks > 0) ? 1u : 0u);
