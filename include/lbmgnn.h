@@ -158,8 +158,11 @@ LBM_API int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape s, float tau
                          void* workspace, size_t ws_bytes, void* stream);
 
 /* Bytes of the activations gnn_forward saves for gnn_backward
- * (1,152 bytes per node): BF16 h0, h1, h2 [N][64], a0, a1 [N][64], FP16
- * AB0, AB1 [N][128] (A = W_a h | B = W_b h of each round). */
+ * (1,152 bytes per node), in this order: BF16 h0, h1, h2 [N][64] (node
+ * states after the encoder and each round), BF16 a0, a1 [N][64] (aggregated
+ * messages of each round), FP16 AB0, AB1 [N][128] (A = W_a h | B = W_b h of
+ * each round).  Each tensor [N][F] is stored in planes of 8 values: value
+ * (n, f) at element ((f / 8) * N + n) * 8 + f % 8 of the tensor. */
 LBM_API size_t gnn_saved_bytes(lbm_shape s);
 
 /* Network forward on PRE-collision populations f_pre (device, shape s):

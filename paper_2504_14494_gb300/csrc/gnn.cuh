@@ -186,6 +186,58 @@ __device__ __forceinline__ void st_g32(__nv_bfloat16* p, const float* v) {
   for (int c = 0; c < 4; ++c) q[c] = pack_bf16x8(v + 8 * c);
 }
 
+// ---- chunked ("plane") layout of per-node activations ---------------------------
+// A per-node tensor [N][F] is stored as F/8 planes (2-byte types) or F/4
+// planes (FP32) of N nodes x 16 bytes: value (n, f) of a 2-byte tensor sits at
+// ((f / 8) * N + n) * 8 + f % 8, of an FP32 tensor at ((f / 4) * N + n) * 4 +
+// f % 4.  A warp reading one 16-byte chunk of 32 consecutive nodes then reads
+// 512 contiguous bytes.
+template <typename T>
+__device__ __forceinline__ const uint4* chunk8(const T* base, int64_t N, int64_t n, int f) {
+  return reinterpret_cast<const uint4*>(base + ((int64_t)(f >> 3) * N + n) * 8);
+}
+template <typename T>
+__device__ __forceinline__ uint4* chunk8w(T* base, int64_t N, int64_t n, int f) {
+  return reinterpret_cast<uint4*>(base + ((int64_t)(f >> 3) * N + n) * 8);
+}
+__device__ __forceinline__ const float4* chunk4(const float* base, int64_t N, int64_t n, int f) {
+  return reinterpret_cast<const float4*>(base + ((int64_t)(f >> 2) * N + n) * 4);
+}
+__device__ __forceinline__ float4* chunk4w(float* base, int64_t N, int64_t n, int f) {
+  return reinterpret_cast<float4*>(base + ((int64_t)(f >> 2) * N + n) * 4);
+}
+// 32 BF16 values (features f0..f0+31) of node n / their store.
+__device__ __forceinline__ void ld_pb32(const __nv_bfloat16* base, int64_t N, int64_t n, int f0,
+                                        float* v) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) unpack_bf16x8(__ldg(chunk8(base, N, n, f0 + 8 * c)), v + 8 * c);
+}
+__device__ __forceinline__ void st_pb32(__nv_bfloat16* base, int64_t N, int64_t n, int f0,
+                                        const float* v) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) *chunk8w(base, N, n, f0 + 8 * c) = pack_bf16x8(v + 8 * c);
+}
+__device__ __forceinline__ void st_ph32(__half* base, int64_t N, int64_t n, int f0, const float* v) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) *chunk8w(base, N, n, f0 + 8 * c) = pack_h8(v + 8 * c);
+}
+// 32 FP32 values (features f0..f0+31) of node n / their store.
+__device__ __forceinline__ void ld_pf32(const float* base, int64_t N, int64_t n, int f0, float* v) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float4 t = __ldg(chunk4(base, N, n, f0 + 4 * c));
+    v[4 * c] = t.x;
+    v[4 * c + 1] = t.y;
+    v[4 * c + 2] = t.z;
+    v[4 * c + 3] = t.w;
+  }
+}
+__device__ __forceinline__ void st_pf32(float* base, int64_t N, int64_t n, int f0, const float* v) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    *chunk4w(base, N, n, f0 + 4 * c) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+}
+
 // Node coordinates within the stacked lattices.
 struct NodeXY {
   int x, y;

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(256, 2) gnn_head_bwd_kernel(
       st_col<NOUT>(XT, 128, 0, node, d);
     }
     float hv[32];
-    ld_g32(h2 + nn * HID + f0, hv);
+    ld_pb32(h2, N, nn, f0, hv);
     st_col<32>(YT, 80, f0, node, hv);
     __syncthreads();
     float dv[32];
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(256, 2) gnn_head_bwd_kernel(
 #pragma unroll
       for (int c = 0; c < 32; ++c) dv[c] = fmaf(g, whf[o * HID + f0 + c], dv[c]);
     }
-    if (on) st_f32x32(dh + n * HID + f0, dv);
+    if (on) st_pf32(dh, N, n, f0, dv);
     const bool acc = !first;
     if (!tc_run(sh, tc, stw, [&] {
           umma_128xN(tc.tmem, smem_u32(XT), 16384, smem_u32(YT), 10240, 2, 80, acc);
@@ -264,8 +264,8 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd1_kernel(
     const int64_t nn = on ? n : N - 1;
     {
       float h[32], a[32];
-      ld_g32(h_in + nn * HID + f0, h);
-      ld_g32(a_in + nn * HID + f0, a);
+      ld_pb32(h_in, N, nn, f0, h);
+      ld_pb32(a_in, N, nn, f0, a);
       st_row32(HA, node, f0, h);
       st_row32(HA + 16384, node, f0, a);
       st_col<32>(HAT, 128, f0, node, h);
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd1_kernel(
     }
     float dz[32], dho[32];
     tmem_ld32(lb + f0, dz);
-    ld_f32x32(dh_out + nn * HID + f0, dho);
+    ld_pf32(dh_out, N, nn, f0, dho);
 #pragma unroll
     for (int c = 0; c < 32; ++c) dz[c] = on ? dho[c] * gelu_grad(dz[c] + bn[f0 + c]) : 0.0f;
     st_row32(DZ, node, f0, dz);
@@ -300,10 +300,10 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd1_kernel(
     if (on) {
 #pragma unroll
       for (int c = 0; c < 32; ++c) d[c] += dho[c];
-      st_f32x32(dh_part + n * HID + f0, d);
+      st_pf32(dh_part, N, n, f0, d);
     }
     tmem_ld32(lb + HID + f0, d);
-    if (on) st_f32x32(da + n * HID + f0, d);
+    if (on) st_pf32(da, N, n, f0, d);
     tc_fence_before();
     __syncthreads();
   }
@@ -372,16 +372,13 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
       const int c0 = f0 + 16 * sc;
       float Aj[16], daj[16], Bj[16], gA[16], gx[16], gy[16], gB[16];
       {
-        const uint4* q = reinterpret_cast<const uint4*>(ab + nn * 128 + c0);
-        unpack_h8(__ldg(q), Aj);
-        unpack_h8(__ldg(q + 1), Aj + 8);
-        q = reinterpret_cast<const uint4*>(ab + nn * 128 + HID + c0);
-        unpack_h8(__ldg(q), Bj);
-        unpack_h8(__ldg(q + 1), Bj + 8);
-        const float4* r = reinterpret_cast<const float4*>(da + nn * HID + c0);
+        unpack_h8(__ldg(chunk8(ab, N, nn, c0)), Aj);
+        unpack_h8(__ldg(chunk8(ab, N, nn, c0 + 8)), Aj + 8);
+        unpack_h8(__ldg(chunk8(ab, N, nn, HID + c0)), Bj);
+        unpack_h8(__ldg(chunk8(ab, N, nn, HID + c0 + 8)), Bj + 8);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const float4 t = __ldg(r + i);
+          const float4 t = __ldg(chunk4(da, N, nn, c0 + 4 * i));
           daj[4 * i] = t.x; daj[4 * i + 1] = t.y; daj[4 * i + 2] = t.z; daj[4 * i + 3] = t.w;
         }
       }
@@ -393,9 +390,8 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
         {
           const int64_t j = node_at(p, ex(k), ey(k), s);
           float Bn[16];
-          const uint4* q = reinterpret_cast<const uint4*>(ab + j * 128 + HID + c0);
-          unpack_h8(__ldg(q), Bn);
-          unpack_h8(__ldg(q + 1), Bn + 8);
+          unpack_h8(__ldg(chunk8(ab, N, j, HID + c0)), Bn);
+          unpack_h8(__ldg(chunk8(ab, N, j, HID + c0 + 8)), Bn + 8);
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
             const float g = daj[c] * gelu_grad(Aj[c] + Bn[c] + c_k[c]);
@@ -407,13 +403,11 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
         {
           const int64_t i = node_at(p, -ex(k), -ey(k), s);
           float Ai[16], dai[16];
-          const uint4* q = reinterpret_cast<const uint4*>(ab + i * 128 + c0);
-          unpack_h8(__ldg(q), Ai);
-          unpack_h8(__ldg(q + 1), Ai + 8);
-          const float4* r = reinterpret_cast<const float4*>(da + i * HID + c0);
+          unpack_h8(__ldg(chunk8(ab, N, i, c0)), Ai);
+          unpack_h8(__ldg(chunk8(ab, N, i, c0 + 8)), Ai + 8);
 #pragma unroll
           for (int t4 = 0; t4 < 4; ++t4) {
-            const float4 t = __ldg(r + t4);
+            const float4 t = __ldg(chunk4(da, N, i, c0 + 4 * t4));
             dai[4 * t4] = t.x; dai[4 * t4 + 1] = t.y; dai[4 * t4 + 2] = t.z; dai[4 * t4 + 3] = t.w;
           }
 #pragma unroll
@@ -440,7 +434,7 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
     }
     {
       float h[32];
-      ld_g32(h_in + nn * HID + f0, h);
+      ld_pb32(h_in, N, nn, f0, h);
       st_col<32>(HT, 80, f0, node, h);
     }
     const bool acc = !first;
@@ -456,10 +450,10 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
     float d[32], dp[32];
     tmem_ld32(lb + f0, d);
     if (on) {
-      ld_f32x32(dh_part + n * HID + f0, dp);
+      ld_pf32(dh_part, N, n, f0, dp);
 #pragma unroll
       for (int c = 0; c < 32; ++c) d[c] += dp[c];
-      st_f32x32(dh_in + n * HID + f0, d);
+      st_pf32(dh_in, N, n, f0, d);
     }
     tc_fence_before();
     __syncthreads();
@@ -563,7 +557,7 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
     {
       float z2[32], g0[32];
       tmem_ld32(lb + f0, z2);
-      ld_f32x32(dh0 + nn * HID + f0, g0);
+      ld_pf32(dh0, N, nn, f0, g0);
 #pragma unroll
       for (int c = 0; c < 32; ++c) d[c] = on ? g0[c] * gelu_grad(z2[c] + b2[f0 + c]) : 0.0f;
     }

@@ -175,16 +175,16 @@ __global__ void __launch_bounds__(256, 3) gnn_encode_kernel(
     tmem_ld32(lb + f0, g);
 #pragma unroll
     for (int c = 0; c < 32; ++c) g[c] = gelu(g[c] + b2[f0 + c]);
-    if (on && h0_out) st_g32(h0_out + n * HID + f0, g);
+    if (on && h0_out) st_pb32(h0_out, N, n, f0, g);
     st_row32(X, node, f0, g);  // the MMA that read X has completed
     if (!tc_run(sh, tc, stw, [&] {
           umma_128xN(tc.tmem, smem_u32(X), 0, smem_u32(sm + enc::WAB), 0, 1, 128, false);
         }))
       break;
     tmem_ld32(lb + f0, g);
-    if (on) st_h32(ab_out + n * 128 + f0, g);
+    if (on) st_ph32(ab_out, N, n, f0, g);
     tmem_ld32(lb + HID + f0, g);
-    if (on) st_h32(ab_out + n * 128 + HID + f0, g);
+    if (on) st_ph32(ab_out, N, n, HID + f0, g);
     tc_fence_before();
     __syncthreads();
   }
@@ -267,15 +267,13 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Geo geo
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int64_t j = geo_nbr(p, ex(k + 1), ey(k + 1)) - base;
-        const uint4* q = reinterpret_cast<const uint4*>(ra.ab_in + j * 128 + HID + c0);
-        braw[k][0] = __ldg(q);
-        braw[k][1] = __ldg(q + 1);
+        braw[k][0] = __ldg(chunk8(ra.ab_in, N, j, HID + c0));
+        braw[k][1] = __ldg(chunk8(ra.ab_in, N, j, HID + c0 + 8));
       }
       uint4 araw[2];
       {
-        const uint4* q = reinterpret_cast<const uint4*>(ra.ab_in + nn * 128 + c0);
-        araw[0] = __ldg(q);
-        araw[1] = __ldg(q + 1);
+        araw[0] = __ldg(chunk8(ra.ab_in, N, nn, c0));
+        araw[1] = __ldg(chunk8(ra.ab_in, N, nn, c0 + 8));
       }
       const uint32_t* aw = reinterpret_cast<const uint32_t*>(araw);
       __half2 acc[8];
@@ -303,13 +301,12 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Geo geo
       *reinterpret_cast<uint4*>(Ag + node * 128 + (((ch + 1) ^ (node & 7)) << 4)) =
           pack_bf16x8(av + 8);
       if (on && ra.a_out) {
-        uint4* q = reinterpret_cast<uint4*>(ra.a_out + n * HID + c0);
-        q[0] = pack_bf16x8(av);
-        q[1] = pack_bf16x8(av + 8);
+        *chunk8w(ra.a_out, N, n, c0) = pack_bf16x8(av);
+        *chunk8w(ra.a_out, N, n, c0 + 8) = pack_bf16x8(av + 8);
       }
     }
     float h[32];
-    ld_g32(ra.h_in + nn * HID + f0, h);
+    ld_pb32(ra.h_in, N, nn, f0, h);
     st_row32(H, node, f0, h);
     // node update: h <- h + GELU(W_n [h; a] + b_n)
     if (!tc_run(sh, tc, stw, [&] {
@@ -320,7 +317,7 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Geo geo
     tmem_ld32(lb + f0, z);
 #pragma unroll
     for (int c = 0; c < 32; ++c) h[c] += gelu(z[c] + bn[f0 + c]);
-    if (on && ra.h_out) st_g32(ra.h_out + n * HID + f0, h);
+    if (on && ra.h_out) st_pb32(ra.h_out, N, n, f0, h);
     st_row32(H, node, f0, h);
     if (MODE == 0) {
       if (!tc_run(sh, tc, stw, [&] {
@@ -331,8 +328,8 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Geo geo
       tmem_ld32(lb + 64 + f0, a);
       tmem_ld32(lb + 128 + f0, b);
       if (on) {
-        st_h32(ra.ab_out + n * 128 + f0, a);
-        st_h32(ra.ab_out + n * 128 + HID + f0, b);
+        st_ph32(ra.ab_out, N, n, f0, a);
+        st_ph32(ra.ab_out, N, n, HID + f0, b);
       }
     } else {
       if (!tc_run(sh, tc, stw, [&] {

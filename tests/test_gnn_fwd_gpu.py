@@ -75,7 +75,9 @@ def test_forward_matches_oracle(lbmlib, cuda, nb, ny, nx):
     ta_o = 0.5 + gnn.sigmoid(y_o[:, 0])
     assert np.max(np.abs(ta_g - ta_o)) <= 1e-2
     for r in range(3):
-        h_g = bf16_to_np(saved[r * N * 64:(r + 1) * N * 64].view(N, 64))
+        # chunked layout: value (n, f) at ((f // 8) * N + n) * 8 + f % 8
+        h_g = bf16_to_np(saved[r * N * 64:(r + 1) * N * 64].view(8, N, 8).permute(1, 0, 2)
+                         .reshape(N, 64))
         e = rel_l2(h_g, h_o[r])
         assert e <= 2e-2, (r, e)
 
