@@ -214,8 +214,14 @@ struct RoundArgs {
   int round;
 };
 
+#ifndef LBM_ROUND_CTAS
+#define LBM_ROUND_CTAS 2
+#endif
+#ifndef LBM_NBR_GROUP
+#define LBM_NBR_GROUP 4  // neighbour loads in flight per thread and chunk
+#endif
 template <int MODE, class Geo>
-__global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Geo geo,
+__global__ void __launch_bounds__(256, LBM_ROUND_CTAS) gnn_round_kernel(RoundArgs ra, Geo geo,
                                                            const uint8_t* __restrict__ packed,
                                                            unsigned* stw) {
   extern __shared__ uint8_t smem_raw[];
@@ -239,7 +245,7 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Geo geo
       ckw[i] = __floats2half2_rn(ckf[2 * i], ckf[2 * i + 1]);
   }
   TcCtx tc;
-  tc_setup(sh, tc);
+  tc_setup(sh, tc, 128);
   const __half2* ckh = reinterpret_cast<const __half2*>(sm + rnd::CKH);
   const float* bn = reinterpret_cast<const float*>(sm + rnd::BN);
   const float* bh = reinterpret_cast<const float*>(sm + rnd::BH);
@@ -263,30 +269,31 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Geo geo
 #pragma unroll
     for (int sc = 0; sc < 2; ++sc) {
       const int c0 = f0 + 16 * sc;
-      uint4 braw[8][2];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int64_t j = geo_nbr(p, ex(k + 1), ey(k + 1)) - base;
-        braw[k][0] = __ldg(chunk8(ra.ab_in, N, j, HID + c0));
-        braw[k][1] = __ldg(chunk8(ra.ab_in, N, j, HID + c0 + 8));
-      }
       uint4 araw[2];
-      {
-        araw[0] = __ldg(chunk8(ra.ab_in, N, nn, c0));
-        araw[1] = __ldg(chunk8(ra.ab_in, N, nn, c0 + 8));
-      }
+      araw[0] = __ldg(chunk8(ra.ab_in, N, nn, c0));
+      araw[1] = __ldg(chunk8(ra.ab_in, N, nn, c0 + 8));
       const uint32_t* aw = reinterpret_cast<const uint32_t*>(araw);
       __half2 acc[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) acc[c] = __float2half2_rn(0.0f);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const uint32_t* bw = reinterpret_cast<const uint32_t*>(braw[k]);
-        const __half2* c_k = ckh + k * (HID / 2) + c0 / 2;
+      for (int g = 0; g < 8; g += LBM_NBR_GROUP) {  // neighbours g .. g+LBM_NBR_GROUP-1
+        uint4 braw[LBM_NBR_GROUP][2];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const __half2 z = __hadd2(__hadd2(u32_as_h2(aw[c]), c_k[c]), u32_as_h2(bw[c]));
-          acc[c] = __hadd2(acc[c], gelu_h2(z));
+        for (int k = 0; k < LBM_NBR_GROUP; ++k) {
+          const int64_t j = geo_nbr(p, ex(g + k + 1), ey(g + k + 1)) - base;
+          braw[k][0] = __ldg(chunk8(ra.ab_in, N, j, HID + c0));
+          braw[k][1] = __ldg(chunk8(ra.ab_in, N, j, HID + c0 + 8));
+        }
+#pragma unroll
+        for (int k = 0; k < LBM_NBR_GROUP; ++k) {
+          const uint32_t* bw = reinterpret_cast<const uint32_t*>(braw[k]);
+          const __half2* c_k = ckh + (g + k) * (HID / 2) + c0 / 2;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const __half2 z = __hadd2(__hadd2(u32_as_h2(aw[c]), c_k[c]), u32_as_h2(bw[c]));
+            acc[c] = __hadd2(acc[c], gelu_h2(z));
+          }
         }
       }
       float av[16];
@@ -321,24 +328,24 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Geo geo
     st_row32(H, node, f0, h);
     if (MODE == 0) {
       if (!tc_run(sh, tc, stw, [&] {
-            umma_128xN(tc.tmem + 64, smem_u32(H), 0, smem_u32(sm + rnd::WX), 0, 1, 128, false);
+            umma_128xN(tc.tmem, smem_u32(H), 0, smem_u32(sm + rnd::WX), 0, 1, 128, false);
           }))
         break;
       float a[32], b[32];
-      tmem_ld32(lb + 64 + f0, a);
-      tmem_ld32(lb + 128 + f0, b);
+      tmem_ld32(lb + f0, a);
+      tmem_ld32(lb + HID + f0, b);
       if (on) {
         st_ph32(ra.ab_out, N, n, f0, a);
         st_ph32(ra.ab_out, N, n, HID + f0, b);
       }
     } else {
       if (!tc_run(sh, tc, stw, [&] {
-            umma_128xN(tc.tmem + 64, smem_u32(H), 0, smem_u32(sm + rnd::WX), 0, 1, 16, false);
+            umma_128xN(tc.tmem, smem_u32(H), 0, smem_u32(sm + rnd::WX), 0, 1, 16, false);
           }))
         break;
       if (half == 0) {
         float y[16];
-        tmem_ld16(lb + 64, y);
+        tmem_ld16(lb, y);
 #pragma unroll
         for (int o = 0; o < NOUT; ++o) y[o] += bh[o];
         if (MODE == 2) {
@@ -371,7 +378,7 @@ __global__ void __launch_bounds__(256, 2) gnn_round_kernel(RoundArgs ra, Geo geo
     tc_fence_before();
     __syncthreads();
   }
-  tc_teardown(sh, tc);
+  tc_teardown(sh, tc, 128);
 }
 
 // ---------------------------------------------------------------------------
@@ -407,7 +414,7 @@ static cudaError_t round_any(int mode, const RoundLaunch& rl, const Geo& geo, in
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
   const uint32_t bytes = rnd::BYTES + 1024;
-  const unsigned grid = grid_for(N, per_sm);
+  const unsigned grid = grid_for(N, per_sm >= 2 ? LBM_ROUND_CTAS : per_sm);
   RoundArgs ra{rl.h_in, rl.ab_in, rl.h_out, rl.a_out, rl.ab_out, rl.y_out, rl.f_post, rl.f_out,
                rl.tau, rl.taus, rl.round};
   cudaError_t e;
