@@ -134,6 +134,27 @@ def run_ours(args, rank, world, local_rank):
         res = gnn_bench(args, L, dev, torch.cuda.current_stream(), side=args.side, only=True)
         print(json.dumps({"case": f"gnn {args.side}x{args.side}", **res}))
         return None
+    if args.only == "train":
+        from paper_2504_14494_gb300 import inputs
+        from paper_2504_14494_gb300.train import Trainer
+        tr = Trainer(dev, theta=inputs.xavier_params(0), lr=1e-4, wd=0.0, seed=1, n=args.side,
+                     batch=64, episode=64)
+        f_in, f_tg, taus = tr.data.next()
+        for i in range(args.warmup):
+            L.gnn_train_step(f_in, f_tg, tr.data.coarse, 1.0, taus, tr.params, tr.packed, tr.m,
+                             tr.v, 1 + i, 1e-4, 0.0, tr.loss, None, tr.ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(args.steps):
+            L.gnn_train_step(f_in, f_tg, tr.data.coarse, 1.0, taus, tr.params, tr.packed, tr.m,
+                             tr.v, 100 + i, 1e-4, 0.0, tr.loss, None, tr.ws)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": f"train 64x{args.side}^2",
+                          "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                          "status": L.lbm_get_status()}))
+        return None
     n = args.side
     nodes = n * n
     s = L.shape(n, n)
@@ -494,7 +515,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["bgk", "gnn"], default=None,
+    ap.add_argument("--only", choices=["bgk", "gnn", "train"], default=None,
                     help="time one kernel family only (profiling runs)")
     ap.add_argument("--side", type=int, default=N_SIDE, help="lattice side for --only runs")
     args = ap.parse_args()
@@ -507,6 +528,8 @@ def main():
         ap.error("--side applies to --only runs")
     if args.only == "gnn" and args.side == N_SIDE:
         args.side = GNN_SIDE
+    if args.only == "train" and args.side == N_SIDE:
+        args.side = 256
     if args.impl == "reference":
         out = run_reference(args, rank)
     else:

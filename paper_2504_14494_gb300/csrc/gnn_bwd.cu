@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd1_kernel(
 // (= sum dA) and the W_c columns (sum dc_x, sum dc_y).
 namespace rb2 {
 constexpr uint32_t DAB = 0, DABT = 32768, DCT = 65536, HT = 98304, WABT = 118784, CK = 135168,
-                   SH = 137216, BYTES = 137344;
+                   CKH = 137216, SH = 138240, BYTES = 138368;
 }
 
 __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
@@ -350,9 +350,15 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
   copy_g2s(sm + rb2::CK, kr + K::CK, 2048);
   __syncthreads();
   ones_row(sm + rb2::HT, 80, 64);
+  {  // c_k as FP16 pairs
+    const float* ckf = reinterpret_cast<const float*>(sm + rb2::CK);
+    __half2* ckw = reinterpret_cast<__half2*>(sm + rb2::CKH);
+    for (int i = threadIdx.x; i < 8 * HID / 2; i += blockDim.x)
+      ckw[i] = __floats2half2_rn(ckf[2 * i], ckf[2 * i + 1]);
+  }
   TcCtx tc;
   tc_setup(sh, tc);
-  const float* ck = reinterpret_cast<const float*>(sm + rb2::CK);
+  const __half2* ckh = reinterpret_cast<const __half2*>(sm + rb2::CKH);
   uint8_t* DAB = sm + rb2::DAB;
   uint8_t* DABT = sm + rb2::DABT;
   uint8_t* DCT = sm + rb2::DCT;
@@ -370,12 +376,18 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
 #pragma unroll 1
     for (int sc = 0; sc < 2; ++sc) {  // two chunks of 16 features
       const int c0 = f0 + 16 * sc;
-      float Aj[16], daj[16], Bj[16], gA[16], gx[16], gy[16], gB[16];
+      // GELU'(z) is evaluated in packed FP16 pairs (z = A + B + c_k is O(1));
+      // the gradients themselves stay FP32 (they would underflow FP16).
+      uint32_t aj[8], bj[8];
+      float daj[16], gA[16], gx[16], gy[16], gB[16];
       {
-        unpack_h8(__ldg(chunk8(ab, N, nn, c0)), Aj);
-        unpack_h8(__ldg(chunk8(ab, N, nn, c0 + 8)), Aj + 8);
-        unpack_h8(__ldg(chunk8(ab, N, nn, HID + c0)), Bj);
-        unpack_h8(__ldg(chunk8(ab, N, nn, HID + c0 + 8)), Bj + 8);
+        const uint4 a0 = __ldg(chunk8(ab, N, nn, c0)), a1 = __ldg(chunk8(ab, N, nn, c0 + 8));
+        const uint4 b0 = __ldg(chunk8(ab, N, nn, HID + c0));
+        const uint4 b1 = __ldg(chunk8(ab, N, nn, HID + c0 + 8));
+        aj[0] = a0.x; aj[1] = a0.y; aj[2] = a0.z; aj[3] = a0.w;
+        aj[4] = a1.x; aj[5] = a1.y; aj[6] = a1.z; aj[7] = a1.w;
+        bj[0] = b0.x; bj[1] = b0.y; bj[2] = b0.z; bj[3] = b0.w;
+        bj[4] = b1.x; bj[5] = b1.y; bj[6] = b1.z; bj[7] = b1.w;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const float4 t = __ldg(chunk4(da, N, nn, c0 + 4 * i));
@@ -384,34 +396,64 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
       }
 #pragma unroll
       for (int c = 0; c < 16; ++c) gA[c] = gx[c] = gy[c] = gB[c] = 0.0f;
-#pragma unroll 1
-      for (int k = 1; k < Q; ++k) {
-        const float* c_k = ck + (k - 1) * HID + c0;
-        {
-          const int64_t j = node_at(p, ex(k), ey(k), s);
-          float Bn[16];
-          unpack_h8(__ldg(chunk8(ab, N, j, HID + c0)), Bn);
-          unpack_h8(__ldg(chunk8(ab, N, j, HID + c0 + 8)), Bn + 8);
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const float g = daj[c] * gelu_grad(Aj[c] + Bn[c] + c_k[c]);
-            gA[c] += g;
-            if (ex(k)) gx[c] += float(ex(k)) * g;
-            if (ey(k)) gy[c] += float(ey(k)) * g;
+      for (int g = 0; g < 8; g += 4) {  // directions k = g+1 .. g+4
+        // dA_j, dc_j: neighbours j + e_k
+        uint4 bn[4][2];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const int k = g + kk + 1;
+          const int64_t j = node_at(p, ex(k), ey(k), s);
+          bn[kk][0] = __ldg(chunk8(ab, N, j, HID + c0));
+          bn[kk][1] = __ldg(chunk8(ab, N, j, HID + c0 + 8));
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const int k = g + kk + 1;
+          const __half2* c_k = ckh + (k - 1) * (HID / 2) + c0 / 2;
+          const uint32_t* bw = reinterpret_cast<const uint32_t*>(bn[kk]);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const __half2 z = __hadd2(__hadd2(u32_as_h2(aj[c]), c_k[c]), u32_as_h2(bw[c]));
+            const float2 gp = __half22float2(gelu_grad_h2(z));
+            const float g0 = daj[2 * c] * gp.x, g1 = daj[2 * c + 1] * gp.y;
+            gA[2 * c] += g0;
+            gA[2 * c + 1] += g1;
+            if (ex(k)) {
+              gx[2 * c] += float(ex(k)) * g0;
+              gx[2 * c + 1] += float(ex(k)) * g1;
+            }
+            if (ey(k)) {
+              gy[2 * c] += float(ey(k)) * g0;
+              gy[2 * c + 1] += float(ey(k)) * g1;
+            }
           }
         }
-        {
+        // dB_j: neighbours i = j - e_k
+        uint4 ai[4][2];
+        float4 di[4][4];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const int k = g + kk + 1;
           const int64_t i = node_at(p, -ex(k), -ey(k), s);
-          float Ai[16], dai[16];
-          unpack_h8(__ldg(chunk8(ab, N, i, c0)), Ai);
-          unpack_h8(__ldg(chunk8(ab, N, i, c0 + 8)), Ai + 8);
+          ai[kk][0] = __ldg(chunk8(ab, N, i, c0));
+          ai[kk][1] = __ldg(chunk8(ab, N, i, c0 + 8));
 #pragma unroll
-          for (int t4 = 0; t4 < 4; ++t4) {
-            const float4 t = __ldg(chunk4(da, N, i, c0 + 4 * t4));
-            dai[4 * t4] = t.x; dai[4 * t4 + 1] = t.y; dai[4 * t4 + 2] = t.z; dai[4 * t4 + 3] = t.w;
+          for (int t4 = 0; t4 < 4; ++t4) di[kk][t4] = __ldg(chunk4(da, N, i, c0 + 4 * t4));
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const int k = g + kk + 1;
+          const __half2* c_k = ckh + (k - 1) * (HID / 2) + c0 / 2;
+          const uint32_t* aw = reinterpret_cast<const uint32_t*>(ai[kk]);
+          const float* dv = reinterpret_cast<const float*>(di[kk]);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const __half2 z = __hadd2(__hadd2(u32_as_h2(aw[c]), c_k[c]), u32_as_h2(bj[c]));
+            const float2 gp = __half22float2(gelu_grad_h2(z));
+            gB[2 * c] += dv[2 * c] * gp.x;
+            gB[2 * c + 1] += dv[2 * c + 1] * gp.y;
           }
-#pragma unroll
-          for (int c = 0; c < 16; ++c) gB[c] += dai[c] * gelu_grad(Ai[c] + Bj[c] + c_k[c]);
         }
       }
       if (!on) {

@@ -273,6 +273,8 @@ __global__ void __launch_bounds__(256, LBM_ROUND_CTAS) gnn_round_kernel(RoundArg
       araw[0] = __ldg(chunk8(ra.ab_in, N, nn, c0));
       araw[1] = __ldg(chunk8(ra.ab_in, N, nn, c0 + 8));
       const uint32_t* aw = reinterpret_cast<const uint32_t*>(araw);
+      // Each message is accumulated as z + z tanh(u) (= 2 GELU(z)); the 1/2 is
+      // applied once to the sum.
       __half2 acc[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) acc[c] = __float2half2_rn(0.0f);
@@ -289,10 +291,13 @@ __global__ void __launch_bounds__(256, LBM_ROUND_CTAS) gnn_round_kernel(RoundArg
         for (int k = 0; k < LBM_NBR_GROUP; ++k) {
           const uint32_t* bw = reinterpret_cast<const uint32_t*>(braw[k]);
           const __half2* c_k = ckh + (g + k) * (HID / 2) + c0 / 2;
+          const __half2 c0h = __float2half2_rn(0.7978845608028654f);
+          const __half2 c1h = __float2half2_rn(0.0356774081363001f);
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             const __half2 z = __hadd2(__hadd2(u32_as_h2(aw[c]), c_k[c]), u32_as_h2(bw[c]));
-            acc[c] = __hadd2(acc[c], gelu_h2(z));
+            const __half2 u = __hmul2(z, __hfma2(c1h, __hmul2(z, z), c0h));
+            acc[c] = __hfma2(z, tanh_h2(u), __hadd2(acc[c], z));
           }
         }
       }
@@ -300,8 +305,8 @@ __global__ void __launch_bounds__(256, LBM_ROUND_CTAS) gnn_round_kernel(RoundArg
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const float2 t = __half22float2(acc[c]);
-        av[2 * c] = t.x;
-        av[2 * c + 1] = t.y;
+        av[2 * c] = 0.5f * t.x;
+        av[2 * c + 1] = 0.5f * t.y;
       }
       const int ch = c0 >> 3;
       *reinterpret_cast<uint4*>(Ag + node * 128 + ((ch ^ (node & 7)) << 4)) = pack_bf16x8(av);
