@@ -294,6 +294,14 @@ def tgv_l2(L, f, s, n, u0, tau, t, dev):
 
 GNN_SIDE = 1024
 GNN_RE = 1000.0
+# Elementwise roofline of the message passing: each edge message costs 7
+# packed-FP16 pipe operations per pair of features (z = A + c + B: 2, u: 3,
+# accumulate z + z tanh u: 2) plus one tanh.approx.f16x2.  The FP16 pipe
+# issues 2 warp instructions per clock per SM (64 lanes x 2 values), so it
+# binds at 128 / 7 = 18.3 edge-feature GELUs per clock per SM; the MUFU
+# (16 lanes x 2 values) allows 32.  Peak = 18.3 x 152 SMs x 2.07 GHz.
+GELU_PER_CLK_SM = 128.0 / 7.0
+EDGE_GELUS_PER_NODE = 2 * 8 * 64
 
 
 def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False, theta=None, label="xavier"):
@@ -341,7 +349,13 @@ def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False, theta=None, label
                      "status": st}
     if only:
         return res
+    peak = GELU_PER_CLK_SM * 152 * 2.07e9 / 1e9
+    ach = EDGE_GELUS_PER_NODE * n * n / (res["gnn"]["ms_per_step"] / 1e3) / 1e9
     return {"workload": f"tgv_gnn_{n}x{n}", "re": GNN_RE, "tau": round(tau, 5), "u0": U0,
+            "roofline": {"bound": "alu", "kernel": "lbm_step_gnn (gnn_encode_kernel + "
+                         "2 x gnn_round_kernel)", "achieved": round(ach, 1),
+                         "peak": round(peak, 1), "unit": "G edge-feature GELU/s",
+                         "frac": round(ach / peak, 4), "traffic": None},
             "weights": label,
             "steps_timed": kk, "steps_run": args.warmup + kk,
             "mlups_gnn": res["gnn"]["mlups"], "mlups_bgk_same_lattice": res["bgk"]["mlups"],
