@@ -236,7 +236,8 @@ def run_ours(args, rank, world, local_rank):
                                 label="trained in this run (see training)"),
            "xavier": gnn_bench(args, L, dev, stream, label="xavier-uniform seed 0, untrained"),
            "training": train_info,
-           "batch": batch_bench(args, L, dev, stream, trained)}
+           "batch": batch_bench(args, L, dev, stream, trained),
+           "stability": stability_bench(L, dev, trained)}
 
     if rank != 0:
         return None
@@ -462,6 +463,56 @@ def batch_bench(args, L, dev, stream, theta, n_lat=512, seed=7):
                 "mlups_total": round(n * kk / (ms / 1e3) / 1e6, 1), "status": st}
     finally:
         L.lbm_batch_plan_destroy(plan)
+
+
+def stability_bench(L, dev, theta, n=64, u0=0.1, res=(400.0, 800.0, 1600.0, 3200.0),
+                    steps=5000, chunk=250):
+    """Reynolds-number study on the 64^2 TGV (paper Sec. 3.4): BGK and GNN-LBM
+    (the network trained in this run) for `steps` steps at each Re = u0 n / nu;
+    the first chunk of `chunk` steps whose state holds a non-finite value
+    (FP64 totals of the library), and the kinetic-energy error against the
+    closed-form decay E(0) exp(-4 nu k^2 t) at the last finite chunk."""
+    import torch
+    s = L.shape(n, n)
+    k = 2 * np.pi / n
+    packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=dev)
+    L.gnn_pack(torch.from_numpy(theta).to(dev), packed)
+    ws = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=dev)
+    fa = torch.empty(9 * n * n, device=dev)
+    fb, fc = torch.empty_like(fa), torch.empty_like(fa)
+    tot = torch.zeros(5, dtype=torch.float64, device=dev)
+    out = []
+    for re in res:
+        nu = u0 * n / re
+        tau = 0.5 + 3.0 * nu
+        row = {"re": re, "tau": round(tau, 6)}
+        for kind in ("bgk", "gnn"):
+            L.lbm_init_tgv(fa, s, 1.0, u0, k, k, False)
+            L.lbm_moments(fa, s, None, None, None, tot)
+            e0 = tot[3].item()
+            done, bad, err = 0, None, None
+            cur, nxt = fa, fb
+            while done < steps:
+                if kind == "bgk":
+                    L.lbm_step_bgk(cur, nxt, fc, s, tau, nsteps=chunk, totals=tot)
+                else:
+                    for _ in range(chunk):
+                        L.lbm_step_gnn(cur, nxt, s, tau, None, packed, None, ws)
+                        cur, nxt = nxt, cur
+                    cur, nxt = nxt, cur
+                    L.lbm_moments(nxt, s, None, None, None, tot)
+                done += chunk
+                cur, nxt = nxt, cur
+                t = tot.cpu().numpy()
+                if t[4] > 0 or not np.isfinite(t[3]):
+                    bad = done
+                    break
+                err = abs(t[3] - e0 * np.exp(-4 * nu * k * k * done)) / (e0 * np.exp(-4 * nu * k * k * done))
+            L.lbm_get_status()  # clear the non-finite flag of an unstable run
+            row[kind] = {"first_nonfinite_by_step": bad, "steps_finite": done if bad is None else bad - chunk,
+                         "energy_rel_error": err}
+        out.append(row)
+    return {"workload": f"tgv_{n}x{n}_u0_{u0}", "steps": steps, "chunk": chunk, "rows": out}
 
 
 def cpu_baseline(budget_s=12.0):

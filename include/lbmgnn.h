@@ -120,7 +120,7 @@ LBM_API int lbm_moments(const float* f, lbm_shape s, float* rho, float* ux, floa
  *   round 1: edge.W[64][130] edge.b[64] node.W[64][128] node.b[64]
  *   round 2: same shapes
  *   head.W[10][64] head.b[10]                     -> 38,922 trainable values
- *   mu[12] sigma[12] s_df                         -> 25 fixed values
+ *   mu[12] sigma[12] s_df variant                 -> 26 fixed values
  * Row-major W[out][in]; edge.W columns are [h_i (64) | h_j (64) | e_k (2)],
  * node.W columns are [h_i (64) | a_i (64)].
  * Weight matrices are used as BF16 (round to nearest even); biases and the
@@ -128,8 +128,15 @@ LBM_API int lbm_moments(const float* f, lbm_shape s, float* rho, float* ux, floa
  * accumulation; activations are stored as BF16.
  * ------------------------------------------------------------------------- */
 
-/* Number of floats of the parameter vector (38,947) and of its trainable
- * prefix (38,922). */
+/* Number of floats of the parameter vector (38,948) and of its trainable
+ * prefix (38,922).  The last value selects a variant of the network (sum of
+ * flags, as a float): LBM_GNN_MLP_ONLY (1) is the paper's Fig. 2 network
+ * (both encoder layers ReLU, no message passing, head on h0; the round
+ * weights are unused and get zero gradients); LBM_GNN_CONSERVATIVE (2)
+ * projects Delta f orthogonal to 1, e_x, e_y, so that Eq. 3 conserves mass
+ * and momentum exactly like Eq. 1 (this library's option; the paper adds
+ * Delta f unconstrained). */
+enum { LBM_GNN_MLP_ONLY = 1, LBM_GNN_CONSERVATIVE = 2 };
 LBM_API size_t gnn_param_count(void);
 LBM_API size_t gnn_trainable_count(void);
 

@@ -27,11 +27,20 @@ Readings where the paper gives no formula (also listed in the design doc):
     bfloat16 (round to nearest even) before use, biases and (mu, sigma, s_df)
     are used as the float32 values given.  The oracle then computes in FP64.
 
+Variants (the last fixed value, a small integer of flags):
+  * 1, MLP-only: the paper's SimpleLBMGNN of Fig. 2 -- the two encoder
+    layers use ReLU ("Linear + ReLU" in Fig. 2), there is no message passing,
+    and the head reads h0.
+  * 2, conservative correction: Delta f is projected onto the populations
+    that carry no mass and no momentum (Euclidean projection orthogonal to
+    1, e_x, e_y; for D2Q9 these are orthogonal with norms 9, 6, 6), so that
+    Eq. 3 conserves mass and momentum like Eq. 1.
+
 Flat parameter vector (float32, 38,922 trainable values, in this order):
   enc1.W[64,12] enc1.b[64] enc2.W[64,64] enc2.b[64]
   {edge.W[64,130] edge.b[64] node.W[64,128] node.b[64]} for round 1, round 2
   head.W[10,64] head.b[10]
-followed by 25 fixed values: mu[12], sigma[12], s_df.
+followed by 26 fixed values: mu[12], sigma[12], s_df, variant.
 """
 import numpy as np
 
@@ -49,7 +58,9 @@ for _r in range(ROUNDS):
                (f"r{_r}.node.W", (HID, 2 * HID)), (f"r{_r}.node.b", (HID,))]
 SHAPES += [("head.W", (NOUT, HID)), ("head.b", (NOUT,))]
 N_TRAINABLE = sum(int(np.prod(s)) for _, s in SHAPES)
-N_FIXED = 2 * NFEAT + 1
+N_FIXED = 2 * NFEAT + 2
+MLP_ONLY = 1
+CONSERVATIVE = 2
 N_TOTAL = N_TRAINABLE + N_FIXED
 
 
@@ -80,6 +91,7 @@ def unpack(theta, round_weights=True):
     p["mu"] = theta[o:o + NFEAT].astype(np.float64)
     p["sigma"] = theta[o + NFEAT:o + 2 * NFEAT].astype(np.float64)
     p["s_df"] = float(theta[o + 2 * NFEAT])
+    p["variant"] = int(round(float(theta[o + 2 * NFEAT + 1])))
     return p
 
 
@@ -100,6 +112,14 @@ def gelu(z):
 def gelu_grad(z):
     t = np.tanh(_C * (z + _A * z ** 3))
     return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * _C * (1.0 + 3.0 * _A * z * z)
+
+
+def relu(z):
+    return np.maximum(z, 0.0)
+
+
+def relu_grad(z):
+    return (np.asarray(z) > 0.0).astype(np.float64)
 
 
 def sigmoid(z):
@@ -141,13 +161,14 @@ def forward(f_pre, p):
     _, ny, nx = f_pre.shape
     nbr = neighbours(nx, ny)
     xh, raw = features(f_pre, p)
+    act = relu if p["variant"] & MLP_ONLY else gelu
     z1 = xh @ p["enc1.W"].T + p["enc1.b"]
-    g1 = gelu(z1)
+    g1 = act(z1)
     z2 = g1 @ p["enc2.W"].T + p["enc2.b"]
-    h = gelu(z2)
+    h = act(z2)
     cache = {"nbr": nbr, "xh": xh, "raw": raw, "z1": z1, "g1": g1, "z2": z2,
              "h": [h], "edge_in": [], "ze": [], "a": [], "zn": []}
-    for r in range(ROUNDS):
+    for r in range(0 if p["variant"] & MLP_ONLY else ROUNDS):
         We, be = p[f"r{r}.edge.W"], p[f"r{r}.edge.b"]
         Wn, bn = p[f"r{r}.node.W"], p[f"r{r}.node.b"]
         a = np.zeros_like(h)
@@ -192,10 +213,23 @@ def forward_split(f_pre, p):
     return h @ p["head.W"].T + p["head.b"]
 
 
+def conserve(df):
+    """Projection of corrections (9, N) orthogonal to 1, e_x, e_y:
+    df - sum(df)/9 - e_x sum(e_x df)/6 - e_y sum(e_y df)/6."""
+    ex = lbm.E[:, 0].astype(np.float64)[:, None]
+    ey = lbm.E[:, 1].astype(np.float64)[:, None]
+    return (df - df.sum(axis=0) / 9.0 - ex * (ex * df).sum(axis=0) / 6.0
+            - ey * (ey * df).sum(axis=0) / 6.0)
+
+
 def heads(y, p):
     """Sec. 2.3.1: tau_adj = 0.5 + sigmoid(y_0) in (0.5, 1.5);
-    Delta f_i = s_df * y_{1+i}.  Returns tau_adj (N,), df (9, N)."""
-    return 0.5 + sigmoid(y[:, 0]), p["s_df"] * y[:, 1:].T
+    Delta f_i = s_df * y_{1+i} (projected with the conservative variant).
+    Returns tau_adj (N,), df (9, N)."""
+    df = p["s_df"] * y[:, 1:].T
+    if p["variant"] & CONSERVATIVE:
+        df = conserve(df)
+    return 0.5 + sigmoid(y[:, 0]), df
 
 
 def gnn_collide(f_pre, y, tau, p):
@@ -230,7 +264,7 @@ def backward(dy, cache, p):
     g["head.W"] = dy.T @ h
     g["head.b"] = dy.sum(axis=0)
     dh = dy @ p["head.W"]
-    for r in reversed(range(ROUNDS)):
+    for r in reversed(range(0 if p["variant"] & MLP_ONLY else ROUNDS)):
         We = p[f"r{r}.edge.W"]
         Wn = p[f"r{r}.node.W"]
         h_in = cache["h"][r]
@@ -253,10 +287,15 @@ def backward(dy, cache, p):
         g[f"r{r}.edge.W"] = gWe
         g[f"r{r}.edge.b"] = gbe
         dh = dh_in
-    dz2 = dh * gelu_grad(cache["z2"])
+    if p["variant"] & MLP_ONLY:
+        for r in range(ROUNDS):
+            for name in ("edge.W", "edge.b", "node.W", "node.b"):
+                g[f"r{r}.{name}"] = np.zeros_like(p[f"r{r}.{name}"])
+    dact = relu_grad if p["variant"] & MLP_ONLY else gelu_grad
+    dz2 = dh * dact(cache["z2"])
     g["enc2.W"] = dz2.T @ cache["g1"]
     g["enc2.b"] = dz2.sum(axis=0)
-    dz1 = (dz2 @ p["enc2.W"]) * gelu_grad(cache["z1"])
+    dz1 = (dz2 @ p["enc2.W"]) * dact(cache["z1"])
     g["enc1.W"] = dz1.T @ cache["xh"]
     g["enc1.b"] = dz1.sum(axis=0)
     dx = (dz1 @ p["enc1.W"]) / p["sigma"]          # d/d raw features (N, 12)
@@ -287,7 +326,8 @@ def collide_loss(f_pre, y, tau, target, p):
     loss = float(np.sum(r * r) / n)
     dfs = 2.0 * r / n                                # dL/d f*
     dy = np.zeros_like(y)
-    dy[:, 1:] = (p["s_df"] * dfs).T
+    # Delta f = s_df P y_1..9 with P symmetric (P = I without the variant)
+    dy[:, 1:] = (p["s_df"] * (conserve(dfs) if p["variant"] & CONSERVATIVE else dfs)).T
     dtau_adj = np.sum(dfs * (f - feq), axis=0) * tau / (teff * teff)
     s = sigmoid(y[:, 0])
     dy[:, 0] = dtau_adj * s * (1.0 - s)

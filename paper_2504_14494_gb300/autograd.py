@@ -4,7 +4,7 @@ of the network (gnn_forward / gnn_backward of liblbmgnn.so).
     y = GnnFunction.apply(f_pre, params, shape)
 
 f_pre: pre-collision populations (device FP32, 9 planes of `shape`);
-params: the FP32 parameter vector (38,947 values; the 25 fixed values get a
+params: the FP32 parameter vector (38,948 values; the 26 fixed values get a
 zero gradient).  Returns y as a [10, N] tensor (plane o = head output o).
 The backward returns dL/df_pre and dL/dparams from the library's kernels.
 """

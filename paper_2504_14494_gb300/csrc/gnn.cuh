@@ -37,8 +37,8 @@ constexpr int ROUND0 = 4992, ROUND_SIZE = 16640;
 constexpr int EDGE_W = 0, EDGE_B = 8320, NODE_W = 8384, NODE_B = 16576;  // within a round
 constexpr int HEAD_W = 38272, HEAD_B = 38912;
 constexpr int TRAINABLE = 38922;
-constexpr int MU = 38922, SIGMA = 38934, S_DF = 38946;
-constexpr int TOTAL = 38947;
+constexpr int MU = 38922, SIGMA = 38934, S_DF = 38946, VARIANT = 38947;
+constexpr int TOTAL = 38948;
 }  // namespace P
 
 // ---- packed device image of the parameters (byte offsets) -------------------
@@ -47,7 +47,7 @@ namespace K {
 constexpr uint32_t W1F = 0;       // fp32 [64][12] (BF16-rounded values)
 constexpr uint32_t B1 = 3072;     // fp32 [64]
 constexpr uint32_t B2 = 3328;     // fp32 [64]
-constexpr uint32_t NORM = 3584;   // fp32 mu[12], sigma[12], s_df, pad -> 32 floats
+constexpr uint32_t NORM = 3584;   // fp32 mu[12], sigma[12], s_df, variant, pad -> 32 floats
 constexpr uint32_t BH = 3712;     // fp32 [16] (10 used)
 constexpr uint32_t WHF = 3776;    // fp32 [10][64] (BF16-rounded values)
 constexpr uint32_t W2 = 7168;     // SW128 [64 out x 64 in]
@@ -92,6 +92,30 @@ __device__ __forceinline__ float gelu_grad(float z) {
   return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * du;
 }
 __device__ __forceinline__ float sigmoid_acc(float y) { return 0.5f * (1.0f + tanhf(0.5f * y)); }
+
+// Network variants (flags in the last fixed parameter): MLP-only network of
+// the paper's Fig. 2 (ReLU encoder, no message passing), and the correction
+// Delta f projected to carry no mass and no momentum.
+enum : int { VAR_MLP_ONLY = 1, VAR_CONSERVATIVE = 2 };
+__device__ __forceinline__ int variant_of(const float* nrm) { return __float2int_rn(nrm[25]); }
+__device__ __forceinline__ float act(float z, bool relu) { return relu ? fmaxf(z, 0.0f) : gelu(z); }
+__device__ __forceinline__ float act_grad(float z, bool relu) {
+  return relu ? (z > 0.0f ? 1.0f : 0.0f) : gelu_grad(z);
+}
+// d <- d - sum(d)/9 - e_x sum(e_x d)/6 - e_y sum(e_y d)/6 (D2Q9: 1, e_x, e_y
+// are orthogonal with squared norms 9, 6, 6).
+__device__ __forceinline__ void conserve9(float (&d)[9]) {
+  float s = 0.0f, sx = 0.0f, sy = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    s += d[q];
+    sx += float(ex(q)) * d[q];
+    sy += float(ey(q)) * d[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q)
+    d[q] -= s * (1.0f / 9.0f) + float(ex(q)) * sx * (1.0f / 6.0f) + float(ey(q)) * sy * (1.0f / 6.0f);
+}
 
 // ---- BF16 vectors ------------------------------------------------------------------
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(256) gnn_collide_loss_kernel(
   const bool on = n < N;
   const int64_t nn = on ? n : N - 1;
   const float sdf = reinterpret_cast<const float*>(packed + K::NORM)[24];
+  const int variant = variant_of(reinterpret_cast<const float*>(packed + K::NORM));
   float fv[Q], yv[NOUT];
 #pragma unroll
   for (int q = 0; q < Q; ++q) fv[q] = __ldg(f_pre + q * s.ps + nn);
@@ -95,18 +96,24 @@ __global__ void __launch_bounds__(256) gnn_collide_loss_kernel(
   const float inv = 1.0f / teff;
   const float scale = 2.0f / (9.0f * (float)N);
   double lp = 0.0;
-  float dta = 0.0f, dyv[NOUT];
+  float dta = 0.0f, dyv[NOUT], d[Q], g[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) d[q] = sdf * yv[1 + q];
+  if (variant & VAR_CONSERVATIVE) conserve9(d);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const float fe = feq_i(q, m, usq15);
-    const float fp = fv[q] - (fv[q] - fe) * inv + sdf * yv[1 + q];
+    const float fp = fv[q] - (fv[q] - fe) * inv + d[q];
     const float r = fp - __ldg(tgt + q * s.ps + nn);
     lp += (double)r * (double)r;
-    const float g = scale * r;  // dL/df*
-    dyv[1 + q] = sdf * g;
-    dta += g * (fv[q] - fe);
+    g[q] = scale * r;  // dL/df*
+    dta += g[q] * (fv[q] - fe);
     if (on && f_pred) f_pred[q * s.ps + n] = fp;
   }
+  // Delta f = s_df P y_1..9 with P the (symmetric) projection, or P = I
+  if (variant & VAR_CONSERVATIVE) conserve9(g);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) dyv[1 + q] = sdf * g[q];
   dyv[0] = dta * t * inv * inv * sg * (1.0f - sg);
   if (on && dy) {
 #pragma unroll
@@ -240,6 +247,7 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd1_kernel(
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   TcShared* sh = reinterpret_cast<TcShared*>(sm + rb1::SH);
   const uint8_t* kr = packed + K::round_base(round);
+  const bool mlp_only = variant_of(reinterpret_cast<const float*>(packed + K::NORM)) & VAR_MLP_ONLY;
   zero_smem(sm + rb1::DZT, rb1::WN - rb1::DZT);  // DZT (upper rows stay 0) and ONES
   copy_g2s(sm + rb1::WN, kr + K::WN, 16384);
   copy_g2s(sm + rb1::WNT, kr + K::WNT, 16384);
@@ -281,7 +289,8 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd1_kernel(
     tmem_ld32(lb + f0, dz);
     ld_pf32(dh_out, N, nn, f0, dho);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) dz[c] = on ? dho[c] * gelu_grad(dz[c] + bn[f0 + c]) : 0.0f;
+    for (int c = 0; c < 32; ++c)
+      dz[c] = (on && !mlp_only) ? dho[c] * gelu_grad(dz[c] + bn[f0 + c]) : 0.0f;
     st_row32(DZ, node, f0, dz);
     st_col<32>(DZT, 128, f0, node, dz);
     const bool acc = !first;
@@ -556,6 +565,7 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
   uint8_t* XT = sm + eb::XT;
   uint8_t* YT = sm + eb::YT;
   const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
+  const bool relu = variant_of(nrm) & VAR_MLP_ONLY;
   const uint32_t lb = lane_base(tc.tmem);
   const int64_t N = (int64_t)s.nb * s.ny * s.nx;
   const int64_t ntiles = (N + TILE - 1) / TILE;
@@ -583,7 +593,7 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
 #pragma unroll
         for (int j = 0; j < NFEAT; ++j) z = fmaf(w1[(f0 + c) * NFEAT + j], xh[j], z);
         z1[c] = z;
-        g[c] = gelu(z);
+        g[c] = act(z, relu);
       }
       st_row32(G1, node, f0, g);
       st_col<32>(YT, 80, f0, node, g);
@@ -601,7 +611,7 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
       tmem_ld32(lb + f0, z2);
       ld_pf32(dh0, N, nn, f0, g0);
 #pragma unroll
-      for (int c = 0; c < 32; ++c) d[c] = on ? g0[c] * gelu_grad(z2[c] + b2[f0 + c]) : 0.0f;
+      for (int c = 0; c < 32; ++c) d[c] = on ? g0[c] * act_grad(z2[c] + b2[f0 + c], relu) : 0.0f;
     }
     st_row32(DZ2, node, f0, d);
     st_col<32>(XT, 128, f0, node, d);
@@ -613,7 +623,7 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
     }
     tmem_ld32(lb + f0, d);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) d[c] *= gelu_grad(z1[c]);  // dz1 (0 for idle nodes)
+    for (int c = 0; c < 32; ++c) d[c] *= act_grad(z1[c], relu);  // dz1 (0 for idle nodes)
     st_col<32>(XT, 128, HID + f0, node, d);
     if (df) {
       float px[NFEAT];

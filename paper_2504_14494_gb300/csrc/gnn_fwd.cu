@@ -34,7 +34,7 @@ __global__ void gnn_pack_kernel(const float* __restrict__ p, uint8_t* __restrict
     reinterpret_cast<float*>(out + K::B2)[e] = p[P::ENC2_B + e];
   }
   for (int e = tid; e < 32; e += nth)
-    reinterpret_cast<float*>(out + K::NORM)[e] = e < 25 ? p[P::MU + e] : 0.0f;
+    reinterpret_cast<float*>(out + K::NORM)[e] = e < 26 ? p[P::MU + e] : 0.0f;
   for (int e = tid; e < 16; e += nth)
     reinterpret_cast<float*>(out + K::BH)[e] = e < NOUT ? p[P::HEAD_B + e] : 0.0f;
   for (int e = tid; e < NOUT * HID; e += nth)
@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(256, 3) gnn_encode_kernel(
   const int64_t N = geo.count();
   const int64_t base = geo.base(), ps = geo.ps();
   const int64_t ntiles = (N + TILE - 1) / TILE;
+  const bool relu = variant_of(nrm) & VAR_MLP_ONLY;
 
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t n = tile * TILE + node;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(256, 3) gnn_encode_kernel(
     float g[32];
     tmem_ld32(lb + f0, g);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) g[c] = gelu(g[c] + b1[f0 + c]);
+    for (int c = 0; c < 32; ++c) g[c] = act(g[c] + b1[f0 + c], relu);
     st_row32(X, node, f0, g);
     if (!tc_run(sh, tc, stw, [&] {
           umma_128xN(tc.tmem, smem_u32(X), 0, smem_u32(sm + enc::W2), 0, 1, 64, false);
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(256, 3) gnn_encode_kernel(
       break;
     tmem_ld32(lb + f0, g);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) g[c] = gelu(g[c] + b2[f0 + c]);
+    for (int c = 0; c < 32; ++c) g[c] = act(g[c] + b2[f0 + c], relu);
     if (on && h0_out) st_pb32(h0_out, N, n, f0, g);
     st_row32(X, node, f0, g);  // the MMA that read X has completed
     if (!tc_run(sh, tc, stw, [&] {
@@ -257,12 +258,20 @@ __global__ void __launch_bounds__(256, LBM_ROUND_CTAS) gnn_round_kernel(RoundArg
   const int64_t N = geo.count();
   const int64_t base = geo.base(), ps = geo.ps();
   const int64_t ntiles = (N + TILE - 1) / TILE;
+  const int variant = variant_of(nrm);
+  const bool mlp_only = variant & VAR_MLP_ONLY;
 
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t n = tile * TILE + node;
     const bool on = n < N;
     const int64_t nn = on ? n : N - 1;
     const GeoPos p = geo.pos(base + nn);
+    if (mlp_only) {  // no message passing: a = 0, h unchanged
+      if (on && ra.a_out) {
+        const float zero[32] = {};
+        st_pb32(ra.a_out, N, n, f0, zero);
+      }
+    } else {
     // messages m_ik = GELU(A_i + B_j + c_k), summed over the 8 neighbours, in
     // packed FP16 pairs; per 16-feature chunk the 8 neighbour loads are
     // issued together.
@@ -317,18 +326,21 @@ __global__ void __launch_bounds__(256, LBM_ROUND_CTAS) gnn_round_kernel(RoundArg
         *chunk8w(ra.a_out, N, n, c0 + 8) = pack_bf16x8(av + 8);
       }
     }
+    }
     float h[32];
     ld_pb32(ra.h_in, N, nn, f0, h);
-    st_row32(H, node, f0, h);
-    // node update: h <- h + GELU(W_n [h; a] + b_n)
-    if (!tc_run(sh, tc, stw, [&] {
-          umma_128xN(tc.tmem, smem_u32(H), 16384, smem_u32(sm + rnd::WN), 8192, 2, 64, false);
-        }))
-      break;
-    float z[32];
-    tmem_ld32(lb + f0, z);
+    if (!mlp_only) {
+      st_row32(H, node, f0, h);
+      // node update: h <- h + GELU(W_n [h; a] + b_n)
+      if (!tc_run(sh, tc, stw, [&] {
+            umma_128xN(tc.tmem, smem_u32(H), 16384, smem_u32(sm + rnd::WN), 8192, 2, 64, false);
+          }))
+        break;
+      float z[32];
+      tmem_ld32(lb + f0, z);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) h[c] += gelu(z[c] + bn[f0 + c]);
+      for (int c = 0; c < 32; ++c) h[c] += gelu(z[c] + bn[f0 + c]);
+    }
     if (on && ra.h_out) st_pb32(ra.h_out, N, n, f0, h);
     st_row32(H, node, f0, h);
     if (MODE == 0) {
@@ -370,11 +382,15 @@ __global__ void __launch_bounds__(256, LBM_ROUND_CTAS) gnn_round_kernel(RoundArg
           const float tadj = 0.5f + sigmoid_acc(y[0]);
           const float inv = 1.0f / (tau * tadj);
           const float sdf = nrm[24];
+          float d[Q];
+#pragma unroll
+          for (int q = 0; q < Q; ++q) d[q] = sdf * y[1 + q];
+          if (variant & VAR_CONSERVATIVE) conserve9(d);
           if (on) {
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
               const float fe = feq_i(q, mm, usq15);
-              ra.f_out[q * ps + base + n] = fv[q] - (fv[q] - fe) * inv + sdf * y[1 + q];
+              ra.f_out[q * ps + base + n] = fv[q] - (fv[q] - fe) * inv + d[q];
             }
           }
         }

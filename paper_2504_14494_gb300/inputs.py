@@ -11,7 +11,9 @@ and the oracle:
   enc1.W[64,12] enc1.b[64] enc2.W[64,64] enc2.b[64]
   {edge.W[64,130] edge.b[64] node.W[64,128] node.b[64]} x 2 rounds
   head.W[10,64] head.b[10]                      -> 38,922 trainable values
-  mu[12] sigma[12] s_df                         -> 25 fixed values
+  mu[12] sigma[12] s_df variant                 -> 26 fixed values
+variant: 0, or a sum of flags: 1 = MLP-only network of the paper's Fig. 2
+(ReLU encoder, no message passing), 2 = mass/momentum-conserving correction.
 """
 import numpy as np
 
@@ -21,7 +23,8 @@ for _ in range(ROUNDS):
     PARAM_SHAPES += [(HID, 2 * HID + 2), (HID,), (HID, 2 * HID), (HID,)]
 PARAM_SHAPES += [(NOUT, HID), (NOUT,)]
 N_TRAINABLE = sum(int(np.prod(s)) for s in PARAM_SHAPES)
-N_PARAMS = N_TRAINABLE + 2 * NFEAT + 1
+N_PARAMS = N_TRAINABLE + 2 * NFEAT + 2
+MLP_ONLY, CONSERVATIVE = 1, 2
 
 # Default input normaliser: populations around their rest-state values
 # (4/9, 1/9 x4, 1/36 x4) with a 10% scale, density around 1, velocity with a
@@ -33,7 +36,7 @@ DEFAULT_S_DF = 1e-4
 
 
 def xavier_params(seed, s_df=DEFAULT_S_DF, mu=None, sigma=None, weight_gain=1.0,
-                  bias_scale=0.0):
+                  bias_scale=0.0, variant=0):
     """Xavier-uniform weights (bound gain*sqrt(6/(fan_in+fan_out))), biases
     zero (or uniform in +-bias_scale), from numpy's PCG64 seeded by `seed`."""
     rng = np.random.default_rng(seed)
@@ -47,18 +50,19 @@ def xavier_params(seed, s_df=DEFAULT_S_DF, mu=None, sigma=None, weight_gain=1.0,
                          if bias_scale > 0 else np.zeros(s, np.float32))
     parts.append(DEFAULT_MU if mu is None else np.asarray(mu, np.float32))
     parts.append(DEFAULT_SIGMA if sigma is None else np.asarray(sigma, np.float32))
-    parts.append(np.array([s_df], np.float32))
+    parts.append(np.array([s_df, float(variant)], np.float32))
     out = np.concatenate(parts).astype(np.float32)
     assert out.shape == (N_PARAMS,)
     return out
 
 
-def zero_params(s_df=DEFAULT_S_DF):
+def zero_params(s_df=DEFAULT_S_DF, variant=0):
     """All trainable values zero; default normaliser."""
     out = np.zeros(N_PARAMS, np.float32)
     out[N_TRAINABLE:N_TRAINABLE + NFEAT] = DEFAULT_MU
     out[N_TRAINABLE + NFEAT:N_TRAINABLE + 2 * NFEAT] = DEFAULT_SIGMA
-    out[-1] = s_df
+    out[-2] = s_df
+    out[-1] = float(variant)
     return out
 
 

@@ -47,7 +47,7 @@ def _oracle_forward(f, theta):
         y, cache = gnn.forward(f[:, b].astype(np.float64), p)
         ys.append(y)
         for r in range(3):
-            hs[r].append(cache["h"][r])
+            hs[r].append(cache["h"][min(r, len(cache["h"]) - 1)])
     return np.concatenate(ys), [np.concatenate(h) for h in hs]
 
 
@@ -203,3 +203,39 @@ def test_full_size_1024_sampled(lbmlib, cuda):
     yg, yo = np.array(yg), np.array(yo)
     assert rel_l2(yg[:, 0], yo[:, 0]) <= 2e-2
     assert rel_l2(yg[:, 1:], yo[:, 1:]) <= 2e-2
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_variants_forward_and_step(lbmlib, cuda, variant):
+    """Variants: 1 = the paper's Fig. 2 MLP (ReLU, no message passing),
+    2 = conservative correction.  Same tolerances as the default network; the
+    conservative step conserves mass and momentum to FP32 rounding."""
+    import torch
+    L = lbmlib
+    nb, ny, nx = 2, 12, 20
+    theta = inputs.xavier_params(71 + variant, s_df=1e-2, bias_scale=0.1, variant=variant)
+    f = _state(nb, ny, nx, seed=variant)
+    pk = _packed(L, theta, cuda)
+    din, _ = to_dev(f, cuda)
+    s = L.shape(nx, ny, nb)
+    N = nb * ny * nx
+    saved = torch.zeros(L.gnn_saved_bytes(s) // 2, dtype=torch.bfloat16, device=cuda)
+    y = torch.zeros(10 * N, dtype=torch.float32, device=cuda)
+    L.gnn_forward(din, s, pk, saved, y)
+    y_g = y.view(10, N).cpu().numpy().T.astype(np.float64)
+    y_o, _ = _oracle_forward(f, theta)
+    assert rel_l2(y_g[:, 0], y_o[:, 0]) <= 2e-2 and rel_l2(y_g[:, 1:], y_o[:, 1:]) <= 2e-2
+    dout = torch.zeros_like(din)
+    ws = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    L.lbm_step_gnn(din, dout, s, 0.8, None, pk, None, ws)
+    assert L.lbm_get_status() == 0
+    got = from_dev(dout, f.shape)
+    ref = np.stack([gnn.gnn_step(f[:, b].astype(np.float64), theta, 0.8) for b in range(nb)], axis=1)
+    bgk = np.stack([lbm.bgk_step(f[:, b].astype(np.float64), 0.8) for b in range(nb)], axis=1)
+    assert rel_l2(got - bgk, ref - bgk) <= 3e-2
+    if variant & 2:
+        for b in range(nb):
+            t0 = lbm.totals(f[:, b].astype(np.float64))
+            t1 = lbm.totals(got[:, b])
+            assert abs(t1[0] - t0[0]) <= 1e-6 * t0[0]
+            assert abs(t1[1] - t0[1]) <= 1e-6 * t0[0] and abs(t1[2] - t0[2]) <= 1e-6 * t0[0]

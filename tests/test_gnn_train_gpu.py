@@ -246,3 +246,47 @@ def test_train_step_matches_oracle_and_descends(lbmlib, cuda):
         losses.append(loss.item())
     print("loss", losses[0], "->", losses[-1])
     assert losses[-1] < 0.5 * losses[0]
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_variant_backward_and_loss_match_oracle(lbmlib, cuda, variant):
+    """Gradients of the Eq. 3 + Eq. 4 loss through the network for the
+    variants (same tolerances as the default network)."""
+    import torch
+    L = lbmlib
+    nb, ny, nx = 1, 8, 12
+    theta = inputs.xavier_params(81 + variant, s_df=1e-2, bias_scale=0.1, variant=variant)
+    f = _state(nb, ny, nx, seed=2 + variant, u0=0.08, amp=5e-2)
+    tg = _state(nb, ny, nx, seed=9 + variant)
+    p, pk = _dev_params(L, theta, cuda)
+    s = L.shape(nx, ny, nb)
+    N = nb * ny * nx
+    din, _ = to_dev(f, cuda)
+    dtg, _ = to_dev(tg, cuda)
+    saved = torch.empty(L.gnn_saved_bytes(s), dtype=torch.uint8, device=cuda)
+    y = torch.empty(10 * N, device=cuda)
+    L.gnn_forward(din, s, pk, saved, y)
+    loss = torch.zeros(1, dtype=torch.float64, device=cuda)
+    dy = torch.zeros(10 * N, device=cuda)
+    lws = torch.empty(L.gnn_loss_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    L.gnn_collide_loss(din, y, dtg, s, 0.7, None, pk, loss, dy, None, lws)
+    grad = torch.zeros(L.gnn_trainable_count(), device=cuda)
+    ws = torch.empty(L.gnn_backward_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    L.gnn_backward(din, s, pk, saved, dy, grad, None, ws)
+    assert L.lbm_get_status() == 0
+    pr = gnn.unpack(theta)
+    yo, cache = gnn.forward(f[:, 0].astype(np.float64), pr)
+    lo, dyo, _ = gnn.collide_loss(f[:, 0].astype(np.float64), yo, 0.7, tg[:, 0].astype(np.float64), pr)
+    assert abs(loss.item() - lo) <= 2e-2 * lo
+    go, _ = gnn.backward(dyo, cache, pr)
+    g_ref = gnn.pack_grads(go)
+    g_gpu = grad.cpu().numpy().astype(np.float64)
+    o = 0
+    for name, shape in gnn.SHAPES:
+        n = int(np.prod(shape))
+        a, r = g_gpu[o:o + n], g_ref[o:o + n]
+        o += n
+        if not np.any(r):
+            assert not np.any(a), name          # unused round weights of the MLP-only net
+            continue
+        assert _cos(a, r) >= 0.999 and rel_l2(a, r) <= 3e-2, (name, _cos(a, r), rel_l2(a, r))

@@ -198,3 +198,87 @@ def test_collide_loss_reduces_to_mse_of_eq3():
     loss, _, f_pred = gnn.collide_loss(f, np.zeros((20, 10)), 0.8, target, p)
     assert np.allclose(f_pred.reshape(9, 4, 5), lbm.bgk_collide(f, 0.8), rtol=0, atol=1e-16)
     assert abs(loss - np.mean((lbm.bgk_collide(f, 0.8) - target) ** 2)) < 1e-18
+
+
+# --- variants: conservative correction (2) and the MLP-only network of Fig. 2 (1) ---
+def test_conservative_projection_invariants():
+    """The projection removes exactly the mass and momentum of Delta f: it is
+    idempotent, symmetric, and leaves already-conserving corrections alone."""
+    rng = np.random.default_rng(21)
+    df = rng.standard_normal((9, 40))
+    P = gnn.conserve(df)
+    e = lbm.E.astype(np.float64)
+    assert np.allclose(P.sum(axis=0), 0.0, atol=1e-14)
+    assert np.allclose(e[:, 0] @ P, 0.0, atol=1e-14)
+    assert np.allclose(e[:, 1] @ P, 0.0, atol=1e-14)
+    assert np.allclose(gnn.conserve(P), P, atol=1e-14)
+    b = rng.standard_normal((9, 40))
+    assert np.allclose(np.sum(gnn.conserve(df) * b, axis=0), np.sum(df * gnn.conserve(b), axis=0))
+    # a population vector orthogonal to 1, e_x, e_y (e_x^2 - e_y^2 pattern)
+    o = (e[:, 0] ** 2 - e[:, 1] ** 2)[:, None] * np.ones((1, 3))
+    assert np.allclose(gnn.conserve(o), o, atol=1e-15)
+
+
+def test_conservative_step_conserves_mass_and_momentum():
+    """With the conservative variant the GNN step (Eq. 3) conserves mass and
+    momentum exactly, like BGK; without it, Delta f moves them."""
+    f = _state(6, 5, 31)
+    for variant, tol in ((2, 1e-13), (0, None)):
+        theta = inputs.xavier_params(33, s_df=1e-2, bias_scale=0.1, variant=variant)
+        g = gnn.gnn_step(f, theta, 0.7)
+        t0, t1 = lbm.totals(f), lbm.totals(g)
+        drift = np.abs(t1[:3] - t0[:3]).max()
+        if tol is None:
+            assert drift > 1e-6
+        else:
+            assert drift < tol
+
+
+def test_mlp_only_is_a_per_node_relu_mlp():
+    """Variant 1 (Fig. 2): no message passing, so a node's output does not
+    depend on its neighbours, and it equals a two-layer ReLU MLP + head
+    written out per node."""
+    theta = inputs.xavier_params(34, s_df=1e-2, bias_scale=0.1, variant=1)
+    p = gnn.unpack(theta)
+    f = _state(5, 4, 35)
+    y, _ = gnn.forward(f, p)
+    f2 = f.copy()
+    f2[:, 0, 1] *= 1.01                      # change a neighbour of node (0, 0)
+    y2, _ = gnn.forward(f2, p)
+    assert np.array_equal(y[0], y2[0]) and not np.array_equal(y[1], y2[1])
+    r = lambda z: np.maximum(z, 0.0)
+    for n in (0, 7, 19):
+        yy, xx = divmod(n, 5)
+        fi = f[:, yy, xx]
+        rho = fi.sum()
+        u = (lbm.E.astype(np.float64).T @ fi) / rho
+        xin = (np.concatenate([fi, [rho, u[0], u[1]]]) - p["mu"]) / p["sigma"]
+        h = r(p["enc2.W"] @ r(p["enc1.W"] @ xin + p["enc1.b"]) + p["enc2.b"])
+        assert np.allclose(y[n], p["head.W"] @ h + p["head.b"], rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_variant_gradients_match_central_differences(variant):
+    nx, ny = 4, 3
+    p = gnn.unpack(inputs.xavier_params(36, s_df=1e-2, bias_scale=0.2, variant=variant))
+    f = _state(nx, ny, 37, u0=0.08, amp=5e-2)
+    target = _state(nx, ny, 38)
+    rng = np.random.default_rng(variant)
+    taus = 0.6 + 0.3 * rng.random(nx * ny)
+
+    def loss(pp, ff):
+        y, _ = gnn.forward(ff, pp)
+        return gnn.collide_loss(ff, y, taus, target, pp)[0]
+
+    y, cache = gnn.forward(f, p)
+    _, dy, _ = gnn.collide_loss(f, y, taus, target, p)
+    g, df = gnn.backward(dy, cache, p)
+    h = 1e-5
+    for name, shape in gnn.SHAPES:
+        d = rng.standard_normal(shape)
+        pp = dict(p); pm = dict(p)
+        pp[name] = p[name] + h * d
+        pm[name] = p[name] - h * d
+        fd = (loss(pp, f) - loss(pm, f)) / (2 * h)
+        an = float(np.sum(g[name] * d))
+        assert abs(fd - an) <= 1e-5 * max(abs(an), 1e-12) + 1e-18, (variant, name, fd, an)
