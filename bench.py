@@ -231,13 +231,17 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / ke
 
-    trained, train_info = train_bench(args, L, dev, stream)
-    gnn = {"trained": gnn_bench(args, L, dev, stream, theta=trained,
-                                label="trained in this run (see training)"),
+    thetas, train_info = train_bench(args, L, dev, stream)
+    names = {0: "message passing (Eq. 3 as printed)", 2: "message passing, conserving correction",
+             3: "Fig. 2 MLP-only, conserving correction"}
+    gnn = {"trained": {str(v): gnn_bench(args, L, dev, stream, theta=th,
+                                         label=f"trained in this run: {names[v]}")
+                       for v, th in thetas.items()},
            "xavier": gnn_bench(args, L, dev, stream, label="xavier-uniform seed 0, untrained"),
            "training": train_info,
-           "batch": batch_bench(args, L, dev, stream, trained),
-           "stability": stability_bench(L, dev, trained)}
+           "batch": batch_bench(args, L, dev, stream, thetas[2]),
+           "stability": {str(v): stability_bench(L, dev, thetas[v], res=(400.0, 1600.0, 3200.0))
+                         for v in (0, 2)}}
 
     if rank != 0:
         return None
@@ -366,16 +370,19 @@ def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False, theta=None, label
             "status": res["gnn"]["status"]}
 
 
-def train_bench(args, L, dev, stream):
+def train_bench(args, L, dev, stream, variants=(0, 2, 3)):
     """Training throughput on the 64 x 256^2 batch workload (4x refined data
-    generated on the GPU, fused train step) and a short training run on 64^2
-    pairs whose weights the GNN-LBM measurement then uses."""
+    generated on the GPU, fused train step), then a short training run on
+    64^2 pairs (16 per batch, 3000 steps, lr 1e-4, head starting at zero so
+    the network starts as BGK) for each network variant (0: the default
+    message-passing network, 2: with the conserving correction, 3: the
+    paper's Fig. 2 MLP-only network with the conserving correction) and the
+    held-out Eq. 4 loss ratio against BGK.  Returns ({variant: theta}, info)."""
     import torch
     from paper_2504_14494_gb300 import inputs
     from paper_2504_14494_gb300.train import Evaluator, PairStream, Trainer
     theta = inputs.xavier_params(0, s_df=1e-4)
     theta[38272:38922] = 0.0
-    # throughput at the full batch workload
     tr = Trainer(dev, theta=theta.copy(), lr=1e-4, wd=0.0, seed=1, n=256, batch=64, episode=64)
     for _ in range(3):
         tr.step()
@@ -388,7 +395,6 @@ def train_bench(args, L, dev, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_full = e0.elapsed_time(e1) / kk
-    # time of the fused gnn_train_step alone (data generation excluded)
     f_in, f_tg, taus = tr.data.next()
     e0.record(stream)
     for i in range(kk):
@@ -398,31 +404,36 @@ def train_bench(args, L, dev, stream):
     torch.cuda.synchronize()
     ms_step = e0.elapsed_time(e1) / kk
     del tr
-    # short training run on 64^2 pairs (16 per batch), then held-out Eq. 4 loss
-    small = Trainer(dev, theta=theta.copy(), lr=1e-4, wd=0.0, seed=1, n=64, batch=16, episode=64)
-    t0 = time.perf_counter()
-    for _ in range(3000):
-        small.step()
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    held = PairStream(dev, n=64, batch=16, m=4, episode=24, seed=12345)
-    ev = Evaluator(dev, held.coarse)
-    zero = torch.from_numpy(inputs.zero_params(s_df=1e-4)).to(dev)
-    lg = lb = 0.0
-    for _ in range(48):
-        a, b, t = held.next()
-        lg += ev.loss_of(small.params, a, b, t)
-        lb += ev.loss_of(zero, a, b, t)
+    thetas, runs = {}, {}
+    for var in variants:
+        th = inputs.xavier_params(0, s_df=1e-4, variant=var)
+        th[38272:38922] = 0.0
+        small = Trainer(dev, theta=th, lr=1e-4, wd=0.0, seed=1, n=64, batch=16, episode=64)
+        t0 = time.perf_counter()
+        for _ in range(3000):
+            small.step()
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        held = PairStream(dev, n=64, batch=16, m=4, episode=24, seed=12345)
+        ev = Evaluator(dev, held.coarse)
+        zero = torch.from_numpy(inputs.zero_params(s_df=1e-4, variant=var)).to(dev)
+        lg = lb = 0.0
+        for _ in range(48):
+            a, b, t = held.next()
+            lg += ev.loss_of(small.params, a, b, t)
+            lb += ev.loss_of(zero, a, b, t)
+        thetas[var] = small.theta()
+        runs[str(var)] = {"steps": 3000, "wall_s": round(t_train, 2),
+                          "held_out_eq4_loss_gnn": lg / 48, "held_out_eq4_loss_bgk": lb / 48,
+                          "ratio": round(lg / lb, 4)}
     info = {"workload": "train_64x256x256_refined4",
             "ms_per_train_step_incl_datagen": round(ms_full, 3),
             "ms_per_fused_train_step": round(ms_step, 3),
             "samples_per_s": round(64 / (ms_full / 1e3), 1),
             "node_updates_per_s_M": round(64 * 256 * 256 / (ms_step / 1e3) / 1e6, 1),
-            "short_run": {"pairs": "64^2 coarse, 16 per batch", "steps": 3000, "lr": 1e-4,
-                          "wall_s": round(t_train, 2),
-                          "held_out_eq4_loss_gnn": lg / 48, "held_out_eq4_loss_bgk": lb / 48,
-                          "ratio": round(lg / lb, 4)}}
-    return small.theta(), info
+            "short_runs_by_variant": runs,
+            "short_run_data": "64^2 coarse pairs from 256^2 refined runs, 16 per batch, lr 1e-4"}
+    return thetas, info
 
 
 def batch_bench(args, L, dev, stream, theta, n_lat=512, seed=7):
