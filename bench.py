@@ -241,7 +241,8 @@ def run_ours(args, rank, world, local_rank):
            "training": train_info,
            "batch": batch_bench(args, L, dev, stream, thetas[2]),
            "stability": {str(v): stability_bench(L, dev, thetas[v], res=(400.0, 1600.0, 3200.0))
-                         for v in (0, 2)}}
+                         for v in (0, 2)},
+           "poiseuille": channel_bench(L, dev)}
 
     if rank != 0:
         return None
@@ -356,11 +357,12 @@ def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False, theta=None, label
         return res
     peak = GELU_PER_CLK_SM * 152 * 2.07e9 / 1e9
     ach = EDGE_GELUS_PER_NODE * n * n / (res["gnn"]["ms_per_step"] / 1e3) / 1e9
+    mlp_only = int(round(float(theta[-1].item()))) & 1
     return {"workload": f"tgv_gnn_{n}x{n}", "re": GNN_RE, "tau": round(tau, 5), "u0": U0,
-            "roofline": {"bound": "alu", "kernel": "lbm_step_gnn (gnn_encode_kernel + "
-                         "2 x gnn_round_kernel)", "achieved": round(ach, 1),
-                         "peak": round(peak, 1), "unit": "G edge-feature GELU/s",
-                         "frac": round(ach / peak, 4), "traffic": None},
+            "roofline": None if mlp_only else {
+                "bound": "alu", "kernel": "lbm_step_gnn (gnn_encode_kernel + 2 x gnn_round_kernel)",
+                "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "G edge-feature GELU/s",
+                "frac": round(ach / peak, 4), "traffic": None},
             "weights": label,
             "steps_timed": kk, "steps_run": args.warmup + kk,
             "mlups_gnn": res["gnn"]["mlups"], "mlups_bgk_same_lattice": res["bgk"]["mlups"],
@@ -524,6 +526,41 @@ def stability_bench(L, dev, theta, n=64, u0=0.1, res=(400.0, 800.0, 1600.0, 3200
                          "energy_rel_error": err}
         out.append(row)
     return {"workload": f"tgv_{n}x{n}_u0_{u0}", "steps": steps, "chunk": chunk, "rows": out}
+
+
+def channel_bench(L, dev, h=32, nx=4, umax=0.05, res=(10.0, 50.0, 100.0, 200.0)):
+    """Poiseuille channel (paper Sec. 3.1, Table 1 analog): BGK with
+    halfway bounce-back walls and Guo forcing, H = 32, centre-line velocity
+    0.05, run to steady state (35 e-folding times of the slowest mode); the
+    maximum velocity error against Eq. 5 relative to the centre-line
+    velocity, and MLUPS of the run."""
+    import torch
+    s = L.shape(nx, h)
+    n = nx * h
+    out = []
+    fa = torch.empty(9 * n, device=dev)
+    fb, fc = torch.empty_like(fa), torch.empty_like(fa)
+    rho = torch.empty(n, device=dev)
+    ux = torch.empty(n, device=dev)
+    for re in res:
+        nu = umax * h / re
+        tau = 0.5 + 3.0 * nu
+        g = 8.0 * nu * umax / (h * h)
+        steps = int(35 * h * h / (np.pi ** 2 * nu))
+        L.lbm_init_tgv(fa, s, 1.0, 0.0, 0.0, 0.0, False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.lbm_step_channel(fa, fb, fc, s, tau, None, g, steps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        L.lbm_moments(fb, s, rho, ux, None)
+        u = (ux.double() + 0.5 * g / rho.double()).view(h, nx)[:, 0].cpu().numpy()
+        y = np.arange(h) + 0.5
+        ua = g / (2 * nu) * y * (h - y)
+        out.append({"re": re, "tau": round(tau, 5), "steps": steps,
+                    "max_velocity_error": float(np.abs(u - ua).max() / umax),
+                    "mlups": round(n * steps / dt / 1e6, 1)})
+    return {"workload": f"poiseuille_{nx}x{h}", "u_max": umax, "rows": out}
 
 
 def cpu_baseline(budget_s=12.0):

@@ -95,6 +95,23 @@ LBM_API int lbm_init_tgv(float* f, lbm_shape s, double rho0, double u0, double k
 LBM_API int lbm_step_bgk(const float* f_in, float* f_out, float* f_tmp, lbm_shape s, float tau,
                  const float* taus, int nsteps, double* totals, void* stream);
 
+/* nsteps steps of the channel (Poiseuille) flow of paper Sec. 3.1: the BGK
+ * step with walls and a body force.  The paper gives no wall or force scheme;
+ * this library's reading: every lattice of the stack is a channel along x
+ * (periodic in x) between walls halfway outside the first and last rows
+ * (y = -1/2 and y = ny - 1/2, channel height H = ny), halfway bounce-back
+ * (a population that would stream in from behind a wall is the node's own
+ * opposite post-collision population), and Guo's forcing for a force
+ * (force_x, 0) per unit volume: the velocity is u = (sum f_i e_i + F/2)/rho
+ * and the collision adds (1 - 1/(2 tau)) w_i [3 (e_i - u) + 9 (e_i.u) e_i].F.
+ * Steady state (rho = 1): u(y) = F/(2 nu) (y + 1/2)(ny - 1/2 - y) plus a
+ * constant wall slip of O(F/nu) (Eq. 5).  Arguments, ping-pong and totals as
+ * lbm_step_bgk (lbm_moments of the result returns sum f e / rho; add F/(2 rho)
+ * for the velocity of the forced scheme). */
+LBM_API int lbm_step_channel(const float* f_in, float* f_out, float* f_tmp, lbm_shape s, float tau,
+                             const float* taus, float force_x, int nsteps, double* totals,
+                             void* stream);
+
 /* Macroscopic variables of a stored state (Fig. 1 'Compute macroscopic
  * variables'): rho = sum f_i, u = sum f_i e_i / rho per node (FP32 out,
  * node-major planes of nb*ny*nx values), and optional FP64 totals (as in

@@ -1,0 +1,84 @@
+"""FP64 oracle for the plain BGK channel (Poiseuille) flow.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Paper passages followed:
+  * Sec. 3.1, Eq. 5 -- Poiseuille flow between two walls driven by a constant
+    force (pressure gradient) G: u(y) = G/(2 mu) y (H - y).
+  * Fig. 1 "Apply Boundary Conditions" (no scheme is given).
+
+Readings (also listed in the design doc):
+  * Channel along x, periodic in x; walls halfway between node rows, at
+    y = -1/2 and y = ny - 1/2, so H = ny and the wall-distance of row y is
+    y + 1/2.  Halfway bounce-back: a population that would be pulled from
+    outside the channel is the opposite population of the same node after
+    collision, f_i(x, y) = f*_opp(i)(x, y).
+  * Body force F = (G, 0) per unit volume by Guo's scheme: the velocity is
+    u = (sum f_i e_i + F/2) / rho, and the collision adds
+    S_i = (1 - 1/(2 tau)) w_i [3 (e_i - u) + 9 (e_i . u) e_i] . F.
+  * With rho = 1, mu = nu = (tau - 1/2)/3, the steady profile is
+    u(y) = G/(2 nu) (y + 1/2) (ny - 1/2 - y).
+  * Re = u_max H / nu with u_max = G H^2 / (8 nu).
+"""
+import numpy as np
+
+from . import lbm
+
+OPP = np.array([0, 3, 4, 1, 2, 7, 8, 5, 6])
+
+
+def guo_source(ux, uy, tau, gx, gy=0.0):
+    """Guo forcing term S_i for force (gx, gy) (per unit volume)."""
+    s = np.empty((lbm.Q,) + np.shape(ux))
+    for i in range(lbm.Q):
+        ex, ey = lbm.E[i]
+        eu = ex * ux + ey * uy
+        tx = 3.0 * (ex - ux) + 9.0 * eu * ex
+        ty = 3.0 * (ey - uy) + 9.0 * eu * ey
+        s[i] = (1.0 - 0.5 / tau) * lbm.W[i] * (tx * gx + ty * gy)
+    return s
+
+
+def moments_forced(f, gx, gy=0.0):
+    """rho and the force-corrected velocity u = (sum f e + F/2)/rho."""
+    rho = f.sum(axis=0)
+    jx = sum(lbm.E[i, 0] * f[i] for i in range(lbm.Q))
+    jy = sum(lbm.E[i, 1] * f[i] for i in range(lbm.Q))
+    return rho, (jx + 0.5 * gx) / rho, (jy + 0.5 * gy) / rho
+
+
+def stream_pull_walls(fpost):
+    """Pull streaming, periodic in x, halfway bounce-back at y = -1/2 and
+    y = ny - 1/2 (explicit indexing)."""
+    _, ny, nx = fpost.shape
+    out = np.empty_like(fpost)
+    xs = np.arange(nx)
+    ys = np.arange(ny)
+    for i in range(lbm.Q):
+        ex, ey = lbm.E[i]
+        src_y = ys - ey
+        inside = (src_y >= 0) & (src_y < ny)
+        out[i][inside] = fpost[i][src_y[inside][:, None], ((xs - ex) % nx)[None, :]]
+        out[i][~inside] = fpost[OPP[i]][~inside]
+    return out
+
+
+def channel_step(fpost, tau, gx):
+    """One step: stream (walls), forced moments, BGK relaxation + Guo source."""
+    f = stream_pull_walls(fpost)
+    rho, ux, uy = moments_forced(f, gx)
+    feq = lbm.equilibrium(rho, ux, uy)
+    return f - (f - feq) / tau + guo_source(ux, uy, tau, gx)
+
+
+def channel_run(fpost, tau, gx, nsteps):
+    f = np.asarray(fpost, np.float64)
+    for _ in range(nsteps):
+        f = channel_step(f, tau, gx)
+    return f
+
+
+def poiseuille_profile(ny, tau, gx):
+    """Eq. 5 in lattice units (rho = 1): u(y) = G/(2 nu) (y+1/2)(ny-1/2-y)."""
+    y = np.arange(ny, dtype=np.float64)
+    return gx / (2.0 * lbm.viscosity(tau)) * (y + 0.5) * (ny - 0.5 - y)

@@ -122,6 +122,41 @@ int lbm_step_bgk(const float* f_in, float* f_out, float* f_tmp, lbm_shape shape,
   return LBM_OK;
 }
 
+int lbm_step_channel(const float* f_in, float* f_out, float* f_tmp, lbm_shape shape, float tau,
+                     const float* taus, float force_x, int nsteps, double* totals, void* stream) {
+  Shape s;
+  if (!f_in || !f_out || nsteps < 0 || !std::isfinite(force_x)) return LBM_ERR_ARG;
+  if (int r = check_shape(shape, &s)) return r;
+  if (!taus) {
+    if (int r = check_tau(tau)) return r;
+  }
+  const int64_t bytes = f_bytes(s);
+  if (overlap(f_in, f_out, bytes)) return LBM_ERR_ALIAS;
+  if (nsteps > 1) {
+    if (!f_tmp) return LBM_ERR_ARG;
+    if (overlap(f_tmp, f_in, bytes) || overlap(f_tmp, f_out, bytes)) return LBM_ERR_ALIAS;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (totals && cudaMemsetAsync(totals, 0, 5 * sizeof(double), st) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  if (nsteps == 0) {
+    if (cudaMemcpyAsync(f_out, f_in, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return LBM_ERR_CUDA;
+    return totals ? cuda_status(launch_moments(f_out, s, nullptr, nullptr, nullptr, totals, st))
+                  : LBM_OK;
+  }
+  const float* src = f_in;
+  for (int k = 0; k < nsteps; ++k) {
+    const int left = nsteps - k;
+    float* dst = (left % 2 == 1) ? f_out : f_tmp;
+    if (launch_channel_step(src, dst, s, tau, taus, force_x, left == 1 ? totals : nullptr, st) !=
+        cudaSuccess)
+      return LBM_ERR_CUDA;
+    src = dst;
+  }
+  return LBM_OK;
+}
+
 int lbm_moments(const float* f, lbm_shape shape, float* rho, float* ux, float* uy,
                 double* totals, void* stream) {
   Shape s;

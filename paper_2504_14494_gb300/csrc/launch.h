@@ -13,6 +13,8 @@ cudaError_t launch_moments(const float* f, const Shape& s, float* rho, float* ux
 cudaError_t launch_tgv_init(float* f, const Shape& s, double rho0, double u0, double kx,
                             double ky, int pc, cudaStream_t st);
 
+cudaError_t launch_channel_step(const float* fin, float* fout, const Shape& s, float tau,
+                                const float* taus, float gx, double* totals, cudaStream_t st);
 cudaError_t launch_stream(const float* fin, float* fout, const Shape& s, cudaStream_t st);
 cudaError_t launch_restrict(const float* ff, const Shape& fs, float* fc, const Shape& cs, int m,
                             float tau_f, const float* taus_f, float tau_c, const float* taus_c,

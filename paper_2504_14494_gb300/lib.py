@@ -50,6 +50,8 @@ _SIGS = {
     "lbm_step_bgk": (ctypes.c_int, [_VP, _VP, _VP, lbm_shape, ctypes.c_float, _VP, ctypes.c_int,
                                     _VP, _VP]),
     "lbm_moments": (ctypes.c_int, [_VP, lbm_shape, _VP, _VP, _VP, _VP, _VP]),
+    "lbm_step_channel": (ctypes.c_int, [_VP, _VP, _VP, lbm_shape, ctypes.c_float, _VP,
+                                        ctypes.c_float, ctypes.c_int, _VP, _VP]),
     "gnn_param_count": (ctypes.c_size_t, []),
     "gnn_trainable_count": (ctypes.c_size_t, []),
     "gnn_packed_bytes": (ctypes.c_size_t, []),
@@ -166,6 +168,13 @@ def lbm_init_tgv(f, s, rho0, u0, kx, ky, pressure_consistent=False, stream=None)
 def lbm_step_bgk(f_in, f_out, f_tmp, s, tau, taus=None, nsteps=1, totals=None, stream=None):
     check(load().lbm_step_bgk(ptr(f_in), ptr(f_out), ptr(f_tmp), s, float(tau), ptr(taus),
                               int(nsteps), ptr(totals), stream_ptr(stream)), "lbm_step_bgk")
+
+
+def lbm_step_channel(f_in, f_out, f_tmp, s, tau, taus=None, force_x=0.0, nsteps=1, totals=None,
+                     stream=None):
+    check(load().lbm_step_channel(ptr(f_in), ptr(f_out), ptr(f_tmp), s, float(tau), ptr(taus),
+                                  float(force_x), int(nsteps), ptr(totals), stream_ptr(stream)),
+          "lbm_step_channel")
 
 
 def lbm_moments(f, s, rho=None, ux=None, uy=None, totals=None, stream=None):
