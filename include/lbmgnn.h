@@ -50,7 +50,7 @@ enum {
   LBM_ERR_CUDA = -6,       /* a CUDA runtime call failed */
   LBM_ERR_NONFINITE = -7,  /* a kernel produced a NaN or Inf population */
   LBM_ERR_TIMEOUT = -8,    /* a device-side wait gave up */
-  LBM_ERR_BOUNDS = -9,     /* a device-side bounds check failed */
+  LBM_ERR_BOUNDS = -9,     /* a device-side bounds check failed (reserved) */
   LBM_ERR_WORKSPACE = -10  /* workspace missing or smaller than required */
 };
 
@@ -67,6 +67,14 @@ LBM_API const char* lbm_status_string(int status);
  * current device.  Returns LBM_OK, or the most severe of LBM_ERR_TIMEOUT,
  * LBM_ERR_BOUNDS, LBM_ERR_NONFINITE raised since the last call. */
 LBM_API int lbm_get_status(void* stream);
+
+/* Failure-detection self-test (no counterpart in the paper): launches one
+ * small kernel that waits on a device barrier nothing arrives on, with a
+ * budget of max_cycles SM cycles (1 .. 2e9); the wait gives up, raises the
+ * timeout bit and the kernel returns, exactly as the tensor-core kernels do
+ * when a wait runs out.  The next lbm_get_status() then returns
+ * LBM_ERR_TIMEOUT.  Nothing traps or hangs. */
+LBM_API int lbm_selftest_wait_timeout(long long max_cycles, void* stream);
 
 /* Taylor-Green vortex initial state (paper Sec. 3.2; the formula is this
  * library's reading): u_x = u0 cos(kx x) sin(ky y), u_y = -u0 sin(kx x)

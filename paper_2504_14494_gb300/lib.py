@@ -45,6 +45,7 @@ _VP = ctypes.c_void_p
 _SIGS = {
     "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lbm_get_status": (ctypes.c_int, [_VP]),
+    "lbm_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_longlong, _VP]),
     "lbm_init_tgv": (ctypes.c_int, [_VP, lbm_shape, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, _VP]),
     "lbm_step_bgk": (ctypes.c_int, [_VP, _VP, _VP, lbm_shape, ctypes.c_float, _VP, ctypes.c_int,
@@ -158,6 +159,11 @@ def status_string(code):
 def lbm_get_status(stream=None):
     """Synchronise the stream and return (not raise) the device status code."""
     return load().lbm_get_status(stream_ptr(stream))
+
+
+def lbm_selftest_wait_timeout(max_cycles, stream=None):
+    check(load().lbm_selftest_wait_timeout(int(max_cycles), stream_ptr(stream)),
+          "lbm_selftest_wait_timeout")
 
 
 def lbm_init_tgv(f, s, rho0, u0, kx, ky, pressure_consistent=False, stream=None):

@@ -239,3 +239,21 @@ def test_full_size_4096_sampled(lbmlib, cuda):
     ref = lbm.bgk_collide(pulled, 0.5614)[:, 0]
     got = f1.view(9, n, n)[:, torch.from_numpy(ys).to(cuda), torch.from_numpy(xs).to(cuda)].double().cpu().numpy()
     assert np.all(np.abs(got - ref) <= 1e-6 * np.abs(ref))
+
+
+def test_bounded_wait_reports_timeout(lbmlib, cuda):
+    """A device wait on a barrier nothing arrives on gives up after its
+    budget (~1 ms here) and reports LBM_ERR_TIMEOUT through the status word;
+    the context stays usable (a BGK step afterwards is correct)."""
+    import torch
+    L = lbmlib
+    assert L.lbm_get_status() == 0
+    L.lbm_selftest_wait_timeout(2_000_000)
+    assert L.lbm_get_status() == -8
+    assert L.lbm_get_status() == 0
+    f = _input(1, 8, 8, seed=12)
+    din, _ = _to_dev(f, cuda)
+    dout = torch.zeros_like(din)
+    L.lbm_step_bgk(din, dout, None, L.shape(8, 8), 0.8)
+    ref = _oracle_step(f, 0.8)
+    assert np.all(np.abs(_from_dev(dout, f.shape, din.numel() // 9) - ref) <= 1e-6 * np.abs(ref))
