@@ -38,7 +38,13 @@ BYTES_PER_NODE = 72  # 9 FP32 loads + 9 FP32 stores
 
 # DRAM bytes per launch from one ncu capture of the kernel, keyed by the
 # SHA-256 of its source file at capture time; ignored once the source changed.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+    #     --clock-control none -k regex:bgk_step_x4 -s 3 -c 1
+    #     python bench.py --only bgk --steps 10 --warmup 3      (4096 x 4096, one launch)
+    "bgk_step_x4": {"bytes_per_launch": 604029696 + 547351808,
+                    "src_sha": "b02111b1f5f94ee636a95844c099c9ee189fa7a72626dd2ab4b27ccce1b3f491"},
+}
 
 
 def _peaks():
@@ -48,6 +54,18 @@ def _peaks():
         return float(p["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def _finite(obj):
+    """Non-finite floats (a diverged rollout's error) become null so that the
+    line stays strict JSON."""
+    if isinstance(obj, float):
+        return obj if np.isfinite(obj) else None
+    if isinstance(obj, dict):
+        return {k: _finite(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [_finite(v) for v in obj]
+    return obj
 
 
 def _src_sha(name):
@@ -132,7 +150,7 @@ def run_ours(args, rank, world, local_rank):
 
     if args.only == "gnn":
         res = gnn_bench(args, L, dev, torch.cuda.current_stream(), side=args.side, only=True)
-        print(json.dumps({"case": f"gnn {args.side}x{args.side}", **res}))
+        print(json.dumps(_finite({"case": f"gnn {args.side}x{args.side}", **res})))
         return None
     if args.only == "train":
         from paper_2504_14494_gb300 import inputs
@@ -368,6 +386,7 @@ def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False, theta=None, label
             "mlups_gnn": res["gnn"]["mlups"], "mlups_bgk_same_lattice": res["bgk"]["mlups"],
             "ms_per_step_gnn": res["gnn"]["ms_per_step"],
             "l2_error_gnn": res["gnn"]["l2_error"], "l2_error_bgk": res["bgk"]["l2_error"],
+            "gnn_rollout_diverged": not np.isfinite(res["gnn"]["l2_error"]),
             "gnn_over_bgk_time": round(res["gnn"]["ms_per_step"] / res["bgk"]["ms_per_step"], 2),
             "status": res["gnn"]["status"]}
 
@@ -648,7 +667,7 @@ def main():
     else:
         out = run_ours(args, rank, world, local_rank)
     if out is not None and rank == 0:
-        print(json.dumps(out), flush=True)
+        print(json.dumps(_finite(out), allow_nan=False), flush=True)
 
 
 if __name__ == "__main__":

@@ -276,6 +276,41 @@ __device__ __forceinline__ void st_pf32(float* base, int64_t N, int64_t n, int f
     *chunk4w(base, N, n, f0 + 4 * c) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
 }
 
+// NF (16 or 32) values versions of the helpers above.
+template <int NF>
+__device__ __forceinline__ void ld_pb(const __nv_bfloat16* base, int64_t N, int64_t n, int f0,
+                                      float* v) {
+#pragma unroll
+  for (int c = 0; c < NF / 8; ++c) unpack_bf16x8(__ldg(chunk8(base, N, n, f0 + 8 * c)), v + 8 * c);
+}
+template <int NF>
+__device__ __forceinline__ void st_pb(__nv_bfloat16* base, int64_t N, int64_t n, int f0,
+                                      const float* v) {
+#pragma unroll
+  for (int c = 0; c < NF / 8; ++c) *chunk8w(base, N, n, f0 + 8 * c) = pack_bf16x8(v + 8 * c);
+}
+template <int NF>
+__device__ __forceinline__ void st_ph(__half* base, int64_t N, int64_t n, int f0, const float* v) {
+#pragma unroll
+  for (int c = 0; c < NF / 8; ++c) *chunk8w(base, N, n, f0 + 8 * c) = pack_h8(v + 8 * c);
+}
+template <int NF>
+__device__ __forceinline__ void st_row(uint8_t* blk, int row, int f0, const float* v) {
+#pragma unroll
+  for (int c = 0; c < NF / 8; ++c) {
+    const int chunk = (f0 >> 3) + c;
+    *reinterpret_cast<uint4*>(blk + row * 128 + ((chunk ^ (row & 7)) << 4)) = pack_bf16x8(v + 8 * c);
+  }
+}
+template <int NF>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[NF]) {
+  if constexpr (NF == 32) {
+    tmem_ld32(taddr, v);
+  } else {
+    tmem_ld16(taddr, v);
+  }
+}
+
 // Node coordinates within the stacked lattices.
 struct NodeXY {
   int x, y;

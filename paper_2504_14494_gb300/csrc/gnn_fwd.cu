@@ -218,13 +218,18 @@ struct RoundArgs {
 #ifndef LBM_ROUND_CTAS
 #define LBM_ROUND_CTAS 2
 #endif
+#ifndef LBM_ROUND_TPN
+#define LBM_ROUND_TPN 2  // threads per node of the round kernel (2 or 4)
+#endif
 #ifndef LBM_NBR_GROUP
 #define LBM_NBR_GROUP 4  // neighbour loads in flight per thread and chunk
 #endif
-template <int MODE, class Geo>
-__global__ void __launch_bounds__(256, LBM_ROUND_CTAS) gnn_round_kernel(RoundArgs ra, Geo geo,
-                                                           const uint8_t* __restrict__ packed,
-                                                           unsigned* stw) {
+// TPN threads per node (2 or 4), each owning FPT = 64 / TPN features; warp w
+// reads tensor-memory lanes 32 (w % 4).. and columns of its feature slice.
+template <int MODE, int TPN, class Geo>
+__global__ void __launch_bounds__(128 * TPN, LBM_ROUND_CTAS) gnn_round_kernel(
+    RoundArgs ra, Geo geo, const uint8_t* __restrict__ packed, unsigned* stw) {
+  constexpr int FPT = HID / TPN;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   TcShared* sh = reinterpret_cast<TcShared*>(sm + rnd::SH);
@@ -253,7 +258,7 @@ __global__ void __launch_bounds__(256, LBM_ROUND_CTAS) gnn_round_kernel(RoundArg
   const float* nrm = reinterpret_cast<const float*>(sm + rnd::NORM);
   uint8_t* H = sm + rnd::HA;
   uint8_t* Ag = sm + rnd::HA + 16384;
-  const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
+  const int node = threadIdx.x & 127, part = threadIdx.x >> 7, f0 = part * FPT;
   const uint32_t lb = lane_base(tc.tmem);
   const int64_t N = geo.count();
   const int64_t base = geo.base(), ps = geo.ps();
@@ -268,15 +273,15 @@ __global__ void __launch_bounds__(256, LBM_ROUND_CTAS) gnn_round_kernel(RoundArg
     const GeoPos p = geo.pos(base + nn);
     if (mlp_only) {  // no message passing: a = 0, h unchanged
       if (on && ra.a_out) {
-        const float zero[32] = {};
-        st_pb32(ra.a_out, N, n, f0, zero);
+        const float zero[FPT] = {};
+        st_pb<FPT>(ra.a_out, N, n, f0, zero);
       }
     } else {
     // messages m_ik = GELU(A_i + B_j + c_k), summed over the 8 neighbours, in
     // packed FP16 pairs; per 16-feature chunk the 8 neighbour loads are
     // issued together.
 #pragma unroll
-    for (int sc = 0; sc < 2; ++sc) {
+    for (int sc = 0; sc < FPT / 16; ++sc) {
       const int c0 = f0 + 16 * sc;
       uint4 araw[2];
       araw[0] = __ldg(chunk8(ra.ab_in, N, nn, c0));
@@ -327,40 +332,38 @@ __global__ void __launch_bounds__(256, LBM_ROUND_CTAS) gnn_round_kernel(RoundArg
       }
     }
     }
-    float h[32];
-    ld_pb32(ra.h_in, N, nn, f0, h);
+    float h[FPT];
+    ld_pb<FPT>(ra.h_in, N, nn, f0, h);
     if (!mlp_only) {
-      st_row32(H, node, f0, h);
+      st_row<FPT>(H, node, f0, h);
       // node update: h <- h + GELU(W_n [h; a] + b_n)
       if (!tc_run(sh, tc, stw, [&] {
             umma_128xN(tc.tmem, smem_u32(H), 16384, smem_u32(sm + rnd::WN), 8192, 2, 64, false);
           }))
         break;
-      float z[32];
-      tmem_ld32(lb + f0, z);
+      float z[FPT];
+      tmem_ld<FPT>(lb + f0, z);
 #pragma unroll
-      for (int c = 0; c < 32; ++c) h[c] += gelu(z[c] + bn[f0 + c]);
+      for (int c = 0; c < FPT; ++c) h[c] += gelu(z[c] + bn[f0 + c]);
     }
-    if (on && ra.h_out) st_pb32(ra.h_out, N, n, f0, h);
-    st_row32(H, node, f0, h);
+    if (on && ra.h_out) st_pb<FPT>(ra.h_out, N, n, f0, h);
+    st_row<FPT>(H, node, f0, h);
     if (MODE == 0) {
       if (!tc_run(sh, tc, stw, [&] {
             umma_128xN(tc.tmem, smem_u32(H), 0, smem_u32(sm + rnd::WX), 0, 1, 128, false);
           }))
         break;
-      float a[32], b[32];
-      tmem_ld32(lb + f0, a);
-      tmem_ld32(lb + HID + f0, b);
-      if (on) {
-        st_ph32(ra.ab_out, N, n, f0, a);
-        st_ph32(ra.ab_out, N, n, HID + f0, b);
-      }
+      float a[FPT];
+      tmem_ld<FPT>(lb + f0, a);
+      if (on) st_ph<FPT>(ra.ab_out, N, n, f0, a);
+      tmem_ld<FPT>(lb + HID + f0, a);
+      if (on) st_ph<FPT>(ra.ab_out, N, n, HID + f0, a);
     } else {
       if (!tc_run(sh, tc, stw, [&] {
             umma_128xN(tc.tmem, smem_u32(H), 0, smem_u32(sm + rnd::WX), 0, 1, 16, false);
           }))
         break;
-      if (half == 0) {
+      if (part == 0) {
         float y[16];
         tmem_ld16(lb, y);
 #pragma unroll
@@ -439,18 +442,19 @@ static cudaError_t round_any(int mode, const RoundLaunch& rl, const Geo& geo, in
   RoundArgs ra{rl.h_in, rl.ab_in, rl.h_out, rl.a_out, rl.ab_out, rl.y_out, rl.f_post, rl.f_out,
                rl.tau, rl.taus, rl.round};
   cudaError_t e;
+  constexpr int T = LBM_ROUND_TPN;
   switch (mode) {
     case 0:
-      if ((e = set_smem(gnn_round_kernel<0, Geo>, bytes)) != cudaSuccess) return e;
-      gnn_round_kernel<0, Geo><<<grid, 256, bytes, st>>>(ra, geo, packed, stw);
+      if ((e = set_smem(gnn_round_kernel<0, T, Geo>, bytes)) != cudaSuccess) return e;
+      gnn_round_kernel<0, T, Geo><<<grid, 128 * T, bytes, st>>>(ra, geo, packed, stw);
       break;
     case 1:
-      if ((e = set_smem(gnn_round_kernel<1, Geo>, bytes)) != cudaSuccess) return e;
-      gnn_round_kernel<1, Geo><<<grid, 256, bytes, st>>>(ra, geo, packed, stw);
+      if ((e = set_smem(gnn_round_kernel<1, T, Geo>, bytes)) != cudaSuccess) return e;
+      gnn_round_kernel<1, T, Geo><<<grid, 128 * T, bytes, st>>>(ra, geo, packed, stw);
       break;
     default:
-      if ((e = set_smem(gnn_round_kernel<2, Geo>, bytes)) != cudaSuccess) return e;
-      gnn_round_kernel<2, Geo><<<grid, 256, bytes, st>>>(ra, geo, packed, stw);
+      if ((e = set_smem(gnn_round_kernel<2, T, Geo>, bytes)) != cudaSuccess) return e;
+      gnn_round_kernel<2, T, Geo><<<grid, 128 * T, bytes, st>>>(ra, geo, packed, stw);
       break;
   }
   return cudaGetLastError();
