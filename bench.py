@@ -138,7 +138,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
     import torch
-    from paper_2504_14494_gb300 import build, lib as L
+    from paper_2504_14494_gb300 import build, lib as L, parallel
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     build.build()
@@ -199,11 +199,10 @@ def run_ours(args, rank, world, local_rank):
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    t_max = ms
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+        dist.barrier()
+    # node updates summed over ranks / the slowest rank's time
+    _, t_max, rate = parallel.aggregate_throughput(nodes * args.steps, ms, device=dev)
     done_steps = args.warmup + args.steps
     assert L.lbm_get_status() == 0
     if args.only == "bgk":
@@ -272,7 +271,7 @@ def run_ours(args, rank, world, local_rank):
     traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == sha else None
     out = {
         "metric": METRIC,
-        "value": round(world * nodes * args.steps / (t_max / 1e3) / 1e6, 1),
+        "value": round(rate / 1e6, 1),
         "unit": "MLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms_step, 5),

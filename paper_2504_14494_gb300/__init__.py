@@ -4,5 +4,10 @@ collision of arXiv 2504.14494 behind the C ABI of liblbmgnn.so.
   lib     -- ctypes binding, one Python function per C entry point
   build   -- in-tree nvcc build of liblbmgnn.so
   inputs  -- seeded synthetic inputs (weights, perturbations, workloads)
+  autograd -- torch.autograd.Function over gnn_forward / gnn_backward
+  train   -- refined-lattice training pairs and the fused training loop
+  parallel -- multi-rank host logic: sharding, timing aggregation,
+              data-parallel training (one gradient all-reduce per step)
+  checkpoint -- CRC-checked save/restore of training state
 """
 from . import lib  # noqa: F401

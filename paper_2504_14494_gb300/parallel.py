@@ -1,0 +1,156 @@
+"""Multi-rank execution: one process per GPU, torch.distributed for the
+little that crosses ranks.
+
+The method's work splits into independent units, so no step of a lattice
+update exchanges data between ranks:
+
+  * stepping (plain BGK, GNN-LBM, batched lattices): each rank advances its
+    own lattices.  The only cross-rank operation is the host-side
+    aggregation of a timed region: the slowest rank's time and the units
+    summed over ranks (`aggregate_throughput`).  Lattices of uneven size are
+    dealt to ranks by `shard` (longest-processing-time first).
+  * training (Sec. 2.4): data parallel over training instances.  Every rank
+    computes the gradient of Eq. 4 on its own pairs; one all-reduce of the
+    38,922 FP32 gradient values per step averages them (with equal node
+    counts per rank the average is the gradient of the mean over the union of
+    the ranks' pairs), then every rank applies the same AdamW update, so the
+    parameter vectors stay identical.
+
+A single lattice split over several GPUs (halo exchange) is not provided.
+
+Every function here works with world size 1 (no process group) and with any
+backend; the host logic is exercised with `gloo` on CPU tensors.
+"""
+import numpy as np
+
+from . import inputs
+from . import lib as L
+
+
+def _dist():
+    import torch.distributed as dist
+    return dist if dist.is_available() and dist.is_initialized() else None
+
+
+def rank_and_size(group=None):
+    """(rank, world size) in `group`; (0, 1) without a process group."""
+    dist = _dist()
+    if dist is None:
+        return 0, 1
+    return dist.get_rank(group), dist.get_world_size(group)
+
+
+def shard(weights, size):
+    """Deal units of the given weights (e.g. node counts) to `size` ranks:
+    heaviest first, each to the currently lightest rank (lowest rank on
+    ties).  Deterministic; returns one sorted index list per rank.  The
+    heaviest rank carries at most the mean load plus the largest unit."""
+    if size < 1:
+        raise ValueError("size must be >= 1")
+    w = [float(x) for x in weights]
+    if any(x < 0 for x in w):
+        raise ValueError("weights must be non-negative")
+    order = sorted(range(len(w)), key=lambda i: (-w[i], i))
+    load = [0.0] * size
+    out = [[] for _ in range(size)]
+    for i in order:
+        r = min(range(size), key=lambda j: (load[j], j))
+        out[r].append(i)
+        load[r] += w[i]
+    return [sorted(o) for o in out]
+
+
+def average_(t, group=None):
+    """In-place mean of tensor `t` over the ranks of `group` (no-op alone)."""
+    dist = _dist()
+    if dist is None:
+        return t
+    size = dist.get_world_size(group)
+    if size > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        t.div_(size)
+    return t
+
+
+def broadcast_(t, src=0, group=None):
+    """In-place copy of rank `src`'s tensor to every rank of `group`."""
+    dist = _dist()
+    if dist is not None and dist.get_world_size(group) > 1:
+        dist.broadcast(t, src=src, group=group)
+    return t
+
+
+def aggregate_throughput(units, ms, device="cpu", group=None):
+    """Host aggregation of a timed region.  `units`: work this rank did
+    (e.g. node updates); `ms`: its measured time.  Returns
+    (units summed over ranks, slowest rank's ms, summed units per second)."""
+    import torch
+    dist = _dist()
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None and dist.get_world_size(group) > 1:
+        dist.all_reduce(u, op=dist.ReduceOp.SUM, group=group)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    total, t_max = float(u.item()), float(t.item())
+    return total, t_max, (total / (t_max / 1e3) if t_max > 0 else float("inf"))
+
+
+class DataParallelTrainer:
+    """AdamW training of the network, data parallel over ranks.
+
+    Per step and rank: the next batch of pairs from this rank's PairStream
+    (instances seeded by `seed` and the rank), then through the C ABI
+    lbm_stream, gnn_forward, gnn_collide_loss (Eq. 3, Eq. 4, dL/dy) and
+    gnn_backward (dL/dparams); the gradient and the loss are averaged over
+    ranks (`average_`), and gnn_adamw plus gnn_pack update every rank's
+    identical parameter copy.  With one rank this is the same computation as
+    the fused gnn_train_step."""
+
+    def __init__(self, device, theta=None, lr=1e-3, wd=1e-2, seed=0, group=None, **stream_kw):
+        import torch
+        from .train import PairStream
+        self.group = group
+        self.rank, self.size = rank_and_size(group)
+        self.data = PairStream(device, seed=seed * 1009 + self.rank, **stream_kw)
+        theta = inputs.xavier_params(seed) if theta is None else theta
+        self.params = torch.from_numpy(np.asarray(theta, np.float32)).to(device)
+        broadcast_(self.params, 0, group)
+        s = self.data.coarse
+        n = s.nx * s.ny * s.nb
+        nt = L.gnn_trainable_count()
+        self.packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=device)
+        L.gnn_pack(self.params, self.packed)
+        self.m = torch.zeros(nt, device=device)
+        self.v = torch.zeros_like(self.m)
+        self.grads = torch.zeros(nt, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=device)
+        self.f_pre = torch.empty(9 * n, device=device)
+        self.y = torch.empty(10 * n, device=device)
+        self.dy = torch.empty(10 * n, device=device)
+        self.saved = torch.empty(L.gnn_saved_bytes(s), dtype=torch.uint8, device=device)
+        self.ws_loss = torch.empty(L.gnn_loss_workspace_bytes(s), dtype=torch.uint8,
+                                   device=device)
+        self.ws_bwd = torch.empty(L.gnn_backward_workspace_bytes(s), dtype=torch.uint8,
+                                  device=device)
+        self.lr, self.wd = lr, wd
+        self.step_count = 0
+
+    def step(self):
+        """One data-parallel step; returns nothing (the rank-averaged loss
+        before the update is left in self.loss)."""
+        s = self.data.coarse
+        f_in, f_tg, tau_c = self.data.next()
+        self.step_count += 1
+        L.lbm_stream(f_in, self.f_pre, s)
+        L.gnn_forward(self.f_pre, s, self.packed, self.saved, self.y)
+        L.gnn_collide_loss(self.f_pre, self.y, f_tg, s, 1.0, tau_c, self.packed, self.loss,
+                           self.dy, None, self.ws_loss)
+        L.gnn_backward(self.f_pre, s, self.packed, self.saved, self.dy, self.grads, None,
+                       self.ws_bwd)
+        average_(self.grads, self.group)
+        average_(self.loss, self.group)
+        L.gnn_adamw(self.params, self.grads, self.m, self.v, self.step_count, self.lr, self.wd)
+        L.gnn_pack(self.params, self.packed)
+
+    def theta(self):
+        return self.params.cpu().numpy().copy()

@@ -290,3 +290,25 @@ def test_variant_backward_and_loss_match_oracle(lbmlib, cuda, variant):
             assert not np.any(a), name          # unused round weights of the MLP-only net
             continue
         assert _cos(a, r) >= 0.999 and rel_l2(a, r) <= 3e-2, (name, _cos(a, r), rel_l2(a, r))
+
+
+def test_data_parallel_trainer_alone_equals_fused_step(lbmlib, cuda):
+    """With one rank, the split data-parallel step (stream, forward,
+    collide+loss, backward, rank average, AdamW, repack) is the fused
+    gnn_train_step computation: identical parameters and losses after 3
+    steps on the same generated pairs (deterministic kernels, same order)."""
+    import torch
+    from paper_2504_14494_gb300.parallel import DataParallelTrainer
+    from paper_2504_14494_gb300.train import Trainer
+    kw = dict(n=32, batch=2, episode=4)
+    theta = inputs.xavier_params(0)
+    a = Trainer(cuda, theta=theta, lr=1e-3, wd=1e-2, seed=0, **kw)
+    b = DataParallelTrainer(cuda, theta=theta, lr=1e-3, wd=1e-2, seed=0, **kw)
+    for _ in range(3):
+        a.step()
+        b.step()
+        torch.cuda.synchronize()
+        assert a.loss.item() == b.loss.item()
+    assert lbmlib.lbm_get_status() == 0
+    assert torch.equal(a.params, b.params)
+    assert torch.equal(a.packed, b.packed)
