@@ -120,6 +120,33 @@ LBM_API int lbm_step_channel(const float* f_in, float* f_out, float* f_tmp, lbm_
                              const float* taus, float force_x, int nsteps, double* totals,
                              void* stream);
 
+/* Bytes of the device workspace of lbm_step_bgk_host for shape s (two
+ * population buffers, the totals and the per-lattice taus); 0 for a bad
+ * shape. */
+LBM_API size_t lbm_host_workspace_bytes(lbm_shape s);
+
+/* lbm_step_bgk for a state held in HOST memory (Eq. 1-2, Fig. 1 loop):
+ * copies f_in_host (host, populations of shape s in the device layout: 9
+ * planes of plane_stride floats) to the device, advances nsteps >= 1 steps,
+ * and copies the FP64 totals of the final state (as lbm_step_bgk) to
+ * totals_host (host double[5], nullable) and the final state to f_out_host
+ * (host, same layout, nullable).  taus_host: nullable host array of nb
+ * per-lattice relaxation times (else tau for every lattice).
+ *
+ * The host-to-device copy runs on a second stream of the library's own in
+ * 16 blocks of lattice rows (one 2D copy of the 9 planes per block);
+ * the first step of a block is launched on `stream` as soon as the rows it
+ * pulls from (y -+ 1 with periodic wrap) have arrived, so the copy overlaps
+ * the step.  Overlap needs page-locked host memory; pageable memory works
+ * without it.  Asynchronous on `stream`: host outputs are valid, and host
+ * inputs may be reused, once `stream` has completed the call's work.
+ * workspace: device, 256-byte aligned, lbm_host_workspace_bytes(s) bytes, not
+ * used by another call in flight on another stream.  Errors as lbm_step_bgk;
+ * LBM_ERR_WORKSPACE for a missing, small or misaligned workspace. */
+LBM_API int lbm_step_bgk_host(const float* f_in_host, float* f_out_host, lbm_shape s, float tau,
+                              const float* taus_host, int nsteps, double* totals_host,
+                              void* workspace, size_t ws_bytes, void* stream);
+
 /* Macroscopic variables of a stored state (Fig. 1 'Compute macroscopic
  * variables'): rho = sum f_i, u = sum f_i e_i / rho per node (FP32 out,
  * node-major planes of nb*ny*nx values), and optional FP64 totals (as in

@@ -1,7 +1,10 @@
 // C ABI entry points of liblbmgnn.so: argument validation, buffer
 // ping-pong, and dispatch to the kernel launchers.  See include/lbmgnn.h for
 // the meaning of every argument.
+#include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "launch.h"
@@ -37,6 +40,42 @@ bool overlap(const void* a, const void* b, int64_t bytes) {
   const char* pa = static_cast<const char*>(a);
   const char* pb = static_cast<const char*>(b);
   return pa < pb + bytes && pb < pa + bytes;
+}
+
+// Side stream and events of lbm_step_bgk_host, created once per device and
+// kept for the life of the process.  Enqueueing is serialised by a mutex;
+// an event may be re-recorded as soon as the waits on it are enqueued.
+#ifndef LBM_HOST_CHUNKS
+#define LBM_HOST_CHUNKS 16  // row blocks of the host-to-device copy
+#endif
+constexpr int HOST_CHUNKS = LBM_HOST_CHUNKS;
+struct HostPipe {
+  bool ready = false;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t entry = nullptr;
+  cudaEvent_t arrived[HOST_CHUNKS] = {};
+};
+std::mutex g_pipe_mu;
+HostPipe g_pipe[64];
+
+HostPipe* host_pipe() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  HostPipe& p = g_pipe[dev];
+  if (!p.ready) {
+    if (cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&p.entry, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    for (auto& e : p.arrived)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    p.ready = true;
+  }
+  return &p;
+}
+
+// Workspace of lbm_step_bgk_host: two population buffers, the FP64 totals
+// (256 bytes) and the per-lattice taus (nb floats), each 256-byte aligned.
+int64_t host_ws_bytes(const Shape& s) {
+  return 2 * ((f_bytes(s) + 255) / 256 * 256) + 256 + ((int64_t)s.nb * 4 + 255) / 256 * 256;
 }
 
 }  // namespace
@@ -166,6 +205,115 @@ int lbm_moments(const float* f, lbm_shape shape, float* rho, float* ux, float* u
   if (totals && cudaMemsetAsync(totals, 0, 5 * sizeof(double), st) != cudaSuccess)
     return LBM_ERR_CUDA;
   return cuda_status(launch_moments(f, s, rho, ux, uy, totals, st));
+}
+
+size_t lbm_host_workspace_bytes(lbm_shape shape) {
+  Shape s;
+  if (check_shape(shape, &s)) return 0;
+  return (size_t)host_ws_bytes(s);
+}
+
+int lbm_step_bgk_host(const float* f_in_host, float* f_out_host, lbm_shape shape, float tau,
+                      const float* taus_host, int nsteps, double* totals_host, void* workspace,
+                      size_t ws_bytes, void* stream) {
+  Shape s;
+  if (!f_in_host || nsteps < 1) return LBM_ERR_ARG;
+  if (int r = check_shape(shape, &s)) return r;
+  if (taus_host) {
+    for (int b = 0; b < s.nb; ++b)
+      if (int r = check_tau(taus_host[b])) return r;
+  } else if (int r = check_tau(tau)) {
+    return r;
+  }
+  if (!workspace || (int64_t)ws_bytes < host_ws_bytes(s) ||
+      (uintptr_t)workspace % 256 != 0)
+    return LBM_ERR_WORKSPACE;
+  const int64_t fb = (f_bytes(s) + 255) / 256 * 256;
+  auto* w = static_cast<char*>(workspace);
+  float* da = reinterpret_cast<float*>(w);
+  float* db = reinterpret_cast<float*>(w + fb);
+  double* dtot = reinterpret_cast<double*>(w + 2 * fb);
+  // per-lattice taus are copied from host memory into the workspace
+  float* dtaus = taus_host ? reinterpret_cast<float*>(w + 2 * fb + 256) : nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  std::lock_guard<std::mutex> lock(g_pipe_mu);
+  HostPipe* p = host_pipe();
+  if (!p) return LBM_ERR_CUDA;
+  // Row blocks: rows [r0, r1) of the nb*ny lattice rows; block c can take
+  // its first step once every row it pulls from (y -+ 1 with periodic wrap,
+  // inside its own lattice) has arrived.
+  const int64_t rows = (int64_t)s.nb * s.ny;
+  const int nc = (int)std::min<int64_t>(HOST_CHUNKS, rows);
+  const int64_t per = (rows + nc - 1) / nc;
+  auto chunk_of = [&](int64_t r) { return (int)(r / per); };
+  std::vector<int> need(nc, 0);
+  for (int64_t r = 0; r < rows; ++r) {
+    const int64_t b = r / s.ny, y = r - b * s.ny;
+    const int64_t up = b * s.ny + (y + 1 == s.ny ? 0 : y + 1);
+    const int64_t dn = b * s.ny + (y == 0 ? s.ny - 1 : y - 1);
+    int& n = need[chunk_of(r)];
+    n = std::max({n, chunk_of(r), chunk_of(up), chunk_of(dn)});
+  }
+  const int used = (int)((rows + per - 1) / per);
+
+  if (cudaEventRecord(p->entry, st) != cudaSuccess) return LBM_ERR_CUDA;
+  if (cudaStreamWaitEvent(p->copy, p->entry, 0) != cudaSuccess) return LBM_ERR_CUDA;
+  if (dtaus && cudaMemcpyAsync(dtaus, taus_host, s.nb * sizeof(float), cudaMemcpyHostToDevice,
+                               st) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  if (totals_host && cudaMemsetAsync(dtot, 0, 5 * sizeof(double), st) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  for (int c = 0; c < used; ++c) {
+    const int64_t r0 = c * per, r1 = std::min(rows, r0 + per);
+    const size_t width = (size_t)((r1 - r0) * s.nx) * sizeof(float);
+    const size_t pitch = (size_t)s.ps * sizeof(float);
+    const int64_t off = r0 * s.nx;
+    if (pitch < (size_t(1) << 31)) {  // the block of all 9 planes as one 2D copy
+      if (cudaMemcpy2DAsync(da + off, pitch, f_in_host + off, pitch, width, Q,
+                            cudaMemcpyHostToDevice, p->copy) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    } else {
+      for (int q = 0; q < Q; ++q)
+        if (cudaMemcpyAsync(da + q * s.ps + off, f_in_host + q * s.ps + off, width,
+                            cudaMemcpyHostToDevice, p->copy) != cudaSuccess)
+          return LBM_ERR_CUDA;
+    }
+    if (cudaEventRecord(p->arrived[c], p->copy) != cudaSuccess) return LBM_ERR_CUDA;
+  }
+  // first step, block by block in order of readiness
+  std::vector<int> order(used);
+  for (int c = 0; c < used; ++c) order[c] = c;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return need[a] < need[b]; });
+  int waited = -1;
+  double* tot1 = (nsteps == 1 && totals_host) ? dtot : nullptr;
+  for (int c : order) {
+    if (need[c] > waited) {
+      if (cudaStreamWaitEvent(st, p->arrived[need[c]], 0) != cudaSuccess) return LBM_ERR_CUDA;
+      waited = need[c];
+    }
+    const int64_t r0 = c * per, r1 = std::min(rows, r0 + per);
+    if (launch_bgk_step_rows(da, db, s, tau, dtaus, tot1, r0, r1, st) != cudaSuccess)
+      return LBM_ERR_CUDA;
+  }
+  // (need[c] >= c, so st has waited for the last block: the copy stream has
+  // no work left that st does not wait for.)  Remaining steps: db -> da -> ...
+  float* src = db;
+  float* dst = da;
+  for (int k = 1; k < nsteps; ++k) {
+    const bool last = (k == nsteps - 1);
+    if (launch_bgk_step(src, dst, s, tau, dtaus, (last && totals_host) ? dtot : nullptr, st) !=
+        cudaSuccess)
+      return LBM_ERR_CUDA;
+    std::swap(src, dst);
+  }
+  if (totals_host && cudaMemcpyAsync(totals_host, dtot, 5 * sizeof(double),
+                                     cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  if (f_out_host && cudaMemcpyAsync(f_out_host, src, (size_t)f_bytes(s),
+                                    cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  return LBM_OK;
 }
 
 }  // extern "C"

@@ -30,68 +30,21 @@ unsigned* status_word() {
 }
 
 // ---------------------------------------------------------------------------
-// Block-wide FP64 reduction of the five totals into totals[0..4] (atomics).
-template <int NT>
-__device__ __forceinline__ void block_totals(double (&t)[5], double* __restrict__ totals) {
-  __shared__ double red[NT / 32][5];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
-  }
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) red[w][k] = t[k];
-  }
-  __syncthreads();
-  if (threadIdx.x < 5) {
-    double acc = 0.0;
-#pragma unroll
-    for (int i = 0; i < NT / 32; ++i) acc += red[i][threadIdx.x];
-    if (acc != 0.0) atomicAdd(totals + threadIdx.x, acc);
-  }
-}
-
-// Totals contribution of one stored node (post-collision values), summed in
-// FP64 from the FP32 populations.
-__device__ __forceinline__ void add_node_totals(double (&t)[5], const float (&o)[Q]) {
-  bool finite = true;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) finite &= isfinite(o[i]);
-  if (!finite) {
-    t[4] += 1.0;
-    return;
-  }
-  double rho = 0.0, jx = 0.0, jy = 0.0;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const double v = o[i];
-    rho += v;
-    if (ex(i)) jx += ex(i) * v;
-    if (ey(i)) jy += ey(i) * v;
-  }
-  t[0] += rho;
-  t[1] += jx;
-  t[2] += jy;
-  t[3] += 0.5 * (jx * jx + jy * jy) / rho;
-}
-
-// ---------------------------------------------------------------------------
 // Fast step: nx % 4 == 0, plane stride % 4 == 0, 16-byte aligned buffers.
 template <bool TOTALS>
 __global__ void __launch_bounds__(128) bgk_step_x4(const float* __restrict__ fin,
                                                    float* __restrict__ fout, Shape s, float tau,
                                                    const float* __restrict__ taus,
-                                                   double* __restrict__ totals, unsigned* stw) {
+                                                   double* __restrict__ totals, unsigned* stw,
+                                                   int64_t row0, int64_t row1) {
+  // Rows row0 .. row1-1 of the nb*ny lattice rows are updated.
   const int lane = threadIdx.x & 31;
   const int64_t wid = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
   const int nchunk = (s.nx + 127) >> 7;
-  const int64_t rows = (int64_t)s.nb * s.ny;
-  int64_t row = wid / nchunk;
-  const int chunk = (int)(wid - row * nchunk);
-  const bool warp_on = row < rows;
-  if (!warp_on) row = rows - 1;
+  int64_t row = row0 + wid / nchunk;
+  const int chunk = (int)(wid % nchunk);
+  const bool warp_on = row < row1;
+  if (!warp_on) row = row1 - 1;
   const int x0 = chunk * 128 + lane * 4;
   const bool on = warp_on && x0 < s.nx;
   const int xl = on ? x0 : s.nx - 4;  // in-range position for idle lanes
@@ -151,13 +104,13 @@ __global__ void __launch_bounds__(128) bgk_step_x4(const float* __restrict__ fin
     }
   }
   if constexpr (TOTALS) {
-    double t[5] = {0, 0, 0, 0, 0};
+    NodeTotals t;
     if (on) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) add_node_totals(t, f[j]);
+      for (int j = 0; j < 4; ++j) t.add(f[j]);
     }
-    if (t[4] != 0.0) raise_status(stw, ST_NONFINITE);
-    block_totals<128>(t, totals);
+    if (t.bad) raise_status(stw, ST_NONFINITE);
+    t.flush<128>(totals);
   }
 }
 
@@ -166,9 +119,11 @@ template <bool TOTALS>
 __global__ void __launch_bounds__(256) bgk_step_any(const float* __restrict__ fin,
                                                     float* __restrict__ fout, Shape s, float tau,
                                                     const float* __restrict__ taus,
-                                                    double* __restrict__ totals, unsigned* stw) {
-  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                                    double* __restrict__ totals, unsigned* stw,
+                                                    int64_t row0, int64_t row1) {
+  // Nodes of rows row0 .. row1-1 of the nb*ny lattice rows are updated.
+  const int64_t N = row1 * s.nx;
+  const int64_t n = row0 * s.nx + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool on = n < N;
   const int64_t nn = on ? n : N - 1;
   const int x = (int)(nn % s.nx);
@@ -190,10 +145,10 @@ __global__ void __launch_bounds__(256) bgk_step_any(const float* __restrict__ fi
     for (int q = 0; q < Q; ++q) fout[q * s.ps + nn] = f[q];
   }
   if constexpr (TOTALS) {
-    double t[5] = {0, 0, 0, 0, 0};
-    if (on) add_node_totals(t, f);
-    if (t[4] != 0.0) raise_status(stw, ST_NONFINITE);
-    block_totals<256>(t, totals);
+    NodeTotals t;
+    if (on) t.add(f);
+    if (t.bad) raise_status(stw, ST_NONFINITE);
+    t.flush<256>(totals);
   }
 }
 
@@ -218,10 +173,10 @@ __global__ void __launch_bounds__(256) moments_kernel(const float* __restrict__ 
     if (uy) uy[nn] = m.uy;
   }
   if (totals) {
-    double t[5] = {0, 0, 0, 0, 0};
-    if (on) add_node_totals(t, v);
-    if (t[4] != 0.0) raise_status(stw, ST_NONFINITE);
-    block_totals<256>(t, totals);
+    NodeTotals t;
+    if (on) t.add(v);
+    if (t.bad) raise_status(stw, ST_NONFINITE);
+    t.flush<256>(totals);
   }
 }
 
@@ -256,26 +211,36 @@ static inline bool x4_ok(const float* a, const float* b, const Shape& s) {
          ((uintptr_t)b % 16 == 0);
 }
 
-cudaError_t launch_bgk_step(const float* fin, float* fout, const Shape& s, float tau,
-                            const float* taus, double* totals, cudaStream_t st) {
-  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+cudaError_t launch_bgk_step_rows(const float* fin, float* fout, const Shape& s, float tau,
+                                 const float* taus, double* totals, int64_t row0, int64_t row1,
+                                 cudaStream_t st) {
+  if (row0 < 0 || row1 > (int64_t)s.nb * s.ny || row0 >= row1) return cudaErrorInvalidValue;
   unsigned* stw = status_word();
   if (totals && !stw) return cudaErrorInvalidDevice;
+  const int64_t rows = row1 - row0;
   if (x4_ok(fin, fout, s)) {
-    const int64_t warps = (int64_t)s.nb * s.ny * ((s.nx + 127) / 128);
+    const int64_t warps = rows * ((s.nx + 127) / 128);
     const unsigned blocks = (unsigned)((warps + 3) / 4);
     if (totals)
-      bgk_step_x4<true><<<blocks, 128, 0, st>>>(fin, fout, s, tau, taus, totals, stw);
+      bgk_step_x4<true><<<blocks, 128, 0, st>>>(fin, fout, s, tau, taus, totals, stw, row0, row1);
     else
-      bgk_step_x4<false><<<blocks, 128, 0, st>>>(fin, fout, s, tau, taus, totals, stw);
+      bgk_step_x4<false><<<blocks, 128, 0, st>>>(fin, fout, s, tau, taus, totals, stw, row0,
+                                                 row1);
   } else {
-    const unsigned blocks = (unsigned)((N + 255) / 256);
+    const unsigned blocks = (unsigned)((rows * s.nx + 255) / 256);
     if (totals)
-      bgk_step_any<true><<<blocks, 256, 0, st>>>(fin, fout, s, tau, taus, totals, stw);
+      bgk_step_any<true><<<blocks, 256, 0, st>>>(fin, fout, s, tau, taus, totals, stw, row0,
+                                                 row1);
     else
-      bgk_step_any<false><<<blocks, 256, 0, st>>>(fin, fout, s, tau, taus, totals, stw);
+      bgk_step_any<false><<<blocks, 256, 0, st>>>(fin, fout, s, tau, taus, totals, stw, row0,
+                                                  row1);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_bgk_step(const float* fin, float* fout, const Shape& s, float tau,
+                            const float* taus, double* totals, cudaStream_t st) {
+  return launch_bgk_step_rows(fin, fout, s, tau, taus, totals, 0, (int64_t)s.nb * s.ny, st);
 }
 
 cudaError_t launch_moments(const float* f, const Shape& s, float* rho, float* ux, float* uy,

@@ -68,6 +68,106 @@ __device__ __forceinline__ void bgk_collide(float (&f)[Q], float omega) {
   for (int i = 0; i < Q; ++i) f[i] = f[i] - omega * (f[i] - feq_i(i, m, usq15));
 }
 
+// ---- totals (mass, momentum, kinetic energy) at FP64 accuracy -------------
+// GB300 runs FP64 at a small fraction of its FP32 rate, so the per-node sums
+// of the totals are carried as unevaluated pairs hi + lo of FP32 values
+// ("double-float"): each addition is Knuth's error-free TwoSum (s + e equals
+// a + b exactly), the rounding errors collect in lo, and the pair is
+// renormalised by another TwoSum once per node.  About 2^-46 relative error
+// per node; FP64 arithmetic is used once per warp.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void df_add(DF& a, float x) {  // a += x (lo not renormalised)
+  float s, e;
+  two_sum(a.hi, x, s, e);
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, e);
+}
+__device__ __forceinline__ void df_norm(DF& a) {
+  float s, e;
+  two_sum(a.hi, a.lo, s, e);
+  a.hi = s;
+  a.lo = e;
+}
+__device__ __forceinline__ void df_add(DF& a, const DF& b) {  // a += b, renormalised
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, __fadd_rn(b.lo, e));
+  df_norm(a);
+}
+__device__ __forceinline__ DF df_shfl_xor(const DF& a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
+// Per-thread totals of stored nodes: mass sum f_i, momentum sum f_i e_i,
+// kinetic energy sum |j|^2 / (2 rho), and the count of nodes holding a
+// non-finite population (excluded from the sums).
+struct NodeTotals {
+  DF m{0.f, 0.f}, px{0.f, 0.f}, py{0.f, 0.f}, e{0.f, 0.f};
+  unsigned bad = 0;
+
+  __device__ __forceinline__ void add(const float (&o)[Q]) {
+    bool finite = true;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) finite &= isfinite(o[i]);
+    if (!finite) {
+      ++bad;
+      return;
+    }
+    DF r{o[0], 0.f}, jx{0.f, 0.f}, jy{0.f, 0.f};
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      df_add(r, o[i]);
+      if (ex(i)) df_add(jx, ex(i) > 0 ? o[i] : -o[i]);
+      if (ey(i)) df_add(jy, ey(i) > 0 ? o[i] : -o[i]);
+    }
+    df_norm(r);
+    df_norm(jx);
+    df_norm(jy);
+    const float en = 0.5f * (jx.hi * jx.hi + jy.hi * jy.hi) / r.hi;
+    df_add(m, r);
+    df_add(px, jx);
+    df_add(py, jy);
+    df_add(e, DF{en, 0.f});
+  }
+
+  // Sum over the block (NT threads) added to totals[0..4] in FP64.
+  template <int NT>
+  __device__ __forceinline__ void flush(double* __restrict__ totals) {
+    __shared__ double red[NT / 32][5];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      df_add(m, df_shfl_xor(m, o));
+      df_add(px, df_shfl_xor(px, o));
+      df_add(py, df_shfl_xor(py, o));
+      df_add(e, df_shfl_xor(e, o));
+    }
+    const unsigned nbad = __reduce_add_sync(0xffffffffu, bad);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      red[w][0] = (double)m.hi + (double)m.lo;
+      red[w][1] = (double)px.hi + (double)px.lo;
+      red[w][2] = (double)py.hi + (double)py.lo;
+      red[w][3] = (double)e.hi + (double)e.lo;
+      red[w][4] = (double)nbad;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+      double acc = 0.0;
+#pragma unroll
+      for (int i = 0; i < NT / 32; ++i) acc += red[i][threadIdx.x];
+      if (acc != 0.0) atomicAdd(totals + threadIdx.x, acc);
+    }
+  }
+};
+
 struct Shape {
   int nx, ny, nb;
   int64_t ps;  // plane stride in elements

@@ -8,6 +8,10 @@ namespace lbmgnn {
 
 cudaError_t launch_bgk_step(const float* fin, float* fout, const Shape& s, float tau,
                             const float* taus, double* totals, cudaStream_t st);
+// The step restricted to lattice rows row0 .. row1-1 (of the nb*ny rows).
+cudaError_t launch_bgk_step_rows(const float* fin, float* fout, const Shape& s, float tau,
+                                 const float* taus, double* totals, int64_t row0, int64_t row1,
+                                 cudaStream_t st);
 cudaError_t launch_moments(const float* f, const Shape& s, float* rho, float* ux, float* uy,
                            double* totals, cudaStream_t st);
 cudaError_t launch_tgv_init(float* f, const Shape& s, double rho0, double u0, double kx,

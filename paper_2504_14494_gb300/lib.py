@@ -51,6 +51,9 @@ _SIGS = {
     "lbm_step_bgk": (ctypes.c_int, [_VP, _VP, _VP, lbm_shape, ctypes.c_float, _VP, ctypes.c_int,
                                     _VP, _VP]),
     "lbm_moments": (ctypes.c_int, [_VP, lbm_shape, _VP, _VP, _VP, _VP, _VP]),
+    "lbm_host_workspace_bytes": (ctypes.c_size_t, [lbm_shape]),
+    "lbm_step_bgk_host": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, ctypes.c_int,
+                                         _VP, _VP, ctypes.c_size_t, _VP]),
     "lbm_step_channel": (ctypes.c_int, [_VP, _VP, _VP, lbm_shape, ctypes.c_float, _VP,
                                         ctypes.c_float, ctypes.c_int, _VP, _VP]),
     "gnn_param_count": (ctypes.c_size_t, []),
@@ -186,6 +189,20 @@ def lbm_step_channel(f_in, f_out, f_tmp, s, tau, taus=None, force_x=0.0, nsteps=
 def lbm_moments(f, s, rho=None, ux=None, uy=None, totals=None, stream=None):
     check(load().lbm_moments(ptr(f), s, ptr(rho), ptr(ux), ptr(uy), ptr(totals),
                              stream_ptr(stream)), "lbm_moments")
+
+
+def lbm_host_workspace_bytes(s):
+    return load().lbm_host_workspace_bytes(s)
+
+
+def lbm_step_bgk_host(f_in_host, f_out_host, s, tau, taus_host=None, nsteps=1,
+                      totals_host=None, workspace=None, ws_bytes=None, stream=None):
+    """lbm_step_bgk on a state in host memory (CPU tensors, page-locked for
+    overlap); asynchronous on `stream` (see include/lbmgnn.h)."""
+    check(load().lbm_step_bgk_host(ptr(f_in_host), ptr(f_out_host), s, float(tau),
+                                   ptr(taus_host), int(nsteps), ptr(totals_host), ptr(workspace),
+                                   int(nbytes(workspace) if ws_bytes is None else ws_bytes),
+                                   stream_ptr(stream)), "lbm_step_bgk_host")
 
 
 # --- GNN path ------------------------------------------------------------------------

@@ -162,6 +162,34 @@ def test_moments_match_oracle(lbmlib, cuda):
     assert abs(t[3] - t_ref[3]) <= 1e-5 * t_ref[3]
 
 
+def test_totals_accuracy_at_scale(lbmlib, cuda):
+    """The totals are summed as FP32 pairs (error-free TwoSum) and combined in
+    FP64 once per warp: on 3 x 256 x 320 nodes of a perturbed state with a
+    few NaN nodes and one strongly non-equilibrium patch, mass within 1e-13
+    relative of the FP64 sum of the same FP32 values, momentum within
+    1e-13 of sum |f|, energy within 1e-6 relative, NaN nodes counted."""
+    import torch
+    L = lbmlib
+    nb, ny, nx = 3, 256, 320
+    f = _input(nb, ny, nx, seed=11, u0=0.08)
+    f[:, 1, 10:20, 30:50] *= inputs.perturbation(f[:, 1, 10:20, 30:50].shape, 12, 0.9)
+    f[3, 2, 7, 9] = np.nan
+    f[0, 0, 100, 1] = np.inf
+    din, _ = _to_dev(f, cuda)
+    tot = torch.zeros(5, dtype=torch.float64, device=cuda)
+    L.lbm_moments(din, L.shape(nx, ny, nb), None, None, None, tot)
+    t = tot.cpu().numpy()
+    assert L.lbm_get_status() == -7          # LBM_ERR_NONFINITE, cleared by the read
+    t_ref = sum(lbm.totals(f[:, b].astype(np.float64)) for b in range(nb))
+    ok = np.all(np.isfinite(f), axis=0)
+    absum = np.sum(np.abs(np.where(ok[None], f.astype(np.float64), 0.0)))
+    assert t[4] == t_ref[4] == 2
+    assert abs(t[0] - t_ref[0]) <= 1e-13 * t_ref[0], (t[0], t_ref[0])
+    assert abs(t[1] - t_ref[1]) <= 1e-13 * absum, (t[1], t_ref[1])
+    assert abs(t[2] - t_ref[2]) <= 1e-13 * absum, (t[2], t_ref[2])
+    assert abs(t[3] - t_ref[3]) <= 1e-6 * t_ref[3], (t[3], t_ref[3])
+
+
 def test_tgv64_1000_steps_matches_oracle(lbmlib, cuda):
     """The 64^2 TGV workload (tau=0.8, u0=0.01, 1000 steps): velocity field,
     L2 error vs the closed form, energy and mass drift against the FP64 oracle
@@ -257,3 +285,52 @@ def test_bounded_wait_reports_timeout(lbmlib, cuda):
     L.lbm_step_bgk(din, dout, None, L.shape(8, 8), 0.8)
     ref = _oracle_step(f, 0.8)
     assert np.all(np.abs(_from_dev(dout, f.shape, din.numel() // 9) - ref) <= 1e-6 * np.abs(ref))
+
+
+@pytest.mark.parametrize("nb,ny,nx,nsteps,per_lattice", [
+    (1, 64, 96, 1, False), (1, 64, 96, 3, False), (3, 20, 36, 2, True), (2, 5, 30, 1, True),
+    (1, 3, 8, 4, False), (5, 7, 12, 1, False)])
+def test_host_buffer_step_equals_device_step(lbmlib, cuda, nb, ny, nx, nsteps, per_lattice):
+    """lbm_step_bgk_host (state in host memory, chunked copy overlapped with
+    the first step) gives bitwise the state and totals of lbm_step_bgk on the
+    device copy, for pinned and pageable host memory."""
+    import torch
+    L = lbmlib
+    s = L.shape(nx, ny, nb)
+    f = _input(nb, ny, nx, seed=21)
+    taus = np.linspace(0.6, 0.9, nb).astype(np.float32)
+    din, _ = _to_dev(f, cuda)
+    dout, tmp = torch.zeros_like(din), torch.zeros_like(din)
+    tot = torch.zeros(5, dtype=torch.float64, device=cuda)
+    dtaus = torch.from_numpy(taus).to(cuda) if per_lattice else None
+    L.lbm_step_bgk(din, dout, tmp, s, 0.7, taus=dtaus, nsteps=nsteps, totals=tot)
+    want, want_tot = dout.cpu(), tot.cpu()
+    ws = torch.empty(L.lbm_host_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    for pinned in (True, False):
+        h_in = torch.from_numpy(f.reshape(-1).copy())
+        h_out = torch.full_like(h_in, -1.0)
+        h_tot = torch.zeros(5, dtype=torch.float64)
+        h_taus = torch.from_numpy(taus.copy()) if per_lattice else None
+        if pinned:
+            h_in, h_out, h_tot = h_in.pin_memory(), h_out.pin_memory(), h_tot.pin_memory()
+        L.lbm_step_bgk_host(h_in, h_out, s, 0.7, h_taus, nsteps, h_tot, ws)
+        torch.cuda.synchronize()
+        assert torch.equal(h_out, want), pinned
+        assert torch.equal(h_tot, want_tot), pinned
+    assert L.lbm_get_status() == 0
+
+
+def test_host_buffer_step_errors(lbmlib, cuda):
+    import torch
+    L = lbmlib
+    s = L.shape(16, 8)
+    h = torch.zeros(9 * 16 * 8)
+    ws = torch.empty(L.lbm_host_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    small = ws[: ws.numel() - 256]
+    for kwargs, code in [(dict(nsteps=0, workspace=ws), "LBM_ERR_ARG"),
+                         (dict(workspace=small), "LBM_ERR_WORKSPACE"),
+                         (dict(workspace=None), "LBM_ERR_WORKSPACE")]:
+        with pytest.raises(L.LbmError, match=code):
+            L.lbm_step_bgk_host(h, None, s, 0.7, **kwargs)
+    with pytest.raises(L.LbmError, match="LBM_ERR_TAU"):
+        L.lbm_step_bgk_host(h, None, s, 0.5, workspace=ws)
