@@ -200,7 +200,8 @@ LBM_API size_t gnn_packed_bytes(void);
  * 16-byte aligned).  Re-run after every change of the parameters. */
 LBM_API int gnn_pack(const float* params, void* packed, void* stream);
 
-/* Workspace bytes lbm_step_gnn needs for shape s (768 bytes per node). */
+/* Workspace bytes lbm_step_gnn needs for shape s (512 bytes per node: the
+ * node states h and edge terms B = W_b h of the encoder and round 1). */
 LBM_API size_t gnn_step_workspace_bytes(lbm_shape s);
 
 /* One GNN-LBM step (Fig. 1 with 'Use GNN?' = yes): pull-stream f_in with
@@ -344,7 +345,7 @@ LBM_API int64_t lbm_batch_nodes(const lbm_batch_plan* plan);
 /* First node of every input lattice in the packed buffers (host int64[n]). */
 LBM_API int lbm_batch_offsets(const lbm_batch_plan* plan, int64_t* offsets);
 
-/* Workspace bytes lbm_batch_run needs (768 per node of the GNN lattices). */
+/* Workspace bytes lbm_batch_run needs (512 per node of the GNN lattices). */
 LBM_API size_t lbm_batch_workspace_bytes(const lbm_batch_plan* plan);
 
 /* Taylor-Green initial state of every lattice (as lbm_init_tgv); params:
@@ -374,7 +375,7 @@ LBM_API int lbm_autotune_load(const char* path);
  * allocator owns the device memory and forbids further allocations, a
  * real-time loop that may not allocate once running, or a binding with no way
  * to hand out a device buffer.  It computes exactly what lbm_step_gnn
- * computes, taking the 768 bytes of scratch per node from a fixed 24 MiB
+ * computes, taking the 512 bytes of scratch per node from a fixed 16 MiB
  * array inside the library (held on every GPU that loads the library's device
  * code, until the process exits) instead of a workspace argument; it calls no
  * cudaMalloc, cudaFree or allocating library routine.

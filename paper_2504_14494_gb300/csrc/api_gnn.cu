@@ -32,6 +32,9 @@ bool overlap(const void* a, int64_t na, const void* b, int64_t nb) {
 
 int64_t f_bytes(const Shape& s) { return (8 * s.ps + nodes(s)) * (int64_t)sizeof(float); }
 
+// lbm_step_gnn scratch per node: BF16 h0, h1 and FP16 B0, B1 ([N][64] each).
+constexpr int64_t STEP_WS_PER_NODE = 512;
+
 }  // namespace
 
 extern "C" {
@@ -54,7 +57,7 @@ int gnn_pack(const float* params, void* packed, void* stream) {
 size_t gnn_step_workspace_bytes(lbm_shape shape) {
   Shape s;
   if (check_shape_g(shape, &s)) return 0;
-  return (size_t)nodes(s) * 768;
+  return (size_t)nodes(s) * STEP_WS_PER_NODE;
 }
 
 int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape shape, float tau, const float* taus,
@@ -66,30 +69,34 @@ int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape shape, float tau, co
   if (!taus && (!std::isfinite(tau) || !(tau > 0.5f))) return LBM_ERR_TAU;
   if (!aligned(packed, 16)) return LBM_ERR_ARG;
   const int64_t N = nodes(s);
-  if (!workspace || ws_bytes < (size_t)N * 768) return LBM_ERR_WORKSPACE;
+  const int64_t wsb = N * STEP_WS_PER_NODE;
+  if (!workspace || (int64_t)ws_bytes < wsb) return LBM_ERR_WORKSPACE;
   if (!aligned(workspace, 16)) return LBM_ERR_WORKSPACE;
   if (overlap(f_in, f_bytes(s), f_out, f_bytes(s))) return LBM_ERR_ALIAS;
-  if (overlap(workspace, N * 768, f_in, f_bytes(s)) ||
-      overlap(workspace, N * 768, f_out, f_bytes(s)))
+  if (overlap(workspace, wsb, f_in, f_bytes(s)) || overlap(workspace, wsb, f_out, f_bytes(s)))
     return LBM_ERR_ALIAS;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint8_t* pk = static_cast<const uint8_t*>(packed);
   auto* ws = static_cast<__nv_bfloat16*>(workspace);
+  // Between the kernels only h and B = W_b h travel through HBM; each round
+  // recomputes its A = W_a h from h.
   __nv_bfloat16* h0 = ws;
-  __half* ab0 = reinterpret_cast<__half*>(h0 + N * 64);
-  __nv_bfloat16* h1 = reinterpret_cast<__nv_bfloat16*>(ab0 + N * 128);
-  __half* ab1 = reinterpret_cast<__half*>(h1 + N * 64);
-  if (launch_gnn_encode(f_in, true, s, pk, h0, ab0, st) != cudaSuccess) return LBM_ERR_CUDA;
+  __half* b0 = reinterpret_cast<__half*>(h0 + N * 64);
+  __nv_bfloat16* h1 = reinterpret_cast<__nv_bfloat16*>(b0 + N * 64);
+  __half* b1 = reinterpret_cast<__half*>(h1 + N * 64);
+  if (launch_gnn_encode(f_in, true, true, s, pk, h0, b0, st) != cudaSuccess) return LBM_ERR_CUDA;
   RoundLaunch r0;
   r0.h_in = h0;
-  r0.ab_in = ab0;
+  r0.ab_in = b0;
+  r0.a_from_h = true;
   r0.h_out = h1;
-  r0.ab_out = ab1;
+  r0.ab_out = b1;
   r0.round = 0;
   if (launch_gnn_round(0, r0, s, pk, st) != cudaSuccess) return LBM_ERR_CUDA;
   RoundLaunch r1;
   r1.h_in = h1;
-  r1.ab_in = ab1;
+  r1.ab_in = b1;
+  r1.a_from_h = true;
   r1.f_post = f_in;
   r1.f_out = f_out;
   r1.tau = tau;
@@ -130,7 +137,8 @@ int gnn_forward(const float* f_pre, lbm_shape shape, const void* packed, void* s
   __nv_bfloat16* a1 = a0 + N * 64;
   __half* ab0 = reinterpret_cast<__half*>(a1 + N * 64);
   __half* ab1 = ab0 + N * 128;
-  if (launch_gnn_encode(f_pre, false, s, pk, h0, ab0, st) != cudaSuccess) return LBM_ERR_CUDA;
+  if (launch_gnn_encode(f_pre, false, false, s, pk, h0, ab0, st) != cudaSuccess)
+    return LBM_ERR_CUDA;
   RoundLaunch r0;
   r0.h_in = h0;
   r0.ab_in = ab0;

@@ -1,7 +1,7 @@
 // lbm_step_gnn_noalloc: the GNN-LBM step for callers that cannot allocate
 // device memory.
 //
-// lbm_step_gnn needs 768 bytes of scratch per node, which its caller passes
+// lbm_step_gnn needs 512 bytes of scratch per node, which its caller passes
 // in.  Some callers cannot provide that: a host application whose own
 // allocator owns all device memory and forbids other allocations after
 // start-up, a real-time loop that may not allocate once running, or a
@@ -9,7 +9,7 @@
 // point takes its scratch from a fixed array in the library's own device
 // memory instead, so the caller passes only inputs and outputs.
 //
-// The array is a file-scope __device__ variable of NOALLOC_BYTES (24 MiB),
+// The array is a file-scope __device__ variable of NOALLOC_BYTES (16 MiB),
 // enough for NOALLOC_MAX_NODES = 32,768 nodes per call.  Every GPU on which
 // the library's device code is loaded holds it until the process exits.  In
 // host code the array's name is only a host-side stand-in, so its device
@@ -29,7 +29,7 @@
 namespace {
 
 constexpr int64_t NOALLOC_MAX_NODES = LBM_STEP_GNN_NOALLOC_MAX_NODES;
-constexpr size_t NOALLOC_BYTES = (size_t)NOALLOC_MAX_NODES * 768;
+constexpr size_t NOALLOC_BYTES = (size_t)NOALLOC_MAX_NODES * 512;
 
 static __device__ __align__(256) unsigned char g_gnn_step_scratch[NOALLOC_BYTES];
 

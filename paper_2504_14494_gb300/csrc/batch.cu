@@ -181,7 +181,7 @@ void plan_release(lbm_batch_plan* p) {
   delete p;
 }
 
-int64_t gnn_ws_bytes(const lbm_batch_plan* p) { return p->gnn_nodes * 768; }
+int64_t gnn_ws_bytes(const lbm_batch_plan* p) { return p->gnn_nodes * 512; }
 
 // One step of every lattice: src -> dst.
 cudaError_t plan_step(lbm_batch_plan* p, const float* src, float* dst, const uint8_t* packed,

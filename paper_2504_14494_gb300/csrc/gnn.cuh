@@ -161,6 +161,9 @@ __device__ __forceinline__ void st_h32(__half* p, const float* v) {
 __device__ __forceinline__ __half2 u32_as_h2(uint32_t u) {
   return *reinterpret_cast<const __half2*>(&u);
 }
+__device__ __forceinline__ uint32_t h2_as_u32(__half2 h) {
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
 __device__ __forceinline__ __half2 tanh_h2(__half2 x) {
   uint32_t y;
   asm("tanh.approx.f16x2 %0, %1;" : "=r"(y) : "r"(*reinterpret_cast<const uint32_t*>(&x)));
@@ -300,6 +303,15 @@ __device__ __forceinline__ void st_row(uint8_t* blk, int row, int f0, const floa
   for (int c = 0; c < NF / 8; ++c) {
     const int chunk = (f0 >> 3) + c;
     *reinterpret_cast<uint4*>(blk + row * 128 + ((chunk ^ (row & 7)) << 4)) = pack_bf16x8(v + 8 * c);
+  }
+}
+template <int NF>
+__device__ __forceinline__ void ld_row(const uint8_t* blk, int row, int f0, float* v) {
+#pragma unroll
+  for (int c = 0; c < NF / 8; ++c) {
+    const int chunk = (f0 >> 3) + c;
+    unpack_bf16x8(*reinterpret_cast<const uint4*>(blk + row * 128 + ((chunk ^ (row & 7)) << 4)),
+                  v + 8 * c);
   }
 }
 template <int NF>
@@ -457,6 +469,74 @@ __device__ __forceinline__ bool tc_run(TcShared* sh, TcCtx& tc, unsigned* stw, I
   tc_fence_after();
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) raise_status(stw, ST_TIMEOUT);
+    return false;
+  }
+  return true;
+}
+
+// ---- thread groups sharing a CTA --------------------------------------------
+// A CTA may run NG independent groups of GT threads, each with its own tile,
+// shared-memory operands, mbarrier and tensor-memory columns, synchronised by
+// named barrier 1 + g (barrier 0 stays __syncthreads).
+__device__ __forceinline__ void group_sync(int g, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(nthreads) : "memory");
+}
+// OR of `v` over the group (also a group barrier).
+__device__ __forceinline__ bool group_any(int g, int nthreads, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(1 + g), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
+// Prologue of a CTA of `ng` groups: one mbarrier per group, cols_per_group
+// tensor-memory columns per group (allocated together by warp 0).
+__device__ __forceinline__ void tc_setup_groups(TcShared* sh, TcCtx& tc, int ng, int g,
+                                                uint32_t cols_per_group) {
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < ng; ++i) {
+      mbar_init(&sh[i].bar, 1);
+      sh[i].abort = 0;
+    }
+  }
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(&sh[0].tmem, cols_per_group * ng);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  tc.tmem = sh[0].tmem + (uint32_t)g * cols_per_group;
+  tc.bar = &sh[g].bar;
+  tc.phase = 0;
+}
+__device__ __forceinline__ void tc_teardown_groups(TcShared* sh, int ng,
+                                                   uint32_t cols_per_group) {
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(sh[0].tmem, cols_per_group * ng);
+}
+// tc_run for group g of nthreads threads (its first thread issues).
+template <typename Issue>
+__device__ __forceinline__ bool tc_run_group(TcCtx& tc, unsigned* stw, int g, int nthreads,
+                                             Issue issue) {
+  fence_async_smem();
+  tc_fence_before();
+  group_sync(g, nthreads);
+  const bool issuer = (int)threadIdx.x == g * nthreads;
+  if (issuer) {
+    tc_fence_after();
+    issue();
+    umma_commit(tc.bar);
+  }
+  const bool ok = mbar_wait(tc.bar, tc.phase);
+  tc.phase ^= 1u;
+  tc_fence_after();
+  if (group_any(g, nthreads, !ok)) {
+    if (issuer) raise_status(stw, ST_TIMEOUT);
     return false;
   }
   return true;

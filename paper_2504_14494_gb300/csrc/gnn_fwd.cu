@@ -10,11 +10,17 @@
 // Dense layers are tcgen05 MMAs (M = 128 nodes, BF16 operands in 128-byte
 // swizzled shared memory, FP32 accumulators in tensor memory).  Elementwise
 // work (12->64 input layer, GELUs, the 8 messages per node) runs on the CUDA
-// cores.  Between the kernels, h (BF16 [N][64]) and the per-node edge terms
-// A = W_a h, B = W_b h (BF16 [N][128]) live in HBM; the 8 neighbour reads of B
-// are served mostly from L2.
+// cores.  Between the kernels, h (BF16 [N][64]) and the per-node edge term
+// B = W_b h (FP16 [N][64]) live in HBM; the 8 neighbour reads of B are served
+// mostly from L2.  The node's own term A = W_a h is recomputed from h by the
+// consuming round kernel (one 128x64x64 MMA per tile) instead of being stored.
+// The training forward (gnn_forward) stores A | B ([N][128]) for the backward.
 #include "gnn.cuh"
 #include "gnn_launch.h"
+
+#ifndef LBM_PREFETCH
+#define LBM_PREFETCH 1  // load the next tile's inputs while computing this one
+#endif
 
 namespace lbmgnn {
 
@@ -96,7 +102,7 @@ constexpr uint32_t W1X = 0, W2 = 8192, WAB = 16384, X1 = 32768, X = 49152, B1 = 
                    B2 = 65792, NORM = 66048, SH = 66176, BYTES = 66304;
 }
 
-template <bool PULL, class Geo>
+template <bool PULL, bool BONLY, class Geo>
 __global__ void __launch_bounds__(256, 3) gnn_encode_kernel(
     const float* __restrict__ f, Geo geo, const uint8_t* __restrict__ packed,
     __nv_bfloat16* __restrict__ h0_out, __half* __restrict__ ab_out, unsigned* stw) {
@@ -126,20 +132,33 @@ __global__ void __launch_bounds__(256, 3) gnn_encode_kernel(
   const int64_t ntiles = (N + TILE - 1) / TILE;
   const bool relu = variant_of(nrm) & VAR_MLP_ONLY;
 
+  // populations of node `t * TILE + node` of tile t (streamed when PULL)
+  auto load_f = [&](int64_t t, float (&v)[Q]) {
+    const int64_t m = t * TILE + node;
+    const int64_t mm = m < N ? m : N - 1;
+    if (PULL) {
+      const GeoPos p = geo.pos(base + mm);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) v[q] = __ldg(f + q * ps + geo_nbr(p, -ex(q), -ey(q)));
+    } else {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) v[q] = __ldg(f + q * ps + base + mm);
+    }
+  };
+  float fnext[Q];
+  if (blockIdx.x < ntiles) load_f(blockIdx.x, fnext);
+
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t n = tile * TILE + node;
     const bool on = n < N;
-    const int64_t nn = on ? n : N - 1;
     {
       float fv[Q];
-      if (PULL) {
-        const GeoPos p = geo.pos(base + nn);
 #pragma unroll
-        for (int q = 0; q < Q; ++q) fv[q] = __ldg(f + q * ps + geo_nbr(p, -ex(q), -ey(q)));
-      } else {
-#pragma unroll
-        for (int q = 0; q < Q; ++q) fv[q] = __ldg(f + q * ps + base + nn);
-      }
+      for (int q = 0; q < Q; ++q) fv[q] = fnext[q];
+#if LBM_PREFETCH
+      // the next tile's loads are in flight while this tile is computed
+      if (tile + gridDim.x < ntiles) load_f(tile + gridDim.x, fnext);
+#endif
       const Moments m = moments9(fv);
       float xh[16];
 #pragma unroll
@@ -178,14 +197,21 @@ __global__ void __launch_bounds__(256, 3) gnn_encode_kernel(
     for (int c = 0; c < 32; ++c) g[c] = act(g[c] + b2[f0 + c], relu);
     if (on && h0_out) st_pb32(h0_out, N, n, f0, g);
     st_row32(X, node, f0, g);  // the MMA that read X has completed
+    // A | B = h0 [W_a; W_b]^T ([N][128]), or B alone ([N][64]) when BONLY
     if (!tc_run(sh, tc, stw, [&] {
-          umma_128xN(tc.tmem, smem_u32(X), 0, smem_u32(sm + enc::WAB), 0, 1, 128, false);
+          umma_128xN(tc.tmem, smem_u32(X), 0, smem_u32(sm + enc::WAB) + (BONLY ? 8192 : 0), 0, 1,
+                     BONLY ? 64 : 128, false);
         }))
       break;
     tmem_ld32(lb + f0, g);
     if (on) st_ph32(ab_out, N, n, f0, g);
-    tmem_ld32(lb + HID + f0, g);
-    if (on) st_ph32(ab_out, N, n, HID + f0, g);
+    if (!BONLY) {
+      tmem_ld32(lb + HID + f0, g);
+      if (on) st_ph32(ab_out, N, n, HID + f0, g);
+    }
+#if !LBM_PREFETCH
+    if (tile + gridDim.x < ntiles) load_f(tile + gridDim.x, fnext);
+#endif
     tc_fence_before();
     __syncthreads();
   }
@@ -196,17 +222,24 @@ __global__ void __launch_bounds__(256, 3) gnn_encode_kernel(
 // Message-passing round r.  MODE 0: inner round -> h_out, AB of round r+1.
 // MODE 1: last round + head + Eq. 3 collision -> f_out (pull from f_post).
 // MODE 2: last round + head -> y [10][N] (FP32) and h_out = h2.
-namespace rnd {
-constexpr uint32_t HA = 0, WN = 32768, WX = 49152, CK = 65536, BN = 67584, BH = 67840,
-                   NORM = 67904, CKH = 68032, SH = 69056, BYTES = 69120;
-}
+// Shared-memory layout of a CTA of NG groups: per group g its node-state tile
+// H (16 KB) and aggregated-message tile Ag (16 KB) at g * 32 KB, then the
+// weights shared by the groups.  With A recomputed from h (AH), WX holds only
+// the next round's W_b (8 KB) or the head, and this round's W_a sits at WA.
+template <int NG>
+struct RndL {
+  static constexpr uint32_t WN = NG * 32768, WX = WN + 16384, WA = WX + 8192, CK = WX + 16384,
+                            BN = CK + 2048, BH = BN + 256, NORM = BH + 64, CKH = NORM + 128,
+                            SH = CKH + 1024, BYTES = SH + 64;
+};
 
 struct RoundArgs {
   const __nv_bfloat16* h_in;   // [N][64]
-  const __half* ab_in;         // [N][128] FP16: A = W_a h, B = W_b h of this round
+  const __half* ab_in;         // [N][128] FP16: A = W_a h, B = W_b h of this round, or
+                               // [N][64] B alone (A recomputed from h_in)
   __nv_bfloat16* h_out;        // [N][64] (MODE 0, 2) or NULL
   __nv_bfloat16* a_out;        // [N][64] aggregated messages (saved for training) or NULL
-  __half* ab_out;              // [N][128] next round's A, B (MODE 0), FP16
+  __half* ab_out;              // next round's A | B or B alone (MODE 0), FP16
   float* y_out;                // [10][N] (MODE 2)
   const float* f_post;         // stored state to pull from (MODE 1)
   float* f_out;                // MODE 1
@@ -219,74 +252,129 @@ struct RoundArgs {
 #define LBM_ROUND_CTAS 2
 #endif
 #ifndef LBM_ROUND_TPN
-#define LBM_ROUND_TPN 2  // threads per node of the round kernel (2 or 4)
+#define LBM_ROUND_TPN 2  // threads per node of the round kernel (1, 2 or 4)
+#endif
+#ifndef LBM_ROUND_GROUPS
+#define LBM_ROUND_GROUPS 1  // independent tile groups per CTA
 #endif
 #ifndef LBM_NBR_GROUP
 #define LBM_NBR_GROUP 4  // neighbour loads in flight per thread and chunk
 #endif
-// TPN threads per node (2 or 4), each owning FPT = 64 / TPN features; warp w
-// reads tensor-memory lanes 32 (w % 4).. and columns of its feature slice.
-template <int MODE, int TPN, class Geo>
-__global__ void __launch_bounds__(128 * TPN, LBM_ROUND_CTAS) gnn_round_kernel(
+// A CTA runs NG groups of 128 TPN threads; each group works through its own
+// sequence of tiles with its own operands, mbarrier and 128 tensor-memory
+// columns.  In a group, TPN threads per node each own FPT = 64 / TPN
+// features; warp w reads tensor-memory lanes 32 (w % 4)..  AH: the edge
+// terms come as B alone and A = W_a h is computed here from h.
+template <int MODE, int TPN, int NG, bool AH, class Geo>
+__global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kernel(
     RoundArgs ra, Geo geo, const uint8_t* __restrict__ packed, unsigned* stw) {
   constexpr int FPT = HID / TPN;
+  constexpr int SL = FPT < 32 ? FPT : 32;  // feature slice of the epilogues
+  constexpr int GT = 128 * TPN;            // threads per group
+  using L = RndL<NG>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  TcShared* sh = reinterpret_cast<TcShared*>(sm + rnd::SH);
+  TcShared* sh = reinterpret_cast<TcShared*>(sm + L::SH);
   const uint8_t* kr = packed + K::round_base(ra.round);
-  copy_g2s(sm + rnd::WN, kr + K::WN, 16384);
-  if (MODE == 0)
-    copy_g2s(sm + rnd::WX, packed + K::round_base(ra.round + 1) + K::WAB, 16384);
+  copy_g2s(sm + L::WN, kr + K::WN, 16384);
+  if (AH) copy_g2s(sm + L::WA, kr + K::WAB, 8192);
+  if (MODE == 0 && AH)  // rows 64..127 of the next round's W_ab block: W_b
+    copy_g2s(sm + L::WX, packed + K::round_base(ra.round + 1) + K::WAB + 8192, 8192);
+  else if (MODE == 0)
+    copy_g2s(sm + L::WX, packed + K::round_base(ra.round + 1) + K::WAB, 16384);
   else
-    copy_g2s(sm + rnd::WX, packed + K::WH, 2048);
-  copy_g2s(sm + rnd::CK, kr + K::CK, 2048);
-  copy_g2s(sm + rnd::BN, kr + K::BN, 256);
-  copy_g2s(sm + rnd::BH, packed + K::BH, 64);
-  copy_g2s(sm + rnd::NORM, packed + K::NORM, 128);
+    copy_g2s(sm + L::WX, packed + K::WH, 2048);
+  copy_g2s(sm + L::CK, kr + K::CK, 2048);
+  copy_g2s(sm + L::BN, kr + K::BN, 256);
+  copy_g2s(sm + L::BH, packed + K::BH, 64);
+  copy_g2s(sm + L::NORM, packed + K::NORM, 128);
   __syncthreads();
   {  // c_k as FP16 pairs
-    const float* ckf = reinterpret_cast<const float*>(sm + rnd::CK);
-    __half2* ckw = reinterpret_cast<__half2*>(sm + rnd::CKH);
+    const float* ckf = reinterpret_cast<const float*>(sm + L::CK);
+    __half2* ckw = reinterpret_cast<__half2*>(sm + L::CKH);
     for (int i = threadIdx.x; i < 8 * HID / 2; i += blockDim.x)
       ckw[i] = __floats2half2_rn(ckf[2 * i], ckf[2 * i + 1]);
   }
+  const int grp = threadIdx.x / GT, tg = threadIdx.x % GT;
   TcCtx tc;
-  tc_setup(sh, tc, 128);
-  const __half2* ckh = reinterpret_cast<const __half2*>(sm + rnd::CKH);
-  const float* bn = reinterpret_cast<const float*>(sm + rnd::BN);
-  const float* bh = reinterpret_cast<const float*>(sm + rnd::BH);
-  const float* nrm = reinterpret_cast<const float*>(sm + rnd::NORM);
-  uint8_t* H = sm + rnd::HA;
-  uint8_t* Ag = sm + rnd::HA + 16384;
-  const int node = threadIdx.x & 127, part = threadIdx.x >> 7, f0 = part * FPT;
+  tc_setup_groups(sh, tc, NG, grp, 128);
+  const __half2* ckh = reinterpret_cast<const __half2*>(sm + L::CKH);
+  const float* bn = reinterpret_cast<const float*>(sm + L::BN);
+  const float* bh = reinterpret_cast<const float*>(sm + L::BH);
+  const float* nrm = reinterpret_cast<const float*>(sm + L::NORM);
+  uint8_t* H = sm + grp * 32768;
+  uint8_t* Ag = H + 16384;
+  const int node = tg & 127, part = tg >> 7, f0 = part * FPT;
   const uint32_t lb = lane_base(tc.tmem);
   const int64_t N = geo.count();
   const int64_t base = geo.base(), ps = geo.ps();
   const int64_t ntiles = (N + TILE - 1) / TILE;
+  const int64_t first = (int64_t)blockIdx.x * NG + grp, stride = (int64_t)gridDim.x * NG;
   const int variant = variant_of(nrm);
   const bool mlp_only = variant & VAR_MLP_ONLY;
+  auto run = [&](auto issue) { return tc_run_group(tc, stw, grp, GT, issue); };
 
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  // raw BF16 h (features f0.. of node `t * TILE + node`) of tile t
+  uint4 hnext[FPT / 8];
+  auto load_h = [&](int64_t t) {
+    const int64_t m = t * TILE + node;
+    const int64_t mm = m < N ? m : N - 1;
+#pragma unroll
+    for (int c = 0; c < FPT / 8; ++c) hnext[c] = __ldg(chunk8(ra.h_in, N, mm, f0 + 8 * c));
+  };
+  if (AH && first < ntiles) load_h(first);
+
+  for (int64_t tile = first; tile < ntiles; tile += stride) {
     const int64_t n = tile * TILE + node;
     const bool on = n < N;
     const int64_t nn = on ? n : N - 1;
     const GeoPos p = geo.pos(base + nn);
+    if constexpr (AH) {  // h -> shared memory, A = h W_a^T -> tensor memory columns 0..63
+#pragma unroll
+      for (int s0 = 0; s0 < FPT; s0 += SL) {
+        float h[SL];
+#pragma unroll
+        for (int c = 0; c < SL / 8; ++c) unpack_bf16x8(hnext[s0 / 8 + c], h + 8 * c);
+        st_row<SL>(H, node, f0 + s0, h);
+      }
+      if (LBM_PREFETCH && tile + stride < ntiles) load_h(tile + stride);
+      if (!mlp_only && !run([&] {
+            umma_128xN(tc.tmem, smem_u32(H), 0, smem_u32(sm + L::WA), 0, 1, 64, false);
+          }))
+        break;
+    } else {  // h -> shared memory
+#pragma unroll
+      for (int s0 = 0; s0 < FPT; s0 += SL) {
+        float h[SL];
+        ld_pb<SL>(ra.h_in, N, nn, f0 + s0, h);
+        st_row<SL>(H, node, f0 + s0, h);
+      }
+    }
     if (mlp_only) {  // no message passing: a = 0, h unchanged
       if (on && ra.a_out) {
-        const float zero[FPT] = {};
-        st_pb<FPT>(ra.a_out, N, n, f0, zero);
+        const float zero[SL] = {};
+#pragma unroll
+        for (int s0 = 0; s0 < FPT; s0 += SL) st_pb<SL>(ra.a_out, N, n, f0 + s0, zero);
       }
     } else {
     // messages m_ik = GELU(A_i + B_j + c_k), summed over the 8 neighbours, in
-    // packed FP16 pairs; per 16-feature chunk the 8 neighbour loads are
-    // issued together.
+    // packed FP16 pairs; per 16-feature chunk the neighbour loads are issued
+    // LBM_NBR_GROUP at a time.
 #pragma unroll
     for (int sc = 0; sc < FPT / 16; ++sc) {
       const int c0 = f0 + 16 * sc;
-      uint4 araw[2];
-      araw[0] = __ldg(chunk8(ra.ab_in, N, nn, c0));
-      araw[1] = __ldg(chunk8(ra.ab_in, N, nn, c0 + 8));
-      const uint32_t* aw = reinterpret_cast<const uint32_t*>(araw);
+      uint32_t aw[8];
+      if constexpr (AH) {
+        float av[16];
+        tmem_ld16(lb + c0, av);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) aw[c] = h2_as_u32(__floats2half2_rn(av[2 * c], av[2 * c + 1]));
+      } else {
+        const uint4 a0 = __ldg(chunk8(ra.ab_in, N, nn, c0));
+        const uint4 a1 = __ldg(chunk8(ra.ab_in, N, nn, c0 + 8));
+        aw[0] = a0.x, aw[1] = a0.y, aw[2] = a0.z, aw[3] = a0.w;
+        aw[4] = a1.x, aw[5] = a1.y, aw[6] = a1.z, aw[7] = a1.w;
+      }
       // Each message is accumulated as z + z tanh(u) (= 2 GELU(z)); the 1/2 is
       // applied once to the sum.
       __half2 acc[8];
@@ -298,8 +386,9 @@ __global__ void __launch_bounds__(128 * TPN, LBM_ROUND_CTAS) gnn_round_kernel(
 #pragma unroll
         for (int k = 0; k < LBM_NBR_GROUP; ++k) {
           const int64_t j = geo_nbr(p, ex(g + k + 1), ey(g + k + 1)) - base;
-          braw[k][0] = __ldg(chunk8(ra.ab_in, N, j, HID + c0));
-          braw[k][1] = __ldg(chunk8(ra.ab_in, N, j, HID + c0 + 8));
+          constexpr int BOFF = AH ? 0 : HID;  // B's first feature in ab_in
+          braw[k][0] = __ldg(chunk8(ra.ab_in, N, j, BOFF + c0));
+          braw[k][1] = __ldg(chunk8(ra.ab_in, N, j, BOFF + c0 + 8));
         }
 #pragma unroll
         for (int k = 0; k < LBM_NBR_GROUP; ++k) {
@@ -331,36 +420,44 @@ __global__ void __launch_bounds__(128 * TPN, LBM_ROUND_CTAS) gnn_round_kernel(
         *chunk8w(ra.a_out, N, n, c0 + 8) = pack_bf16x8(av + 8);
       }
     }
+    // node update: h <- h + GELU(W_n [h; a] + b_n)
+    if (!run([&] {
+          umma_128xN(tc.tmem, smem_u32(H), 16384, smem_u32(sm + L::WN), 8192, 2, 64, false);
+        }))
+      break;
     }
-    float h[FPT];
-    ld_pb<FPT>(ra.h_in, N, nn, f0, h);
-    if (!mlp_only) {
-      st_row<FPT>(H, node, f0, h);
-      // node update: h <- h + GELU(W_n [h; a] + b_n)
-      if (!tc_run(sh, tc, stw, [&] {
-            umma_128xN(tc.tmem, smem_u32(H), 16384, smem_u32(sm + rnd::WN), 8192, 2, 64, false);
-          }))
-        break;
-      float z[FPT];
-      tmem_ld<FPT>(lb + f0, z);
+    // new h (the node-update MMA has completed: H may be overwritten)
 #pragma unroll
-      for (int c = 0; c < FPT; ++c) h[c] += gelu(z[c] + bn[f0 + c]);
+    for (int s0 = 0; s0 < FPT; s0 += SL) {
+      float h[SL];
+      ld_row<SL>(H, node, f0 + s0, h);  // h as stored (BF16)
+      if (!mlp_only) {
+        float z[SL];
+        tmem_ld<SL>(lb + f0 + s0, z);
+#pragma unroll
+        for (int c = 0; c < SL; ++c) h[c] += gelu(z[c] + bn[f0 + s0 + c]);
+      }
+      if (on && ra.h_out) st_pb<SL>(ra.h_out, N, n, f0 + s0, h);
+      st_row<SL>(H, node, f0 + s0, h);
     }
-    if (on && ra.h_out) st_pb<FPT>(ra.h_out, N, n, f0, h);
-    st_row<FPT>(H, node, f0, h);
-    if (MODE == 0) {
-      if (!tc_run(sh, tc, stw, [&] {
-            umma_128xN(tc.tmem, smem_u32(H), 0, smem_u32(sm + rnd::WX), 0, 1, 128, false);
+    if (MODE == 0) {  // next round's A | B, or B alone
+      if (!run([&] {
+            umma_128xN(tc.tmem, smem_u32(H), 0, smem_u32(sm + L::WX), 0, 1, AH ? 64 : 128, false);
           }))
         break;
-      float a[FPT];
-      tmem_ld<FPT>(lb + f0, a);
-      if (on) st_ph<FPT>(ra.ab_out, N, n, f0, a);
-      tmem_ld<FPT>(lb + HID + f0, a);
-      if (on) st_ph<FPT>(ra.ab_out, N, n, HID + f0, a);
+#pragma unroll
+      for (int s0 = 0; s0 < FPT; s0 += SL) {
+        float a[SL];
+        tmem_ld<SL>(lb + f0 + s0, a);
+        if (on) st_ph<SL>(ra.ab_out, N, n, f0 + s0, a);
+        if constexpr (!AH) {
+          tmem_ld<SL>(lb + HID + f0 + s0, a);
+          if (on) st_ph<SL>(ra.ab_out, N, n, HID + f0 + s0, a);
+        }
+      }
     } else {
-      if (!tc_run(sh, tc, stw, [&] {
-            umma_128xN(tc.tmem, smem_u32(H), 0, smem_u32(sm + rnd::WX), 0, 1, 16, false);
+      if (!run([&] {
+            umma_128xN(tc.tmem, smem_u32(H), 0, smem_u32(sm + L::WX), 0, 1, 16, false);
           }))
         break;
       if (part == 0) {
@@ -399,10 +496,11 @@ __global__ void __launch_bounds__(128 * TPN, LBM_ROUND_CTAS) gnn_round_kernel(
         }
       }
     }
+    if (AH && !LBM_PREFETCH && tile + stride < ntiles) load_h(tile + stride);
     tc_fence_before();
-    __syncthreads();
+    group_sync(grp, GT);
   }
-  tc_teardown(sh, tc, 128);
+  tc_teardown_groups(sh, NG, 128);
 }
 
 // ---------------------------------------------------------------------------
@@ -413,22 +511,40 @@ cudaError_t launch_gnn_pack(const float* params, uint8_t* packed, cudaStream_t s
 }
 
 
+template <bool PULL, bool BONLY, class Geo>
+static cudaError_t encode_t(const float* f, const Geo& geo, unsigned grid, uint32_t bytes,
+                           const uint8_t* packed, __nv_bfloat16* h0, __half* ab, unsigned* stw,
+                           cudaStream_t st) {
+  cudaError_t e;
+  if ((e = set_smem(gnn_encode_kernel<PULL, BONLY, Geo>, bytes)) != cudaSuccess) return e;
+  gnn_encode_kernel<PULL, BONLY, Geo><<<grid, 256, bytes, st>>>(f, geo, packed, h0, ab, stw);
+  return cudaGetLastError();
+}
+
+// pull: f is a stored state (stream first); b_only: write B alone ([N][64]).
 template <class Geo>
-static cudaError_t encode_any(const float* f, bool pull, const Geo& geo, int64_t N,
+static cudaError_t encode_any(const float* f, bool pull, bool b_only, const Geo& geo, int64_t N,
                               const uint8_t* packed, __nv_bfloat16* h0, __half* ab,
                               cudaStream_t st, int per_sm = 2) {
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
   const uint32_t bytes = enc::BYTES + 1024;
   const unsigned grid = grid_for(N, per_sm + (per_sm >= 2 ? 1 : 0));
+  if (pull)
+    return b_only ? encode_t<true, true>(f, geo, grid, bytes, packed, h0, ab, stw, st)
+                  : encode_t<true, false>(f, geo, grid, bytes, packed, h0, ab, stw, st);
+  return b_only ? encode_t<false, true>(f, geo, grid, bytes, packed, h0, ab, stw, st)
+                : encode_t<false, false>(f, geo, grid, bytes, packed, h0, ab, stw, st);
+}
+
+template <int MODE, bool AH, class Geo>
+static cudaError_t round_t(const RoundArgs& ra, const Geo& geo, unsigned grid,
+                           const uint8_t* packed, unsigned* stw, cudaStream_t st) {
+  constexpr int T = LBM_ROUND_TPN, G = LBM_ROUND_GROUPS;
+  const uint32_t bytes = RndL<G>::BYTES + 1024;
   cudaError_t e;
-  if (pull) {
-    if ((e = set_smem(gnn_encode_kernel<true, Geo>, bytes)) != cudaSuccess) return e;
-    gnn_encode_kernel<true, Geo><<<grid, 256, bytes, st>>>(f, geo, packed, h0, ab, stw);
-  } else {
-    if ((e = set_smem(gnn_encode_kernel<false, Geo>, bytes)) != cudaSuccess) return e;
-    gnn_encode_kernel<false, Geo><<<grid, 256, bytes, st>>>(f, geo, packed, h0, ab, stw);
-  }
+  if ((e = set_smem(gnn_round_kernel<MODE, T, G, AH, Geo>, bytes)) != cudaSuccess) return e;
+  gnn_round_kernel<MODE, T, G, AH, Geo><<<grid, 128 * T * G, bytes, st>>>(ra, geo, packed, stw);
   return cudaGetLastError();
 }
 
@@ -437,32 +553,30 @@ static cudaError_t round_any(int mode, const RoundLaunch& rl, const Geo& geo, in
                              const uint8_t* packed, cudaStream_t st, int per_sm = 2) {
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
-  const uint32_t bytes = rnd::BYTES + 1024;
-  const unsigned grid = grid_for(N, per_sm >= 2 ? LBM_ROUND_CTAS : per_sm);
+  // persistent grid: at most per_sm CTAs per SM, each running LBM_ROUND_GROUPS tiles at a time
+  const int64_t cta_tiles = (N + (int64_t)TILE * LBM_ROUND_GROUPS - 1) / ((int64_t)TILE * LBM_ROUND_GROUPS);
+  const unsigned grid = grid_for(cta_tiles * TILE, per_sm >= 2 ? LBM_ROUND_CTAS : per_sm);
   RoundArgs ra{rl.h_in, rl.ab_in, rl.h_out, rl.a_out, rl.ab_out, rl.y_out, rl.f_post, rl.f_out,
                rl.tau, rl.taus, rl.round};
-  cudaError_t e;
-  constexpr int T = LBM_ROUND_TPN;
-  switch (mode) {
-    case 0:
-      if ((e = set_smem(gnn_round_kernel<0, T, Geo>, bytes)) != cudaSuccess) return e;
-      gnn_round_kernel<0, T, Geo><<<grid, 128 * T, bytes, st>>>(ra, geo, packed, stw);
-      break;
-    case 1:
-      if ((e = set_smem(gnn_round_kernel<1, T, Geo>, bytes)) != cudaSuccess) return e;
-      gnn_round_kernel<1, T, Geo><<<grid, 128 * T, bytes, st>>>(ra, geo, packed, stw);
-      break;
-    default:
-      if ((e = set_smem(gnn_round_kernel<2, T, Geo>, bytes)) != cudaSuccess) return e;
-      gnn_round_kernel<2, T, Geo><<<grid, 128 * T, bytes, st>>>(ra, geo, packed, stw);
-      break;
+  if (rl.a_from_h) {
+    switch (mode) {
+      case 0: return round_t<0, true>(ra, geo, grid, packed, stw, st);
+      case 1: return round_t<1, true>(ra, geo, grid, packed, stw, st);
+      default: return round_t<2, true>(ra, geo, grid, packed, stw, st);
+    }
   }
-  return cudaGetLastError();
+  switch (mode) {
+    case 0: return round_t<0, false>(ra, geo, grid, packed, stw, st);
+    case 1: return round_t<1, false>(ra, geo, grid, packed, stw, st);
+    default: return round_t<2, false>(ra, geo, grid, packed, stw, st);
+  }
 }
 
-cudaError_t launch_gnn_encode(const float* f, bool pull, const Shape& s, const uint8_t* packed,
-                              __nv_bfloat16* h0, __half* ab, cudaStream_t st) {
-  return encode_any(f, pull, GeoStack{s}, (int64_t)s.nb * s.ny * s.nx, packed, h0, ab, st);
+cudaError_t launch_gnn_encode(const float* f, bool pull, bool b_only, const Shape& s,
+                              const uint8_t* packed, __nv_bfloat16* h0, __half* ab,
+                              cudaStream_t st) {
+  return encode_any(f, pull, b_only, GeoStack{s}, (int64_t)s.nb * s.ny * s.nx, packed, h0, ab,
+                    st);
 }
 
 cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
@@ -477,22 +591,24 @@ cudaError_t launch_gnn_step_table(const float* f_in, float* f_out, const LatDesc
   if (count <= 0) return cudaSuccess;
   const GeoTable geo{lat, first, n, base, count, ps};
   __nv_bfloat16* h0 = ws;
-  __half* ab0 = reinterpret_cast<__half*>(h0 + count * 64);
-  __nv_bfloat16* h1 = reinterpret_cast<__nv_bfloat16*>(ab0 + count * 128);
-  __half* ab1 = reinterpret_cast<__half*>(h1 + count * 64);
+  __half* b0 = reinterpret_cast<__half*>(h0 + count * 64);
+  __nv_bfloat16* h1 = reinterpret_cast<__nv_bfloat16*>(b0 + count * 64);
+  __half* b1 = reinterpret_cast<__half*>(h1 + count * 64);
   cudaError_t e;
-  if ((e = encode_any(f_in, true, geo, count, packed, h0, ab0, st, per_sm)) != cudaSuccess)
+  if ((e = encode_any(f_in, true, true, geo, count, packed, h0, b0, st, per_sm)) != cudaSuccess)
     return e;
   RoundLaunch r0;
   r0.h_in = h0;
-  r0.ab_in = ab0;
+  r0.ab_in = b0;
+  r0.a_from_h = true;
   r0.h_out = h1;
-  r0.ab_out = ab1;
+  r0.ab_out = b1;
   r0.round = 0;
   if ((e = round_any(0, r0, geo, count, packed, st, per_sm)) != cudaSuccess) return e;
   RoundLaunch r1;
   r1.h_in = h1;
-  r1.ab_in = ab1;
+  r1.ab_in = b1;
+  r1.a_from_h = true;
   r1.f_post = f_in;
   r1.f_out = f_out;
   r1.round = 1;

@@ -10,7 +10,8 @@ namespace lbmgnn {
 
 struct RoundLaunch {
   const __nv_bfloat16* h_in = nullptr;
-  const __half* ab_in = nullptr;     // A | B, FP16
+  const __half* ab_in = nullptr;     // A | B ([N][128]) or B alone ([N][64]), FP16
+  bool a_from_h = false;             // ab_in/ab_out hold B alone; A = W_a h recomputed
   __nv_bfloat16* h_out = nullptr;
   __nv_bfloat16* a_out = nullptr;
   __half* ab_out = nullptr;
@@ -23,8 +24,10 @@ struct RoundLaunch {
 };
 
 cudaError_t launch_gnn_pack(const float* params, uint8_t* packed, cudaStream_t st);
-cudaError_t launch_gnn_encode(const float* f, bool pull, const Shape& s, const uint8_t* packed,
-                              __nv_bfloat16* h0, __half* ab, cudaStream_t st);
+// pull: f is a stored state (streamed first); b_only: ab receives B alone.
+cudaError_t launch_gnn_encode(const float* f, bool pull, bool b_only, const Shape& s,
+                              const uint8_t* packed, __nv_bfloat16* h0, __half* ab,
+                              cudaStream_t st);
 // mode 0: inner round; 1: last round + head + Eq. 3 collision; 2: last round + head -> y
 cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
                              const uint8_t* packed, cudaStream_t st);
@@ -32,7 +35,7 @@ cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
 struct LatDesc;
 // GNN-LBM step (encoder, 2 rounds, head + Eq. 3) on the lattices first ..
 // first+n-1 of a device descriptor table, whose nodes are [base, base+count)
-// of population buffers with plane stride ps; ws: count * 768 bytes;
+// of population buffers with plane stride ps; ws: count * 512 bytes;
 // per_sm: resident CTAs per SM of the persistent grids.
 cudaError_t launch_gnn_step_table(const float* f_in, float* f_out, const LatDesc* lat, int first,
                                   int n, int64_t base, int64_t count, int64_t ps,
