@@ -339,13 +339,37 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd1_kernel(
 //   dB_j = sum_k da_i * GELU'(A_i + B_j + c_k),  i = j - e_k
 //   dc_x,j / dc_y,j = the e_kx / e_ky weighted sums of the dA_j terms.
 // dh_in = dh_part + [dA | dB] [W_a; W_b]; accumulates [dW_a; dW_b], db_e
-// (= sum dA) and the W_c columns (sum dc_x, sum dc_y).
+// (= sum dA) on the tensor cores and the W_c columns (sum dc_x, sum dc_y) in
+// registers (butterfly reduction over the warp's nodes).
 namespace rb2 {
-constexpr uint32_t DAB = 0, DABT = 32768, DCT = 65536, HT = 98304, WABT = 118784, CK = 135168,
-                   CKH = 137216, SH = 138240, BYTES = 138368;
+constexpr uint32_t DAB = 0, DABT = 32768, HT = 65536, WABT = 86016, CK = 102400, CKH = 104448,
+                   DCR = 105472, SH = 107520, BYTES = 107648;
+}
+#ifndef LBM_RB2_CTAS
+#define LBM_RB2_CTAS 1  // resident CTAs per SM (2 fit; measured slower)
+#endif
+#ifndef LBM_RB2_GROUP
+#define LBM_RB2_GROUP 4  // neighbours whose loads are in flight together
+#endif
+
+// Sum over the 32 lanes of v[0..31] (lane-private values): afterwards lane l
+// holds the sum of v[l] over the warp (31 shuffles; halves the vector per step).
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool upper = lane & w;  // keep the upper half of the current range
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const float send = upper ? v[i] : v[i + w];
+      const float keep = upper ? v[i + w] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0];
 }
 
-__global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
+__global__ void __launch_bounds__(256, LBM_RB2_CTAS) gnn_round_bwd2_kernel(
     const __half* __restrict__ ab, const float* __restrict__ da,
     const float* __restrict__ dh_part, const __nv_bfloat16* __restrict__ h_in,
     float* __restrict__ dh_in, int round, float* __restrict__ G, Shape s,
@@ -370,8 +394,9 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
   const __half2* ckh = reinterpret_cast<const __half2*>(sm + rb2::CKH);
   uint8_t* DAB = sm + rb2::DAB;
   uint8_t* DABT = sm + rb2::DABT;
-  uint8_t* DCT = sm + rb2::DCT;
   uint8_t* HT = sm + rb2::HT;
+  // per chunk: lane l's running sum of value l of [dc_x | dc_y] over this warp's nodes
+  float dcacc0 = 0.0f, dcacc1 = 0.0f;
   const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
   const uint32_t lb = lane_base(tc.tmem);
   const int64_t N = (int64_t)s.nb * s.ny * s.nx;
@@ -385,103 +410,125 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
 #pragma unroll 1
     for (int sc = 0; sc < 2; ++sc) {  // two chunks of 16 features
       const int c0 = f0 + 16 * sc;
-      // GELU'(z) is evaluated in packed FP16 pairs (z = A + B + c_k is O(1));
-      // the gradients themselves stay FP32 (they would underflow FP16).
-      uint32_t aj[8], bj[8];
-      float daj[16], gA[16], gx[16], gy[16], gB[16];
-      {
-        const uint4 a0 = __ldg(chunk8(ab, N, nn, c0)), a1 = __ldg(chunk8(ab, N, nn, c0 + 8));
-        const uint4 b0 = __ldg(chunk8(ab, N, nn, HID + c0));
-        const uint4 b1 = __ldg(chunk8(ab, N, nn, HID + c0 + 8));
-        aj[0] = a0.x; aj[1] = a0.y; aj[2] = a0.z; aj[3] = a0.w;
-        aj[4] = a1.x; aj[5] = a1.y; aj[6] = a1.z; aj[7] = a1.w;
-        bj[0] = b0.x; bj[1] = b0.y; bj[2] = b0.z; bj[3] = b0.w;
-        bj[4] = b1.x; bj[5] = b1.y; bj[6] = b1.z; bj[7] = b1.w;
+      const int ch = c0 >> 3;
+      // 2 GELU'(z) is evaluated in packed FP16 pairs (z = A + B + c_k is O(1)).
+      // dA_j = da_j * sum_k GELU'(z_jk) factors: the sums over k (and their
+      // e_kx / e_ky weighted forms) are taken in FP16 and multiplied by da_j
+      // once.  dB_j needs the neighbours' da, so its terms are accumulated in
+      // FP32 (gradients would underflow FP16).  The two halves run one after
+      // the other to keep few values live.
+      {  // dA_j and dc_j over the neighbours j + e_k
+        uint32_t aj[8];
+        {
+          const uint4 a0 = __ldg(chunk8(ab, N, nn, c0)), a1 = __ldg(chunk8(ab, N, nn, c0 + 8));
+          aj[0] = a0.x; aj[1] = a0.y; aj[2] = a0.z; aj[3] = a0.w;
+          aj[4] = a1.x; aj[5] = a1.y; aj[6] = a1.z; aj[7] = a1.w;
+        }
+        __half2 S[8], Sx[8], Sy[8];  // sums over k of 2 GELU'(z_jk), e_kx and e_ky weighted
+#pragma unroll
+        for (int c = 0; c < 8; ++c) S[c] = Sx[c] = Sy[c] = __float2half2_rn(0.0f);
+#pragma unroll
+        for (int g = 0; g < 8; g += LBM_RB2_GROUP) {  // directions k = g+1 .. g+LBM_RB2_GROUP
+          uint4 bn[LBM_RB2_GROUP][2];
+#pragma unroll
+          for (int kk = 0; kk < LBM_RB2_GROUP; ++kk) {
+            const int k = g + kk + 1;
+            const int64_t j = node_at(p, ex(k), ey(k), s);
+            bn[kk][0] = __ldg(chunk8(ab, N, j, HID + c0));
+            bn[kk][1] = __ldg(chunk8(ab, N, j, HID + c0 + 8));
+          }
+#pragma unroll
+          for (int kk = 0; kk < LBM_RB2_GROUP; ++kk) {
+            const int k = g + kk + 1;
+            const __half2* c_k = ckh + (k - 1) * (HID / 2) + c0 / 2;
+            const uint32_t* bw = reinterpret_cast<const uint32_t*>(bn[kk]);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const __half2 z = __hadd2(__hadd2(u32_as_h2(aj[c]), c_k[c]), u32_as_h2(bw[c]));
+              const __half2 gp = gelu_grad2_h2(z);
+              S[c] = __hadd2(S[c], gp);
+              if (ex(k) > 0) Sx[c] = __hadd2(Sx[c], gp);
+              if (ex(k) < 0) Sx[c] = __hsub2(Sx[c], gp);
+              if (ey(k) > 0) Sy[c] = __hadd2(Sy[c], gp);
+              if (ey(k) < 0) Sy[c] = __hsub2(Sy[c], gp);
+            }
+          }
+        }
+        float gA[16], v[32];  // v = [dc_x | dc_y] of this node
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const float4 t = __ldg(chunk4(da, N, nn, c0 + 4 * i));
-          daj[4 * i] = t.x; daj[4 * i + 1] = t.y; daj[4 * i + 2] = t.z; daj[4 * i + 3] = t.w;
-        }
-      }
+          const float dd[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
-      for (int c = 0; c < 16; ++c) gA[c] = gx[c] = gy[c] = gB[c] = 0.0f;
-#pragma unroll
-      for (int g = 0; g < 8; g += 4) {  // directions k = g+1 .. g+4
-        // dA_j, dc_j: neighbours j + e_k
-        uint4 bn[4][2];
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const int k = g + kk + 1;
-          const int64_t j = node_at(p, ex(k), ey(k), s);
-          bn[kk][0] = __ldg(chunk8(ab, N, j, HID + c0));
-          bn[kk][1] = __ldg(chunk8(ab, N, j, HID + c0 + 8));
-        }
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const int k = g + kk + 1;
-          const __half2* c_k = ckh + (k - 1) * (HID / 2) + c0 / 2;
-          const uint32_t* bw = reinterpret_cast<const uint32_t*>(bn[kk]);
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const __half2 z = __hadd2(__hadd2(u32_as_h2(aj[c]), c_k[c]), u32_as_h2(bw[c]));
-            const float2 gp = __half22float2(gelu_grad_h2(z));
-            const float g0 = daj[2 * c] * gp.x, g1 = daj[2 * c + 1] * gp.y;
-            gA[2 * c] += g0;
-            gA[2 * c + 1] += g1;
-            if (ex(k)) {
-              gx[2 * c] += float(ex(k)) * g0;
-              gx[2 * c + 1] += float(ex(k)) * g1;
-            }
-            if (ey(k)) {
-              gy[2 * c] += float(ey(k)) * g0;
-              gy[2 * c + 1] += float(ey(k)) * g1;
-            }
+          for (int q = 0; q < 4; ++q) {  // the factor 1/2 of 2 GELU' is applied here
+            const int c = 4 * i + q;
+            const float d = on ? 0.5f * dd[q] : 0.0f;
+            const float2 sv = __half22float2(S[c >> 1]), sx = __half22float2(Sx[c >> 1]);
+            const float2 sy = __half22float2(Sy[c >> 1]);
+            gA[c] = d * ((c & 1) ? sv.y : sv.x);
+            v[c] = d * ((c & 1) ? sx.y : sx.x);
+            v[16 + c] = d * ((c & 1) ? sy.y : sy.x);
           }
         }
-        // dB_j: neighbours i = j - e_k
-        uint4 ai[4][2];
-        float4 di[4][4];
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const int k = g + kk + 1;
-          const int64_t i = node_at(p, -ex(k), -ey(k), s);
-          ai[kk][0] = __ldg(chunk8(ab, N, i, c0));
-          ai[kk][1] = __ldg(chunk8(ab, N, i, c0 + 8));
-#pragma unroll
-          for (int t4 = 0; t4 < 4; ++t4) di[kk][t4] = __ldg(chunk4(da, N, i, c0 + 4 * t4));
-        }
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const int k = g + kk + 1;
-          const __half2* c_k = ckh + (k - 1) * (HID / 2) + c0 / 2;
-          const uint32_t* aw = reinterpret_cast<const uint32_t*>(ai[kk]);
-          const float* dv = reinterpret_cast<const float*>(di[kk]);
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const __half2 z = __hadd2(__hadd2(u32_as_h2(aw[c]), c_k[c]), u32_as_h2(bj[c]));
-            const float2 gp = __half22float2(gelu_grad_h2(z));
-            gB[2 * c] += dv[2 * c] * gp.x;
-            gB[2 * c + 1] += dv[2 * c + 1] * gp.y;
-          }
-        }
-      }
-      if (!on) {
-#pragma unroll
-        for (int c = 0; c < 16; ++c) gA[c] = gx[c] = gy[c] = gB[c] = 0.0f;
-      }
-      // node-major [dA | dB] (A operand of the dh MMA)
-      {
-        const int ch = c0 >> 3;
+        // node-major dA (A operand of the dh MMA) and its transpose
         *reinterpret_cast<uint4*>(DAB + node * 128 + ((ch ^ (node & 7)) << 4)) = pack_bf16x8(gA);
-        *reinterpret_cast<uint4*>(DAB + node * 128 + (((ch + 1) ^ (node & 7)) << 4)) = pack_bf16x8(gA + 8);
+        *reinterpret_cast<uint4*>(DAB + node * 128 + (((ch + 1) ^ (node & 7)) << 4)) =
+            pack_bf16x8(gA + 8);
+        st_col<16>(DABT, 128, c0, node, gA);
+        // dc sums over this warp's 32 nodes: lane l gets value l of [dc_x | dc_y]
+        const float t = warp_transpose_sum(v);
+        if (sc == 0)
+          dcacc0 += t;
+        else
+          dcacc1 += t;
+      }
+      {  // dB_j over the neighbours i = j - e_k
+        uint32_t bj[8];
+        {
+          const uint4 b0 = __ldg(chunk8(ab, N, nn, HID + c0));
+          const uint4 b1 = __ldg(chunk8(ab, N, nn, HID + c0 + 8));
+          bj[0] = b0.x; bj[1] = b0.y; bj[2] = b0.z; bj[3] = b0.w;
+          bj[4] = b1.x; bj[5] = b1.y; bj[6] = b1.z; bj[7] = b1.w;
+        }
+        float gB[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) gB[c] = 0.0f;
+#pragma unroll
+        for (int g = 0; g < 8; g += LBM_RB2_GROUP) {
+          uint4 ai[LBM_RB2_GROUP][2];
+          float4 di[LBM_RB2_GROUP][4];
+#pragma unroll
+          for (int kk = 0; kk < LBM_RB2_GROUP; ++kk) {
+            const int k = g + kk + 1;
+            const int64_t i = node_at(p, -ex(k), -ey(k), s);
+            ai[kk][0] = __ldg(chunk8(ab, N, i, c0));
+            ai[kk][1] = __ldg(chunk8(ab, N, i, c0 + 8));
+#pragma unroll
+            for (int t4 = 0; t4 < 4; ++t4) di[kk][t4] = __ldg(chunk4(da, N, i, c0 + 4 * t4));
+          }
+#pragma unroll
+          for (int kk = 0; kk < LBM_RB2_GROUP; ++kk) {
+            const int k = g + kk + 1;
+            const __half2* c_k = ckh + (k - 1) * (HID / 2) + c0 / 2;
+            const uint32_t* aw = reinterpret_cast<const uint32_t*>(ai[kk]);
+            const float* dv = reinterpret_cast<const float*>(di[kk]);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const __half2 z = __hadd2(__hadd2(u32_as_h2(aw[c]), c_k[c]), u32_as_h2(bj[c]));
+              const float2 gp = __half22float2(gelu_grad2_h2(z));
+              gB[2 * c] = fmaf(dv[2 * c], gp.x, gB[2 * c]);
+              gB[2 * c + 1] = fmaf(dv[2 * c + 1], gp.y, gB[2 * c + 1]);
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) gB[c] = on ? 0.5f * gB[c] : 0.0f;
         uint8_t* b1 = DAB + 16384;
         *reinterpret_cast<uint4*>(b1 + node * 128 + ((ch ^ (node & 7)) << 4)) = pack_bf16x8(gB);
-        *reinterpret_cast<uint4*>(b1 + node * 128 + (((ch + 1) ^ (node & 7)) << 4)) = pack_bf16x8(gB + 8);
+        *reinterpret_cast<uint4*>(b1 + node * 128 + (((ch + 1) ^ (node & 7)) << 4)) =
+            pack_bf16x8(gB + 8);
+        st_col<16>(DABT, 128, HID + c0, node, gB);
       }
-      st_col<16>(DABT, 128, c0, node, gA);
-      st_col<16>(DABT, 128, HID + c0, node, gB);
-      st_col<16>(DCT, 128, c0, node, gx);
-      st_col<16>(DCT, 128, HID + c0, node, gy);
     }
     {
       float h[32];
@@ -492,7 +539,6 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
     if (!tc_run(sh, tc, stw, [&] {
           umma_128xN(tc.tmem, smem_u32(DAB), 16384, smem_u32(sm + rb2::WABT), 8192, 2, 64, false);
           umma_128xN(tc.tmem + 64, smem_u32(DABT), 16384, smem_u32(HT), 10240, 2, 80, acc);
-          umma_128xN(tc.tmem + 144, smem_u32(DCT), 16384, smem_u32(HT) + 8192, 10240, 2, 16, acc);
         })) {
       ok = false;
       break;
@@ -517,13 +563,24 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd2_kernel(
     float v[32];
     tmem_ld32(lb + 64 + f0, v);
     for (int c = 0; c < 32; ++c) g[P::EDGE_W + o * 130 + col_off + f0 + c] = v[c];
-    float u[16];
     if (half == 0) {
+      float u[16];
       tmem_ld16(lb + 128, u);  // column sum of [dA | dB]
       if (row < HID) g[P::EDGE_B + o] = u[0];
-    } else {
-      tmem_ld16(lb + 144, u);  // column sum of [dc_x | dc_y]
-      g[P::EDGE_W + o * 130 + 128 + (row < HID ? 0 : 1)] = u[0];
+    }
+    // W_c columns: the 4 warps of a feature half hold disjoint node sets;
+    // summed in fixed order.
+    float* dcr = reinterpret_cast<float*>(sm + rb2::DCR);  // [8 warps][2 chunks][32]
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    dcr[(w * 2 + 0) * 32 + lane] = dcacc0;
+    dcr[(w * 2 + 1) * 32 + lane] = dcacc1;
+    __syncthreads();
+    if (threadIdx.x < 128) {
+      const int hh = threadIdx.x >> 6, sc = (threadIdx.x >> 5) & 1, l = threadIdx.x & 31;
+      float t = 0.0f;
+      for (int q = 0; q < 4; ++q) t += dcr[((hh * 4 + q) * 2 + sc) * 32 + l];
+      const int of = 32 * hh + 16 * sc + (l & 15);
+      g[P::EDGE_W + of * 130 + 128 + (l >> 4)] = t;
     }
   }
   tc_teardown(sh, tc);
@@ -762,7 +819,7 @@ cudaError_t launch_gnn_backward(const BackwardLaunch& bl, const Shape& s, const 
     {
       const uint32_t bytes = rb2::BYTES + 1024;
       if ((e = set_smem(gnn_round_bwd2_kernel, bytes)) != cudaSuccess) return e;
-      gnn_round_bwd2_kernel<<<grad_grid(N, 1), 256, bytes, st>>>(abs_[r], bl.da, bl.dh[1], hs[r],
+      gnn_round_bwd2_kernel<<<grad_grid(N, LBM_RB2_CTAS), 256, bytes, st>>>(abs_[r], bl.da, bl.dh[1], hs[r],
                                                                  bl.dh[0], r, bl.G, s, packed, stw);
     }
   }
