@@ -42,8 +42,8 @@ NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #     --clock-control none -k regex:bgk_step_x4 -s 3 -c 1
     #     python bench.py --only bgk --steps 10 --warmup 3      (4096 x 4096, one launch)
-    "bgk_step_x4": {"bytes_per_launch": 604029696 + 547351808,
-                    "src_sha": "b02111b1f5f94ee636a95844c099c9ee189fa7a72626dd2ab4b27ccce1b3f491"},
+    "bgk_step_x4": {"bytes_per_launch": 604025600 + 547085312,
+                    "src_sha": "9de0c99f1f5c28d8f088a57433a6ea795415ff32b022b5de84dfbb4e0da9b168"},
 }
 
 
@@ -298,6 +298,7 @@ def run_ours(args, rank, world, local_rank):
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
+        out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores()
     return out
 
 
@@ -602,6 +603,39 @@ def cpu_baseline(budget_s=12.0):
             "kind": "oracle",
             "sample": f"oracle.lbm.bgk_step (numpy FP64) on a 1024x1024 TGV sub-lattice, "
                       f"{steps} steps, {dt:.1f} s"}
+
+
+def _oracle_worker(budget_s):
+    """One host core: the oracle BGK step on its own 512 x 512 TGV lattice
+    until ~budget_s have passed; returns node updates."""
+    from oracle import lbm
+    n = 512
+    k = 2 * np.pi / n
+    f = lbm.tgv_init(n, n, 1.0, U0, k, k)
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        f = lbm.bgk_step(f, TAU)
+        steps += 1
+    return n * n * steps
+
+
+def cpu_baseline_all_cores(budget_s=8.0):
+    """The same oracle on every host core at once (one process per core, each
+    with an independent lattice: weak scaling, no exchange)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(var, "1")
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_worker, [0.0] * cores)  # interpreters and numpy loaded
+        t0 = time.perf_counter()
+        updates = sum(pool.map(_oracle_worker, [budget_s] * cores))
+        dt = time.perf_counter() - t0
+    return {"value": round(updates / dt / 1e6, 3), "unit": "MLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"oracle.lbm.bgk_step (numpy FP64) on {cores} independent 512x512 TGV "
+                      f"lattices, one process per core, {dt:.1f} s"}
 
 
 def run_reference(args, rank):
