@@ -95,6 +95,44 @@ def test_batched_run_equals_per_lattice_runs(lbmlib, cuda, tmp_path):
         L.lbm_batch_plan_destroy(plan)
 
 
+def test_stack_and_table_geometry_agree_bitwise(lbmlib, cuda):
+    """Lattices whose rows are whole 128-node tiles, stepped alone by
+    lbm_step_gnn (stack geometry) and together by the batched run (table
+    geometry, lattice found by binary search): the same arithmetic in the
+    same order, so bitwise equal."""
+    import torch
+    L = lbmlib
+    lat = [(128, 6, 1, 0.7), (256, 3, 1, 0.62), (384, 2, 1, 0.9)]
+    theta = inputs.xavier_params(19, s_df=1e-2, bias_scale=0.1)
+    params = torch.from_numpy(theta).to(cuda)
+    packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=cuda)
+    L.gnn_pack(params, packed)
+    plan = L.lbm_batch_plan_create(lat)
+    try:
+        n = L.lbm_batch_nodes(plan)
+        off = L.lbm_batch_offsets(plan, len(lat))
+        prm = np.array([_prm(i, l[0], l[1]) for i, l in enumerate(lat)])
+        f0 = torch.empty(9 * n, device=cuda)
+        L.lbm_batch_init_tgv(plan, f0, prm, False)
+        g = torch.Generator(device=cuda)
+        g.manual_seed(11)
+        f0.mul_(1 + 2e-2 * (2 * torch.rand(f0.shape, generator=g, device=cuda) - 1))
+        f1, f2 = torch.empty_like(f0), torch.empty_like(f0)
+        ws = torch.empty(L.lbm_batch_workspace_bytes(plan), dtype=torch.uint8, device=cuda)
+        L.lbm_batch_run(plan, f0, f1, f2, 1, packed, ws)
+        for i, (nx, ny, _, tau) in enumerate(lat):
+            m = nx * ny
+            a = f0.view(9, n)[:, off[i]:off[i] + m].contiguous().reshape(-1)
+            b = torch.empty_like(a)
+            s = L.shape(nx, ny)
+            w = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+            L.lbm_step_gnn(a, b, s, tau, None, packed, None, w)
+            assert torch.equal(f1.view(9, n)[:, off[i]:off[i] + m], b.view(9, m)), (nx, ny)
+        assert L.lbm_get_status() == 0
+    finally:
+        L.lbm_batch_plan_destroy(plan)
+
+
 def test_batch_plan_argument_checks(lbmlib):
     L = lbmlib
     with pytest.raises(L.LbmError) as e:

@@ -85,7 +85,10 @@ def test_forward_matches_oracle(lbmlib, cuda, nb, ny, nx):
         assert e <= 2e-2, (r, e)
 
 
-@pytest.mark.parametrize("nb,ny,nx", [(1, 16, 16), (2, 5, 7), (1, 64, 64)])
+# (1, 6, 128), (2, 3, 256): rows of whole 128-node tiles (tile-aligned rows,
+# x and y wrap, 2 lattices)
+@pytest.mark.parametrize("nb,ny,nx", [(1, 16, 16), (2, 5, 7), (1, 64, 64), (1, 6, 128),
+                                      (2, 3, 256)])
 def test_step_gnn_matches_oracle(lbmlib, cuda, nb, ny, nx):
     import torch
     L = lbmlib
@@ -239,3 +242,45 @@ def test_variants_forward_and_step(lbmlib, cuda, variant):
             t1 = lbm.totals(got[:, b])
             assert abs(t1[0] - t0[0]) <= 1e-6 * t0[0]
             assert abs(t1[1] - t0[1]) <= 1e-6 * t0[0] and abs(t1[2] - t0[2]) <= 1e-6 * t0[0]
+
+
+def test_step_gnn_full_size_1024_sampled(lbmlib, cuda):
+    """lbm_step_gnn at the 1024^2 inference workload, in the launch
+    configuration the benchmark times: the stepped state
+    at 40 sampled nodes (and the 4 corners) against the oracle's GNN step on
+    the 13x13 periodic patch around each node (the result depends on the 7x7
+    neighbourhood: streaming plus two message-passing hops)."""
+    import torch
+    L = lbmlib
+    n = 1024
+    s = L.shape(n, n)
+    k = 2 * np.pi / n
+    f = torch.empty(9 * n * n, device=cuda)
+    L.lbm_init_tgv(f, s, 1.0, 0.05, k, k, False)
+    g = torch.Generator(device=cuda)
+    g.manual_seed(5)
+    f.mul_(1 + 2e-2 * (2 * torch.rand(f.shape, generator=g, device=cuda) - 1))
+    theta = inputs.xavier_params(53, s_df=1e-2, bias_scale=0.1)
+    pk = _packed(L, theta, cuda)
+    out = torch.empty_like(f)
+    ws = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    L.lbm_step_gnn(f, out, s, 0.65, None, pk, None, ws)
+    assert L.lbm_get_status() == 0
+    F = f.view(9, n, n).cpu().numpy().astype(np.float64)
+    O = out.view(9, n, n).cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(2)
+    pts = [(int(a), int(b)) for a, b in zip(rng.integers(0, n, 40), rng.integers(0, n, 40))]
+    pts += [(0, 0), (0, n - 1), (n - 1, 0), (n - 1, n - 1)]
+    got, ref, bgk = [], [], []
+    for (x, yy) in pts:
+        xs = (np.arange(x - 6, x + 7)) % n
+        ys = (np.arange(yy - 6, yy + 7)) % n
+        patch = F[:, ys[:, None], xs[None, :]]
+        ref.append(gnn.gnn_step(patch, theta, 0.65)[:, 6, 6])
+        bgk.append(lbm.bgk_step(patch, 0.65)[:, 6, 6])
+        got.append(O[:, yy, x])
+    got, ref, bgk = np.array(got), np.array(ref), np.array(bgk)
+    assert rel_l2(got - bgk, ref - bgk) <= 3e-2
+    corr = np.max(np.abs(ref - bgk))
+    assert np.max(np.abs(got - ref) - 1e-6 * np.abs(ref)) / corr <= 5e-2
+
