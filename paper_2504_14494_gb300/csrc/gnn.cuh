@@ -337,6 +337,24 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[NF]) {
   }
 }
 
+// Division of a 32-bit unsigned n < 2^31 by a fixed divisor d >= 1 with one
+// multiply-high (Granlund and Montgomery, "Division by invariant integers
+// using multiplication", 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1 (the low 32 bits of the 33-bit multiplier
+// floor(2^(32+l) / d) + 1), n / d = (umulhi(m, n) + n) >> l.
+struct FastDiv {
+  uint32_t d, m, l;
+};
+inline FastDiv fast_div(uint32_t d) {
+  uint32_t l = 0;
+  while ((uint64_t(1) << l) < d) ++l;
+  const uint64_t m = ((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1;
+  return {d, (uint32_t)m, l};
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  return (__umulhi(f.m, n) + n) >> f.l;
+}
+
 // Node coordinates within the stacked lattices.
 struct NodeXY {
   int x, y;
@@ -375,10 +393,17 @@ __device__ __forceinline__ int64_t geo_nbr(const GeoPos& p, int dx, int dy) {
 
 struct GeoStack {
   Shape s;
+  FastDiv dnx, dny;  // for stacks of fewer than 2^31 nodes (`small`)
+  bool small;
   __device__ __forceinline__ int64_t count() const { return (int64_t)s.nb * s.ny * s.nx; }
   __device__ __forceinline__ int64_t base() const { return 0; }
   __device__ __forceinline__ int64_t ps() const { return s.ps; }
   __device__ __forceinline__ GeoPos pos(int64_t g) const {
+    if (small) {
+      const uint32_t gu = (uint32_t)g, row = fdiv(gu, dnx), b = fdiv(row, dny);
+      return {(int)(gu - row * (uint32_t)s.nx), (int)(row - b * (uint32_t)s.ny), s.nx, s.ny,
+              (int64_t)b * s.ny * s.nx, (int)b};
+    }
     const int64_t row = g / s.nx;
     const int x = (int)(g - row * s.nx);
     const int64_t b = row / s.ny;
@@ -392,6 +417,15 @@ struct GeoStack {
 
 // One lattice of a batched run: first node in the packed buffers, size and
 // relaxation time.
+inline GeoStack make_geo_stack(const Shape& s) {
+  GeoStack g;
+  g.s = s;
+  g.dnx = fast_div((uint32_t)s.nx);
+  g.dny = fast_div((uint32_t)s.ny);
+  g.small = (int64_t)s.nb * s.ny * s.nx < (int64_t(1) << 31);
+  return g;
+}
+
 struct LatDesc {
   int64_t offset;
   int32_t nx, ny;

@@ -575,13 +575,13 @@ static cudaError_t round_any(int mode, const RoundLaunch& rl, const Geo& geo, in
 cudaError_t launch_gnn_encode(const float* f, bool pull, bool b_only, const Shape& s,
                               const uint8_t* packed, __nv_bfloat16* h0, __half* ab,
                               cudaStream_t st) {
-  return encode_any(f, pull, b_only, GeoStack{s}, (int64_t)s.nb * s.ny * s.nx, packed, h0, ab,
+  return encode_any(f, pull, b_only, make_geo_stack(s), (int64_t)s.nb * s.ny * s.nx, packed, h0, ab,
                     st);
 }
 
 cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
                              const uint8_t* packed, cudaStream_t st) {
-  return round_any(mode, rl, GeoStack{s}, (int64_t)s.nb * s.ny * s.nx, packed, st);
+  return round_any(mode, rl, make_geo_stack(s), (int64_t)s.nb * s.ny * s.nx, packed, st);
 }
 
 cudaError_t launch_gnn_step_table(const float* f_in, float* f_out, const LatDesc* lat, int first,
