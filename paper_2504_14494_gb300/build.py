@@ -18,6 +18,11 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbmgnn.so")
+# Test build: every computed gather index checked against its buffer
+# (-DLBM_BOUNDS_CHECK); a failed check raises the status word's bounds bit
+# instead of accessing memory out of range.
+OBJDIR_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "liblbmgnn_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
@@ -48,20 +53,22 @@ def _stamp(extra_flags):
     return h.hexdigest()
 
 
-def build(verbose=False, extra_flags=(), force=False):
-    """Compile (if needed) and return the path of liblbmgnn.so."""
-    extra_flags = list(extra_flags)
+def build(verbose=False, extra_flags=(), force=False, checked=False):
+    """Compile (if needed) and return the path of liblbmgnn.so (with
+    checked=True: of the bounds-checked test build liblbmgnn_checked.so)."""
+    extra_flags = list(extra_flags) + (["-DLBM_BOUNDS_CHECK"] if checked else [])
+    objdir, lib = (OBJDIR_CHECKED, LIB_CHECKED) if checked else (OBJDIR, LIB)
     stamp = _stamp(extra_flags)
-    stamp_file = os.path.join(OBJDIR, "stamp")
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_file):
+    stamp_file = os.path.join(objdir, "stamp")
+    if not force and os.path.exists(lib) and os.path.exists(stamp_file):
         with open(stamp_file) as fh:
             if fh.read().strip() == stamp:
-                return LIB
-    os.makedirs(OBJDIR, exist_ok=True)
+                return lib
+    os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -70,17 +77,17 @@ def build(verbose=False, extra_flags=(), force=False):
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp_file, "w") as fh:
         fh.write(stamp)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

@@ -8,6 +8,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "trace.h"
 
 using namespace lbmgnn;
 
@@ -115,6 +116,7 @@ int lbm_get_status(void* stream) {
 
 int lbm_init_tgv(float* f, lbm_shape shape, double rho0, double u0, double kx, double ky,
                  int pressure_consistent, void* stream) {
+  LBM_TRACE("lbm_init_tgv");
   Shape s;
   if (!f) return LBM_ERR_ARG;
   if (int r = check_shape(shape, &s)) return r;
@@ -127,6 +129,7 @@ int lbm_init_tgv(float* f, lbm_shape shape, double rho0, double u0, double kx, d
 
 int lbm_step_bgk(const float* f_in, float* f_out, float* f_tmp, lbm_shape shape, float tau,
                  const float* taus, int nsteps, double* totals, void* stream) {
+  LBM_TRACE("lbm_step_bgk");
   Shape s;
   if (!f_in || !f_out || nsteps < 0) return LBM_ERR_ARG;
   if (int r = check_shape(shape, &s)) return r;
@@ -163,6 +166,7 @@ int lbm_step_bgk(const float* f_in, float* f_out, float* f_tmp, lbm_shape shape,
 
 int lbm_step_channel(const float* f_in, float* f_out, float* f_tmp, lbm_shape shape, float tau,
                      const float* taus, float force_x, int nsteps, double* totals, void* stream) {
+  LBM_TRACE("lbm_step_channel");
   Shape s;
   if (!f_in || !f_out || nsteps < 0 || !std::isfinite(force_x)) return LBM_ERR_ARG;
   if (int r = check_shape(shape, &s)) return r;
@@ -198,6 +202,7 @@ int lbm_step_channel(const float* f_in, float* f_out, float* f_tmp, lbm_shape sh
 
 int lbm_moments(const float* f, lbm_shape shape, float* rho, float* ux, float* uy,
                 double* totals, void* stream) {
+  LBM_TRACE("lbm_moments");
   Shape s;
   if (!f) return LBM_ERR_ARG;
   if (int r = check_shape(shape, &s)) return r;
@@ -216,6 +221,7 @@ size_t lbm_host_workspace_bytes(lbm_shape shape) {
 int lbm_step_bgk_host(const float* f_in_host, float* f_out_host, lbm_shape shape, float tau,
                       const float* taus_host, int nsteps, double* totals_host, void* workspace,
                       size_t ws_bytes, void* stream) {
+  LBM_TRACE("lbm_step_bgk_host");
   Shape s;
   if (!f_in_host || nsteps < 1) return LBM_ERR_ARG;
   if (int r = check_shape(shape, &s)) return r;

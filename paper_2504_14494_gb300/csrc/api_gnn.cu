@@ -5,6 +5,7 @@
 #include "gnn.cuh"
 #include "gnn_launch.h"
 #include "launch.h"
+#include "trace.h"
 
 using namespace lbmgnn;
 
@@ -44,6 +45,7 @@ size_t gnn_trainable_count(void) { return P::TRAINABLE; }
 size_t gnn_packed_bytes(void) { return K::TOTAL; }
 
 int gnn_pack(const float* params, void* packed, void* stream) {
+  LBM_TRACE("gnn_pack");
   if (!params || !packed) return LBM_ERR_ARG;
   if (!aligned(packed, 16)) return LBM_ERR_ARG;
   if (cudaMemsetAsync(packed, 0, K::TOTAL, static_cast<cudaStream_t>(stream)) != cudaSuccess)
@@ -63,6 +65,7 @@ size_t gnn_step_workspace_bytes(lbm_shape shape) {
 int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape shape, float tau, const float* taus,
                  const void* packed, double* totals, void* workspace, size_t ws_bytes,
                  void* stream) {
+  LBM_TRACE("lbm_step_gnn");
   Shape s;
   if (!f_in || !f_out || !packed) return LBM_ERR_ARG;
   if (int r = check_shape_g(shape, &s)) return r;
@@ -119,6 +122,7 @@ size_t gnn_saved_bytes(lbm_shape shape) {
 
 int gnn_forward(const float* f_pre, lbm_shape shape, const void* packed, void* saved, float* y,
                 void* stream) {
+  LBM_TRACE("gnn_forward");
   Shape s;
   if (!f_pre || !packed || !saved || !y) return LBM_ERR_ARG;
   if (int r = check_shape_g(shape, &s)) return r;

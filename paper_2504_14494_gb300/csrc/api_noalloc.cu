@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "trace.h"
 
 namespace {
 
@@ -53,6 +54,7 @@ extern "C" {
 
 int lbm_step_gnn_noalloc(const float* f_in, float* f_out, lbm_shape s, float tau,
                          const float* taus, const void* packed, double* totals, void* stream) {
+  LBM_TRACE("lbm_step_gnn_noalloc");
   if (s.nx < 1 || s.ny < 1 || s.nb < 1) return LBM_ERR_SIZE;
   const int64_t n = (int64_t)s.nx * s.ny * s.nb;
   if (n > NOALLOC_MAX_NODES) return LBM_ERR_SIZE;

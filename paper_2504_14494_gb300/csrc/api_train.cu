@@ -7,6 +7,7 @@
 #include "gnn.cuh"
 #include "gnn_launch.h"
 #include "launch.h"
+#include "trace.h"
 
 using namespace lbmgnn;
 
@@ -68,6 +69,7 @@ void set_saved(const void* saved, int64_t N, BackwardLaunch& bl) {
 extern "C" {
 
 int lbm_stream(const float* f_in, float* f_out, lbm_shape shape, void* stream) {
+  LBM_TRACE("lbm_stream");
   Shape s;
   if (!f_in || !f_out) return LBM_ERR_ARG;
   if (int r = check_shape_t(shape, &s)) return r;
@@ -79,6 +81,7 @@ int lbm_stream(const float* f_in, float* f_out, lbm_shape shape, void* stream) {
 
 int lbm_init_tgv_batch(float* f, lbm_shape shape, const double* params, int pressure_consistent,
                        void* stream) {
+  LBM_TRACE("lbm_init_tgv_batch");
   Shape s;
   if (!f || !params) return LBM_ERR_ARG;
   if (int r = check_shape_t(shape, &s)) return r;
@@ -91,6 +94,7 @@ int lbm_init_tgv_batch(float* f, lbm_shape shape, const double* params, int pres
 int lbm_restrict(const float* f_fine, lbm_shape fine, float* f_coarse, lbm_shape coarse,
                  int factor, float tau_f, const float* taus_f, float tau_c, const float* taus_c,
                  void* stream) {
+  LBM_TRACE("lbm_restrict");
   Shape fs, cs;
   if (!f_fine || !f_coarse || factor < 1) return LBM_ERR_ARG;
   if (int r = check_shape_t(fine, &fs)) return r;
@@ -116,6 +120,7 @@ size_t gnn_loss_workspace_bytes(lbm_shape shape) {
 int gnn_collide_loss(const float* f_pre, const float* y, const float* f_target, lbm_shape shape,
                      float tau, const float* taus, const void* packed, double* loss, float* dy,
                      float* f_pred, void* workspace, size_t ws_bytes, void* stream) {
+  LBM_TRACE("gnn_collide_loss");
   Shape s;
   if (!f_pre || !y || !f_target || !packed || !loss) return LBM_ERR_ARG;
   if (int r = check_shape_t(shape, &s)) return r;
@@ -142,6 +147,7 @@ size_t gnn_backward_workspace_bytes(lbm_shape shape) {
 int gnn_backward(const float* f_pre, lbm_shape shape, const void* packed, const void* saved,
                  const float* dy, float* dparams, float* df_pre, void* workspace, size_t ws_bytes,
                  void* stream) {
+  LBM_TRACE("gnn_backward");
   Shape s;
   if (!f_pre || !packed || !saved || !dy || !dparams) return LBM_ERR_ARG;
   if (int r = check_shape_t(shape, &s)) return r;
@@ -165,6 +171,7 @@ int gnn_backward(const float* f_pre, lbm_shape shape, const void* packed, const 
 
 int gnn_adamw(float* params, const float* grads, float* m, float* v, int64_t step, float lr,
               float wd, float beta1, float beta2, float eps, void* stream) {
+  LBM_TRACE("gnn_adamw");
   if (!params || !grads || !m || !v || step < 1) return LBM_ERR_ARG;
   if (!(lr >= 0.0f) || !(wd >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
       !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
@@ -187,6 +194,7 @@ int gnn_train_step(const float* f_in, const float* f_target, lbm_shape shape, fl
                    const float* taus, float* params, void* packed, float* adam_m, float* adam_v,
                    int64_t step, float lr, float wd, double* loss, float* grads, void* workspace,
                    size_t ws_bytes, void* stream) {
+  LBM_TRACE("gnn_train_step");
   Shape s;
   if (!f_in || !f_target || !params || !packed || !adam_m || !adam_v || !loss || step < 1)
     return LBM_ERR_ARG;

@@ -18,6 +18,7 @@
 #include "gnn.cuh"
 #include "gnn_launch.h"
 #include "launch.h"
+#include "trace.h"
 
 using namespace lbmgnn;
 
@@ -29,14 +30,15 @@ template <int NT>
 __global__ void __launch_bounds__(NT) bgk_batch_kernel(const float* __restrict__ fin,
                                                        float* __restrict__ fout,
                                                        const LatDesc* __restrict__ lat, int nlat,
-                                                       int64_t count, int64_t ps) {
+                                                       int64_t count, int64_t ps, unsigned* stw) {
   const int64_t g = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (g >= count) return;
   const GeoTable geo{lat, 0, nlat, 0, count, ps};
   const GeoPos p = geo.pos(g);
   float f[Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) f[q] = __ldg(fin + q * ps + geo_nbr(p, -ex(q), -ey(q)));
+  for (int q = 0; q < Q; ++q)
+    f[q] = __ldg(fin + q * ps + checked(geo_nbr(p, -ex(q), -ey(q)), 0, count, stw));
   bgk_collide(f, 1.0f / __ldg(&lat[p.b].tau));
 #pragma unroll
   for (int q = 0; q < Q; ++q) fout[q * ps + g] = f[q];
@@ -130,18 +132,20 @@ int tune(const char* kernel, int64_t nodes, const std::vector<int>& cand, cudaSt
 cudaError_t launch_bgk_batch(const float* fin, float* fout, const LatDesc* lat, int nlat,
                              int64_t count, int64_t ps, int block, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
+  unsigned* stw = status_word();
+  if (!stw) return cudaErrorInvalidDevice;
   switch (block) {
     case 128:
       bgk_batch_kernel<128><<<(unsigned)((count + 127) / 128), 128, 0, st>>>(fin, fout, lat, nlat,
-                                                                          count, ps);
+                                                                          count, ps, stw);
       break;
     case 512:
       bgk_batch_kernel<512><<<(unsigned)((count + 511) / 512), 512, 0, st>>>(fin, fout, lat, nlat,
-                                                                          count, ps);
+                                                                          count, ps, stw);
       break;
     default:
       bgk_batch_kernel<256><<<(unsigned)((count + 255) / 256), 256, 0, st>>>(fin, fout, lat, nlat,
-                                                                          count, ps);
+                                                                          count, ps, stw);
       break;
   }
   return cudaGetLastError();
@@ -204,6 +208,7 @@ cudaError_t plan_step(lbm_batch_plan* p, const float* src, float* dst, const uin
 extern "C" {
 
 int lbm_batch_plan_create(const lbm_lattice_desc* lattices, int n, lbm_batch_plan** out) {
+  LBM_TRACE("lbm_batch_plan_create");
   if (!out) return LBM_ERR_ARG;
   *out = nullptr;
   if (!lattices || n < 1) return LBM_ERR_ARG;
@@ -262,6 +267,7 @@ void lbm_batch_plan_destroy(lbm_batch_plan* plan) { plan_release(plan); }
 int64_t lbm_batch_nodes(const lbm_batch_plan* plan) { return plan ? plan->total : -1; }
 
 int lbm_batch_offsets(const lbm_batch_plan* plan, int64_t* offsets) {
+  LBM_TRACE("lbm_batch_offsets");
   if (!plan || !offsets) return LBM_ERR_ARG;
   std::memcpy(offsets, plan->offset_of_input.data(), sizeof(int64_t) * plan->n);
   return LBM_OK;
@@ -273,6 +279,7 @@ size_t lbm_batch_workspace_bytes(const lbm_batch_plan* plan) {
 
 int lbm_batch_init_tgv(lbm_batch_plan* plan, float* f, const double* params,
                        int pressure_consistent, void* stream) {
+  LBM_TRACE("lbm_batch_init_tgv");
   if (!plan || !f || !params) return LBM_ERR_ARG;
   std::vector<double> sorted(4 * (size_t)plan->n);
   for (int j = 0; j < plan->n; ++j)
@@ -289,6 +296,7 @@ int lbm_batch_init_tgv(lbm_batch_plan* plan, float* f, const double* params,
 
 int lbm_batch_run(lbm_batch_plan* plan, const float* f_in, float* f_out, float* f_tmp, int steps,
                   const void* packed, void* workspace, size_t ws_bytes, void* stream) {
+  LBM_TRACE("lbm_batch_run");
   if (!plan || !f_in || !f_out || steps < 0) return LBM_ERR_ARG;
   if (steps > 1 && !f_tmp) return LBM_ERR_ARG;
   if (f_in == f_out || f_tmp == f_in || (f_tmp && f_tmp == f_out)) return LBM_ERR_ALIAS;
@@ -366,6 +374,7 @@ int lbm_batch_run(lbm_batch_plan* plan, const float* f_in, float* f_out, float* 
 }
 
 int lbm_autotune_save(const char* path) {
+  LBM_TRACE("lbm_autotune_save");
   if (!path) return LBM_ERR_ARG;
   FILE* fh = std::fopen(path, "w");
   if (!fh) return LBM_ERR_ARG;
@@ -382,6 +391,7 @@ int lbm_autotune_save(const char* path) {
 }
 
 int lbm_autotune_load(const char* path) {
+  LBM_TRACE("lbm_autotune_load");
   if (!path) return LBM_ERR_ARG;
   FILE* fh = std::fopen(path, "r");
   if (!fh) return LBM_ERR_ARG;

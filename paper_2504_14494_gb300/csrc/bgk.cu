@@ -62,22 +62,24 @@ __global__ void __launch_bounds__(128) bgk_step_x4(const float* __restrict__ fin
   const bool need_r = (lane == 31) || (xl + 4 >= s.nx);
   const int64_t ps = s.ps;
 
+  const int64_t nn4 = (int64_t)s.nb * s.ny * s.nx - 3;  // last valid start of a 4-vector
+  const int64_t nn1 = nn4 + 3;
   auto v4 = [&](int q, int64_t r) {
-    return __ldg(reinterpret_cast<const float4*>(fin + q * ps + r + xl));
+    return __ldg(reinterpret_cast<const float4*>(fin + q * ps + checked(r + xl, 0, nn4, stw)));
   };
   const float4 c0 = v4(0, r0), c1 = v4(1, r0), c2 = v4(2, rm), c3 = v4(3, r0), c4 = v4(4, rp);
   const float4 c5 = v4(5, rm), c6 = v4(6, rm), c7 = v4(7, rp), c8 = v4(8, rp);
   // lane-edge scalars (predicated loads)
   float l1 = 0.f, l5 = 0.f, l8 = 0.f, e3 = 0.f, e6 = 0.f, e7 = 0.f;
   if (need_l) {
-    l1 = __ldg(fin + 1 * ps + r0 + xm);
-    l5 = __ldg(fin + 5 * ps + rm + xm);
-    l8 = __ldg(fin + 8 * ps + rp + xm);
+    l1 = __ldg(fin + 1 * ps + checked(r0 + xm, 0, nn1, stw));
+    l5 = __ldg(fin + 5 * ps + checked(rm + xm, 0, nn1, stw));
+    l8 = __ldg(fin + 8 * ps + checked(rp + xm, 0, nn1, stw));
   }
   if (need_r) {
-    e3 = __ldg(fin + 3 * ps + r0 + xr);
-    e6 = __ldg(fin + 6 * ps + rm + xr);
-    e7 = __ldg(fin + 7 * ps + rp + xr);
+    e3 = __ldg(fin + 3 * ps + checked(r0 + xr, 0, nn1, stw));
+    e6 = __ldg(fin + 6 * ps + checked(rm + xr, 0, nn1, stw));
+    e7 = __ldg(fin + 7 * ps + checked(rp + xr, 0, nn1, stw));
   }
   const float s1 = __shfl_up_sync(0xffffffffu, c1.w, 1);
   const float s5 = __shfl_up_sync(0xffffffffu, c5.w, 1);
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(256) bgk_step_any(const float* __restrict__ fi
     int xs = x - ex(q), ys = y - ey(q);
     xs = xs < 0 ? xs + s.nx : (xs >= s.nx ? xs - s.nx : xs);
     ys = ys < 0 ? ys + s.ny : (ys >= s.ny ? ys - s.ny : ys);
-    f[q] = __ldg(fin + q * s.ps + lat + (int64_t)ys * s.nx + xs);
+    f[q] = __ldg(fin + q * s.ps + checked(lat + (int64_t)ys * s.nx + xs, 0, N, stw));
   }
   bgk_collide(f, 1.0f / (taus ? __ldg(taus + b) : tau));
   if (on) {

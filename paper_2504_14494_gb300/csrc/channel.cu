@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(256) channel_step_kernel(const float* __restri
     } else {
       int xs = x - ex(q);
       xs = xs < 0 ? xs + s.nx : (xs >= s.nx ? xs - s.nx : xs);
-      f[q] = __ldg(fin + q * s.ps + lat + (int64_t)ys * s.nx + xs);
+      f[q] = __ldg(fin + q * s.ps +
+                   checked(lat + (int64_t)ys * s.nx + xs, 0, (int64_t)s.nb * s.ny * s.nx, stw));
     }
   }
   const float t = taus ? __ldg(taus + b) : tau;

@@ -40,6 +40,21 @@ unsigned* status_word();
 
 __device__ __forceinline__ void raise_status(unsigned* w, unsigned bits) { atomicOr(w, bits); }
 
+// Bounds-checked builds (-DLBM_BOUNDS_CHECK, liblbmgnn_checked.so): a computed
+// gather index outside [lo, hi) raises ST_BOUNDS and is replaced by lo, so
+// the access stays inside the buffer and the run goes on; the regular build
+// compiles the check away.  (The pool offers no memory checker; this build
+// plus small cases and the oracle stand in for one.)
+__device__ __forceinline__ int64_t checked(int64_t i, int64_t lo, int64_t hi, unsigned* stw) {
+#ifdef LBM_BOUNDS_CHECK
+  if (i < lo || i >= hi) {
+    raise_status(stw, ST_BOUNDS);
+    return lo;
+  }
+#endif
+  return i;
+}
+
 // Moments of one node: rho = sum f_i, (jx, jy) = sum f_i e_i.
 struct Moments {
   float rho, ux, uy;

@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(256, LBM_RB2_CTAS) gnn_round_bwd2_kernel(
 #pragma unroll
           for (int kk = 0; kk < LBM_RB2_GROUP; ++kk) {
             const int k = g + kk + 1;
-            const int64_t j = node_at(p, ex(k), ey(k), s);
+            const int64_t j = checked(node_at(p, ex(k), ey(k), s), 0, N, stw);
             bn[kk][0] = __ldg(chunk8(ab, N, j, HID + c0));
             bn[kk][1] = __ldg(chunk8(ab, N, j, HID + c0 + 8));
           }
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(256, LBM_RB2_CTAS) gnn_round_bwd2_kernel(
 #pragma unroll
           for (int kk = 0; kk < LBM_RB2_GROUP; ++kk) {
             const int k = g + kk + 1;
-            const int64_t i = node_at(p, -ex(k), -ey(k), s);
+            const int64_t i = checked(node_at(p, -ex(k), -ey(k), s), 0, N, stw);
             ai[kk][0] = __ldg(chunk8(ab, N, i, c0));
             ai[kk][1] = __ldg(chunk8(ab, N, i, c0 + 8));
 #pragma unroll

@@ -139,7 +139,8 @@ __global__ void __launch_bounds__(256, 3) gnn_encode_kernel(
     if (PULL) {
       const GeoPos p = geo.pos(base + mm);
 #pragma unroll
-      for (int q = 0; q < Q; ++q) v[q] = __ldg(f + q * ps + geo_nbr(p, -ex(q), -ey(q)));
+      for (int q = 0; q < Q; ++q)
+        v[q] = __ldg(f + q * ps + checked(geo_nbr(p, -ex(q), -ey(q)), base, base + N, stw));
     } else {
 #pragma unroll
       for (int q = 0; q < Q; ++q) v[q] = __ldg(f + q * ps + base + mm);
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
         uint4 braw[LBM_NBR_GROUP][2];
 #pragma unroll
         for (int k = 0; k < LBM_NBR_GROUP; ++k) {
-          const int64_t j = geo_nbr(p, ex(g + k + 1), ey(g + k + 1)) - base;
+          const int64_t j = checked(geo_nbr(p, ex(g + k + 1), ey(g + k + 1)) - base, 0, N, stw);
           constexpr int BOFF = AH ? 0 : HID;  // B's first feature in ab_in
           braw[k][0] = __ldg(chunk8(ra.ab_in, N, j, BOFF + c0));
           braw[k][1] = __ldg(chunk8(ra.ab_in, N, j, BOFF + c0 + 8));
@@ -475,7 +476,8 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
           float fv[Q];
 #pragma unroll
           for (int q = 0; q < Q; ++q)
-            fv[q] = __ldg(ra.f_post + q * ps + geo_nbr(p, -ex(q), -ey(q)));
+            fv[q] = __ldg(ra.f_post + q * ps +
+                          checked(geo_nbr(p, -ex(q), -ey(q)), base, base + N, stw));
           const Moments mm = moments9(fv);
           const float usq15 = 1.5f * (mm.ux * mm.ux + mm.uy * mm.uy);
           const float tau = geo.tau(p, ra.tau, ra.taus);
