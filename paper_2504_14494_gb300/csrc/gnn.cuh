@@ -83,6 +83,31 @@ __device__ __forceinline__ float gelu(float z) {
   const float hz = 0.5f * z;
   return fmaf(hz, tanh_fast(u), hz);
 }
+// Two GELUs with Blackwell's packed FP32 pair arithmetic (FMUL2/FFMA2: one
+// instruction for both lanes); same formula as gelu().
+__device__ __forceinline__ float2 gelu2(float2 z) {
+  const float2 c0 = make_float2(0.7978845608028654f, 0.7978845608028654f);
+  const float2 c1 = make_float2(0.0356774081363001f, 0.0356774081363001f);
+  const float2 h = make_float2(0.5f, 0.5f);
+  const float2 u = __fmul2_rn(z, __ffma2_rn(c1, __fmul2_rn(z, z), c0));
+  const float2 hz = __fmul2_rn(h, z);
+  return __ffma2_rn(hz, make_float2(tanh_fast(u.x), tanh_fast(u.y)), hz);
+}
+// v[c] <- act(v[c] + b[c]) for c < n (n even), GELU in packed pairs.
+__device__ __forceinline__ void bias_act(float* v, const float* b, int n, bool relu) {
+  if (relu) {
+#pragma unroll
+    for (int c = 0; c < n; ++c) v[c] = fmaxf(v[c] + b[c], 0.0f);
+    return;
+  }
+#pragma unroll
+  for (int c = 0; c < n; c += 2) {
+    const float2 z = __fadd2_rn(make_float2(v[c], v[c + 1]), make_float2(b[c], b[c + 1]));
+    const float2 g = gelu2(z);
+    v[c] = g.x;
+    v[c + 1] = g.y;
+  }
+}
 // GELU and its derivative.
 __device__ __forceinline__ float gelu_grad(float z) {
   const float z2 = z * z;
