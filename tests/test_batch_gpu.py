@@ -96,13 +96,14 @@ def test_batched_run_equals_per_lattice_runs(lbmlib, cuda, tmp_path):
 
 
 def test_stack_and_table_geometry_agree_bitwise(lbmlib, cuda):
-    """Lattices whose rows are whole 128-node tiles, stepped alone by
-    lbm_step_gnn (stack geometry) and together by the batched run (table
-    geometry, lattice found by binary search): the same arithmetic in the
-    same order, so bitwise equal."""
+    """Lattices stepped alone by lbm_step_gnn (stack geometry, positions by
+    multiply-high division) and together by the batched run (table geometry,
+    lattice found by binary search): the same arithmetic in the same order,
+    so bitwise equal."""
     import torch
     L = lbmlib
-    lat = [(128, 6, 1, 0.7), (256, 3, 1, 0.62), (384, 2, 1, 0.9)]
+    lat = [(128, 6, 1, 0.7), (256, 3, 1, 0.62), (384, 2, 1, 0.9), (64, 8, 1, 0.75),
+           (32, 4, 1, 0.8), (96, 12, 1, 0.66)]
     theta = inputs.xavier_params(19, s_df=1e-2, bias_scale=0.1)
     params = torch.from_numpy(theta).to(cuda)
     packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=cuda)

@@ -85,10 +85,10 @@ def test_forward_matches_oracle(lbmlib, cuda, nb, ny, nx):
         assert e <= 2e-2, (r, e)
 
 
-# (1, 6, 128), (2, 3, 256): rows of whole 128-node tiles (tile-aligned rows,
-# x and y wrap, 2 lattices)
+# (1, 6, 128), (2, 3, 256): rows of whole 128-node tiles; (1, 8, 64),
+# (2, 4, 32), (1, 12, 96): sides multiples of 32 x 4 (x and y wrap, 2 lattices)
 @pytest.mark.parametrize("nb,ny,nx", [(1, 16, 16), (2, 5, 7), (1, 64, 64), (1, 6, 128),
-                                      (2, 3, 256)])
+                                      (2, 3, 256), (1, 8, 64), (2, 4, 32), (1, 12, 96)])
 def test_step_gnn_matches_oracle(lbmlib, cuda, nb, ny, nx):
     import torch
     L = lbmlib
