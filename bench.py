@@ -44,6 +44,13 @@ NCU_TRAFFIC = {
     #     python bench.py --only bgk --steps 10 --warmup 3      (4096 x 4096, one launch)
     "bgk_step_x4": {"bytes_per_launch": 604044544 + 547293952,
                     "src_sha": "73ddfc6fddc151022938a0730e3eed432c1fd6803934835b201a9fd12f4cf21a"},
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+    #     --clock-control none -k regex:"gnn_(encode|round)_kernel" -s 3 -c 3
+    #     python bench.py --only gnn --steps 20 --warmup 3   (one GNN-LBM step, 1024 x 1024:
+    #     encoder + 2 rounds; key file gnn_fwd.cu)
+    "lbm_step_gnn": {"bytes_per_launch": (37825536 + 206303232) + (270710528 + 218478592)
+                     + (306585344 + 27377152), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
+                     "src_sha": "4bc8d7fd45c8dce546cd97f79b0ea5ff636f035ae75ce3040336fa885fedb1cd"},
 }
 
 
@@ -379,11 +386,15 @@ def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False, theta=None, label
     peak = GELU_PER_CLK_SM * 152 * 2.07e9 / 1e9
     ach = EDGE_GELUS_PER_NODE * n * n / (res["gnn"]["ms_per_step"] / 1e3) / 1e9
     mlp_only = int(round(float(theta[-1].item()))) & 1
+    tr = NCU_TRAFFIC.get("lbm_step_gnn")
+    traffic = (tr["bytes_per_launch"] if tr and tr["nodes"] == n * n and not mlp_only
+               and tr["src_sha"] == _src_sha(tr["file"]) else None)
     return {"workload": f"tgv_gnn_{n}x{n}", "re": GNN_RE, "tau": round(tau, 5), "u0": U0,
             "roofline": None if mlp_only else {
                 "bound": "alu", "kernel": "lbm_step_gnn (gnn_encode_kernel + 2 x gnn_round_kernel)",
                 "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "G edge-feature GELU/s",
-                "frac": round(ach / peak, 4), "traffic": None},
+                "frac": round(ach / peak, 4), "traffic": traffic,
+                "traffic_note": "DRAM bytes of one step (3 kernels), ncu"},
             "weights": label,
             "steps_timed": kk, "steps_run": args.warmup + kk,
             "mlups_gnn": res["gnn"]["mlups"], "mlups_bgk_same_lattice": res["bgk"]["mlups"],
