@@ -338,6 +338,22 @@ GELU_PER_CLK_SM = 128.0 / 7.0
 EDGE_GELUS_PER_NODE = 2 * 8 * 64
 
 
+def _sm_count(dev):
+    import torch
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
+def _max_sm_hz(dev):
+    """Maximum SM clock of the device (nvidia-smi), else GB300's 2,070 MHz."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(dev.index or 0),
+                              "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        return float(out.splitlines()[0]) * 1e6
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return 2.07e9
+
+
 def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False, theta=None, label="xavier"):
     """GNN-LBM MLUPS on the 1024^2 TGV (Re = 1000, u0 = 0.05) beside BGK MLUPS
     on the same lattice, and both TGV velocity L2 errors after the same number
@@ -383,7 +399,7 @@ def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False, theta=None, label
                      "status": st}
     if only:
         return res
-    peak = GELU_PER_CLK_SM * 152 * 2.07e9 / 1e9
+    peak = GELU_PER_CLK_SM * _sm_count(dev) * _max_sm_hz(dev) / 1e9
     ach = EDGE_GELUS_PER_NODE * n * n / (res["gnn"]["ms_per_step"] / 1e3) / 1e9
     mlp_only = int(round(float(theta[-1].item()))) & 1
     tr = NCU_TRAFFIC.get("lbm_step_gnn")
@@ -392,6 +408,8 @@ def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False, theta=None, label
     return {"workload": f"tgv_gnn_{n}x{n}", "re": GNN_RE, "tau": round(tau, 5), "u0": U0,
             "roofline": None if mlp_only else {
                 "bound": "alu", "kernel": "lbm_step_gnn (gnn_encode_kernel + 2 x gnn_round_kernel)",
+                "peak_basis": f"{GELU_PER_CLK_SM:.2f} edge GELUs/clock/SM x {_sm_count(dev)} SMs "
+                              f"x {_max_sm_hz(dev) / 1e6:.0f} MHz (FP16 pipe, 7 ops per pair)",
                 "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "G edge-feature GELU/s",
                 "frac": round(ach / peak, 4), "traffic": traffic,
                 "traffic_note": "DRAM bytes of one step (3 kernels), ncu"},

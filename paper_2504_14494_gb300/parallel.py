@@ -16,7 +16,14 @@ update exchanges data between ranks:
     the ranks' pairs), then every rank applies the same AdamW update, so the
     parameter vectors stay identical.
 
-A single lattice split over several GPUs (halo exchange) is not provided.
+  * one large lattice split over ranks (`SlabLattice`): each rank owns a slab
+    of rows plus `halo` ghost rows on each side; a step is one ghost-row
+    exchange with the two neighbouring ranks (the only data-path
+    communication: 9 x halo x nx values each way) followed by the ordinary
+    periodic step on the padded slab, which leaves every owned row exact
+    (the step reads rows at most `halo` away: 1 for BGK, 3 for the GNN step,
+    which streams and then passes messages twice) and only the ghost rows
+    stale until the next exchange.
 
 Every function here works with world size 1 (no process group) and with any
 backend; the host logic is exercised with `gloo` on CPU tensors.
@@ -154,3 +161,79 @@ class DataParallelTrainer:
 
     def theta(self):
         return self.params.cpu().numpy().copy()
+
+
+class SlabLattice:
+    """One periodic nx x ny lattice split into row slabs over the ranks of
+    `group`: rank r owns rows [ny r / P, ny (r + 1) / P) and keeps them with
+    `halo` ghost rows below and above in a [9, rows + 2 halo, nx] tensor
+    (`f`).  `step(step_fn)` exchanges the ghost rows with the neighbouring
+    ranks (periodic in y) and applies step_fn, a periodic step on a
+    [9, R, nx] population tensor returning the stepped tensor.  With one
+    rank the ghost rows come from the slab's own periodic wrap."""
+
+    def __init__(self, nx, ny, halo, device="cpu", dtype=None, group=None):
+        import torch
+        self.group = group
+        self.rank, self.size = rank_and_size(group)
+        self.nx, self.ny, self.halo = nx, ny, halo
+        self.r0 = ny * self.rank // self.size
+        self.r1 = ny * (self.rank + 1) // self.size
+        self.rows = self.r1 - self.r0
+        if self.rows < halo:
+            raise ValueError("every rank needs at least `halo` rows")
+        self.f = torch.zeros((9, self.rows + 2 * halo, nx), device=device,
+                             dtype=dtype or torch.float32)
+
+    def load(self, full):
+        """Owned rows from a full [9, ny, nx] state (a tensor on any device)."""
+        self.f[:, self.halo:self.halo + self.rows] = full[:, self.r0:self.r1].to(self.f)
+
+    def interior(self):
+        return self.f[:, self.halo:self.halo + self.rows]
+
+    def exchange(self):
+        """Ghost rows below <- the previous rank's top `halo` owned rows,
+        ghost rows above <- the next rank's bottom `halo` owned rows."""
+        import torch
+        h, R = self.halo, self.rows
+        top = self.f[:, R:R + h].contiguous()        # my top owned rows
+        bottom = self.f[:, h:2 * h].contiguous()      # my bottom owned rows
+        dist = _dist()
+        if dist is None or self.size == 1:
+            self.f[:, :h] = top
+            self.f[:, R + h:] = bottom
+            return
+        prev = (self.rank - 1) % self.size
+        nxt = (self.rank + 1) % self.size
+        below = torch.empty_like(top)
+        above = torch.empty_like(bottom)
+        ops = [dist.P2POp(dist.isend, top, nxt, self.group, 0),
+               dist.P2POp(dist.isend, bottom, prev, self.group, 1),
+               dist.P2POp(dist.irecv, below, prev, self.group, 0),
+               dist.P2POp(dist.irecv, above, nxt, self.group, 1)]
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+        self.f[:, :h] = below
+        self.f[:, R + h:] = above
+
+    def step(self, step_fn):
+        self.exchange()
+        self.f = step_fn(self.f)
+
+    def gather(self):
+        """The full [9, ny, nx] state on every rank (all-gather of the slabs)."""
+        import torch
+        dist = _dist()
+        mine = self.interior().contiguous()
+        if dist is None or self.size == 1:
+            return mine.clone()
+        counts = [self.ny * (r + 1) // self.size - self.ny * r // self.size
+                  for r in range(self.size)]
+        width = max(counts)  # all-gather wants equal shapes: pad the slabs
+        padded = torch.zeros((9, width, self.nx), device=mine.device, dtype=mine.dtype)
+        padded[:, :self.rows] = mine
+        parts = [torch.empty_like(padded) for _ in counts]
+        dist.all_gather(parts, padded, group=self.group)
+        return torch.cat([p[:, :c] for p, c in zip(parts, counts)], dim=1)
+

@@ -312,3 +312,41 @@ def test_data_parallel_trainer_alone_equals_fused_step(lbmlib, cuda):
     assert lbmlib.lbm_get_status() == 0
     assert torch.equal(a.params, b.params)
     assert torch.equal(a.packed, b.packed)
+
+
+def test_slab_lattice_on_one_gpu_equals_full_lattice(lbmlib, cuda):
+    """The row-slab decomposition of one lattice (ghost rows + the periodic
+    step on the padded slab) with one rank on the GPU: BGK (1 ghost row) and
+    the GNN step (3 ghost rows) through the C ABI equal the full-lattice
+    steps bitwise."""
+    import torch
+    from paper_2504_14494_gb300.parallel import SlabLattice
+    L = lbmlib
+    nx, ny, tau = 64, 24, 0.7
+    f = torch.from_numpy(_state(1, ny, nx, seed=9)[:, 0].copy()).to(cuda)
+    theta = inputs.xavier_params(11, s_df=1e-3)  # a network that keeps the state finite
+    _, pk = _dev_params(L, theta, cuda)
+
+    def bgk(g):
+        out = torch.empty_like(g)
+        L.lbm_step_bgk(g, out, None, L.shape(nx, g.shape[1]), tau)
+        return out
+
+    def gnn(g):
+        out = torch.empty_like(g)
+        s = L.shape(nx, g.shape[1])
+        ws = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+        L.lbm_step_gnn(g, out, s, tau, None, pk, None, ws)
+        return out
+
+    for fn, halo in ((bgk, 1), (gnn, 3)):
+        slab = SlabLattice(nx, ny, halo, device=cuda)
+        slab.load(f.view(9, ny, nx))
+        full = f.view(9, ny, nx).clone()
+        for _ in range(3):
+            slab.step(fn)
+            full = fn(full)
+        assert torch.isfinite(full).all()
+        assert torch.equal(slab.gather(), full), halo
+    assert L.lbm_get_status() == 0
+

@@ -139,3 +139,72 @@ def test_two_gloo_ranks():
             for p in ctx.processes:
                 p.kill()
             pytest.fail("the gloo ranks did not finish within 300 s")
+
+
+def _oracle_step_fn(kind, theta=None, tau=0.7):
+    """A periodic step on a [9, R, nx] torch tensor through the oracle."""
+    import torch
+    from oracle import gnn, lbm
+
+    def fn(f):
+        a = f.numpy()
+        out = lbm.bgk_step(a, tau) if kind == "bgk" else gnn.gnn_step(a, theta, tau)
+        return torch.from_numpy(np.ascontiguousarray(out))
+    return fn
+
+
+def _full_state(nx, ny, seed):
+    from oracle import lbm
+    f = lbm.tgv_init(nx, ny, 1.0, 0.04, 2 * np.pi / nx, 2 * np.pi / ny)
+    return f * inputs.perturbation(f.shape, seed, 2e-2)
+
+
+def _slab_worker(rank, port, size, result_q):
+    import torch
+    import torch.distributed as dist
+    from oracle import gnn, lbm
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=size, timeout=datetime.timedelta(seconds=60))
+    try:
+        full = _full_state(12, 10, 3)
+        theta = inputs.xavier_params(5, s_df=1e-2, bias_scale=0.1)
+        for kind, halo, steps in (("bgk", 1, 4), ("gnn", 3, 2)):
+            slab = parallel.SlabLattice(12, 10, halo, dtype=torch.float64)
+            slab.load(torch.from_numpy(full))
+            for _ in range(steps):
+                slab.step(_oracle_step_fn(kind, theta))
+            got = slab.gather().numpy()
+            ref = full
+            for _ in range(steps):
+                ref = lbm.bgk_step(ref, 0.7) if kind == "bgk" else gnn.gnn_step(ref, theta, 0.7)
+            if kind == "bgk":
+                assert np.array_equal(got, ref), kind   # the same FP64 operations per node
+            else:
+                assert np.allclose(got, ref, rtol=1e-12, atol=1e-15), kind
+        result_q.put((rank, "ok"))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("size", [1, 2, 3])
+def test_slab_decomposition_equals_single_domain(size):
+    """One 12 x 10 lattice split into row slabs over 1-3 gloo ranks: ghost-row
+    exchange + the periodic step on each padded slab reproduces the
+    single-domain oracle run (BGK: 1 ghost row, bitwise; GNN step: 3 ghost
+    rows, to FP64 rounding of the batched matrix products)."""
+    pytest.importorskip("torch")
+    import time
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.SimpleQueue()
+    procs = mp.start_processes(_slab_worker, args=(_free_port(), size, q), nprocs=size,
+                               join=False, start_method="spawn")
+    deadline = time.monotonic() + 300
+    while not procs.join(timeout=5):
+        if time.monotonic() > deadline:
+            for p in procs.processes:
+                p.kill()
+            pytest.fail("the gloo ranks did not finish within 300 s")
+    got = sorted(q.get() for _ in range(size))
+    assert got == [(r, "ok") for r in range(size)]
+
