@@ -297,6 +297,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_kind": peak_kind, "kernel": "bgk_step_x4",
                      "algorithmic_bytes_per_launch": BYTES_PER_NODE * nodes},
         "tau_sweep": sweep,
+        "tgv64": small_tgv_bench(L, dev),
         "e2e": {"value": round(nodes / (e2e_ms / 1e3) / 1e6, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": 9 * nodes * 4, "d2h_bytes_per_step": 5 * 8},
         "clocks": clk.summary(),
@@ -307,6 +308,41 @@ def run_ours(args, rank, world, local_rank):
         out["cpu_baseline"] = cpu_baseline()
         out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores()
     return out
+
+
+def small_tgv_bench(L, dev, n=64, tau=0.8, u0=0.01, steps=1000):
+    """The 64^2 Taylor-Green workload: 1000 BGK steps (one call), the
+    velocity L2 error against the closed form, the kinetic-energy error
+    against E0 exp(-4 nu k^2 t), and the mass / momentum drift of the FP64
+    totals; its MLUPS are latency-bound (147 KB per buffer) and not a
+    bandwidth figure."""
+    import torch
+    s = L.shape(n, n)
+    k = 2 * np.pi / n
+    f0 = torch.empty(9 * n * n, device=dev)
+    L.lbm_init_tgv(f0, s, 1.0, u0, k, k, False)
+    t0 = torch.zeros(5, dtype=torch.float64, device=dev)
+    L.lbm_moments(f0, s, None, None, None, t0)
+    f1, tmp = torch.empty_like(f0), torch.empty_like(f0)
+    tot = torch.zeros(5, dtype=torch.float64, device=dev)
+    L.lbm_step_bgk(f0, f1, tmp, s, tau, nsteps=10)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    L.lbm_step_bgk(f0, f1, tmp, s, tau, nsteps=steps, totals=tot)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    a, b = t0.cpu().numpy(), tot.cpu().numpy()
+    nu = (tau - 0.5) / 3.0
+    e_ref = a[3] * np.exp(-4.0 * nu * k * k * steps)
+    return {"workload": f"tgv_bgk_{n}x{n}", "tau": tau, "u0": u0, "steps": steps,
+            "mlups": round(n * n * steps / (ms / 1e3) / 1e6, 1),
+            "velocity_l2_error": tgv_l2(L, f1, s, n, u0, tau, steps, dev),
+            "energy_rel_error": float(abs(b[3] - e_ref) / e_ref),
+            "mass_rel_drift": float(abs(b[0] - a[0]) / a[0]),
+            "momentum_drift": [float(b[1] - a[1]), float(b[2] - a[2])],
+            "status": L.lbm_get_status()}
 
 
 def tgv_l2(L, f, s, n, u0, tau, t, dev):
@@ -458,13 +494,19 @@ def train_bench(args, L, dev, stream, variants=(0, 2, 3)):
     ms_step = e0.elapsed_time(e1) / kk
     del tr
     thetas, runs = {}, {}
-    for var in variants:
+    # (variant, lr, weight decay): lr 1e-4 without decay for the networks
+    # used below, and the default network at AdamW lr 1e-3, decay 1e-2
+    plan = [(v, 1e-4, 0.0) for v in variants] + [(0, 1e-3, 1e-2)]
+    for var, lr, wd in plan:
         th = inputs.xavier_params(0, s_df=1e-4, variant=var)
         th[38272:38922] = 0.0
-        small = Trainer(dev, theta=th, lr=1e-4, wd=0.0, seed=1, n=64, batch=16, episode=64)
+        small = Trainer(dev, theta=th, lr=lr, wd=wd, seed=1, n=64, batch=16, episode=64)
+        curve = []
         t0 = time.perf_counter()
-        for _ in range(3000):
+        for i in range(3000):
             small.step()
+            if i % 250 == 0 or i == 2999:
+                curve.append([i + 1, small.loss.item()])  # Eq. 4 loss before step i+1's update
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
         held = PairStream(dev, n=64, batch=16, m=4, episode=24, seed=12345)
@@ -475,17 +517,20 @@ def train_bench(args, L, dev, stream, variants=(0, 2, 3)):
             a, b, t = held.next()
             lg += ev.loss_of(small.params, a, b, t)
             lb += ev.loss_of(zero, a, b, t)
-        thetas[var] = small.theta()
-        runs[str(var)] = {"steps": 3000, "wall_s": round(t_train, 2),
-                          "held_out_eq4_loss_gnn": lg / 48, "held_out_eq4_loss_bgk": lb / 48,
-                          "ratio": round(lg / lb, 4)}
+        key = str(var) if lr == 1e-4 else f"{var}_lr{lr:g}_wd{wd:g}"
+        if lr == 1e-4:
+            thetas[var] = small.theta()
+        runs[key] = {"steps": 3000, "lr": lr, "weight_decay": wd, "wall_s": round(t_train, 2),
+                     "held_out_eq4_loss_gnn": lg / 48, "held_out_eq4_loss_bgk": lb / 48,
+                     "ratio": round(lg / lb, 4), "loss_curve": curve}
     info = {"workload": "train_64x256x256_refined4",
             "ms_per_train_step_incl_datagen": round(ms_full, 3),
             "ms_per_fused_train_step": round(ms_step, 3),
             "samples_per_s": round(64 / (ms_full / 1e3), 1),
             "node_updates_per_s_M": round(64 * 256 * 256 / (ms_step / 1e3) / 1e6, 1),
             "short_runs_by_variant": runs,
-            "short_run_data": "64^2 coarse pairs from 256^2 refined runs, 16 per batch, lr 1e-4"}
+            "short_run_data": "64^2 coarse pairs from 256^2 refined runs, 16 per batch; "
+                              "loss_curve: [step, Eq. 4 loss of that step's batch]"}
     return thetas, info
 
 

@@ -333,11 +333,9 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
     const GeoPos p = geo.pos(base + nn);
     if constexpr (AH) {  // h -> shared memory, A = h W_a^T -> tensor memory columns 0..63
 #pragma unroll
-      for (int s0 = 0; s0 < FPT; s0 += SL) {
-        float h[SL];
-#pragma unroll
-        for (int c = 0; c < SL / 8; ++c) unpack_bf16x8(hnext[s0 / 8 + c], h + 8 * c);
-        st_row<SL>(H, node, f0 + s0, h);
+      for (int c = 0; c < FPT / 8; ++c) {  // the BF16 words go to the swizzled row as they are
+        const int chunk = (f0 >> 3) + c;
+        *reinterpret_cast<uint4*>(H + node * 128 + ((chunk ^ (node & 7)) << 4)) = hnext[c];
       }
       if (LBM_PREFETCH && tile + stride < ntiles) load_h(tile + stride);
       if (!mlp_only && !run([&] {
@@ -407,11 +405,12 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
         }
       }
       float av[16];
+      const __half2 half_h2 = __float2half2_rn(0.5f);
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        const float2 t = __half22float2(acc[c]);
-        av[2 * c] = 0.5f * t.x;
-        av[2 * c + 1] = 0.5f * t.y;
+        const float2 t = __half22float2(__hmul2(acc[c], half_h2));
+        av[2 * c] = t.x;
+        av[2 * c + 1] = t.y;
       }
       const int ch = c0 >> 3;
       *reinterpret_cast<uint4*>(Ag + node * 128 + ((ch ^ (node & 7)) << 4)) = pack_bf16x8(av);
