@@ -124,6 +124,42 @@ __device__ __forceinline__ float sigmoid_acc(float y) { return 0.5f * (1.0f + ta
 enum : int { VAR_MLP_ONLY = 1, VAR_CONSERVATIVE = 2 };
 __device__ __forceinline__ int variant_of(const float* nrm) { return __float2int_rn(nrm[25]); }
 __device__ __forceinline__ float act(float z, bool relu) { return relu ? fmaxf(z, 0.0f) : gelu(z); }
+// gelu_grad() of two values with packed FP32 pair arithmetic.
+__device__ __forceinline__ float2 gelu_grad2(float2 z) {
+  const float2 c0 = make_float2(0.7978845608028654f, 0.7978845608028654f);
+  const float2 c1 = make_float2(0.0356774081363001f, 0.0356774081363001f);
+  const float2 c3 = make_float2(0.1070322244089003f, 0.1070322244089003f);
+  const float2 h = make_float2(0.5f, 0.5f), one = make_float2(1.0f, 1.0f);
+  const float2 z2 = __fmul2_rn(z, z);
+  const float2 u = __fmul2_rn(z, __ffma2_rn(c1, z2, c0));
+  const float2 t = make_float2(tanh_fast(u.x), tanh_fast(u.y));
+  const float2 omt = __ffma2_rn(make_float2(-t.x, -t.y), t, one);  // 1 - t^2
+  const float2 q = __fmul2_rn(__fmul2_rn(__fmul2_rn(h, z), omt), __ffma2_rn(c3, z2, c0));
+  return __fadd2_rn(__ffma2_rn(h, t, h), q);
+}
+// v[c] <- act(v[c] + b[c]) for c < n (n even): g receives the activations,
+// d the derivatives at the same points (either may be NULL).
+__device__ __forceinline__ void act_and_grad(const float* z, const float* b, int n, bool relu,
+                                             float* g, float* d) {
+#pragma unroll
+  for (int c = 0; c < n; c += 2) {
+    const float2 x = b ? __fadd2_rn(make_float2(z[c], z[c + 1]), make_float2(b[c], b[c + 1]))
+                       : make_float2(z[c], z[c + 1]);
+    if (relu) {
+      if (g) g[c] = fmaxf(x.x, 0.0f), g[c + 1] = fmaxf(x.y, 0.0f);
+      if (d) d[c] = x.x > 0.0f ? 1.0f : 0.0f, d[c + 1] = x.y > 0.0f ? 1.0f : 0.0f;
+    } else {
+      if (g) {
+        const float2 r = gelu2(x);
+        g[c] = r.x, g[c + 1] = r.y;
+      }
+      if (d) {
+        const float2 r = gelu_grad2(x);
+        d[c] = r.x, d[c + 1] = r.y;
+      }
+    }
+  }
+}
 __device__ __forceinline__ float act_grad(float z, bool relu) {
   return relu ? (z > 0.0f ? 1.0f : 0.0f) : gelu_grad(z);
 }

@@ -610,6 +610,11 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
   copy_g2s(sm + eb::W1F, packed + K::W1F, 3712);
   __syncthreads();
   ones_row(sm + eb::YT, 80, 76);
+  // 1 / sigma (the forward encoder normalises by this product too), beside
+  // the tensor-core context
+  float* isg = reinterpret_cast<float*>(sm + eb::SH + 64);
+  if (threadIdx.x < NFEAT)
+    isg[threadIdx.x] = 1.0f / reinterpret_cast<const float*>(sm + eb::NORM)[NFEAT + threadIdx.x];
   TcCtx tc;
   tc_setup(sh, tc);
   const float* w1 = reinterpret_cast<const float*>(sm + eb::W1F);
@@ -637,11 +642,11 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
     const Moments m = moments9(fv);
     float xh[NFEAT];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) xh[q] = (fv[q] - nrm[q]) / nrm[NFEAT + q];
-    xh[9] = (m.rho - nrm[9]) / nrm[NFEAT + 9];
-    xh[10] = (m.ux - nrm[10]) / nrm[NFEAT + 10];
-    xh[11] = (m.uy - nrm[11]) / nrm[NFEAT + 11];
-    float z1[32];
+    for (int q = 0; q < Q; ++q) xh[q] = (fv[q] - nrm[q]) * isg[q];
+    xh[9] = (m.rho - nrm[9]) * isg[9];
+    xh[10] = (m.ux - nrm[10]) * isg[10];
+    xh[11] = (m.uy - nrm[11]) * isg[11];
+    float z1[32];  // after the layer: GELU'(z1), the only use of z1 left
     {
       float g[32];
 #pragma unroll
@@ -650,8 +655,8 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
 #pragma unroll
         for (int j = 0; j < NFEAT; ++j) z = fmaf(w1[(f0 + c) * NFEAT + j], xh[j], z);
         z1[c] = z;
-        g[c] = act(z, relu);
       }
+      act_and_grad(z1, nullptr, 32, relu, g, z1);
       st_row32(G1, node, f0, g);
       st_col<32>(YT, 80, f0, node, g);
     }
@@ -667,8 +672,9 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
       float z2[32], g0[32];
       tmem_ld32(lb + f0, z2);
       ld_pf32(dh0, N, nn, f0, g0);
+      act_and_grad(z2, b2 + f0, 32, relu, nullptr, d);
 #pragma unroll
-      for (int c = 0; c < 32; ++c) d[c] = on ? g0[c] * act_grad(z2[c] + b2[f0 + c], relu) : 0.0f;
+      for (int c = 0; c < 32; ++c) d[c] = on ? g0[c] * d[c] : 0.0f;
     }
     st_row32(DZ2, node, f0, d);
     st_col<32>(XT, 128, f0, node, d);
@@ -680,7 +686,7 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
     }
     tmem_ld32(lb + f0, d);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) d[c] *= act_grad(z1[c], relu);  // dz1 (0 for idle nodes)
+    for (int c = 0; c < 32; ++c) d[c] *= z1[c];  // dz1 = dg1 GELU'(z1) (0 for idle nodes)
     st_col<32>(XT, 128, HID + f0, node, d);
     if (df) {
       float px[NFEAT];
@@ -706,7 +712,7 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
       float dx[NFEAT];
 #pragma unroll
       for (int j = 0; j < NFEAT; ++j)
-        dx[j] = (dxh[node * NFEAT + j] + dxh[(128 + node) * NFEAT + j]) / nrm[NFEAT + j];
+        dx[j] = (dxh[node * NFEAT + j] + dxh[(128 + node) * NFEAT + j]) * isg[j];
       const float ir = 1.0f / m.rho;
 #pragma unroll
       for (int q = 0; q < Q; ++q)
