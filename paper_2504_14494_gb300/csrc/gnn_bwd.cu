@@ -51,6 +51,23 @@ __device__ __forceinline__ void ones_row(uint8_t* op, int R, int row) {
   }
 }
 
+// Sum over the 32 lanes of v[0..31] (lane-private values): afterwards lane l
+// holds the sum of v[l] over the warp (31 shuffles; halves the vector per step).
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool upper = lane & w;  // keep the upper half of the current range
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const float send = upper ? v[i] : v[i + w];
+      const float keep = upper ? v[i + w] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0];
+}
+
 __device__ __forceinline__ void ld_f32x32(const float* p, float* v) {
   const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
@@ -232,14 +249,21 @@ __global__ void __launch_bounds__(256, 2) gnn_head_bwd_kernel(
 
 // ---------------------------------------------------------------------------
 // Round backward, part 1 (per node): recompute z_n = W_n [h; a] + b_n,
-// dz_n = dh_out * GELU'(z_n), d[h; a] = dz_n W_n; accumulate dW_n and db_n.
-// Outputs dh_part = dh_out + d[h; a]_h and da = d[h; a]_a (FP32).
+// dz_n = dh_out * GELU'(z_n), d[h; a] = dz_n W_n; accumulate dW_n (tensor
+// cores, [h; a]^T dz_n) and db_n (sum of dz_n, in registers by a butterfly
+// reduction over each warp's nodes).  Outputs dh_part = dh_out + d[h; a]_h
+// and da = d[h; a]_a (FP32).
 namespace rb1 {
-constexpr uint32_t HA = 0, HAT = 32768, DZ = 65536, DZT = 81920, ONES = 114688, WN = 118784,
-                   WNT = 135168, BN = 151552, SH = 151808, BYTES = 151936;
+// U holds [h; a] node-major (A of the z_n recompute) until that MMA is done,
+// then dz node-major (16 KB) and dz transposed (16 KB, 64 rows per K block).
+constexpr uint32_t U = 0, HAT = 32768, WN = 65536, WNT = 81920, BN = 98304, DBR = 98560,
+                   SH = 99584, BYTES = 99712;
 }
+#ifndef LBM_RB1_CTAS
+#define LBM_RB1_CTAS 2  // resident CTAs per SM
+#endif
 
-__global__ void __launch_bounds__(256, 1) gnn_round_bwd1_kernel(
+__global__ void __launch_bounds__(256, LBM_RB1_CTAS) gnn_round_bwd1_kernel(
     const __nv_bfloat16* __restrict__ h_in, const __nv_bfloat16* __restrict__ a_in,
     const float* __restrict__ dh_out, float* __restrict__ dh_part, float* __restrict__ da,
     int round, float* __restrict__ G, Shape s, const uint8_t* __restrict__ packed, unsigned* stw) {
@@ -248,36 +272,35 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd1_kernel(
   TcShared* sh = reinterpret_cast<TcShared*>(sm + rb1::SH);
   const uint8_t* kr = packed + K::round_base(round);
   const bool mlp_only = variant_of(reinterpret_cast<const float*>(packed + K::NORM)) & VAR_MLP_ONLY;
-  zero_smem(sm + rb1::DZT, rb1::WN - rb1::DZT);  // DZT (upper rows stay 0) and ONES
   copy_g2s(sm + rb1::WN, kr + K::WN, 16384);
   copy_g2s(sm + rb1::WNT, kr + K::WNT, 16384);
   copy_g2s(sm + rb1::BN, kr + K::BN, 256);
   __syncthreads();
-  ones_row(sm + rb1::ONES, 16, 0);
   TcCtx tc;
   tc_setup(sh, tc);
   const float* bn = reinterpret_cast<const float*>(sm + rb1::BN);
-  uint8_t* HA = sm + rb1::HA;
+  uint8_t* HA = sm + rb1::U;
+  uint8_t* DZ = sm + rb1::U;            // after the z_n MMA
+  uint8_t* DZT = sm + rb1::U + 16384;   // after the z_n MMA
   uint8_t* HAT = sm + rb1::HAT;
-  uint8_t* DZ = sm + rb1::DZ;
-  uint8_t* DZT = sm + rb1::DZT;
   const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
   const uint32_t lb = lane_base(tc.tmem);
   const int64_t N = (int64_t)s.nb * s.ny * s.nx;
   const int64_t ntiles = (N + TILE - 1) / TILE;
+  float dbacc = 0.0f;  // lane l: running sum of dz[f0 + l] over this warp's nodes
   bool first = true, ok = true;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t n = tile * TILE + node;
     const bool on = n < N;
     const int64_t nn = on ? n : N - 1;
     {
-      float h[32], a[32];
-      ld_pb32(h_in, N, nn, f0, h);
-      ld_pb32(a_in, N, nn, f0, a);
-      st_row32(HA, node, f0, h);
-      st_row32(HA + 16384, node, f0, a);
-      st_col<32>(HAT, 128, f0, node, h);
-      st_col<32>(HAT, 128, HID + f0, node, a);
+      float v[32];
+      ld_pb32(h_in, N, nn, f0, v);
+      st_row32(HA, node, f0, v);
+      st_col<32>(HAT, 128, f0, node, v);
+      ld_pb32(a_in, N, nn, f0, v);
+      st_row32(HA + 16384, node, f0, v);
+      st_col<32>(HAT, 128, HID + f0, node, v);
     }
     if (!tc_run(sh, tc, stw, [&] {
           umma_128xN(tc.tmem, smem_u32(HA), 16384, smem_u32(sm + rb1::WN), 8192, 2, 64, false);
@@ -285,49 +308,56 @@ __global__ void __launch_bounds__(256, 1) gnn_round_bwd1_kernel(
       ok = false;
       break;
     }
-    float dz[32], dho[32];
-    tmem_ld32(lb + f0, dz);
-    ld_pf32(dh_out, N, nn, f0, dho);
+    {
+      float dz[32], dho[32];
+      tmem_ld32(lb + f0, dz);
+      ld_pf32(dh_out, N, nn, f0, dho);
+      act_and_grad(dz, bn + f0, 32, false, nullptr, dz);  // GELU'(z_n), packed pairs
 #pragma unroll
-    for (int c = 0; c < 32; ++c)
-      dz[c] = (on && !mlp_only) ? dho[c] * gelu_grad(dz[c] + bn[f0 + c]) : 0.0f;
-    st_row32(DZ, node, f0, dz);
-    st_col<32>(DZT, 128, f0, node, dz);
+      for (int c = 0; c < 32; ++c) dz[c] = (on && !mlp_only) ? dho[c] * dz[c] : 0.0f;
+      // the z_n MMA has read [h; a]: its space now takes dz
+      st_row32(DZ, node, f0, dz);
+      st_col<32>(DZT, 64, f0, node, dz);
+      dbacc += warp_transpose_sum(dz);
+    }
     const bool acc = !first;
     if (!tc_run(sh, tc, stw, [&] {
           umma_128xN(tc.tmem, smem_u32(DZ), 0, smem_u32(sm + rb1::WNT), 0, 1, 128, false);
-          umma_128xN(tc.tmem + 128, smem_u32(HAT), 16384, smem_u32(DZT), 16384, 2, 64, acc);
-          umma_128xN(tc.tmem + 192, smem_u32(DZT), 16384, smem_u32(sm + rb1::ONES), 2048, 2, 16,
-                     acc);
+          umma_128xN(tc.tmem + 128, smem_u32(HAT), 16384, smem_u32(DZT), 8192, 2, 64, acc);
         })) {
       ok = false;
       break;
     }
     first = false;
-    float d[32];
-    tmem_ld32(lb + f0, d);
-    if (on) {
+    {
+      float d[32], dho[32];
+      tmem_ld32(lb + f0, d);           // warp-collective: every lane takes part
+      ld_pf32(dh_out, N, nn, f0, dho);  // again (an L2 hit): fewer values live across the MMA
 #pragma unroll
       for (int c = 0; c < 32; ++c) d[c] += dho[c];
-      st_pf32(dh_part, N, n, f0, d);
+      if (on) st_pf32(dh_part, N, n, f0, d);
+      tmem_ld32(lb + HID + f0, d);
+      if (on) st_pf32(da, N, n, f0, d);
     }
-    tmem_ld32(lb + HID + f0, d);
-    if (on) st_pf32(da, N, n, f0, d);
     tc_fence_before();
     __syncthreads();
   }
   if (ok) {
-    // D_wn[i][o] at columns 128..191 (row i = input feature of [h; a]);
-    // D_bn[o][0] at column 192.
+    // D_wn[i][o] at columns 128..191 (row i = input feature of [h; a])
     const int row = 32 * ((threadIdx.x >> 5) & 3) + (threadIdx.x & 31);
     float* g = G + (int64_t)blockIdx.x * P::TRAINABLE + P::ROUND0 + round * P::ROUND_SIZE;
     float v[32];
     tmem_ld32(lb + 128 + f0, v);
     for (int c = 0; c < 32; ++c) g[P::NODE_W + (f0 + c) * 128 + row] = v[c];
-    if (half == 0) {
-      float u[16];
-      tmem_ld16(lb + 192, u);
-      if (row < HID) g[P::NODE_B + row] = u[0];
+    // db_n: the 4 warps of a feature half hold disjoint node sets; fixed order
+    float* dbr = reinterpret_cast<float*>(sm + rb1::DBR);  // [8 warps][32]
+    dbr[(threadIdx.x >> 5) * 32 + (threadIdx.x & 31)] = dbacc;
+    __syncthreads();
+    if (threadIdx.x < HID) {
+      const int hh = threadIdx.x >> 5, l = threadIdx.x & 31;
+      float t = 0.0f;
+      for (int q = 0; q < 4; ++q) t += dbr[(hh * 4 + q) * 32 + l];
+      g[P::NODE_B + threadIdx.x] = t;
     }
   }
   tc_teardown(sh, tc);
@@ -351,23 +381,6 @@ constexpr uint32_t DAB = 0, DABT = 32768, HT = 65536, WABT = 86016, CK = 102400,
 #ifndef LBM_RB2_GROUP
 #define LBM_RB2_GROUP 4  // neighbours whose loads are in flight together
 #endif
-
-// Sum over the 32 lanes of v[0..31] (lane-private values): afterwards lane l
-// holds the sum of v[l] over the warp (31 shuffles; halves the vector per step).
-__device__ __forceinline__ float warp_transpose_sum(float (&v)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
-    const bool upper = lane & w;  // keep the upper half of the current range
-#pragma unroll
-    for (int i = 0; i < w; ++i) {
-      const float send = upper ? v[i] : v[i + w];
-      const float keep = upper ? v[i + w] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-    }
-  }
-  return v[0];
-}
 
 __global__ void __launch_bounds__(256, LBM_RB2_CTAS) gnn_round_bwd2_kernel(
     const __half* __restrict__ ab, const float* __restrict__ da,
@@ -819,7 +832,7 @@ cudaError_t launch_gnn_backward(const BackwardLaunch& bl, const Shape& s, const 
     {
       const uint32_t bytes = rb1::BYTES + 1024;
       if ((e = set_smem(gnn_round_bwd1_kernel, bytes)) != cudaSuccess) return e;
-      gnn_round_bwd1_kernel<<<grad_grid(N, 1), 256, bytes, st>>>(hs[r], as[r], bl.dh[0], bl.dh[1],
+      gnn_round_bwd1_kernel<<<grad_grid(N, LBM_RB1_CTAS), 256, bytes, st>>>(hs[r], as[r], bl.dh[0], bl.dh[1],
                                                                  bl.da, r, bl.G, s, packed, stw);
     }
     {
