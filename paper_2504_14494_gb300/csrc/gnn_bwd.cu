@@ -606,12 +606,16 @@ __global__ void __launch_bounds__(256, LBM_RB2_CTAS) gnn_round_bwd2_kernel(
 // dW2, db2 (rows 0..63) and dW1, db1 (rows 64..127).  Optionally the input
 // gradient dL/df_pre through x_hat (f_i, rho and u = j / rho).
 namespace eb {
-constexpr uint32_t G1 = 0, DZ2 = 16384, XT = 32768, YT = 65536, W2 = 86016, W2T = 94208,
-                   W1F = 102400, B1 = 105472, B2 = 105728, NORM = 105984, DXH = 106112,
-                   SH = 118400, BYTES = 118528;
+// U holds, one after the other within a tile, g1 node-major (A of the z2
+// MMA), dz2 node-major (A of the dg1 MMA) and the df partial sums.
+constexpr uint32_t U = 0, XT = 16384, YT = 49152, W2 = 69632, W2T = 77824, W1F = 86016,
+                   B1 = 89088, B2 = 89344, NORM = 89600, SH = 89728, BYTES = 89856;
 }
+#ifndef LBM_EB_CTAS
+#define LBM_EB_CTAS 2  // resident CTAs per SM
+#endif
 
-__global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
+__global__ void __launch_bounds__(256, LBM_EB_CTAS) gnn_encode_bwd_kernel(
     const float* __restrict__ f_pre, const float* __restrict__ dh0, float* __restrict__ df,
     float* __restrict__ G, Shape s, const uint8_t* __restrict__ packed, unsigned* stw) {
   extern __shared__ uint8_t smem_raw[];
@@ -634,9 +638,9 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
   const float* b1 = reinterpret_cast<const float*>(sm + eb::B1);
   const float* b2 = reinterpret_cast<const float*>(sm + eb::B2);
   const float* nrm = reinterpret_cast<const float*>(sm + eb::NORM);
-  float* dxh = reinterpret_cast<float*>(sm + eb::DXH);
-  uint8_t* G1 = sm + eb::G1;
-  uint8_t* DZ2 = sm + eb::DZ2;
+  float* dxh = reinterpret_cast<float*>(sm + eb::U);  // after the dg1 MMA
+  uint8_t* G1 = sm + eb::U;
+  uint8_t* DZ2 = sm + eb::U;                           // after the z2 MMA
   uint8_t* XT = sm + eb::XT;
   uint8_t* YT = sm + eb::YT;
   const int node = threadIdx.x & 127, half = threadIdx.x >> 7, f0 = half * 32;
@@ -659,9 +663,11 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
     xh[9] = (m.rho - nrm[9]) * isg[9];
     xh[10] = (m.ux - nrm[10]) * isg[10];
     xh[11] = (m.uy - nrm[11]) * isg[11];
-    float z1[32];  // after the layer: GELU'(z1), the only use of z1 left
+    // GELU'(z1), the only later use of z1, kept as FP16 pairs (values in
+    // [-0.2, 1.2]; dz1 is rounded to BF16 for the weight-gradient MMA anyway)
+    __half2 gp1[16];
     {
-      float g[32];
+      float z1[32], g[32];
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
         float z = b1[f0 + c];
@@ -670,6 +676,8 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
         z1[c] = z;
       }
       act_and_grad(z1, nullptr, 32, relu, g, z1);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) gp1[c] = __floats2half2_rn(z1[2 * c], z1[2 * c + 1]);
       st_row32(G1, node, f0, g);
       st_col<32>(YT, 80, f0, node, g);
     }
@@ -699,7 +707,11 @@ __global__ void __launch_bounds__(256, 1) gnn_encode_bwd_kernel(
     }
     tmem_ld32(lb + f0, d);
 #pragma unroll
-    for (int c = 0; c < 32; ++c) d[c] *= z1[c];  // dz1 = dg1 GELU'(z1) (0 for idle nodes)
+    for (int c = 0; c < 16; ++c) {  // dz1 = dg1 GELU'(z1) (0 for idle nodes)
+      const float2 gp = __half22float2(gp1[c]);
+      d[2 * c] *= gp.x;
+      d[2 * c + 1] *= gp.y;
+    }
     st_col<32>(XT, 128, HID + f0, node, d);
     if (df) {
       float px[NFEAT];
@@ -845,7 +857,7 @@ cudaError_t launch_gnn_backward(const BackwardLaunch& bl, const Shape& s, const 
   {
     const uint32_t bytes = eb::BYTES + 1024;
     if ((e = set_smem(gnn_encode_bwd_kernel, bytes)) != cudaSuccess) return e;
-    gnn_encode_bwd_kernel<<<grad_grid(N, 1), 256, bytes, st>>>(bl.f_pre, bl.dh[0], bl.df, bl.G, s,
+    gnn_encode_bwd_kernel<<<grad_grid(N, LBM_EB_CTAS), 256, bytes, st>>>(bl.f_pre, bl.dh[0], bl.df, bl.G, s,
                                                                packed, stw);
   }
   grad_reduce_kernel<<<(P::TRAINABLE + 255) / 256, 256, 0, st>>>(bl.G, GRAD_ROWS, bl.grad);
