@@ -48,9 +48,9 @@ NCU_TRAFFIC = {
     #     --clock-control none -k regex:"gnn_(encode|round)_kernel" -s 3 -c 3
     #     python bench.py --only gnn --steps 20 --warmup 3   (one GNN-LBM step, 1024 x 1024:
     #     encoder + 2 rounds; key file gnn_fwd.cu)
-    "lbm_step_gnn": {"bytes_per_launch": (37825536 + 206303232) + (270710528 + 218478592)
-                     + (306585344 + 27377152), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
-                     "src_sha": "4bc8d7fd45c8dce546cd97f79b0ea5ff636f035ae75ce3040336fa885fedb1cd"},
+    "lbm_step_gnn": {"bytes_per_launch": (37825280 + 206667776) + (270285056 + 218373376)
+                     + (306583296 + 27248128), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
+                     "src_sha": "c6f89232a844ebae7ead6d547c8c08c2a9274b6c62f1254fc741e215e269d5f8"},
 }
 
 
