@@ -192,6 +192,18 @@ enum { LBM_GNN_MLP_ONLY = 1, LBM_GNN_CONSERVATIVE = 2 };
 LBM_API size_t gnn_param_count(void);
 LBM_API size_t gnn_trainable_count(void);
 
+/* Fills a parameter vector in HOST memory (gnn_param_count() floats) with a
+ * starting point for training (Sec. 2.2 names the layers, not their
+ * initialisation): every weight matrix Xavier-uniform, U(-b, b) with
+ * b = sqrt(6 / (fan_in + fan_out)), every bias 0, drawn in parameter order
+ * from a SplitMix64 stream seeded with `seed` (the same seed gives the same
+ * vector on any machine); the input normaliser mu / sigma at the rest-state
+ * populations (4/9, 1/9 x4, 1/36 x4) with a 10 % scale, rho 1 with scale
+ * 0.01, u 0 with scale 0.01; the Delta f scale s_df (> 0, finite); and the
+ * variant flags (0..3, see above).  Host-only: no GPU is needed.  Returns
+ * LBM_ERR_ARG for a NULL vector, a bad s_df or unknown flags. */
+LBM_API int gnn_params_init_xavier(float* params_host, uint64_t seed, float s_df, int variant);
+
 /* Bytes of the packed device image of the parameters. */
 LBM_API size_t gnn_packed_bytes(void);
 

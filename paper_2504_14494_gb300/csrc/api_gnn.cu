@@ -41,6 +41,51 @@ constexpr int64_t STEP_WS_PER_NODE = 512;
 extern "C" {
 
 size_t gnn_param_count(void) { return P::TOTAL; }
+
+int gnn_params_init_xavier(float* params, uint64_t seed, float s_df, int variant) {
+  if (!params || !std::isfinite(s_df) || !(s_df > 0.0f) || variant < 0 || variant > 3)
+    return LBM_ERR_ARG;
+  uint64_t state = seed;
+  auto uniform = [&state]() {  // SplitMix64 (Steele, Lea and Flood 2014), top 24 bits
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 40) * (1.0 / 16777216.0);  // [0, 1)
+  };
+  auto matrix = [&](int off, int rows, int cols) {
+    const double b = std::sqrt(6.0 / (double)(rows + cols));
+    for (int i = 0; i < rows * cols; ++i) params[off + i] = (float)((2.0 * uniform() - 1.0) * b);
+  };
+  auto zeros = [&](int off, int n) {
+    for (int i = 0; i < n; ++i) params[off + i] = 0.0f;
+  };
+  matrix(P::ENC1_W, HID, NFEAT);
+  zeros(P::ENC1_B, HID);
+  matrix(P::ENC2_W, HID, HID);
+  zeros(P::ENC2_B, HID);
+  for (int r = 0; r < 2; ++r) {
+    const int base = P::ROUND0 + r * P::ROUND_SIZE;
+    matrix(base + P::EDGE_W, HID, 2 * HID + 2);
+    zeros(base + P::EDGE_B, HID);
+    matrix(base + P::NODE_W, HID, 2 * HID);
+    zeros(base + P::NODE_B, HID);
+  }
+  matrix(P::HEAD_W, NOUT, HID);
+  zeros(P::HEAD_B, NOUT);
+  const float rest[Q] = {4.0f / 9, 1.0f / 9, 1.0f / 9, 1.0f / 9, 1.0f / 9,
+                         1.0f / 36, 1.0f / 36, 1.0f / 36, 1.0f / 36};
+  for (int q = 0; q < Q; ++q) {
+    params[P::MU + q] = rest[q];
+    params[P::SIGMA + q] = 0.1f * rest[q];
+  }
+  params[P::MU + 9] = 1.0f;
+  params[P::MU + 10] = params[P::MU + 11] = 0.0f;
+  params[P::SIGMA + 9] = params[P::SIGMA + 10] = params[P::SIGMA + 11] = 0.01f;
+  params[P::S_DF] = s_df;
+  params[P::VARIANT] = (float)variant;
+  return LBM_OK;
+}
 size_t gnn_trainable_count(void) { return P::TRAINABLE; }
 size_t gnn_packed_bytes(void) { return K::TOTAL; }
 

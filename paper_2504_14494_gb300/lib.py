@@ -58,6 +58,7 @@ _SIGS = {
                                         ctypes.c_float, ctypes.c_int, _VP, _VP]),
     "gnn_param_count": (ctypes.c_size_t, []),
     "gnn_trainable_count": (ctypes.c_size_t, []),
+    "gnn_params_init_xavier": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_float, ctypes.c_int]),
     "gnn_packed_bytes": (ctypes.c_size_t, []),
     "gnn_pack": (ctypes.c_int, [_VP, _VP, _VP]),
     "gnn_step_workspace_bytes": (ctypes.c_size_t, [lbm_shape]),
@@ -206,6 +207,21 @@ def lbm_step_bgk_host(f_in_host, f_out_host, s, tau, taus_host=None, nsteps=1,
 
 
 # --- GNN path ------------------------------------------------------------------------
+def gnn_params_init_xavier(params_host, seed, s_df=1e-4, variant=0):
+    """Fills a host float32 array / CPU tensor of gnn_param_count() values
+    (see include/lbmgnn.h); returns it."""
+    import numpy as np
+    if isinstance(params_host, np.ndarray):
+        if params_host.dtype != np.float32 or not params_host.flags.c_contiguous:
+            raise ValueError("params_host must be a contiguous float32 array")
+        addr = params_host.ctypes.data
+    else:
+        addr = ptr(params_host)
+    check(load().gnn_params_init_xavier(addr, int(seed), float(s_df), int(variant)),
+          "gnn_params_init_xavier")
+    return params_host
+
+
 def gnn_param_count():
     return load().gnn_param_count()
 
