@@ -30,10 +30,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS, plain BGK vs GNN-LBM on 1 GB300, at stated TGV velocity L2 error"
-N_SIDE = 4096
-U0 = 0.05
-TAU = 0.8
-TAU_SWEEP = (0.8, 0.5614, 0.5005)
+from paper_2504_14494_gb300 import workloads as W  # noqa: E402  (sizes, taus, seeds)
+
+N_SIDE = W.TGV_4096.n
+U0 = W.TGV_4096.u0
+TAU = W.TGV_4096.tau
+TAU_SWEEP = W.TGV_4096.tau_sweep
 BYTES_PER_NODE = 72  # 9 FP32 loads + 9 FP32 stores
 
 # DRAM bytes per launch from one ncu capture of the kernel, keyed by the
@@ -310,7 +312,8 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-def small_tgv_bench(L, dev, n=64, tau=0.8, u0=0.01, steps=1000):
+def small_tgv_bench(L, dev, n=W.TGV_64.n, tau=W.TGV_64.tau, u0=W.TGV_64.u0,
+                    steps=W.TGV_64.steps):
     """The 64^2 Taylor-Green workload: 1000 BGK steps (one call), the
     velocity L2 error against the closed form, the kinetic-energy error
     against E0 exp(-4 nu k^2 t), and the mass / momentum drift of the FP64
@@ -362,8 +365,8 @@ def tgv_l2(L, f, s, n, u0, tau, t, dev):
                             / (uxa ** 2 + uya ** 2).sum()).item())
 
 
-GNN_SIDE = 1024
-GNN_RE = 1000.0
+GNN_SIDE = W.TGV_GNN_1024.n
+GNN_RE = W.TGV_GNN_1024.re
 # Elementwise roofline of the message passing: each edge message costs 7
 # packed-FP16 pipe operations per pair of features (z = A + c + B: 2, u: 3,
 # accumulate z + z tanh u: 2) plus one tanh.approx.f16x2.  The FP16 pipe
@@ -472,7 +475,9 @@ def train_bench(args, L, dev, stream, variants=(0, 2, 3)):
     from paper_2504_14494_gb300.train import Evaluator, PairStream, Trainer
     theta = inputs.xavier_params(0, s_df=1e-4)
     theta[38272:38922] = 0.0
-    tr = Trainer(dev, theta=theta.copy(), lr=1e-4, wd=0.0, seed=1, n=256, batch=64, episode=64)
+    T = W.TRAIN_64x256
+    tr = Trainer(dev, theta=theta.copy(), lr=T.lr, wd=T.weight_decay, seed=T.seed, n=T.n,
+                 batch=T.batch, m=T.refine, episode=T.episode)
     for _ in range(3):
         tr.step()
     torch.cuda.synchronize()
@@ -534,7 +539,7 @@ def train_bench(args, L, dev, stream, variants=(0, 2, 3)):
     return thetas, info
 
 
-def batch_bench(args, L, dev, stream, theta, n_lat=512, seed=7):
+def batch_bench(args, L, dev, stream, theta, n_lat=W.BATCH_512.lattices, seed=W.BATCH_512.seed):
     """The serving-style batch: 512 TGV lattices, sides log-uniform in
     [32, 1024], Re ~ U[100, 5000], u0 ~ U[0.01, 0.08], first half plain BGK,
     second half GNN-corrected (trained weights); 1,000 steps of all lattices
@@ -542,7 +547,8 @@ def batch_bench(args, L, dev, stream, theta, n_lat=512, seed=7):
     also timed alone (100 steps) for its own MLUPS."""
     import torch
     from paper_2504_14494_gb300 import inputs
-    draws = inputs.batch_lattices(n_lat, seed)
+    B = W.BATCH_512
+    draws = inputs.batch_lattices(n_lat, seed, B.side_lo, B.side_hi, B.re_lo, B.re_hi)
     packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=dev)
     L.gnn_pack(torch.from_numpy(theta).to(dev), packed)
 
@@ -571,7 +577,7 @@ def batch_bench(args, L, dev, stream, theta, n_lat=512, seed=7):
         finally:
             L.lbm_batch_plan_destroy(plan)
 
-    kk = 1000 if args.steps >= 1000 else max(2, args.steps)
+    kk = B.steps if args.steps >= B.steps else max(2, args.steps)
     n, ms, st = run(lambda d: True, kk)
     halves = {}
     for name, sel in (("bgk_half", lambda d: not d["gnn"]), ("gnn_half", lambda d: d["gnn"])):

@@ -9,5 +9,6 @@ collision of arXiv 2504.14494 behind the C ABI of liblbmgnn.so.
   parallel -- multi-rank host logic: sharding, timing aggregation,
               data-parallel training (one gradient all-reduce per step)
   checkpoint -- CRC-checked save/restore of training state
+  workloads -- the benchmark workloads (sizes, relaxation times, seeds)
 """
 from . import lib  # noqa: F401
