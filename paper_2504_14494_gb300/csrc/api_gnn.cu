@@ -137,6 +137,7 @@ int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape shape, float tau, co
   r0.h_in = h0;
   r0.ab_in = b0;
   r0.a_from_h = true;
+  r0.h_skip = h0;
   r0.h_out = h1;
   r0.ab_out = b1;
   r0.round = 0;
@@ -145,6 +146,7 @@ int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape shape, float tau, co
   r1.h_in = h1;
   r1.ab_in = b1;
   r1.a_from_h = true;
+  r1.h_skip = h0;
   r1.f_post = f_in;
   r1.f_out = f_out;
   r1.tau = tau;

@@ -200,16 +200,20 @@ __global__ void __launch_bounds__(256, LBM_ENC_CTAS) gnn_encode_kernel(
     if (on && h0_out) st_pb32(h0_out, N, n, f0, g);
     st_row32(X, node, f0, g);  // the MMA that read X has completed
     // A | B = h0 [W_a; W_b]^T ([N][128]), or B alone ([N][64]) when BONLY
-    if (!tc_run(sh, tc, stw, [&] {
-          umma_128xN(tc.tmem, smem_u32(X), 0, smem_u32(sm + enc::WAB) + (BONLY ? 8192 : 0), 0, 1,
-                     BONLY ? 64 : 128, false);
-        }))
-      break;
-    tmem_ld32(lb + f0, g);
-    if (on) st_ph32(ab_out, N, n, f0, g);
-    if (!BONLY) {
-      tmem_ld32(lb + HID + f0, g);
-      if (on) st_ph32(ab_out, N, n, HID + f0, g);
+    // (inference; nothing at all for the MLP-only network, which passes no
+    // messages)
+    if (!(BONLY && relu)) {
+      if (!tc_run(sh, tc, stw, [&] {
+            umma_128xN(tc.tmem, smem_u32(X), 0, smem_u32(sm + enc::WAB) + (BONLY ? 8192 : 0), 0, 1,
+                       BONLY ? 64 : 128, false);
+          }))
+        break;
+      tmem_ld32(lb + f0, g);
+      if (on) st_ph32(ab_out, N, n, f0, g);
+      if (!BONLY) {
+        tmem_ld32(lb + HID + f0, g);
+        if (on) st_ph32(ab_out, N, n, HID + f0, g);
+      }
     }
 #if !LBM_PREFETCH
     if (tile + gridDim.x < ntiles) load_f(tile + gridDim.x, fnext);
@@ -248,6 +252,9 @@ struct RoundArgs {
   float tau;
   const float* taus;           // per-lattice tau or NULL
   int round;
+  // Inference path: h0.  For the MLP-only network (no message passing) the
+  // inner round then returns at once and the last round reads h0 from here.
+  const __nv_bfloat16* h_skip;
 };
 
 #ifndef LBM_ROUND_CTAS
@@ -270,6 +277,9 @@ struct RoundArgs {
 template <int MODE, int TPN, int NG, bool AH, class Geo>
 __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kernel(
     RoundArgs ra, Geo geo, const uint8_t* __restrict__ packed, unsigned* stw) {
+  if (MODE == 0 && ra.h_skip &&
+      (variant_of(reinterpret_cast<const float*>(packed + K::NORM)) & VAR_MLP_ONLY))
+    return;  // MLP-only network: nothing to pass between rounds
   constexpr int FPT = HID / TPN;
   constexpr int SL = FPT < 32 ? FPT : 32;  // feature slice of the epilogues
   constexpr int GT = 128 * TPN;            // threads per group
@@ -314,6 +324,7 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
   const int64_t first = (int64_t)blockIdx.x * NG + grp, stride = (int64_t)gridDim.x * NG;
   const int variant = variant_of(nrm);
   const bool mlp_only = variant & VAR_MLP_ONLY;
+  const __nv_bfloat16* h_src = (mlp_only && ra.h_skip) ? ra.h_skip : ra.h_in;
   auto run = [&](auto issue) { return tc_run_group(tc, stw, grp, GT, issue); };
 
   // raw BF16 h (features f0.. of node `t * TILE + node`) of tile t
@@ -322,7 +333,7 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
     const int64_t m = t * TILE + node;
     const int64_t mm = m < N ? m : N - 1;
 #pragma unroll
-    for (int c = 0; c < FPT / 8; ++c) hnext[c] = __ldg(chunk8(ra.h_in, N, mm, f0 + 8 * c));
+    for (int c = 0; c < FPT / 8; ++c) hnext[c] = __ldg(chunk8(h_src, N, mm, f0 + 8 * c));
   };
   if (AH && first < ntiles) load_h(first);
 
@@ -346,7 +357,7 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
 #pragma unroll
       for (int s0 = 0; s0 < FPT; s0 += SL) {
         float h[SL];
-        ld_pb<SL>(ra.h_in, N, nn, f0 + s0, h);
+        ld_pb<SL>(h_src, N, nn, f0 + s0, h);
         st_row<SL>(H, node, f0 + s0, h);
       }
     }
@@ -564,7 +575,7 @@ static cudaError_t round_any(int mode, const RoundLaunch& rl, const Geo& geo, in
   const int64_t cta_tiles = (N + (int64_t)TILE * LBM_ROUND_GROUPS - 1) / ((int64_t)TILE * LBM_ROUND_GROUPS);
   const unsigned grid = grid_for(cta_tiles * TILE, per_sm >= 2 ? LBM_ROUND_CTAS : per_sm);
   RoundArgs ra{rl.h_in, rl.ab_in, rl.h_out, rl.a_out, rl.ab_out, rl.y_out, rl.f_post, rl.f_out,
-               rl.tau, rl.taus, rl.round};
+               rl.tau, rl.taus, rl.round, rl.h_skip};
   if (rl.a_from_h) {
     switch (mode) {
       case 0: return round_t<0, true>(ra, geo, grid, packed, stw, st);
@@ -608,6 +619,7 @@ cudaError_t launch_gnn_step_table(const float* f_in, float* f_out, const LatDesc
   r0.h_in = h0;
   r0.ab_in = b0;
   r0.a_from_h = true;
+  r0.h_skip = h0;
   r0.h_out = h1;
   r0.ab_out = b1;
   r0.round = 0;
@@ -616,6 +628,7 @@ cudaError_t launch_gnn_step_table(const float* f_in, float* f_out, const LatDesc
   r1.h_in = h1;
   r1.ab_in = b1;
   r1.a_from_h = true;
+  r1.h_skip = h0;
   r1.f_post = f_in;
   r1.f_out = f_out;
   r1.round = 1;

@@ -21,6 +21,9 @@ struct RoundLaunch {
   float tau = 1.0f;
   const float* taus = nullptr;
   int round = 0;
+  // inference path: h0, read by the last round of the MLP-only network
+  // (whose inner round is then skipped); NULL elsewhere
+  const __nv_bfloat16* h_skip = nullptr;
 };
 
 cudaError_t launch_gnn_pack(const float* params, uint8_t* packed, cudaStream_t st);

@@ -95,16 +95,18 @@ def test_batched_run_equals_per_lattice_runs(lbmlib, cuda, tmp_path):
         L.lbm_batch_plan_destroy(plan)
 
 
-def test_stack_and_table_geometry_agree_bitwise(lbmlib, cuda):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_stack_and_table_geometry_agree_bitwise(lbmlib, cuda, variant):
     """Lattices stepped alone by lbm_step_gnn (stack geometry, positions by
     multiply-high division) and together by the batched run (table geometry,
     lattice found by binary search): the same arithmetic in the same order,
-    so bitwise equal."""
+    so bitwise equal.  Variant 1 (MLP only) takes the short path of both:
+    no edge terms, no inner round."""
     import torch
     L = lbmlib
     lat = [(128, 6, 1, 0.7), (256, 3, 1, 0.62), (384, 2, 1, 0.9), (64, 8, 1, 0.75),
            (32, 4, 1, 0.8), (96, 12, 1, 0.66)]
-    theta = inputs.xavier_params(19, s_df=1e-2, bias_scale=0.1)
+    theta = inputs.xavier_params(19, s_df=1e-2, bias_scale=0.1, variant=variant)
     params = torch.from_numpy(theta).to(cuda)
     packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=cuda)
     L.gnn_pack(params, packed)
