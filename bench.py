@@ -50,9 +50,9 @@ NCU_TRAFFIC = {
     #     --clock-control none -k regex:"gnn_(encode|round)_kernel" -s 3 -c 3
     #     python bench.py --only gnn --steps 20 --warmup 3   (one GNN-LBM step, 1024 x 1024:
     #     encoder + 2 rounds; key file gnn_fwd.cu)
-    "lbm_step_gnn": {"bytes_per_launch": (37825280 + 206667776) + (270285056 + 218373376)
-                     + (306583296 + 27248128), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
-                     "src_sha": "c6f89232a844ebae7ead6d547c8c08c2a9274b6c62f1254fc741e215e269d5f8"},
+    "lbm_step_gnn": {"bytes_per_launch": (37824512 + 206253568) + (270561536 + 219437824)
+                     + (306546688 + 27308544), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
+                     "src_sha": "a901ff369a7c29f976506681b32bd683a0c21bbc8fc931169beaf15c26673a27"},
 }
 
 
