@@ -12,7 +12,7 @@ from gpu_util import to_dev
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(1, 1, 1), (1, 3, 5), (2, 5, 7), (1, 16, 24), (1, 6, 128), (3, 4, 130)]
+SHAPES = [(1, 1, 1), (1, 3, 5), (2, 5, 7), (1, 16, 24), (1, 6, 128), (3, 4, 130), (2, 8, 16)]
 
 
 def _state(nb, ny, nx, seed):

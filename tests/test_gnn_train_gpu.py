@@ -42,8 +42,10 @@ def _cos(a, b):
     return float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
 
 
-@pytest.mark.parametrize("nb,ny,nx", [(1, 4, 4), (1, 5, 3), (2, 8, 12), (1, 16, 24)])
+@pytest.mark.parametrize("nb,ny,nx", [(1, 4, 4), (1, 5, 3), (2, 8, 12), (1, 16, 24), (2, 8, 16),
+                                      (1, 16, 48)])
 def test_backward_matches_oracle(lbmlib, cuda, nb, ny, nx):
+
     import torch
     L = lbmlib
     theta = inputs.xavier_params(61 + nx, s_df=1e-2, bias_scale=0.1)
