@@ -39,6 +39,9 @@ class lbm_lattice_desc(ctypes.Structure):
 
 
 LBM_COLLIDE_BGK, LBM_COLLIDE_GNN = 0, 1
+# status codes (include/lbmgnn.h)
+(LBM_OK, LBM_ERR_ARG, LBM_ERR_ALIAS, LBM_ERR_SIZE, LBM_ERR_TAU, LBM_ERR_BLOB, LBM_ERR_CUDA,
+ LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT, LBM_ERR_BOUNDS, LBM_ERR_WORKSPACE) = range(0, -11, -1)
 
 
 _VP = ctypes.c_void_p
