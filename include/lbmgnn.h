@@ -65,7 +65,8 @@ LBM_API const char* lbm_status_string(int status);
 
 /* Waits for `stream`, then reads and clears the device status word of the
  * current device.  Returns LBM_OK, or the most severe of LBM_ERR_TIMEOUT,
- * LBM_ERR_BOUNDS, LBM_ERR_NONFINITE raised since the last call. */
+ * LBM_ERR_BOUNDS, LBM_ERR_BLOB, LBM_ERR_NONFINITE raised since the last
+ * call. */
 LBM_API int lbm_get_status(void* stream);
 
 /* Failure-detection self-test (no counterpart in the paper): launches one
@@ -209,7 +210,14 @@ LBM_API size_t gnn_packed_bytes(void);
 
 /* Converts the FP32 parameter vector (device, gnn_param_count() floats) into
  * the packed image the kernels read (device, gnn_packed_bytes() bytes,
- * 16-byte aligned).  Re-run after every change of the parameters. */
+ * 16-byte aligned).  Re-run after every change of the parameters.
+ * The image carries a validity word (layout version 1), written only when
+ * the vector's fixed values are usable: every mu finite, every sigma and
+ * s_df finite and > 0, variant one of 0..3; otherwise the pack raises
+ * LBM_ERR_BLOB in the status word.  Every kernel that reads an image checks
+ * the word first; given one without it (never packed, packed from invalid
+ * fixed values, or another buffer) it computes and writes nothing (a loss
+ * output becomes NaN) and raises LBM_ERR_BLOB in the status word. */
 LBM_API int gnn_pack(const float* params, void* packed, void* stream);
 
 /* Workspace bytes lbm_step_gnn needs for shape s (512 bytes per node: the

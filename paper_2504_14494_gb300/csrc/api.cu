@@ -110,6 +110,7 @@ int lbm_get_status(void* stream) {
   if (v != 0 && cudaMemset(w, 0, sizeof(v)) != cudaSuccess) return LBM_ERR_CUDA;
   if (v & ST_TIMEOUT) return LBM_ERR_TIMEOUT;
   if (v & ST_BOUNDS) return LBM_ERR_BOUNDS;
+  if (v & ST_BLOB) return LBM_ERR_BLOB;
   if (v & ST_NONFINITE) return LBM_ERR_NONFINITE;
   return LBM_OK;
 }

@@ -35,6 +35,7 @@ enum : unsigned {
   ST_NONFINITE = 1u << 0,
   ST_TIMEOUT = 1u << 1,
   ST_BOUNDS = 1u << 2,
+  ST_BLOB = 1u << 3,  // a kernel was given a packed parameter image without its validity word
 };
 unsigned* status_word();
 

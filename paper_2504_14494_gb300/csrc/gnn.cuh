@@ -47,7 +47,7 @@ namespace K {
 constexpr uint32_t W1F = 0;       // fp32 [64][12] (BF16-rounded values)
 constexpr uint32_t B1 = 3072;     // fp32 [64]
 constexpr uint32_t B2 = 3328;     // fp32 [64]
-constexpr uint32_t NORM = 3584;   // fp32 mu[12], sigma[12], s_df, variant, pad -> 32 floats
+constexpr uint32_t NORM = 3584;   // fp32 mu[12], sigma[12], s_df, variant, pad, validity word
 constexpr uint32_t BH = 3712;     // fp32 [16] (10 used)
 constexpr uint32_t WHF = 3776;    // fp32 [10][64] (BF16-rounded values)
 constexpr uint32_t W2 = 7168;     // SW128 [64 out x 64 in]
@@ -69,7 +69,22 @@ constexpr uint32_t BN = 67840;     // fp32 [64]
 constexpr uint32_t W1X = ROUND0 + 2 * ROUND_SIZE;  // 162816
 constexpr uint32_t TOTAL = W1X + 8192;              // 171008
 __host__ __device__ constexpr uint32_t round_base(int r) { return ROUND0 + r * ROUND_SIZE; }
+// Validity word of the image (slot 31 of NORM), written by the pack kernel
+// when the fixed values of the parameter vector are usable: "LBG1", layout
+// version 1.
+constexpr uint32_t MAGIC_SLOT = NORM + 31 * 4;
+constexpr uint32_t MAGIC = 0x4C424731u;
 }  // namespace K
+
+// Every kernel that reads a packed image checks its validity word first; on
+// a mismatch (an image never packed, or packed from invalid fixed values)
+// thread 0 of each CTA raises ST_BLOB and the whole CTA returns before any
+// other access, so nothing is computed from it.
+__device__ __forceinline__ bool blob_ok(const uint8_t* packed, unsigned* stw) {
+  if (__ldg(reinterpret_cast<const unsigned*>(packed + K::MAGIC_SLOT)) == K::MAGIC) return true;
+  if (threadIdx.x == 0 && stw) atomicOr(stw, (unsigned)ST_BLOB);
+  return false;
+}
 
 // ---- activations ----------------------------------------------------------------
 __device__ __forceinline__ float tanh_fast(float x) {

@@ -92,7 +92,12 @@ __device__ __forceinline__ void st_f32x32(float* p, const float* v) {
 __global__ void __launch_bounds__(256) gnn_collide_loss_kernel(
     const float* __restrict__ f_pre, const float* __restrict__ y, const float* __restrict__ tgt,
     Shape s, float tau, const float* __restrict__ taus, const uint8_t* __restrict__ packed,
-    double* __restrict__ lossp, float* __restrict__ dy, float* __restrict__ f_pred) {
+    double* __restrict__ lossp, float* __restrict__ dy, float* __restrict__ f_pred,
+    unsigned* stw) {
+  if (!blob_ok(packed, stw)) {  // no loss from an invalid image: NaN
+    if (threadIdx.x == 0) lossp[blockIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
+    return;
+  }
   const int64_t N = (int64_t)s.nb * s.ny * s.nx;
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool on = n < N;
@@ -175,6 +180,7 @@ constexpr uint32_t XT = 0, YT = 32768, WHF = 53248, DYS = 55808, SH = 60928, BYT
 __global__ void __launch_bounds__(256, 2) gnn_head_bwd_kernel(
     const float* __restrict__ dy, const __nv_bfloat16* __restrict__ h2, float* __restrict__ dh,
     float* __restrict__ G, Shape s, const uint8_t* __restrict__ packed, unsigned* stw) {
+  if (!blob_ok(packed, stw)) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   TcShared* sh = reinterpret_cast<TcShared*>(sm + hb::SH);
@@ -267,6 +273,7 @@ __global__ void __launch_bounds__(256, LBM_RB1_CTAS) gnn_round_bwd1_kernel(
     const __nv_bfloat16* __restrict__ h_in, const __nv_bfloat16* __restrict__ a_in,
     const float* __restrict__ dh_out, float* __restrict__ dh_part, float* __restrict__ da,
     int round, float* __restrict__ G, Shape s, const uint8_t* __restrict__ packed, unsigned* stw) {
+  if (!blob_ok(packed, stw)) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   TcShared* sh = reinterpret_cast<TcShared*>(sm + rb1::SH);
@@ -387,6 +394,7 @@ __global__ void __launch_bounds__(256, LBM_RB2_CTAS) gnn_round_bwd2_kernel(
     const float* __restrict__ dh_part, const __nv_bfloat16* __restrict__ h_in,
     float* __restrict__ dh_in, int round, float* __restrict__ G, Shape s,
     const uint8_t* __restrict__ packed, unsigned* stw) {
+  if (!blob_ok(packed, stw)) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   TcShared* sh = reinterpret_cast<TcShared*>(sm + rb2::SH);
@@ -618,6 +626,7 @@ constexpr uint32_t U = 0, XT = 16384, YT = 49152, W2 = 69632, W2T = 77824, W1F =
 __global__ void __launch_bounds__(256, LBM_EB_CTAS) gnn_encode_bwd_kernel(
     const float* __restrict__ f_pre, const float* __restrict__ dh0, float* __restrict__ df,
     float* __restrict__ G, Shape s, const uint8_t* __restrict__ packed, unsigned* stw) {
+  if (!blob_ok(packed, stw)) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   TcShared* sh = reinterpret_cast<TcShared*>(sm + eb::SH);
@@ -804,8 +813,10 @@ cudaError_t launch_collide_loss(const float* f_pre, const float* y, const float*
   const int64_t N = (int64_t)s.nb * s.ny * s.nx;
   const unsigned blocks = (unsigned)((N + 255) / 256);
   *nblk = (int)blocks;
+  unsigned* stw = status_word();
+  if (!stw) return cudaErrorInvalidDevice;
   gnn_collide_loss_kernel<<<blocks, 256, 0, st>>>(f_pre, y, tgt, s, tau, taus, packed, lossp, dy,
-                                                   f_pred);
+                                                   f_pred, stw);
   return cudaGetLastError();
 }
 

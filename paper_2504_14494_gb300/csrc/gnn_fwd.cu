@@ -30,7 +30,8 @@ __device__ __forceinline__ void put_sw(uint8_t* blk, int row, int k, float v) {
   *reinterpret_cast<__nv_bfloat16*>(blk + sw128_off(row, k)) = __float2bfloat16_rn(v);
 }
 
-__global__ void gnn_pack_kernel(const float* __restrict__ p, uint8_t* __restrict__ out) {
+__global__ void gnn_pack_kernel(const float* __restrict__ p, uint8_t* __restrict__ out,
+                                unsigned* stw) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
   float* w1f = reinterpret_cast<float*>(out + K::W1F);
@@ -39,8 +40,17 @@ __global__ void gnn_pack_kernel(const float* __restrict__ p, uint8_t* __restrict
     reinterpret_cast<float*>(out + K::B1)[e] = p[P::ENC1_B + e];
     reinterpret_cast<float*>(out + K::B2)[e] = p[P::ENC2_B + e];
   }
-  for (int e = tid; e < 32; e += nth)
+  for (int e = tid; e < 31; e += nth)
     reinterpret_cast<float*>(out + K::NORM)[e] = e < 26 ? p[P::MU + e] : 0.0f;
+  if (tid == 0) {  // the fixed values: finite mu, sigma > 0, s_df > 0, variant 0..3
+    bool ok = p[P::S_DF] > 0.0f && isfinite(p[P::S_DF]);
+    for (int i = 0; i < NFEAT; ++i)
+      ok = ok && isfinite(p[P::MU + i]) && p[P::SIGMA + i] > 0.0f && isfinite(p[P::SIGMA + i]);
+    const float v = p[P::VARIANT];
+    ok = ok && (v == 0.0f || v == 1.0f || v == 2.0f || v == 3.0f);
+    *reinterpret_cast<unsigned*>(out + K::MAGIC_SLOT) = ok ? K::MAGIC : 0u;
+    if (!ok) atomicOr(stw, (unsigned)ST_BLOB);
+  }
   for (int e = tid; e < 16; e += nth)
     reinterpret_cast<float*>(out + K::BH)[e] = e < NOUT ? p[P::HEAD_B + e] : 0.0f;
   for (int e = tid; e < NOUT * HID; e += nth)
@@ -109,6 +119,7 @@ template <bool PULL, bool BONLY, class Geo>
 __global__ void __launch_bounds__(256, LBM_ENC_CTAS) gnn_encode_kernel(
     const float* __restrict__ f, Geo geo, const uint8_t* __restrict__ packed,
     __nv_bfloat16* __restrict__ h0_out, __half* __restrict__ ab_out, unsigned* stw) {
+  if (!blob_ok(packed, stw)) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   TcShared* sh = reinterpret_cast<TcShared*>(sm + enc::SH);
@@ -277,6 +288,7 @@ struct RoundArgs {
 template <int MODE, int TPN, int NG, bool AH, class Geo>
 __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kernel(
     RoundArgs ra, Geo geo, const uint8_t* __restrict__ packed, unsigned* stw) {
+  if (!blob_ok(packed, stw)) return;
   if (MODE == 0 && ra.h_skip &&
       (variant_of(reinterpret_cast<const float*>(packed + K::NORM)) & VAR_MLP_ONLY))
     return;  // MLP-only network: nothing to pass between rounds
@@ -524,7 +536,9 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
 // ---------------------------------------------------------------------------
 // Launchers
 cudaError_t launch_gnn_pack(const float* params, uint8_t* packed, cudaStream_t st) {
-  gnn_pack_kernel<<<64, 256, 0, st>>>(params, packed);
+  unsigned* stw = status_word();
+  if (!stw) return cudaErrorInvalidDevice;
+  gnn_pack_kernel<<<64, 256, 0, st>>>(params, packed, stw);
   return cudaGetLastError();
 }
 
