@@ -348,7 +348,7 @@ LBM_API int gnn_train_step(const float* f_in, const float* f_target, lbm_shape s
 enum { LBM_COLLIDE_BGK = 0, LBM_COLLIDE_GNN = 1 };
 
 typedef struct {
-  int32_t nx, ny;     /* lattice size, each >= 1 */
+  int32_t nx, ny;     /* lattice size, each >= 1, nx * ny < 2^31 */
   int32_t collision;  /* LBM_COLLIDE_BGK or LBM_COLLIDE_GNN */
   float tau;          /* relaxation time, > 1/2 */
 } lbm_lattice_desc;

@@ -30,10 +30,11 @@ template <int NT>
 __global__ void __launch_bounds__(NT) bgk_batch_kernel(const float* __restrict__ fin,
                                                        float* __restrict__ fout,
                                                        const LatDesc* __restrict__ lat, int nlat,
-                                                       int64_t count, int64_t ps, unsigned* stw) {
+                                                       const int* __restrict__ hint, int64_t count,
+                                                       int64_t ps, unsigned* stw) {
   const int64_t g = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (g >= count) return;
-  const GeoTable geo{lat, 0, nlat, 0, count, ps};
+  const GeoTable geo{lat, 0, nlat, 0, count, ps, hint};
   const GeoPos p = geo.pos(g);
   float f[Q];
 #pragma unroll
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(256) tgv_init_table_kernel(float* __restrict__
                                                              int pc) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= count) return;
-  const GeoTable geo{lat, 0, nlat, 0, count, count};
+  const GeoTable geo{lat, 0, nlat, 0, count, count, nullptr};
   const GeoPos p = geo.pos(g);
   const double rho0 = prm[4 * p.b], u0 = prm[4 * p.b + 1], kx = prm[4 * p.b + 2],
                ky = prm[4 * p.b + 3];
@@ -130,22 +131,23 @@ int tune(const char* kernel, int64_t nodes, const std::vector<int>& cand, cudaSt
 }  // namespace
 
 cudaError_t launch_bgk_batch(const float* fin, float* fout, const LatDesc* lat, int nlat,
-                             int64_t count, int64_t ps, int block, cudaStream_t st) {
+                             const int* hint, int64_t count, int64_t ps, int block,
+                             cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
   switch (block) {
     case 128:
       bgk_batch_kernel<128><<<(unsigned)((count + 127) / 128), 128, 0, st>>>(fin, fout, lat, nlat,
-                                                                          count, ps, stw);
+                                                                          hint, count, ps, stw);
       break;
     case 512:
       bgk_batch_kernel<512><<<(unsigned)((count + 511) / 512), 512, 0, st>>>(fin, fout, lat, nlat,
-                                                                          count, ps, stw);
+                                                                          hint, count, ps, stw);
       break;
     default:
       bgk_batch_kernel<256><<<(unsigned)((count + 255) / 256), 256, 0, st>>>(fin, fout, lat, nlat,
-                                                                          count, ps, stw);
+                                                                          hint, count, ps, stw);
       break;
   }
   return cudaGetLastError();
@@ -159,6 +161,7 @@ struct lbm_batch_plan {
   int n = 0, n_bgk = 0, n_gnn = 0;
   std::vector<int64_t> offset_of_input;  // first node of input lattice i
   LatDesc* d_lat = nullptr;               // sorted: BGK group, then GNN group
+  int* d_hint = nullptr;                  // per 128-node block: lattice of its first node
   double* d_prm = nullptr;                // [n][4] TGV parameters (sorted order)
   std::vector<int> sorted_to_input;
   int64_t bgk_nodes = 0, gnn_nodes = 0, total = 0;
@@ -181,6 +184,7 @@ void plan_release(lbm_batch_plan* p) {
   if (p->cap) cudaStreamDestroy(p->cap);
   if (p->side) cudaStreamDestroy(p->side);
   if (p->d_lat) cudaFree(p->d_lat);
+  if (p->d_hint) cudaFree(p->d_hint);
   if (p->d_prm) cudaFree(p->d_prm);
   delete p;
 }
@@ -192,12 +196,14 @@ cudaError_t plan_step(lbm_batch_plan* p, const float* src, float* dst, const uin
                       __nv_bfloat16* ws, cudaStream_t s_bgk, cudaStream_t s_gnn) {
   cudaError_t e = cudaSuccess;
   if (p->n_bgk > 0) {
-    e = launch_bgk_batch(src, dst, p->d_lat, p->n_bgk, p->bgk_nodes, p->total, p->bgk_block,
+    e = launch_bgk_batch(src, dst, p->d_lat, p->n_bgk, p->d_hint, p->bgk_nodes, p->total,
+                         p->bgk_block,
                          s_bgk);
     if (e != cudaSuccess) return e;
   }
   if (p->n_gnn > 0) {
-    e = launch_gnn_step_table(src, dst, p->d_lat, p->n_bgk, p->n_gnn, p->bgk_nodes, p->gnn_nodes,
+    e = launch_gnn_step_table(src, dst, p->d_lat, p->n_bgk, p->n_gnn, p->d_hint, p->bgk_nodes,
+                              p->gnn_nodes,
                               p->total, packed, ws, s_gnn, p->gnn_per_sm);
   }
   return e;
@@ -214,7 +220,7 @@ int lbm_batch_plan_create(const lbm_lattice_desc* lattices, int n, lbm_batch_pla
   if (!lattices || n < 1) return LBM_ERR_ARG;
   for (int i = 0; i < n; ++i) {
     const auto& d = lattices[i];
-    if (d.nx < 1 || d.ny < 1) return LBM_ERR_SIZE;
+    if (d.nx < 1 || d.ny < 1 || (int64_t)d.nx * d.ny >= (int64_t(1) << 31)) return LBM_ERR_SIZE;
     if (d.collision != LBM_COLLIDE_BGK && d.collision != LBM_COLLIDE_GNN) return LBM_ERR_ARG;
     if (!std::isfinite(d.tau) || !(d.tau > 0.5f)) return LBM_ERR_TAU;
   }
@@ -246,8 +252,18 @@ int lbm_batch_plan_create(const lbm_lattice_desc* lattices, int n, lbm_batch_pla
     plan_release(p);
     return LBM_ERR_SIZE;
   }
+  // lattice of the first node of every 128-node block
+  std::vector<int> hint((size_t)((p->total + 127) / 128));
+  for (size_t blk = 0, lo = 0; blk < hint.size(); ++blk) {
+    const int64_t g = (int64_t)blk * 128;
+    while (lo + 1 < table.size() && table[lo + 1].offset <= g) ++lo;
+    hint[blk] = (int)lo;
+  }
   if (cudaGetDevice(&p->device) != cudaSuccess ||
       cudaMalloc(&p->d_lat, sizeof(LatDesc) * n) != cudaSuccess ||
+      cudaMalloc(&p->d_hint, sizeof(int) * hint.size()) != cudaSuccess ||
+      cudaMemcpy(p->d_hint, hint.data(), sizeof(int) * hint.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
       cudaMalloc(&p->d_prm, sizeof(double) * 4 * n) != cudaSuccess ||
       cudaMemcpy(p->d_lat, table.data(), sizeof(LatDesc) * n, cudaMemcpyHostToDevice) !=
           cudaSuccess ||
@@ -320,7 +336,8 @@ int lbm_batch_run(lbm_batch_plan* plan, const float* f_in, float* f_out, float* 
   if (!plan->bgk_block) {
     plan->bgk_block = plan->n_bgk == 0 ? 256 : tune("bgk_batch", plan->bgk_nodes, {128, 256, 512}, st,
         [&](int c) {
-          return launch_bgk_batch(f_in, f_out, plan->d_lat, plan->n_bgk, plan->bgk_nodes,
+          return launch_bgk_batch(f_in, f_out, plan->d_lat, plan->n_bgk, plan->d_hint,
+                                  plan->bgk_nodes,
                                   plan->total, c, st);
         });
   }
@@ -328,7 +345,7 @@ int lbm_batch_run(lbm_batch_plan* plan, const float* f_in, float* f_out, float* 
     plan->gnn_per_sm = plan->n_gnn == 0 ? 2 : tune("gnn_step_table", plan->gnn_nodes, {1, 2}, st,
         [&](int c) {
           return launch_gnn_step_table(f_in, f_out, plan->d_lat, plan->n_bgk, plan->n_gnn,
-                                       plan->bgk_nodes, plan->gnn_nodes, plan->total, pk, ws, st,
+                                       plan->d_hint, plan->bgk_nodes, plan->gnn_nodes, plan->total, pk, ws, st,
                                        c);
         });
   }

@@ -513,20 +513,29 @@ struct GeoTable {
   const LatDesc* lat;  // device table, sorted by offset
   int first, n;        // lattices first .. first+n-1 form this range
   int64_t base_, cnt, ps_;
+  // optional: hint[g >> 7] = the lattice holding global node (g >> 7) << 7
+  const int* hint;
   __device__ __forceinline__ int64_t count() const { return cnt; }
   __device__ __forceinline__ int64_t base() const { return base_; }
   __device__ __forceinline__ int64_t ps() const { return ps_; }
   __device__ __forceinline__ GeoPos pos(int64_t g) const {
-    int lo = first, hi = first + n - 1;
-    while (lo < hi) {  // last lattice whose offset <= g
-      const int mid = (lo + hi + 1) >> 1;
-      if (__ldg(&lat[mid].offset) <= g) lo = mid; else hi = mid - 1;
+    int lo;  // last lattice whose offset <= g
+    if (hint) {  // from the lattice of g's 128-node block, forward over the lattices it spans
+      lo = max(__ldg(hint + (g >> 7)), first);
+      while (lo + 1 < first + n && __ldg(&lat[lo + 1].offset) <= g) ++lo;
+    } else {
+      lo = first;
+      int hi = first + n - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&lat[mid].offset) <= g) lo = mid; else hi = mid - 1;
+      }
     }
     const int64_t off = __ldg(&lat[lo].offset);
     const int nx = __ldg(&lat[lo].nx), ny = __ldg(&lat[lo].ny);
-    const int64_t r = g - off;
-    const int y = (int)(r / nx);
-    return {(int)(r - (int64_t)y * nx), y, nx, ny, off, lo};
+    const uint32_t r = (uint32_t)(g - off);  // a lattice holds fewer than 2^31 nodes
+    const uint32_t y = r / (uint32_t)nx;
+    return {(int)(r - y * (uint32_t)nx), (int)y, nx, ny, off, lo};
   }
   __device__ __forceinline__ float tau(const GeoPos& p, float, const float*) const {
     return __ldg(&lat[p.b].tau);

@@ -617,11 +617,11 @@ cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
 }
 
 cudaError_t launch_gnn_step_table(const float* f_in, float* f_out, const LatDesc* lat, int first,
-                                  int n, int64_t base, int64_t count, int64_t ps,
+                                  int n, const int* hint, int64_t base, int64_t count, int64_t ps,
                                   const uint8_t* packed, __nv_bfloat16* ws, cudaStream_t st,
                                   int per_sm) {
   if (count <= 0) return cudaSuccess;
-  const GeoTable geo{lat, first, n, base, count, ps};
+  const GeoTable geo{lat, first, n, base, count, ps, hint};
   __nv_bfloat16* h0 = ws;
   __half* b0 = reinterpret_cast<__half*>(h0 + count * 64);
   __nv_bfloat16* h1 = reinterpret_cast<__nv_bfloat16*>(b0 + count * 64);

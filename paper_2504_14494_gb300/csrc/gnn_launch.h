@@ -38,10 +38,12 @@ cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
 struct LatDesc;
 // GNN-LBM step (encoder, 2 rounds, head + Eq. 3) on the lattices first ..
 // first+n-1 of a device descriptor table, whose nodes are [base, base+count)
-// of population buffers with plane stride ps; ws: count * 512 bytes;
-// per_sm: resident CTAs per SM of the persistent grids.
+// of population buffers with plane stride ps; hint: device int per 128-node
+// block of the buffers, the lattice holding the block's first node (or
+// NULL: binary search); ws: count * 512 bytes; per_sm: resident CTAs per SM
+// of the persistent grids.
 cudaError_t launch_gnn_step_table(const float* f_in, float* f_out, const LatDesc* lat, int first,
-                                  int n, int64_t base, int64_t count, int64_t ps,
+                                  int n, const int* hint, int64_t base, int64_t count, int64_t ps,
                                   const uint8_t* packed, __nv_bfloat16* ws, cudaStream_t st,
                                   int per_sm);
 
