@@ -147,3 +147,6 @@ def test_batch_plan_argument_checks(lbmlib):
     with pytest.raises(L.LbmError) as e:
         L.lbm_batch_plan_create([(8, 8, 7, 0.8)])
     assert e.value.code == -1
+    with pytest.raises(L.LbmError) as e:  # a lattice of 2^31 nodes
+        L.lbm_batch_plan_create([(8, 8, 0, 0.8), (65536, 32768, 1, 0.8)])
+    assert e.value.code == L.LBM_ERR_SIZE
