@@ -50,9 +50,9 @@ NCU_TRAFFIC = {
     #     --clock-control none -k regex:"gnn_(encode|round)_kernel" -s 3 -c 3
     #     python bench.py --only gnn --steps 20 --warmup 3   (one GNN-LBM step, 1024 x 1024:
     #     encoder + 2 rounds; key file gnn_fwd.cu)
-    "lbm_step_gnn": {"bytes_per_launch": (37867008 + 206008576) + (270411264 + 219638016)
-                     + (306578432 + 26664704), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
-                     "src_sha": "2afacd7dc2694e3e66bae19c1d252700458723eef2d3cd17ef2dc7b29cd3041f"},
+    "lbm_step_gnn": {"bytes_per_launch": (37824256 + 206268416) + (270372352 + 219566592)
+                     + (306563328 + 26811904), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
+                     "src_sha": "afca757585da3786af3af28cfacb5d4e0c09e86e44d64be1aa804072edcbfd6d"},
 }
 
 
