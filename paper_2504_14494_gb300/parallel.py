@@ -23,7 +23,8 @@ update exchanges data between ranks:
     periodic step on the padded slab, which leaves every owned row exact
     (the step reads rows at most `halo` away: 1 for BGK, 3 for the GNN step,
     which streams and then passes messages twice) and only the ghost rows
-    stale until the next exchange.
+    stale until the next exchange.  The domain totals are one FP64
+    all-reduce of the ranks' owned-row totals.
 
 Every function here works with world size 1 (no process group) and with any
 backend; the host logic is exercised with `gloo` on CPU tensors.
@@ -163,6 +164,17 @@ class DataParallelTrainer:
         return self.params.cpu().numpy().copy()
 
 
+def _device_totals(view):
+    """lbm_moments totals of a [9, rows, nx] FP32 device view whose planes
+    are strided (rows contiguous within a plane)."""
+    import torch
+    q, rows, nx = view.shape
+    assert view.stride(2) == 1 and view.stride(1) == nx, "rows must be contiguous"
+    out = torch.zeros(5, dtype=torch.float64, device=view.device)
+    L.lbm_moments(view.data_ptr(), L.shape(nx, rows, 1, view.stride(0)), None, None, None, out)
+    return out
+
+
 class SlabLattice:
     """One periodic nx x ny lattice split into row slabs over the ranks of
     `group`: rank r owns rows [ny r / P, ny (r + 1) / P) and keeps them with
@@ -220,6 +232,24 @@ class SlabLattice:
     def step(self, step_fn):
         self.exchange()
         self.f = step_fn(self.f)
+
+    def totals(self, moments_fn=None):
+        """FP64 domain totals of the whole lattice (mass, x- and y-momentum,
+        kinetic energy, non-finite node count; the quantities of
+        lbm_moments): each rank's totals over its owned rows, summed over
+        ranks by one FP64 all-reduce.  moments_fn(view) -> float64 tensor[5]
+        computes them for a [9, rows, nx] view of the owned rows (a strided
+        view into the padded slab); default: lbm_moments through the C ABI
+        on that view in place (plane stride of the padded slab)."""
+        import torch
+        view = self.interior()
+        if moments_fn is None:
+            moments_fn = _device_totals
+        t = moments_fn(view).to(torch.float64)
+        dist = _dist()
+        if dist is not None and self.size > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.SUM, group=self.group)
+        return t
 
     def gather(self):
         """The full [9, ny, nx] state on every rank (all-gather of the slabs)."""

@@ -320,7 +320,9 @@ def test_slab_lattice_on_one_gpu_equals_full_lattice(lbmlib, cuda):
     """The row-slab decomposition of one lattice (ghost rows + the periodic
     step on the padded slab) with one rank on the GPU: BGK (1 ghost row) and
     the GNN step (3 ghost rows) through the C ABI equal the full-lattice
-    steps bitwise."""
+    steps bitwise; the slab's totals (lbm_moments on the owned rows of the
+    padded slab, plane-strided) equal the full lattice's to FP64 summation
+    order."""
     import torch
     from paper_2504_14494_gb300.parallel import SlabLattice
     L = lbmlib
@@ -350,5 +352,12 @@ def test_slab_lattice_on_one_gpu_equals_full_lattice(lbmlib, cuda):
             full = fn(full)
         assert torch.isfinite(full).all()
         assert torch.equal(slab.gather(), full), halo
+        # totals of the owned rows, in place through a plane-strided view
+        tot = slab.totals().cpu().numpy()
+        want = torch.zeros(5, dtype=torch.float64, device=cuda)
+        L.lbm_moments(full.contiguous(), L.shape(nx, ny), None, None, None, want)
+        want = want.cpu().numpy()
+        assert np.allclose(tot[:4], want[:4], rtol=1e-12, atol=1e-12), (tot, want)
+        assert tot[4] == want[4] == 0.0
     assert L.lbm_get_status() == 0
 

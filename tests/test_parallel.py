@@ -181,6 +181,11 @@ def _slab_worker(rank, port, size, result_q):
                 assert np.array_equal(got, ref), kind   # the same FP64 operations per node
             else:
                 assert np.allclose(got, ref, rtol=1e-12, atol=1e-15), kind
+            # domain totals: owned-row totals of every rank, one FP64 all-reduce
+            tot = slab.totals(lambda v: torch.tensor(np.asarray(lbm.totals(v.numpy()), float)))
+            want = np.asarray(lbm.totals(ref), float)
+            assert np.allclose(tot.numpy()[:4], want[:4], rtol=1e-12, atol=1e-14), kind
+            assert tot.numpy()[4] == want[4] == 0.0
         result_q.put((rank, "ok"))
     finally:
         dist.destroy_process_group()
@@ -191,7 +196,9 @@ def test_slab_decomposition_equals_single_domain(size):
     """One 12 x 10 lattice split into row slabs over 1-3 gloo ranks: ghost-row
     exchange + the periodic step on each padded slab reproduces the
     single-domain oracle run (BGK: 1 ghost row, bitwise; GNN step: 3 ghost
-    rows, to FP64 rounding of the batched matrix products)."""
+    rows, to FP64 rounding of the batched matrix products), and the FP64
+    all-reduce of the ranks' owned-row totals equals the totals of the whole
+    lattice to summation-order rounding."""
     pytest.importorskip("torch")
     import time
     import torch.multiprocessing as mp
