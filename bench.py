@@ -161,6 +161,12 @@ def run_ours(args, rank, world, local_rank):
         res = gnn_bench(args, L, dev, torch.cuda.current_stream(), side=args.side, only=True)
         print(json.dumps(_finite({"case": f"gnn {args.side}x{args.side}", **res})))
         return None
+    if args.only == "batch":  # the 512-lattice serving batch, untrained conserving network
+        from paper_2504_14494_gb300 import inputs
+        theta = inputs.xavier_params(W.TGV_GNN_1024.weight_seed, variant=2)
+        res = batch_bench(args, L, dev, torch.cuda.current_stream(), theta)
+        print(json.dumps(_finite({"case": res["workload"], **res})))
+        return None
     if args.only == "train":
         from paper_2504_14494_gb300 import inputs
         from paper_2504_14494_gb300.train import Trainer
@@ -776,7 +782,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["bgk", "gnn", "train"], default=None,
+    ap.add_argument("--only", choices=["bgk", "gnn", "train", "batch"], default=None,
                     help="time one kernel family only (profiling runs)")
     ap.add_argument("--side", type=int, default=N_SIDE, help="lattice side for --only runs")
     args = ap.parse_args()
