@@ -38,6 +38,26 @@ __device__ __forceinline__ void st_col(uint8_t* op, int R, int row0, int node, c
     *reinterpret_cast<__nv_bfloat16*>(blk + sw128_off(row0 + c, k)) = __float2bfloat16_rn(v[c]);
 }
 
+#ifndef LBM_BWD_PF
+#define LBM_BWD_PF 1  // L2 prefetch of the next tile's per-node inputs
+#endif
+
+// L2 prefetch (a hint: no registers, no completion to wait for) of nodes
+// [m0, m0 + 128) of plane `plane` of a per-node tensor: chunked planes of 16
+// bytes per node (esz 16, plane stride N nodes) or FP32 planes (esz 4, plane
+// stride `ps` nodes).  The range is shrunk to 16-byte boundaries inside the
+// tensor's own bytes.
+__device__ __forceinline__ void l2_prefetch_nodes(const void* base, int plane, int64_t ps,
+                                                  int esz, int64_t m0, int64_t N) {
+  if (m0 >= N) return;
+  const int64_t cnt = N - m0 < 128 ? N - m0 : 128;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(base) + (uintptr_t)((plane * ps + m0) * esz);
+  const uintptr_t lo = a & ~uintptr_t(15), hi = (a + (uintptr_t)(cnt * esz)) & ~uintptr_t(15);
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo))
+                 : "memory");
+}
+
 __device__ __forceinline__ void zero_smem(uint8_t* p, uint32_t bytes) {
   uint4* q = reinterpret_cast<uint4*>(p);
   for (uint32_t i = threadIdx.x; i < bytes / 16; i += blockDim.x) q[i] = make_uint4(0, 0, 0, 0);
@@ -203,6 +223,11 @@ __global__ void __launch_bounds__(256, 2) gnn_head_bwd_kernel(
     const int64_t n = tile * TILE + node;
     const bool on = n < N;
     const int64_t nn = on ? n : N - 1;
+    if (LBM_BWD_PF && threadIdx.x < NOUT + 8) {  // next tile: dy (10 FP32 planes), h2 (8 planes)
+      const int64_t m0 = (tile + gridDim.x) * TILE;
+      if (threadIdx.x < NOUT) l2_prefetch_nodes(dy, threadIdx.x, N, 4, m0, N);
+      else l2_prefetch_nodes(h2, threadIdx.x - NOUT, N, 16, m0, N);
+    }
     if (half == 0) {
       float d[NOUT];
 #pragma unroll
@@ -300,6 +325,13 @@ __global__ void __launch_bounds__(256, LBM_RB1_CTAS) gnn_round_bwd1_kernel(
     const int64_t n = tile * TILE + node;
     const bool on = n < N;
     const int64_t nn = on ? n : N - 1;
+    if (LBM_BWD_PF && threadIdx.x < 32) {  // next tile: h, a (8 planes each), dh_out (16)
+      const int64_t m0 = (tile + gridDim.x) * TILE;
+      const int t = threadIdx.x;
+      if (t < 8) l2_prefetch_nodes(h_in, t, N, 16, m0, N);
+      else if (t < 16) l2_prefetch_nodes(a_in, t - 8, N, 16, m0, N);
+      else l2_prefetch_nodes(dh_out, t - 16, N, 16, m0, N);
+    }
     {
       float v[32];
       ld_pb32(h_in, N, nn, f0, v);
@@ -662,6 +694,11 @@ __global__ void __launch_bounds__(256, LBM_EB_CTAS) gnn_encode_bwd_kernel(
     const int64_t n = tile * TILE + node;
     const bool on = n < N;
     const int64_t nn = on ? n : N - 1;
+    if (LBM_BWD_PF && threadIdx.x < Q + 16) {  // next tile: f_pre (9 FP32 planes), dh0 (16)
+      const int64_t m0 = (tile + gridDim.x) * TILE;
+      if (threadIdx.x < Q) l2_prefetch_nodes(f_pre, threadIdx.x, s.ps, 4, m0, N);
+      else l2_prefetch_nodes(dh0, threadIdx.x - Q, N, 16, m0, N);
+    }
     float fv[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) fv[q] = __ldg(f_pre + q * s.ps + nn);
