@@ -788,6 +788,8 @@ def main():
     ap.add_argument("--only", choices=["bgk", "gnn", "train", "batch"], default=None,
                     help="time one kernel family only (profiling runs)")
     ap.add_argument("--side", type=int, default=N_SIDE, help="lattice side for --only runs")
+    ap.add_argument("--log", default=None,
+                    help="also append the JSON line to this JSON-lines file (rank 0)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -805,7 +807,13 @@ def main():
     else:
         out = run_ours(args, rank, world, local_rank)
     if out is not None and rank == 0:
-        print(json.dumps(_finite(out), allow_nan=False), flush=True)
+        line = json.dumps(_finite(out), allow_nan=False)
+        print(line, flush=True)
+        if args.log:
+            d = os.path.dirname(os.path.abspath(args.log))
+            os.makedirs(d, exist_ok=True)
+            with open(args.log, "a") as fh:
+                fh.write(line + "\n")
 
 
 if __name__ == "__main__":
