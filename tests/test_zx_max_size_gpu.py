@@ -70,3 +70,61 @@ def test_bgk_step_beyond_2_31_nodes(lbmlib, cuda):
     assert t[4] == 0.0
     del f_in, f_out
     torch.cuda.empty_cache()
+
+
+def test_gnn_step_at_16384_squared(lbmlib, cuda):
+    """lbm_step_gnn on one 16,384^2 lattice (268 M nodes: 137 GB of
+    workspace, plane offsets beyond 2^35 bytes), bounds-checked build first,
+    then the regular build: sampled nodes (the last rows and columns
+    included) against the oracle's GNN step of the 13 x 13 periodic patch
+    around each (streaming plus two message-passing hops reach 3 nodes), at
+    the tolerance of the 1024^2 sampled test."""
+    import torch
+    from oracle import gnn
+    from paper_2504_14494_gb300 import build, inputs, lib as L
+    from gpu_util import rel_l2
+    n = 16384
+    torch.cuda.empty_cache()
+    s = L.shape(n, n)
+    need = 2 * 9 * n * n * 4 + L.gnn_step_workspace_bytes(s) + (4 << 30)
+    if torch.cuda.mem_get_info()[0] < need:
+        pytest.skip("needs 162 GB of free device memory")
+    k = 2 * np.pi / n
+    f = torch.empty(9 * n * n, device=cuda)
+    out = torch.empty_like(f)
+    ws = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    theta = inputs.xavier_params(53, s_df=1e-2, bias_scale=0.1)
+    params = torch.from_numpy(theta).to(cuda)
+
+    def run():
+        pk = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=cuda)
+        L.gnn_pack(params, pk)
+        L.lbm_init_tgv(f, s, 1.0, 0.05, k, k, False)
+        L.lbm_step_gnn(f, out, s, 0.65, None, pk, None, ws)
+        torch.cuda.synchronize()
+        return L.lbm_get_status()
+
+    regular = L._lib
+    try:
+        L._lib = None
+        L.load(build.build(checked=True))
+        assert run() == L.LBM_OK  # LBM_ERR_BOUNDS: an index out of range
+    finally:
+        L._lib = regular
+    assert run() == L.LBM_OK
+    rng = np.random.default_rng(3)
+    pts = [(int(a), int(b)) for a, b in zip(rng.integers(0, n, 24), rng.integers(0, n, 24))]
+    pts += [(0, 0), (n - 1, n - 1), (n - 1, 0), (0, n - 1), (n // 2, n - 1)]
+    F = f.view(9, n, n)
+    got, ref, bgk = [], [], []
+    for (x, y) in pts:
+        xs = torch.tensor((np.arange(x - 6, x + 7)) % n, device=cuda)
+        ys = torch.tensor((np.arange(y - 6, y + 7)) % n, device=cuda)
+        patch = F[:, ys[:, None], xs[None, :]].double().cpu().numpy()
+        ref.append(gnn.gnn_step(patch, theta, 0.65)[:, 6, 6])
+        bgk.append(lbm.bgk_step(patch, 0.65)[:, 6, 6])
+        got.append(out.view(9, n, n)[:, y, x].double().cpu().numpy())
+    got, ref, bgk = np.array(got), np.array(ref), np.array(bgk)
+    assert rel_l2(got - bgk, ref - bgk) <= 3e-2
+    del f, out, ws
+    torch.cuda.empty_cache()
