@@ -44,8 +44,8 @@ NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #     --clock-control none -k regex:bgk_step_x4 -s 3 -c 1
     #     python bench.py --only bgk --steps 10 --warmup 3      (4096 x 4096, one launch)
-    "bgk_step_x4": {"bytes_per_launch": 604044544 + 547293952,
-                    "src_sha": "73ddfc6fddc151022938a0730e3eed432c1fd6803934835b201a9fd12f4cf21a"},
+    "bgk_step_x4": {"bytes_per_launch": 604054528 + 547321088,
+                    "src_sha": "75175dfa13fa1003a94d217d10ae26bfeaf1caf2b0033fe04d22f926f7b425a7"},
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #     --clock-control none -k regex:"gnn_(encode|round)_kernel" -s 3 -c 3
     #     python bench.py --only gnn --steps 20 --warmup 3   (one GNN-LBM step, 1024 x 1024:

@@ -10,6 +10,8 @@
 // the aligned vector of the lane and take the one missing value from the
 // neighbouring lane by a shuffle; the warp's edge lanes fetch it with a
 // scalar load (which also implements the periodic wrap).  Row wrap is a select.
+#include <atomic>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -18,15 +20,19 @@ namespace lbmgnn {
 __device__ unsigned g_status = 0;
 
 unsigned* status_word() {
-  static unsigned* addr[64] = {nullptr};
+  // per-device cache of the symbol's address (host threads may race on the
+  // first call: both store the same address)
+  static std::atomic<unsigned*> addr[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  if (!addr[dev]) {
+  unsigned* a = addr[dev].load(std::memory_order_acquire);
+  if (!a) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
-    addr[dev] = static_cast<unsigned*>(p);
+    a = static_cast<unsigned*>(p);
+    addr[dev].store(a, std::memory_order_release);
   }
-  return addr[dev];
+  return a;
 }
 
 // ---------------------------------------------------------------------------
