@@ -50,9 +50,9 @@ NCU_TRAFFIC = {
     #     --clock-control none -k regex:"gnn_(encode|round)_kernel" -s 3 -c 3
     #     python bench.py --only gnn --steps 20 --warmup 3   (one GNN-LBM step, 1024 x 1024:
     #     encoder + 2 rounds; key file gnn_fwd.cu)
-    "lbm_step_gnn": {"bytes_per_launch": (37824256 + 206268416) + (270372352 + 219566592)
-                     + (306563328 + 26811904), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
-                     "src_sha": "afca757585da3786af3af28cfacb5d4e0c09e86e44d64be1aa804072edcbfd6d"},
+    "lbm_step_gnn": {"bytes_per_launch": (37877760 + 206217216) + (270408704 + 219210752)
+                     + (306548992 + 26482944), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
+                     "src_sha": "8c7b8d16c695c0d7df3f4e30cfcb32d0e79f033d6ba3a2332cfe924552298247"},
 }
 
 

@@ -15,6 +15,8 @@
 // mostly from L2.  The node's own term A = W_a h is recomputed from h by the
 // consuming round kernel (one 128x64x64 MMA per tile) instead of being stored.
 // The training forward (gnn_forward) stores A | B ([N][128]) for the backward.
+#include <type_traits>
+
 #include "gnn.cuh"
 #include "gnn_launch.h"
 
@@ -113,10 +115,17 @@ constexpr uint32_t W1X = 0, W2 = 8192, WAB = 16384, X1 = 32768, X = 49152, B1 = 
 }
 
 #ifndef LBM_ENC_CTAS
-#define LBM_ENC_CTAS 2  // resident encoder CTAs per SM (2 and 3 measured within 0.5 %)
+#define LBM_ENC_CTAS 2  // resident encoder CTAs per SM
 #endif
+// The inference encoder of one stack of lattices (pull, B only) fits 80
+// registers without spilling and runs 3 CTAs per SM (the step 2 % faster);
+// the other instances would spill there and keep LBM_ENC_CTAS.
 template <bool PULL, bool BONLY, class Geo>
-__global__ void __launch_bounds__(256, LBM_ENC_CTAS) gnn_encode_kernel(
+constexpr int enc_ctas() {
+  return (PULL && BONLY && std::is_same<Geo, GeoStack>::value) ? 3 : LBM_ENC_CTAS;
+}
+template <bool PULL, bool BONLY, class Geo>
+__global__ void __launch_bounds__(256, (enc_ctas<PULL, BONLY, Geo>())) gnn_encode_kernel(
     const float* __restrict__ f, Geo geo, const uint8_t* __restrict__ packed,
     __nv_bfloat16* __restrict__ h0_out, __half* __restrict__ ab_out, unsigned* stw) {
   if (!blob_ok(packed, stw)) return;
@@ -544,9 +553,10 @@ cudaError_t launch_gnn_pack(const float* params, uint8_t* packed, cudaStream_t s
 
 
 template <bool PULL, bool BONLY, class Geo>
-static cudaError_t encode_t(const float* f, const Geo& geo, unsigned grid, uint32_t bytes,
-                           const uint8_t* packed, __nv_bfloat16* h0, __half* ab, unsigned* stw,
-                           cudaStream_t st) {
+static cudaError_t encode_t(const float* f, const Geo& geo, int64_t N, int per_sm,
+                           uint32_t bytes, const uint8_t* packed, __nv_bfloat16* h0, __half* ab,
+                           unsigned* stw, cudaStream_t st) {
+  const unsigned grid = grid_for(N, per_sm >= 2 ? enc_ctas<PULL, BONLY, Geo>() : per_sm);
   cudaError_t e;
   if ((e = set_smem(gnn_encode_kernel<PULL, BONLY, Geo>, bytes)) != cudaSuccess) return e;
   gnn_encode_kernel<PULL, BONLY, Geo><<<grid, 256, bytes, st>>>(f, geo, packed, h0, ab, stw);
@@ -561,12 +571,11 @@ static cudaError_t encode_any(const float* f, bool pull, bool b_only, const Geo&
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
   const uint32_t bytes = enc::BYTES + 1024;
-  const unsigned grid = grid_for(N, per_sm >= 2 ? LBM_ENC_CTAS : per_sm);
   if (pull)
-    return b_only ? encode_t<true, true>(f, geo, grid, bytes, packed, h0, ab, stw, st)
-                  : encode_t<true, false>(f, geo, grid, bytes, packed, h0, ab, stw, st);
-  return b_only ? encode_t<false, true>(f, geo, grid, bytes, packed, h0, ab, stw, st)
-                : encode_t<false, false>(f, geo, grid, bytes, packed, h0, ab, stw, st);
+    return b_only ? encode_t<true, true>(f, geo, N, per_sm, bytes, packed, h0, ab, stw, st)
+                  : encode_t<true, false>(f, geo, N, per_sm, bytes, packed, h0, ab, stw, st);
+  return b_only ? encode_t<false, true>(f, geo, N, per_sm, bytes, packed, h0, ab, stw, st)
+                : encode_t<false, false>(f, geo, N, per_sm, bytes, packed, h0, ab, stw, st);
 }
 
 template <int MODE, bool AH, class Geo>
