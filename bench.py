@@ -50,9 +50,9 @@ NCU_TRAFFIC = {
     #     --clock-control none -k regex:"gnn_(encode|round)_kernel" -s 3 -c 3
     #     python bench.py --only gnn --steps 20 --warmup 3   (one GNN-LBM step, 1024 x 1024:
     #     encoder + 2 rounds; key file gnn_fwd.cu)
-    "lbm_step_gnn": {"bytes_per_launch": (37877760 + 206217216) + (270408704 + 219210752)
-                     + (306548992 + 26482944), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
-                     "src_sha": "8c7b8d16c695c0d7df3f4e30cfcb32d0e79f033d6ba3a2332cfe924552298247"},
+    "lbm_step_gnn": {"bytes_per_launch": (37826304 + 206351872) + (270360832 + 219446784)
+                     + (306558976 + 26833664), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
+                     "src_sha": "78ce5f8ea00048b46cf6cc60063fa32eb68fb5ea5b09379064de3b816ba13dd4"},
 }
 
 

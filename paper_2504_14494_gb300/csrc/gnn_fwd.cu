@@ -15,8 +15,6 @@
 // mostly from L2.  The node's own term A = W_a h is recomputed from h by the
 // consuming round kernel (one 128x64x64 MMA per tile) instead of being stored.
 // The training forward (gnn_forward) stores A | B ([N][128]) for the backward.
-#include <type_traits>
-
 #include "gnn.cuh"
 #include "gnn_launch.h"
 
@@ -117,12 +115,13 @@ constexpr uint32_t W1X = 0, W2 = 8192, WAB = 16384, X1 = 32768, X = 49152, B1 = 
 #ifndef LBM_ENC_CTAS
 #define LBM_ENC_CTAS 2  // resident encoder CTAs per SM
 #endif
-// The inference encoder of one stack of lattices (pull, B only) fits 80
-// registers without spilling and runs 3 CTAs per SM (the step 2 % faster);
-// the other instances would spill there and keep LBM_ENC_CTAS.
+// The inference encoder (pull, B only) runs 3 CTAs per SM at 80 registers:
+// for one stack of lattices without spilling (the step 2 % faster), for the
+// table geometry of batched runs with a few spilled values and still 3 %
+// faster; the training instances would spill more and keep LBM_ENC_CTAS.
 template <bool PULL, bool BONLY, class Geo>
 constexpr int enc_ctas() {
-  return (PULL && BONLY && std::is_same<Geo, GeoStack>::value) ? 3 : LBM_ENC_CTAS;
+  return (PULL && BONLY) ? 3 : LBM_ENC_CTAS;
 }
 template <bool PULL, bool BONLY, class Geo>
 __global__ void __launch_bounds__(256, (enc_ctas<PULL, BONLY, Geo>())) gnn_encode_kernel(
