@@ -2,8 +2,12 @@
 
 Every function here has the name and argument order of the C entry point in
 include/lbmgnn.h.  Buffer arguments accept a torch tensor (its data_ptr() is
-passed), a raw integer address, or None for a NULL pointer.  `stream`
-defaults to torch's current CUDA stream.  A non-zero status raises LbmError.
+passed), a raw integer address (trusted), or None for a NULL pointer.  A
+tensor for a device buffer must be a contiguous CUDA tensor of the dtype and
+at least the size the call implies (dptr), one for a host buffer a CPU
+tensor or numpy array (hptr); otherwise ValueError is raised before the
+library is called.  `stream` defaults to torch's current CUDA stream.  A
+non-zero status raises LbmError.
 
 There is no fallback: if the shared library is missing or cannot be loaded,
 every call raises.
@@ -136,13 +140,69 @@ def register(name, restype, argtypes):
         fn.argtypes = argtypes
 
 
-def ptr(x):
-    """Device/host address of a tensor, an int, or None (NULL)."""
-    if x is None:
-        return None
-    if isinstance(x, int):
+def _torch():
+    import torch
+    return torch
+
+
+def _elems(s):
+    """(nodes, plane stride, elements a population buffer of shape s spans)."""
+    n = int(s.nx) * int(s.ny) * int(s.nb)
+    ps = int(s.plane_stride) or n
+    return n, ps, 8 * ps + n
+
+
+def dptr(x, name, dtype=None, numel=0, nbytes_min=0):
+    """Address of a DEVICE buffer argument: a contiguous CUDA tensor (of
+    `dtype`, with at least `numel` elements and `nbytes_min` bytes when
+    given), a raw int address (trusted), or None (NULL).  Anything else
+    raises ValueError before the library is called: a host tensor here would
+    hand a kernel a host address."""
+    if x is None or isinstance(x, int):
         return x
+    torch = _torch()
+    if not isinstance(x, torch.Tensor):
+        raise ValueError(f"{name}: a CUDA tensor or a device address is required, "
+                         f"not {type(x).__name__}")
+    if not x.is_cuda:
+        raise ValueError(f"{name}: a CUDA tensor is required (got one on {x.device})")
+    return _checked_tensor(x, name, dtype, numel, nbytes_min)
+
+
+def hptr(x, name, dtype=None, numel=0):
+    """Address of a HOST buffer argument: a contiguous CPU tensor or numpy
+    array (of `dtype` and at least `numel` elements when given), a raw int
+    address, or None."""
+    if x is None or isinstance(x, int):
+        return x
+    import numpy as np
+    if isinstance(x, np.ndarray):
+        x = _torch().from_numpy(x)
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or x.is_cuda:
+        raise ValueError(f"{name}: a host (CPU) tensor or array is required")
+    return _checked_tensor(x, name, dtype, numel, 0)
+
+
+def _checked_tensor(x, name, dtype, numel, nbytes_min):
+    if not x.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if dtype is not None and x.dtype != dtype:
+        raise ValueError(f"{name}: dtype {x.dtype}, {dtype} required")
+    if x.numel() < numel:
+        raise ValueError(f"{name}: {x.numel()} elements, at least {numel} required")
+    if x.numel() * x.element_size() < nbytes_min:
+        raise ValueError(f"{name}: {x.numel() * x.element_size()} bytes, at least "
+                         f"{nbytes_min} required")
     return x.data_ptr()
+
+
+def _f32():
+    return _torch().float32
+
+
+def _f64():
+    return _torch().float64
 
 
 def stream_ptr(stream=None):
@@ -174,25 +234,38 @@ def lbm_selftest_wait_timeout(max_cycles, stream=None):
 
 
 def lbm_init_tgv(f, s, rho0, u0, kx, ky, pressure_consistent=False, stream=None):
-    check(load().lbm_init_tgv(ptr(f), s, rho0, u0, kx, ky, int(bool(pressure_consistent)),
-                              stream_ptr(stream)), "lbm_init_tgv")
+    _, _, fe = _elems(s)
+    check(load().lbm_init_tgv(dptr(f, "f", _f32(), fe), s, rho0, u0, kx, ky,
+                              int(bool(pressure_consistent)), stream_ptr(stream)), "lbm_init_tgv")
 
 
 def lbm_step_bgk(f_in, f_out, f_tmp, s, tau, taus=None, nsteps=1, totals=None, stream=None):
-    check(load().lbm_step_bgk(ptr(f_in), ptr(f_out), ptr(f_tmp), s, float(tau), ptr(taus),
-                              int(nsteps), ptr(totals), stream_ptr(stream)), "lbm_step_bgk")
+    _, _, fe = _elems(s)
+    f32 = _f32()
+    check(load().lbm_step_bgk(dptr(f_in, "f_in", f32, fe), dptr(f_out, "f_out", f32, fe),
+                              dptr(f_tmp, "f_tmp", f32, fe), s, float(tau),
+                              dptr(taus, "taus", f32, int(s.nb)), int(nsteps),
+                              dptr(totals, "totals", _f64(), 5), stream_ptr(stream)),
+          "lbm_step_bgk")
 
 
 def lbm_step_channel(f_in, f_out, f_tmp, s, tau, taus=None, force_x=0.0, nsteps=1, totals=None,
                      stream=None):
-    check(load().lbm_step_channel(ptr(f_in), ptr(f_out), ptr(f_tmp), s, float(tau), ptr(taus),
-                                  float(force_x), int(nsteps), ptr(totals), stream_ptr(stream)),
+    _, _, fe = _elems(s)
+    f32 = _f32()
+    check(load().lbm_step_channel(dptr(f_in, "f_in", f32, fe), dptr(f_out, "f_out", f32, fe),
+                                  dptr(f_tmp, "f_tmp", f32, fe), s, float(tau),
+                                  dptr(taus, "taus", f32, int(s.nb)), float(force_x), int(nsteps),
+                                  dptr(totals, "totals", _f64(), 5), stream_ptr(stream)),
           "lbm_step_channel")
 
 
 def lbm_moments(f, s, rho=None, ux=None, uy=None, totals=None, stream=None):
-    check(load().lbm_moments(ptr(f), s, ptr(rho), ptr(ux), ptr(uy), ptr(totals),
-                             stream_ptr(stream)), "lbm_moments")
+    n, _, fe = _elems(s)
+    f32 = _f32()
+    check(load().lbm_moments(dptr(f, "f", f32, fe), s, dptr(rho, "rho", f32, n),
+                             dptr(ux, "ux", f32, n), dptr(uy, "uy", f32, n),
+                             dptr(totals, "totals", _f64(), 5), stream_ptr(stream)), "lbm_moments")
 
 
 def lbm_host_workspace_bytes(s):
@@ -203,8 +276,13 @@ def lbm_step_bgk_host(f_in_host, f_out_host, s, tau, taus_host=None, nsteps=1,
                       totals_host=None, workspace=None, ws_bytes=None, stream=None):
     """lbm_step_bgk on a state in host memory (CPU tensors, page-locked for
     overlap); asynchronous on `stream` (see include/lbmgnn.h)."""
-    check(load().lbm_step_bgk_host(ptr(f_in_host), ptr(f_out_host), s, float(tau),
-                                   ptr(taus_host), int(nsteps), ptr(totals_host), ptr(workspace),
+    _, _, fe = _elems(s)
+    f32 = _f32()
+    check(load().lbm_step_bgk_host(hptr(f_in_host, "f_in_host", f32, fe),
+                                   hptr(f_out_host, "f_out_host", f32, fe), s, float(tau),
+                                   hptr(taus_host, "taus_host", f32, int(s.nb)), int(nsteps),
+                                   hptr(totals_host, "totals_host", _f64(), 5),
+                                   dptr(workspace, "workspace"),
                                    int(nbytes(workspace) if ws_bytes is None else ws_bytes),
                                    stream_ptr(stream)), "lbm_step_bgk_host")
 
@@ -219,7 +297,7 @@ def gnn_params_init_xavier(params_host, seed, s_df=1e-4, variant=0):
             raise ValueError("params_host must be a contiguous float32 array")
         addr = params_host.ctypes.data
     else:
-        addr = ptr(params_host)
+        addr = hptr(params_host, "params_host", _f32(), gnn_param_count())
     check(load().gnn_params_init_xavier(addr, int(seed), float(s_df), int(variant)),
           "gnn_params_init_xavier")
     return params_host
@@ -238,7 +316,9 @@ def gnn_packed_bytes():
 
 
 def gnn_pack(params, packed, stream=None):
-    check(load().gnn_pack(ptr(params), ptr(packed), stream_ptr(stream)), "gnn_pack")
+    check(load().gnn_pack(dptr(params, "params", _f32(), gnn_param_count()),
+                          dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
+                          stream_ptr(stream)), "gnn_pack")
 
 
 def gnn_step_workspace_bytes(s):
@@ -253,9 +333,13 @@ def lbm_step_gnn(f_in, f_out, s, tau, taus, packed, totals, workspace, ws_bytes=
                  stream=None):
     if ws_bytes is None:
         ws_bytes = nbytes(workspace)
-    check(load().lbm_step_gnn(ptr(f_in), ptr(f_out), s, float(tau), ptr(taus), ptr(packed),
-                              ptr(totals), ptr(workspace), int(ws_bytes), stream_ptr(stream)),
-          "lbm_step_gnn")
+    _, _, fe = _elems(s)
+    f32 = _f32()
+    check(load().lbm_step_gnn(dptr(f_in, "f_in", f32, fe), dptr(f_out, "f_out", f32, fe), s,
+                              float(tau), dptr(taus, "taus", f32, int(s.nb)),
+                              dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
+                              dptr(totals, "totals", _f64(), 5), dptr(workspace, "workspace"),
+                              int(ws_bytes), stream_ptr(stream)), "lbm_step_gnn")
 
 
 def gnn_saved_bytes(s):
@@ -263,25 +347,36 @@ def gnn_saved_bytes(s):
 
 
 def gnn_forward(f_pre, s, packed, saved, y, stream=None):
-    check(load().gnn_forward(ptr(f_pre), s, ptr(packed), ptr(saved), ptr(y), stream_ptr(stream)),
-          "gnn_forward")
+    n, _, fe = _elems(s)
+    check(load().gnn_forward(dptr(f_pre, "f_pre", _f32(), fe), s,
+                             dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
+                             dptr(saved, "saved", nbytes_min=gnn_saved_bytes(s)),
+                             dptr(y, "y", _f32(), 10 * n), stream_ptr(stream)), "gnn_forward")
 
 
 # --- auxiliary lattice operations and training ------------------------------------
 def lbm_stream(f_in, f_out, s, stream=None):
-    check(load().lbm_stream(ptr(f_in), ptr(f_out), s, stream_ptr(stream)), "lbm_stream")
+    _, _, fe = _elems(s)
+    check(load().lbm_stream(dptr(f_in, "f_in", _f32(), fe), dptr(f_out, "f_out", _f32(), fe), s,
+                            stream_ptr(stream)), "lbm_stream")
 
 
 def lbm_init_tgv_batch(f, s, params, pressure_consistent=False, stream=None):
-    check(load().lbm_init_tgv_batch(ptr(f), s, ptr(params), int(bool(pressure_consistent)),
-                                    stream_ptr(stream)), "lbm_init_tgv_batch")
+    _, _, fe = _elems(s)
+    check(load().lbm_init_tgv_batch(dptr(f, "f", _f32(), fe), s,
+                                    dptr(params, "params", _f64(), 4 * int(s.nb)),
+                                    int(bool(pressure_consistent)), stream_ptr(stream)),
+          "lbm_init_tgv_batch")
 
 
 def lbm_restrict(f_fine, fine, f_coarse, coarse, factor, tau_f, taus_f, tau_c, taus_c,
                  stream=None):
-    check(load().lbm_restrict(ptr(f_fine), fine, ptr(f_coarse), coarse, int(factor), float(tau_f),
-                              ptr(taus_f), float(tau_c), ptr(taus_c), stream_ptr(stream)),
-          "lbm_restrict")
+    f32 = _f32()
+    check(load().lbm_restrict(dptr(f_fine, "f_fine", f32, _elems(fine)[2]), fine,
+                              dptr(f_coarse, "f_coarse", f32, _elems(coarse)[2]), coarse,
+                              int(factor), float(tau_f), dptr(taus_f, "taus_f", f32, int(fine.nb)),
+                              float(tau_c), dptr(taus_c, "taus_c", f32, int(coarse.nb)),
+                              stream_ptr(stream)), "lbm_restrict")
 
 
 def gnn_loss_workspace_bytes(s):
@@ -290,8 +385,14 @@ def gnn_loss_workspace_bytes(s):
 
 def gnn_collide_loss(f_pre, y, f_target, s, tau, taus, packed, loss, dy, f_pred, workspace,
                      ws_bytes=None, stream=None):
-    check(load().gnn_collide_loss(ptr(f_pre), ptr(y), ptr(f_target), s, float(tau), ptr(taus),
-                                  ptr(packed), ptr(loss), ptr(dy), ptr(f_pred), ptr(workspace),
+    n, _, fe = _elems(s)
+    f32 = _f32()
+    check(load().gnn_collide_loss(dptr(f_pre, "f_pre", f32, fe), dptr(y, "y", f32, 10 * n),
+                                  dptr(f_target, "f_target", f32, fe), s, float(tau),
+                                  dptr(taus, "taus", f32, int(s.nb)),
+                                  dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
+                                  dptr(loss, "loss", _f64(), 1), dptr(dy, "dy", f32, 10 * n),
+                                  dptr(f_pred, "f_pred", f32, fe), dptr(workspace, "workspace"),
                                   int(nbytes(workspace) if ws_bytes is None else ws_bytes),
                                   stream_ptr(stream)), "gnn_collide_loss")
 
@@ -302,14 +403,22 @@ def gnn_backward_workspace_bytes(s):
 
 def gnn_backward(f_pre, s, packed, saved, dy, dparams, df_pre, workspace, ws_bytes=None,
                  stream=None):
-    check(load().gnn_backward(ptr(f_pre), s, ptr(packed), ptr(saved), ptr(dy), ptr(dparams),
-                              ptr(df_pre), ptr(workspace),
+    n, _, fe = _elems(s)
+    f32 = _f32()
+    check(load().gnn_backward(dptr(f_pre, "f_pre", f32, fe), s,
+                              dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
+                              dptr(saved, "saved", nbytes_min=gnn_saved_bytes(s)),
+                              dptr(dy, "dy", f32, 10 * n),
+                              dptr(dparams, "dparams", f32, gnn_trainable_count()),
+                              dptr(df_pre, "df_pre", f32, fe), dptr(workspace, "workspace"),
                               int(nbytes(workspace) if ws_bytes is None else ws_bytes),
                               stream_ptr(stream)), "gnn_backward")
 
 
 def gnn_adamw(params, grads, m, v, step, lr, wd, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
-    check(load().gnn_adamw(ptr(params), ptr(grads), ptr(m), ptr(v), int(step), float(lr),
+    nt, f32 = gnn_trainable_count(), _f32()
+    check(load().gnn_adamw(dptr(params, "params", f32, nt), dptr(grads, "grads", f32, nt),
+                           dptr(m, "m", f32, nt), dptr(v, "v", f32, nt), int(step), float(lr),
                            float(wd), float(beta1), float(beta2), float(eps), stream_ptr(stream)),
           "gnn_adamw")
 
@@ -320,9 +429,15 @@ def gnn_train_workspace_bytes(s):
 
 def gnn_train_step(f_in, f_target, s, tau, taus, params, packed, adam_m, adam_v, step, lr, wd,
                    loss, grads, workspace, ws_bytes=None, stream=None):
-    check(load().gnn_train_step(ptr(f_in), ptr(f_target), s, float(tau), ptr(taus), ptr(params),
-                                ptr(packed), ptr(adam_m), ptr(adam_v), int(step), float(lr),
-                                float(wd), ptr(loss), ptr(grads), ptr(workspace),
+    _, _, fe = _elems(s)
+    nt, f32 = gnn_trainable_count(), _f32()
+    check(load().gnn_train_step(dptr(f_in, "f_in", f32, fe), dptr(f_target, "f_target", f32, fe),
+                                s, float(tau), dptr(taus, "taus", f32, int(s.nb)),
+                                dptr(params, "params", f32, gnn_param_count()),
+                                dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
+                                dptr(adam_m, "adam_m", f32, nt), dptr(adam_v, "adam_v", f32, nt),
+                                int(step), float(lr), float(wd), dptr(loss, "loss", _f64(), 1),
+                                dptr(grads, "grads", f32, nt), dptr(workspace, "workspace"),
                                 int(nbytes(workspace) if ws_bytes is None else ws_bytes),
                                 stream_ptr(stream)), "gnn_train_step")
 
@@ -330,8 +445,12 @@ def gnn_train_step(f_in, f_target, s, tau, taus, params, packed, adam_m, adam_v,
 def lbm_step_gnn_noalloc(f_in, f_out, s, tau, taus, packed, totals, stream=None):
     """lbm_step_gnn with the library's fixed internal scratch (no workspace
     argument, nothing allocated; see include/lbmgnn.h)."""
-    check(load().lbm_step_gnn_noalloc(ptr(f_in), ptr(f_out), s, float(tau), ptr(taus),
-                                      ptr(packed), ptr(totals), stream_ptr(stream)),
+    _, _, fe = _elems(s)
+    f32 = _f32()
+    check(load().lbm_step_gnn_noalloc(dptr(f_in, "f_in", f32, fe), dptr(f_out, "f_out", f32, fe),
+                                      s, float(tau), dptr(taus, "taus", f32, int(s.nb)),
+                                      dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
+                                      dptr(totals, "totals", _f64(), 5), stream_ptr(stream)),
           "lbm_step_gnn_noalloc")
 
 
@@ -370,13 +489,19 @@ def lbm_batch_init_tgv(plan, f, params, pressure_consistent=False, stream=None):
     """params: host float64 array [n][4] = (rho0, u0, kx, ky)."""
     import numpy as np
     prm = np.ascontiguousarray(params, dtype=np.float64)
-    check(load().lbm_batch_init_tgv(plan, ptr(f), prm.ctypes.data, int(bool(pressure_consistent)),
-                                    stream_ptr(stream)), "lbm_batch_init_tgv")
+    fe = 9 * max(lbm_batch_nodes(plan), 0) if plan else 0
+    check(load().lbm_batch_init_tgv(plan, dptr(f, "f", _f32(), fe), prm.ctypes.data,
+                                    int(bool(pressure_consistent)), stream_ptr(stream)),
+          "lbm_batch_init_tgv")
 
 
 def lbm_batch_run(plan, f_in, f_out, f_tmp, steps, packed, workspace, ws_bytes=None, stream=None):
-    check(load().lbm_batch_run(plan, ptr(f_in), ptr(f_out), ptr(f_tmp), int(steps), ptr(packed),
-                               ptr(workspace),
+    fe = 9 * max(lbm_batch_nodes(plan), 0) if plan else 0
+    f32 = _f32()
+    check(load().lbm_batch_run(plan, dptr(f_in, "f_in", f32, fe), dptr(f_out, "f_out", f32, fe),
+                               dptr(f_tmp, "f_tmp", f32, fe), int(steps),
+                               dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
+                               dptr(workspace, "workspace"),
                                int(nbytes(workspace) if ws_bytes is None else ws_bytes),
                                stream_ptr(stream)), "lbm_batch_run")
 
