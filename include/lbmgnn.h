@@ -46,18 +46,18 @@ enum {
   LBM_ERR_ALIAS = -2,      /* an output buffer aliases an input buffer */
   LBM_ERR_SIZE = -3,       /* nx, ny, nb or plane_stride out of range */
   LBM_ERR_TAU = -4,        /* tau <= 1/2 (negative viscosity) or not finite */
-  LBM_ERR_BLOB = -5,       /* parameter blob of the wrong size or version */
+  LBM_ERR_BLOB = -5,       /* packed parameter image invalid (see gnn_pack) */
   LBM_ERR_CUDA = -6,       /* a CUDA runtime call failed */
   LBM_ERR_NONFINITE = -7,  /* a kernel produced a NaN or Inf population */
   LBM_ERR_TIMEOUT = -8,    /* a device-side wait gave up */
-  LBM_ERR_BOUNDS = -9,     /* a device-side bounds check failed (reserved) */
+  LBM_ERR_BOUNDS = -9,     /* a gather index failed its bounds check (checked build) */
   LBM_ERR_WORKSPACE = -10  /* workspace missing or smaller than required */
 };
 
 typedef struct {
   int32_t nx, ny;        /* nodes per lattice in x and y, each >= 1 */
-  int32_t nb;            /* number of stacked lattices, >= 1 */
-  int64_t plane_stride;  /* elements between planes; 0 = nb*ny*nx */
+  int32_t nb;            /* number of stacked lattices, >= 1; nb*ny*nx <= 2^36 */
+  int64_t plane_stride;  /* elements between planes (>= nb*ny*nx); 0 = nb*ny*nx */
 } lbm_shape;
 
 /* Human-readable name of a status code (static string). */
