@@ -63,6 +63,15 @@ typedef struct {
 /* Human-readable name of a status code (static string). */
 LBM_API const char* lbm_status_string(int status);
 
+/* Versions of this library (no counterpart in the paper; host-only, no GPU
+ * needed): *abi receives LBM_ABI_VERSION, the version of the calls and
+ * structs declared here, *packed_layout the layout version of the packed
+ * parameter image that gnn_pack writes and the kernels check.  Either
+ * pointer may be NULL.  Returns LBM_OK. */
+#define LBM_ABI_VERSION 1
+#define LBM_PACKED_LAYOUT_VERSION 1
+LBM_API int lbm_version(int* abi, int* packed_layout);
+
 /* Waits for `stream`, then reads and clears the device status word of the
  * current device.  Returns LBM_OK, or the most severe of LBM_ERR_TIMEOUT,
  * LBM_ERR_BOUNDS, LBM_ERR_BLOB, LBM_ERR_NONFINITE raised since the last

@@ -100,6 +100,12 @@ const char* lbm_status_string(int status) {
   }
 }
 
+int lbm_version(int* abi, int* packed_layout) {
+  if (abi) *abi = LBM_ABI_VERSION;
+  if (packed_layout) *packed_layout = LBM_PACKED_LAYOUT_VERSION;
+  return LBM_OK;
+}
+
 int lbm_get_status(void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (cudaStreamSynchronize(st) != cudaSuccess) return LBM_ERR_CUDA;

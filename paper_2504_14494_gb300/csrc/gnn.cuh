@@ -70,10 +70,12 @@ constexpr uint32_t W1X = ROUND0 + 2 * ROUND_SIZE;  // 162816
 constexpr uint32_t TOTAL = W1X + 8192;              // 171008
 __host__ __device__ constexpr uint32_t round_base(int r) { return ROUND0 + r * ROUND_SIZE; }
 // Validity word of the image (slot 31 of NORM), written by the pack kernel
-// when the fixed values of the parameter vector are usable: "LBG1", layout
-// version 1.
+// when the fixed values of the parameter vector are usable: "LBG" followed
+// by the layout version (LBM_PACKED_LAYOUT_VERSION, as an ASCII digit).
 constexpr uint32_t MAGIC_SLOT = NORM + 31 * 4;
-constexpr uint32_t MAGIC = 0x4C424731u;
+constexpr uint32_t MAGIC = 0x4C424730u + LBM_PACKED_LAYOUT_VERSION;
+static_assert(LBM_PACKED_LAYOUT_VERSION >= 1 && LBM_PACKED_LAYOUT_VERSION <= 9,
+              "layout version is one ASCII digit of the validity word");
 }  // namespace K
 
 // Every kernel that reads a packed image checks its validity word first; on

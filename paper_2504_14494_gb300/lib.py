@@ -51,6 +51,7 @@ LBM_COLLIDE_BGK, LBM_COLLIDE_GNN = 0, 1
 _VP = ctypes.c_void_p
 _SIGS = {
     "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "lbm_version": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "lbm_get_status": (ctypes.c_int, [_VP]),
     "lbm_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_longlong, _VP]),
     "lbm_init_tgv": (ctypes.c_int, [_VP, lbm_shape, ctypes.c_double, ctypes.c_double,
@@ -220,6 +221,13 @@ def check(rc, what=""):
 
 def status_string(code):
     return load().lbm_status_string(int(code)).decode()
+
+
+def lbm_version():
+    """(ABI version, packed-parameter layout version) of the loaded library."""
+    abi, layout = ctypes.c_int(0), ctypes.c_int(0)
+    check(load().lbm_version(ctypes.byref(abi), ctypes.byref(layout)), "lbm_version")
+    return abi.value, layout.value
 
 
 # --- BGK path ------------------------------------------------------------------------

@@ -49,6 +49,8 @@ static int host_part(void) {
     sum += theta[i];
     sum_abs += fabs(theta[i]);
   }
+  int abi = 0, layout = 0;
+  CHECK(lbm_version(&abi, &layout));
   /* a NULL vector and an unknown variant are rejected */
   const int bad_null = gnn_params_init_xavier(NULL, 5, 1e-2f, 0);
   const int bad_variant = gnn_params_init_xavier(theta, 5, 1e-2f, 4);
@@ -56,11 +58,11 @@ static int host_part(void) {
          "\"step_ws\": %zu, \"host_ws\": %zu, \"saved_bytes\": %zu, "
          "\"xavier_sum\": %.17g, \"xavier_sum_abs\": %.17g, \"xavier_first\": %.9g, "
          "\"xavier_last\": %.9g, \"bad_null\": %d, \"bad_variant\": %d, "
-         "\"status_ok\": \"%s\", \"status_tau\": \"%s\"}\n",
+         "\"status_ok\": \"%s\", \"status_tau\": \"%s\", \"abi\": %d, \"layout\": %d}\n",
          np, gnn_trainable_count(), gnn_packed_bytes(), gnn_step_workspace_bytes(s),
          lbm_host_workspace_bytes(s), gnn_saved_bytes(s), sum, sum_abs, theta[0],
          theta[np - 1], bad_null, bad_variant, lbm_status_string(LBM_OK),
-         lbm_status_string(LBM_ERR_TAU));
+         lbm_status_string(LBM_ERR_TAU), abi, layout);
   free(theta);
   return 0;
 }

@@ -66,3 +66,14 @@ def test_binding_raises_on_error(lbmlib):
     with pytest.raises(L.LbmError) as ei:
         L.lbm_step_bgk(None, None, None, L.shape(4, 4), 0.8, stream=0)
     assert ei.value.code == -1
+
+
+def test_versions(lbmlib):
+    """lbm_version: the ABI and packed-layout versions the header declares."""
+    L = lbmlib
+    header = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                               "include", "lbmgnn.h")).read()
+    abi = int(re.search(r"#define LBM_ABI_VERSION (\d+)", header).group(1))
+    layout = int(re.search(r"#define LBM_PACKED_LAYOUT_VERSION (\d+)", header).group(1))
+    assert L.lbm_version() == (abi, layout)
+    assert L.load().lbm_version(None, None) == L.LBM_OK

@@ -63,6 +63,7 @@ def test_host_calls_from_c_agree_with_the_binding(consumer):
     assert got["bad_null"] == L.LBM_ERR_ARG and got["bad_variant"] == L.LBM_ERR_ARG
     assert got["status_ok"] == L.status_string(L.LBM_OK)
     assert got["status_tau"] == L.status_string(L.LBM_ERR_TAU)
+    assert (got["abi"], got["layout"]) == L.lbm_version()
 
 
 @pytest.mark.gpu
