@@ -37,6 +37,7 @@ U0 = W.TGV_4096.u0
 TAU = W.TGV_4096.tau
 TAU_SWEEP = W.TGV_4096.tau_sweep
 BYTES_PER_NODE = 72  # 9 FP32 loads + 9 FP32 stores
+RUNS = 5  # the timed steps are split into this many consecutive runs; median run reported
 
 # DRAM bytes per launch from one ncu capture of the kernel, keyed by the
 # SHA-256 of its source file at capture time; ignored once the source changed.
@@ -207,16 +208,23 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # The K timed steps run back to back as R consecutive runs of about K/R
+    # steps, an event on the launching stream between runs; the headline
+    # takes the median run (per-step time), the whole region is reported too.
+    runs = chunk_sizes(args.steps, RUNS)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(runs) + 1)]
     with ClockSampler(local_rank) as clk:
-        ev0.record(stream)
-        steps(args.steps, TAU, bufs)
-        ev1.record(stream)
+        evs[0].record(stream)
+        for i, c in enumerate(runs):
+            steps(c, TAU, bufs)
+            evs[i + 1].record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
+    ms_region = evs[0].elapsed_time(evs[-1])
+    per_step = [evs[i].elapsed_time(evs[i + 1]) / c for i, c in enumerate(runs)]
+    ms = statistics.median(per_step) * args.steps
     if dist:
         dist.barrier()
-    # node updates summed over ranks / the slowest rank's time
+    # node updates summed over ranks / the slowest rank's (median-run) time
     _, t_max, rate = parallel.aggregate_throughput(nodes * args.steps, ms, device=dev)
     done_steps = args.warmup + args.steps
     assert L.lbm_get_status() == 0
@@ -247,24 +255,29 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the C ABI with host buffers (lbm_step_bgk_host): per
     # step the state is copied from pinned host memory (in row blocks that
-    # overlap the step), stepped, and its FP64 totals copied back to the host.
-    host_in = torch.empty(9 * nodes, dtype=torch.float32, pin_memory=True)
+    # overlap the step), stepped, and the stepped state and its FP64 totals
+    # are copied back to pinned host memory.  The output of one step is the
+    # input of the next (host ping-pong), as a host-resident simulation runs.
+    host = [torch.empty(9 * nodes, dtype=torch.float32, pin_memory=True) for _ in range(2)]
     L.lbm_init_tgv(fa, s, 1.0, U0, k, k, False)
-    host_in.copy_(fa)
+    host[0].copy_(fa)
     host_tot = torch.empty(5, dtype=torch.float64, pin_memory=True)
     hws = torch.empty(L.lbm_host_workspace_bytes(s), dtype=torch.uint8, device=dev)
     ke = max(3, min(args.steps, 30))
     for _ in range(3):
-        L.lbm_step_bgk_host(host_in, None, s, TAU, None, 1, host_tot, hws)
+        L.lbm_step_bgk_host(host[0], host[1], s, TAU, None, 1, host_tot, hws)
+        host.reverse()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(ke):
-        L.lbm_step_bgk_host(host_in, None, s, TAU, None, 1, host_tot, hws)
+        L.lbm_step_bgk_host(host[0], host[1], s, TAU, None, 1, host_tot, hws)
+        host.reverse()
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / ke
     assert L.lbm_get_status() == 0
+    e2e_l2 = tgv_l2(L, host[0].to(dev), s, n, U0, TAU, 3 + ke, dev)
 
     thetas, train_info = train_bench(args, L, dev, stream)
     names = {0: "message passing (Eq. 3 as printed)", 2: "message passing, conserving correction",
@@ -293,6 +306,11 @@ def run_ours(args, rank, world, local_rank):
         "unit": "MLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms_step, 5),
+        "timing": {"runs": len(runs), "steps_per_run": runs,
+                   "median_run_ms_per_step": round(statistics.median(per_step), 5),
+                   "run_ms_per_step": [round(v, 5) for v in per_step],
+                   "whole_region_ms_per_step": round(ms_region / args.steps, 5),
+                   "headline": "median run"},
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "tgv_bgk_4096x4096", "nx": n, "ny": n, "tau": TAU,
@@ -307,7 +325,10 @@ def run_ours(args, rank, world, local_rank):
         "tau_sweep": sweep,
         "tgv64": small_tgv_bench(L, dev),
         "e2e": {"value": round(nodes / (e2e_ms / 1e3) / 1e6, 1), "unit": "MLUPS",
-                "h2d_bytes_per_step": 9 * nodes * 4, "d2h_bytes_per_step": 5 * 8},
+                "h2d_bytes_per_step": 9 * nodes * 4, "d2h_bytes_per_step": 9 * nodes * 4 + 5 * 8,
+                "call": "lbm_step_bgk_host: pinned host state in, stepped state and FP64 "
+                        "totals out, every step",
+                "velocity_l2_error": e2e_l2},
         "clocks": clk.summary(),
         "gpu_launches": args.steps,
         "gnn": gnn,
@@ -315,7 +336,53 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
         out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores()
+        out["cpu_baseline"]["gnn"] = cpu_baseline_gnn()
     return out
+
+
+def chunk_sizes(k, r):
+    """k steps as min(r, k) consecutive runs of near-equal length."""
+    r = max(1, min(r, k))
+    return [k // r + (1 if i < k % r else 0) for i in range(r)]
+
+
+def _gnn_oracle_worker(args):
+    """One host core: the oracle GNN-LBM step (brute-force 130-wide edge MLP,
+    numpy FP64) on an n x n TGV at Re = 1000, `count` steps."""
+    n, count = args
+    from oracle import gnn, lbm
+    from paper_2504_14494_gb300 import inputs
+    theta = inputs.xavier_params(W.TGV_GNN_1024.weight_seed)
+    k = 2 * np.pi / n
+    tau = 0.5 + 3.0 * U0 * n / W.TGV_GNN_1024.re
+    f = lbm.tgv_init(n, n, 1.0, U0, k, k)
+    t0 = time.perf_counter()
+    for _ in range(count):
+        f = gnn.gnn_step(f, theta, tau)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_gnn(n=256, count=3):
+    """The FP64 oracle's GNN-LBM step, as it stands, on one host core (BLAS
+    limited to one thread in a spawned process): n x n TGV, `count` steps."""
+    import multiprocessing as mp
+    saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                             "MKL_NUM_THREADS")}
+    for v in saved:
+        os.environ[v] = "1"
+    try:
+        with mp.get_context("spawn").Pool(1) as pool:
+            dt = pool.map(_gnn_oracle_worker, [(n, count)])[0]
+    finally:
+        for v, old in saved.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+    return {"value": round(n * n * count / dt / 1e6, 4), "unit": "MLUPS", "cores": 1,
+            "kind": "oracle",
+            "sample": f"oracle.gnn.gnn_step (numpy FP64, brute-force 130-wide edge MLP) on a "
+                      f"{n}x{n} TGV at Re = 1000, {count} steps, {dt:.1f} s"}
 
 
 def small_tgv_bench(L, dev, n=W.TGV_64.n, tau=W.TGV_64.tau, u0=W.TGV_64.u0,

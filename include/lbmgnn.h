@@ -147,8 +147,11 @@ LBM_API size_t lbm_host_workspace_bytes(lbm_shape s);
  * 16 blocks of lattice rows (one 2D copy of the 9 planes per block);
  * the first step of a block is launched on `stream` as soon as the rows it
  * pulls from (y -+ 1 with periodic wrap) have arrived, so the copy overlaps
- * the step.  Overlap needs page-locked host memory; pageable memory works
- * without it.  Asynchronous on `stream`: host outputs are valid, and host
+ * the step.  The final step is also launched by row blocks, and each block of
+ * the final state is copied to f_out_host on a third stream as soon as its
+ * kernel is done (overlapping the rest of the step and, for nsteps == 1, the
+ * host-to-device copy of the remaining blocks).  Overlap needs page-locked
+ * host memory; pageable memory works without it.  Asynchronous on `stream`: host outputs are valid, and host
  * inputs may be reused, once `stream` has completed the call's work.
  * workspace: device, 256-byte aligned, lbm_host_workspace_bytes(s) bytes, not
  * used by another call in flight on another stream.  Errors as lbm_step_bgk;

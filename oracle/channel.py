@@ -7,7 +7,7 @@ Paper passages followed:
     force (pressure gradient) G: u(y) = G/(2 mu) y (H - y).
   * Fig. 1 "Apply Boundary Conditions" (no scheme is given).
 
-Readings (also listed in the design doc):
+Readings where the paper gives no scheme:
   * Channel along x, periodic in x; walls halfway between node rows, at
     y = -1/2 and y = ny - 1/2, so H = ny and the wall-distance of row y is
     y + 1/2.  Halfway bounce-back: a population that would be pulled from

@@ -12,7 +12,7 @@ Paper passages followed:
     predicts the corrections Delta f_i directly.
   * Eq. 3 -- f_i^* = f_i - (f_i - f_i^eq)/(tau tau_adj) + Delta f_i.
 
-Readings where the paper gives no formula (also listed in the design doc):
+Readings where the paper gives no formula:
   * Widths: encoder 12-64-64 (two Linear layers, each followed by GELU),
     two message-passing rounds with separate weights, edge MLP 130->64 and
     node MLP 128->64 (each one Linear + GELU), head 64->10 (linear).

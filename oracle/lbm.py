@@ -11,7 +11,7 @@ Paper passages followed:
   * Sec. 3.2         -- Taylor-Green vortex benchmark and its analytic decay.
   * Sec. 3.3, Eq. 6  -- convergence rate alpha = log(E1/E2)/log(h1/h2).
 
-Readings of passages the paper leaves open (each also listed in the design doc):
+Readings of passages the paper leaves open:
   * D2Q9 velocity order and weights (Sec. 2.1 names w_i and c_s but lists no
     values): e_0=(0,0); e_1..4=(1,0),(0,1),(-1,0),(0,-1);
     e_5..8=(1,1),(-1,1),(-1,-1),(1,-1); w = 4/9, 1/9 (x4), 1/36 (x4); c_s^2=1/3.

@@ -7,7 +7,7 @@ Paper passages followed:
   * Sec. 2.4 -- supervised training on pairs generated by high-resolution
     standard LBM runs; the loss is Eq. 4 (``oracle.gnn.collide_loss``).
 
-Readings where the paper is silent (also listed in the design doc):
+Readings where the paper is silent:
   * "High resolution" = an m-times refined lattice (m = 4 by default) under
     acoustic scaling: the same lattice velocity u0, k_f = k_c / m,
     tau_f = 1/2 + m (tau_c - 1/2), and m fine steps per coarse step.

@@ -52,9 +52,12 @@ bool overlap(const void* a, const void* b, int64_t bytes) {
 constexpr int HOST_CHUNKS = LBM_HOST_CHUNKS;
 struct HostPipe {
   bool ready = false;
-  cudaStream_t copy = nullptr;
+  cudaStream_t copy = nullptr;      // host-to-device row blocks
+  cudaStream_t copy_out = nullptr;  // device-to-host row blocks of the final state
   cudaEvent_t entry = nullptr;
+  cudaEvent_t out_done = nullptr;
   cudaEvent_t arrived[HOST_CHUNKS] = {};
+  cudaEvent_t stepped[HOST_CHUNKS] = {};
 };
 std::mutex g_pipe_mu;
 HostPipe g_pipe[64];
@@ -65,8 +68,14 @@ HostPipe* host_pipe() {
   HostPipe& p = g_pipe[dev];
   if (!p.ready) {
     if (cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (cudaStreamCreateWithFlags(&p.copy_out, cudaStreamNonBlocking) != cudaSuccess)
+      return nullptr;
     if (cudaEventCreateWithFlags(&p.entry, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&p.out_done, cudaEventDisableTiming) != cudaSuccess)
+      return nullptr;
     for (auto& e : p.arrived)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    for (auto& e : p.stepped)
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
     p.ready = true;
   }
@@ -277,23 +286,36 @@ int lbm_step_bgk_host(const float* f_in_host, float* f_out_host, lbm_shape shape
     return LBM_ERR_CUDA;
   if (totals_host && cudaMemsetAsync(dtot, 0, 5 * sizeof(double), st) != cudaSuccess)
     return LBM_ERR_CUDA;
-  for (int c = 0; c < used; ++c) {
+  // rows [r0, r1) of all 9 planes between host and device (one 2D copy)
+  auto copy_rows = [&](float* dst, const float* src, int c, cudaMemcpyKind kind,
+                       cudaStream_t cs) -> bool {
     const int64_t r0 = c * per, r1 = std::min(rows, r0 + per);
     const size_t width = (size_t)((r1 - r0) * s.nx) * sizeof(float);
     const size_t pitch = (size_t)s.ps * sizeof(float);
     const int64_t off = r0 * s.nx;
-    if (pitch < (size_t(1) << 31)) {  // the block of all 9 planes as one 2D copy
-      if (cudaMemcpy2DAsync(da + off, pitch, f_in_host + off, pitch, width, Q,
-                            cudaMemcpyHostToDevice, p->copy) != cudaSuccess)
-        return LBM_ERR_CUDA;
-    } else {
-      for (int q = 0; q < Q; ++q)
-        if (cudaMemcpyAsync(da + q * s.ps + off, f_in_host + q * s.ps + off, width,
-                            cudaMemcpyHostToDevice, p->copy) != cudaSuccess)
-          return LBM_ERR_CUDA;
-    }
+    if (pitch < (size_t(1) << 31))
+      return cudaMemcpy2DAsync(dst + off, pitch, src + off, pitch, width, Q, kind, cs) ==
+             cudaSuccess;
+    for (int q = 0; q < Q; ++q)
+      if (cudaMemcpyAsync(dst + q * s.ps + off, src + q * s.ps + off, width, kind, cs) !=
+          cudaSuccess)
+        return false;
+    return true;
+  };
+  for (int c = 0; c < used; ++c) {
+    if (!copy_rows(da, f_in_host, c, cudaMemcpyHostToDevice, p->copy)) return LBM_ERR_CUDA;
     if (cudaEventRecord(p->arrived[c], p->copy) != cudaSuccess) return LBM_ERR_CUDA;
   }
+  // The final step is launched block by block; each block's rows of the final
+  // state go back to the host on copy_out as soon as its kernel is done, so
+  // the device-to-host copy overlaps the rest of the step (and, on the first
+  // step, the host-to-device copy of the remaining blocks).
+  auto block_done = [&](float* fin_dev, int c) -> bool {
+    if (!f_out_host) return true;
+    return cudaEventRecord(p->stepped[c], st) == cudaSuccess &&
+           cudaStreamWaitEvent(p->copy_out, p->stepped[c], 0) == cudaSuccess &&
+           copy_rows(f_out_host, fin_dev, c, cudaMemcpyDeviceToHost, p->copy_out);
+  };
   // first step, block by block in order of readiness
   std::vector<int> order(used);
   for (int c = 0; c < used; ++c) order[c] = c;
@@ -308,6 +330,7 @@ int lbm_step_bgk_host(const float* f_in_host, float* f_out_host, lbm_shape shape
     const int64_t r0 = c * per, r1 = std::min(rows, r0 + per);
     if (launch_bgk_step_rows(da, db, s, tau, dtaus, tot1, r0, r1, st) != cudaSuccess)
       return LBM_ERR_CUDA;
+    if (nsteps == 1 && !block_done(db, c)) return LBM_ERR_CUDA;
   }
   // (need[c] >= c, so st has waited for the last block: the copy stream has
   // no work left that st does not wait for.)  Remaining steps: db -> da -> ...
@@ -315,17 +338,27 @@ int lbm_step_bgk_host(const float* f_in_host, float* f_out_host, lbm_shape shape
   float* dst = da;
   for (int k = 1; k < nsteps; ++k) {
     const bool last = (k == nsteps - 1);
-    if (launch_bgk_step(src, dst, s, tau, dtaus, (last && totals_host) ? dtot : nullptr, st) !=
-        cudaSuccess)
+    double* tk = (last && totals_host) ? dtot : nullptr;
+    if (last && f_out_host) {
+      for (int c = 0; c < used; ++c) {
+        const int64_t r0 = c * per, r1 = std::min(rows, r0 + per);
+        if (launch_bgk_step_rows(src, dst, s, tau, dtaus, tk, r0, r1, st) != cudaSuccess ||
+            !block_done(dst, c))
+          return LBM_ERR_CUDA;
+      }
+    } else if (launch_bgk_step(src, dst, s, tau, dtaus, tk, st) != cudaSuccess) {
       return LBM_ERR_CUDA;
+    }
     std::swap(src, dst);
   }
   if (totals_host && cudaMemcpyAsync(totals_host, dtot, 5 * sizeof(double),
                                      cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return LBM_ERR_CUDA;
-  if (f_out_host && cudaMemcpyAsync(f_out_host, src, (size_t)f_bytes(s),
-                                    cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return LBM_ERR_CUDA;
+  if (f_out_host) {  // the caller's stream completes only after the last block is back
+    if (cudaEventRecord(p->out_done, p->copy_out) != cudaSuccess ||
+        cudaStreamWaitEvent(st, p->out_done, 0) != cudaSuccess)
+      return LBM_ERR_CUDA;
+  }
   return LBM_OK;
 }
 

@@ -22,6 +22,7 @@
 // Nothing in it needs to start at zero (every value the kernels read from it
 // was written earlier in the same call), but calls that overlap on the GPU
 // (on different streams, or from several host threads) race on it.
+#include <atomic>
 #include <cmath>
 
 #include "common.cuh"
@@ -35,17 +36,19 @@ constexpr size_t NOALLOC_BYTES = (size_t)NOALLOC_MAX_NODES * 512;
 static __device__ __align__(256) unsigned char g_gnn_step_scratch[NOALLOC_BYTES];
 
 // Device address of the scratch array on the current device (set-up on the
-// first use per device); nullptr if the lookup failed.
+// first use per device); nullptr if the lookup failed.  The per-device cache
+// is atomic: host threads whose first calls race each look the address up
+// and store the same value.
 void* scratch_address() {
-  static void* addr[64] = {nullptr};
+  static std::atomic<void*> addr[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  if (!addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_gnn_step_scratch) != cudaSuccess) return nullptr;
-    addr[dev] = p;
+  void* a = addr[dev].load(std::memory_order_acquire);
+  if (!a) {
+    if (cudaGetSymbolAddress(&a, g_gnn_step_scratch) != cudaSuccess) return nullptr;
+    addr[dev].store(a, std::memory_order_release);
   }
-  return addr[dev];
+  return a;
 }
 
 }  // namespace

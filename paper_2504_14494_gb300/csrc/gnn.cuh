@@ -248,6 +248,9 @@ __device__ __forceinline__ __half2 tanh_h2(__half2 x) {
   return u32_as_h2(y);
 }
 // GELU (tanh form) on two FP16 values: 0.5 z (1 + tanh(z (c0 + c1 z^2))).
+// Saturated arguments give exact results: z^2 may overflow to inf, which
+// only makes u = +-inf and tanh(u) = +-1, and hz + hz tanh(u) is one fused
+// operation, so a strongly negative z gives exactly 0.
 __device__ __forceinline__ __half2 gelu_h2(__half2 z) {
   const __half2 c0 = __float2half2_rn(0.7978845608028654f);
   const __half2 c1 = __float2half2_rn(0.0356774081363001f);
@@ -255,6 +258,15 @@ __device__ __forceinline__ __half2 gelu_h2(__half2 z) {
   const __half2 u = __hmul2(z, __hfma2(c1, __hmul2(z, z), c0));
   const __half2 hz = __hmul2(hh, z);
   return __hfma2(hz, tanh_h2(u), hz);
+}
+
+// z^2 for the GELU derivative in FP16, capped at 64.  z^2 itself overflows
+// FP16 for |z| >= 256, and inf times the exact zero 1 - t^2 of the saturated
+// tanh would give NaN.  Beyond |z| = 8 the cap changes nothing: u = z (c0 +
+// 64 c1) is then past 24, where tanh(u) is +-1 in FP16, so the derivative is
+// already its saturated value (1 for z > 0, 0 for z < 0).
+__device__ __forceinline__ __half2 zsq_capped_h2(__half2 z) {
+  return __hmin2(__hmul2(z, z), __float2half2_rn(64.0f));
 }
 
 // Derivative of the tanh-form GELU on two FP16 values:
@@ -265,7 +277,7 @@ __device__ __forceinline__ __half2 gelu_grad_h2(__half2 z) {
   const __half2 c3 = __float2half2_rn(0.1070322244089003f);
   const __half2 hh = __float2half2_rn(0.5f);
   const __half2 one = __float2half2_rn(1.0f);
-  const __half2 z2 = __hmul2(z, z);
+  const __half2 z2 = zsq_capped_h2(z);
   const __half2 t = tanh_h2(__hmul2(z, __hfma2(c1, z2, c0)));
   const __half2 q = __hmul2(__hmul2(z, __hfma2(__hneg2(t), t, one)), __hfma2(c3, z2, c0));
   return __hfma2(hh, __hadd2(t, q), hh);
@@ -279,7 +291,7 @@ __device__ __forceinline__ __half2 gelu_grad2_h2(__half2 z) {
   const __half2 c1 = __float2half2_rn(0.0356774081363001f);
   const __half2 c3 = __float2half2_rn(0.1070322244089003f);
   const __half2 one = __float2half2_rn(1.0f);
-  const __half2 z2 = __hmul2(z, z);
+  const __half2 z2 = zsq_capped_h2(z);
   const __half2 t = tanh_h2(__hmul2(z, __hfma2(c1, z2, c0)));
   const __half2 zr = __hmul2(z, __hfma2(__hneg2(t), t, one));
   return __hfma2(zr, __hfma2(c3, z2, c0), __hadd2(t, one));

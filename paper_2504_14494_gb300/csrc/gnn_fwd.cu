@@ -406,8 +406,9 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
         aw[0] = a0.x, aw[1] = a0.y, aw[2] = a0.z, aw[3] = a0.w;
         aw[4] = a1.x, aw[5] = a1.y, aw[6] = a1.z, aw[7] = a1.w;
       }
-      // Each message is accumulated as z + z tanh(u) (= 2 GELU(z)); the 1/2 is
-      // applied once to the sum.
+      // Each message 2 GELU(z) = z + z tanh(u) is formed by one fused
+      // operation (exactly 0 once tanh(u) saturates at -1, however large |z|)
+      // and then added to the sum; the 1/2 is applied once to the sum.
       __half2 acc[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) acc[c] = __float2half2_rn(0.0f);
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
           for (int c = 0; c < 8; ++c) {
             const __half2 z = __hadd2(__hadd2(u32_as_h2(aw[c]), c_k[c]), u32_as_h2(bw[c]));
             const __half2 u = __hmul2(z, __hfma2(c1h, __hmul2(z, z), c0h));
-            acc[c] = __hfma2(z, tanh_h2(u), __hadd2(acc[c], z));
+            acc[c] = __hadd2(acc[c], __hfma2(z, tanh_h2(u), z));
           }
         }
       }

@@ -175,6 +175,15 @@ def _device_totals(view):
     return out
 
 
+# D2Q9 populations that cross a row boundary of the slab in one streaming
+# step: e_y = +1 (moving up: read by the row above from the row below) and
+# e_y = -1 (moving down).
+CROSS_UP = (2, 5, 6)
+CROSS_DOWN = (4, 7, 8)
+NOT_UP = tuple(q for q in range(9) if q not in CROSS_UP)
+NOT_DOWN = tuple(q for q in range(9) if q not in CROSS_DOWN)
+
+
 class SlabLattice:
     """One periodic nx x ny lattice split into row slabs over the ranks of
     `group`: rank r owns rows [ny r / P, ny (r + 1) / P) and keeps them with
@@ -182,13 +191,25 @@ class SlabLattice:
     (`f`).  `step(step_fn)` exchanges the ghost rows with the neighbouring
     ranks (periodic in y) and applies step_fn, a periodic step on a
     [9, R, nx] population tensor returning the stepped tensor.  With one
-    rank the ghost rows come from the slab's own periodic wrap."""
+    rank the ghost rows come from the slab's own periodic wrap.
 
-    def __init__(self, nx, ny, halo, device="cpu", dtype=None, group=None):
+    With one ghost row (the BGK step: streaming is the only coupling between
+    rows) only the 3 populations that stream across each face are exchanged
+    (`faces_only`, the default for halo 1): the owned rows read nothing else
+    from the ghost rows.  The other 6 populations of each ghost row are
+    filled locally from the adjacent owned row, so the ghost rows that
+    step_fn also steps hold plausible, finite states.  With more ghost rows
+    (the GNN step reads all populations of nodes up to 3 rows away) all 9
+    populations are exchanged."""
+
+    def __init__(self, nx, ny, halo, device="cpu", dtype=None, group=None, faces_only=None):
         import torch
         self.group = group
         self.rank, self.size = rank_and_size(group)
         self.nx, self.ny, self.halo = nx, ny, halo
+        self.faces_only = (halo == 1) if faces_only is None else bool(faces_only)
+        if self.faces_only and halo != 1:
+            raise ValueError("faces_only needs exactly one ghost row")
         self.r0 = ny * self.rank // self.size
         self.r1 = ny * (self.rank + 1) // self.size
         self.rows = self.r1 - self.r0
@@ -206,15 +227,26 @@ class SlabLattice:
 
     def exchange(self):
         """Ghost rows below <- the previous rank's top `halo` owned rows,
-        ghost rows above <- the next rank's bottom `halo` owned rows."""
+        ghost rows above <- the next rank's bottom `halo` owned rows (with
+        `faces_only`: the 3 populations crossing each face, 3 x nx values
+        each way instead of 9 x nx)."""
         import torch
         h, R = self.halo, self.rows
-        top = self.f[:, R:R + h].contiguous()        # my top owned rows
-        bottom = self.f[:, h:2 * h].contiguous()      # my bottom owned rows
+        if self.faces_only:
+            up, down = list(CROSS_UP), list(CROSS_DOWN)
+            top = self.f[up, R:R + 1].contiguous()       # moving up out of my top row
+            bottom = self.f[down, 1:2].contiguous()      # moving down out of my bottom row
+            # the rest of each ghost row: a local copy of the adjacent owned row
+            self.f[list(NOT_UP), 0:1] = self.f[list(NOT_UP), 1:2]
+            self.f[list(NOT_DOWN), R + 1:R + 2] = self.f[list(NOT_DOWN), R:R + 1]
+        else:
+            top = self.f[:, R:R + h].contiguous()        # my top owned rows
+            bottom = self.f[:, h:2 * h].contiguous()      # my bottom owned rows
+        gsel = (list(CROSS_UP), list(CROSS_DOWN)) if self.faces_only else (slice(None),) * 2
         dist = _dist()
         if dist is None or self.size == 1:
-            self.f[:, :h] = top
-            self.f[:, R + h:] = bottom
+            self.f[gsel[0], :h] = top
+            self.f[gsel[1], R + h:] = bottom
             return
         prev = (self.rank - 1) % self.size
         nxt = (self.rank + 1) % self.size
@@ -226,8 +258,8 @@ class SlabLattice:
                dist.P2POp(dist.irecv, above, nxt, self.group, 1)]
         for req in dist.batch_isend_irecv(ops):
             req.wait()
-        self.f[:, :h] = below
-        self.f[:, R + h:] = above
+        self.f[gsel[0], :h] = below
+        self.f[gsel[1], R + h:] = above
 
     def step(self, step_fn):
         self.exchange()
