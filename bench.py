@@ -162,6 +162,10 @@ def run_ours(args, rank, world, local_rank):
         res = gnn_bench(args, L, dev, torch.cuda.current_stream(), side=args.side, only=True)
         print(json.dumps(_finite({"case": f"gnn {args.side}x{args.side}", **res})))
         return None
+    if args.only == "mlp":
+        res = mlp_bench(args, L, dev, torch.cuda.current_stream(), side=args.side)
+        print(json.dumps(_finite({"case": f"gnn_mlp {args.side}x{args.side}", **res})))
+        return None
     if args.only == "batch":  # the 512-lattice serving batch, untrained conserving network
         from paper_2504_14494_gb300 import inputs
         theta = inputs.xavier_params(W.TGV_GNN_1024.weight_seed, variant=2)
@@ -290,7 +294,8 @@ def run_ours(args, rank, world, local_rank):
            "batch": batch_bench(args, L, dev, stream, thetas[2]),
            "stability": {str(v): stability_bench(L, dev, thetas[v], res=(400.0, 1600.0, 3200.0))
                          for v in (0, 2)},
-           "poiseuille": channel_bench(L, dev)}
+           "poiseuille": channel_bench(L, dev),
+           "mlp_fused": mlp_bench(args, L, dev, stream, theta=thetas[3])}
 
     if rank != 0:
         return None
@@ -533,6 +538,67 @@ def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False, theta=None, label
             "gnn_rollout_diverged": not np.isfinite(res["gnn"]["l2_error"]),
             "gnn_over_bgk_time": round(res["gnn"]["ms_per_step"] / res["bgk"]["ms_per_step"], 2),
             "status": res["gnn"]["status"]}
+
+
+MLP_SIDE = 4096
+
+
+def mlp_bench(args, L, dev, stream, theta=None, side=MLP_SIDE):
+    """The paper's Fig. 2 network (MLP-only; here with the conserving
+    correction, variant 3) stepped by the fused kernel lbm_step_gnn_mlp on
+    the side x side TGV (u0 = 0.05, Re = 1000 by tau): MLUPS beside the BGK
+    step on the same lattice, and the HBM roofline of the fused kernel (72
+    algorithmic bytes per node, as BGK; the two 604 MB buffers exceed L2)."""
+    import torch
+    from paper_2504_14494_gb300 import inputs
+    n = side
+    s = L.shape(n, n)
+    k = 2 * np.pi / n
+    tau = 0.5 + 3.0 * U0 * n / GNN_RE
+    if theta is None:
+        theta = inputs.xavier_params(0, s_df=1e-4, variant=3)
+    packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=dev)
+    L.gnn_pack(torch.from_numpy(np.asarray(theta, np.float32)).to(dev), packed)
+    fa = torch.empty(9 * n * n, device=dev)
+    fb = torch.empty_like(fa)
+    kk = max(10, min(args.steps, 200))
+    res = {}
+    for kind in ("mlp", "bgk"):
+        L.lbm_init_tgv(fa, s, 1.0, U0, k, k, False)
+        bufs = [fa, fb]
+
+        def run(count):
+            for _ in range(count):
+                if kind == "mlp":
+                    L.lbm_step_gnn_mlp(bufs[0], bufs[1], s, tau, None, packed, None)
+                else:
+                    L.lbm_step_bgk(bufs[0], bufs[1], None, s, tau)
+                bufs.reverse()
+        run(max(3, args.warmup))
+        torch.cuda.synchronize()
+        runs = chunk_sizes(kk, RUNS)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(runs) + 1)]
+        evs[0].record(stream)
+        for i, c in enumerate(runs):
+            run(c)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median(evs[i].elapsed_time(evs[i + 1]) / c for i, c in enumerate(runs))
+        res[kind] = {"ms_per_step": round(ms, 5), "mlups": round(n * n / (ms / 1e3) / 1e6, 1),
+                     "status": L.lbm_get_status()}
+    peak, peak_kind = _peaks()
+    ach = BYTES_PER_NODE * n * n / (res["mlp"]["ms_per_step"] / 1e3) / 1e9
+    return {"workload": f"tgv_gnn_mlp_{n}x{n}", "network": "Fig. 2 MLP-only, conserving (variant 3)",
+            "call": "lbm_step_gnn_mlp (one fused kernel: gnn_mlp_step_kernel)", "tau": round(tau, 5),
+            "steps_timed": kk, "timing": "median of 5 runs",
+            "mlups_gnn_mlp": res["mlp"]["mlups"], "mlups_bgk_same_lattice": res["bgk"]["mlups"],
+            "ms_per_step_gnn_mlp": res["mlp"]["ms_per_step"],
+            "ms_per_step_bgk": res["bgk"]["ms_per_step"],
+            "gnn_over_bgk_time": round(res["mlp"]["ms_per_step"] / res["bgk"]["ms_per_step"], 3),
+            "roofline": {"bound": "hbm", "kernel": "gnn_mlp_step_kernel", "achieved": round(ach, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                         "peak_kind": peak_kind, "algorithmic_bytes_per_node": BYTES_PER_NODE},
+            "status": res["mlp"]["status"]}
 
 
 def train_bench(args, L, dev, stream, variants=(0, 2, 3)):
@@ -852,7 +918,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["bgk", "gnn", "train", "batch"], default=None,
+    ap.add_argument("--only", choices=["bgk", "gnn", "train", "batch", "mlp"], default=None,
                     help="time one kernel family only (profiling runs)")
     ap.add_argument("--side", type=int, default=N_SIDE, help="lattice side for --only runs")
     ap.add_argument("--log", default=None,
@@ -869,6 +935,8 @@ def main():
         args.side = GNN_SIDE
     if args.only == "train" and args.side == N_SIDE:
         args.side = 256
+    if args.only == "mlp" and args.side == N_SIDE:
+        args.side = MLP_SIDE
     if args.impl == "reference":
         out = run_reference(args, rank)
     else:

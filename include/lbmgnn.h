@@ -200,8 +200,13 @@ LBM_API int lbm_moments(const float* f, lbm_shape s, float* rho, float* ux, floa
  * weights are unused and get zero gradients); LBM_GNN_CONSERVATIVE (2)
  * projects Delta f orthogonal to 1, e_x, e_y, so that Eq. 3 conserves mass
  * and momentum exactly like Eq. 1 (this library's option; the paper adds
- * Delta f unconstrained). */
-enum { LBM_GNN_MLP_ONLY = 1, LBM_GNN_CONSERVATIVE = 2 };
+ * Delta f unconstrained); LBM_GNN_FIXED_TAU (4) leaves the relaxation-time
+ * head unused: tau_adj = 1 in Eq. 3 (the BGK relaxation time), the network
+ * acts through Delta f alone and the head's first row gets zero gradients
+ * (this library's option for training: a learned tau_adj multiplies the
+ * relaxation of every non-equilibrium moment, i.e. it changes the
+ * viscosity). */
+enum { LBM_GNN_MLP_ONLY = 1, LBM_GNN_CONSERVATIVE = 2, LBM_GNN_FIXED_TAU = 4 };
 LBM_API size_t gnn_param_count(void);
 LBM_API size_t gnn_trainable_count(void);
 
@@ -213,7 +218,7 @@ LBM_API size_t gnn_trainable_count(void);
  * vector on any machine); the input normaliser mu / sigma at the rest-state
  * populations (4/9, 1/9 x4, 1/36 x4) with a 10 % scale, rho 1 with scale
  * 0.01, u 0 with scale 0.01; the Delta f scale s_df (> 0, finite); and the
- * variant flags (0..3, see above).  Host-only: no GPU is needed.  Returns
+ * variant flags (0..7, see above).  Host-only: no GPU is needed.  Returns
  * LBM_ERR_ARG for a NULL vector, a bad s_df or unknown flags. */
 LBM_API int gnn_params_init_xavier(float* params_host, uint64_t seed, float s_df, int variant);
 
@@ -225,7 +230,7 @@ LBM_API size_t gnn_packed_bytes(void);
  * 16-byte aligned).  Re-run after every change of the parameters.
  * The image carries a validity word (layout version 1), written only when
  * the vector's fixed values are usable: every mu finite, every sigma and
- * s_df finite and > 0, variant one of 0..3; otherwise the pack raises
+ * s_df finite and > 0, variant one of 0..7; otherwise the pack raises
  * LBM_ERR_BLOB in the status word.  Every kernel that reads an image checks
  * the word first; given one without it (never packed, packed from invalid
  * fixed values, or another buffer) it computes and writes nothing (a loss
@@ -248,6 +253,19 @@ LBM_API size_t gnn_step_workspace_bytes(lbm_shape s);
 LBM_API int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape s, float tau,
                          const float* taus, const void* packed, double* totals,
                          void* workspace, size_t ws_bytes, void* stream);
+
+/* One GNN-LBM step of the paper's Fig. 2 network (SimpleLBMGNN: the
+ * MLP-only variant, LBM_GNN_MLP_ONLY set in the image) as a single fused
+ * kernel: pull-stream, moments, features, Linear + ReLU twice and the heads
+ * on the tensor cores, Eq. 3, store; 72 bytes of memory traffic per node and
+ * no workspace.  lbm_step_gnn takes the same kernel for such an image (after
+ * reading the variant on the device), at the cost of three more launches
+ * that return at once.  Arguments and results as lbm_step_gnn.  An image of
+ * a message-passing network is refused on the device: nothing is written
+ * and LBM_ERR_BLOB is raised in the status word. */
+LBM_API int lbm_step_gnn_mlp(const float* f_in, float* f_out, lbm_shape s, float tau,
+                             const float* taus, const void* packed, double* totals,
+                             void* stream);
 
 /* Bytes of the activations gnn_forward saves for gnn_backward
  * (1,152 bytes per node), in this order: BF16 h0, h1, h2 [N][64] (node

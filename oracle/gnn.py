@@ -35,6 +35,9 @@ Variants (the last fixed value, a small integer of flags):
     that carry no mass and no momentum (Euclidean projection orthogonal to
     1, e_x, e_y; for D2Q9 these are orthogonal with norms 9, 6, 6), so that
     Eq. 3 conserves mass and momentum like Eq. 1.
+  * 4, fixed relaxation time: tau_adj = 1 in Eq. 3 whatever y_0 is (the
+    head's first output is unused; dL/dy_0 = 0), so the network corrects
+    through Delta f alone and Eq. 3 keeps the BGK relaxation time.
 
 Flat parameter vector (float32, 38,922 trainable values, in this order):
   enc1.W[64,12] enc1.b[64] enc2.W[64,64] enc2.b[64]
@@ -61,6 +64,7 @@ N_TRAINABLE = sum(int(np.prod(s)) for _, s in SHAPES)
 N_FIXED = 2 * NFEAT + 2
 MLP_ONLY = 1
 CONSERVATIVE = 2
+FIXED_TAU = 4
 N_TOTAL = N_TRAINABLE + N_FIXED
 
 
@@ -223,12 +227,14 @@ def conserve(df):
 
 
 def heads(y, p):
-    """Sec. 2.3.1: tau_adj = 0.5 + sigmoid(y_0) in (0.5, 1.5);
-    Delta f_i = s_df * y_{1+i} (projected with the conservative variant).
-    Returns tau_adj (N,), df (9, N)."""
+    """Sec. 2.3.1: tau_adj = 0.5 + sigmoid(y_0) in (0.5, 1.5) (1 with the
+    fixed-tau variant); Delta f_i = s_df * y_{1+i} (projected with the
+    conservative variant).  Returns tau_adj (N,), df (9, N)."""
     df = p["s_df"] * y[:, 1:].T
     if p["variant"] & CONSERVATIVE:
         df = conserve(df)
+    if p["variant"] & FIXED_TAU:
+        return np.ones(y.shape[0]), df
     return 0.5 + sigmoid(y[:, 0]), df
 
 
@@ -330,5 +336,5 @@ def collide_loss(f_pre, y, tau, target, p):
     dy[:, 1:] = (p["s_df"] * (conserve(dfs) if p["variant"] & CONSERVATIVE else dfs)).T
     dtau_adj = np.sum(dfs * (f - feq), axis=0) * tau / (teff * teff)
     s = sigmoid(y[:, 0])
-    dy[:, 0] = dtau_adj * s * (1.0 - s)
+    dy[:, 0] = 0.0 if p["variant"] & FIXED_TAU else dtau_adj * s * (1.0 - s)
     return loss, dy, f_pred

@@ -43,7 +43,7 @@ extern "C" {
 size_t gnn_param_count(void) { return P::TOTAL; }
 
 int gnn_params_init_xavier(float* params, uint64_t seed, float s_df, int variant) {
-  if (!params || !std::isfinite(s_df) || !(s_df > 0.0f) || variant < 0 || variant > 3)
+  if (!params || !std::isfinite(s_df) || !(s_df > 0.0f) || variant < 0 || variant > VAR_ALL)
     return LBM_ERR_ARG;
   uint64_t state = seed;
   auto uniform = [&state]() {  // SplitMix64 (Steele, Lea and Flood 2014), top 24 bits
@@ -132,6 +132,11 @@ int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape shape, float tau, co
   __half* b0 = reinterpret_cast<__half*>(h0 + N * 64);
   __nv_bfloat16* h1 = reinterpret_cast<__nv_bfloat16*>(b0 + N * 64);
   __half* b1 = reinterpret_cast<__half*>(h1 + N * 64);
+  // The paper's Fig. 2 network (MLP-only variant, read from the image on the
+  // device) is stepped by one fused kernel; for it the three kernels below
+  // return at once, for every other network the fused kernel does.
+  if (launch_gnn_mlp_step(f_in, f_out, s, tau, taus, pk, false, st) != cudaSuccess)
+    return LBM_ERR_CUDA;
   if (launch_gnn_encode(f_in, true, true, s, pk, h0, b0, st) != cudaSuccess) return LBM_ERR_CUDA;
   RoundLaunch r0;
   r0.h_in = h0;
@@ -153,6 +158,27 @@ int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape shape, float tau, co
   r1.taus = taus;
   r1.round = 1;
   if (launch_gnn_round(1, r1, s, pk, st) != cudaSuccess) return LBM_ERR_CUDA;
+  if (totals) {
+    if (cudaMemsetAsync(totals, 0, 5 * sizeof(double), st) != cudaSuccess) return LBM_ERR_CUDA;
+    if (launch_moments(f_out, s, nullptr, nullptr, nullptr, totals, st) != cudaSuccess)
+      return LBM_ERR_CUDA;
+  }
+  return LBM_OK;
+}
+
+int lbm_step_gnn_mlp(const float* f_in, float* f_out, lbm_shape shape, float tau,
+                     const float* taus, const void* packed, double* totals, void* stream) {
+  LBM_TRACE("lbm_step_gnn_mlp");
+  Shape s;
+  if (!f_in || !f_out || !packed) return LBM_ERR_ARG;
+  if (int r = check_shape_g(shape, &s)) return r;
+  if (!taus && (!std::isfinite(tau) || !(tau > 0.5f))) return LBM_ERR_TAU;
+  if (!aligned(packed, 16)) return LBM_ERR_ARG;
+  if (overlap(f_in, f_bytes(s), f_out, f_bytes(s))) return LBM_ERR_ALIAS;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (launch_gnn_mlp_step(f_in, f_out, s, tau, taus, static_cast<const uint8_t*>(packed), true,
+                          st) != cudaSuccess)
+    return LBM_ERR_CUDA;
   if (totals) {
     if (cudaMemsetAsync(totals, 0, 5 * sizeof(double), st) != cudaSuccess) return LBM_ERR_CUDA;
     if (launch_moments(f_out, s, nullptr, nullptr, nullptr, totals, st) != cudaSuccess)

@@ -136,10 +136,16 @@ __device__ __forceinline__ float gelu_grad(float z) {
 __device__ __forceinline__ float sigmoid_acc(float y) { return 0.5f * (1.0f + tanhf(0.5f * y)); }
 
 // Network variants (flags in the last fixed parameter): MLP-only network of
-// the paper's Fig. 2 (ReLU encoder, no message passing), and the correction
-// Delta f projected to carry no mass and no momentum.
-enum : int { VAR_MLP_ONLY = 1, VAR_CONSERVATIVE = 2 };
+// the paper's Fig. 2 (ReLU encoder, no message passing), the correction
+// Delta f projected to carry no mass and no momentum, and a network whose
+// relaxation-time head is not used (tau_adj = 1: Eq. 3 keeps the BGK
+// relaxation time and the network acts through Delta f alone).
+enum : int { VAR_MLP_ONLY = 1, VAR_CONSERVATIVE = 2, VAR_FIXED_TAU = 4, VAR_ALL = 7 };
 __device__ __forceinline__ int variant_of(const float* nrm) { return __float2int_rn(nrm[25]); }
+// tau_adj of Eq. 3: 1/2 + sigmoid(y_0), or 1 for the fixed-tau variant.
+__device__ __forceinline__ float tau_adj_of(float y0, int variant) {
+  return (variant & VAR_FIXED_TAU) ? 1.0f : 0.5f + sigmoid_acc(y0);
+}
 __device__ __forceinline__ float act(float z, bool relu) { return relu ? fmaxf(z, 0.0f) : gelu(z); }
 // gelu_grad() of two values with packed FP32 pair arithmetic.
 __device__ __forceinline__ float2 gelu_grad2(float2 z) {
@@ -503,6 +509,10 @@ struct GeoStack {
   __device__ __forceinline__ float tau(const GeoPos& p, float tau0, const float* taus) const {
     return taus ? __ldg(taus + p.b) : tau0;
   }
+  // address of the node's relaxation time, or NULL for the scalar tau0
+  __device__ __forceinline__ const float* tau_ptr(const GeoPos& p, const float* taus) const {
+    return taus ? taus + p.b : nullptr;
+  }
 };
 
 // One lattice of a batched run: first node in the packed buffers, size and
@@ -553,6 +563,9 @@ struct GeoTable {
   }
   __device__ __forceinline__ float tau(const GeoPos& p, float, const float*) const {
     return __ldg(&lat[p.b].tau);
+  }
+  __device__ __forceinline__ const float* tau_ptr(const GeoPos& p, const float*) const {
+    return &lat[p.b].tau;
   }
 };
 

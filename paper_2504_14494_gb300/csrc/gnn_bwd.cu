@@ -133,8 +133,9 @@ __global__ void __launch_bounds__(256) gnn_collide_loss_kernel(
   const float t = taus ? __ldg(taus + b) : tau;
   const Moments m = moments9(fv);
   const float usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy);
+  const bool fixed_tau = variant & VAR_FIXED_TAU;
   const float sg = sigmoid_acc(yv[0]);
-  const float teff = t * (0.5f + sg);
+  const float teff = t * tau_adj_of(yv[0], variant);
   const float inv = 1.0f / teff;
   const float scale = 2.0f / (9.0f * (float)N);
   double lp = 0.0;
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(256) gnn_collide_loss_kernel(
   if (variant & VAR_CONSERVATIVE) conserve9(g);
 #pragma unroll
   for (int q = 0; q < Q; ++q) dyv[1 + q] = sdf * g[q];
-  dyv[0] = dta * t * inv * inv * sg * (1.0f - sg);
+  dyv[0] = fixed_tau ? 0.0f : dta * t * inv * inv * sg * (1.0f - sg);
   if (on && dy) {
 #pragma unroll
     for (int o = 0; o < NOUT; ++o) dy[o * N + n] = dyv[o];

@@ -42,12 +42,12 @@ __global__ void gnn_pack_kernel(const float* __restrict__ p, uint8_t* __restrict
   }
   for (int e = tid; e < 31; e += nth)
     reinterpret_cast<float*>(out + K::NORM)[e] = e < 26 ? p[P::MU + e] : 0.0f;
-  if (tid == 0) {  // the fixed values: finite mu, sigma > 0, s_df > 0, variant 0..3
+  if (tid == 0) {  // the fixed values: finite mu, sigma > 0, s_df > 0, variant 0..7
     bool ok = p[P::S_DF] > 0.0f && isfinite(p[P::S_DF]);
     for (int i = 0; i < NFEAT; ++i)
       ok = ok && isfinite(p[P::MU + i]) && p[P::SIGMA + i] > 0.0f && isfinite(p[P::SIGMA + i]);
     const float v = p[P::VARIANT];
-    ok = ok && (v == 0.0f || v == 1.0f || v == 2.0f || v == 3.0f);
+    ok = ok && v >= 0.0f && v <= (float)VAR_ALL && v == floorf(v);
     *reinterpret_cast<unsigned*>(out + K::MAGIC_SLOT) = ok ? K::MAGIC : 0u;
     if (!ok) atomicOr(stw, (unsigned)ST_BLOB);
   }
@@ -128,6 +128,9 @@ __global__ void __launch_bounds__(256, (enc_ctas<PULL, BONLY, Geo>())) gnn_encod
     const float* __restrict__ f, Geo geo, const uint8_t* __restrict__ packed,
     __nv_bfloat16* __restrict__ h0_out, __half* __restrict__ ab_out, unsigned* stw) {
   if (!blob_ok(packed, stw)) return;
+  if (PULL && BONLY &&
+      (variant_of(reinterpret_cast<const float*>(packed + K::NORM)) & VAR_MLP_ONLY))
+    return;  // inference step of the MLP-only network: the fused kernel (gnn_mlp.cu) did it
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   TcShared* sh = reinterpret_cast<TcShared*>(sm + enc::SH);
@@ -297,9 +300,9 @@ template <int MODE, int TPN, int NG, bool AH, class Geo>
 __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kernel(
     RoundArgs ra, Geo geo, const uint8_t* __restrict__ packed, unsigned* stw) {
   if (!blob_ok(packed, stw)) return;
-  if (MODE == 0 && ra.h_skip &&
+  if ((MODE == 0 || MODE == 1) && ra.h_skip &&
       (variant_of(reinterpret_cast<const float*>(packed + K::NORM)) & VAR_MLP_ONLY))
-    return;  // MLP-only network: nothing to pass between rounds
+    return;  // MLP-only network: no rounds; its inference step is the fused kernel (gnn_mlp.cu)
   constexpr int FPT = HID / TPN;
   constexpr int SL = FPT < 32 ? FPT : 32;  // feature slice of the epilogues
   constexpr int GT = 128 * TPN;            // threads per group
@@ -518,7 +521,7 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
           const Moments mm = moments9(fv);
           const float usq15 = 1.5f * (mm.ux * mm.ux + mm.uy * mm.uy);
           const float tau = geo.tau(p, ra.tau, ra.taus);
-          const float tadj = 0.5f + sigmoid_acc(y[0]);
+          const float tadj = tau_adj_of(y[0], variant);
           const float inv = 1.0f / (tau * tadj);
           const float sdf = nrm[24];
           float d[Q];
@@ -636,6 +639,10 @@ cudaError_t launch_gnn_step_table(const float* f_in, float* f_out, const LatDesc
   __nv_bfloat16* h1 = reinterpret_cast<__nv_bfloat16*>(b0 + count * 64);
   __half* b1 = reinterpret_cast<__half*>(h1 + count * 64);
   cudaError_t e;
+  // MLP-only network: the fused step; the kernels below then return at once
+  if ((e = launch_gnn_mlp_step_table(f_in, f_out, lat, first, n, hint, base, count, ps, packed, st,
+                                     per_sm)) != cudaSuccess)
+    return e;
   if ((e = encode_any(f_in, true, true, geo, count, packed, h0, b0, st, per_sm)) != cudaSuccess)
     return e;
   RoundLaunch r0;

@@ -35,7 +35,18 @@ cudaError_t launch_gnn_encode(const float* f, bool pull, bool b_only, const Shap
 cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
                              const uint8_t* packed, cudaStream_t st);
 
+// The paper's Fig. 2 network (MLP-only variant) as one fused GNN-LBM step
+// kernel (pull, features, 3 MMAs, heads, Eq. 3, store).  For any other
+// network the kernel writes nothing (and with require_mlp raises ST_BLOB).
+cudaError_t launch_gnn_mlp_step(const float* f_in, float* f_out, const Shape& s, float tau,
+                                const float* taus, const uint8_t* packed, bool require_mlp,
+                                cudaStream_t st);
+
 struct LatDesc;
+cudaError_t launch_gnn_mlp_step_table(const float* f_in, float* f_out, const LatDesc* lat,
+                                      int first, int n, const int* hint, int64_t base,
+                                      int64_t count, int64_t ps, const uint8_t* packed,
+                                      cudaStream_t st, int per_sm);
 // GNN-LBM step (encoder, 2 rounds, head + Eq. 3) on the lattices first ..
 // first+n-1 of a device descriptor table, whose nodes are [base, base+count)
 // of population buffers with plane stride ps; hint: device int per 128-node

@@ -13,7 +13,8 @@ and the oracle:
   head.W[10,64] head.b[10]                      -> 38,922 trainable values
   mu[12] sigma[12] s_df variant                 -> 26 fixed values
 variant: 0, or a sum of flags: 1 = MLP-only network of the paper's Fig. 2
-(ReLU encoder, no message passing), 2 = mass/momentum-conserving correction.
+(ReLU encoder, no message passing), 2 = mass/momentum-conserving correction,
+4 = relaxation-time head unused (tau_adj = 1).
 """
 import numpy as np
 
@@ -24,7 +25,7 @@ for _ in range(ROUNDS):
 PARAM_SHAPES += [(NOUT, HID), (NOUT,)]
 N_TRAINABLE = sum(int(np.prod(s)) for s in PARAM_SHAPES)
 N_PARAMS = N_TRAINABLE + 2 * NFEAT + 2
-MLP_ONLY, CONSERVATIVE = 1, 2
+MLP_ONLY, CONSERVATIVE, FIXED_TAU = 1, 2, 4
 
 # Default input normaliser: populations around their rest-state values
 # (4/9, 1/9 x4, 1/36 x4) with a 10% scale, density around 1, velocity with a

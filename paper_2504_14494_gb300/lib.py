@@ -93,6 +93,7 @@ _SIGS = {
                                       _VP, ctypes.c_size_t, _VP]),
     "lbm_step_gnn_noalloc": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP,
                                             _VP]),
+    "lbm_step_gnn_mlp": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP, _VP]),
     "lbm_batch_plan_create": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "lbm_batch_plan_destroy": (None, [_VP]),
     "lbm_batch_nodes": (ctypes.c_int64, [_VP]),
@@ -348,6 +349,18 @@ def lbm_step_gnn(f_in, f_out, s, tau, taus, packed, totals, workspace, ws_bytes=
                               dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
                               dptr(totals, "totals", _f64(), 5), dptr(workspace, "workspace"),
                               int(ws_bytes), stream_ptr(stream)), "lbm_step_gnn")
+
+
+def lbm_step_gnn_mlp(f_in, f_out, s, tau, taus, packed, totals, stream=None):
+    """The paper's Fig. 2 (MLP-only) network's GNN-LBM step as one fused
+    kernel, no workspace (see include/lbmgnn.h)."""
+    _, _, fe = _elems(s)
+    f32 = _f32()
+    check(load().lbm_step_gnn_mlp(dptr(f_in, "f_in", f32, fe), dptr(f_out, "f_out", f32, fe), s,
+                                  float(tau), dptr(taus, "taus", f32, int(s.nb)),
+                                  dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
+                                  dptr(totals, "totals", _f64(), 5), stream_ptr(stream)),
+          "lbm_step_gnn_mlp")
 
 
 def gnn_saved_bytes(s):

@@ -138,3 +138,64 @@ class Evaluator:
         L.gnn_collide_loss(self.f_pre, self.y, f_target, self.s, 1.0, taus, self.packed, self.loss,
                            None, None, self.ws)
         return self.loss.item()
+
+
+class HeldOutRollout:
+    """A held-out Taylor-Green case run three ways through the C ABI: the
+    m-times refined BGK reference (m fine steps per coarse step, restricted
+    to the coarse lattice when asked), and the coarse lattice advanced from
+    the restricted initial state by the BGK step and by the GNN-LBM step
+    (parameters `theta`).  Default: the evaluation case of the training
+    workload, k = 4 (2 pi / 256), u0 = 0.08, Re = 5000 on 256^2 coarse
+    nodes, the refined run started from the pressure-consistent density like
+    the training data."""
+
+    def __init__(self, device, theta, n=256, m=4, u0=0.08, k_mult=4, re=5000.0,
+                 pressure_consistent=True):
+        import torch
+        self.dev, self.n, self.m = device, n, m
+        nu = u0 * n / re
+        self.tau_c = 0.5 + 3.0 * nu
+        self.tau_f = 0.5 + m * (self.tau_c - 0.5)
+        nf = m * n
+        kf = k_mult * 2 * np.pi / nf
+        self.fine, self.coarse = L.shape(nf, nf), L.shape(n, n)
+        self.ff = [torch.empty(9 * nf * nf, device=device) for _ in range(2)]
+        self.fb = [torch.empty(9 * n * n, device=device) for _ in range(2)]
+        self.fg = [torch.empty(9 * n * n, device=device) for _ in range(2)]
+        self.ref = torch.empty(9 * n * n, device=device)
+        L.lbm_init_tgv(self.ff[0], self.fine, 1.0, u0, kf, kf, pressure_consistent)
+        L.lbm_restrict(self.ff[0], self.fine, self.fb[0], self.coarse, m, self.tau_f, None,
+                       self.tau_c, None)
+        self.fg[0].copy_(self.fb[0])
+        self.packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=device)
+        L.gnn_pack(torch.from_numpy(np.asarray(theta, np.float32)).to(device), self.packed)
+        self.ws = torch.empty(L.gnn_step_workspace_bytes(self.coarse), dtype=torch.uint8,
+                              device=device)
+        self.t = 0
+
+    def step(self):
+        """One coarse step of all three runs."""
+        for _ in range(self.m):
+            L.lbm_step_bgk(self.ff[0], self.ff[1], None, self.fine, self.tau_f)
+            self.ff.reverse()
+        L.lbm_step_bgk(self.fb[0], self.fb[1], None, self.coarse, self.tau_c)
+        self.fb.reverse()
+        L.lbm_step_gnn(self.fg[0], self.fg[1], self.coarse, self.tau_c, None, self.packed, None,
+                       self.ws)
+        self.fg.reverse()
+        self.t += 1
+
+    def velocities(self):
+        """(ux, uy) device planes of the restricted reference, the BGK run
+        and the GNN run at the current step."""
+        import torch
+        L.lbm_restrict(self.ff[0], self.fine, self.ref, self.coarse, self.m, self.tau_f, None,
+                       self.tau_c, None)
+        out = []
+        nn = self.n * self.n
+        for f in (self.ref, self.fb[0], self.fg[0]):
+            ux, uy = torch.empty(nn, device=self.dev), torch.empty(nn, device=self.dev)
+            L.lbm_moments(f, self.coarse, None, ux, uy, None)
+            out.append((ux, uy))
+        return out

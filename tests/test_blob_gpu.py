@@ -1,6 +1,6 @@
 """The packed parameter image's validity word (gnn_pack; include/lbmgnn.h):
 an image that was never packed, or was packed from invalid fixed values
-(variant outside 0..3, sigma or s_df not > 0, a non-finite normaliser), is
+(variant outside 0..7, sigma or s_df not > 0, a non-finite normaliser), is
 refused by every kernel that reads it: nothing is written, a loss becomes
 NaN, and lbm_get_status() reports LBM_ERR_BLOB.  A valid pack afterwards
 works as before.  (Error path of the boundary: the paper's method has no
@@ -105,7 +105,7 @@ def test_invalid_fixed_values_are_refused(lbmlib, cuda, what):
     o = inputs.N_TRAINABLE  # mu[12], sigma[12], s_df, variant
     bad = theta.copy()
     if what == "variant":
-        bad[o + 25] = 7.0
+        bad[o + 25] = 8.0
     elif what == "sigma":
         bad[o + 12 + 3] = 0.0
     elif what == "s_df":

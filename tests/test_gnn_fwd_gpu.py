@@ -208,10 +208,10 @@ def test_full_size_1024_sampled(lbmlib, cuda):
     assert rel_l2(yg[:, 1:], yo[:, 1:]) <= 2e-2
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 6])
 def test_variants_forward_and_step(lbmlib, cuda, variant):
     """Variants: 1 = the paper's Fig. 2 MLP (ReLU, no message passing),
-    2 = conservative correction.  Same tolerances as the default network; the
+    2 = conservative correction, 4 = tau_adj fixed at 1.  Same tolerances as the default network; the
     conservative step conserves mass and momentum to FP32 rounding."""
     import torch
     L = lbmlib

@@ -250,7 +250,7 @@ def test_train_step_matches_oracle_and_descends(lbmlib, cuda):
     assert losses[-1] < 0.5 * losses[0]
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 4])
 def test_variant_backward_and_loss_match_oracle(lbmlib, cuda, variant):
     """Gradients of the Eq. 3 + Eq. 4 loss through the network for the
     variants (same tolerances as the default network)."""

@@ -257,7 +257,7 @@ def test_mlp_only_is_a_per_node_relu_mlp():
         assert np.allclose(y[n], p["head.W"] @ h + p["head.b"], rtol=1e-13, atol=1e-13)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 6])
 def test_variant_gradients_match_central_differences(variant):
     nx, ny = 4, 3
     p = gnn.unpack(inputs.xavier_params(36, s_df=1e-2, bias_scale=0.2, variant=variant))
@@ -282,3 +282,29 @@ def test_variant_gradients_match_central_differences(variant):
         fd = (loss(pp, f) - loss(pm, f)) / (2 * h)
         an = float(np.sum(g[name] * d))
         assert abs(fd - an) <= 1e-5 * max(abs(an), 1e-12) + 1e-18, (variant, name, fd, an)
+
+
+def test_fixed_tau_variant_ignores_the_tau_head():
+    """Variant 4: tau_adj = 1 in Eq. 3 whatever the head's first row is, so
+    with Delta f switched off (s_df tiny) the step is the BGK step, two
+    networks differing only in that row give the same step, and the loss
+    gradient of that row is zero."""
+    nx, ny, tau = 5, 4, 0.65
+    th = inputs.xavier_params(41, s_df=1e-2, bias_scale=0.2, variant=4)
+    th2 = th.copy()
+    th2[38272:38336] += 0.5           # head.W row 0
+    th2[38912] -= 3.0                 # head.b[0]
+    f = _state(nx, ny, 42)
+    a, b = gnn.gnn_step(f, th, tau), gnn.gnn_step(f, th2, tau)
+    assert np.array_equal(a, b)
+    th0 = th.copy()
+    th0[38336:38912] = 0.0            # head.W rows 1..9 and head.b[1..9]: Delta f = 0
+    th0[38913:38922] = 0.0
+    assert np.allclose(gnn.gnn_step(f, th0, tau), lbm.bgk_step(f, tau), rtol=1e-14, atol=0)
+    p = gnn.unpack(th)
+    fp = lbm.stream_pull(f)
+    y, cache = gnn.forward(fp, p)
+    _, dy, _ = gnn.collide_loss(fp, y, tau, _state(nx, ny, 43), p)
+    assert not np.any(dy[:, 0])
+    g, _ = gnn.backward(dy, cache, p)
+    assert not np.any(g["head.W"][0]) and g["head.b"][0] == 0.0

@@ -45,7 +45,7 @@ def test_seed_determinism(lbmlib):
 
 def test_bad_arguments(lbmlib):
     L = lbmlib
-    for s_df, variant in ((float("nan"), 0), (0.0, 0), (-1.0, 0), (1e-4, 4), (1e-4, -1)):
+    for s_df, variant in ((float("nan"), 0), (0.0, 0), (-1.0, 0), (1e-4, 8), (1e-4, -1)):
         with pytest.raises(L.LbmError, match="LBM_ERR_ARG"):
             _init(L, 1, s_df, variant)
     with pytest.raises(L.LbmError, match="LBM_ERR_ARG"):  # NULL vector
