@@ -6,36 +6,44 @@
 // loads, 9 FP32 stores: 72 bytes), like the BGK step.
 //
 // Work unit: a tile of 128 consecutive nodes; a CTA of 128 threads (thread t
-// = node t of the tile, warp w reads tensor-memory lanes 32w..32w+31) loops
-// over tiles (persistent grid, several CTAs per SM).  The pulled populations
-// of the next two tiles are fetched with 4-byte cp.async copies into a
-// 3-stage shared-memory ring, so the loads are in flight while the current
-// tile runs its three MMAs (M = 128 nodes, BF16 operands in 128-byte
-// swizzled shared memory, FP32 accumulators in 64 tensor-memory columns):
+// = node t of the tile, warp w owns tensor-memory lanes 32w..32w+31) loops
+// over tiles (persistent grid, 4 CTAs per SM).  The pulled populations of
+// the next two tiles are fetched with 4-byte cp.async copies into a 3-stage
+// shared-memory ring while the current tile runs its three MMAs (M = 128
+// nodes, FP32 accumulators in tensor memory):
 //   D = [x_hi | x_lo] W1x^T   (K = 32: the FP32 features split into two BF16
-//                              parts, ~16 bits kept)          -> ReLU(+b1)
+//                              parts, ~16 bits kept; b1 rides along as two
+//                              extra K columns against feature columns of 1)
 //   D = g1 W2^T               (K = 64)                        -> ReLU(+b2)
 //   D = h0 Wh^T               (K = 64, N = 16, 10 used)       -> y (+bh)
-// and f* = f - (f - f^eq)/(tau tau_adj) + s_df y_1..9 (Eq. 3).  The one
-// activation tile is reused by the three products (each epilogue writes it
-// after the MMA that read it has completed).
+// and f* = f - (f - f^eq)/(tau tau_adj) + s_df y_1..9 (Eq. 3).  The
+// activations never touch shared memory: each epilogue reads the node's
+// accumulator row from tensor memory, applies bias and ReLU, rounds to BF16
+// and stores the row back into tensor memory, where the next MMA reads its
+// A operand (weights B from shared memory).  Shared memory then carries
+// only the weights and the staged populations, and the tensor core reads
+// 14 KB of it per tile instead of 54 KB.
 #include "gnn.cuh"
 #include "gnn_launch.h"
 
 namespace lbmgnn {
 
+#ifndef LBM_MLP_CTAS
+#define LBM_MLP_CTAS 4  // resident CTAs per SM (128 tensor-memory columns each)
+#endif
+
 namespace mlp {
+// Shared memory holds only the weights and the staged populations: the
+// activations live in tensor memory (columns 0..63: accumulator, 64..95:
+// the BF16 input of the next product).
 constexpr int STAGES = 3;
 constexpr int SLOTS = Q + 1;  // per node and stage: the 9 pulled populations and tau
-constexpr uint32_t W1X = 0, W2 = 8192, ACT = 16384, WH = 32768, STG = 34816,
+constexpr uint32_t W1X = 0, W2 = 8192, WH = 16384, STG = 18432,
                    STG_BYTES = SLOTS * TILE * 4,                   // 5120 per stage
-                   B2 = STG + STAGES * STG_BYTES,                  // 50176
+                   B2 = STG + STAGES * STG_BYTES,                  // 33792
                    BH = B2 + 256, NORM = BH + 64, SH = NORM + 128, BYTES = SH + 64;
+constexpr uint32_t TM_D = 0, TM_A = 64, TM_COLS = 128;
 }  // namespace mlp
-
-#ifndef LBM_MLP_CTAS
-#define LBM_MLP_CTAS 4  // resident CTAs per SM
-#endif
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
@@ -60,25 +68,46 @@ __device__ __forceinline__ uint32_t bf16x2(float a, float b) {
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
   return r;
 }
-
-// ReLU of 32 accumulator columns (plus a bias, if given) rounded to BF16 and
-// stored into chunks c0 .. c0+3 of the swizzled activation row.
-__device__ __forceinline__ void relu_row32(uint8_t* act, int row, int c0, const float (&z)[32],
-                                           const float* b) {
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    uint32_t w[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      float2 v = make_float2(z[8 * c + 2 * j], z[8 * c + 2 * j + 1]);
-      if (b) v = __fadd2_rn(v, *reinterpret_cast<const float2*>(b + 8 * c + 2 * j));
-      w[j] = relu_bf16x2(v.x, v.y);
-    }
-    *reinterpret_cast<uint4*>(act + row * 128 + (((c0 + c) ^ (row & 7)) << 4)) =
-        make_uint4(w[0], w[1], w[2], w[3]);
-  }
+// Moments with a fast reciprocal of rho (the MUFU approximation, ~1 ulp).
+__device__ __forceinline__ Moments moments9_fast(const float (&f)[Q]) {
+  const float rho = ((f[0] + (f[1] + f[3])) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8]));
+  const float jx = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
+  const float jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+  const float inv = __fdividef(1.0f, rho);
+  return {rho, jx * inv, jy * inv};
 }
 
+// One layer's epilogue: ReLU(D + b) of the node's 64 accumulator columns,
+// rounded to BF16, written back to tensor memory as the next product's A
+// (32 columns of BF16 pairs).  b: NULL (bias already in D) or 64 floats in
+// shared memory.
+__device__ __forceinline__ void relu_to_tmem(uint32_t lane_d, uint32_t lane_a, const float* b) {
+  uint32_t w[32];
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    float z[32];
+    tmem_ld32(lane_d + 32u * half, z);
+#pragma unroll
+    for (int c = 0; c < 32; c += 8) {
+      float bb[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (b) {
+        const float4 b0 = *reinterpret_cast<const float4*>(b + 32 * half + c);
+        const float4 b1 = *reinterpret_cast<const float4*>(b + 32 * half + c + 4);
+        bb[0] = b0.x, bb[1] = b0.y, bb[2] = b0.z, bb[3] = b0.w;
+        bb[4] = b1.x, bb[5] = b1.y, bb[6] = b1.z, bb[7] = b1.w;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        float2 v = make_float2(z[c + j], z[c + j + 1]);
+        if (b) v = __fadd2_rn(v, make_float2(bb[j], bb[j + 1]));
+        w[16 * half + (c + j) / 2] = relu_bf16x2(v.x, v.y);
+      }
+    }
+  }
+  tmem_st32(lane_a, w);
+}
+
+// One fused GNN-LBM step of the MLP-only network over the nodes of `geo`.
 template <class Geo>
 __global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
     const float* __restrict__ f_in, float* __restrict__ f_out, Geo geo, float tau0,
@@ -145,99 +174,104 @@ __global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
         __float2bfloat16_rn(b - hi);
   }
   TcCtx tc;
-  tc_setup(sh, tc, 64);  // (its barrier also publishes the writes above)
+  tc_setup(sh, tc, mlp::TM_COLS);  // (its barrier also publishes the writes above)
   const float* b2 = reinterpret_cast<const float*>(sm + mlp::B2);
   const float* bh = reinterpret_cast<const float*>(sm + mlp::BH);
   const float* nrm = nrmw;
-  uint8_t* act = sm + mlp::ACT;
   const uint32_t lb = lane_base(tc.tmem);
+  const uint32_t ld = lb + mlp::TM_D, la = lb + mlp::TM_A;
+  const uint32_t td = tc.tmem + mlp::TM_D, ta = tc.tmem + mlp::TM_A;
+  const uint32_t w1x = smem_u32(sm + mlp::W1X), w2 = smem_u32(sm + mlp::W2),
+                 wh = smem_u32(sm + mlp::WH);
   const float sdf = nrm[24];
-  const uint32_t ones = bf16x2(1.0f, 1.0f);
+
+  // The A operand was stored to tensor memory by every thread -> barrier ->
+  // one thread issues the MMA chain and commits it; all threads wait.
+  auto run = [&](auto issue) -> bool {
+    tmem_st_wait();
+    tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      issue();
+      umma_commit(tc.bar);
+    }
+    const bool ok = mbar_wait(tc.bar, tc.phase);
+    tc.phase ^= 1u;
+    tc_fence_after();
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) raise_status(stw, ST_TIMEOUT);
+      return false;
+    }
+    return true;
+  };
 
   int s = 0;
   for (int64_t tile = first; tile < ntiles; tile += stride) {
     fetch(tile + 2 * stride, s == 0 ? 2 : s - 1);  // the stage read two tiles ago
     cp_async_wait<2>();                             // this thread's copies of `tile`
     const int64_t n = tile * TILE + t;
-    const bool on = n < N;
-    float fv[Q];
-    const float* sv = stg + s * (mlp::SLOTS * TILE) + t;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) fv[q] = sv[q * TILE];
-    const float tau = sv[Q * TILE];
+    const float* sv = stg + s * (mlp::SLOTS * TILE) + t;  // read again by the collision
     s = s == 2 ? 0 : s + 1;
-    const Moments m = moments9(fv);
-    {  // features normalised, as [x_hi (k 0..11), 1, 1, 0, 0 | x_lo (k 16..27), 0 x 4]
+    {  // features normalised: A = [x_hi (k 0..11), 1, 1, 0, 0 | x_lo (k 16..27), 0 x 4]
+      float fv[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) fv[q] = sv[q * TILE];
+      const Moments m = moments9_fast(fv);
       float xh[NFEAT];
 #pragma unroll
       for (int q = 0; q < Q; ++q) xh[q] = (fv[q] - nrm[q]) * nrm[NFEAT + q];
       xh[9] = (m.rho - nrm[9]) * nrm[NFEAT + 9];
       xh[10] = (m.ux - nrm[10]) * nrm[NFEAT + 10];
       xh[11] = (m.uy - nrm[11]) * nrm[NFEAT + 11];
-      uint32_t hw[8], lw[8];
+      uint32_t w[16];
 #pragma unroll
       for (int j = 0; j < NFEAT / 2; ++j) {
-        hw[j] = bf16x2(xh[2 * j], xh[2 * j + 1]);
+        const uint32_t hw = bf16x2(xh[2 * j], xh[2 * j + 1]);
         const float2 lo = __fadd2_rn(make_float2(xh[2 * j], xh[2 * j + 1]),
-                                     make_float2(-__uint_as_float(hw[j] << 16),
-                                                 -__uint_as_float(hw[j] & 0xFFFF0000u)));
-        lw[j] = bf16x2(lo.x, lo.y);
+                                     make_float2(-__uint_as_float(hw << 16),
+                                                 -__uint_as_float(hw & 0xFFFF0000u)));
+        w[j] = hw;
+        w[8 + j] = bf16x2(lo.x, lo.y);
       }
-      hw[6] = ones;
-      hw[7] = lw[6] = lw[7] = 0u;
-      uint8_t* row = act + t * 128;
-      const int sw = t & 7;
-      *reinterpret_cast<uint4*>(row + ((0 ^ sw) << 4)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-      *reinterpret_cast<uint4*>(row + ((1 ^ sw) << 4)) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
-      *reinterpret_cast<uint4*>(row + ((2 ^ sw) << 4)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-      *reinterpret_cast<uint4*>(row + ((3 ^ sw) << 4)) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+      w[6] = 0x3F803F80u;  // BF16 pair (1, 1): the bias columns
+      w[7] = w[14] = w[15] = 0u;
+      tmem_st16(la, w);
     }
-    if (!tc_run(sh, tc, stw, [&] {
-          umma_128xN(tc.tmem, smem_u32(act), 0, smem_u32(sm + mlp::W1X), 0, 1, 64, false, 2);
-        }))
-      break;
-    {  // g1 = ReLU(W1 x + b1) (the bias came with the MMA)
-      float z[32];
-      tmem_ld32(lb, z);
-      relu_row32(act, t, 0, z, nullptr);
-      tmem_ld32(lb + 32, z);
-      relu_row32(act, t, 4, z, nullptr);
-    }
-    if (!tc_run(sh, tc, stw, [&] {
-          umma_128xN(tc.tmem, smem_u32(act), 0, smem_u32(sm + mlp::W2), 0, 1, 64, false);
-        }))
-      break;
-    {  // h0 = ReLU(W2 g1 + b2)
-      float z[32];
-      tmem_ld32(lb, z);
-      relu_row32(act, t, 0, z, b2);
-      tmem_ld32(lb + 32, z);
-      relu_row32(act, t, 4, z, b2 + 32);
-    }
-    if (!tc_run(sh, tc, stw, [&] {
-          umma_128xN(tc.tmem, smem_u32(act), 0, smem_u32(sm + mlp::WH), 0, 1, 16, false);
-        }))
-      break;
+    if (!run([&] { umma_128xN_ts(td, ta, w1x, 64, 2); })) break;
+    relu_to_tmem(ld, la, nullptr);  // g1 = ReLU(W1 x + b1) (bias in D)
+    if (!run([&] { umma_128xN_ts(td, ta, w2, 64, 4); })) break;
+    relu_to_tmem(ld, la, b2);       // h0 = ReLU(W2 g1 + b2)
+    if (!run([&] { umma_128xN_ts(td, ta, wh, 16, 4); })) break;
     {  // heads and Eq. 3
       float y[16];
-      tmem_ld16(lb, y);
-      const float inv = 1.0f / (tau * tau_adj_of(y[0] + bh[0], variant));
+      tmem_ld16(ld, y);
+      float fv[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) fv[q] = sv[q * TILE];
+      const float tau = sv[Q * TILE];
+      const Moments m = moments9_fast(fv);
+      // tau_adj = 1/2 + sigmoid(y_0) = 1 + tanh(y_0 / 2) / 2 (or 1)
+      const float tadj = (variant & VAR_FIXED_TAU)
+                             ? 1.0f
+                             : fmaf(0.5f, tanh_fast(0.5f * (y[0] + bh[0])), 1.0f);
+      const float inv = __fdividef(1.0f, tau * tadj);
       float d[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) d[q] = sdf * (y[1 + q] + bh[1 + q]);
       if (variant & VAR_CONSERVATIVE) conserve9(d);
       const float usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy);
-      if (on) {
+      if (n < N) {
 #pragma unroll
         for (int q = 0; q < Q; ++q)
-          f_out[q * ps + base + n] = fv[q] - (fv[q] - feq_i(q, m, usq15)) * inv + d[q];
+          f_out[q * ps + base + n] = fmaf(feq_i(q, m, usq15) - fv[q], inv, fv[q]) + d[q];
       }
     }
     tc_fence_before();
     __syncthreads();  // the head's accumulator is read before the next tile's MMA
   }
   cp_async_wait<0>();
-  tc_teardown(sh, tc, 64);
+  tc_teardown(sh, tc, mlp::TM_COLS);
 }
 
 template <class Geo>

@@ -109,6 +109,18 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint6
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// D[tmem] (+)= A * B^T with the A slice (M = 128 rows x 16 K, BF16) read from
+// tensor memory: lane r holds row r, K packed two per 32-bit column (element
+// 2c in the low half of column c), 8 columns per K step starting at tmem_a.
+__device__ __forceinline__ void umma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc,
+                                             uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // Arrive on `bar` when all previously issued MMAs of this thread completed.
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile(
@@ -132,6 +144,44 @@ __device__ __forceinline__ void umma_128xN(uint32_t tmem_d, uint32_t a_addr, uin
       umma_bf16(tmem_d, ad, bd, id, (accumulate || kb > 0 || ks > 0) ? 1u : 0u);
     }
   }
+}
+
+// D (M = 128) = A * B^T over `nks` K steps of 16, A from tensor memory at
+// tmem_a (8 columns per step), B from one SW128 block of N rows at b_addr.
+__device__ __forceinline__ void umma_128xN_ts(uint32_t tmem_d, uint32_t tmem_a, uint32_t b_addr,
+                                              int N, int nks) {
+  const uint32_t id = idesc_bf16(128, N);
+  for (int ks = 0; ks < nks; ++ks)
+    umma_bf16_ts(tmem_d, tmem_a + 8u * ks, sw128_desc(b_addr + ks * 32), id, ks > 0 ? 1u : 0u);
+}
+
+// ---- tensor memory stores ---------------------------------------------------------
+// 16 / 32 consecutive 32-bit columns of the calling thread's lane; the
+// stores are complete for later tensor-core reads after tmem_st_wait()
+// and a thread barrier with the tcgen05 fences.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&w)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]),
+      "r"(w[8]), "r"(w[9]), "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]),
+      "r"(w[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&w)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]),
+      "r"(w[8]), "r"(w[9]), "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]),
+      "r"(w[15]), "r"(w[16]), "r"(w[17]), "r"(w[18]), "r"(w[19]), "r"(w[20]), "r"(w[21]),
+      "r"(w[22]), "r"(w[23]), "r"(w[24]), "r"(w[25]), "r"(w[26]), "r"(w[27]), "r"(w[28]),
+      "r"(w[29]), "r"(w[30]), "r"(w[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // ---- tensor memory loads ---------------------------------------------------------
