@@ -38,11 +38,14 @@ namespace mlp {
 // the BF16 input of the next product).
 constexpr int STAGES = 3;
 constexpr int SLOTS = Q + 1;  // per node and stage: the 9 pulled populations and tau
-constexpr uint32_t W1X = 0, W2 = 8192, WH = 16384, STG = 18432,
+// B2X / BHX: SW128 blocks whose K columns 0 and 1 hold the layer-2 and head
+// biases as BF16 pairs hi + lo (~16 bits): one extra K step against a
+// constant A of ones adds the bias inside the MMA.
+constexpr uint32_t W1X = 0, W2 = 8192, WH = 16384, B2X = 18432, BHX = 26624, STG = 28672,
                    STG_BYTES = SLOTS * TILE * 4,                   // 5120 per stage
-                   B2 = STG + STAGES * STG_BYTES,                  // 33792
-                   BH = B2 + 256, NORM = BH + 64, SH = NORM + 128, BYTES = SH + 64;
-constexpr uint32_t TM_D = 0, TM_A = 64, TM_COLS = 128;
+                   NORM = STG + STAGES * STG_BYTES,                // 44032
+                   SH = NORM + 128, BYTES = SH + 64;
+constexpr uint32_t TM_D = 0, TM_A = 64, TM_ONES = 96, TM_COLS = 128;
 }  // namespace mlp
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
@@ -158,31 +161,48 @@ __global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
   copy_g2s(sm + mlp::W1X, packed + K::W1X, 8192);
   copy_g2s(sm + mlp::W2, packed + K::W2, 8192);
   copy_g2s(sm + mlp::WH, packed + K::WH, 2048);
-  copy_g2s(sm + mlp::B2, packed + K::B2, 256);
-  copy_g2s(sm + mlp::BH, packed + K::BH, 64);
   copy_g2s(sm + mlp::NORM, packed + K::NORM, 128);
+  for (uint32_t i = t; i < (mlp::STG - mlp::B2X) / 16; i += blockDim.x)  // bias blocks: zeros
+    reinterpret_cast<uint4*>(sm + mlp::B2X)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   float* nrmw = reinterpret_cast<float*>(sm + mlp::NORM);
   if (t < NFEAT) nrmw[NFEAT + t] = 1.0f / nrmw[NFEAT + t];  // sigma -> 1/sigma
-  if (t < HID) {
-    // layer-1 bias folded into the MMA: K columns 12 and 13 of W1x hold b1 as
-    // a BF16 pair hi + lo (~16 bits), multiplied by feature columns equal to 1
-    const float b = __ldg(reinterpret_cast<const float*>(packed + K::B1) + t);
+  // The biases ride along in the MMAs as BF16 pairs hi + lo (~16 bits):
+  // b1 in K columns 12 and 13 of W1x (multiplied by feature columns equal to
+  // 1), b2 and the head bias in K columns 0 and 1 of their own blocks
+  // (multiplied by a constant A of ones in tensor memory).
+  auto put_pair = [&](uint32_t blk, int row, int k, float b) {
     const float hi = bf16_round(b);
-    *reinterpret_cast<__nv_bfloat16*>(sm + mlp::W1X + sw128_off(t, 12)) = __float2bfloat16_rn(hi);
-    *reinterpret_cast<__nv_bfloat16*>(sm + mlp::W1X + sw128_off(t, 13)) =
+    *reinterpret_cast<__nv_bfloat16*>(sm + blk + sw128_off(row, k)) = __float2bfloat16_rn(hi);
+    *reinterpret_cast<__nv_bfloat16*>(sm + blk + sw128_off(row, k + 1)) =
         __float2bfloat16_rn(b - hi);
+  };
+  if (t < HID) {
+    put_pair(mlp::W1X, t, 12, __ldg(reinterpret_cast<const float*>(packed + K::B1) + t));
+    put_pair(mlp::B2X, t, 0, __ldg(reinterpret_cast<const float*>(packed + K::B2) + t));
   }
+  if (t < NOUT) put_pair(mlp::BHX, t, 0, __ldg(reinterpret_cast<const float*>(packed + K::BH) + t));
   TcCtx tc;
   tc_setup(sh, tc, mlp::TM_COLS);  // (its barrier also publishes the writes above)
-  const float* b2 = reinterpret_cast<const float*>(sm + mlp::B2);
-  const float* bh = reinterpret_cast<const float*>(sm + mlp::BH);
   const float* nrm = nrmw;
   const uint32_t lb = lane_base(tc.tmem);
   const uint32_t ld = lb + mlp::TM_D, la = lb + mlp::TM_A;
-  const uint32_t td = tc.tmem + mlp::TM_D, ta = tc.tmem + mlp::TM_A;
+  const uint32_t td = tc.tmem + mlp::TM_D, ta = tc.tmem + mlp::TM_A,
+                 tones = tc.tmem + mlp::TM_ONES;
   const uint32_t w1x = smem_u32(sm + mlp::W1X), w2 = smem_u32(sm + mlp::W2),
-                 wh = smem_u32(sm + mlp::WH);
+                 wh = smem_u32(sm + mlp::WH), b2x = smem_u32(sm + mlp::B2X),
+                 bhx = smem_u32(sm + mlp::BHX);
+  {  // the constant A of ones for the bias K steps: K 0, 1 = 1, the rest 0
+    uint32_t w[16] = {0x3F803F80u};
+    tmem_st16(lb + mlp::TM_ONES, w);  // (published by the first MMA's barrier)
+  }
+  // D = A W^T over nks K steps, then D += ones bias^T (one more K step)
+  auto mma_bias = [&](uint32_t w, uint32_t bias, int n_out) {
+    const uint32_t id = idesc_bf16(128, n_out);
+    for (int ks = 0; ks < 4; ++ks)
+      umma_bf16_ts(td, ta + 8u * ks, sw128_desc(w + ks * 32), id, ks > 0 ? 1u : 0u);
+    umma_bf16_ts(td, tones, sw128_desc(bias), id, 1u);
+  };
   const float sdf = nrm[24];
 
   // The A operand was stored to tensor memory by every thread -> barrier ->
@@ -240,9 +260,9 @@ __global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
     }
     if (!run([&] { umma_128xN_ts(td, ta, w1x, 64, 2); })) break;
     relu_to_tmem(ld, la, nullptr);  // g1 = ReLU(W1 x + b1) (bias in D)
-    if (!run([&] { umma_128xN_ts(td, ta, w2, 64, 4); })) break;
-    relu_to_tmem(ld, la, b2);       // h0 = ReLU(W2 g1 + b2)
-    if (!run([&] { umma_128xN_ts(td, ta, wh, 16, 4); })) break;
+    if (!run([&] { mma_bias(w2, b2x, 64); })) break;
+    relu_to_tmem(ld, la, nullptr);  // h0 = ReLU(W2 g1 + b2) (bias in D)
+    if (!run([&] { mma_bias(wh, bhx, 16); })) break;
     {  // heads and Eq. 3
       float y[16];
       tmem_ld16(ld, y);
@@ -254,11 +274,11 @@ __global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
       // tau_adj = 1/2 + sigmoid(y_0) = 1 + tanh(y_0 / 2) / 2 (or 1)
       const float tadj = (variant & VAR_FIXED_TAU)
                              ? 1.0f
-                             : fmaf(0.5f, tanh_fast(0.5f * (y[0] + bh[0])), 1.0f);
+                             : fmaf(0.5f, tanh_fast(0.5f * y[0]), 1.0f);
       const float inv = __fdividef(1.0f, tau * tadj);
       float d[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) d[q] = sdf * (y[1 + q] + bh[1 + q]);
+      for (int q = 0; q < Q; ++q) d[q] = sdf * y[1 + q];
       if (variant & VAR_CONSERVATIVE) conserve9(d);
       const float usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy);
       if (n < N) {
