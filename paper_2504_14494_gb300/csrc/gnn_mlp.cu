@@ -28,8 +28,8 @@
 
 namespace lbmgnn {
 
-#ifndef LBM_MLP_CTAS
-#define LBM_MLP_CTAS 4  // resident CTAs per SM (128 tensor-memory columns each)
+#ifndef LBM_MLP_GROUPS
+#define LBM_MLP_GROUPS 4  // independent 128-thread tile groups per CTA (one CTA per SM)
 #endif
 
 namespace mlp {
@@ -40,12 +40,21 @@ constexpr int STAGES = 3;
 constexpr int SLOTS = Q + 1;  // per node and stage: the 9 pulled populations and tau
 // B2X / BHX: SW128 blocks whose K columns 0 and 1 hold the layer-2 and head
 // biases as BF16 pairs hi + lo (~16 bits): one extra K step against a
-// constant A of ones adds the bias inside the MMA.
-constexpr uint32_t W1X = 0, W2 = 8192, WH = 16384, B2X = 18432, BHX = 26624, STG = 28672,
-                   STG_BYTES = SLOTS * TILE * 4,                   // 5120 per stage
-                   NORM = STG + STAGES * STG_BYTES,                // 44032
-                   SH = NORM + 128, BYTES = SH + 64;
-constexpr uint32_t TM_D = 0, TM_A = 64, TM_ONES = 96, TM_COLS = 128;
+// constant A of ones adds the bias inside the MMA.  WH is the head as this
+// kernel uses it (32 output rows, see the prologue).
+constexpr int NG = LBM_MLP_GROUPS;
+constexpr uint32_t W1X = 0, W2 = 8192, WH = 16384, B2X = 20480, BHX = 28672, STG = 32768,
+                   STG_BYTES = SLOTS * TILE * 4,                   // 5120 per stage and group
+                   NORM = STG + NG * STAGES * STG_BYTES,
+                   SH = NORM + 128, BYTES = SH + NG * 16;
+// tensor memory: group g's accumulator D at 64 g (64 columns), its A
+// operand at 64 NG + 32 g (32 columns of BF16 pairs); one constant block of
+// ones after them
+constexpr uint32_t TM_COLS = 512, TM_ONES = 96 * NG;
+__host__ __device__ constexpr uint32_t tm_d(int g) { return 64u * g; }
+__host__ __device__ constexpr uint32_t tm_a(int g) { return 64u * NG + 32u * g; }
+static_assert(TM_ONES + 16 <= TM_COLS, "tensor-memory columns");
+static_assert(TM_COLS == 512, "one allocation of the whole tensor memory (power of two)");
 }  // namespace mlp
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
@@ -112,7 +121,7 @@ __device__ __forceinline__ void relu_to_tmem(uint32_t lane_d, uint32_t lane_a, c
 
 // One fused GNN-LBM step of the MLP-only network over the nodes of `geo`.
 template <class Geo>
-__global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
+__global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
     const float* __restrict__ f_in, float* __restrict__ f_out, Geo geo, float tau0,
     const float* __restrict__ taus, const uint8_t* __restrict__ packed, bool require_mlp,
     unsigned* stw) {
@@ -125,12 +134,16 @@ __global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   TcShared* sh = reinterpret_cast<TcShared*>(sm + mlp::SH);
-  float* stg = reinterpret_cast<float*>(sm + mlp::STG);
-  const int t = threadIdx.x;
+  // group grp of 128 threads: t = node of its tile, warp (t / 32) owns
+  // tensor-memory lanes 32 (t / 32)..; its own tile sequence, staging ring,
+  // mbarrier, tensor-memory slice and named barrier
+  const int grp = threadIdx.x >> 7, t = threadIdx.x & 127;
+  float* stg = reinterpret_cast<float*>(sm + mlp::STG) + grp * (mlp::STAGES * mlp::SLOTS * TILE);
   const int64_t N = geo.count();
   const int64_t base = geo.base(), ps = geo.ps();
   const int64_t ntiles = (N + TILE - 1) / TILE;
-  const int64_t first = blockIdx.x, stride = gridDim.x;
+  const int64_t first = (int64_t)blockIdx.x * mlp::NG + grp,
+                stride = (int64_t)gridDim.x * mlp::NG;
 
   // Node t of tile `tile` -> stage st (cp.async): its 9 populations pulled
   // from x - e_q (periodic wrap inside its lattice) and its relaxation time.
@@ -160,13 +173,13 @@ __global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
 
   copy_g2s(sm + mlp::W1X, packed + K::W1X, 8192);
   copy_g2s(sm + mlp::W2, packed + K::W2, 8192);
-  copy_g2s(sm + mlp::WH, packed + K::WH, 2048);
   copy_g2s(sm + mlp::NORM, packed + K::NORM, 128);
-  for (uint32_t i = t; i < (mlp::STG - mlp::B2X) / 16; i += blockDim.x)  // bias blocks: zeros
-    reinterpret_cast<uint4*>(sm + mlp::B2X)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (uint32_t i = threadIdx.x; i < (mlp::STG - mlp::WH) / 16; i += blockDim.x)  // head, biases: 0
+    reinterpret_cast<uint4*>(sm + mlp::WH)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   float* nrmw = reinterpret_cast<float*>(sm + mlp::NORM);
-  if (t < NFEAT) nrmw[NFEAT + t] = 1.0f / nrmw[NFEAT + t];  // sigma -> 1/sigma
+  if (threadIdx.x < NFEAT)  // sigma -> 1/sigma
+    nrmw[NFEAT + threadIdx.x] = 1.0f / nrmw[NFEAT + threadIdx.x];
   // The biases ride along in the MMAs as BF16 pairs hi + lo (~16 bits):
   // b1 in K columns 12 and 13 of W1x (multiplied by feature columns equal to
   // 1), b2 and the head bias in K columns 0 and 1 of their own blocks
@@ -177,25 +190,81 @@ __global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
     *reinterpret_cast<__nv_bfloat16*>(sm + blk + sw128_off(row, k + 1)) =
         __float2bfloat16_rn(b - hi);
   };
-  if (t < HID) {
-    put_pair(mlp::W1X, t, 12, __ldg(reinterpret_cast<const float*>(packed + K::B1) + t));
-    put_pair(mlp::B2X, t, 0, __ldg(reinterpret_cast<const float*>(packed + K::B2) + t));
+  if (threadIdx.x < HID) {
+    const int o = threadIdx.x;
+    put_pair(mlp::W1X, o, 12, __ldg(reinterpret_cast<const float*>(packed + K::B1) + o));
+    put_pair(mlp::B2X, o, 0, __ldg(reinterpret_cast<const float*>(packed + K::B2) + o));
   }
-  if (t < NOUT) put_pair(mlp::BHX, t, 0, __ldg(reinterpret_cast<const float*>(packed + K::BH) + t));
+  // The head as this kernel uses it (N = 32): row 0 is the tau head W_h[0]
+  // (BF16 already); rows 1..9 and 17..25 hold the BF16 pair hi + lo of
+  // s_df P W_h[1..9], with P the projection of the conserving variant (else
+  // the identity), so that Delta f = y_q + y_{16+q} comes out of the MMA
+  // (bias likewise: s_df P b_h[1..9] and b_h[0] in BHX).
+  {
+    const float* whf = reinterpret_cast<const float*>(packed + K::WHF);  // FP32 [10][64]
+    const float* bhg = reinterpret_cast<const float*>(packed + K::BH);
+    const float sdf0 = __ldg(reinterpret_cast<const float*>(packed + K::NORM) + 24);
+    const bool cons = variant & VAR_CONSERVATIVE;
+    auto proj = [&](int q, int k) {  // s_df (P w)_q of column k (k = HID: the bias)
+      auto w = [&](int r) { return k < HID ? __ldg(whf + (1 + r) * HID + k) : __ldg(bhg + 1 + r); };
+      if (!cons) return sdf0 * w(q);
+      float s0 = 0.f, sx = 0.f, sy = 0.f;
+      for (int r = 0; r < Q; ++r) {
+        const float v = w(r);
+        s0 += v;
+        sx += float(ex(r)) * v;
+        sy += float(ey(r)) * v;
+      }
+      return sdf0 * (w(q) - s0 * (1.0f / 9.0f) - float(ex(q)) * sx * (1.0f / 6.0f) -
+                     float(ey(q)) * sy * (1.0f / 6.0f));
+    };
+    for (int i = threadIdx.x; i < (Q + 1) * (HID + 1); i += blockDim.x) {
+      const int q = i / (HID + 1) - 1, k = i % (HID + 1);  // q = -1: the tau row
+      if (k < HID) {
+        if (q < 0) {
+          *reinterpret_cast<__nv_bfloat16*>(sm + mlp::WH + sw128_off(0, k)) =
+              __float2bfloat16_rn(__ldg(whf + k));
+        } else {
+          const float v = proj(q, k), hi = bf16_round(v);
+          *reinterpret_cast<__nv_bfloat16*>(sm + mlp::WH + sw128_off(1 + q, k)) =
+              __float2bfloat16_rn(hi);
+          *reinterpret_cast<__nv_bfloat16*>(sm + mlp::WH + sw128_off(17 + q, k)) =
+              __float2bfloat16_rn(v - hi);
+        }
+      } else {
+        put_pair(mlp::BHX, 1 + q, 0, q < 0 ? __ldg(bhg) : proj(q, HID));
+      }
+    }
+  }
+  // one mbarrier per group; warp 0 allocates all 512 tensor-memory columns
+  // (a power of two, as tcgen05.alloc requires; one CTA per SM)
+  if (threadIdx.x == 0)
+    for (int g = 0; g < mlp::NG; ++g) mbar_init(&sh[g].bar, 1);
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(&sh[0].tmem, mlp::TM_COLS);
+  tc_fence_before();
+  __syncthreads();  // (also publishes the shared-memory writes above)
+  tc_fence_after();
   TcCtx tc;
-  tc_setup(sh, tc, mlp::TM_COLS);  // (its barrier also publishes the writes above)
+  tc.bar = &sh[grp].bar;  // the group's own mbarrier; its slice of the columns:
+  tc.phase = 0;
+  tc.tmem = sh[0].tmem;
+  const uint32_t tbase = sh[0].tmem;
   const float* nrm = nrmw;
-  const uint32_t lb = lane_base(tc.tmem);
-  const uint32_t ld = lb + mlp::TM_D, la = lb + mlp::TM_A;
-  const uint32_t td = tc.tmem + mlp::TM_D, ta = tc.tmem + mlp::TM_A,
-                 tones = tc.tmem + mlp::TM_ONES;
+  const uint32_t lb = lane_base(tbase);
+  const uint32_t ld = lb + mlp::tm_d(grp), la = lb + mlp::tm_a(grp);
+  const uint32_t td = tbase + mlp::tm_d(grp), ta = tbase + mlp::tm_a(grp),
+                 tones = tbase + mlp::TM_ONES;
   const uint32_t w1x = smem_u32(sm + mlp::W1X), w2 = smem_u32(sm + mlp::W2),
                  wh = smem_u32(sm + mlp::WH), b2x = smem_u32(sm + mlp::B2X),
                  bhx = smem_u32(sm + mlp::BHX);
-  {  // the constant A of ones for the bias K steps: K 0, 1 = 1, the rest 0
+  if (grp == 0) {  // the constant A of ones for the bias K steps: K 0, 1 = 1, the rest 0
     uint32_t w[16] = {0x3F803F80u};
-    tmem_st16(lb + mlp::TM_ONES, w);  // (published by the first MMA's barrier)
+    tmem_st16(lane_base(tbase) + mlp::TM_ONES, w);
+    tmem_st_wait();
   }
+  tc_fence_before();
+  __syncthreads();  // the ones are in place for every group's MMAs
+  tc_fence_after();
   // D = A W^T over nks K steps, then D += ones bias^T (one more K step)
   auto mma_bias = [&](uint32_t w, uint32_t bias, int n_out) {
     const uint32_t id = idesc_bf16(128, n_out);
@@ -203,14 +272,13 @@ __global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
       umma_bf16_ts(td, ta + 8u * ks, sw128_desc(w + ks * 32), id, ks > 0 ? 1u : 0u);
     umma_bf16_ts(td, tones, sw128_desc(bias), id, 1u);
   };
-  const float sdf = nrm[24];
 
   // The A operand was stored to tensor memory by every thread -> barrier ->
   // one thread issues the MMA chain and commits it; all threads wait.
   auto run = [&](auto issue) -> bool {
     tmem_st_wait();
     tc_fence_before();
-    __syncthreads();
+    group_sync(grp, 128);
     if (t == 0) {
       tc_fence_after();
       issue();
@@ -219,7 +287,7 @@ __global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
     const bool ok = mbar_wait(tc.bar, tc.phase);
     tc.phase ^= 1u;
     tc_fence_after();
-    if (__syncthreads_or(!ok)) {
+    if (group_any(grp, 128, !ok)) {
       if (t == 0) raise_status(stw, ST_TIMEOUT);
       return false;
     }
@@ -262,10 +330,10 @@ __global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
     relu_to_tmem(ld, la, nullptr);  // g1 = ReLU(W1 x + b1) (bias in D)
     if (!run([&] { mma_bias(w2, b2x, 64); })) break;
     relu_to_tmem(ld, la, nullptr);  // h0 = ReLU(W2 g1 + b2) (bias in D)
-    if (!run([&] { mma_bias(wh, bhx, 16); })) break;
+    if (!run([&] { mma_bias(wh, bhx, 32); })) break;
     {  // heads and Eq. 3
-      float y[16];
-      tmem_ld16(ld, y);
+      float y[32];
+      tmem_ld32(ld, y);
       float fv[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) fv[q] = sv[q * TILE];
@@ -276,10 +344,9 @@ __global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
                              ? 1.0f
                              : fmaf(0.5f, tanh_fast(0.5f * y[0]), 1.0f);
       const float inv = __fdividef(1.0f, tau * tadj);
-      float d[Q];
+      float d[Q];  // Delta f = s_df P y_1..9 (hi + lo rows of the head)
 #pragma unroll
-      for (int q = 0; q < Q; ++q) d[q] = sdf * y[1 + q];
-      if (variant & VAR_CONSERVATIVE) conserve9(d);
+      for (int q = 0; q < Q; ++q) d[q] = y[1 + q] + y[17 + q];
       const float usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy);
       if (n < N) {
 #pragma unroll
@@ -288,24 +355,29 @@ __global__ void __launch_bounds__(128, LBM_MLP_CTAS) gnn_mlp_step_kernel(
       }
     }
     tc_fence_before();
-    __syncthreads();  // the head's accumulator is read before the next tile's MMA
+    group_sync(grp, 128);  // the head's accumulator is read before the next tile's MMA
   }
   cp_async_wait<0>();
-  tc_teardown(sh, tc, mlp::TM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tbase, mlp::TM_COLS);
 }
 
 template <class Geo>
 static cudaError_t mlp_step(const float* f_in, float* f_out, const Geo& geo, int64_t N, float tau,
                             const float* taus, const uint8_t* packed, bool require_mlp,
-                            cudaStream_t st, int per_sm) {
+                            cudaStream_t st) {
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
   if (N <= 0) return cudaSuccess;
   const uint32_t bytes = mlp::BYTES + 1024;
   cudaError_t e;
   if ((e = set_smem(gnn_mlp_step_kernel<Geo>, bytes)) != cudaSuccess) return e;
-  const unsigned grid = grid_for(N, per_sm);
-  gnn_mlp_step_kernel<Geo><<<grid, 128, bytes, st>>>(f_in, f_out, geo, tau, taus, packed,
+  // one CTA (NG tile groups) per SM, fewer for small lattices
+  const int64_t ntiles = (N + TILE - 1) / TILE;
+  const int64_t want = (ntiles + mlp::NG - 1) / mlp::NG;
+  const unsigned grid = (unsigned)(want < num_sms() ? want : num_sms());
+  gnn_mlp_step_kernel<Geo><<<grid, 128 * mlp::NG, bytes, st>>>(f_in, f_out, geo, tau, taus, packed,
                                                       require_mlp, stw);
   return cudaGetLastError();
 }
@@ -314,7 +386,7 @@ cudaError_t launch_gnn_mlp_step(const float* f_in, float* f_out, const Shape& s,
                                 const float* taus, const uint8_t* packed, bool require_mlp,
                                 cudaStream_t st) {
   return mlp_step(f_in, f_out, make_geo_stack(s), (int64_t)s.nb * s.ny * s.nx, tau, taus, packed,
-                  require_mlp, st, LBM_MLP_CTAS);
+                  require_mlp, st);
 }
 
 cudaError_t launch_gnn_mlp_step_table(const float* f_in, float* f_out, const LatDesc* lat,
@@ -322,8 +394,8 @@ cudaError_t launch_gnn_mlp_step_table(const float* f_in, float* f_out, const Lat
                                       int64_t count, int64_t ps, const uint8_t* packed,
                                       cudaStream_t st, int per_sm) {
   const GeoTable geo{lat, first, n, base, count, ps, hint};
-  return mlp_step(f_in, f_out, geo, count, 0.0f, nullptr, packed, false, st,
-                  per_sm >= 2 ? LBM_MLP_CTAS : per_sm);
+  (void)per_sm;  // one CTA of LBM_MLP_GROUPS tile groups per SM, whatever the batch plan chose
+  return mlp_step(f_in, f_out, geo, count, 0.0f, nullptr, packed, false, st);
 }
 
 }  // namespace lbmgnn
