@@ -370,8 +370,13 @@ LBM_API int gnn_train_step(const float* f_in, const float* f_target, lbm_shape s
  * kernel over all BGK lattices and, concurrently on a second branch, the GNN
  * kernels over all GNN lattices.  The graph is recorded on the first call with
  * a given (buffers, steps) and replayed afterwards.  Launch shapes are chosen
- * on first use by the autotuner (timed with CUDA events; cached per kernel,
- * SM count and size bucket; lbm_autotune_save/load persist the cache as JSON).
+ * on first use by the autotuner (each candidate timed with CUDA events, best
+ * of three; cached per kernel, SM count and size bucket; lbm_autotune_save/
+ * load persist the cache as JSON): the tile shape of the batched BGK kernel
+ * (128, 256 or 512 threads per block x 1, 2 or 4 nodes per thread; cache
+ * value = threads * 10 + nodes per thread) and the resident CTAs per SM of
+ * the GNN kernels (1 or 2).  A GNN group whose network is the MLP-only one
+ * runs the fused step kernel (one CTA of 4 tile groups per SM).
  * lbm_batch_plan_create allocates the plan's device tables (cudaMalloc) and
  * two streams; lbm_batch_plan_destroy frees them.
  * ------------------------------------------------------------------------- */

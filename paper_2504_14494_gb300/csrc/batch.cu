@@ -24,25 +24,40 @@ using namespace lbmgnn;
 
 namespace lbmgnn {
 
-// One thread per node of the BGK group: pull-stream from the lattice's own
-// nodes (periodic wrap), Eq. 1-2 with the lattice's tau, store.
-template <int NT>
+// The BGK group: pull-stream from the lattice's own nodes (periodic wrap),
+// Eq. 1-2 with the lattice's tau, store.  Tile shape: a block of NT threads
+// covers NT * NPT consecutive nodes, thread t the nodes t, t + NT, ... (each
+// pass coalesced), so that NPT nodes' loads are in flight per thread.
+template <int NT, int NPT>
 __global__ void __launch_bounds__(NT) bgk_batch_kernel(const float* __restrict__ fin,
                                                        float* __restrict__ fout,
                                                        const LatDesc* __restrict__ lat, int nlat,
                                                        const int* __restrict__ hint, int64_t count,
                                                        int64_t ps, unsigned* stw) {
-  const int64_t g = (int64_t)blockIdx.x * NT + threadIdx.x;
-  if (g >= count) return;
   const GeoTable geo{lat, 0, nlat, 0, count, ps, hint};
-  const GeoPos p = geo.pos(g);
-  float f[Q];
+  const int64_t g0 = (int64_t)blockIdx.x * (NT * NPT) + threadIdx.x;
+  float f[NPT][Q];
+  int b[NPT];
 #pragma unroll
-  for (int q = 0; q < Q; ++q)
-    f[q] = __ldg(fin + q * ps + checked(geo_nbr(p, -ex(q), -ey(q)), 0, count, stw));
-  bgk_collide(f, 1.0f / __ldg(&lat[p.b].tau));
+  for (int k = 0; k < NPT; ++k) {
+    const int64_t g = g0 + k * NT;
+    if (g < count) {
+      const GeoPos p = geo.pos(g);
+      b[k] = p.b;
 #pragma unroll
-  for (int q = 0; q < Q; ++q) fout[q * ps + g] = f[q];
+      for (int q = 0; q < Q; ++q)
+        f[k][q] = __ldg(fin + q * ps + checked(geo_nbr(p, -ex(q), -ey(q)), 0, count, stw));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    const int64_t g = g0 + k * NT;
+    if (g < count) {
+      bgk_collide(f[k], 1.0f / __ldg(&lat[b[k]].tau));
+#pragma unroll
+      for (int q = 0; q < Q; ++q) fout[q * ps + g] = f[k][q];
+    }
+  }
 }
 
 // Taylor-Green initial state of every lattice (per-lattice rho0, u0, kx, ky).
@@ -130,25 +145,34 @@ int tune(const char* kernel, int64_t nodes, const std::vector<int>& cand, cudaSt
 }
 }  // namespace
 
+// Tile shapes of the batched BGK kernel the autotuner chooses from, encoded
+// as threads per block * 10 + nodes per thread.
+const std::vector<int> kBgkTiles = {1281, 1282, 1284, 2561, 2562, 2564, 5121, 5122};
+
+template <int NT, int NPT>
+static void bgk_batch_t(const float* fin, float* fout, const LatDesc* lat, int nlat,
+                        const int* hint, int64_t count, int64_t ps, unsigned* stw,
+                        cudaStream_t st) {
+  const int64_t per = (int64_t)NT * NPT;
+  bgk_batch_kernel<NT, NPT><<<(unsigned)((count + per - 1) / per), NT, 0, st>>>(
+      fin, fout, lat, nlat, hint, count, ps, stw);
+}
+
 cudaError_t launch_bgk_batch(const float* fin, float* fout, const LatDesc* lat, int nlat,
-                             const int* hint, int64_t count, int64_t ps, int block,
+                             const int* hint, int64_t count, int64_t ps, int tile,
                              cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
-  switch (block) {
-    case 128:
-      bgk_batch_kernel<128><<<(unsigned)((count + 127) / 128), 128, 0, st>>>(fin, fout, lat, nlat,
-                                                                          hint, count, ps, stw);
-      break;
-    case 512:
-      bgk_batch_kernel<512><<<(unsigned)((count + 511) / 512), 512, 0, st>>>(fin, fout, lat, nlat,
-                                                                          hint, count, ps, stw);
-      break;
-    default:
-      bgk_batch_kernel<256><<<(unsigned)((count + 255) / 256), 256, 0, st>>>(fin, fout, lat, nlat,
-                                                                          hint, count, ps, stw);
-      break;
+  switch (tile) {
+    case 1281: bgk_batch_t<128, 1>(fin, fout, lat, nlat, hint, count, ps, stw, st); break;
+    case 1282: bgk_batch_t<128, 2>(fin, fout, lat, nlat, hint, count, ps, stw, st); break;
+    case 1284: bgk_batch_t<128, 4>(fin, fout, lat, nlat, hint, count, ps, stw, st); break;
+    case 2562: bgk_batch_t<256, 2>(fin, fout, lat, nlat, hint, count, ps, stw, st); break;
+    case 2564: bgk_batch_t<256, 4>(fin, fout, lat, nlat, hint, count, ps, stw, st); break;
+    case 5121: bgk_batch_t<512, 1>(fin, fout, lat, nlat, hint, count, ps, stw, st); break;
+    case 5122: bgk_batch_t<512, 2>(fin, fout, lat, nlat, hint, count, ps, stw, st); break;
+    default: bgk_batch_t<256, 1>(fin, fout, lat, nlat, hint, count, ps, stw, st); break;
   }
   return cudaGetLastError();
 }
@@ -165,7 +189,7 @@ struct lbm_batch_plan {
   double* d_prm = nullptr;                // [n][4] TGV parameters (sorted order)
   std::vector<int> sorted_to_input;
   int64_t bgk_nodes = 0, gnn_nodes = 0, total = 0;
-  int bgk_block = 0, gnn_per_sm = 0;
+  int bgk_block = 0, gnn_per_sm = 0;  // tuned launch shapes (BGK: tile code, see kBgkTiles)
   // cached graph of one run configuration
   cudaStream_t cap = nullptr, side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -334,7 +358,7 @@ int lbm_batch_run(lbm_batch_plan* plan, const float* f_in, float* f_out, float* 
   auto* ws = static_cast<__nv_bfloat16*>(workspace);
   // Launch shapes: tuned once per size bucket (the timing runs write f_out).
   if (!plan->bgk_block) {
-    plan->bgk_block = plan->n_bgk == 0 ? 256 : tune("bgk_batch", plan->bgk_nodes, {128, 256, 512}, st,
+    plan->bgk_block = plan->n_bgk == 0 ? 2561 : tune("bgk_batch_tile", plan->bgk_nodes, kBgkTiles, st,
         [&](int c) {
           return launch_bgk_batch(f_in, f_out, plan->d_lat, plan->n_bgk, plan->d_hint,
                                   plan->bgk_nodes,

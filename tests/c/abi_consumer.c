@@ -53,7 +53,7 @@ static int host_part(void) {
   CHECK(lbm_version(&abi, &layout));
   /* a NULL vector and an unknown variant are rejected */
   const int bad_null = gnn_params_init_xavier(NULL, 5, 1e-2f, 0);
-  const int bad_variant = gnn_params_init_xavier(theta, 5, 1e-2f, 4);
+  const int bad_variant = gnn_params_init_xavier(theta, 5, 1e-2f, 8);
   printf("{\"param_count\": %zu, \"trainable_count\": %zu, \"packed_bytes\": %zu, "
          "\"step_ws\": %zu, \"host_ws\": %zu, \"saved_bytes\": %zu, "
          "\"xavier_sum\": %.17g, \"xavier_sum_abs\": %.17g, \"xavier_first\": %.9g, "

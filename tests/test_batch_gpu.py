@@ -88,7 +88,7 @@ def test_batched_run_equals_per_lattice_runs(lbmlib, cuda, tmp_path):
         path = tmp_path / "tune.json"
         L.lbm_autotune_save(path)
         tuned = json.loads(path.read_text())
-        assert any(k.startswith("bgk_batch/") for k in tuned)
+        assert any(k.startswith("bgk_batch_tile/") for k in tuned)
         assert any(k.startswith("gnn_step_table/") for k in tuned)
         L.lbm_autotune_load(path)
     finally:
@@ -150,3 +150,110 @@ def test_batch_plan_argument_checks(lbmlib):
     with pytest.raises(L.LbmError) as e:  # a lattice of 2^31 nodes
         L.lbm_batch_plan_create([(8, 8, 0, 0.8), (65536, 32768, 1, 0.8)])
     assert e.value.code == L.LBM_ERR_SIZE
+
+
+def test_every_bgk_tile_shape_gives_the_same_bits(lbmlib, cuda, tmp_path):
+    """Each tile shape the autotuner can choose for the batched BGK kernel
+    (threads per block x nodes per thread, forced through a loaded cache)
+    schedules the same per-node arithmetic: identical results."""
+    import torch
+    L = lbmlib
+    lat = [(8, 8, 0, 0.8), (33, 7, 0, 0.7), (130, 5, 0, 0.55), (1, 1, 0, 0.9), (64, 40, 0, 1.1)]
+    nodes = sum(a * b for a, b, _, _ in lat)
+    sms = torch.cuda.get_device_properties(cuda).multi_processor_count
+    bucket = int(np.floor(np.log2(nodes)))
+    out = None
+    for tile in (1281, 1282, 1284, 2561, 2562, 2564, 5121, 5122):
+        path = tmp_path / f"tile{tile}.json"
+        path.write_text(json.dumps({f"bgk_batch_tile/sm{sms}/n2^{bucket}": tile}))
+        L.lbm_autotune_load(path)
+        plan = L.lbm_batch_plan_create(lat)
+        try:
+            n = L.lbm_batch_nodes(plan)
+            prm = np.array([_prm(i, l[0], l[1]) for i, l in enumerate(lat)])
+            f0 = torch.empty(9 * n, device=cuda)
+            L.lbm_batch_init_tgv(plan, f0, prm, False)
+            f1, f2 = torch.empty_like(f0), torch.empty_like(f0)
+            L.lbm_batch_run(plan, f0, f1, f2, 3, None, None)
+            assert L.lbm_get_status() == 0
+            if out is None:
+                out = f1.clone()
+            else:
+                assert torch.equal(out, f1), tile
+        finally:
+            L.lbm_batch_plan_destroy(plan)
+
+
+def test_serving_batch_of_512_lattices_sampled_against_the_oracle(lbmlib, cuda):
+    """The 512-lattice serving workload as the benchmark builds it (sides
+    log-uniform in [32, 1024], Re ~ U[100, 5000], u0 ~ U[0.01, 0.08], seed 7;
+    half BGK, half GNN-LBM with a message-passing conserving network), one
+    batched step: sampled nodes of the largest, the smallest and 10 more GNN
+    lattices (corners, edges, interior) against the oracle's GNN step of the
+    13 x 13 periodic patch around each, and of 8 BGK lattices against the
+    oracle's BGK step of the 3 x 3 patch.  Tolerances as the single-lattice
+    GNN-LBM step tests (correction rel L2 <= 3e-2, per-population bound) and
+    1e-6 per population for BGK."""
+    import torch
+    from oracle import gnn
+    from gpu_util import rel_l2
+    L = lbmlib
+    draws = inputs.batch_lattices(512, 7, 32, 1024, 100.0, 5000.0)
+    lat = [(d["side"], d["side"], 1 if d["gnn"] else 0, 0.5 + 3.0 * d["nu"]) for d in draws]
+    theta = inputs.xavier_params(0, s_df=1e-2, bias_scale=0.1, variant=2)
+    packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=cuda)
+    L.gnn_pack(torch.from_numpy(theta).to(cuda), packed)
+    plan = L.lbm_batch_plan_create(lat)
+    try:
+        n = L.lbm_batch_nodes(plan)
+        off = L.lbm_batch_offsets(plan, len(lat))
+        prm = np.array([(1.0, d["u0"], 2 * np.pi / d["side"], 2 * np.pi / d["side"])
+                        for d in draws])
+        f0 = torch.empty(9 * n, device=cuda)
+        L.lbm_batch_init_tgv(plan, f0, prm, True)
+        g = torch.Generator(device=cuda)
+        g.manual_seed(5)
+        f0.mul_(1 + 1e-2 * (2 * torch.rand(f0.shape, generator=g, device=cuda) - 1))
+        f1 = torch.empty_like(f0)
+        ws = torch.empty(L.lbm_batch_workspace_bytes(plan), dtype=torch.uint8, device=cuda)
+        L.lbm_batch_run(plan, f0, f1, None, 1, packed, ws)
+        assert L.lbm_get_status() == 0
+        F0, F1 = f0.view(9, n), f1.view(9, n)
+        rng = np.random.default_rng(3)
+        gnn_ids = [i for i, d in enumerate(draws) if d["gnn"]]
+        bgk_ids = [i for i, d in enumerate(draws) if not d["gnn"]]
+        by_size = sorted(gnn_ids, key=lambda i: draws[i]["side"])
+        pick = [by_size[-1], by_size[0]] + [int(i) for i in rng.choice(by_size[1:-1], 10, False)]
+        got, ref, bgk = [], [], []
+        for i in pick:
+            side, tau = draws[i]["side"], lat[i][3]
+            lf0 = F0[:, off[i]:off[i] + side * side].view(9, side, side)
+            lf1 = F1[:, off[i]:off[i] + side * side].view(9, side, side)
+            pts = [(0, 0), (side - 1, side - 1), (0, side // 2)]
+            pts.append(tuple(int(v) for v in rng.integers(0, side, 2)))
+            for (y, x) in pts:
+                ys = [(y + d) % side for d in range(-6, 7)]
+                xs = [(x + d) % side for d in range(-6, 7)]
+                patch = lf0[:, ys][:, :, xs].double().cpu().numpy()
+                ref.append(gnn.gnn_step(patch, theta, tau)[:, 6, 6])
+                bgk.append(lbm.bgk_step(patch, tau)[:, 6, 6])
+                got.append(lf1[:, y, x].double().cpu().numpy())
+        got, ref, bgk = np.array(got), np.array(ref), np.array(bgk)
+        e_corr = rel_l2(got - bgk, ref - bgk)
+        e_f = np.max(np.abs(got - ref) - 1e-6 * np.abs(ref)) / np.max(np.abs(ref - bgk))
+        print(f"{len(got)} GNN nodes of {len(pick)} lattices: correction rel L2 {e_corr:.2e}, "
+              f"max err / max correction {e_f:.2e}")
+        assert e_corr <= 3e-2 and e_f <= 5e-2, (e_corr, e_f)
+        for i in [int(v) for v in rng.choice(bgk_ids, 8, False)]:
+            side, tau = draws[i]["side"], lat[i][3]
+            lf0 = F0[:, off[i]:off[i] + side * side].view(9, side, side)
+            lf1 = F1[:, off[i]:off[i] + side * side].view(9, side, side)
+            for (y, x) in [(0, 0), (side - 1, 3), tuple(int(v) for v in rng.integers(0, side, 2))]:
+                ys = [(y + d) % side for d in (-1, 0, 1)]
+                xs = [(x + d) % side for d in (-1, 0, 1)]
+                patch = lf0[:, ys][:, :, xs].double().cpu().numpy()
+                want = lbm.bgk_step(patch, tau)[:, 1, 1]
+                have = lf1[:, y, x].double().cpu().numpy()
+                assert np.all(np.abs(have - want) <= 1e-6 * np.abs(want)), (i, y, x)
+    finally:
+        L.lbm_batch_plan_destroy(plan)
