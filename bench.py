@@ -285,15 +285,19 @@ def run_ours(args, rank, world, local_rank):
 
     thetas, train_info = train_bench(args, L, dev, stream)
     names = {0: "message passing (Eq. 3 as printed)", 2: "message passing, conserving correction",
-             3: "Fig. 2 MLP-only, conserving correction"}
-    gnn = {"trained": {str(v): gnn_bench(args, L, dev, stream, theta=th,
-                                         label=f"trained in this run: {names[v]}")
-                       for v, th in thetas.items()},
+             3: "Fig. 2 MLP-only, conserving correction",
+             4: "message passing, tau_adj fixed at 1 (64 x 256^2 recipe)"}
+    trained = {}
+    for v, th in thetas.items():
+        r = gnn_bench(args, L, dev, stream, theta=th, label=f"trained in this run: {names[v]}")
+        r["rollout_1000_steps"] = rollout_error(L, dev, th)
+        trained[str(v)] = r
+    gnn = {"trained": trained,
            "xavier": gnn_bench(args, L, dev, stream, label="xavier-uniform seed 0, untrained"),
            "training": train_info,
+           "held_out_rollout": held_out_rollout(L, dev, thetas[4], names[4]),
            "batch": batch_bench(args, L, dev, stream, thetas[2]),
-           "stability": {str(v): stability_bench(L, dev, thetas[v], res=(400.0, 1600.0, 3200.0))
-                         for v in (0, 2)},
+           "stability": {str(v): stability_bench(L, dev, thetas[v]) for v in (0, 2, 4)},
            "poiseuille": channel_bench(L, dev),
            "mlp_fused": mlp_bench(args, L, dev, stream, theta=thetas[3])}
 
@@ -601,6 +605,55 @@ def mlp_bench(args, L, dev, stream, theta=None, side=MLP_SIDE):
             "status": res["mlp"]["status"]}
 
 
+def rollout_error(L, dev, theta, n=GNN_SIDE, re=GNN_RE, u0=U0, steps=1000):
+    """Velocity L2 error against the closed-form TGV decay after `steps`
+    steps of the n^2 TGV at Re (uniform initial density, as the timed
+    GNN-LBM workload): BGK and the GNN-LBM step with parameters theta."""
+    import torch
+    tau = 0.5 + 3.0 * u0 * n / re
+    k = 2 * np.pi / n
+    s = L.shape(n, n)
+    packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=dev)
+    L.gnn_pack(torch.from_numpy(np.asarray(theta, np.float32)).to(dev), packed)
+    ws = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=dev)
+    out = {"workload": f"tgv_{n}x{n}_re{re:g}", "steps": steps}
+    for kind in ("bgk", "gnn"):
+        f = [torch.empty(9 * n * n, device=dev) for _ in range(2)]
+        L.lbm_init_tgv(f[0], s, 1.0, u0, k, k, False)
+        for _ in range(steps):
+            if kind == "bgk":
+                L.lbm_step_bgk(f[0], f[1], None, s, tau)
+            else:
+                L.lbm_step_gnn(f[0], f[1], s, tau, None, packed, None, ws)
+            f.reverse()
+        out[f"l2_error_{kind}"] = tgv_l2(L, f[0], s, n, u0, tau, steps, dev)
+    out["gnn_over_bgk"] = out["l2_error_gnn"] / out["l2_error_bgk"]
+    L.lbm_get_status()
+    return out
+
+
+def held_out_rollout(L, dev, theta, label, marks=(10, 25, 50, 100, 200, 400)):
+    """The held-out rollout check (k = 4 (2 pi / 256), u0 = 0.08, Re = 5000 on
+    256^2 coarse nodes): velocity error of BGK and of the GNN-LBM step against
+    the restricted 4x refined run, both from the restricted initial state."""
+    import torch
+    from paper_2504_14494_gb300.train import HeldOutRollout
+    run = HeldOutRollout(dev, theta)
+    rows = []
+    for t in range(1, max(marks) + 1):
+        run.step()
+        if t in marks:
+            (rx, ry), (bx, by), (gx, gy) = [tuple(v.double() for v in u) for u in run.velocities()]
+            den = float(torch.sqrt((rx ** 2 + ry ** 2).sum()))
+            e_b = float(torch.sqrt(((bx - rx) ** 2 + (by - ry) ** 2).sum())) / den
+            e_g = float(torch.sqrt(((gx - rx) ** 2 + (gy - ry) ** 2).sum())) / den
+            rows.append({"step": t, "l2_error_bgk": e_b, "l2_error_gnn": e_g,
+                         "ratio": e_g / e_b if e_b > 0 else None})
+    return {"case": "held-out TGV k = 4 (2 pi / 256), u0 = 0.08, Re = 5000, 256^2 coarse, "
+                    "against the restricted 4x refined run", "network": label,
+            "rows": rows, "status": L.lbm_get_status()}
+
+
 def train_bench(args, L, dev, stream, variants=(0, 2, 3)):
     """Training throughput on the 64 x 256^2 batch workload (4x refined data
     generated on the GPU, fused train step), then a short training run on
@@ -667,6 +720,24 @@ def train_bench(args, L, dev, stream, variants=(0, 2, 3)):
         runs[key] = {"steps": 3000, "lr": lr, "weight_decay": wd, "wall_s": round(t_train, 2),
                      "held_out_eq4_loss_gnn": lg / 48, "held_out_eq4_loss_bgk": lb / 48,
                      "ratio": round(lg / lb, 4), "loss_curve": curve}
+    # the fixed-tau network of the held-out rollout check: message passing,
+    # Delta f unconstrained, tau_adj = 1; 16 x 256^2 pairs per batch (4x
+    # refined), AdamW lr 1e-3, weight decay 1e-2, 3000 steps
+    th = inputs.xavier_params(0, s_df=1e-4, variant=inputs.FIXED_TAU)
+    th[38272:38922] = 0.0
+    fixed = Trainer(dev, theta=th, lr=1e-3, wd=1e-2, seed=1, n=256, batch=16, m=4, episode=32)
+    t0 = time.perf_counter()
+    curve = []
+    for i in range(3000):
+        fixed.step()
+        if i % 500 == 0 or i == 2999:
+            curve.append([i + 1, fixed.loss.item()])
+    torch.cuda.synchronize()
+    thetas[4] = fixed.theta()
+    runs["4_fixed_tau_256"] = {"steps": 3000, "lr": 1e-3, "weight_decay": 1e-2, "batch": 16,
+                               "coarse": 256, "wall_s": round(time.perf_counter() - t0, 2),
+                               "loss_curve": curve}
+    del fixed
     info = {"workload": "train_64x256x256_refined4",
             "ms_per_train_step_incl_datagen": round(ms_full, 3),
             "ms_per_fused_train_step": round(ms_step, 3),
@@ -720,6 +791,12 @@ def batch_bench(args, L, dev, stream, theta, n_lat=W.BATCH_512.lattices, seed=W.
 
     kk = B.steps if args.steps >= B.steps else max(2, args.steps)
     n, ms, st = run(lambda d: True, kk)
+    import tempfile
+    with tempfile.TemporaryDirectory() as tdir:
+        path = os.path.join(tdir, "tune.json")
+        L.lbm_autotune_save(path)
+        with open(path) as fh:
+            tuned = json.load(fh)
     halves = {}
     for name, sel in (("bgk_half", lambda d: not d["gnn"]), ("gnn_half", lambda d: d["gnn"])):
         nh, msh, sth = run(sel, min(kk, 100), replay=True)
@@ -732,16 +809,19 @@ def batch_bench(args, L, dev, stream, theta, n_lat=W.BATCH_512.lattices, seed=W.
             "graph_launches": 1, "ms_per_step": round(ms / kk, 3),
             "mlups_total": round(n * kk / (ms / 1e3) / 1e6, 1), "status": st,
             "timing": "one lbm_batch_run call of all steps (graph recording included)",
+            "autotuner_choices": tuned,
             **halves}
 
 
-def stability_bench(L, dev, theta, n=64, u0=0.1, res=(400.0, 800.0, 1600.0, 3200.0),
-                    steps=5000, chunk=250):
-    """Reynolds-number study on the 64^2 TGV (paper Sec. 3.4): BGK and GNN-LBM
-    (the network trained in this run) for `steps` steps at each Re = u0 n / nu;
-    the first chunk of `chunk` steps whose state holds a non-finite value
-    (FP64 totals of the library), and the kinetic-energy error against the
-    closed-form decay E(0) exp(-4 nu k^2 t) at the last finite chunk."""
+def stability_bench(L, dev, theta, n=64, u0s=(0.1, 0.2, 0.3),
+                    res=(400.0, 1600.0, 3200.0, 12800.0, 51200.0), steps=5000, chunk=250):
+    """Reynolds-number study on the 64^2 TGV (paper Sec. 3.4), widened in
+    Mach number (u0) and Re until the plain BGK step fails: BGK and GNN-LBM
+    (the network trained in this run) for `steps` steps at each u0 and
+    Re = u0 n / nu; the first chunk of `chunk` steps whose state holds a
+    non-finite value (FP64 totals of the library), and the kinetic-energy
+    error against the closed-form decay E(0) exp(-4 nu k^2 t) at the last
+    finite chunk."""
     import torch
     s = L.shape(n, n)
     k = 2 * np.pi / n
@@ -752,10 +832,10 @@ def stability_bench(L, dev, theta, n=64, u0=0.1, res=(400.0, 800.0, 1600.0, 3200
     fb, fc = torch.empty_like(fa), torch.empty_like(fa)
     tot = torch.zeros(5, dtype=torch.float64, device=dev)
     out = []
-    for re in res:
+    for u0, re in [(a, b) for a in u0s for b in res]:
         nu = u0 * n / re
         tau = 0.5 + 3.0 * nu
-        row = {"re": re, "tau": round(tau, 6)}
+        row = {"u0": u0, "re": re, "tau": round(tau, 6)}
         for kind in ("bgk", "gnn"):
             L.lbm_init_tgv(fa, s, 1.0, u0, k, k, False)
             L.lbm_moments(fa, s, None, None, None, tot)
@@ -782,7 +862,7 @@ def stability_bench(L, dev, theta, n=64, u0=0.1, res=(400.0, 800.0, 1600.0, 3200
             row[kind] = {"first_nonfinite_by_step": bad, "steps_finite": done if bad is None else bad - chunk,
                          "energy_rel_error": err}
         out.append(row)
-    return {"workload": f"tgv_{n}x{n}_u0_{u0}", "steps": steps, "chunk": chunk, "rows": out}
+    return {"workload": f"tgv_{n}x{n}", "steps": steps, "chunk": chunk, "rows": out}
 
 
 def channel_bench(L, dev, h=32, nx=4, umax=0.05, res=(10.0, 50.0, 100.0, 200.0)):
