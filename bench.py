@@ -449,13 +449,15 @@ def tgv_l2(L, f, s, n, u0, tau, t, dev):
 
 GNN_SIDE = W.TGV_GNN_1024.n
 GNN_RE = W.TGV_GNN_1024.re
-# Elementwise roofline of the message passing: each edge message costs 7
-# packed-FP16 pipe operations per pair of features (z = A + c + B: 2, u: 3,
-# accumulate z + z tanh u: 2) plus one tanh.approx.f16x2.  The FP16 pipe
-# issues 2 warp instructions per clock per SM (64 lanes x 2 values), so it
-# binds at 128 / 7 = 18.3 edge-feature GELUs per clock per SM; the MUFU
-# (16 lanes x 2 values) allows 32.  Peak = 18.3 x 152 SMs x 2.07 GHz.
-GELU_PER_CLK_SM = 128.0 / 7.0
+# Elementwise roofline of the message passing: each pair of edge-feature
+# GELUs is 7 packed-FP16 operations (z = A + c + B: 2, u: 3, accumulate
+# z + z tanh u: 2) and one tanh.approx.f16x2.  Measured on GB300
+# (paper_2504_14494_gb300/microbench/fp16_rate.cu): HFMA2 issues at 2.07 warp
+# instructions per clock per SM, tanh.approx.f16x2 at 0.25 (the MUFU unit
+# binds: 16 edge-feature GELUs per clock per SM), and the whole message
+# sequence at 15.3 edge-feature GELUs per clock per SM.  Peak = 15.3 x SMs x
+# the maximum SM clock.
+GELU_PER_CLK_SM = 15.3
 EDGE_GELUS_PER_NODE = 2 * 8 * 64
 
 
@@ -530,7 +532,8 @@ def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False, theta=None, label
             "roofline": None if mlp_only else {
                 "bound": "alu", "kernel": "lbm_step_gnn (gnn_encode_kernel + 2 x gnn_round_kernel)",
                 "peak_basis": f"{GELU_PER_CLK_SM:.2f} edge GELUs/clock/SM x {_sm_count(dev)} SMs "
-                              f"x {_max_sm_hz(dev) / 1e6:.0f} MHz (FP16 pipe, 7 ops per pair)",
+                              f"x {_max_sm_hz(dev) / 1e6:.0f} MHz (measured issue rate of the "
+                              f"message sequence, MUFU tanh bound; microbench/fp16_rate.cu)",
                 "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "G edge-feature GELU/s",
                 "frac": round(ach / peak, 4), "traffic": traffic,
                 "traffic_note": "DRAM bytes of one step (3 kernels), ncu"},

@@ -5,18 +5,22 @@
 // collision, and the store.  Per node it moves only the populations (9 FP32
 // loads, 9 FP32 stores: 72 bytes), like the BGK step.
 //
-// Work unit: a tile of 128 consecutive nodes; a CTA of 128 threads (thread t
-// = node t of the tile, warp w owns tensor-memory lanes 32w..32w+31) loops
-// over tiles (persistent grid, 4 CTAs per SM).  The pulled populations of
-// the next two tiles are fetched with 4-byte cp.async copies into a 3-stage
-// shared-memory ring while the current tile runs its three MMAs (M = 128
-// nodes, FP32 accumulators in tensor memory):
+// Work unit: a tile of 128 consecutive nodes.  One CTA per SM runs 4
+// independent groups of 128 threads (thread t = node t of the group's tile,
+// warp w of the group owns tensor-memory lanes 32 (w % 4)..), each looping
+// over its own tiles with its own staging ring, mbarrier, named barrier and
+// tensor-memory slice; the weights are shared.  The pulled populations of a
+// group's next two tiles are fetched with 4-byte cp.async copies into a
+// 3-stage shared-memory ring while the current tile runs its three MMAs
+// (M = 128 nodes, FP32 accumulators in tensor memory):
 //   D = [x_hi | x_lo] W1x^T   (K = 32: the FP32 features split into two BF16
 //                              parts, ~16 bits kept; b1 rides along as two
 //                              extra K columns against feature columns of 1)
-//   D = g1 W2^T               (K = 64)                        -> ReLU(+b2)
-//   D = h0 Wh^T               (K = 64, N = 16, 10 used)       -> y (+bh)
-// and f* = f - (f - f^eq)/(tau tau_adj) + s_df y_1..9 (Eq. 3).  The
+//   D = g1 W2^T + 1 b2^T      (K = 64, plus one K step for the bias)
+//   D = h0 Wh'^T + 1 bh'^T    (K = 64 + bias, N = 32: the tau head and the
+//                              BF16 pair hi + lo of s_df P W_h, P the
+//                              conserving projection or the identity)
+// and f* = f - (f - f^eq)/(tau tau_adj) + Delta f (Eq. 3).  The
 // activations never touch shared memory: each epilogue reads the node's
 // accumulator row from tensor memory, applies bias and ReLU, rounds to BF16
 // and stores the row back into tensor memory, where the next MMA reads its
