@@ -289,6 +289,8 @@ def run_ours(args, rank, world, local_rank):
              4: "message passing, tau_adj fixed at 1 (64 x 256^2 recipe)"}
     trained = {}
     for v, th in thetas.items():
+        if v == "relative":
+            continue
         r = gnn_bench(args, L, dev, stream, theta=th, label=f"trained in this run: {names[v]}")
         r["rollout_1000_steps"] = rollout_error(L, dev, th)
         trained[str(v)] = r
@@ -296,6 +298,10 @@ def run_ours(args, rank, world, local_rank):
            "xavier": gnn_bench(args, L, dev, stream, label="xavier-uniform seed 0, untrained"),
            "training": train_info,
            "held_out_rollout": held_out_rollout(L, dev, thetas[4], names[4]),
+           "held_out_rollout_weighted": {
+               f"seed{sd}": held_out_rollout(L, dev, th, "Eq. 3 as printed, trained with "
+                                             "per-instance relative weights, seed %d" % sd)
+               for sd, th in thetas["relative"].items()},
            "batch": batch_bench(args, L, dev, stream, thetas[2]),
            "stability": {str(v): stability_bench(L, dev, thetas[v]) for v in (0, 2, 4)},
            "poiseuille": channel_bench(L, dev),
@@ -737,6 +743,25 @@ def train_bench(args, L, dev, stream, variants=(0, 2, 3)):
             curve.append([i + 1, fixed.loss.item()])
     torch.cuda.synchronize()
     thetas[4] = fixed.theta()
+    # the network of Eq. 3 as printed trained with each instance weighted by
+    # its error relative to BGK (lbm_pair_weights + gnn_train_step_weighted),
+    # same recipe, three training seeds
+    thetas["relative"] = {}
+    for sd in (1, 2, 3):
+        th = inputs.xavier_params(0, s_df=1e-4)
+        th[38272:38922] = 0.0
+        wtr = Trainer(dev, theta=th, lr=1e-3, wd=1e-2, seed=sd, n=256, batch=16, m=4, episode=32,
+                      weighting="relative")
+        t0 = time.perf_counter()
+        for _ in range(3000):
+            wtr.step()
+        torch.cuda.synchronize()
+        thetas["relative"][sd] = wtr.theta()
+        runs[f"0_relative_256_seed{sd}"] = {"steps": 3000, "lr": 1e-3, "weight_decay": 1e-2,
+                                            "batch": 16, "coarse": 256, "weighting": "relative",
+                                            "wall_s": round(time.perf_counter() - t0, 2),
+                                            "last_weighted_loss": wtr.loss.item()}
+        del wtr
     runs["4_fixed_tau_256"] = {"steps": 3000, "lr": 1e-3, "weight_decay": 1e-2, "batch": 16,
                                "coarse": 256, "wall_s": round(time.perf_counter() - t0, 2),
                                "loss_curve": curve}

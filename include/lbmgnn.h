@@ -359,6 +359,33 @@ LBM_API int gnn_train_step(const float* f_in, const float* f_target, lbm_shape s
                            float* adam_v, int64_t step, float lr, float wd, double* loss,
                            float* grads, void* workspace, size_t ws_bytes, void* stream);
 
+/* Per-instance weights of the training loss (this library's option; the
+ * paper's Eq. 4 is the plain mean): for every lattice b of the stack of
+ * training pairs, D_b = the mean over its nodes x 9 of the squared one-step
+ * residual of the plain method, (BGK step of f_in) - f_target (Eq. 1-2 with
+ * tau / taus), and weights[b] = mean_c(D_c) / D_b, capped at 1e4 (device
+ * FP32 [nb]).  Weighting the loss by them makes every instance count by its
+ * error relative to the method without the network, so that pairs of the
+ * developed flow weigh as much as the start-up transient (whose residuals
+ * are ~1e3 larger); the weighted loss of the zero network equals the plain
+ * one.  workspace: device, lbm_pair_weights_workspace_bytes(s) bytes,
+ * 16-byte aligned.  nb <= 65535.  Deterministic. */
+LBM_API size_t lbm_pair_weights_workspace_bytes(lbm_shape s);
+LBM_API int lbm_pair_weights(const float* f_in, const float* f_target, lbm_shape s, float tau,
+                             const float* taus, float* weights, void* workspace,
+                             size_t ws_bytes, void* stream);
+
+/* gnn_train_step with the loss of Eq. 4 weighted per lattice:
+ * L = 1/(9 N) sum_b lat_weights[b] sum_{nodes of b, q} (f*_pred - f*_target)^2
+ * (lat_weights: device FP32 [nb], e.g. from lbm_pair_weights; all 1 gives
+ * gnn_train_step).  Other arguments and results as gnn_train_step. */
+LBM_API int gnn_train_step_weighted(const float* f_in, const float* f_target, lbm_shape s,
+                                    float tau, const float* taus, const float* lat_weights,
+                                    float* params, void* packed, float* adam_m, float* adam_v,
+                                    int64_t step, float lr, float wd, double* loss,
+                                    float* grads, void* workspace, size_t ws_bytes,
+                                    void* stream);
+
 /* ---------------------------------------------------------------------------
  * Batched runs of many lattices of uneven size (serving-style workload)
  *

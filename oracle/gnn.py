@@ -314,11 +314,13 @@ def backward(dy, cache, p):
     return g, df
 
 
-def collide_loss(f_pre, y, tau, target, p):
+def collide_loss(f_pre, y, tau, target, p, node_weight=None):
     """Eq. 3 followed by Eq. 4 (mean over nodes x 9 of the squared error).
 
-    tau may be a scalar or a per-node array (N,).  Returns (loss, dL/dy (N,10),
-    f_pred (9, N))."""
+    tau may be a scalar or a per-node array (N,).  node_weight (N,), optional:
+    each node's squared error multiplied by it (the per-instance weights of
+    the library's weighted training step; None is Eq. 4).  Returns (loss,
+    dL/dy (N,10), f_pred (9, N))."""
     q = f_pre.shape[0]
     rho, ux, uy = lbm.moments(f_pre)
     feq = lbm.equilibrium(rho, ux, uy).reshape(q, -1)
@@ -329,8 +331,9 @@ def collide_loss(f_pre, y, tau, target, p):
     f_pred = f - (f - feq) / teff + df
     n = f.size
     r = f_pred - t
-    loss = float(np.sum(r * r) / n)
-    dfs = 2.0 * r / n                                # dL/d f*
+    wn = 1.0 if node_weight is None else np.asarray(node_weight, np.float64)[None, :]
+    loss = float(np.sum(wn * r * r) / n)
+    dfs = 2.0 * wn * r / n                           # dL/d f*
     dy = np.zeros_like(y)
     # Delta f = s_df P y_1..9 with P symmetric (P = I without the variant)
     dy[:, 1:] = (p["s_df"] * (conserve(dfs) if p["variant"] & CONSERVATIVE else dfs)).T

@@ -57,6 +57,20 @@ def tgv_pair(n_c, u0, k_mult, tau_c, n_steps, m=4):
     return f_in, restrict(f, m, tau_f, tau_c)
 
 
+def pair_weights(f_in, f_target, taus, wmax=1.0e4):
+    """Per-instance loss weights of a stack of training pairs (this
+    library's training option): D_b = mean over nodes x 9 of (BGK step of
+    f_in[b]) - f_target[b])^2 (Eq. 1-2), w_b = mean(D) / D_b capped at wmax.
+    f_in, f_target: lists of (9, ny, nx) states; taus: per instance.
+    Returns (D, w)."""
+    d = np.array([np.mean((lbm.bgk_step(np.asarray(a, np.float64), t)
+                           - np.asarray(b, np.float64)) ** 2)
+                  for a, b, t in zip(f_in, f_target, taus)])
+    mean = d.mean()
+    w = np.where(d * wmax > mean, mean / np.where(d > 0, d, 1.0), wmax)
+    return d, w
+
+
 def adamw_step(theta, grad, m, v, t, lr, wd, beta1=0.9, beta2=0.999, eps=1e-8):
     """One AdamW update at step t (1-based).  Returns (theta, m, v)."""
     theta = np.asarray(theta, np.float64) * (1.0 - lr * wd)

@@ -190,11 +190,14 @@ size_t gnn_train_workspace_bytes(lbm_shape shape) {
   return (size_t)train_ws(s);
 }
 
-int gnn_train_step(const float* f_in, const float* f_target, lbm_shape shape, float tau,
-                   const float* taus, float* params, void* packed, float* adam_m, float* adam_v,
-                   int64_t step, float lr, float wd, double* loss, float* grads, void* workspace,
-                   size_t ws_bytes, void* stream) {
-  LBM_TRACE("gnn_train_step");
+}  // extern "C"
+
+namespace {
+// The fused training step; lw: per-lattice loss weights or NULL (Eq. 4).
+int train_step(const float* f_in, const float* f_target, lbm_shape shape, float tau,
+               const float* taus, const float* lw, float* params, void* packed, float* adam_m,
+               float* adam_v, int64_t step, float lr, float wd, double* loss, float* grads,
+               void* workspace, size_t ws_bytes, void* stream) {
   Shape s;
   if (!f_in || !f_target || !params || !packed || !adam_m || !adam_v || !loss || step < 1)
     return LBM_ERR_ARG;
@@ -224,8 +227,8 @@ int gnn_train_step(const float* f_in, const float* f_target, lbm_shape shape, fl
   if (launch_stream(f_in, f_pre, s, st) != cudaSuccess) return LBM_ERR_CUDA;
   if (int r = gnn_forward(f_pre, shape, packed, saved, y, stream)) return r;
   int nblk = 0;
-  if (launch_collide_loss(f_pre, y, f_target, s, tau, taus, pk, lossp, &nblk, dy, nullptr, st) !=
-      cudaSuccess)
+  if (launch_collide_loss(f_pre, y, f_target, s, tau, taus, pk, lossp, &nblk, dy, nullptr, st,
+                          lw) != cudaSuccess)
     return LBM_ERR_CUDA;
   if (launch_loss_finish(lossp, nblk, 9.0 * (double)N, loss, st) != cudaSuccess)
     return LBM_ERR_CUDA;
@@ -239,6 +242,52 @@ int gnn_train_step(const float* f_in, const float* f_target, lbm_shape shape, fl
   if (int r = gnn_adamw(params, g, adam_m, adam_v, step, lr, wd, 0.9f, 0.999f, 1e-8f, stream))
     return r;
   return gnn_pack(params, packed, stream);
+}
+}  // namespace
+
+extern "C" {
+
+int gnn_train_step(const float* f_in, const float* f_target, lbm_shape shape, float tau,
+                   const float* taus, float* params, void* packed, float* adam_m, float* adam_v,
+                   int64_t step, float lr, float wd, double* loss, float* grads, void* workspace,
+                   size_t ws_bytes, void* stream) {
+  LBM_TRACE("gnn_train_step");
+  return train_step(f_in, f_target, shape, tau, taus, nullptr, params, packed, adam_m, adam_v,
+                    step, lr, wd, loss, grads, workspace, ws_bytes, stream);
+}
+
+int gnn_train_step_weighted(const float* f_in, const float* f_target, lbm_shape shape, float tau,
+                            const float* taus, const float* lat_weights, float* params,
+                            void* packed, float* adam_m, float* adam_v, int64_t step, float lr,
+                            float wd, double* loss, float* grads, void* workspace,
+                            size_t ws_bytes, void* stream) {
+  LBM_TRACE("gnn_train_step_weighted");
+  if (!lat_weights) return LBM_ERR_ARG;
+  return train_step(f_in, f_target, shape, tau, taus, lat_weights, params, packed, adam_m,
+                    adam_v, step, lr, wd, loss, grads, workspace, ws_bytes, stream);
+}
+
+size_t lbm_pair_weights_workspace_bytes(lbm_shape shape) {
+  Shape s;
+  if (check_shape_t(shape, &s)) return 0;
+  return (size_t)pair_weights_ws(s);
+}
+
+int lbm_pair_weights(const float* f_in, const float* f_target, lbm_shape shape, float tau,
+                     const float* taus, float* weights, void* workspace, size_t ws_bytes,
+                     void* stream) {
+  LBM_TRACE("lbm_pair_weights");
+  Shape s;
+  if (!f_in || !f_target || !weights) return LBM_ERR_ARG;
+  if (int r = check_shape_t(shape, &s)) return r;
+  if (s.nb > 65535) return LBM_ERR_SIZE;
+  if (!taus && (!std::isfinite(tau) || !(tau > 0.5f))) return LBM_ERR_TAU;
+  if (!workspace || (int64_t)ws_bytes < pair_weights_ws(s) || !aligned16(workspace))
+    return LBM_ERR_WORKSPACE;
+  return launch_pair_weights(f_in, f_target, s, tau, taus, weights, workspace,
+                             static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? LBM_OK
+             : LBM_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) gnn_collide_loss_kernel(
     const float* __restrict__ f_pre, const float* __restrict__ y, const float* __restrict__ tgt,
     Shape s, float tau, const float* __restrict__ taus, const uint8_t* __restrict__ packed,
     double* __restrict__ lossp, float* __restrict__ dy, float* __restrict__ f_pred,
-    unsigned* stw) {
+    const float* __restrict__ lw, unsigned* stw) {
   if (!blob_ok(packed, stw)) {  // no loss from an invalid image: NaN
     if (threadIdx.x == 0) lossp[blockIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
     return;
@@ -131,13 +131,14 @@ __global__ void __launch_bounds__(256) gnn_collide_loss_kernel(
   for (int o = 0; o < NOUT; ++o) yv[o] = __ldg(y + o * N + nn);
   const int64_t b = nn / ((int64_t)s.nx * s.ny);
   const float t = taus ? __ldg(taus + b) : tau;
+  const float wb = lw ? __ldg(lw + b) : 1.0f;  // per-instance loss weight (1: Eq. 4)
   const Moments m = moments9(fv);
   const float usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy);
   const bool fixed_tau = variant & VAR_FIXED_TAU;
   const float sg = sigmoid_acc(yv[0]);
   const float teff = t * tau_adj_of(yv[0], variant);
   const float inv = 1.0f / teff;
-  const float scale = 2.0f / (9.0f * (float)N);
+  const float scale = 2.0f * wb / (9.0f * (float)N);
   double lp = 0.0;
   float dta = 0.0f, dyv[NOUT], d[Q], g[Q];
 #pragma unroll
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(256) gnn_collide_loss_kernel(
     const float fe = feq_i(q, m, usq15);
     const float fp = fv[q] - (fv[q] - fe) * inv + d[q];
     const float r = fp - __ldg(tgt + q * s.ps + nn);
-    lp += (double)r * (double)r;
+    lp += (double)wb * (double)r * (double)r;
     g[q] = scale * r;  // dL/df*
     dta += g[q] * (fv[q] - fe);
     if (on && f_pred) f_pred[q * s.ps + n] = fp;
@@ -847,14 +848,14 @@ __global__ void adamw_kernel(float* __restrict__ theta, const float* __restrict_
 cudaError_t launch_collide_loss(const float* f_pre, const float* y, const float* tgt,
                                 const Shape& s, float tau, const float* taus,
                                 const uint8_t* packed, double* lossp, int* nblk, float* dy,
-                                float* f_pred, cudaStream_t st) {
+                                float* f_pred, cudaStream_t st, const float* lw) {
   const int64_t N = (int64_t)s.nb * s.ny * s.nx;
   const unsigned blocks = (unsigned)((N + 255) / 256);
   *nblk = (int)blocks;
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
   gnn_collide_loss_kernel<<<blocks, 256, 0, st>>>(f_pre, y, tgt, s, tau, taus, packed, lossp, dy,
-                                                   f_pred, stw);
+                                                   f_pred, lw, stw);
   return cudaGetLastError();
 }
 

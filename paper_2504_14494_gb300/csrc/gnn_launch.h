@@ -84,7 +84,12 @@ cudaError_t launch_gnn_backward(const BackwardLaunch& bl, const Shape& s, const 
 cudaError_t launch_collide_loss(const float* f_pre, const float* y, const float* tgt,
                                 const Shape& s, float tau, const float* taus,
                                 const uint8_t* packed, double* lossp, int* nblk, float* dy,
-                                float* f_pred, cudaStream_t st);
+                                float* f_pred, cudaStream_t st, const float* lw = nullptr);
+// Per-instance loss weights (weights.cu): w_b = mean_c D_c / D_b with D_b the
+// mean squared one-step BGK residual of lattice b against its target.
+int64_t pair_weights_ws(const Shape& s);
+cudaError_t launch_pair_weights(const float* f_in, const float* tgt, const Shape& s, float tau,
+                                const float* taus, float* w, void* ws, cudaStream_t st);
 cudaError_t launch_loss_finish(const double* lossp, int nblk, double count, double* loss,
                                cudaStream_t st);
 cudaError_t launch_adamw(float* theta, const float* g, float* m, float* v, float lr, float wd,

@@ -94,6 +94,13 @@ _SIGS = {
     "lbm_step_gnn_noalloc": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP,
                                             _VP]),
     "lbm_step_gnn_mlp": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP, _VP]),
+    "lbm_pair_weights_workspace_bytes": (ctypes.c_size_t, [lbm_shape]),
+    "lbm_pair_weights": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP,
+                                        ctypes.c_size_t, _VP]),
+    "gnn_train_step_weighted": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP,
+                                               _VP, _VP, _VP, ctypes.c_int64, ctypes.c_float,
+                                               ctypes.c_float, _VP, _VP, _VP, ctypes.c_size_t,
+                                               _VP]),
     "lbm_batch_plan_create": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "lbm_batch_plan_destroy": (None, [_VP]),
     "lbm_batch_nodes": (ctypes.c_int64, [_VP]),
@@ -446,6 +453,40 @@ def gnn_adamw(params, grads, m, v, step, lr, wd, beta1=0.9, beta2=0.999, eps=1e-
 
 def gnn_train_workspace_bytes(s):
     return load().gnn_train_workspace_bytes(s)
+
+
+def lbm_pair_weights_workspace_bytes(s):
+    return load().lbm_pair_weights_workspace_bytes(s)
+
+
+def lbm_pair_weights(f_in, f_target, s, tau, taus, weights, workspace, ws_bytes=None,
+                     stream=None):
+    """Per-lattice loss weights mean(D) / D_b from the one-step BGK residuals
+    (see include/lbmgnn.h); weights: device FP32 [nb]."""
+    _, _, fe = _elems(s)
+    f32 = _f32()
+    check(load().lbm_pair_weights(dptr(f_in, "f_in", f32, fe), dptr(f_target, "f_target", f32, fe),
+                                  s, float(tau), dptr(taus, "taus", f32, int(s.nb)),
+                                  dptr(weights, "weights", f32, int(s.nb)),
+                                  dptr(workspace, "workspace"),
+                                  int(nbytes(workspace) if ws_bytes is None else ws_bytes),
+                                  stream_ptr(stream)), "lbm_pair_weights")
+
+
+def gnn_train_step_weighted(f_in, f_target, s, tau, taus, lat_weights, params, packed, adam_m,
+                            adam_v, step, lr, wd, loss, grads, workspace, ws_bytes=None,
+                            stream=None):
+    _, _, fe = _elems(s)
+    nt, f32 = gnn_trainable_count(), _f32()
+    check(load().gnn_train_step_weighted(
+        dptr(f_in, "f_in", f32, fe), dptr(f_target, "f_target", f32, fe), s, float(tau),
+        dptr(taus, "taus", f32, int(s.nb)), dptr(lat_weights, "lat_weights", f32, int(s.nb)),
+        dptr(params, "params", f32, gnn_param_count()),
+        dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
+        dptr(adam_m, "adam_m", f32, nt), dptr(adam_v, "adam_v", f32, nt), int(step), float(lr),
+        float(wd), dptr(loss, "loss", _f64(), 1), dptr(grads, "grads", f32, nt),
+        dptr(workspace, "workspace"), int(nbytes(workspace) if ws_bytes is None else ws_bytes),
+        stream_ptr(stream)), "gnn_train_step_weighted")
 
 
 def gnn_train_step(f_in, f_target, s, tau, taus, params, packed, adam_m, adam_v, step, lr, wd,

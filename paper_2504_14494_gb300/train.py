@@ -86,9 +86,14 @@ class PairStream:
 
 
 class Trainer:
-    """AdamW training of the network on a PairStream (fused C ABI step)."""
+    """AdamW training of the network on a PairStream (fused C ABI step).
 
-    def __init__(self, device, theta=None, lr=1e-3, wd=1e-2, seed=0, **stream_kw):
+    weighting: "eq4" (the paper's loss) or "relative" (each training instance
+    weighted by mean(D) / D_b, D_b its one-step BGK residual: lbm_pair_weights
+    and gnn_train_step_weighted)."""
+
+    def __init__(self, device, theta=None, lr=1e-3, wd=1e-2, seed=0, weighting="eq4",
+                 **stream_kw):
         import torch
         self.data = PairStream(device, seed=seed, **stream_kw)
         theta = inputs.xavier_params(seed) if theta is None else theta
@@ -102,10 +107,24 @@ class Trainer:
                               device=device)
         self.lr, self.wd = lr, wd
         self.step_count = 0
+        if weighting not in ("eq4", "relative"):
+            raise ValueError(f"unknown weighting {weighting!r}")
+        self.weighting = weighting
+        if weighting == "relative":
+            nb = self.data.coarse.nb
+            self.lat_w = torch.ones(nb, device=device)
+            self.pw_ws = torch.empty(L.lbm_pair_weights_workspace_bytes(self.data.coarse),
+                                     dtype=torch.uint8, device=device)
 
     def step(self):
         f_in, f_tg, tau_c = self.data.next()
         self.step_count += 1
+        if self.weighting == "relative":
+            L.lbm_pair_weights(f_in, f_tg, self.data.coarse, 1.0, tau_c, self.lat_w, self.pw_ws)
+            L.gnn_train_step_weighted(f_in, f_tg, self.data.coarse, 1.0, tau_c, self.lat_w,
+                                      self.params, self.packed, self.m, self.v, self.step_count,
+                                      self.lr, self.wd, self.loss, None, self.ws)
+            return
         L.gnn_train_step(f_in, f_tg, self.data.coarse, 1.0, tau_c, self.params, self.packed,
                          self.m, self.v, self.step_count, self.lr, self.wd, self.loss, None,
                          self.ws)

@@ -250,6 +250,68 @@ def test_train_step_matches_oracle_and_descends(lbmlib, cuda):
     assert losses[-1] < 0.5 * losses[0]
 
 
+def test_pair_weights_and_weighted_train_step_match_oracle(lbmlib, cuda):
+    """Per-instance loss weights (lbm_pair_weights: mean(D) / D_b with D_b
+    the mean squared one-step BGK residual, FP32 arithmetic per node, FP64
+    sums) within 1e-3 relative of the oracle's, and one weighted training
+    step: loss within 1e-2 relative and gradient cosine >= 0.999 against the
+    oracle's Eq. 3 + weighted Eq. 4 + backward; with all weights 1 the
+    weighted step is the plain gnn_train_step bit for bit."""
+    import torch
+    L = lbmlib
+    nb, n = 3, 16
+    taus = [0.6, 0.75, 1.05]
+    theta = inputs.xavier_params(8, s_df=1e-4)
+    pairs = [train.tgv_pair(n, 0.05, km, t, 2, 4) for km, t in zip((1, 2, 1), taus)]
+    f_in = np.stack([pp[0] for pp in pairs], axis=1).astype(np.float32)
+    f_tg = np.stack([pp[1] for pp in pairs], axis=1).astype(np.float32)
+    s = L.shape(n, n, nb)
+    din, _ = to_dev(f_in, cuda)
+    dtg, _ = to_dev(f_tg, cuda)
+    td = torch.tensor(taus, dtype=torch.float32, device=cuda)
+    w = torch.zeros(nb, device=cuda)
+    pws = torch.empty(L.lbm_pair_weights_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    L.lbm_pair_weights(din, dtg, s, 1.0, td, w, pws)
+    assert L.lbm_get_status() == 0
+    d_ref, w_ref = train.pair_weights([f_in[:, b].astype(np.float64) for b in range(nb)],
+                                      [f_tg[:, b].astype(np.float64) for b in range(nb)], taus)
+    wg = w.cpu().numpy().astype(np.float64)
+    print("weights", wg, w_ref, "residuals", d_ref)
+    assert np.allclose(wg, w_ref, rtol=1e-3, atol=0)
+
+    def step(weighted, wt):
+        p, pk = _dev_params(L, theta, cuda)
+        m = torch.zeros(L.gnn_trainable_count(), device=cuda)
+        v = torch.zeros_like(m)
+        loss = torch.zeros(1, dtype=torch.float64, device=cuda)
+        grads = torch.zeros_like(m)
+        ws = torch.empty(L.gnn_train_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+        if weighted:
+            L.gnn_train_step_weighted(din, dtg, s, 1.0, td, wt, p, pk, m, v, 1, 1e-3, 0.0, loss,
+                                      grads, ws)
+        else:
+            L.gnn_train_step(din, dtg, s, 1.0, td, p, pk, m, v, 1, 1e-3, 0.0, loss, grads, ws)
+        assert L.lbm_get_status() == 0
+        return loss.item(), grads.cpu().numpy().astype(np.float64), p
+
+    lw, gw, _ = step(True, w)
+    pr = gnn.unpack(theta)
+    l_ref, g_ref = 0.0, np.zeros(gnn.N_TRAINABLE)
+    for b in range(nb):
+        fpre = lbm.stream_pull(f_in[:, b].astype(np.float64))
+        y, cache = gnn.forward(fpre, pr)
+        lb, dyb, _ = gnn.collide_loss(fpre, y, taus[b], f_tg[:, b].astype(np.float64), pr,
+                                      node_weight=np.full(n * n, wg[b]))
+        l_ref += lb / nb
+        g, _ = gnn.backward(dyb / nb, cache, pr)
+        g_ref += gnn.pack_grads(g)
+    assert abs(lw - l_ref) <= 1e-2 * l_ref, (lw, l_ref)
+    assert _cos(gw, g_ref) >= 0.999, _cos(gw, g_ref)
+    l1, g1, p1 = step(True, torch.ones(nb, device=cuda))
+    l0, g0, p0 = step(False, None)
+    assert l1 == l0 and np.array_equal(g1, g0) and torch.equal(p1, p0)
+
+
 @pytest.mark.parametrize("variant", [1, 2, 4])
 def test_variant_backward_and_loss_match_oracle(lbmlib, cuda, variant):
     """Gradients of the Eq. 3 + Eq. 4 loss through the network for the

@@ -200,6 +200,57 @@ def test_collide_loss_reduces_to_mse_of_eq3():
     assert abs(loss - np.mean((lbm.bgk_collide(f, 0.8) - target) ** 2)) < 1e-18
 
 
+def test_weighted_collide_loss_gradient_and_special_cases():
+    """Per-node weights in Eq. 4 (the weighted training step): the gradient
+    matches central differences; all weights 1 give the plain loss; a weight
+    w on one lattice scales exactly that lattice's share."""
+    nx, ny = 4, 3
+    p = gnn.unpack(_params(17, s_df=1e-3))
+    f = _state(nx, ny, 21)
+    target = _state(nx, ny, 22)
+    rng = np.random.default_rng(7)
+    y = rng.standard_normal((nx * ny, 10))
+    w = 0.5 + rng.random(nx * ny)
+    loss, dy, _ = gnn.collide_loss(f, y, 0.7, target, p, node_weight=w)
+    h = 1e-6
+    for _ in range(20):
+        n, c = int(rng.integers(nx * ny)), int(rng.integers(10))
+        yp, ym = y.copy(), y.copy()
+        yp[n, c] += h
+        ym[n, c] -= h
+        fd = (gnn.collide_loss(f, yp, 0.7, target, p, node_weight=w)[0]
+              - gnn.collide_loss(f, ym, 0.7, target, p, node_weight=w)[0]) / (2 * h)
+        assert abs(fd - dy[n, c]) <= 1e-6 * abs(dy[n, c]) + 1e-14, (n, c, fd, dy[n, c])
+    one = gnn.collide_loss(f, y, 0.7, target, p, node_weight=np.ones(nx * ny))
+    plain = gnn.collide_loss(f, y, 0.7, target, p)
+    assert one[0] == plain[0] and np.array_equal(one[1], plain[1])
+    _, _, f_pred = plain
+    r2 = ((f_pred - target.reshape(9, -1)) ** 2).sum(axis=0)
+    w3 = np.ones(nx * ny)
+    w3[:nx] = 3.0                     # the first row of nodes
+    l3 = gnn.collide_loss(f, y, 0.7, target, p, node_weight=w3)[0]
+    assert abs(l3 - (plain[0] + 2.0 * r2[:nx].sum() / (9 * nx * ny))) <= 1e-15
+
+
+def test_pair_weights_definition():
+    """D_b is the mean squared one-step BGK residual of instance b; w_b =
+    mean(D) / D_b (the zero network's weighted loss then equals the plain
+    one); the cap applies to an instance whose residual vanishes."""
+    from oracle import train
+    rng = np.random.default_rng(9)
+    f_in = [_state(5, 4, 30 + b) for b in range(3)]
+    taus = [0.6, 0.8, 1.1]
+    tg = [lbm.bgk_step(a, t) + 1e-4 * (b + 1) * rng.standard_normal(a.shape)
+          for b, (a, t) in enumerate(zip(f_in, taus))]
+    tg[2] = lbm.bgk_step(f_in[2], taus[2])  # no residual at all
+    d, w = train.pair_weights(f_in, tg, taus)
+    for b in range(3):
+        assert abs(d[b] - np.mean((lbm.bgk_step(f_in[b], taus[b]) - tg[b]) ** 2)) <= 1e-24
+    assert d[2] == 0.0 and w[2] == 1.0e4
+    assert np.allclose(w[:2], d.mean() / d[:2], rtol=1e-14)
+    assert abs(np.mean(w[:2] * d[:2]) - d.mean()) <= 1e-15 * d.mean() * 10
+
+
 # --- variants: conservative correction (2) and the MLP-only network of Fig. 2 (1) ---
 def test_conservative_projection_invariants():
     """The projection removes exactly the mass and momentum of Delta f: it is
