@@ -71,6 +71,25 @@ def channel_step(fpost, tau, gx):
     return f - (f - feq) / tau + guo_source(ux, uy, tau, gx)
 
 
+def gnn_channel_step(fpost, theta, tau, gx):
+    """One GNN-LBM step of the channel (Sec. 3.1 with the collision of Eq. 3;
+    readings: the network runs on the channel's graph - periodic in x, no
+    neighbour across a wall, whose messages are left out of the sum - with
+    the force-corrected velocity among its features, and Guo's source uses
+    the network's relaxation time tau tau_adj):
+      f* = f - (f - f^eq)/(tau tau_adj) + S(tau tau_adj) + Delta f."""
+    from . import gnn
+    p = gnn.unpack(theta)
+    f = stream_pull_walls(np.asarray(fpost, np.float64))
+    q, ny, nx = f.shape
+    y, _ = gnn.forward(f, p, walls=True, force_x=gx)
+    tau_adj, df = gnn.heads(y, p)
+    teff = (tau * tau_adj).reshape(ny, nx)
+    rho, ux, uy = moments_forced(f, gx)
+    feq = lbm.equilibrium(rho, ux, uy)
+    return f - (f - feq) / teff + guo_source(ux, uy, teff, gx) + df.reshape(q, ny, nx)
+
+
 def channel_run(fpost, tau, gx, nsteps):
     f = np.asarray(fpost, np.float64)
     for _ in range(nsteps):

@@ -145,33 +145,49 @@ def neighbours(nx, ny):
 
 
 # --- forward ---------------------------------------------------------------------
-def features(f_pre, p):
+def inside_mask(nx, ny):
+    """inside[n, k]: the neighbour x + e_k of node n lies inside a channel with
+    walls beyond the first and last rows (periodic in x only)."""
+    y = np.repeat(np.arange(ny), nx)
+    return np.stack([(y + lbm.E[k, 1] >= 0) & (y + lbm.E[k, 1] < ny) for k in range(lbm.Q)],
+                    axis=1)
+
+
+def features(f_pre, p, force_x=0.0):
     """Fig. 2 input: [f_0..f_8, rho, u_x, u_y] per node, then (x - mu)/sigma.
 
-    f_pre: (9, ny, nx) pre-collision populations.  Returns (N, 12) x_hat and
-    the raw (N, 12) feature matrix."""
+    f_pre: (9, ny, nx) pre-collision populations.  With a body force (the
+    channel of Sec. 3.1, Guo's scheme) u is the force-corrected velocity
+    (sum f e + F/2) / rho.  Returns (N, 12) x_hat and the raw (N, 12)
+    feature matrix."""
     rho, ux, uy = lbm.moments(f_pre)
+    ux = ux + 0.5 * force_x / rho
     q = f_pre.shape[0]
     raw = np.concatenate([np.asarray(f_pre, np.float64).reshape(q, -1).T,
                           rho.reshape(-1, 1), ux.reshape(-1, 1), uy.reshape(-1, 1)], axis=1)
     return (raw - p["mu"]) / p["sigma"], raw
 
 
-def forward(f_pre, p):
+def forward(f_pre, p, walls=False, force_x=0.0):
     """Network output y (N, 10) for pre-collision populations f_pre (9, ny, nx).
 
     The edge MLP is applied per edge to the full 130-wide concatenation
-    [h_i; h_j; e_k] (brute force, no algebraic split).  Returns (y, cache)."""
+    [h_i; h_j; e_k] (brute force, no algebraic split).  walls: the channel's
+    graph (periodic in x, no neighbour across the walls beyond the first and
+    last rows: such messages are left out of the sum); force_x: the body
+    force of the channel (forced velocity in the features).  Returns
+    (y, cache)."""
     _, ny, nx = f_pre.shape
     nbr = neighbours(nx, ny)
-    xh, raw = features(f_pre, p)
+    keep = inside_mask(nx, ny) if walls else np.ones((nx * ny, lbm.Q), bool)
+    xh, raw = features(f_pre, p, force_x)
     act = relu if p["variant"] & MLP_ONLY else gelu
     z1 = xh @ p["enc1.W"].T + p["enc1.b"]
     g1 = act(z1)
     z2 = g1 @ p["enc2.W"].T + p["enc2.b"]
     h = act(z2)
     cache = {"nbr": nbr, "xh": xh, "raw": raw, "z1": z1, "g1": g1, "z2": z2,
-             "h": [h], "edge_in": [], "ze": [], "a": [], "zn": []}
+             "h": [h], "edge_in": [], "ze": [], "a": [], "zn": [], "walls": walls}
     for r in range(0 if p["variant"] & MLP_ONLY else ROUNDS):
         We, be = p[f"r{r}.edge.W"], p[f"r{r}.edge.b"]
         Wn, bn = p[f"r{r}.node.W"], p[f"r{r}.node.b"]
@@ -181,7 +197,7 @@ def forward(f_pre, p):
             ek = np.broadcast_to(lbm.E[k].astype(np.float64), (h.shape[0], 2))
             inp = np.concatenate([h, h[nbr[:, k]], ek], axis=1)   # (N, 130)
             ze = inp @ We.T + be
-            a = a + gelu(ze)
+            a = a + gelu(ze) * keep[:, k:k + 1]
             ins.append(inp)
             zes.append(ze)
         zn = np.concatenate([h, a], axis=1) @ Wn.T + bn
@@ -263,7 +279,9 @@ def backward(dy, cache, p):
 
     Returns (grads, d_f_pre): grads maps every trainable name to dL/d(param)
     in FP64 (w.r.t. the effective, already rounded values); d_f_pre is
-    dL/d f_pre (9, N) through the features (f_i, rho, u)."""
+    dL/d f_pre (9, N) through the features (f_i, rho, u).  (Periodic graph,
+    no body force: the forward's defaults.)"""
+    assert not cache.get("walls"), "backward of the channel graph is not defined here"
     g = {}
     nbr = cache["nbr"]
     h = cache["h"][-1]

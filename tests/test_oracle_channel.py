@@ -62,3 +62,66 @@ def test_velocity_error_converges_at_second_order():
     for i in range(2):
         alpha = lbm.convergence_rate(errs[i], errs[i + 1], 1.0 / hs[i], 1.0 / hs[i + 1])
         assert abs(alpha - 2.0) < 0.01, (alpha, errs)
+
+
+def _net(seed, variant=0, s_df=1e-2):
+    from paper_2504_14494_gb300 import inputs
+    return inputs.xavier_params(seed, s_df=s_df, bias_scale=0.1, variant=variant)
+
+
+def test_gnn_channel_step_with_zero_network_is_the_bgk_channel_step():
+    """All trainable values zero: tau_adj = 1, Delta f = 0, so the GNN channel
+    step (Eq. 3 with Guo forcing) is the BGK channel step exactly."""
+    from paper_2504_14494_gb300 import inputs
+    f = _rest(6, 5) * (1 + 1e-2 * np.random.default_rng(1).standard_normal((9, 6, 5)))
+    a = channel.gnn_channel_step(f, inputs.zero_params(), 0.7, 2e-5)
+    b = channel.channel_step(f, 0.7, 2e-5)
+    assert np.allclose(a, b, rtol=1e-15, atol=1e-17)
+
+
+def test_gnn_channel_messages_stop_at_the_walls():
+    """Brute force on a 3 x 4 channel: a node's aggregated message sums GELU
+    of the edge MLP over the neighbours inside the channel only (periodic in
+    x); the first and last rows have 5 neighbours, the middle rows 8."""
+    from oracle import gnn
+    nx, ny = 3, 4
+    p = gnn.unpack(_net(3))
+    f = lbm.equilibrium(np.ones((ny, nx)), np.full((ny, nx), 0.02), np.zeros((ny, nx)))
+    f = f * (1 + 1e-2 * np.random.default_rng(4).standard_normal(f.shape))
+    _, cache = gnn.forward(f, p, walls=True, force_x=1e-4)
+    h0 = cache["h"][0]
+    We, be = p["r0.edge.W"], p["r0.edge.b"]
+    for y in range(ny):
+        for x in range(nx):
+            a, cnt = np.zeros(64), 0
+            for k in range(1, 9):
+                yy = y + lbm.E[k, 1]
+                if yy < 0 or yy >= ny:
+                    continue
+                j = yy * nx + (x + lbm.E[k, 0]) % nx
+                inp = np.concatenate([h0[y * nx + x], h0[j], lbm.E[k].astype(float)])
+                a += gnn.gelu(We @ inp + be)
+                cnt += 1
+            assert cnt == (5 if y in (0, ny - 1) else 8)
+            assert np.allclose(cache["a"][0][y * nx + x], a, rtol=1e-13, atol=1e-15)
+
+
+def test_gnn_channel_features_use_the_forced_velocity():
+    """The velocity feature is (sum f e + F/2) / rho."""
+    from oracle import gnn
+    p = gnn.unpack(_net(5))
+    f = _rest(4, 3) * (1 + 1e-2 * np.random.default_rng(6).standard_normal((9, 4, 3)))
+    _, raw = gnn.features(f, p, force_x=3e-3)
+    rho, ux, uy = channel.moments_forced(f, 3e-3)
+    assert np.allclose(raw[:, 10], ux.ravel(), rtol=1e-15, atol=0)
+    assert np.allclose(raw[:, 11], uy.ravel(), rtol=1e-15, atol=0)
+
+
+def test_gnn_channel_step_commutes_with_x_shifts():
+    """The channel is periodic in x: shifting the state in x commutes with
+    the GNN channel step."""
+    f = _rest(5, 6) * (1 + 1e-2 * np.random.default_rng(8).standard_normal((9, 5, 6)))
+    th = _net(7)
+    a = np.roll(channel.gnn_channel_step(f, th, 0.75, 1e-4), 2, axis=2)
+    b = channel.gnn_channel_step(np.roll(f, 2, axis=2), th, 0.75, 1e-4)
+    assert np.allclose(a, b, rtol=1e-13, atol=1e-16)
