@@ -267,6 +267,36 @@ LBM_API int lbm_step_gnn_mlp(const float* f_in, float* f_out, lbm_shape s, float
                              const float* taus, const void* packed, double* totals,
                              void* stream);
 
+/* Workspace bytes lbm_step_gnn_channel needs for shape s: the pre-collision
+ * populations (rounded up to 256 bytes) and 808 bytes per node (node states,
+ * edge terms and head output of the network); 0 for a bad shape. */
+LBM_API size_t gnn_channel_workspace_bytes(lbm_shape s);
+
+/* One GNN-LBM step of the channel flow of paper Sec. 3.1 (walls and body
+ * force as in lbm_step_channel) with the collision of Eq. 3.  The paper does
+ * not say how the network meets the walls; this library's reading: the
+ * message-passing graph is the channel's own (periodic in x; a node next to
+ * a wall has no neighbour beyond it, and that message is left out of the
+ * sum), the velocity feature is the force-corrected one (sum f e + F/2)/rho,
+ * and Guo's source is taken with the network's relaxation time:
+ *   f* = f - (f - f^eq)/(tau tau_adj) + (1 - 1/(2 tau tau_adj)) w_i
+ *        [3 (e_i - u) + 9 (e_i.u) e_i].F + Delta f,
+ * f the populations pulled with halfway bounce-back.  With a network whose
+ * heads give tau_adj = 1 and Delta f = 0 this is exactly lbm_step_channel.
+ *   f_in, f_out  device populations of shape s; f_out != f_in.
+ *   tau / taus   as in lbm_step_bgk; force_x finite.
+ *   packed       device image from gnn_pack (any variant).
+ *   totals       optional device double[5], of f_out.
+ *   workspace    device scratch of ws_bytes >= gnn_channel_workspace_bytes(s),
+ *                256-byte aligned; contents undefined afterwards.
+ * Errors: LBM_ERR_ARG (null pointer, non-finite force, misaligned image),
+ * LBM_ERR_SIZE, LBM_ERR_TAU, LBM_ERR_WORKSPACE, LBM_ERR_ALIAS; an invalid
+ * image writes nothing and raises LBM_ERR_BLOB in the status word. */
+LBM_API int lbm_step_gnn_channel(const float* f_in, float* f_out, lbm_shape s, float tau,
+                                 const float* taus, float force_x, const void* packed,
+                                 double* totals, void* workspace, size_t ws_bytes,
+                                 void* stream);
+
 /* Bytes of the activations gnn_forward saves for gnn_backward
  * (1,152 bytes per node), in this order: BF16 h0, h1, h2 [N][64] (node
  * states after the encoder and each round), BF16 a0, a1 [N][64] (aggregated

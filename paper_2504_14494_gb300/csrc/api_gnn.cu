@@ -187,6 +187,53 @@ int lbm_step_gnn_mlp(const float* f_in, float* f_out, lbm_shape shape, float tau
   return LBM_OK;
 }
 
+// lbm_step_gnn_channel scratch: f_pre (rounded up to 256 bytes), then per
+// node BF16 h0 [64], FP16 AB0 [128], BF16 h1 [64], FP16 AB1 [128], FP32 y [10].
+static int64_t channel_ws_bytes(const Shape& s) {
+  return ((f_bytes(s) + 255) / 256) * 256 + nodes(s) * (128 + 256 + 128 + 256 + 40);
+}
+
+size_t gnn_channel_workspace_bytes(lbm_shape shape) {
+  Shape s;
+  if (check_shape_g(shape, &s)) return 0;
+  return (size_t)channel_ws_bytes(s);
+}
+
+int lbm_step_gnn_channel(const float* f_in, float* f_out, lbm_shape shape, float tau,
+                         const float* taus, float force_x, const void* packed, double* totals,
+                         void* workspace, size_t ws_bytes, void* stream) {
+  LBM_TRACE("lbm_step_gnn_channel");
+  Shape s;
+  if (!f_in || !f_out || !packed || !std::isfinite(force_x)) return LBM_ERR_ARG;
+  if (int r = check_shape_g(shape, &s)) return r;
+  if (!taus && (!std::isfinite(tau) || !(tau > 0.5f))) return LBM_ERR_TAU;
+  if (!aligned(packed, 16)) return LBM_ERR_ARG;
+  const int64_t N = nodes(s), wsb = channel_ws_bytes(s);
+  if (!workspace || (int64_t)ws_bytes < wsb || !aligned(workspace, 256)) return LBM_ERR_WORKSPACE;
+  if (overlap(f_in, f_bytes(s), f_out, f_bytes(s))) return LBM_ERR_ALIAS;
+  if (overlap(workspace, wsb, f_in, f_bytes(s)) || overlap(workspace, wsb, f_out, f_bytes(s)))
+    return LBM_ERR_ALIAS;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint8_t* pk = static_cast<const uint8_t*>(packed);
+  char* w = static_cast<char*>(workspace);
+  float* f_pre = reinterpret_cast<float*>(w);
+  w += ((f_bytes(s) + 255) / 256) * 256;
+  auto* h0 = reinterpret_cast<__nv_bfloat16*>(w);
+  auto* ab0 = reinterpret_cast<__half*>(w + N * 128);
+  auto* h1 = reinterpret_cast<__nv_bfloat16*>(w + N * 384);
+  auto* ab1 = reinterpret_cast<__half*>(w + N * 512);
+  auto* y = reinterpret_cast<float*>(w + N * 768);
+  if (totals && cudaMemsetAsync(totals, 0, 5 * sizeof(double), st) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  if (launch_channel_pull(f_in, f_pre, s, st) != cudaSuccess) return LBM_ERR_CUDA;
+  if (launch_gnn_forward_channel(f_pre, s, force_x, pk, h0, ab0, h1, ab1, y, st) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  if (launch_channel_gnn_collide(f_pre, y, f_out, s, tau, taus, force_x, pk, totals, st) !=
+      cudaSuccess)
+    return LBM_ERR_CUDA;
+  return LBM_OK;
+}
+
 size_t gnn_saved_bytes(lbm_shape shape) {
   Shape s;
   if (check_shape_g(shape, &s)) return 0;

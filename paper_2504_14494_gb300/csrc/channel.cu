@@ -7,31 +7,23 @@
 //   f*_i = f_i - (f_i - f_i^eq)/tau + (1 - 1/(2 tau)) w_i [3 (e_i - u) + 9 (e_i.u) e_i].F
 // In pull form the bounce-back reads f_i(x, y) = f*_opp(i)(x, y) whenever
 // (x - e_ix, y - e_iy) lies outside the channel.
+//
+// The GNN-LBM step of the channel (Eq. 3 in place of the BGK relaxation)
+// runs as pull (channel_pull_kernel) -> network on the walled graph
+// (gnn_fwd.cu, GeoChannel) -> channel_gnn_collide_kernel, which relaxes with
+// the network's time tau tau_adj, adds Guo's source with that same time and
+// the correction Delta f.
 #include "common.cuh"
+#include "gnn.cuh"
 #include "launch.h"
 
 namespace lbmgnn {
 
-__device__ __forceinline__ constexpr int opp(int i) {
-  return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 5 + 2) % 4) + 5);
-}
-
-template <bool TOTALS>
-__global__ void __launch_bounds__(256) channel_step_kernel(const float* __restrict__ fin,
-                                                           float* __restrict__ fout, Shape s,
-                                                           float tau, const float* __restrict__ taus,
-                                                           float gx, double* __restrict__ totals,
-                                                           unsigned* stw) {
-  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
-  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool on = n < N;
-  const int64_t nn = on ? n : N - 1;
-  const int x = (int)(nn % s.nx);
-  const int64_t row = nn / s.nx;
-  const int b = (int)(row / s.ny);
-  const int y = (int)(row - (int64_t)b * s.ny);
-  const int64_t lat = (int64_t)b * s.ny * s.nx;
-  float f[Q];
+// Node n = (b, y, x): the nine populations pulled from the stored state with
+// the channel's walls.
+__device__ __forceinline__ void channel_pull(const float* __restrict__ fin, const Shape& s,
+                                             int64_t nn, int x, int y, int64_t lat,
+                                             float (&f)[Q], unsigned* stw) {
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int ys = y - ey(q);
@@ -44,7 +36,55 @@ __global__ void __launch_bounds__(256) channel_step_kernel(const float* __restri
                    checked(lat + (int64_t)ys * s.nx + xs, 0, (int64_t)s.nb * s.ny * s.nx, stw));
     }
   }
-  const float t = taus ? __ldg(taus + b) : tau;
+}
+
+// Block sums of the totals (mass, momentum, energy, non-finite count) of the
+// written populations, one atomic per quantity and block.
+__device__ __forceinline__ void channel_totals(const float (&f)[Q], bool on,
+                                               double* __restrict__ totals, unsigned* stw) {
+  double tt[5] = {0, 0, 0, 0, 0};
+  if (on) {
+    bool finite = true;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) finite &= isfinite(f[q]);
+    if (finite) {
+      double r = 0.0, px = 0.0, py = 0.0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        r += f[q];
+        if (ex(q)) px += ex(q) * (double)f[q];
+        if (ey(q)) py += ey(q) * (double)f[q];
+      }
+      tt[0] = r;
+      tt[1] = px;
+      tt[2] = py;
+      tt[3] = 0.5 * (px * px + py * py) / r;
+    } else {
+      tt[4] = 1.0;
+    }
+  }
+  if (tt[4] != 0.0) raise_status(stw, ST_NONFINITE);
+  __shared__ double red[8][5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tt[k] += __shfl_xor_sync(0xffffffffu, tt[k], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) red[threadIdx.x >> 5][k] = tt[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double acc = 0.0;
+    for (int i = 0; i < 8; ++i) acc += red[i][threadIdx.x];
+    if (acc != 0.0) atomicAdd(totals + threadIdx.x, acc);
+  }
+}
+
+// f_i - (f_i - f_i^eq(rho, u))/t + (1 - 1/(2t)) w_i [3 (e_i - u) + 9 (e_i.u) e_i].(gx, 0)
+// with u the force-corrected velocity; t is tau (BGK) or tau tau_adj (Eq. 3).
+__device__ __forceinline__ void channel_relax(float (&f)[Q], float t, float gx) {
   const float rho = ((f[0] + (f[1] + f[3])) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8]));
   const float jx = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
   const float jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
@@ -58,50 +98,42 @@ __global__ void __launch_bounds__(256) channel_step_kernel(const float* __restri
     const float src = pre * wq(q) * (3.0f * (float(ex(q)) - m.ux) + 9.0f * eu * float(ex(q))) * gx;
     f[q] = f[q] - omega * (f[q] - feq_i(q, m, usq15)) + src;
   }
-  if (on) {
+}
+
+struct NodeIdx {
+  int64_t n, nn, lat;
+  int x, y, b;
+  bool on;
+};
+__device__ __forceinline__ NodeIdx node_idx(const Shape& s) {
+  NodeIdx r;
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  r.n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  r.on = r.n < N;
+  r.nn = r.on ? r.n : N - 1;
+  r.x = (int)(r.nn % s.nx);
+  const int64_t row = r.nn / s.nx;
+  r.b = (int)(row / s.ny);
+  r.y = (int)(row - (int64_t)r.b * s.ny);
+  r.lat = (int64_t)r.b * s.ny * s.nx;
+  return r;
+}
+
+template <bool TOTALS>
+__global__ void __launch_bounds__(256) channel_step_kernel(const float* __restrict__ fin,
+                                                           float* __restrict__ fout, Shape s,
+                                                           float tau, const float* __restrict__ taus,
+                                                           float gx, double* __restrict__ totals,
+                                                           unsigned* stw) {
+  const NodeIdx i = node_idx(s);
+  float f[Q];
+  channel_pull(fin, s, i.nn, i.x, i.y, i.lat, f, stw);
+  channel_relax(f, taus ? __ldg(taus + i.b) : tau, gx);
+  if (i.on) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) fout[q * s.ps + nn] = f[q];
+    for (int q = 0; q < Q; ++q) fout[q * s.ps + i.nn] = f[q];
   }
-  if constexpr (TOTALS) {
-    double tt[5] = {0, 0, 0, 0, 0};
-    if (on) {
-      bool finite = true;
-#pragma unroll
-      for (int q = 0; q < Q; ++q) finite &= isfinite(f[q]);
-      if (finite) {
-        double r = 0.0, px = 0.0, py = 0.0;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          r += f[q];
-          if (ex(q)) px += ex(q) * (double)f[q];
-          if (ey(q)) py += ey(q) * (double)f[q];
-        }
-        tt[0] = r;
-        tt[1] = px;
-        tt[2] = py;
-        tt[3] = 0.5 * (px * px + py * py) / r;
-      } else {
-        tt[4] = 1.0;
-      }
-    }
-    if (tt[4] != 0.0) raise_status(stw, ST_NONFINITE);
-    __shared__ double red[8][5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) tt[k] += __shfl_xor_sync(0xffffffffu, tt[k], o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-      for (int k = 0; k < 5; ++k) red[threadIdx.x >> 5][k] = tt[k];
-    }
-    __syncthreads();
-    if (threadIdx.x < 5) {
-      double acc = 0.0;
-      for (int i = 0; i < 8; ++i) acc += red[i][threadIdx.x];
-      if (acc != 0.0) atomicAdd(totals + threadIdx.x, acc);
-    }
-  }
+  if constexpr (TOTALS) channel_totals(f, i.on, totals, stw);
 }
 
 cudaError_t launch_channel_step(const float* fin, float* fout, const Shape& s, float tau,
@@ -114,6 +146,77 @@ cudaError_t launch_channel_step(const float* fin, float* fout, const Shape& s, f
     channel_step_kernel<true><<<blocks, 256, 0, st>>>(fin, fout, s, tau, taus, gx, totals, stw);
   else
     channel_step_kernel<false><<<blocks, 256, 0, st>>>(fin, fout, s, tau, taus, gx, totals, stw);
+  return cudaGetLastError();
+}
+
+// ---- GNN-LBM step of the channel ------------------------------------------------
+
+// f_pre = stream(f_post) with the walls: the network's input (Fig. 2) and the
+// populations that Eq. 3 relaxes.
+__global__ void __launch_bounds__(256) channel_pull_kernel(const float* __restrict__ fin,
+                                                           float* __restrict__ fpre, Shape s,
+                                                           unsigned* stw) {
+  const NodeIdx i = node_idx(s);
+  float f[Q];
+  channel_pull(fin, s, i.nn, i.x, i.y, i.lat, f, stw);
+  if (i.on) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) fpre[q * s.ps + i.nn] = f[q];
+  }
+}
+
+// Eq. 3 with Guo's source: f* = f - (f - f^eq)/(tau tau_adj) + S(tau tau_adj)
+// + Delta f, from the head output y [10][N] (tau_adj and Delta f as in the
+// periodic step: fixed-tau and conserving variants read from the image).
+template <bool TOTALS>
+__global__ void __launch_bounds__(256) channel_gnn_collide_kernel(
+    const float* __restrict__ fpre, const float* __restrict__ y, float* __restrict__ fout,
+    Shape s, float tau, const float* __restrict__ taus, float gx,
+    const uint8_t* __restrict__ packed, double* __restrict__ totals, unsigned* stw) {
+  if (!blob_ok(packed, stw)) return;
+  const NodeIdx i = node_idx(s);
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const float* nrm = reinterpret_cast<const float*>(packed + K::NORM);
+  const float sdf = __ldg(nrm + 24);
+  const int variant = variant_of(nrm);
+  float f[Q], d[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) f[q] = __ldg(fpre + q * s.ps + i.nn);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) d[q] = sdf * __ldg(y + (int64_t)(1 + q) * N + i.nn);
+  if (variant & VAR_CONSERVATIVE) conserve9(d);
+  const float t = (taus ? __ldg(taus + i.b) : tau) * tau_adj_of(__ldg(y + i.nn), variant);
+  channel_relax(f, t, gx);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) f[q] += d[q];
+  if (i.on) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) fout[q * s.ps + i.nn] = f[q];
+  }
+  if constexpr (TOTALS) channel_totals(f, i.on, totals, stw);
+}
+
+cudaError_t launch_channel_pull(const float* fin, float* fpre, const Shape& s, cudaStream_t st) {
+  unsigned* stw = status_word();
+  if (!stw) return cudaErrorInvalidDevice;
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  channel_pull_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(fin, fpre, s, stw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_channel_gnn_collide(const float* fpre, const float* y, float* fout,
+                                       const Shape& s, float tau, const float* taus, float gx,
+                                       const uint8_t* packed, double* totals, cudaStream_t st) {
+  unsigned* stw = status_word();
+  if (!stw) return cudaErrorInvalidDevice;
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const unsigned blocks = (unsigned)((N + 255) / 256);
+  if (totals)
+    channel_gnn_collide_kernel<true>
+        <<<blocks, 256, 0, st>>>(fpre, y, fout, s, tau, taus, gx, packed, totals, stw);
+  else
+    channel_gnn_collide_kernel<false>
+        <<<blocks, 256, 0, st>>>(fpre, y, fout, s, tau, taus, gx, packed, totals, stw);
   return cudaGetLastError();
 }
 

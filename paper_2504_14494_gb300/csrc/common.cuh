@@ -26,6 +26,10 @@ __host__ __device__ constexpr int ey(int i) {
 __host__ __device__ constexpr float wq(int i) {
   return i == 0 ? 4.0f / 9.0f : (i <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
 }
+// the direction opposite to e_i
+__host__ __device__ constexpr int opp(int i) {
+  return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 5 + 2) % 4) + 5);
+}
 
 // Device status word: bit flags raised by kernels, read (and cleared) by
 // lbm_get_status().  One per device that loaded the library; kernels receive

@@ -488,6 +488,7 @@ __device__ __forceinline__ int64_t geo_nbr(const GeoPos& p, int dx, int dy) {
 }
 
 struct GeoStack {
+  static constexpr bool kWalls = false;  // periodic in x and y
   Shape s;
   FastDiv dnx, dny;  // for stacks of fewer than 2^31 nodes (`small`)
   bool small;
@@ -513,6 +514,21 @@ struct GeoStack {
   __device__ __forceinline__ const float* tau_ptr(const GeoPos& p, const float* taus) const {
     return taus ? taus + p.b : nullptr;
   }
+  __device__ __forceinline__ bool inside(const GeoPos&, int) const { return true; }
+  __device__ __forceinline__ float force_x() const { return 0.0f; }
+};
+
+// A stack of channels (Sec. 3.1): periodic in x, walls halfway beyond the
+// first and last rows of every lattice, a body force (force_x, 0).  The
+// network's graph stops at the walls: a neighbour x + e_k exists only if its
+// row lies inside the channel.
+struct GeoChannel : GeoStack {
+  static constexpr bool kWalls = true;
+  float fx;
+  __device__ __forceinline__ bool inside(const GeoPos& p, int dy) const {
+    return (unsigned)(p.y + dy) < (unsigned)p.ny;
+  }
+  __device__ __forceinline__ float force_x() const { return fx; }
 };
 
 // One lattice of a batched run: first node in the packed buffers, size and
@@ -534,6 +550,7 @@ struct LatDesc {
 };
 
 struct GeoTable {
+  static constexpr bool kWalls = false;
   const LatDesc* lat;  // device table, sorted by offset
   int first, n;        // lattices first .. first+n-1 form this range
   int64_t base_, cnt, ps_;
@@ -567,6 +584,8 @@ struct GeoTable {
   __device__ __forceinline__ const float* tau_ptr(const GeoPos& p, const float*) const {
     return &lat[p.b].tau;
   }
+  __device__ __forceinline__ bool inside(const GeoPos&, int) const { return true; }
+  __device__ __forceinline__ float force_x() const { return 0.0f; }
 };
 
 // Copies `bytes` (multiple of 16) from global to shared memory with all threads.

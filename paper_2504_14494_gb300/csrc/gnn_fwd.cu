@@ -190,7 +190,9 @@ __global__ void __launch_bounds__(256, (enc_ctas<PULL, BONLY, Geo>())) gnn_encod
 #pragma unroll
       for (int q = 0; q < Q; ++q) xh[q] = (fv[q] - nrm[q]) * nrm[NFEAT + q];
       xh[9] = (m.rho - nrm[9]) * nrm[NFEAT + 9];
-      xh[10] = (m.ux - nrm[10]) * nrm[NFEAT + 10];
+      // channel: the force-corrected velocity (sum f e + F/2) / rho
+      const float ux = Geo::kWalls ? m.ux + 0.5f * geo.force_x() / m.rho : m.ux;
+      xh[10] = (ux - nrm[10]) * nrm[NFEAT + 10];
       xh[11] = (m.uy - nrm[11]) * nrm[NFEAT + 11];
       xh[12] = xh[13] = xh[14] = xh[15] = 0.0f;
       // half 0 writes x_hi (k 0..15), half 1 writes x_lo = x - x_hi (k 16..31)
@@ -431,11 +433,17 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
           const __half2* c_k = ckh + (g + k) * (HID / 2) + c0 / 2;
           const __half2 c0h = __float2half2_rn(0.7978845608028654f);
           const __half2 c1h = __float2half2_rn(0.0356774081363001f);
+          // channel: no message from a neighbour beyond a wall (its address
+          // wrapped to a row inside, so the load stays in range)
+          const __half2 keep = __float2half2_rn(geo.inside(p, ey(g + k + 1)) ? 1.0f : 0.0f);
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             const __half2 z = __hadd2(__hadd2(u32_as_h2(aw[c]), c_k[c]), u32_as_h2(bw[c]));
             const __half2 u = __hmul2(z, __hfma2(c1h, __hmul2(z, z), c0h));
-            acc[c] = __hadd2(acc[c], __hfma2(z, tanh_h2(u), z));
+            if constexpr (Geo::kWalls)
+              acc[c] = __hadd2(acc[c], __hmul2(keep, __hfma2(z, tanh_h2(u), z)));
+            else
+              acc[c] = __hadd2(acc[c], __hfma2(z, tanh_h2(u), z));
           }
         }
       }
@@ -626,6 +634,33 @@ cudaError_t launch_gnn_encode(const float* f, bool pull, bool b_only, const Shap
 cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
                              const uint8_t* packed, cudaStream_t st) {
   return round_any(mode, rl, make_geo_stack(s), (int64_t)s.nb * s.ny * s.nx, packed, st);
+}
+
+// The network forward of the channel (GeoChannel: graph stopped at the
+// walls, forced velocity among the features) on pre-collision populations:
+// encoder -> h0, A|B of round 0; inner round -> h1, A|B of round 1; last
+// round -> the head output y [10][N].  No activation is saved for training.
+cudaError_t launch_gnn_forward_channel(const float* f_pre, const Shape& s, float force_x,
+                                       const uint8_t* packed, __nv_bfloat16* h0, __half* ab0,
+                                       __nv_bfloat16* h1, __half* ab1, float* y,
+                                       cudaStream_t st) {
+  unsigned* stw = status_word();
+  if (!stw) return cudaErrorInvalidDevice;
+  GeoChannel geo;
+  static_cast<GeoStack&>(geo) = make_geo_stack(s);
+  geo.fx = force_x;
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  cudaError_t e;
+  if ((e = encode_t<false, false>(f_pre, geo, N, 2, enc::BYTES + 1024, packed, h0, ab0, stw,
+                                  st)) != cudaSuccess)
+    return e;
+  const int64_t cta_tiles =
+      (N + (int64_t)TILE * LBM_ROUND_GROUPS - 1) / ((int64_t)TILE * LBM_ROUND_GROUPS);
+  const unsigned grid = grid_for(cta_tiles * TILE, LBM_ROUND_CTAS);
+  RoundArgs r0{h0, ab0, h1, nullptr, ab1, nullptr, nullptr, nullptr, 1.0f, nullptr, 0, nullptr};
+  if ((e = round_t<0, false>(r0, geo, grid, packed, stw, st)) != cudaSuccess) return e;
+  RoundArgs r1{h1, ab1, nullptr, nullptr, nullptr, y, nullptr, nullptr, 1.0f, nullptr, 1, nullptr};
+  return round_t<2, false>(r1, geo, grid, packed, stw, st);
 }
 
 cudaError_t launch_gnn_step_table(const float* f_in, float* f_out, const LatDesc* lat, int first,

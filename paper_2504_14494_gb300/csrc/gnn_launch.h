@@ -35,6 +35,20 @@ cudaError_t launch_gnn_encode(const float* f, bool pull, bool b_only, const Shap
 cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
                              const uint8_t* packed, cudaStream_t st);
 
+// Channel (walls beyond the first and last rows, force (force_x, 0)): the
+// network forward on pre-collision populations over the walled graph, no
+// activation saved: h0, h1 [N][64] BF16, ab0, ab1 [N][128] FP16, y [10][N].
+cudaError_t launch_gnn_forward_channel(const float* f_pre, const Shape& s, float force_x,
+                                       const uint8_t* packed, __nv_bfloat16* h0, __half* ab0,
+                                       __nv_bfloat16* h1, __half* ab1, float* y,
+                                       cudaStream_t st);
+// The channel's pull with bounce-back into f_pre, and Eq. 3 with Guo's
+// source (relaxation time tau tau_adj) from the head output y.
+cudaError_t launch_channel_pull(const float* fin, float* fpre, const Shape& s, cudaStream_t st);
+cudaError_t launch_channel_gnn_collide(const float* fpre, const float* y, float* fout,
+                                       const Shape& s, float tau, const float* taus, float gx,
+                                       const uint8_t* packed, double* totals, cudaStream_t st);
+
 // The paper's Fig. 2 network (MLP-only variant) as one fused GNN-LBM step
 // kernel (pull, features, 3 MMAs, heads, Eq. 3, store).  For any other
 // network the kernel writes nothing (and with require_mlp raises ST_BLOB).

@@ -94,6 +94,9 @@ _SIGS = {
     "lbm_step_gnn_noalloc": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP,
                                             _VP]),
     "lbm_step_gnn_mlp": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP, _VP]),
+    "gnn_channel_workspace_bytes": (ctypes.c_size_t, [lbm_shape]),
+    "lbm_step_gnn_channel": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP,
+                                            ctypes.c_float, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "lbm_pair_weights_workspace_bytes": (ctypes.c_size_t, [lbm_shape]),
     "lbm_pair_weights": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP, _VP, _VP,
                                         ctypes.c_size_t, _VP]),
@@ -368,6 +371,27 @@ def lbm_step_gnn_mlp(f_in, f_out, s, tau, taus, packed, totals, stream=None):
                                   dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
                                   dptr(totals, "totals", _f64(), 5), stream_ptr(stream)),
           "lbm_step_gnn_mlp")
+
+
+def gnn_channel_workspace_bytes(s):
+    return load().gnn_channel_workspace_bytes(s)
+
+
+def lbm_step_gnn_channel(f_in, f_out, s, tau, taus, force_x, packed, totals, workspace,
+                         ws_bytes=None, stream=None):
+    """GNN-LBM step of the channel (walls, Guo forcing, Eq. 3; see
+    include/lbmgnn.h)."""
+    if ws_bytes is None:
+        ws_bytes = nbytes(workspace)
+    _, _, fe = _elems(s)
+    f32 = _f32()
+    check(load().lbm_step_gnn_channel(dptr(f_in, "f_in", f32, fe), dptr(f_out, "f_out", f32, fe),
+                                      s, float(tau), dptr(taus, "taus", f32, int(s.nb)),
+                                      float(force_x),
+                                      dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
+                                      dptr(totals, "totals", _f64(), 5),
+                                      dptr(workspace, "workspace"), int(ws_bytes),
+                                      stream_ptr(stream)), "lbm_step_gnn_channel")
 
 
 def gnn_saved_bytes(s):

@@ -60,6 +60,18 @@ def test_host_argument_checks(lbmlib):
     assert so.lbm_init_tgv(None, s, 1.0, 0.01, 0.1, 0.1, 0, None) == -1
     assert so.lbm_init_tgv(1 << 20, s, -1.0, 0.01, 0.1, 0.1, 0, None) == -1
     assert so.lbm_moments(None, s, None, None, None, None, None) == -1
+    # GNN step of the channel: workspace size, force, tau, aliasing
+    need = L.gnn_channel_workspace_bytes(s)
+    assert need == ((9 * 64 * 4 + 255) // 256) * 256 + 808 * 64
+    assert L.gnn_channel_workspace_bytes(L.shape(0, 8)) == 0
+    a, b, pk, ws = 1 << 20, 1 << 24, 1 << 28, 1 << 32
+    assert so.lbm_step_gnn_channel(a, b, s, 0.8, None, 1e-3, pk, None, ws, need - 1, None) == -10
+    assert so.lbm_step_gnn_channel(a, b, s, 0.8, None, 1e-3, pk, None, ws + 16, need, None) == -10
+    assert so.lbm_step_gnn_channel(a, b, s, 0.8, None, float("nan"), pk, None, ws, need,
+                                   None) == -1
+    assert so.lbm_step_gnn_channel(a, b, s, 0.5, None, 1e-3, pk, None, ws, need, None) == -4
+    assert so.lbm_step_gnn_channel(a, a, s, 0.8, None, 1e-3, pk, None, ws, need, None) == -2
+    assert so.lbm_step_gnn_channel(a, b, s, 0.8, None, 1e-3, pk, None, a + 256, need, None) == -2
 
 
 def test_binding_raises_on_error(lbmlib):

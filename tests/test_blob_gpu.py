@@ -46,6 +46,11 @@ def test_unpacked_image_is_refused_by_every_kernel(lbmlib, cuda):
     L.lbm_step_gnn_noalloc(f, out, s, 0.8, None, zero, None)
     assert L.lbm_get_status() == L.LBM_ERR_BLOB
     assert bool((out == -7.0).all())
+    # channel step (walls, Guo forcing)
+    wc = torch.empty(L.gnn_channel_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    L.lbm_step_gnn_channel(f, out, s, 0.8, None, 1e-3, zero, None, wc)
+    assert L.lbm_get_status() == L.LBM_ERR_BLOB
+    assert bool((out == -7.0).all())
     # training forward, Eq. 3 + Eq. 4, backward, fused step
     saved = torch.empty(L.gnn_saved_bytes(s), dtype=torch.uint8, device=cuda)
     y = torch.full((10 * n,), -7.0, device=cuda)

@@ -1,0 +1,188 @@
+"""Parity of the GNN-LBM step of the channel (lbm_step_gnn_channel: walls,
+Guo forcing, Eq. 3) with the FP64 oracle's gnn_channel_step, through the C
+ABI.
+
+Stated tolerances (the network in BF16 with FP32 accumulation and FP16
+messages, as in the periodic step):
+  * the pulled populations (workspace head) equal the oracle's pull with
+    halfway bounce-back exactly (a copy);
+  * head output y over the walled graph: relative L2 <= 2e-2 per output
+    group; tau_adj max |difference| <= 2e-2;
+  * the post-collision state: relative L2 of (f* - f*_channel BGK) <= 3e-2,
+    and per population |f* - f*_oracle| <= 1e-6 |f*_oracle| + 5e-2 max
+    |f*_oracle - f*_channel BGK|;
+  * a network with tau_adj = 1 and Delta f = 0 (all trainable values zero)
+    reproduces lbm_step_channel to 2e-7 relative (the same FP32 arithmetic).
+The y and f_pre checks read the workspace in the layout the library uses
+internally (f_pre first, y in the last 40 bytes per node)."""
+import numpy as np
+import pytest
+
+from oracle import channel, gnn, lbm
+from paper_2504_14494_gb300 import inputs
+from gpu_util import from_dev, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _state(nb, ny, nx, seed, umax=0.1, amp=2e-2):
+    """Parabolic channel profile at equilibrium, perturbed per population."""
+    y = np.arange(ny)
+    u = np.repeat((umax * (y + 0.5) * (ny - 0.5 - y) / max(ny * ny / 4.0, 1.0))[:, None], nx, 1)
+    f = np.stack([lbm.equilibrium(np.ones((ny, nx)), u, np.zeros((ny, nx)))] * nb, axis=1)
+    return (f * inputs.perturbation(f.shape, seed, amp)).astype(np.float32)
+
+
+def _packed(L, theta, dev):
+    import torch
+    p = torch.from_numpy(np.asarray(theta, np.float32)).to(dev)
+    pk = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=dev)
+    L.gnn_pack(p, pk)
+    return pk
+
+
+def _run(L, cuda, f, theta, taus, gx, totals=False):
+    import torch
+    _, nb, ny, nx = f.shape
+    s = L.shape(nx, ny, nb)
+    din, _ = to_dev(f, cuda)
+    dout = torch.full_like(din, float("nan"))
+    ws = torch.empty(L.gnn_channel_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    tot = torch.zeros(5, dtype=torch.float64, device=cuda) if totals else None
+    L.lbm_step_gnn_channel(din, dout, s, 0.0, torch.from_numpy(taus).to(cuda), gx,
+                           _packed(L, theta, cuda), tot, ws)
+    assert L.lbm_get_status() == 0
+    N = nb * ny * nx
+    fb = ((9 * N * 4 + 255) // 256) * 256
+    f_pre = ws[:9 * N * 4].view(torch.float32).view(9, nb, ny, nx).cpu().numpy()
+    y = ws[fb + 768 * N:fb + 808 * N].view(torch.float32).view(10, N).cpu().numpy().T
+    return from_dev(dout, f.shape), f_pre.astype(np.float64), y.astype(np.float64), tot
+
+
+SHAPES = [(1, 8, 16), (2, 5, 9), (1, 1, 5), (1, 32, 130), (3, 3, 7)]
+
+
+@pytest.mark.parametrize("nb,ny,nx", SHAPES)
+def test_channel_gnn_step_matches_oracle(lbmlib, cuda, nb, ny, nx):
+    L = lbmlib
+    gx = 1e-3
+    theta = inputs.xavier_params(61 + nx, s_df=1e-2, bias_scale=0.1)
+    f = _state(nb, ny, nx, seed=3 * ny + nx)
+    taus = np.array([0.8, 0.65, 1.1][:nb], np.float32)
+    got, f_pre, y_g, tot = _run(L, cuda, f, theta, taus, gx, totals=True)
+    p = gnn.unpack(theta)
+    N1 = ny * nx
+    for b in range(nb):
+        fb = f[:, b].astype(np.float64)
+        pre = channel.stream_pull_walls(fb)
+        assert np.array_equal(f_pre[:, b], pre), b
+        y_o, _ = gnn.forward(pre, p, walls=True, force_x=gx)
+        yb = y_g[b * N1:(b + 1) * N1]
+        e0, e1 = rel_l2(yb[:, 0], y_o[:, 0]), rel_l2(yb[:, 1:], y_o[:, 1:])
+        assert e0 <= 2e-2 and e1 <= 2e-2, (b, e0, e1)
+        assert np.max(np.abs(gnn.sigmoid(yb[:, 0]) - gnn.sigmoid(y_o[:, 0]))) <= 2e-2
+        ref = channel.gnn_channel_step(fb, theta, float(taus[b]), gx)
+        bgk = channel.channel_step(fb, float(taus[b]), gx)
+        e_corr = rel_l2(got[:, b] - bgk, ref - bgk)
+        e_f = np.max(np.abs(got[:, b] - ref) - 1e-6 * np.abs(ref)) / np.max(np.abs(ref - bgk))
+        print(f"b {b}: y rel L2 {e0:.2e} {e1:.2e}; correction {e_corr:.2e}; max err {e_f:.2e}")
+        assert e_corr <= 3e-2 and e_f <= 5e-2, (b, e_corr, e_f)
+    t_ref = sum(lbm.totals(got[:, b]) for b in range(nb))
+    assert abs(tot[0].item() - t_ref[0]) <= 1e-12 * t_ref[0]
+
+
+def test_channel_gnn_graph_stops_at_walls(lbmlib, cuda):
+    """On a 5-row channel the walled graph and the periodic one give head
+    outputs 0.25 apart (relative L2); the kernel's y matches the walled one
+    within 2e-2 and is farther than 0.1 from the periodic one."""
+    L = lbmlib
+    nb, ny, nx, gx = 1, 5, 9, 1e-3
+    theta = inputs.xavier_params(70, s_df=1e-2, bias_scale=0.1)
+    f = _state(nb, ny, nx, seed=11)
+    _, f_pre, y_g, _ = _run(L, cuda, f, theta, np.array([0.8], np.float32), gx)
+    p = gnn.unpack(theta)
+    y_w, _ = gnn.forward(f_pre[:, 0], p, walls=True, force_x=gx)
+    y_p, _ = gnn.forward(f_pre[:, 0], p, walls=False, force_x=gx)
+    assert rel_l2(y_p, y_w) > 0.15
+    assert rel_l2(y_g, y_w) <= 2e-2
+    assert rel_l2(y_g, y_p) > 0.1
+
+
+def test_channel_gnn_force_feature(lbmlib, cuda):
+    """With a strong force (G = 2e-2) the force-corrected velocity feature
+    moves y well beyond the tolerance; the kernel follows the oracle with
+    the force in the features."""
+    L = lbmlib
+    nb, ny, nx, gx = 1, 8, 16, 2e-2
+    theta = inputs.xavier_params(72, s_df=1e-2, bias_scale=0.1)
+    f = _state(nb, ny, nx, seed=12)
+    _, f_pre, y_g, _ = _run(L, cuda, f, theta, np.array([0.9], np.float32), gx)
+    p = gnn.unpack(theta)
+    y_f, _ = gnn.forward(f_pre[:, 0], p, walls=True, force_x=gx)
+    y_0, _ = gnn.forward(f_pre[:, 0], p, walls=True, force_x=0.0)
+    assert rel_l2(y_0, y_f) > 0.06
+    assert rel_l2(y_g, y_f) <= 2e-2
+    assert rel_l2(y_g, y_0) > 0.04
+
+
+@pytest.mark.parametrize("variant", [1, 2, 4, 6])
+def test_channel_gnn_variants(lbmlib, cuda, variant):
+    """MLP-only, conserving and fixed-tau networks in the channel: same
+    tolerances; the conserving correction adds no mass (the step's mass
+    then equals the BGK channel step's to FP32 rounding)."""
+    L = lbmlib
+    nb, ny, nx, gx = 2, 6, 12, 1e-3
+    theta = inputs.xavier_params(80 + variant, s_df=1e-2, bias_scale=0.1, variant=variant)
+    f = _state(nb, ny, nx, seed=20 + variant)
+    taus = np.array([0.75, 0.95], np.float32)
+    got, _, _, _ = _run(L, cuda, f, theta, taus, gx)
+    for b in range(nb):
+        fb = f[:, b].astype(np.float64)
+        ref = channel.gnn_channel_step(fb, theta, float(taus[b]), gx)
+        bgk = channel.channel_step(fb, float(taus[b]), gx)
+        assert rel_l2(got[:, b] - bgk, ref - bgk) <= 3e-2, b
+        if variant & 2:  # relaxation, Guo's source and the correction add no mass
+            assert abs(got[:, b].sum() - bgk.sum()) <= 1e-6 * bgk.sum()
+
+
+def test_channel_gnn_zero_network_equals_channel_step(lbmlib, cuda):
+    import torch
+    L = lbmlib
+    nb, ny, nx, gx = 2, 7, 10, 1e-3
+    f = _state(nb, ny, nx, seed=5)
+    taus = torch.tensor([0.7, 1.2], dtype=torch.float32, device=cuda)
+    s = L.shape(nx, ny, nb)
+    din, _ = to_dev(f, cuda)
+    a, b = torch.zeros_like(din), torch.zeros_like(din)
+    ws = torch.empty(L.gnn_channel_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    L.lbm_step_gnn_channel(din, a, s, 0.0, taus, gx, _packed(L, inputs.zero_params(), cuda), None,
+                           ws)
+    L.lbm_step_channel(din, b, None, s, 0.0, taus, gx)
+    torch.cuda.synchronize()
+    assert L.lbm_get_status() == 0
+    assert torch.allclose(a, b, rtol=2e-7, atol=0)
+
+
+def test_channel_gnn_argument_errors(lbmlib, cuda):
+    import torch
+    L = lbmlib
+    s = L.shape(8, 4)
+    f = torch.zeros(9 * 32, device=cuda)
+    g = torch.zeros_like(f)
+    pk = _packed(L, inputs.zero_params(), cuda)
+    need = L.gnn_channel_workspace_bytes(s)
+    assert need == ((9 * 32 * 4 + 255) // 256) * 256 + 808 * 32
+    small = torch.empty(need - 16, dtype=torch.uint8, device=cuda)
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_step_gnn_channel(f, g, s, 0.8, None, 1e-3, pk, None, small)
+    assert ei.value.code == L.LBM_ERR_WORKSPACE
+    ws = torch.empty(need, dtype=torch.uint8, device=cuda)
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_step_gnn_channel(f, g, s, 0.8, None, float("inf"), pk, None, ws)
+    assert ei.value.code == L.LBM_ERR_ARG
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_step_gnn_channel(f, g, s, 0.5, None, 1e-3, pk, None, ws)
+    assert ei.value.code == L.LBM_ERR_TAU
+    with pytest.raises(L.LbmError) as ei:
+        L.lbm_step_gnn_channel(f, f, s, 0.8, None, 1e-3, pk, None, ws)
+    assert ei.value.code == L.LBM_ERR_ALIAS
