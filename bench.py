@@ -51,9 +51,9 @@ NCU_TRAFFIC = {
     #     --clock-control none -k regex:"gnn_(encode|round)_kernel" -s 3 -c 3
     #     python bench.py --only gnn --steps 20 --warmup 3   (one GNN-LBM step, 1024 x 1024:
     #     encoder + 2 rounds; key file gnn_fwd.cu)
-    "lbm_step_gnn": {"bytes_per_launch": (37826304 + 206351872) + (270360832 + 219446784)
-                     + (306558976 + 26833664), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
-                     "src_sha": "78ce5f8ea00048b46cf6cc60063fa32eb68fb5ea5b09379064de3b816ba13dd4"},
+    "lbm_step_gnn": {"bytes_per_launch": (37851136 + 206329344) + (270832128 + 219547392)
+                     + (306571520 + 26678016), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
+                     "src_sha": "51df8f91288bf957faef3afdf0bd590dbded1979ca06ae399842409c856de4b4"},
 }
 
 
@@ -170,6 +170,11 @@ def run_ours(args, rank, world, local_rank):
         from paper_2504_14494_gb300 import inputs
         theta = inputs.xavier_params(W.TGV_GNN_1024.weight_seed, variant=2)
         res = batch_bench(args, L, dev, torch.cuda.current_stream(), theta)
+        print(json.dumps(_finite({"case": res["workload"], **res})))
+        return None
+    if args.only == "channel":  # Poiseuille study, untrained conserving fixed-tau network
+        from paper_2504_14494_gb300 import inputs
+        res = channel_bench(L, dev, {"xavier_v6": inputs.xavier_params(0, variant=6, s_df=1e-4)})
         print(json.dumps(_finite({"case": res["workload"], **res})))
         return None
     if args.only == "train":
@@ -304,7 +309,9 @@ def run_ours(args, rank, world, local_rank):
                for sd, th in thetas["relative"].items()},
            "batch": batch_bench(args, L, dev, stream, thetas[2]),
            "stability": {str(v): stability_bench(L, dev, thetas[v]) for v in (0, 2, 4)},
-           "poiseuille": channel_bench(L, dev),
+           "poiseuille": channel_bench(L, dev, {
+               "tau_fixed_v4": thetas[4], "conserving_v2": thetas[2],
+               "eq3_relative_seed2": thetas["relative"][2]}),
            "mlp_fused": mlp_bench(args, L, dev, stream, theta=thetas[3])}
 
     if rank != 0:
@@ -893,39 +900,130 @@ def stability_bench(L, dev, theta, n=64, u0s=(0.1, 0.2, 0.3),
     return {"workload": f"tgv_{n}x{n}", "steps": steps, "chunk": chunk, "rows": out}
 
 
-def channel_bench(L, dev, h=32, nx=4, umax=0.05, res=(10.0, 50.0, 100.0, 200.0)):
-    """Poiseuille channel (paper Sec. 3.1, Table 1 analog): BGK with
-    halfway bounce-back walls and Guo forcing, H = 32, centre-line velocity
-    0.05, run to steady state (35 e-folding times of the slowest mode); the
-    maximum velocity error against Eq. 5 relative to the centre-line
-    velocity, and MLUPS of the run."""
+def _channel_profile_error(L, f, s, h, nx, g, nu, umax, dev):
+    """Maximum |u - u_Eq.5| over the channel's rows, relative to u_max, with
+    the forced velocity (sum f e + F/2)/rho of column 0."""
     import torch
-    s = L.shape(nx, h)
     n = nx * h
-    out = []
-    fa = torch.empty(9 * n, device=dev)
-    fb, fc = torch.empty_like(fa), torch.empty_like(fa)
     rho = torch.empty(n, device=dev)
     ux = torch.empty(n, device=dev)
-    for re in res:
-        nu = umax * h / re
-        tau = 0.5 + 3.0 * nu
-        g = 8.0 * nu * umax / (h * h)
-        steps = int(35 * h * h / (np.pi ** 2 * nu))
+    L.lbm_moments(f, s, rho, ux, None)
+    u = (ux.double() + 0.5 * g / rho.double()).view(h, nx)[:, 0].cpu().numpy()
+    y = np.arange(h) + 0.5
+    ua = g / (2 * nu) * y * (h - y)
+    return float(np.abs(u - ua).max() / umax) if np.all(np.isfinite(u)) else None
+
+
+def _channel_gnn_run(L, dev, s, fa, fb, tau, g, steps, packed, ws, chunk=100):
+    """`steps` GNN-LBM steps of the channel from fa, ping-pong between fa
+    and fb; `chunk` steps (even) replayed as one CUDA graph.  Returns the
+    buffer holding the final state."""
+    import torch
+
+    def step(a, b):
+        L.lbm_step_gnn_channel(a, b, s, tau, None, g, packed, None, ws)
+
+    cur, nxt = fa, fb
+    done = 0
+    while done < min(steps, 2):  # warm-up outside the capture
+        step(cur, nxt)
+        cur, nxt = nxt, cur
+        done += 1
+    torch.cuda.synchronize()
+    if steps - done >= chunk:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+            for _ in range(chunk // 2):
+                step(cur, nxt)
+                step(nxt, cur)
+        while steps - done >= chunk:
+            graph.replay()
+            done += chunk
+    while done < steps:
+        step(cur, nxt)
+        cur, nxt = nxt, cur
+        done += 1
+    torch.cuda.synchronize()
+    return cur
+
+
+def channel_bench(L, dev, thetas=None, h=32, nx=4, umax=0.05, res=(10.0, 50.0, 100.0, 200.0),
+                  sides=(8, 16, 32, 64), re_sides=10.0, tau_sides=0.6):
+    """Poiseuille channel (paper Sec. 3.1, Table 1 analog): halfway
+    bounce-back walls and Guo forcing, H = 32, centre-line velocity 0.05.
+    BGK runs from rest to steady state (35 e-folding times h^2/(pi^2 nu) of
+    the slowest mode); each network in `thetas` (GNN-LBM step of the channel,
+    lbm_step_gnn_channel) then runs from the BGK steady state for 7 more
+    e-folding times (its own steady state differs from BGK's by a small
+    offset, which decays at the same rate), with the error after 6 reported
+    as a convergence check.  Error: maximum |u - u_Eq.5| over the rows,
+    relative to the centre-line velocity.  Grid refinement: heights `sides`
+    at fixed tau_sides and Re = re_sides (u_max = Re nu / H: the diffusive
+    scaling, under which the wall slip of halfway bounce-back falls as
+    1/H^2)."""
+    import torch
+    thetas = thetas or {}
+    packs = {}
+    for name, th in thetas.items():
+        pk = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=dev)
+        L.gnn_pack(torch.from_numpy(np.asarray(th, np.float32)).to(dev), pk)
+        packs[name] = pk
+
+    def case(hh, re, tau=None):
+        s = L.shape(nx, hh)
+        n = nx * hh
+        if tau is None:
+            um = umax
+            nu = um * hh / re
+            tau = 0.5 + 3.0 * nu
+        else:
+            nu = (tau - 0.5) / 3.0
+            um = re * nu / hh
+        g = 8.0 * nu * um / (hh * hh)
+        efold = hh * hh / (np.pi ** 2 * nu)
+        steps = int(35 * efold)
+        fa = torch.empty(9 * n, device=dev)
+        fb, fc = torch.empty_like(fa), torch.empty_like(fa)
         L.lbm_init_tgv(fa, s, 1.0, 0.0, 0.0, 0.0, False)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         L.lbm_step_channel(fa, fb, fc, s, tau, None, g, steps)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        L.lbm_moments(fb, s, rho, ux, None)
-        u = (ux.double() + 0.5 * g / rho.double()).view(h, nx)[:, 0].cpu().numpy()
-        y = np.arange(h) + 0.5
-        ua = g / (2 * nu) * y * (h - y)
-        out.append({"re": re, "tau": round(tau, 5), "steps": steps,
-                    "max_velocity_error": float(np.abs(u - ua).max() / umax),
-                    "mlups": round(n * steps / dt / 1e6, 1)})
-    return {"workload": f"poiseuille_{nx}x{h}", "u_max": umax, "rows": out}
+        row = {"re": re, "h": hh, "tau": round(tau, 5), "u_max": round(um, 6), "steps": steps,
+               "max_velocity_error": _channel_profile_error(L, fb, s, hh, nx, g, nu, um, dev),
+               "mlups": round(n * steps / dt / 1e6, 1)}
+        if packs:
+            ws = torch.empty(L.gnn_channel_workspace_bytes(s), dtype=torch.uint8, device=dev)
+            gnn = {}
+            k6, k1 = int(6 * efold), int(efold)
+            for name, pk in packs.items():
+                fa.copy_(fb)
+                fin = _channel_gnn_run(L, dev, s, fa, fc, tau, g, k6, pk, ws)
+                e6 = _channel_profile_error(L, fin, s, hh, nx, g, nu, um, dev)
+                other = fc if fin is fa else fa
+                fin = _channel_gnn_run(L, dev, s, fin, other, tau, g, k1, pk, ws)
+                err = _channel_profile_error(L, fin, s, hh, nx, g, nu, um, dev)
+                L.lbm_get_status()  # clear a non-finite flag
+                base = row["max_velocity_error"]
+                gnn[name] = {"max_velocity_error": err, "after_6_efolds": e6,
+                             "improvement_pct": (None if err is None or not base
+                                                 else round(100 * (1 - err / base), 2))}
+            row["gnn_from_bgk_steady_state"] = {"steps": k6 + k1, "networks": gnn}
+        return row
+
+    t0 = time.perf_counter()
+    out = [case(h, re) for re in res]
+    grid = [case(hh, re_sides, tau_sides) for hh in sides]
+    for a, b in zip(grid, grid[1:]):
+        if a["max_velocity_error"] and b["max_velocity_error"]:
+            b["order_vs_previous"] = round(float(np.log2(a["max_velocity_error"]
+                                                         / b["max_velocity_error"])), 3)
+    return {"workload": f"poiseuille_{nx}x{h}", "u_max": umax,
+            "call": "lbm_step_channel (BGK); lbm_step_gnn_channel (GNN, CUDA-graph chunks)",
+            "networks": list(packs), "rows": out,
+            "grid_refinement": {"re": re_sides, "tau": tau_sides, "rows": grid},
+            "wall_s": round(time.perf_counter() - t0, 1)}
 
 
 def cpu_baseline(budget_s=12.0):
@@ -1026,7 +1124,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["bgk", "gnn", "train", "batch", "mlp"], default=None,
+    ap.add_argument("--only", choices=["bgk", "gnn", "train", "batch", "mlp", "channel"],
+                    default=None,
                     help="time one kernel family only (profiling runs)")
     ap.add_argument("--side", type=int, default=N_SIDE, help="lattice side for --only runs")
     ap.add_argument("--log", default=None,
