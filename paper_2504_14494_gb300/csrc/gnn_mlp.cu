@@ -41,14 +41,20 @@ namespace mlp {
 // activations live in tensor memory (columns 0..63: accumulator, 64..95:
 // the BF16 input of the next product).
 constexpr int STAGES = 3;
-constexpr int SLOTS = Q + 1;  // per node and stage: the 9 pulled populations and tau
+// Per stage and population q a run of RUN floats: position 4 + t - e_qx
+// holds the value node t of the tile pulls (so a tile whose 128 nodes lie in
+// one lattice row can fetch each population's source run [x0 - 4, x0 + 132)
+// as 34 aligned 16-byte chunks); then 128 slots of tau.
+constexpr int RUN = TILE + 8;
+constexpr int CHUNKS = RUN / 4;  // 16-byte chunks per population run
+constexpr int STAGE_FLOATS = Q * RUN + TILE;
 // B2X / BHX: SW128 blocks whose K columns 0 and 1 hold the layer-2 and head
 // biases as BF16 pairs hi + lo (~16 bits): one extra K step against a
 // constant A of ones adds the bias inside the MMA.  WH is the head as this
 // kernel uses it (32 output rows, see the prologue).
 constexpr int NG = LBM_MLP_GROUPS;
 constexpr uint32_t W1X = 0, W2 = 8192, WH = 16384, B2X = 20480, BHX = 28672, STG = 32768,
-                   STG_BYTES = SLOTS * TILE * 4,                   // 5120 per stage and group
+                   STG_BYTES = STAGE_FLOATS * 4,                   // 5408 per stage and group
                    NORM = STG + NG * STAGES * STG_BYTES,
                    SH = NORM + 128, BYTES = SH + NG * 16;
 // tensor memory: group g's accumulator D at 64 g (64 columns), its A
@@ -63,6 +69,10 @@ static_assert(TM_COLS == 512, "one allocation of the whole tensor memory (power 
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
@@ -128,7 +138,7 @@ template <class Geo>
 __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
     const float* __restrict__ f_in, float* __restrict__ f_out, Geo geo, float tau0,
     const float* __restrict__ taus, const uint8_t* __restrict__ packed, bool require_mlp,
-    unsigned* stw) {
+    bool rows, unsigned* stw) {
   if (!blob_ok(packed, stw)) return;
   const int variant = variant_of(reinterpret_cast<const float*>(packed + K::NORM));
   if (!(variant & VAR_MLP_ONLY)) {  // message-passing networks: the unfused kernels
@@ -142,33 +152,60 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
   // tensor-memory lanes 32 (t / 32)..; its own tile sequence, staging ring,
   // mbarrier, tensor-memory slice and named barrier
   const int grp = threadIdx.x >> 7, t = threadIdx.x & 127;
-  float* stg = reinterpret_cast<float*>(sm + mlp::STG) + grp * (mlp::STAGES * mlp::SLOTS * TILE);
+  float* stg = reinterpret_cast<float*>(sm + mlp::STG) + grp * (mlp::STAGES * mlp::STAGE_FLOATS);
   const int64_t N = geo.count();
   const int64_t base = geo.base(), ps = geo.ps();
   const int64_t ntiles = (N + TILE - 1) / TILE;
   const int64_t first = (int64_t)blockIdx.x * mlp::NG + grp,
                 stride = (int64_t)gridDim.x * mlp::NG;
 
-  // Node t of tile `tile` -> stage st (cp.async): its 9 populations pulled
-  // from x - e_q (periodic wrap inside its lattice) and its relaxation time.
+  // The pulled populations of tile `tile` -> stage st (cp.async), and each
+  // node's relaxation time.  rows (a stack whose rows are whole tiles,
+  // 16-byte aligned planes): per population q the run [x0 - 4, x0 + 132) of
+  // row y - e_qy in 16-byte chunks, wrapped at the row's ends, the chunks
+  // shared out over the group's threads; otherwise each node pulls its 9
+  // values from x - e_q (periodic wrap inside its lattice) with 4-byte copies.
   auto fetch = [&](int64_t tile, int st) {
     if (tile < ntiles) {
-      const int64_t m = tile * TILE + t;
-      const GeoPos p = geo.pos(base + (m < N ? m : N - 1));
-      const int xm = p.x == 0 ? p.nx - 1 : p.x - 1, xp = p.x == p.nx - 1 ? 0 : p.x + 1;
-      const int64_t r0 = p.lat + (int64_t)p.y * p.nx;
-      const int64_t rm = p.lat + (int64_t)(p.y == 0 ? p.ny - 1 : p.y - 1) * p.nx;
-      const int64_t rp = p.lat + (int64_t)(p.y == p.ny - 1 ? 0 : p.y + 1) * p.nx;
-      // source of q: (x, y) (x-1, y) (x, y-1) (x+1, y) (x, y+1) (x-1, y-1) (x+1, y-1)
-      // (x+1, y+1) (x-1, y+1)
-      const int64_t src[Q] = {r0 + p.x, r0 + xm, rm + p.x, r0 + xp, rp + p.x,
-                              rm + xm,  rm + xp, rp + xp,  rp + xm};
-      float* d = stg + st * (mlp::SLOTS * TILE) + t;
+      float* sg = stg + st * mlp::STAGE_FLOATS;
+      if (rows) {
+        const GeoPos p = geo.pos(base + tile * TILE);  // node t = (x0 + t, y)
+        if (t < 3 * mlp::CHUNKS) {  // thread t: chunk c of the 3 populations of row set rs
+          const int rs = t / mlp::CHUNKS, c = t - rs * mlp::CHUNKS;
+          const int dy = rs == 0 ? 0 : (rs == 1 ? -1 : 1);  // source row y + dy
+          const int ys = p.y + dy < 0 ? p.ny - 1 : (p.y + dy >= p.ny ? 0 : p.y + dy);
+          int xs = p.x - 4 + 4 * c;
+          xs += xs < 0 ? p.nx : 0;
+          xs -= xs >= p.nx ? p.nx : 0;
+          const int64_t src = checked(p.lat + (int64_t)ys * p.nx + xs, base, base + N, stw);
+          // row y: q = 0, 1, 3; row y - 1: q = 2, 5, 6; row y + 1: q = 4, 7, 8
+          const int q0 = rs == 0 ? 0 : (rs == 1 ? 2 : 4);
+          const int q1 = rs == 0 ? 1 : (rs == 1 ? 5 : 7);
+          const int q2 = rs == 0 ? 3 : (rs == 1 ? 6 : 8);
+          cp_async16(sg + q0 * mlp::RUN + 4 * c, f_in + q0 * ps + src);
+          cp_async16(sg + q1 * mlp::RUN + 4 * c, f_in + q1 * ps + src);
+          cp_async16(sg + q2 * mlp::RUN + 4 * c, f_in + q2 * ps + src);
+        }
+        const float* tp = geo.tau_ptr(p, taus);
+        if (tp) cp_async4(sg + Q * mlp::RUN + t, tp); else sg[Q * mlp::RUN + t] = tau0;
+      } else {
+        const int64_t m = tile * TILE + t;
+        const GeoPos p = geo.pos(base + (m < N ? m : N - 1));
+        const int xm = p.x == 0 ? p.nx - 1 : p.x - 1, xp = p.x == p.nx - 1 ? 0 : p.x + 1;
+        const int64_t r0 = p.lat + (int64_t)p.y * p.nx;
+        const int64_t rm = p.lat + (int64_t)(p.y == 0 ? p.ny - 1 : p.y - 1) * p.nx;
+        const int64_t rp = p.lat + (int64_t)(p.y == p.ny - 1 ? 0 : p.y + 1) * p.nx;
+        // source of q: (x, y) (x-1, y) (x, y-1) (x+1, y) (x, y+1) (x-1, y-1) (x+1, y-1)
+        // (x+1, y+1) (x-1, y+1)
+        const int64_t src[Q] = {r0 + p.x, r0 + xm, rm + p.x, r0 + xp, rp + p.x,
+                                rm + xm,  rm + xp, rp + xp,  rp + xm};
 #pragma unroll
-      for (int q = 0; q < Q; ++q)
-        cp_async4(d + q * TILE, f_in + q * ps + checked(src[q], base, base + N, stw));
-      const float* tp = geo.tau_ptr(p, taus);
-      if (tp) cp_async4(d + Q * TILE, tp); else d[Q * TILE] = tau0;
+        for (int q = 0; q < Q; ++q)
+          cp_async4(sg + q * mlp::RUN + 4 + t - ex(q),
+                    f_in + q * ps + checked(src[q], base, base + N, stw));
+        const float* tp = geo.tau_ptr(p, taus);
+        if (tp) cp_async4(sg + Q * mlp::RUN + t, tp); else sg[Q * mlp::RUN + t] = tau0;
+      }
     }
     cp_async_commit();  // (an empty group past the last tile keeps the counting uniform)
   };
@@ -302,13 +339,14 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
   for (int64_t tile = first; tile < ntiles; tile += stride) {
     fetch(tile + 2 * stride, s == 0 ? 2 : s - 1);  // the stage read two tiles ago
     cp_async_wait<2>();                             // this thread's copies of `tile`
+    if (rows) group_sync(grp, 128);                 // and the other threads' chunks
     const int64_t n = tile * TILE + t;
-    const float* sv = stg + s * (mlp::SLOTS * TILE) + t;  // read again by the collision
+    const float* sv = stg + s * mlp::STAGE_FLOATS + 4 + t;  // read again by the collision
     s = s == 2 ? 0 : s + 1;
     {  // features normalised: A = [x_hi (k 0..11), 1, 1, 0, 0 | x_lo (k 16..27), 0 x 4]
       float fv[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) fv[q] = sv[q * TILE];
+      for (int q = 0; q < Q; ++q) fv[q] = sv[q * mlp::RUN - ex(q)];
       const Moments m = moments9_fast(fv);
       float xh[NFEAT];
 #pragma unroll
@@ -340,8 +378,8 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
       tmem_ld32(ld, y);
       float fv[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) fv[q] = sv[q * TILE];
-      const float tau = sv[Q * TILE];
+      for (int q = 0; q < Q; ++q) fv[q] = sv[q * mlp::RUN - ex(q)];
+      const float tau = sv[Q * mlp::RUN - 4];
       const Moments m = moments9_fast(fv);
       // tau_adj = 1/2 + sigmoid(y_0) = 1 + tanh(y_0 / 2) / 2 (or 1)
       const float tadj = (variant & VAR_FIXED_TAU)
@@ -369,7 +407,7 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
 
 template <class Geo>
 static cudaError_t mlp_step(const float* f_in, float* f_out, const Geo& geo, int64_t N, float tau,
-                            const float* taus, const uint8_t* packed, bool require_mlp,
+                            const float* taus, const uint8_t* packed, bool require_mlp, bool rows,
                             cudaStream_t st) {
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
@@ -382,15 +420,18 @@ static cudaError_t mlp_step(const float* f_in, float* f_out, const Geo& geo, int
   const int64_t want = (ntiles + mlp::NG - 1) / mlp::NG;
   const unsigned grid = (unsigned)(want < num_sms() ? want : num_sms());
   gnn_mlp_step_kernel<Geo><<<grid, 128 * mlp::NG, bytes, st>>>(f_in, f_out, geo, tau, taus, packed,
-                                                      require_mlp, stw);
+                                                      require_mlp, rows, stw);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gnn_mlp_step(const float* f_in, float* f_out, const Shape& s, float tau,
                                 const float* taus, const uint8_t* packed, bool require_mlp,
                                 cudaStream_t st) {
+  // row runs: every tile inside one lattice row, 16-byte aligned population planes
+  const bool rows = s.nx % TILE == 0 && s.ps % 4 == 0 &&
+                    (reinterpret_cast<uintptr_t>(f_in) & 15) == 0;
   return mlp_step(f_in, f_out, make_geo_stack(s), (int64_t)s.nb * s.ny * s.nx, tau, taus, packed,
-                  require_mlp, st);
+                  require_mlp, rows, st);
 }
 
 cudaError_t launch_gnn_mlp_step_table(const float* f_in, float* f_out, const LatDesc* lat,
@@ -399,7 +440,7 @@ cudaError_t launch_gnn_mlp_step_table(const float* f_in, float* f_out, const Lat
                                       cudaStream_t st, int per_sm) {
   const GeoTable geo{lat, first, n, base, count, ps, hint};
   (void)per_sm;  // one CTA of LBM_MLP_GROUPS tile groups per SM, whatever the batch plan chose
-  return mlp_step(f_in, f_out, geo, count, 0.0f, nullptr, packed, false, st);
+  return mlp_step(f_in, f_out, geo, count, 0.0f, nullptr, packed, false, false, st);
 }
 
 }  // namespace lbmgnn

@@ -44,7 +44,8 @@ def _check(got, f, theta, taus):
 # ragged last tiles, 1x1, wraps in x and y, stacks, a padded plane stride
 @pytest.mark.parametrize("nb,ny,nx,pad,variant", [
     (1, 16, 16, 0, 1), (1, 1, 1, 0, 1), (2, 5, 7, 0, 3), (1, 12, 130, 0, 1), (3, 9, 64, 37, 3),
-    (1, 33, 128, 0, 5), (2, 20, 24, 0, 7)])
+    (1, 33, 128, 0, 5), (2, 20, 24, 0, 7), (2, 4, 256, 0, 3), (1, 3, 384, 4, 1),
+    (1, 1, 128, 0, 3)])
 def test_fused_mlp_step_matches_oracle(lbmlib, cuda, nb, ny, nx, pad, variant):
     import torch
     L = lbmlib
@@ -71,6 +72,30 @@ def test_fused_mlp_step_matches_oracle(lbmlib, cuda, nb, ny, nx, pad, variant):
     assert torch.equal(out.view(9, ps)[:, :n], out2.view(9, ps)[:, :n])
     t_ref = sum(lbm.totals(got[:, b]) for b in range(nb))
     assert abs(tot[0].item() - t_ref[0]) <= 1e-12 * t_ref[0]
+
+
+@pytest.mark.parametrize("nb,ny,nx", [(2, 6, 256), (1, 1, 128), (1, 5, 512), (3, 2, 128)])
+def test_fused_mlp_row_runs_equal_node_pulls(lbmlib, cuda, nb, ny, nx):
+    """Rows of whole tiles with 16-byte aligned planes take the row-run fetch
+    (each population's source run of a tile in 16-byte chunks); a plane
+    stride that is not a multiple of 4 takes the per-node 4-byte pulls.  The
+    arithmetic after the fetch is the same, so the two give the same bits."""
+    import torch
+    L = lbmlib
+    theta = inputs.xavier_params(95 + ny, s_df=1e-2, bias_scale=0.1, variant=3)
+    f = _state(nb, ny, nx, seed=nx + ny)
+    n = nb * ny * nx
+    pk = _packed(L, theta, cuda)
+    td = torch.tensor([0.6 + 0.1 * b for b in range(nb)], dtype=torch.float32, device=cuda)
+    outs = []
+    for ps in (n, n + 1):
+        din, _ = to_dev(f, cuda, plane_stride=ps)
+        out = torch.full_like(din, float("nan"))
+        L.lbm_step_gnn_mlp(din, out, L.shape(nx, ny, nb, ps), 1.0, td, pk, None)
+        assert L.lbm_get_status() == 0
+        outs.append(out.view(9, ps)[:, :n])
+    assert torch.equal(outs[0], outs[1])
+    _check(from_dev(outs[0].reshape(-1), f.shape), f, theta, [0.6 + 0.1 * b for b in range(nb)])
 
 
 def test_fused_mlp_step_refuses_a_message_passing_image(lbmlib, cuda):
