@@ -280,7 +280,10 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
   // one mbarrier per group; warp 0 allocates all 512 tensor-memory columns
   // (a power of two, as tcgen05.alloc requires; one CTA per SM)
   if (threadIdx.x == 0)
-    for (int g = 0; g < mlp::NG; ++g) mbar_init(&sh[g].bar, 1);
+    for (int g = 0; g < mlp::NG; ++g) {
+      mbar_init(&sh[g].bar, 1);
+      sh[g].abort = 0;
+    }
   if ((threadIdx.x >> 5) == 0) tmem_alloc(&sh[0].tmem, mlp::TM_COLS);
   tc_fence_before();
   __syncthreads();  // (also publishes the shared-memory writes above)
@@ -315,8 +318,12 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
   };
 
   // The A operand was stored to tensor memory by every thread -> barrier ->
-  // one thread issues the MMA chain and commits it; all threads wait.
-  auto run = [&](auto issue) -> bool {
+  // one thread issues the MMA chain and commits it; all threads wait.  A
+  // wait that gives up marks the group's abort word; the group leaves the
+  // tile loop together at the next end-of-tile barrier (every wait after a
+  // lost one is bounded too, and every thread passes the same barriers).
+  volatile int* abort_flag = &sh[grp].abort;
+  auto run = [&](auto issue) {
     tmem_st_wait();
     tc_fence_before();
     group_sync(grp, 128);
@@ -325,14 +332,9 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
       issue();
       umma_commit(tc.bar);
     }
-    const bool ok = mbar_wait(tc.bar, tc.phase);
+    if (!mbar_wait(tc.bar, tc.phase)) *abort_flag = 1;
     tc.phase ^= 1u;
     tc_fence_after();
-    if (group_any(grp, 128, !ok)) {
-      if (t == 0) raise_status(stw, ST_TIMEOUT);
-      return false;
-    }
-    return true;
   };
 
   int s = 0;
@@ -368,11 +370,11 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
       w[7] = w[14] = w[15] = 0u;
       tmem_st16(la, w);
     }
-    if (!run([&] { umma_128xN_ts(td, ta, w1x, 64, 2); })) break;
+    run([&] { umma_128xN_ts(td, ta, w1x, 64, 2); });
     relu_to_tmem(ld, la, nullptr);  // g1 = ReLU(W1 x + b1) (bias in D)
-    if (!run([&] { mma_bias(w2, b2x, 64); })) break;
+    run([&] { mma_bias(w2, b2x, 64); });
     relu_to_tmem(ld, la, nullptr);  // h0 = ReLU(W2 g1 + b2) (bias in D)
-    if (!run([&] { mma_bias(wh, bhx, 32); })) break;
+    run([&] { mma_bias(wh, bhx, 32); });
     {  // heads and Eq. 3
       float y[32];
       tmem_ld32(ld, y);
@@ -398,6 +400,10 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
     }
     tc_fence_before();
     group_sync(grp, 128);  // the head's accumulator is read before the next tile's MMA
+    if (*abort_flag) {     // a wait gave up: the whole group stops here
+      if (t == 0) raise_status(stw, ST_TIMEOUT);
+      break;
+    }
   }
   cp_async_wait<0>();
   tc_fence_before();

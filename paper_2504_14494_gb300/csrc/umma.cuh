@@ -88,11 +88,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// The same test with a suspend-time hint: a thread whose phase is not yet
+// complete may sleep up to `ns` nanoseconds and is woken when it completes,
+// so a wait costs one instruction instead of a polling loop.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait: gives up after ~`max_cycles` SM cycles and returns false.
+// Each try may sleep up to 0.1 ms (woken at once by the phase's completion);
+// the clock is read only when a try comes back empty.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
                                           long long max_cycles = 4000000000LL) {
+  if (mbar_try_wait_sleep(bar, parity, 100000u)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
+  while (!mbar_try_wait_sleep(bar, parity, 100000u)) {
     if (clock64() - t0 > max_cycles) return false;
   }
   return true;
