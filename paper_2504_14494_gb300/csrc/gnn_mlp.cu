@@ -103,32 +103,19 @@ __device__ __forceinline__ Moments moments9_fast(const float (&f)[Q]) {
   return {rho, jx * inv, jy * inv};
 }
 
-// One layer's epilogue: ReLU(D + b) of the node's 64 accumulator columns,
-// rounded to BF16, written back to tensor memory as the next product's A
-// (32 columns of BF16 pairs).  b: NULL (bias already in D) or 64 floats in
-// shared memory.
-__device__ __forceinline__ void relu_to_tmem(uint32_t lane_d, uint32_t lane_a, const float* b) {
-  uint32_t w[32];
+// One layer's epilogue: ReLU(D) of the node's 64 accumulator columns (the
+// bias is already in D), rounded to BF16, written back to tensor memory as
+// the next product's A (32 columns of BF16 pairs).  Both halves of D are
+// loaded before the one wait.
+__device__ __forceinline__ void relu_to_tmem(uint32_t lane_d, uint32_t lane_a) {
+  uint32_t z0[32], z1[32], w[32];
+  tmem_ld32_async(lane_d, z0);
+  tmem_ld32_async(lane_d + 32u, z1);
+  tmem_ld_wait();
 #pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    float z[32];
-    tmem_ld32(lane_d + 32u * half, z);
-#pragma unroll
-    for (int c = 0; c < 32; c += 8) {
-      float bb[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (b) {
-        const float4 b0 = *reinterpret_cast<const float4*>(b + 32 * half + c);
-        const float4 b1 = *reinterpret_cast<const float4*>(b + 32 * half + c + 4);
-        bb[0] = b0.x, bb[1] = b0.y, bb[2] = b0.z, bb[3] = b0.w;
-        bb[4] = b1.x, bb[5] = b1.y, bb[6] = b1.z, bb[7] = b1.w;
-      }
-#pragma unroll
-      for (int j = 0; j < 8; j += 2) {
-        float2 v = make_float2(z[c + j], z[c + j + 1]);
-        if (b) v = __fadd2_rn(v, make_float2(bb[j], bb[j + 1]));
-        w[16 * half + (c + j) / 2] = relu_bf16x2(v.x, v.y);
-      }
-    }
+  for (int j = 0; j < 16; ++j) {
+    w[j] = relu_bf16x2(__uint_as_float(z0[2 * j]), __uint_as_float(z0[2 * j + 1]));
+    w[16 + j] = relu_bf16x2(__uint_as_float(z1[2 * j]), __uint_as_float(z1[2 * j + 1]));
   }
   tmem_st32(lane_a, w);
 }
@@ -219,8 +206,11 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
     reinterpret_cast<uint4*>(sm + mlp::WH)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   float* nrmw = reinterpret_cast<float*>(sm + mlp::NORM);
-  if (threadIdx.x < NFEAT)  // sigma -> 1/sigma
-    nrmw[NFEAT + threadIdx.x] = 1.0f / nrmw[NFEAT + threadIdx.x];
+  if (threadIdx.x < NFEAT) {  // (mu, sigma) -> (-mu / sigma, 1 / sigma): x_hat = x rs + c
+    const float rs = 1.0f / nrmw[NFEAT + threadIdx.x];
+    nrmw[NFEAT + threadIdx.x] = rs;
+    nrmw[threadIdx.x] = -nrmw[threadIdx.x] * rs;
+  }
   // The biases ride along in the MMAs as BF16 pairs hi + lo (~16 bits):
   // b1 in K columns 12 and 13 of W1x (multiplied by feature columns equal to
   // 1), b2 and the head bias in K columns 0 and 1 of their own blocks
@@ -345,17 +335,18 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
     const int64_t n = tile * TILE + t;
     const float* sv = stg + s * mlp::STAGE_FLOATS + 4 + t;  // read again by the collision
     s = s == 2 ? 0 : s + 1;
+    Moments m;  // of the pulled populations, kept for the collision
     {  // features normalised: A = [x_hi (k 0..11), 1, 1, 0, 0 | x_lo (k 16..27), 0 x 4]
       float fv[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) fv[q] = sv[q * mlp::RUN - ex(q)];
-      const Moments m = moments9_fast(fv);
+      m = moments9_fast(fv);
       float xh[NFEAT];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) xh[q] = (fv[q] - nrm[q]) * nrm[NFEAT + q];
-      xh[9] = (m.rho - nrm[9]) * nrm[NFEAT + 9];
-      xh[10] = (m.ux - nrm[10]) * nrm[NFEAT + 10];
-      xh[11] = (m.uy - nrm[11]) * nrm[NFEAT + 11];
+      for (int q = 0; q < Q; ++q) xh[q] = fmaf(fv[q], nrm[NFEAT + q], nrm[q]);
+      xh[9] = fmaf(m.rho, nrm[NFEAT + 9], nrm[9]);
+      xh[10] = fmaf(m.ux, nrm[NFEAT + 10], nrm[10]);
+      xh[11] = fmaf(m.uy, nrm[NFEAT + 11], nrm[11]);
       uint32_t w[16];
 #pragma unroll
       for (int j = 0; j < NFEAT / 2; ++j) {
@@ -371,9 +362,9 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
       tmem_st16(la, w);
     }
     run([&] { umma_128xN_ts(td, ta, w1x, 64, 2); });
-    relu_to_tmem(ld, la, nullptr);  // g1 = ReLU(W1 x + b1) (bias in D)
+    relu_to_tmem(ld, la);  // g1 = ReLU(W1 x + b1) (bias in D)
     run([&] { mma_bias(w2, b2x, 64); });
-    relu_to_tmem(ld, la, nullptr);  // h0 = ReLU(W2 g1 + b2) (bias in D)
+    relu_to_tmem(ld, la);  // h0 = ReLU(W2 g1 + b2) (bias in D)
     run([&] { mma_bias(wh, bhx, 32); });
     {  // heads and Eq. 3
       float y[32];
@@ -382,7 +373,6 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
 #pragma unroll
       for (int q = 0; q < Q; ++q) fv[q] = sv[q * mlp::RUN - ex(q)];
       const float tau = sv[Q * mlp::RUN - 4];
-      const Moments m = moments9_fast(fv);
       // tau_adj = 1/2 + sigmoid(y_0) = 1 + tanh(y_0 / 2) / 2 (or 1)
       const float tadj = (variant & VAR_FIXED_TAU)
                              ? 1.0f
