@@ -721,6 +721,26 @@ __device__ __forceinline__ bool tc_run_group(TcCtx& tc, unsigned* stw, int g, in
   return true;
 }
 
+// tc_run_group without the OR-barrier after the wait: a wait that gives up
+// sets the group's abort word, which the caller tests after its next group
+// barrier (every later wait is bounded as well, and all threads keep passing
+// the same barriers until then).
+template <typename Issue>
+__device__ __forceinline__ void tc_run_group_flag(TcCtx& tc, volatile int* abort_word, int g,
+                                                  int nthreads, Issue issue) {
+  fence_async_smem();
+  tc_fence_before();
+  group_sync(g, nthreads);
+  if ((int)threadIdx.x == g * nthreads) {
+    tc_fence_after();
+    issue();
+    umma_commit(tc.bar);
+  }
+  if (!mbar_wait(tc.bar, tc.phase)) *abort_word = 1;
+  tc.phase ^= 1u;
+  tc_fence_after();
+}
+
 __device__ __forceinline__ uint32_t lane_base(uint32_t tmem) {
   return tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16);
 }

@@ -350,7 +350,11 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
   const int variant = variant_of(nrm);
   const bool mlp_only = variant & VAR_MLP_ONLY;
   const __nv_bfloat16* h_src = (mlp_only && ra.h_skip) ? ra.h_skip : ra.h_in;
-  auto run = [&](auto issue) { return tc_run_group(tc, stw, grp, GT, issue); };
+  volatile int* abort_word = &sh[grp].abort;
+  auto run = [&](auto issue) {
+    tc_run_group_flag(tc, abort_word, grp, GT, issue);
+    return true;
+  };
 
   // raw BF16 h (features f0.. of node `t * TILE + node`) of tile t
   uint4 hnext[FPT / 8];
@@ -482,8 +486,9 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
         for (int c = 0; c < SL; c += 2) {
           const float2 g = gelu2(__fadd2_rn(make_float2(z[c], z[c + 1]),
                                             make_float2(bn[f0 + s0 + c], bn[f0 + s0 + c + 1])));
-          h[c] += g.x;
-          h[c + 1] += g.y;
+          const float2 hn = __fadd2_rn(make_float2(h[c], h[c + 1]), g);
+          h[c] = hn.x;
+          h[c + 1] = hn.y;
         }
       }
       if (on && ra.h_out) st_pb<SL>(ra.h_out, N, n, f0 + s0, h);
@@ -549,6 +554,10 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
     if (AH && !LBM_PREFETCH && tile + stride < ntiles) load_h(tile + stride);
     tc_fence_before();
     group_sync(grp, GT);
+    if (*abort_word) {  // a tensor-core wait gave up: the group stops here
+      if (tg == 0) raise_status(stw, ST_TIMEOUT);
+      break;
+    }
   }
   tc_teardown_groups(sh, NG, 128);
 }
