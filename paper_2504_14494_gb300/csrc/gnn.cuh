@@ -588,6 +588,14 @@ struct GeoTable {
   __device__ __forceinline__ float force_x() const { return 0.0f; }
 };
 
+// The dynamic shared-memory block aligned up to 1024 bytes (the SW128
+// operand layouts need it), by pointer arithmetic on the __shared__ array:
+// the compiler then still knows the address space and emits shared-memory
+// loads and stores rather than generic ones.
+__device__ __forceinline__ uint8_t* smem_align1024(uint8_t* raw) {
+  return raw + ((1024u - (static_cast<uint32_t>(__cvta_generic_to_shared(raw)) & 1023u)) & 1023u);
+}
+
 // Copies `bytes` (multiple of 16) from global to shared memory with all threads.
 __device__ __forceinline__ void copy_g2s(void* dst, const void* src, uint32_t bytes) {
   const uint4* s = reinterpret_cast<const uint4*>(src);

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256, 2) gnn_head_bwd_kernel(
     float* __restrict__ G, Shape s, const uint8_t* __restrict__ packed, unsigned* stw) {
   if (!blob_ok(packed, stw)) return;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sm = smem_align1024(smem_raw);
   TcShared* sh = reinterpret_cast<TcShared*>(sm + hb::SH);
   zero_smem(sm, hb::WHF);
   copy_g2s(sm + hb::WHF, packed + K::WHF, 2560);
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256, LBM_RB1_CTAS) gnn_round_bwd1_kernel(
     int round, float* __restrict__ G, Shape s, const uint8_t* __restrict__ packed, unsigned* stw) {
   if (!blob_ok(packed, stw)) return;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sm = smem_align1024(smem_raw);
   TcShared* sh = reinterpret_cast<TcShared*>(sm + rb1::SH);
   const uint8_t* kr = packed + K::round_base(round);
   const bool mlp_only = variant_of(reinterpret_cast<const float*>(packed + K::NORM)) & VAR_MLP_ONLY;
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(256, LBM_RB2_CTAS) gnn_round_bwd2_kernel(
     const uint8_t* __restrict__ packed, unsigned* stw) {
   if (!blob_ok(packed, stw)) return;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sm = smem_align1024(smem_raw);
   TcShared* sh = reinterpret_cast<TcShared*>(sm + rb2::SH);
   const uint8_t* kr = packed + K::round_base(round);
   zero_smem(sm + rb2::HT, rb2::WABT - rb2::HT);
@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(256, LBM_EB_CTAS) gnn_encode_bwd_kernel(
     float* __restrict__ G, Shape s, const uint8_t* __restrict__ packed, unsigned* stw) {
   if (!blob_ok(packed, stw)) return;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sm = smem_align1024(smem_raw);
   TcShared* sh = reinterpret_cast<TcShared*>(sm + eb::SH);
   zero_smem(sm + eb::YT, eb::W2 - eb::YT);
   copy_g2s(sm + eb::W2, packed + K::W2, 8192);

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256, (enc_ctas<PULL, BONLY, Geo>())) gnn_encod
       (variant_of(reinterpret_cast<const float*>(packed + K::NORM)) & VAR_MLP_ONLY))
     return;  // inference step of the MLP-only network: the fused kernel (gnn_mlp.cu) did it
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sm = smem_align1024(smem_raw);
   TcShared* sh = reinterpret_cast<TcShared*>(sm + enc::SH);
   copy_g2s(sm + enc::W1X, packed + K::W1X, 8192);
   copy_g2s(sm + enc::W2, packed + K::W2, 8192);
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(128 * TPN * NG, LBM_ROUND_CTAS) gnn_round_kern
   constexpr int GT = 128 * TPN;            // threads per group
   using L = RndL<NG>;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sm = smem_align1024(smem_raw);
   TcShared* sh = reinterpret_cast<TcShared*>(sm + L::SH);
   const uint8_t* kr = packed + K::round_base(ra.round);
   copy_g2s(sm + L::WN, kr + K::WN, 16384);

@@ -133,6 +133,9 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
     return;
   }
   extern __shared__ uint8_t smem_raw[];
+  // aligned through an integer: the staged populations are then read with
+  // generic loads, measured faster here than shared-memory loads (the other
+  // tensor-core kernels use smem_align1024)
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   TcShared* sh = reinterpret_cast<TcShared*>(sm + mlp::SH);
   // group grp of 128 threads: t = node of its tile, warp (t / 32) owns
