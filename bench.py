@@ -294,7 +294,7 @@ def run_ours(args, rank, world, local_rank):
              4: "message passing, tau_adj fixed at 1 (64 x 256^2 recipe)"}
     trained = {}
     for v, th in thetas.items():
-        if v == "relative":
+        if not isinstance(v, int):  # the weighted and the high-Re networks: below
             continue
         r = gnn_bench(args, L, dev, stream, theta=th, label=f"trained in this run: {names[v]}")
         r["rollout_1000_steps"] = rollout_error(L, dev, th)
@@ -308,7 +308,8 @@ def run_ours(args, rank, world, local_rank):
                                              "per-instance relative weights, seed %d" % sd)
                for sd, th in thetas["relative"].items()},
            "batch": batch_bench(args, L, dev, stream, thetas[2]),
-           "stability": {str(v): stability_bench(L, dev, thetas[v]) for v in (0, 2, 4)},
+           "stability": {**{str(v): stability_bench(L, dev, thetas[v]) for v in (0, 2, 4)},
+                         "2_high_re": stability_bench(L, dev, thetas["2_high_re"])},
            "poiseuille": channel_bench(L, dev, {
                "tau_fixed_v4": thetas[4], "conserving_v2": thetas[2],
                "eq3_relative_seed2": thetas["relative"][2]}),
@@ -750,6 +751,7 @@ def train_bench(args, L, dev, stream, variants=(0, 2, 3)):
             curve.append([i + 1, fixed.loss.item()])
     torch.cuda.synchronize()
     thetas[4] = fixed.theta()
+    t_fixed = time.perf_counter() - t0
     # the network of Eq. 3 as printed trained with each instance weighted by
     # its error relative to BGK (lbm_pair_weights + gnn_train_step_weighted),
     # same recipe, three training seeds
@@ -770,9 +772,28 @@ def train_bench(args, L, dev, stream, variants=(0, 2, 3)):
                                             "last_weighted_loss": wtr.loss.item()}
         del wtr
     runs["4_fixed_tau_256"] = {"steps": 3000, "lr": 1e-3, "weight_decay": 1e-2, "batch": 16,
-                               "coarse": 256, "wall_s": round(time.perf_counter() - t0, 2),
-                               "loss_curve": curve}
+                               "coarse": 256, "wall_s": round(t_fixed, 2), "loss_curve": curve}
     del fixed
+    # the conserving network trained on high-Re pairs for the stability
+    # sweep: u0 ~ U[0.1, 0.3], Re log-uniform in [400, 51200], 64^2 coarse
+    # (4x refined), 16 per batch, AdamW lr 1e-3, decay 1e-2, 3000 steps
+    th = inputs.xavier_params(0, s_df=1e-4, variant=inputs.CONSERVATIVE)
+    th[38272:38922] = 0.0
+    hre = Trainer(dev, theta=th, lr=1e-3, wd=1e-2, seed=7, n=64, batch=16, m=4, episode=64,
+                  instances={"u0_range": (0.1, 0.3), "re_range": (400.0, 51200.0),
+                             "log_re": True})
+    t0 = time.perf_counter()
+    curve = []
+    for i in range(3000):
+        hre.step()
+        if i % 500 == 0 or i == 2999:
+            curve.append([i + 1, hre.loss.item()])
+    torch.cuda.synchronize()
+    thetas["2_high_re"] = hre.theta()
+    runs["2_high_re_64"] = {"steps": 3000, "lr": 1e-3, "weight_decay": 1e-2, "batch": 16,
+                            "coarse": 64, "u0": [0.1, 0.3], "re_log_uniform": [400, 51200],
+                            "wall_s": round(time.perf_counter() - t0, 2), "loss_curve": curve}
+    del hre
     info = {"workload": "train_64x256x256_refined4",
             "ms_per_train_step_incl_datagen": round(ms_full, 3),
             "ms_per_fused_train_step": round(ms_step, 3),

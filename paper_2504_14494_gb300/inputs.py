@@ -78,16 +78,21 @@ def normal(shape, seed, scale=1.0):
     return (scale * rng.standard_normal(shape)).astype(np.float64)
 
 
-def training_instances(n, seed, n_coarse=256):
+def training_instances(n, seed, n_coarse=256, u0_range=(0.01, 0.08), re_range=(100.0, 5000.0),
+                       log_re=False):
     """Per-instance TGV draws of the training workload: k multiple in
-    {1, 2, 4}, u0 ~ U[0.01, 0.08], Re ~ U[100, 5000].  Returns a list of dicts
+    {1, 2, 4}, u0 ~ U[u0_range] (default [0.01, 0.08]), Re ~ U[re_range]
+    (default [100, 5000]; log-uniform with log_re).  Returns a list of dicts
     with the lattice viscosity from Re = u0 N / nu (tau follows from nu)."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(n):
         kmult = int(rng.choice([1, 2, 4]))
-        u0 = float(rng.uniform(0.01, 0.08))
-        re = float(rng.uniform(100.0, 5000.0))
+        u0 = float(rng.uniform(*u0_range))
+        if log_re:
+            re = float(np.exp(rng.uniform(np.log(re_range[0]), np.log(re_range[1]))))
+        else:
+            re = float(rng.uniform(*re_range))
         nu = u0 * n_coarse / re
         out.append({"k_mult": kmult, "u0": u0, "re": re, "nu": nu})
     return out

@@ -30,9 +30,12 @@ class PairStream:
     equilibrium and yields `episode` consecutive coarse pairs."""
 
     def __init__(self, device, n=256, batch=64, m=4, episode=32, seed=0,
-                 pressure_consistent=True):
+                 pressure_consistent=True, instances=None):
         import torch
         self.dev = device
+        # keyword arguments of inputs.training_instances (u0_range, re_range,
+        # log_re): the distribution of the TGV instances
+        self.instance_kw = dict(instances or {})
         self.n, self.batch, self.m, self.episode = n, batch, m, episode
         self.rng_seed = seed
         self.draw = 0
@@ -49,7 +52,8 @@ class PairStream:
 
     def _new_episode(self):
         import torch
-        inst = inputs.training_instances(self.batch, self.rng_seed * 100003 + self.draw, self.n)
+        inst = inputs.training_instances(self.batch, self.rng_seed * 100003 + self.draw, self.n,
+                                         **self.instance_kw)
         self.draw += 1
         nf = self.m * self.n
         prm = np.zeros((self.batch, 4))
