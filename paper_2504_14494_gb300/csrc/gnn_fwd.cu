@@ -285,10 +285,10 @@ struct RoundArgs {
 #define LBM_ROUND_CTAS 2
 #endif
 #ifndef LBM_ROUND_TPN
-#define LBM_ROUND_TPN 2  // threads per node of the round kernel (1, 2 or 4)
+#define LBM_ROUND_TPN 1  // threads per node of the round kernel (1, 2 or 4)
 #endif
 #ifndef LBM_ROUND_GROUPS
-#define LBM_ROUND_GROUPS 1  // independent tile groups per CTA
+#define LBM_ROUND_GROUPS 2  // independent tile groups per CTA
 #endif
 #ifndef LBM_NBR_GROUP
 #define LBM_NBR_GROUP 4  // neighbour loads in flight per thread and chunk
