@@ -51,9 +51,9 @@ NCU_TRAFFIC = {
     #     --clock-control none -k regex:"gnn_(encode|round)_kernel" -s 3 -c 3
     #     python bench.py --only gnn --steps 20 --warmup 3   (one GNN-LBM step, 1024 x 1024:
     #     encoder + 2 rounds; key file gnn_fwd.cu)
-    "lbm_step_gnn": {"bytes_per_launch": (37851136 + 206329344) + (270832128 + 219547392)
-                     + (306571520 + 26678016), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
-                     "src_sha": "51df8f91288bf957faef3afdf0bd590dbded1979ca06ae399842409c856de4b4"},
+    "lbm_step_gnn": {"bytes_per_launch": (37890048 + 210455296) + (269706752 + 213404160)
+                     + (306596096 + 25463040), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
+                     "src_sha": "9fdd68c903b64ac57bdf7ce902e12790a9b64b100d484931c976db3d2f2f72a6"},
 }
 
 
