@@ -308,6 +308,9 @@ def run_ours(args, rank, world, local_rank):
                                              "per-instance relative weights, seed %d" % sd)
                for sd, th in thetas["relative"].items()},
            "batch": batch_bench(args, L, dev, stream, thetas[2]),
+           "tgv_tables": tgv_tables(L, dev, {"conserving_v2": thetas[2], "mlp_v3": thetas[3],
+                                             "tau_fixed_v4": thetas[4],
+                                             "eq3_relative_seed2": thetas["relative"][2]}),
            "stability": {**{str(v): stability_bench(L, dev, thetas[v]) for v in (0, 2, 4)},
                          "2_high_re": stability_bench(L, dev, thetas["2_high_re"])},
            "poiseuille": channel_bench(L, dev, {
@@ -647,6 +650,61 @@ def rollout_error(L, dev, theta, n=GNN_SIDE, re=GNN_RE, u0=U0, steps=1000):
     out["gnn_over_bgk"] = out["l2_error_gnn"] / out["l2_error_bgk"]
     L.lbm_get_status()
     return out
+
+
+def tgv_tables(L, dev, thetas, u0=U0):
+    """Analogs of the paper's TGV tables (Sec. 3.2-3.3; the paper states
+    neither its u0 nor its error norm): velocity error (relative L2 against
+    the closed form) and kinetic-energy error (relative, against
+    E(0) exp(-4 nu k^2 t)) for BGK and each network in `thetas`.
+      table2: 64^2, Re = 100, after 1000, 3000 and 5000 steps;
+      table3: 32^2, 64^2, 128^2 at Re = 100, after the same convective time
+              (1000 steps at 64^2, scaled with N);
+      energy_re800: 64^2, Re = 800, energy error after 1000 and 5000 steps.
+    Re = u0 N / nu; uniform initial density."""
+    import torch
+    packs = {}
+    for name, th in thetas.items():
+        pk = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=dev)
+        L.gnn_pack(torch.from_numpy(np.asarray(th, np.float32)).to(dev), pk)
+        packs[name] = pk
+
+    def run(n, re, marks, kind):
+        s = L.shape(n, n)
+        k = 2 * np.pi / n
+        tau = 0.5 + 3.0 * u0 * n / re
+        nu = (tau - 0.5) / 3.0
+        fa = torch.empty(9 * n * n, device=dev)
+        fb = torch.empty_like(fa)
+        tot = torch.zeros(5, dtype=torch.float64, device=dev)
+        ws = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=dev)
+        L.lbm_init_tgv(fa, s, 1.0, u0, k, k, False)
+        L.lbm_moments(fa, s, None, None, None, tot)
+        e0 = tot[3].item()
+        bufs, done, out = [fa, fb], 0, {}
+        for mark in marks:
+            while done < mark:
+                if kind == "bgk":
+                    L.lbm_step_bgk(bufs[0], bufs[1], None, s, tau)
+                else:
+                    L.lbm_step_gnn(bufs[0], bufs[1], s, tau, None, packs[kind], None, ws)
+                bufs.reverse()
+                done += 1
+            L.lbm_moments(bufs[0], s, None, None, None, tot)
+            t = tot.cpu().numpy()
+            ea = e0 * np.exp(-4 * nu * k * k * mark)
+            ok = t[4] == 0 and np.isfinite(t[3])
+            out[str(mark)] = {"velocity_l2": tgv_l2(L, bufs[0], s, n, u0, tau, mark, dev) if ok else None,
+                              "energy_rel_error": float(abs(t[3] - ea) / ea) if ok else None}
+        L.lbm_get_status()
+        return {"n": n, "re": re, "tau": round(tau, 6), "errors": out}
+
+    kinds = ["bgk"] + list(packs)
+    table2 = {kd: run(64, 100.0, (1000, 3000, 5000), kd) for kd in kinds}
+    table3 = {kd: [run(n, 100.0, (1000 * n // 64,), kd) for n in (32, 64, 128)] for kd in kinds}
+    energy = {kd: run(64, 800.0, (1000, 5000), kd) for kd in kinds}
+    return {"u0": u0, "networks": list(packs), "table2_64_re100": table2,
+            "table3_resolution_re100": table3, "energy_64_re800": energy}
 
 
 def held_out_rollout(L, dev, theta, label, marks=(10, 25, 50, 100, 200, 400)):
