@@ -12,7 +12,8 @@ from gpu_util import to_dev
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(1, 1, 1), (1, 3, 5), (2, 5, 7), (1, 16, 24), (1, 6, 128), (3, 4, 130), (2, 8, 16)]
+SHAPES = [(1, 1, 1), (1, 3, 5), (2, 5, 7), (1, 16, 24), (1, 6, 128), (3, 4, 130), (2, 8, 16),
+          (2, 3, 256)]
 
 
 def _state(nb, ny, nx, seed):
@@ -28,6 +29,11 @@ def _scenario(L, dev):
     p = torch.from_numpy(theta).to(dev)
     pk = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=dev)
     L.gnn_pack(p, pk)
+    # the paper's Fig. 2 network for the fused step (row-run fetch where the
+    # rows are whole tiles, per-node pulls elsewhere)
+    pk_mlp = torch.empty_like(pk)
+    L.gnn_pack(torch.from_numpy(inputs.xavier_params(8, s_df=1e-2, bias_scale=0.1,
+                                                     variant=3)).to(dev), pk_mlp)
     for (nb, ny, nx) in SHAPES:
         f = _state(nb, ny, nx, seed=nx + ny)
         din, _ = to_dev(f, dev)
@@ -40,6 +46,11 @@ def _scenario(L, dev):
         out.append(a.clone())
         ws = torch.empty(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=dev)
         L.lbm_step_gnn(din, a, s, 0.75, None, pk, None, ws)
+        out.append(a.clone())
+        L.lbm_step_gnn_mlp(din, a, s, 0.75, None, pk_mlp, None)
+        out.append(a.clone())
+        wc = torch.empty(L.gnn_channel_workspace_bytes(s), dtype=torch.uint8, device=dev)
+        L.lbm_step_gnn_channel(din, a, s, 0.8, None, 1e-5, pk, None, wc)
         out.append(a.clone())
         # training path: forward, Eq. 3 + Eq. 4, backward (edge-term gathers)
         n = nb * ny * nx
