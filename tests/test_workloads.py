@@ -25,3 +25,22 @@ def test_batch_record_draws_the_serving_mix():
     assert all(B.side_lo <= x["side"] <= B.side_hi for x in d)
     assert all(B.re_lo <= x["re"] <= B.re_hi for x in d)
     assert d == inputs.batch_lattices(512, 7)   # the defaults are the same draw
+
+
+def test_training_instance_ranges():
+    """The training draws: defaults u0 ~ U[0.01, 0.08], Re ~ U[100, 5000]
+    (unchanged by the range arguments), and the high-Re recipe of the
+    stability sweep (u0 ~ U[0.1, 0.3], Re log-uniform in [400, 51200])."""
+    import numpy as np
+    d = inputs.training_instances(2000, 3, 64)
+    assert d == inputs.training_instances(2000, 3, 64, (0.01, 0.08), (100.0, 5000.0))
+    assert all(0.01 <= x["u0"] <= 0.08 and 100.0 <= x["re"] <= 5000.0 for x in d)
+    assert all(x["nu"] == pytest.approx(x["u0"] * 64 / x["re"]) for x in d)
+    assert {x["k_mult"] for x in d} == {1, 2, 4}
+    h = inputs.training_instances(2000, 3, 64, (0.1, 0.3), (400.0, 51200.0), log_re=True)
+    re = np.array([x["re"] for x in h])
+    assert re.min() >= 400.0 and re.max() <= 51200.0
+    # log-uniform: each factor-2 band of the 7 between 400 and 51200 holds ~1/7
+    counts = np.histogram(np.log2(re / 400.0), bins=7, range=(0, 7))[0]
+    assert counts.min() > 200 and counts.max() < 380
+    assert all(0.1 <= x["u0"] <= 0.3 for x in h)
