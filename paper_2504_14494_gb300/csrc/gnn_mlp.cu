@@ -10,8 +10,10 @@
 // warp w of the group owns tensor-memory lanes 32 (w % 4)..), each looping
 // over its own tiles with its own staging ring, mbarrier, named barrier and
 // tensor-memory slice; the weights are shared.  The pulled populations of a
-// group's next two tiles are fetched with 4-byte cp.async copies into a
-// 3-stage shared-memory ring while the current tile runs its three MMAs
+// group's next two tiles are fetched with cp.async into a 3-stage
+// shared-memory ring (where lattice rows are whole tiles: per population the
+// tile's source run in 16-byte chunks shared out over the group; otherwise
+// 4-byte copies per node) while the current tile runs its three MMAs
 // (M = 128 nodes, FP32 accumulators in tensor memory):
 //   D = [x_hi | x_lo] W1x^T   (K = 32: the FP32 features split into two BF16
 //                              parts, ~16 bits kept; b1 rides along as two
@@ -20,9 +22,10 @@
 //   D = h0 Wh'^T + 1 bh'^T    (K = 64 + bias, N = 32: the tau head and the
 //                              BF16 pair hi + lo of s_df P W_h, P the
 //                              conserving projection or the identity)
-// and f* = f - (f - f^eq)/(tau tau_adj) + Delta f (Eq. 3).  The
+// and f* = f - (f - f^eq)/(tau tau_adj) + Delta f (Eq. 3, in packed FP32
+// pairs of directions).  The
 // activations never touch shared memory: each epilogue reads the node's
-// accumulator row from tensor memory, applies bias and ReLU, rounds to BF16
+// accumulator row from tensor memory, applies ReLU, rounds to BF16
 // and stores the row back into tensor memory, where the next MMA reads its
 // A operand (weights B from shared memory).  Shared memory then carries
 // only the weights and the staged populations, and the tensor core reads
