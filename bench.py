@@ -54,6 +54,12 @@ NCU_TRAFFIC = {
     "lbm_step_gnn": {"bytes_per_launch": (37890048 + 210455296) + (269706752 + 213404160)
                      + (306596096 + 25463040), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
                      "src_sha": "9fdd68c903b64ac57bdf7ce902e12790a9b64b100d484931c976db3d2f2f72a6"},
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+    #     --clock-control none -k regex:gnn_mlp_step -s 3 -c 1
+    #     python bench.py --only mlp --side 4096 --steps 10 --warmup 3   (one fused step)
+    "gnn_mlp_step_kernel": {"bytes_per_launch": 604117248 + 555008768, "nodes": 4096 * 4096,
+                            "file": "gnn_mlp.cu",
+                            "src_sha": "9e55ae020a3cb4d9f301912650c363479018179b385dfd1147437c664c88c18a"},
 }
 
 
@@ -613,6 +619,9 @@ def mlp_bench(args, L, dev, stream, theta=None, side=MLP_SIDE):
                      "status": L.lbm_get_status()}
     peak, peak_kind = _peaks()
     ach = BYTES_PER_NODE * n * n / (res["mlp"]["ms_per_step"] / 1e3) / 1e9
+    tr = NCU_TRAFFIC.get("gnn_mlp_step_kernel")
+    traffic = (tr["bytes_per_launch"] if tr and tr["nodes"] == n * n
+               and tr["src_sha"] == _src_sha(tr["file"]) else None)
     return {"workload": f"tgv_gnn_mlp_{n}x{n}", "network": "Fig. 2 MLP-only, conserving (variant 3)",
             "call": "lbm_step_gnn_mlp (one fused kernel: gnn_mlp_step_kernel)", "tau": round(tau, 5),
             "steps_timed": kk, "timing": "median of 5 runs",
@@ -622,7 +631,8 @@ def mlp_bench(args, L, dev, stream, theta=None, side=MLP_SIDE):
             "gnn_over_bgk_time": round(res["mlp"]["ms_per_step"] / res["bgk"]["ms_per_step"], 3),
             "roofline": {"bound": "hbm", "kernel": "gnn_mlp_step_kernel", "achieved": round(ach, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-                         "peak_kind": peak_kind, "algorithmic_bytes_per_node": BYTES_PER_NODE},
+                         "peak_kind": peak_kind, "algorithmic_bytes_per_node": BYTES_PER_NODE,
+                         "traffic": traffic},
             "status": res["mlp"]["status"]}
 
 
