@@ -47,7 +47,7 @@ bool overlap(const void* a, const void* b, int64_t bytes) {
 // kept for the life of the process.  Enqueueing is serialised by a mutex;
 // an event may be re-recorded as soon as the waits on it are enqueued.
 #ifndef LBM_HOST_CHUNKS
-#define LBM_HOST_CHUNKS 32  // row blocks of the host copies (swept: 8, 16, 32, 64)
+#define LBM_HOST_CHUNKS 16  // row blocks of the host copies (swept: 8, 16, 32, 64)
 #endif
 constexpr int HOST_CHUNKS = LBM_HOST_CHUNKS;
 struct HostPipe {
