@@ -137,7 +137,7 @@ int lbm_step_gnn(const float* f_in, float* f_out, lbm_shape shape, float tau, co
   // return at once, for every other network the fused kernel does.
   if (launch_gnn_mlp_step(f_in, f_out, s, tau, taus, pk, false, st) != cudaSuccess)
     return LBM_ERR_CUDA;
-  if (launch_gnn_encode(f_in, true, true, s, pk, h0, b0, st) != cudaSuccess) return LBM_ERR_CUDA;
+  if (launch_gnn_encode_fused(f_in, s, pk, h0, b0, st) != cudaSuccess) return LBM_ERR_CUDA;
   RoundLaunch r0;
   r0.h_in = h0;
   r0.ab_in = b0;

@@ -687,7 +687,11 @@ cudaError_t launch_gnn_step_table(const float* f_in, float* f_out, const LatDesc
   if ((e = launch_gnn_mlp_step_table(f_in, f_out, lat, first, n, hint, base, count, ps, packed, st,
                                      per_sm)) != cudaSuccess)
     return e;
-  if ((e = encode_any(f_in, true, true, geo, count, packed, h0, b0, st, per_sm)) != cudaSuccess)
+  // encoder (pull, features, two layers, B = W_b h0): the fused kernel of
+  // gnn_mlp.cu in its encoder mode
+  (void)per_sm;
+  if ((e = launch_gnn_encode_fused_table(f_in, lat, first, n, hint, base, count, ps, packed, h0, b0,
+                                         st)) != cudaSuccess)
     return e;
   RoundLaunch r0;
   r0.h_in = h0;

@@ -57,6 +57,17 @@ cudaError_t launch_gnn_mlp_step(const float* f_in, float* f_out, const Shape& s,
                                 cudaStream_t st);
 
 struct LatDesc;
+// The inference encoder of a message-passing network in the fused kernel's
+// design (pull, features, two GELU layers, B = W_b h0; h0 BF16 and B FP16
+// [N][64] in the chunked plane layout); returns at once for the MLP-only
+// network.  The table form takes the nodes [base, base+count) of the lattices
+// first .. first+n-1 of a device descriptor table.
+cudaError_t launch_gnn_encode_fused(const float* f_in, const Shape& s, const uint8_t* packed,
+                                    __nv_bfloat16* h0, __half* b, cudaStream_t st);
+cudaError_t launch_gnn_encode_fused_table(const float* f_in, const LatDesc* lat, int first, int n,
+                                          const int* hint, int64_t base, int64_t count, int64_t ps,
+                                          const uint8_t* packed, __nv_bfloat16* h0, __half* b,
+                                          cudaStream_t st);
 cudaError_t launch_gnn_mlp_step_table(const float* f_in, float* f_out, const LatDesc* lat,
                                       int first, int n, const int* hint, int64_t base,
                                       int64_t count, int64_t ps, const uint8_t* packed,

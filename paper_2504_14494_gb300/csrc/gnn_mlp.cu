@@ -56,6 +56,10 @@ constexpr int STAGE_FLOATS = Q * RUN + TILE;
 // constant A of ones adds the bias inside the MMA.  WH is the head as this
 // kernel uses it (32 output rows, see the prologue).
 constexpr int NG = LBM_MLP_GROUPS;
+// Encoder mode (the inference encoder of a message-passing network): the
+// round-0 edge weights W_b (SW128, 64 x 64) at WB_E and the layer-2 bias
+// block at B2X_E instead of the head blocks.
+constexpr uint32_t WB_E = 16384, B2X_E = 24576;
 constexpr uint32_t W1X = 0, W2 = 8192, WH = 16384, B2X = 20480, BHX = 28672, STG = 32768,
                    STG_BYTES = STAGE_FLOATS * 4,                   // 5408 per stage and group
                    NORM = STG + NG * STAGES * STG_BYTES,
@@ -123,16 +127,41 @@ __device__ __forceinline__ void relu_to_tmem(uint32_t lane_d, uint32_t lane_a) {
   tmem_st32(lane_a, w);
 }
 
-// One fused GNN-LBM step of the MLP-only network over the nodes of `geo`.
-template <class Geo>
+// The encoder's epilogue: GELU(D) (bias already in D) of the node's 64
+// accumulator columns in packed FP32 pairs, rounded to BF16 pairs (w, in
+// feature order), written back to tensor memory as the next product's A.
+__device__ __forceinline__ void gelu_to_tmem(uint32_t lane_d, uint32_t lane_a,
+                                             uint32_t (&w)[32]) {
+  uint32_t z0[32], z1[32];
+  tmem_ld32_async(lane_d, z0);
+  tmem_ld32_async(lane_d + 32u, z1);
+  tmem_ld_wait();
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const float2 a = gelu2(make_float2(__uint_as_float(z0[2 * j]), __uint_as_float(z0[2 * j + 1])));
+    const float2 b = gelu2(make_float2(__uint_as_float(z1[2 * j]), __uint_as_float(z1[2 * j + 1])));
+    w[j] = bf16x2(a.x, a.y);
+    w[16 + j] = bf16x2(b.x, b.y);
+  }
+  tmem_st32(lane_a, w);
+}
+
+// One fused GNN-LBM step of the MLP-only network over the nodes of `geo`
+// (ENC = false), or (ENC = true) the inference encoder of a message-passing
+// network: the same pull, features and first two layers with GELU, then the
+// round-0 edge term B = W_b h0; h0 (BF16) and B (FP16) go to HBM in the
+// chunked plane layout of the round kernels.
+template <class Geo, bool ENC>
 __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
     const float* __restrict__ f_in, float* __restrict__ f_out, Geo geo, float tau0,
     const float* __restrict__ taus, const uint8_t* __restrict__ packed, bool require_mlp,
-    bool rows, unsigned* stw) {
+    bool rows, __nv_bfloat16* __restrict__ h0_out, __half* __restrict__ b_out, unsigned* stw) {
   if (!blob_ok(packed, stw)) return;
   const int variant = variant_of(reinterpret_cast<const float*>(packed + K::NORM));
-  if (!(variant & VAR_MLP_ONLY)) {  // message-passing networks: the unfused kernels
-    if (require_mlp && threadIdx.x == 0) raise_status(stw, ST_BLOB);
+  if (ENC ? (variant & VAR_MLP_ONLY) != 0 : !(variant & VAR_MLP_ONLY)) {
+    // the MLP-only network is stepped by the MLP mode alone; message-passing
+    // networks by the encoder mode and the round kernels
+    if (!ENC && require_mlp && threadIdx.x == 0) raise_status(stw, ST_BLOB);
     return;
   }
   extern __shared__ uint8_t smem_raw[];
@@ -208,8 +237,14 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
   copy_g2s(sm + mlp::W1X, packed + K::W1X, 8192);
   copy_g2s(sm + mlp::W2, packed + K::W2, 8192);
   copy_g2s(sm + mlp::NORM, packed + K::NORM, 128);
-  for (uint32_t i = threadIdx.x; i < (mlp::STG - mlp::WH) / 16; i += blockDim.x)  // head, biases: 0
-    reinterpret_cast<uint4*>(sm + mlp::WH)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if constexpr (ENC) {  // W_b: rows 64..127 of round 0's [W_a; W_b] block; the bias block 0
+    copy_g2s(sm + mlp::WB_E, packed + K::round_base(0) + K::WAB + 8192, 8192);
+    for (uint32_t i = threadIdx.x; i < (mlp::STG - mlp::B2X_E) / 16; i += blockDim.x)
+      reinterpret_cast<uint4*>(sm + mlp::B2X_E)[i] = make_uint4(0u, 0u, 0u, 0u);
+  } else {
+    for (uint32_t i = threadIdx.x; i < (mlp::STG - mlp::WH) / 16; i += blockDim.x)  // head, biases: 0
+      reinterpret_cast<uint4*>(sm + mlp::WH)[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
   __syncthreads();
   float* nrmw = reinterpret_cast<float*>(sm + mlp::NORM);
   if (threadIdx.x < NFEAT) {  // (mu, sigma) -> (-mu / sigma, 1 / sigma): x_hat = x rs + c
@@ -230,14 +265,15 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
   if (threadIdx.x < HID) {
     const int o = threadIdx.x;
     put_pair(mlp::W1X, o, 12, __ldg(reinterpret_cast<const float*>(packed + K::B1) + o));
-    put_pair(mlp::B2X, o, 0, __ldg(reinterpret_cast<const float*>(packed + K::B2) + o));
+    put_pair(ENC ? mlp::B2X_E : mlp::B2X, o, 0,
+             __ldg(reinterpret_cast<const float*>(packed + K::B2) + o));
   }
-  // The head as this kernel uses it (N = 32): row 0 is the tau head W_h[0]
+  // (MLP mode) The head as this kernel uses it (N = 32): row 0 is the tau head W_h[0]
   // (BF16 already); rows 1..9 and 17..25 hold the BF16 pair hi + lo of
   // s_df P W_h[1..9], with P the projection of the conserving variant (else
   // the identity), so that Delta f = y_q + y_{16+q} comes out of the MMA
   // (bias likewise: s_df P b_h[1..9] and b_h[0] in BHX).
-  {
+  if constexpr (!ENC) {
     const float* whf = reinterpret_cast<const float*>(packed + K::WHF);  // FP32 [10][64]
     const float* bhg = reinterpret_cast<const float*>(packed + K::BH);
     const float sdf0 = __ldg(reinterpret_cast<const float*>(packed + K::NORM) + 24);
@@ -295,8 +331,8 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
   const uint32_t td = tbase + mlp::tm_d(grp), ta = tbase + mlp::tm_a(grp),
                  tones = tbase + mlp::TM_ONES;
   const uint32_t w1x = smem_u32(sm + mlp::W1X), w2 = smem_u32(sm + mlp::W2),
-                 wh = smem_u32(sm + mlp::WH), b2x = smem_u32(sm + mlp::B2X),
-                 bhx = smem_u32(sm + mlp::BHX);
+                 wh = smem_u32(sm + mlp::WH), b2x = smem_u32(sm + (ENC ? mlp::B2X_E : mlp::B2X)),
+                 bhx = smem_u32(sm + mlp::BHX), wb = smem_u32(sm + mlp::WB_E);
   if (grp == 0) {  // the constant A of ones for the bias K steps: K 0, 1 = 1, the rest 0
     uint32_t w[16] = {0x3F803F80u};
     tmem_st16(lane_base(tbase) + mlp::TM_ONES, w);
@@ -368,6 +404,37 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
       tmem_st16(la, w);
     }
     run([&] { umma_128xN_ts(td, ta, w1x, 64, 2); });
+    if constexpr (ENC) {
+      uint32_t w[32];
+      gelu_to_tmem(ld, la, w);  // g1 = GELU(W1 x + b1) (bias in D)
+      run([&] { mma_bias(w2, b2x, 64); });
+      gelu_to_tmem(ld, la, w);  // h0 = GELU(W2 g1 + b2), and to HBM
+      if (n < N) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          *chunk8w(h0_out, N, n, 8 * c) =
+              make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+      }
+      run([&] { umma_128xN_ts(td, ta, wb, 64, 4); });  // B = W_b h0 (no bias)
+      uint32_t z0[32], z1[32];
+      tmem_ld32_async(ld, z0);
+      tmem_ld32_async(ld + 32u, z1);
+      tmem_ld_wait();
+      if (n < N) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const uint32_t* z = c < 4 ? z0 + 8 * c : z1 + 8 * (c - 4);
+          uint32_t hv[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const __half2 hh = __floats2half2_rn(__uint_as_float(z[2 * j]),
+                                                 __uint_as_float(z[2 * j + 1]));
+            hv[j] = *reinterpret_cast<const uint32_t*>(&hh);
+          }
+          *chunk8w(b_out, N, n, 8 * c) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        }
+      }
+    } else {
     relu_to_tmem(ld, la);  // g1 = ReLU(W1 x + b1) (bias in D)
     run([&] { mma_bias(w2, b2x, 64); });
     relu_to_tmem(ld, la);  // h0 = ReLU(W2 g1 + b2) (bias in D)
@@ -415,6 +482,7 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
         o[5 * ps] = o56.x, o[6 * ps] = o56.y, o[7 * ps] = o78.x, o[8 * ps] = o78.y;
       }
     }
+    }
     tc_fence_before();
     group_sync(grp, 128);  // the head's accumulator is read before the next tile's MMA
     if (*abort_flag) {     // a wait gave up: the whole group stops here
@@ -428,22 +496,22 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
   if ((threadIdx.x >> 5) == 0) tmem_dealloc(tbase, mlp::TM_COLS);
 }
 
-template <class Geo>
+template <class Geo, bool ENC = false>
 static cudaError_t mlp_step(const float* f_in, float* f_out, const Geo& geo, int64_t N, float tau,
                             const float* taus, const uint8_t* packed, bool require_mlp, bool rows,
-                            cudaStream_t st) {
+                            cudaStream_t st, __nv_bfloat16* h0 = nullptr, __half* b = nullptr) {
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
   if (N <= 0) return cudaSuccess;
   const uint32_t bytes = mlp::BYTES + 1024;
   cudaError_t e;
-  if ((e = set_smem(gnn_mlp_step_kernel<Geo>, bytes)) != cudaSuccess) return e;
+  if ((e = set_smem(gnn_mlp_step_kernel<Geo, ENC>, bytes)) != cudaSuccess) return e;
   // one CTA (NG tile groups) per SM, fewer for small lattices
   const int64_t ntiles = (N + TILE - 1) / TILE;
   const int64_t want = (ntiles + mlp::NG - 1) / mlp::NG;
   const unsigned grid = (unsigned)(want < num_sms() ? want : num_sms());
-  gnn_mlp_step_kernel<Geo><<<grid, 128 * mlp::NG, bytes, st>>>(f_in, f_out, geo, tau, taus, packed,
-                                                      require_mlp, rows, stw);
+  gnn_mlp_step_kernel<Geo, ENC><<<grid, 128 * mlp::NG, bytes, st>>>(
+      f_in, f_out, geo, tau, taus, packed, require_mlp, rows, h0, b, stw);
   return cudaGetLastError();
 }
 
@@ -455,6 +523,23 @@ cudaError_t launch_gnn_mlp_step(const float* f_in, float* f_out, const Shape& s,
                     (reinterpret_cast<uintptr_t>(f_in) & 15) == 0;
   return mlp_step(f_in, f_out, make_geo_stack(s), (int64_t)s.nb * s.ny * s.nx, tau, taus, packed,
                   require_mlp, rows, st);
+}
+
+cudaError_t launch_gnn_encode_fused(const float* f_in, const Shape& s, const uint8_t* packed,
+                                    __nv_bfloat16* h0, __half* b, cudaStream_t st) {
+  const bool rows = s.nx % TILE == 0 && s.ps % 4 == 0 &&
+                    (reinterpret_cast<uintptr_t>(f_in) & 15) == 0;
+  return mlp_step<GeoStack, true>(f_in, nullptr, make_geo_stack(s), (int64_t)s.nb * s.ny * s.nx,
+                                  1.0f, nullptr, packed, false, rows, st, h0, b);
+}
+
+cudaError_t launch_gnn_encode_fused_table(const float* f_in, const LatDesc* lat, int first, int n,
+                                          const int* hint, int64_t base, int64_t count, int64_t ps,
+                                          const uint8_t* packed, __nv_bfloat16* h0, __half* b,
+                                          cudaStream_t st) {
+  const GeoTable geo{lat, first, n, base, count, ps, hint};
+  return mlp_step<GeoTable, true>(f_in, nullptr, geo, count, 0.0f, nullptr, packed, false, false,
+                                  st, h0, b);
 }
 
 cudaError_t launch_gnn_mlp_step_table(const float* f_in, float* f_out, const LatDesc* lat,
