@@ -48,18 +48,21 @@ NCU_TRAFFIC = {
     "bgk_step_x4": {"bytes_per_launch": 604054528 + 547321088,
                     "src_sha": "75175dfa13fa1003a94d217d10ae26bfeaf1caf2b0033fe04d22f926f7b425a7"},
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
-    #     --clock-control none -k regex:"gnn_(encode|round)_kernel" -s 3 -c 3
+    #     --clock-control none -k regex:"gnn_(mlp_step|round)_kernel" -s 4 -c 4
     #     python bench.py --only gnn --steps 20 --warmup 3   (one GNN-LBM step, 1024 x 1024:
-    #     encoder + 2 rounds; key file gnn_fwd.cu)
-    "lbm_step_gnn": {"bytes_per_launch": (37890048 + 210455296) + (269706752 + 213404160)
-                     + (306596096 + 25463040), "nodes": 1024 * 1024, "file": "gnn_fwd.cu",
-                     "src_sha": "9fdd68c903b64ac57bdf7ce902e12790a9b64b100d484931c976db3d2f2f72a6"},
+    #     the MLP-only kernel returning at once, the fused encoder, 2 rounds; key files
+    #     gnn_fwd.cu and gnn_mlp.cu)
+    "lbm_step_gnn": {"bytes_per_launch": 50176 + (37928448 + 204323328) + (269613824 + 213887488)
+                     + (306643712 + 25620480), "nodes": 1024 * 1024,
+                     "file": ["gnn_fwd.cu", "gnn_mlp.cu"],
+                     "src_sha": ["f60b456f59d6393ae43959e1f1c5d49f56088d007d374aac0545b23c1f9399fc",
+                                 "37f70dacffcab504f7d6e1398a52f8eaa0907899fa6fe9ce7007c05ea87143df"]},
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #     --clock-control none -k regex:gnn_mlp_step -s 3 -c 1
     #     python bench.py --only mlp --side 4096 --steps 10 --warmup 3   (one fused step)
-    "gnn_mlp_step_kernel": {"bytes_per_launch": 604117248 + 555008768, "nodes": 4096 * 4096,
+    "gnn_mlp_step_kernel": {"bytes_per_launch": 604083200 + 554795520, "nodes": 4096 * 4096,
                             "file": "gnn_mlp.cu",
-                            "src_sha": "9e55ae020a3cb4d9f301912650c363479018179b385dfd1147437c664c88c18a"},
+                            "src_sha": "37f70dacffcab504f7d6e1398a52f8eaa0907899fa6fe9ce7007c05ea87143df"},
 }
 
 
@@ -85,6 +88,9 @@ def _finite(obj):
 
 
 def _src_sha(name):
+    """SHA-256 of a csrc file, or the list of them for a list of names."""
+    if isinstance(name, (list, tuple)):
+        return [_src_sha(n) for n in name]
     with open(os.path.join(ROOT, "paper_2504_14494_gb300", "csrc", name), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()
 
@@ -554,13 +560,14 @@ def gnn_bench(args, L, dev, stream, side=GNN_SIDE, only=False, theta=None, label
                and tr["src_sha"] == _src_sha(tr["file"]) else None)
     return {"workload": f"tgv_gnn_{n}x{n}", "re": GNN_RE, "tau": round(tau, 5), "u0": U0,
             "roofline": None if mlp_only else {
-                "bound": "alu", "kernel": "lbm_step_gnn (gnn_encode_kernel + 2 x gnn_round_kernel)",
+                "bound": "alu",
+                "kernel": "lbm_step_gnn (fused encoder gnn_mlp_step_kernel<ENC> + 2 x gnn_round_kernel)",
                 "peak_basis": f"{GELU_PER_CLK_SM:.2f} edge GELUs/clock/SM x {_sm_count(dev)} SMs "
                               f"x {_max_sm_hz(dev) / 1e6:.0f} MHz (measured issue rate of the "
                               f"message sequence, MUFU tanh bound; microbench/fp16_rate.cu)",
                 "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "G edge-feature GELU/s",
                 "frac": round(ach / peak, 4), "traffic": traffic,
-                "traffic_note": "DRAM bytes of one step (3 kernels), ncu"},
+                "traffic_note": "DRAM bytes of one step (fused encoder, 2 rounds and the MLP-only kernel returning at once), ncu"},
             "weights": label,
             "steps_timed": kk, "steps_run": args.warmup + kk,
             "mlups_gnn": res["gnn"]["mlups"], "mlups_bgk_same_lattice": res["bgk"]["mlups"],
