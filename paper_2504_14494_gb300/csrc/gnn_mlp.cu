@@ -30,6 +30,11 @@
 // A operand (weights B from shared memory).  Shared memory then carries
 // only the weights and the staged populations, and the tensor core reads
 // 14 KB of it per tile instead of 54 KB.
+//
+// The same kernel in its encoder mode (ENC) is the inference encoder of the
+// message-passing network: the same pull and features, the two layers with
+// GELU instead of ReLU, then B = W_b h0 (round 0's edge term of the
+// neighbours) in place of the head; h0 and B go to HBM for the round kernels.
 #include "gnn.cuh"
 #include "gnn_launch.h"
 
@@ -434,54 +439,54 @@ __global__ void __launch_bounds__(128 * LBM_MLP_GROUPS, 1) gnn_mlp_step_kernel(
           *chunk8w(b_out, N, n, 8 * c) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
         }
       }
-    } else {
-    relu_to_tmem(ld, la);  // g1 = ReLU(W1 x + b1) (bias in D)
-    run([&] { mma_bias(w2, b2x, 64); });
-    relu_to_tmem(ld, la);  // h0 = ReLU(W2 g1 + b2) (bias in D)
-    run([&] { mma_bias(wh, bhx, 32); });
-    {  // heads and Eq. 3
-      float y[32];
-      tmem_ld32(ld, y);
-      float fv[Q];
+    } else {  // MLP mode: the head and Eq. 3
+      relu_to_tmem(ld, la);  // g1 = ReLU(W1 x + b1) (bias in D)
+      run([&] { mma_bias(w2, b2x, 64); });
+      relu_to_tmem(ld, la);  // h0 = ReLU(W2 g1 + b2) (bias in D)
+      run([&] { mma_bias(wh, bhx, 32); });
+      {  // heads and Eq. 3
+        float y[32];
+        tmem_ld32(ld, y);
+        float fv[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) fv[q] = sv[q * mlp::RUN - ex(q)];
-      const float tau = sv[Q * mlp::RUN - 4];
-      // tau_adj = 1/2 + sigmoid(y_0) = 1 + tanh(y_0 / 2) / 2 (or 1)
-      const float tadj = (variant & VAR_FIXED_TAU)
-                             ? 1.0f
-                             : fmaf(0.5f, tanh_fast(0.5f * y[0]), 1.0f);
-      const float inv = __fdividef(1.0f, tau * tadj);
-      // Delta f = s_df P y_1..9 (hi + lo rows of the head)
-      auto dpair = [&](int q) {
-        return __fadd2_rn(make_float2(y[1 + q], y[2 + q]), make_float2(y[17 + q], y[18 + q]));
-      };
-      // Eq. 3, f* = f (1 - 1/t) + f^eq / t + Delta f, in packed FP32 pairs
-      // of directions with equal weights: f^eq_q = w rho (c1 + e.u (3 + 4.5 e.u)),
-      // c1 = 1 - 1.5 u^2; directions 3, 4 and 7, 8 are 1, 2 and 5, 6 with
-      // e.u negated (the sign moves onto the 3).
-      const float c1 = 1.0f - 1.5f * (m.ux * m.ux + m.uy * m.uy);
-      const float omi = 1.0f - inv;
-      const float2 C1 = make_float2(c1, c1), INV = make_float2(inv, inv),
-                   OMI = make_float2(omi, omi), H45 = make_float2(4.5f, 4.5f);
-      const float2 E1 = make_float2(m.ux, m.uy);                  // e.u of q = 1, 2
-      const float2 E2 = make_float2(m.ux + m.uy, m.uy - m.ux);    // e.u of q = 5, 6
-      const float r9 = m.rho * (1.0f / 9.0f), r36 = m.rho * (1.0f / 36.0f);
-      auto pair = [&](int q, float2 e, float sg, float w) {
-        const float2 tt = __ffma2_rn(e, __ffma2_rn(e, H45, make_float2(3.0f * sg, 3.0f * sg)), C1);
-        const float2 feq = __fmul2_rn(tt, make_float2(w, w));
-        const float2 fq = make_float2(fv[q], fv[q + 1]);
-        return __fadd2_rn(__ffma2_rn(feq, INV, __fmul2_rn(fq, OMI)), dpair(q));
-      };
-      const float2 o12 = pair(1, E1, 1.0f, r9), o34 = pair(3, E1, -1.0f, r9);
-      const float2 o56 = pair(5, E2, 1.0f, r36), o78 = pair(7, E2, -1.0f, r36);
-      const float o0 = fmaf(m.rho * (4.0f / 9.0f) * c1, inv, fv[0] * omi) + (y[1] + y[17]);
-      if (n < N) {
-        float* o = f_out + base + n;
-        o[0] = o0;
-        o[ps] = o12.x, o[2 * ps] = o12.y, o[3 * ps] = o34.x, o[4 * ps] = o34.y;
-        o[5 * ps] = o56.x, o[6 * ps] = o56.y, o[7 * ps] = o78.x, o[8 * ps] = o78.y;
+        for (int q = 0; q < Q; ++q) fv[q] = sv[q * mlp::RUN - ex(q)];
+        const float tau = sv[Q * mlp::RUN - 4];
+        // tau_adj = 1/2 + sigmoid(y_0) = 1 + tanh(y_0 / 2) / 2 (or 1)
+        const float tadj = (variant & VAR_FIXED_TAU)
+                               ? 1.0f
+                               : fmaf(0.5f, tanh_fast(0.5f * y[0]), 1.0f);
+        const float inv = __fdividef(1.0f, tau * tadj);
+        // Delta f = s_df P y_1..9 (hi + lo rows of the head)
+        auto dpair = [&](int q) {
+          return __fadd2_rn(make_float2(y[1 + q], y[2 + q]), make_float2(y[17 + q], y[18 + q]));
+        };
+        // Eq. 3, f* = f (1 - 1/t) + f^eq / t + Delta f, in packed FP32 pairs
+        // of directions with equal weights: f^eq_q = w rho (c1 + e.u (3 + 4.5 e.u)),
+        // c1 = 1 - 1.5 u^2; directions 3, 4 and 7, 8 are 1, 2 and 5, 6 with
+        // e.u negated (the sign moves onto the 3).
+        const float c1 = 1.0f - 1.5f * (m.ux * m.ux + m.uy * m.uy);
+        const float omi = 1.0f - inv;
+        const float2 C1 = make_float2(c1, c1), INV = make_float2(inv, inv),
+                     OMI = make_float2(omi, omi), H45 = make_float2(4.5f, 4.5f);
+        const float2 E1 = make_float2(m.ux, m.uy);                  // e.u of q = 1, 2
+        const float2 E2 = make_float2(m.ux + m.uy, m.uy - m.ux);    // e.u of q = 5, 6
+        const float r9 = m.rho * (1.0f / 9.0f), r36 = m.rho * (1.0f / 36.0f);
+        auto pair = [&](int q, float2 e, float sg, float w) {
+          const float2 tt = __ffma2_rn(e, __ffma2_rn(e, H45, make_float2(3.0f * sg, 3.0f * sg)), C1);
+          const float2 feq = __fmul2_rn(tt, make_float2(w, w));
+          const float2 fq = make_float2(fv[q], fv[q + 1]);
+          return __fadd2_rn(__ffma2_rn(feq, INV, __fmul2_rn(fq, OMI)), dpair(q));
+        };
+        const float2 o12 = pair(1, E1, 1.0f, r9), o34 = pair(3, E1, -1.0f, r9);
+        const float2 o56 = pair(5, E2, 1.0f, r36), o78 = pair(7, E2, -1.0f, r36);
+        const float o0 = fmaf(m.rho * (4.0f / 9.0f) * c1, inv, fv[0] * omi) + (y[1] + y[17]);
+        if (n < N) {
+          float* o = f_out + base + n;
+          o[0] = o0;
+          o[ps] = o12.x, o[2 * ps] = o12.y, o[3 * ps] = o34.x, o[4 * ps] = o34.y;
+          o[5 * ps] = o56.x, o[6 * ps] = o56.y, o[7 * ps] = o78.x, o[8 * ps] = o78.y;
+        }
       }
-    }
     }
     tc_fence_before();
     group_sync(grp, 128);  // the head's accumulator is read before the next tile's MMA
