@@ -52,17 +52,17 @@ NCU_TRAFFIC = {
     #     python bench.py --only gnn --steps 20 --warmup 3   (one GNN-LBM step, 1024 x 1024:
     #     the MLP-only kernel returning at once, the fused encoder, 2 rounds; key files
     #     gnn_fwd.cu and gnn_mlp.cu)
-    "lbm_step_gnn": {"bytes_per_launch": 50176 + (37928448 + 204323328) + (269613824 + 213887488)
-                     + (306643712 + 25620480), "nodes": 1024 * 1024,
+    "lbm_step_gnn": {"bytes_per_launch": 50176 + (37915392 + 204349440) + (269272064 + 213337344)
+                     + (306696192 + 25646592), "nodes": 1024 * 1024,
                      "file": ["gnn_fwd.cu", "gnn_mlp.cu"],
                      "src_sha": ["f60b456f59d6393ae43959e1f1c5d49f56088d007d374aac0545b23c1f9399fc",
-                                 "37f70dacffcab504f7d6e1398a52f8eaa0907899fa6fe9ce7007c05ea87143df"]},
+                                 "f4c35f4c20b57a0feca1e66b043ceb113a26a00364f07f524735a77ff9b9f640"]},
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #     --clock-control none -k regex:gnn_mlp_step -s 3 -c 1
     #     python bench.py --only mlp --side 4096 --steps 10 --warmup 3   (one fused step)
-    "gnn_mlp_step_kernel": {"bytes_per_launch": 604083200 + 554795520, "nodes": 4096 * 4096,
+    "gnn_mlp_step_kernel": {"bytes_per_launch": 604143616 + 555024640, "nodes": 4096 * 4096,
                             "file": "gnn_mlp.cu",
-                            "src_sha": "37f70dacffcab504f7d6e1398a52f8eaa0907899fa6fe9ce7007c05ea87143df"},
+                            "src_sha": "f4c35f4c20b57a0feca1e66b043ceb113a26a00364f07f524735a77ff9b9f640"},
 }
 
 
