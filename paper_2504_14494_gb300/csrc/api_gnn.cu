@@ -36,6 +36,12 @@ int64_t f_bytes(const Shape& s) { return (8 * s.ps + nodes(s)) * (int64_t)sizeof
 // lbm_step_gnn scratch per node: BF16 h0, h1 and FP16 B0, B1 ([N][64] each).
 constexpr int64_t STEP_WS_PER_NODE = 512;
 
+// lbm_step_gnn_channel scratch: f_pre (rounded up to 256 bytes), then per
+// node BF16 h0 [64], FP16 AB0 [128], BF16 h1 [64], FP16 AB1 [128], FP32 y [10].
+int64_t channel_ws_bytes(const Shape& s) {
+  return ((f_bytes(s) + 255) / 256) * 256 + nodes(s) * (128 + 256 + 128 + 256 + 40);
+}
+
 }  // namespace
 
 extern "C" {
@@ -185,12 +191,6 @@ int lbm_step_gnn_mlp(const float* f_in, float* f_out, lbm_shape shape, float tau
       return LBM_ERR_CUDA;
   }
   return LBM_OK;
-}
-
-// lbm_step_gnn_channel scratch: f_pre (rounded up to 256 bytes), then per
-// node BF16 h0 [64], FP16 AB0 [128], BF16 h1 [64], FP16 AB1 [128], FP32 y [10].
-static int64_t channel_ws_bytes(const Shape& s) {
-  return ((f_bytes(s) + 255) / 256) * 256 + nodes(s) * (128 + 256 + 128 + 256 + 40);
 }
 
 size_t gnn_channel_workspace_bytes(lbm_shape shape) {
