@@ -284,3 +284,38 @@ def test_step_gnn_full_size_1024_sampled(lbmlib, cuda):
     corr = np.max(np.abs(ref - bgk))
     assert np.max(np.abs(got - ref) - 1e-6 * np.abs(ref)) / corr <= 5e-2
 
+
+
+@pytest.mark.parametrize("nb,ny,nx", [(1, 6, 128), (2, 3, 256), (1, 5, 7), (2, 4, 130)])
+def test_inference_encoder_outputs_match_oracle(lbmlib, cuda, nb, ny, nx):
+    """The inference encoder of lbm_step_gnn (the fused kernel's encoder mode;
+    rows of whole tiles take its row-run fetch, the others the per-node
+    pulls) leaves h0 (BF16) and B = W_b h0 (FP16) at the head of the step's
+    workspace in the chunked layout: both within relative L2 2e-2 of the
+    oracle's h0 and W_b h0 (the workspace layout is the library's internal
+    one: h0 [N][64] BF16, then B [N][64] FP16)."""
+    import torch
+    L = lbmlib
+    theta = inputs.xavier_params(55 + nx, s_df=1e-2, bias_scale=0.1)
+    f = _state(nb, ny, nx, seed=nx + ny)
+    pk = _packed(L, theta, cuda)
+    din, _ = to_dev(f, cuda)
+    s = L.shape(nx, ny, nb)
+    N = nb * ny * nx
+    ws = torch.zeros(L.gnn_step_workspace_bytes(s), dtype=torch.uint8, device=cuda)
+    out = torch.empty_like(din)
+    L.lbm_step_gnn(din, out, s, 0.8, None, pk, None, ws)
+    assert L.lbm_get_status() == 0
+    h0 = ws[:N * 128].view(torch.bfloat16).view(8, N, 8).permute(1, 0, 2).reshape(N, 64)
+    b0 = ws[N * 128:N * 256].view(torch.float16).view(8, N, 8).permute(1, 0, 2).reshape(N, 64)
+    h0 = h0.float().cpu().numpy().astype(np.float64)
+    b0 = b0.float().cpu().numpy().astype(np.float64)
+    p = gnn.unpack(theta)
+    h_o, b_o = [], []
+    for b in range(nb):
+        _, cache = gnn.forward(lbm.stream_pull(f[:, b].astype(np.float64)), p)
+        h_o.append(cache["h"][0])
+        b_o.append(cache["h"][0] @ p["r0.edge.W"][:, 64:128].T)
+    eh, eb = rel_l2(h0, np.concatenate(h_o)), rel_l2(b0, np.concatenate(b_o))
+    print(f"h0 rel L2 {eh:.2e}, B rel L2 {eb:.2e}")
+    assert eh <= 2e-2 and eb <= 2e-2, (eh, eb)
