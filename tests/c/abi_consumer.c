@@ -55,12 +55,12 @@ static int host_part(void) {
   const int bad_null = gnn_params_init_xavier(NULL, 5, 1e-2f, 0);
   const int bad_variant = gnn_params_init_xavier(theta, 5, 1e-2f, 8);
   printf("{\"param_count\": %zu, \"trainable_count\": %zu, \"packed_bytes\": %zu, "
-         "\"step_ws\": %zu, \"host_ws\": %zu, \"saved_bytes\": %zu, "
+         "\"step_ws\": %zu, \"channel_ws\": %zu, \"host_ws\": %zu, \"saved_bytes\": %zu, "
          "\"xavier_sum\": %.17g, \"xavier_sum_abs\": %.17g, \"xavier_first\": %.9g, "
          "\"xavier_last\": %.9g, \"bad_null\": %d, \"bad_variant\": %d, "
          "\"status_ok\": \"%s\", \"status_tau\": \"%s\", \"abi\": %d, \"layout\": %d}\n",
          np, gnn_trainable_count(), gnn_packed_bytes(), gnn_step_workspace_bytes(s),
-         lbm_host_workspace_bytes(s), gnn_saved_bytes(s), sum, sum_abs, theta[0],
+         gnn_channel_workspace_bytes(s), lbm_host_workspace_bytes(s), gnn_saved_bytes(s), sum, sum_abs, theta[0],
          theta[np - 1], bad_null, bad_variant, lbm_status_string(LBM_OK),
          lbm_status_string(LBM_ERR_TAU), abi, layout);
   free(theta);
@@ -96,24 +96,34 @@ static int gpu_part(const char* out_path) {
   /* GNN-LBM step of the BGK result: fb -> fa */
   CHECK(lbm_step_gnn(fb, fa, s, 0.7f, NULL, packed, NULL, ws, wsb, NULL));
   CHECK(lbm_get_status(NULL));
+  /* GNN-LBM step of the channel (walls beyond rows 0 and ny-1, force 1e-4)
+     of the BGK result: fb -> ft */
+  const size_t wcb = gnn_channel_workspace_bytes(s);
+  void* wc = NULL;
+  CUDA(cudaMalloc(&wc, wcb));
+  CHECK(lbm_step_gnn_channel(fb, ft, s, 0.7f, NULL, 1e-4f, packed, NULL, wc, wcb, NULL));
+  CHECK(lbm_get_status(NULL));
   /* an aliased output is rejected before anything is launched */
   const int alias = lbm_step_bgk(fa, fa, NULL, s, 0.7f, NULL, 1, NULL, NULL);
 
-  float* host = (float*)malloc(2 * fbytes);
+  float* host = (float*)malloc(3 * fbytes);
   double th[5];
   if (!host) return 1;
   CUDA(cudaMemcpy(host, fb, fbytes, cudaMemcpyDeviceToHost));
   CUDA(cudaMemcpy(th, tot, sizeof th, cudaMemcpyDeviceToHost));
   CUDA(cudaMemcpy(host + 9 * n, fa, fbytes, cudaMemcpyDeviceToHost));
+  CUDA(cudaMemcpy(host + 18 * n, ft, fbytes, cudaMemcpyDeviceToHost));
   FILE* fh = fopen(out_path, "wb");
   if (!fh) return 1;
   const int ok = fwrite(host, 1, fbytes, fh) == fbytes && fwrite(th, 1, sizeof th, fh) == sizeof th &&
-                 fwrite(host + 9 * n, 1, fbytes, fh) == fbytes;
+                 fwrite(host + 9 * n, 1, fbytes, fh) == fbytes &&
+                 fwrite(host + 18 * n, 1, fbytes, fh) == fbytes;
   fclose(fh);
   if (!ok) return 1;
   printf("{\"nodes\": %zu, \"mass\": %.17g, \"alias\": %d}\n", n, th[0], alias);
   free(host);
   free(theta);
+  cudaFree(wc);
   cudaFree(ws);
   cudaFree(packed);
   cudaFree(params);

@@ -52,6 +52,7 @@ def test_host_calls_from_c_agree_with_the_binding(consumer):
     assert got["trainable_count"] == L.gnn_trainable_count()
     assert got["packed_bytes"] == L.gnn_packed_bytes()
     assert got["step_ws"] == L.gnn_step_workspace_bytes(s)
+    assert got["channel_ws"] == L.gnn_channel_workspace_bytes(s)
     assert got["host_ws"] == L.lbm_host_workspace_bytes(s)
     assert got["saved_bytes"] == L.gnn_saved_bytes(s)
     theta = L.gnn_params_init_xavier(np.zeros(L.gnn_param_count(), np.float32), 5, 1e-2, 0)
@@ -79,7 +80,9 @@ def test_gpu_calls_from_c_match_the_oracle(consumer, tmp_path):
     fb = 9 * n * 4
     bgk = np.frombuffer(raw[:fb], np.float32).reshape(9, nb, ny, nx).astype(np.float64)
     tot = np.frombuffer(raw[fb:fb + 40], np.float64)
-    gstate = np.frombuffer(raw[fb + 40:], np.float32).reshape(9, nb, ny, nx).astype(np.float64)
+    gstate = np.frombuffer(raw[fb + 40:2 * fb + 40], np.float32).reshape(9, nb, ny, nx)
+    gstate = gstate.astype(np.float64)
+    cstate = np.frombuffer(raw[2 * fb + 40:], np.float32).reshape(9, nb, ny, nx).astype(np.float64)
     f0 = lbm.tgv_init(nx, ny, 1.0, 0.05, 2 * np.pi / nx, 2 * np.pi / ny)
     ref = lbm.bgk_run(f0, 0.7, 7)
     for b in range(nb):
@@ -91,4 +94,10 @@ def test_gpu_calls_from_c_match_the_oracle(consumer, tmp_path):
         want = gnn.gnn_step(bgk[:, b], theta.astype(np.float64), 0.7)
         plain = lbm.bgk_step(bgk[:, b], 0.7)
         d, w = gstate[:, b] - plain, want - plain
+        assert float(np.sqrt(np.sum((d - w) ** 2) / np.sum(w ** 2))) <= 3e-2
+    from oracle import channel
+    for b in range(nb):  # the channel's GNN-LBM step of the same state
+        want = channel.gnn_channel_step(bgk[:, b], theta.astype(np.float64), 0.7, 1e-4)
+        plain = channel.channel_step(bgk[:, b], 0.7, 1e-4)
+        d, w = cstate[:, b] - plain, want - plain
         assert float(np.sqrt(np.sum((d - w) ** 2) / np.sum(w ** 2))) <= 3e-2
