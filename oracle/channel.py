@@ -19,6 +19,8 @@ Readings where the paper gives no scheme:
   * With rho = 1, mu = nu = (tau - 1/2)/3, the steady profile is
     u(y) = G/(2 nu) (y + 1/2) (ny - 1/2 - y).
   * Re = u_max H / nu with u_max = G H^2 / (8 nu).
+  * Training loss of the channel network: Eq. 3 with Guo's source at the
+    network's relaxation time, then Eq. 4 (``collide_loss_channel``).
 """
 import numpy as np
 
@@ -27,16 +29,22 @@ from . import lbm
 OPP = np.array([0, 3, 4, 1, 2, 7, 8, 5, 6])
 
 
-def guo_source(ux, uy, tau, gx, gy=0.0):
-    """Guo forcing term S_i for force (gx, gy) (per unit volume)."""
-    s = np.empty((lbm.Q,) + np.shape(ux))
+def guo_term(ux, uy, gx, gy=0.0):
+    """w_i [3 (e_i - u) + 9 (e_i . u) e_i] . F, Guo's source without its
+    relaxation factor (1 - 1/(2 tau))."""
+    s = np.empty((lbm.Q,) + np.broadcast(ux, uy, gx, gy).shape)
     for i in range(lbm.Q):
         ex, ey = lbm.E[i]
         eu = ex * ux + ey * uy
         tx = 3.0 * (ex - ux) + 9.0 * eu * ex
         ty = 3.0 * (ey - uy) + 9.0 * eu * ey
-        s[i] = (1.0 - 0.5 / tau) * lbm.W[i] * (tx * gx + ty * gy)
+        s[i] = lbm.W[i] * (tx * gx + ty * gy)
     return s
+
+
+def guo_source(ux, uy, tau, gx, gy=0.0):
+    """Guo forcing term S_i for force (gx, gy) (per unit volume)."""
+    return (1.0 - 0.5 / tau) * guo_term(ux, uy, gx, gy)
 
 
 def moments_forced(f, gx, gy=0.0):
@@ -101,3 +109,36 @@ def poiseuille_profile(ny, tau, gx):
     """Eq. 5 in lattice units (rho = 1): u(y) = G/(2 nu) (y+1/2)(ny-1/2-y)."""
     y = np.arange(ny, dtype=np.float64)
     return gx / (2.0 * lbm.viscosity(tau)) * (y + 0.5) * (ny - 0.5 - y)
+
+
+def collide_loss_channel(f_pre, y, tau, target, p, gx, node_weight=None):
+    """The channel's form of Eq. 3 followed by Eq. 4 (the training loss of
+    the channel network): with t = tau tau_adj,
+        f_pred = f - (f - f^eq(rho, u))/t + (1 - 1/(2 t)) S(u) + Delta f,
+    u the force-corrected velocity, S = guo_term(u, F); loss = mean over
+    nodes x 9 of (f_pred - target)^2 (times node_weight, if given).
+    tau, gx: scalars or per-node arrays (N,).  d f_pred / d t is
+    ((f - f^eq) + S/2) / t^2.  Returns (loss, dL/dy (N, 10), f_pred (9, N))."""
+    from . import gnn
+    q = f_pre.shape[0]
+    f = np.asarray(f_pre, np.float64).reshape(q, -1)
+    gx = np.broadcast_to(np.asarray(gx, np.float64), f.shape[1:])
+    rho, ux, uy = moments_forced(f, gx)
+    feq = lbm.equilibrium(rho, ux, uy)
+    src = guo_term(ux, uy, gx)
+    t = np.asarray(target, np.float64).reshape(q, -1)
+    tau_adj, df = gnn.heads(y, p)
+    teff = tau * tau_adj
+    f_pred = f - (f - feq) / teff + (1.0 - 0.5 / teff) * src + df
+    n = f.size
+    r = f_pred - t
+    wn = 1.0 if node_weight is None else np.asarray(node_weight, np.float64)[None, :]
+    loss = float(np.sum(wn * r * r) / n)
+    dfs = 2.0 * wn * r / n
+    dy = np.zeros_like(y)
+    dy[:, 1:] = (p["s_df"] * (gnn.conserve(dfs) if p["variant"] & gnn.CONSERVATIVE
+                              else dfs)).T
+    dteff = np.sum(dfs * ((f - feq) + 0.5 * src), axis=0) / (teff * teff)
+    s = gnn.sigmoid(y[:, 0])
+    dy[:, 0] = 0.0 if p["variant"] & gnn.FIXED_TAU else dteff * tau * s * (1.0 - s)
+    return loss, dy, f_pred

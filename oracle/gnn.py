@@ -187,7 +187,8 @@ def forward(f_pre, p, walls=False, force_x=0.0):
     z2 = g1 @ p["enc2.W"].T + p["enc2.b"]
     h = act(z2)
     cache = {"nbr": nbr, "xh": xh, "raw": raw, "z1": z1, "g1": g1, "z2": z2,
-             "h": [h], "edge_in": [], "ze": [], "a": [], "zn": [], "walls": walls}
+             "h": [h], "edge_in": [], "ze": [], "a": [], "zn": [], "walls": walls,
+             "keep": keep}
     for r in range(0 if p["variant"] & MLP_ONLY else ROUNDS):
         We, be = p[f"r{r}.edge.W"], p[f"r{r}.edge.b"]
         Wn, bn = p[f"r{r}.node.W"], p[f"r{r}.node.b"]
@@ -279,9 +280,12 @@ def backward(dy, cache, p):
 
     Returns (grads, d_f_pre): grads maps every trainable name to dL/d(param)
     in FP64 (w.r.t. the effective, already rounded values); d_f_pre is
-    dL/d f_pre (9, N) through the features (f_i, rho, u).  (Periodic graph,
-    no body force: the forward's defaults.)"""
-    assert not cache.get("walls"), "backward of the channel graph is not defined here"
+    dL/d f_pre (9, N) through the features (f_i, rho, u).  On the channel's
+    graph (forward with walls) an edge that the forward left out of the sum
+    passes no gradient; with a body force the velocity feature is
+    (j + F/2)/rho, whose derivative w.r.t. f_i is (e_i - u)/rho with that u
+    (cache "raw" holds it)."""
+    keep = cache.get("keep")
     g = {}
     nbr = cache["nbr"]
     h = cache["h"][-1]
@@ -303,6 +307,8 @@ def backward(dy, cache, p):
         gbe = np.zeros(HID)
         for kk, k in enumerate(range(1, lbm.Q)):
             dze = da * gelu_grad(cache["ze"][r][kk])
+            if keep is not None:
+                dze = dze * keep[:, k:k + 1]
             gWe += dze.T @ cache["edge_in"][r][kk]
             gbe += dze.sum(axis=0)
             dinp = dze @ We

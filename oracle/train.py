@@ -18,6 +18,11 @@ Readings where the paper is silent:
         f_neq_f = (f*_f - f^eq) / (1 - 1/tau_f),
     rescaled to the coarse lattice, f_neq_c = m (tau_c / tau_f) f_neq_f, and
     the coarse post-collision state is f*_c = f^eq + (1 - 1/tau_c) f_neq_c.
+  * Channel (forced) data: an odd factor m (3) so that fine and coarse nodes
+    coincide with the walls halfway beyond the outer rows, the force scaled
+    as F_f = F_c / m, and the restriction of ``restrict_forced``, which
+    separates the force part of the non-equilibrium populations from the
+    gradient part and works from the pre-collision state.
   * A training pair is (restricted state at coarse step n, at step n+1); the
     prediction is one GNN-LBM coarse step on the first element.
   * The optimiser (unnamed in the paper) is AdamW with decoupled weight decay
@@ -41,6 +46,52 @@ def restrict(f_fine, m, tau_f, tau_c):
     fneq_f = (sub - feq) / (1.0 - 1.0 / tau_f)
     fneq_c = m * (tau_c / tau_f) * fneq_f
     return feq + (1.0 - 1.0 / tau_c) * fneq_c
+
+
+def restrict_forced(f_pre_fine, m, tau_f, tau_c, gx_f):
+    """Restrict a fine channel state, given PRE-collision (9, m ny, m nx),
+    to the coarse post-collision state at the same time (readings for a
+    forced flow, Sec. 2.4 with Sec. 3.1):
+      * m odd; coarse node (I, J) coincides with fine node (m I + (m-1)/2,
+        m J + (m-1)/2), so both lattices put their walls halfway beyond the
+        outer rows;
+      * the force per unit volume scales as F_f = F_c / m (same lattice
+        velocity with nu_f = m nu_c on an m-times wider channel);
+      * the non-equilibrium part of the pre-collision state splits into a
+        gradient part G = -tau D f^eq, which scales to the coarse lattice by
+        m tau_c / tau_f, and a force part P = (tau - 1/2) w_i [3 (e_i - u) +
+        9 (e_i . u) e_i] . F, which is the same in both lattices' units;
+      * the coarse post-collision state is
+            f*_c = f^eq + (1 - 1/tau_c) m (tau_c / tau_f) G + P.
+    The pre-collision state is used because the post-collision one holds
+    (1 - 1/tau_f) G, whose inversion fails at tau_f = 1."""
+    from . import channel
+    assert m % 2 == 1, "co-located nodes need an odd refinement factor"
+    o = (m - 1) // 2
+    sub = np.asarray(f_pre_fine, np.float64)[:, o::m, o::m]
+    rho, ux, uy = channel.moments_forced(sub, gx_f)
+    feq = lbm.equilibrium(rho, ux, uy)
+    pf = (tau_f - 0.5) * channel.guo_term(ux, uy, gx_f)
+    g = sub - feq - pf
+    return feq + (1.0 - 1.0 / tau_c) * m * (tau_c / tau_f) * g + pf
+
+
+def channel_pair(ny_c, nx_c, tau_c, gx_c, n_steps, m=3, f0_fine=None):
+    """One training pair on an ny_c x nx_c coarse channel (force gx_c): the
+    fine channel (m ny_c x m nx_c, tau_f, F_c / m) runs from f0_fine (rest
+    when None) for m n_steps - 1 steps; its pull with the walls is the
+    pre-collision state at coarse step n, restricted to f_in; m more fine
+    steps give the target.  Returns (f_in, f_target)."""
+    from . import channel
+    tau_f = fine_tau(tau_c, m)
+    gx_f = gx_c / m
+    f = (lbm.equilibrium(np.ones((m * ny_c, m * nx_c)), np.zeros((m * ny_c, m * nx_c)),
+                         np.zeros((m * ny_c, m * nx_c)))
+         if f0_fine is None else np.asarray(f0_fine, np.float64))
+    f = channel.channel_run(f, tau_f, gx_f, m * n_steps - 1)
+    f_in = restrict_forced(channel.stream_pull_walls(f), m, tau_f, tau_c, gx_f)
+    f = channel.channel_run(f, tau_f, gx_f, m)
+    return f_in, restrict_forced(channel.stream_pull_walls(f), m, tau_f, tau_c, gx_f)
 
 
 def tgv_pair(n_c, u0, k_mult, tau_c, n_steps, m=4):

@@ -125,3 +125,85 @@ def test_gnn_channel_step_commutes_with_x_shifts():
     a = np.roll(channel.gnn_channel_step(f, th, 0.75, 1e-4), 2, axis=2)
     b = channel.gnn_channel_step(np.roll(f, 2, axis=2), th, 0.75, 1e-4)
     assert np.allclose(a, b, rtol=1e-13, atol=1e-16)
+
+
+def test_walled_backward_matches_central_differences():
+    """Reverse mode on the channel's graph with a body force (edges across
+    the walls left out, forced velocity feature) vs central differences in
+    FP64: directional derivatives of every tensor and of the inputs."""
+    from oracle import gnn
+    nx, ny = 3, 4
+    p = gnn.unpack(_net(21, s_df=1e-2))
+    rng = np.random.default_rng(22)
+    f = lbm.equilibrium(np.ones((ny, nx)), np.full((ny, nx), 0.03), np.zeros((ny, nx)))
+    f = f * (1 + 3e-2 * rng.standard_normal(f.shape))
+    gx = 2e-3
+    dy = rng.standard_normal((nx * ny, 10))
+    J = lambda pp, ff: float(np.sum(dy * gnn.forward(ff, pp, walls=True, force_x=gx)[0]))
+    _, cache = gnn.forward(f, p, walls=True, force_x=gx)
+    g, df = gnn.backward(dy, cache, p)
+    h = 1e-6
+    for name, shape in gnn.SHAPES:
+        d = rng.standard_normal(shape)
+        q1, q2 = dict(p), dict(p)
+        q1[name] = p[name] + h * d
+        q2[name] = p[name] - h * d
+        fd = (J(q1, f) - J(q2, f)) / (2 * h)
+        an = float(np.sum(g[name] * d))
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (name, fd, an)
+    d = rng.standard_normal(f.shape) * 1e-2
+    hf = 1e-5
+    fd = (J(p, f + hf * d) - J(p, f - hf * d)) / (2 * hf)
+    an = float(np.sum(df * d.reshape(9, -1)))
+    assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+    # the periodic graph's gradient differs: the mask is in effect
+    _, cache_p = gnn.forward(f, p, walls=False, force_x=gx)
+    gp, _ = gnn.backward(dy, cache_p, p)
+    assert np.abs(gp["r0.edge.W"] - g["r0.edge.W"]).max() > 1e-3 * np.abs(g["r0.edge.W"]).max()
+
+
+def test_channel_loss_gradient_matches_central_differences():
+    """The channel loss (Eq. 3 with Guo's source at tau tau_adj, Eq. 4):
+    dL/dy vs central differences, per-node tau and force."""
+    from oracle import gnn
+    nx, ny = 4, 3
+    p = gnn.unpack(_net(23, s_df=1e-3))
+    rng = np.random.default_rng(24)
+    f = _rest(ny, nx) * (1 + 2e-2 * rng.standard_normal((9, ny, nx)))
+    target = _rest(ny, nx) * (1 + 2e-2 * rng.standard_normal((9, ny, nx)))
+    y = rng.standard_normal((nx * ny, 10))
+    taus = 0.55 + 0.4 * rng.random(nx * ny)
+    gx = 1e-3 * (1 + rng.random(nx * ny))
+    loss, dy, _ = channel.collide_loss_channel(f, y, taus, target, p, gx)
+    L = lambda yy: channel.collide_loss_channel(f, yy, taus, target, p, gx)[0]
+    h = 1e-6
+    for _ in range(30):
+        n, c = int(rng.integers(nx * ny)), int(rng.integers(10))
+        yp, ym = y.copy(), y.copy()
+        yp[n, c] += h
+        ym[n, c] -= h
+        fd = (L(yp) - L(ym)) / (2 * h)
+        assert abs(fd - dy[n, c]) <= 1e-6 * abs(dy[n, c]) + 1e-14, (n, c, fd, dy[n, c])
+
+
+def test_channel_loss_special_cases():
+    """Zero network: the prediction is the BGK channel collision, so on the
+    pulled state it equals one channel step; without force the loss is the
+    periodic one (Eq. 3 + Eq. 4)."""
+    from oracle import gnn
+    from paper_2504_14494_gb300 import inputs
+    rng = np.random.default_rng(25)
+    fpost = _rest(5, 4) * (1 + 1e-2 * rng.standard_normal((9, 5, 4)))
+    target = _rest(5, 4) * (1 + 1e-2 * rng.standard_normal((9, 5, 4)))
+    p0 = gnn.unpack(inputs.zero_params())
+    fpre = channel.stream_pull_walls(fpost)
+    loss, dy, pred = channel.collide_loss_channel(fpre, np.zeros((20, 10)), 0.8, target, p0, 3e-4)
+    step = channel.channel_step(fpost, 0.8, 3e-4)
+    assert np.allclose(pred.reshape(9, 5, 4), step, rtol=0, atol=1e-16)
+    assert abs(loss - np.mean((step - target) ** 2)) < 1e-18
+    p = gnn.unpack(_net(26, s_df=1e-3))
+    y = rng.standard_normal((20, 10))
+    a = channel.collide_loss_channel(fpre, y, 0.7, target, p, 0.0)
+    b = gnn.collide_loss(fpre, y, 0.7, target, p)
+    assert abs(a[0] - b[0]) <= 1e-15 * b[0]
+    assert np.allclose(a[1], b[1], rtol=1e-13, atol=1e-20)

@@ -95,3 +95,123 @@ def test_adamw_first_step_closed_form():
     th = np.array([1.0, -1.0, 0.5, 2.0])
     out, _, _ = train.adamw_step(th, g, np.zeros(4), np.zeros(4), 1, 1e-2, 0.1)
     assert np.allclose(out, th * (1 - 1e-3) - 1e-2 * g / (np.abs(g) + 1e-8), rtol=1e-14, atol=1e-16)
+
+
+# ---- the forced (channel) restriction ---------------------------------------------
+def _accelerating(tau, g, n, shape=(3, 3), u0=0.02, v0=0.01):
+    """A uniform flow under a uniform force, n LBM steps with Guo's scheme
+    (streaming is the identity on a uniform state).  Starts at time-level
+    velocity (u0, v0): the stored post-collision state carries j = rho u + F/2."""
+    from oracle import channel
+    f = lbm.equilibrium(np.ones(shape), np.full(shape, u0 + g / 2), np.full(shape, v0))
+    for _ in range(n):
+        rho, ux, uy = channel.moments_forced(f, g)
+        f = f - (f - lbm.equilibrium(rho, ux, uy)) / tau + channel.guo_source(ux, uy, tau, g)
+    return f
+
+
+@pytest.mark.parametrize("tau_c", [0.55, 0.6, 0.9, 1.3])
+def test_restrict_forced_accelerating_flow_is_the_coarse_state(tau_c):
+    """A uniformly accelerated flow is the same physical flow on both
+    lattices: the fine pre-collision state after 3n steps (F/3, tau_f)
+    restricts to the coarse lattice's own state after n steps (F, tau_c) to
+    round-off, although its non-equilibrium part is all force and time
+    derivative; the force part taken as gradient part, dropped, scaled by m
+    or the gradient scale without its m all miss by over 10 %."""
+    from oracle import channel
+    m, gc, nc = 3, 2e-4, 60
+    tf, gf = train.fine_tau(tau_c, m), gc / m
+    fc = _accelerating(tau_c, gc, nc)
+    fpre = _accelerating(tf, gf, m * nc - 1)   # = the pull of the stored state
+    r = train.restrict_forced(fpre, m, tf, tau_c, gf)
+    rho, jx, uy = lbm.moments(fc)
+    scale = np.abs(fc - lbm.equilibrium(rho, jx - gc / 2 / rho, uy)).max()
+    assert np.abs(r - fc).max() < 1e-7 * scale
+    sub = fpre[:, 1::3, 1::3]
+    rr, a, b = channel.moments_forced(sub, gf)
+    fe = lbm.equilibrium(rr, a, b)
+    pf = (tf - 0.5) * channel.guo_term(a, b, gf)
+    k = (1 - 1 / tau_c) * m * tau_c / tf
+    for wrong in (fe + k * (sub - fe), fe + k * (sub - fe - pf),
+                  fe + k * (sub - fe - pf) + m * pf,
+                  fe + (k / m) * (sub - fe - pf) + pf):
+        assert np.abs(wrong - fc).max() > 0.1 * scale
+
+
+def test_restrict_forced_without_force_is_the_post_collision_restriction():
+    """F = 0: restricting the pre-collision state equals restricting the
+    post-collision state that one BGK collision makes of it (the periodic
+    reading), with the fine node (3I + 1, 3J + 1) as the co-located one."""
+    rng = np.random.default_rng(31)
+    fpre = lbm.tgv_init(9, 12, 1.0, 0.04, 2 * np.pi / 9, 2 * np.pi / 12)
+    fpre = fpre * (1 + 1e-2 * rng.standard_normal(fpre.shape))
+    tau_c = 0.8
+    tf = train.fine_tau(tau_c, 3)
+    post = lbm.bgk_collide(fpre, tf)
+    a = train.restrict_forced(fpre, 3, tf, tau_c, 0.0)
+    b = train.restrict(np.roll(post, (-1, -1), axis=(1, 2)), 3, tf, tau_c)
+    assert a.shape == (9, 4, 3)
+    assert np.allclose(a, b, rtol=0, atol=1e-15)
+
+
+def test_restrict_forced_injects_forced_moments():
+    """rho is injected and the coarse state's time-level velocity
+    (sum f* e - F_c/2) / rho equals the fine node's forced velocity, with
+    F_c = 3 F_f."""
+    from oracle import channel
+    rng = np.random.default_rng(32)
+    f = lbm.equilibrium(np.ones((6, 9)), np.full((6, 9), 0.02), np.zeros((6, 9)))
+    f = channel.channel_run(f * (1 + 1e-2 * rng.standard_normal(f.shape)), 0.9, 1e-4, 5)
+    fpre = channel.stream_pull_walls(f)
+    c = train.restrict_forced(fpre, 3, 0.9, 0.6333333333333333, 1e-4)
+    rho_f, ux_f, uy_f = channel.moments_forced(fpre[:, 1::3, 1::3], 1e-4)
+    rho_c, jx, jy = lbm.moments(c)
+    assert np.allclose(rho_c, rho_f, rtol=1e-14, atol=0)
+    assert np.allclose(jx - 1.5e-4 / rho_c, ux_f, rtol=0, atol=1e-15)
+    assert np.allclose(jy, uy_f, rtol=0, atol=1e-15)
+
+
+def test_restrict_forced_steady_channel_converges_at_second_order():
+    """The steady channel on a 3x finer lattice, restricted, approaches the
+    coarse lattice's steady channel as H grows: the gap in the
+    non-equilibrium part shrinks at second order (the wall slip's order)."""
+    from oracle import channel
+
+    def steady(ny, nx, tau, g):
+        f = lbm.equilibrium(np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+        return channel.channel_run(f, tau, g, int(14 * ny * ny / (np.pi ** 2 * lbm.viscosity(tau))) + 300)
+
+    def neq(f, g):
+        rho, jx, jy = lbm.moments(f)
+        return f - lbm.equilibrium(rho, jx - g / 2 / rho, jy)
+
+    tau_c, umax = 0.6, 0.02
+    gaps = []
+    for h in (4, 8):
+        gc = 8 * lbm.viscosity(tau_c) * umax / h ** 2
+        tf = train.fine_tau(tau_c, 3)
+        fc = steady(h, 1, tau_c, gc)
+        ff = steady(3 * h, 3, tf, gc / 3)
+        r = train.restrict_forced(channel.stream_pull_walls(ff), 3, tf, tau_c, gc / 3)
+        a = neq(fc, gc)
+        gaps.append(np.abs(neq(r, gc) - a).max() / np.abs(a).max())
+    assert gaps[0] < 0.02 and 3.5 < gaps[0] / gaps[1] < 4.5, gaps
+
+
+def test_channel_pair_is_close_to_one_coarse_channel_step():
+    """A restricted channel pair (start-up from rest) is consistent with the
+    coarse lattice away from the walls: one coarse BGK channel step from the
+    input lands near the target in the interior rows, over 10x nearer than
+    the input itself; in the rows next to the walls the coarse step misses
+    by the difference between the two lattices' bounce-back slips (the
+    error a trained collision can remove)."""
+    from oracle import channel
+    tau_c, ny, nx = 0.7, 8, 2
+    gc = 8 * lbm.viscosity(tau_c) * 0.03 / ny ** 2
+    f_in, f_tg = train.channel_pair(ny, nx, tau_c, gc, 30)
+    assert f_in.shape == f_tg.shape == (9, ny, nx)
+    step = channel.channel_step(f_in, tau_c, gc)
+    inner = slice(1, ny - 1)
+    err = np.abs(step - f_tg)[:, inner].max()
+    assert err < 0.1 * np.abs(f_in - f_tg)[:, inner].max()
+    assert np.abs(step - f_tg)[:, [0, ny - 1]].max() > 10 * err
