@@ -338,6 +338,29 @@ LBM_API int lbm_restrict(const float* f_fine, lbm_shape fine, float* f_coarse, l
                          int factor, float tau_f, const float* taus_f, float tau_c,
                          const float* taus_c, void* stream);
 
+/* Restriction of an m-times refined CHANNEL (Sec. 3.1 flow, lbm_step_channel
+ * geometry; training data of Sec. 2.4 for the channel network; the scheme is
+ * this library's reading): m odd, fine = (m nx, m ny, nb) of coarse; coarse
+ * node (X, Y) of lattice b sits where fine node (m X + (m-1)/2,
+ * m Y + (m-1)/2) does, so both lattices put the walls halfway beyond their
+ * outer rows.  f_fine is the fine STORED state one fine step before the
+ * sampled time: the fine node's populations are pulled from it with the
+ * walls (its pre-collision state at the sampled time).  With the fine force
+ * F_f = (force_x_f, 0) (forces_x_f: device FP32 [nb] per lattice, else NULL;
+ * the coarse force is m F_f), u = (sum f e + F_f/2)/rho:
+ *   P   = (tau_f - 1/2) w_i [3 (e_i - u) + 9 (e_i . u) e_i] . F_f  (force part,
+ *         equal in both lattices' units),
+ *   G   = f - f^eq(rho, u) - P                          (gradient part),
+ *   f*_c = f^eq + (1 - 1/tau_c) m (tau_c / tau_f) G + P,
+ * the coarse post-collision state at the sampled time.  tau_f / taus_f and
+ * tau_c / taus_c as in lbm_restrict.  Errors: LBM_ERR_ARG (NULL buffer, even
+ * or non-positive factor, non-finite scalar force), LBM_ERR_SIZE,
+ * LBM_ERR_TAU, LBM_ERR_ALIAS (f_fine and f_coarse overlap). */
+LBM_API int lbm_restrict_channel(const float* f_fine, lbm_shape fine, float* f_coarse,
+                                 lbm_shape coarse, int factor, float tau_f, const float* taus_f,
+                                 float tau_c, const float* taus_c, float force_x_f,
+                                 const float* forces_x_f, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Training (Sec. 2.4, Eq. 4)
  * ------------------------------------------------------------------------- */
@@ -415,6 +438,21 @@ LBM_API int gnn_train_step_weighted(const float* f_in, const float* f_target, lb
                                     int64_t step, float lr, float wd, double* loss,
                                     float* grads, void* workspace, size_t ws_bytes,
                                     void* stream);
+
+/* gnn_train_step for the channel network (Sec. 3.1 flow): the prediction is
+ * one lbm_step_gnn_channel step of f_in (pull with halfway bounce-back,
+ * network on the walled graph with the forced velocity feature, Eq. 3 with
+ * Guo's source at tau tau_adj), with force (force_x, 0), or (forces_x[b], 0)
+ * per lattice when forces_x (device FP32 [nb]) is not NULL; lat_weights:
+ * per-lattice loss weights (as gnn_train_step_weighted) or NULL for Eq. 4.
+ * Workspace: gnn_train_workspace_bytes(s).  Other arguments and results as
+ * gnn_train_step; LBM_ERR_ARG also for a non-finite scalar force. */
+LBM_API int gnn_train_step_channel(const float* f_in, const float* f_target, lbm_shape s,
+                                   float tau, const float* taus, float force_x,
+                                   const float* forces_x, const float* lat_weights, float* params,
+                                   void* packed, float* adam_m, float* adam_v, int64_t step,
+                                   float lr, float wd, double* loss, float* grads,
+                                   void* workspace, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Batched runs of many lattices of uneven size (serving-style workload)

@@ -226,7 +226,12 @@ int lbm_step_gnn_channel(const float* f_in, float* f_out, lbm_shape shape, float
   if (totals && cudaMemsetAsync(totals, 0, 5 * sizeof(double), st) != cudaSuccess)
     return LBM_ERR_CUDA;
   if (launch_channel_pull(f_in, f_pre, s, st) != cudaSuccess) return LBM_ERR_CUDA;
-  if (launch_gnn_forward_channel(f_pre, s, force_x, pk, h0, ab0, h1, ab1, y, st) != cudaSuccess)
+  ChannelSaved sv;
+  sv.h0 = h0;
+  sv.ab0 = ab0;
+  sv.h1 = h1;
+  sv.ab1 = ab1;
+  if (launch_gnn_forward_channel(f_pre, s, force_x, nullptr, pk, sv, y, st) != cudaSuccess)
     return LBM_ERR_CUDA;
   if (launch_channel_gnn_collide(f_pre, y, f_out, s, tau, taus, force_x, pk, totals, st) !=
       cudaSuccess)

@@ -193,16 +193,24 @@ size_t gnn_train_workspace_bytes(lbm_shape shape) {
 }  // extern "C"
 
 namespace {
-// The fused training step; lw: per-lattice loss weights or NULL (Eq. 4).
+// The channel's force of a training step: (fx, 0), or (fxs[b], 0) per lattice.
+struct ChannelForce {
+  float fx;
+  const float* fxs;
+};
+
+// The fused training step; lw: per-lattice loss weights or NULL (Eq. 4); ch:
+// the channel (walled graph, Guo forcing) or NULL (periodic lattices).
 int train_step(const float* f_in, const float* f_target, lbm_shape shape, float tau,
                const float* taus, const float* lw, float* params, void* packed, float* adam_m,
                float* adam_v, int64_t step, float lr, float wd, double* loss, float* grads,
-               void* workspace, size_t ws_bytes, void* stream) {
+               void* workspace, size_t ws_bytes, void* stream, const ChannelForce* ch = nullptr) {
   Shape s;
   if (!f_in || !f_target || !params || !packed || !adam_m || !adam_v || !loss || step < 1)
     return LBM_ERR_ARG;
   if (int r = check_shape_t(shape, &s)) return r;
   if (!taus && (!std::isfinite(tau) || !(tau > 0.5f))) return LBM_ERR_TAU;
+  if (ch && !ch->fxs && !std::isfinite(ch->fx)) return LBM_ERR_ARG;
   if (!aligned16(packed)) return LBM_ERR_ARG;
   const int64_t N = nodes(s);
   if (!workspace || (int64_t)ws_bytes < train_ws(s) || !aligned16(workspace))
@@ -224,12 +232,31 @@ int train_step(const float* f_in, const float* f_target, lbm_shape shape, float 
   w += bwd_ws(N);
   float* g = grads ? grads : reinterpret_cast<float*>(w);
 
-  if (launch_stream(f_in, f_pre, s, st) != cudaSuccess) return LBM_ERR_CUDA;
-  if (int r = gnn_forward(f_pre, shape, packed, saved, y, stream)) return r;
   int nblk = 0;
-  if (launch_collide_loss(f_pre, y, f_target, s, tau, taus, pk, lossp, &nblk, dy, nullptr, st,
-                          lw) != cudaSuccess)
-    return LBM_ERR_CUDA;
+  if (!ch) {
+    if (launch_stream(f_in, f_pre, s, st) != cudaSuccess) return LBM_ERR_CUDA;
+    if (int r = gnn_forward(f_pre, shape, packed, saved, y, stream)) return r;
+    if (launch_collide_loss(f_pre, y, f_target, s, tau, taus, pk, lossp, &nblk, dy, nullptr, st,
+                            lw) != cudaSuccess)
+      return LBM_ERR_CUDA;
+  } else {
+    // the saved activations in gnn_forward's layout (set_saved)
+    auto* sb = static_cast<__nv_bfloat16*>(saved);
+    ChannelSaved sv;
+    sv.h0 = sb;
+    sv.h1 = sb + N * 64;
+    sv.h2 = sb + 2 * N * 64;
+    sv.a0 = sb + 3 * N * 64;
+    sv.a1 = sb + 4 * N * 64;
+    sv.ab0 = reinterpret_cast<__half*>(sb + 5 * N * 64);
+    sv.ab1 = sv.ab0 + N * 128;
+    if (launch_channel_pull(f_in, f_pre, s, st) != cudaSuccess) return LBM_ERR_CUDA;
+    if (launch_gnn_forward_channel(f_pre, s, ch->fx, ch->fxs, pk, sv, y, st) != cudaSuccess)
+      return LBM_ERR_CUDA;
+    if (launch_collide_loss_channel(f_pre, y, f_target, s, tau, taus, ch->fx, ch->fxs, pk, lossp,
+                                    &nblk, dy, nullptr, st, lw) != cudaSuccess)
+      return LBM_ERR_CUDA;
+  }
   if (launch_loss_finish(lossp, nblk, 9.0 * (double)N, loss, st) != cudaSuccess)
     return LBM_ERR_CUDA;
   BackwardLaunch bl;
@@ -238,6 +265,11 @@ int train_step(const float* f_in, const float* f_target, lbm_shape shape, float 
   set_saved(saved, N, bl);
   carve_bwd(bws, N, bl);
   bl.grad = g;
+  if (ch) {
+    bl.walls = true;
+    bl.fx = ch->fx;
+    bl.fxs = ch->fxs;
+  }
   if (launch_gnn_backward(bl, s, pk, st) != cudaSuccess) return LBM_ERR_CUDA;
   if (int r = gnn_adamw(params, g, adam_m, adam_v, step, lr, wd, 0.9f, 0.999f, 1e-8f, stream))
     return r;
@@ -265,6 +297,40 @@ int gnn_train_step_weighted(const float* f_in, const float* f_target, lbm_shape 
   if (!lat_weights) return LBM_ERR_ARG;
   return train_step(f_in, f_target, shape, tau, taus, lat_weights, params, packed, adam_m,
                     adam_v, step, lr, wd, loss, grads, workspace, ws_bytes, stream);
+}
+
+int gnn_train_step_channel(const float* f_in, const float* f_target, lbm_shape shape, float tau,
+                           const float* taus, float force_x, const float* forces_x,
+                           const float* lat_weights, float* params, void* packed, float* adam_m,
+                           float* adam_v, int64_t step, float lr, float wd, double* loss,
+                           float* grads, void* workspace, size_t ws_bytes, void* stream) {
+  LBM_TRACE("gnn_train_step_channel");
+  const ChannelForce ch{force_x, forces_x};
+  return train_step(f_in, f_target, shape, tau, taus, lat_weights, params, packed, adam_m, adam_v,
+                    step, lr, wd, loss, grads, workspace, ws_bytes, stream, &ch);
+}
+
+int lbm_restrict_channel(const float* f_fine, lbm_shape fine, float* f_coarse, lbm_shape coarse,
+                         int factor, float tau_f, const float* taus_f, float tau_c,
+                         const float* taus_c, float force_x_f, const float* forces_x_f,
+                         void* stream) {
+  LBM_TRACE("lbm_restrict_channel");
+  Shape fs, cs;
+  if (!f_fine || !f_coarse || factor < 1 || factor % 2 == 0) return LBM_ERR_ARG;
+  if (!forces_x_f && !std::isfinite(force_x_f)) return LBM_ERR_ARG;
+  if (int r = check_shape_t(fine, &fs)) return r;
+  if (int r = check_shape_t(coarse, &cs)) return r;
+  if (fs.nb != cs.nb || (int64_t)fs.nx != (int64_t)factor * cs.nx ||
+      (int64_t)fs.ny != (int64_t)factor * cs.ny)
+    return LBM_ERR_SIZE;
+  if (!taus_f && (!std::isfinite(tau_f) || !(tau_f > 0.5f))) return LBM_ERR_TAU;
+  if (!taus_c && (!std::isfinite(tau_c) || !(tau_c > 0.5f))) return LBM_ERR_TAU;
+  if (overlap(f_fine, f_bytes(fs), f_coarse, f_bytes(cs))) return LBM_ERR_ALIAS;
+  return launch_channel_restrict(f_fine, fs, f_coarse, cs, factor, tau_f, taus_f, tau_c, taus_c,
+                                 force_x_f, forces_x_f, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? LBM_OK
+             : LBM_ERR_CUDA;
 }
 
 size_t lbm_pair_weights_workspace_bytes(lbm_shape shape) {

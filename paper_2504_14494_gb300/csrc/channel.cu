@@ -15,6 +15,7 @@
 // the correction Delta f.
 #include "common.cuh"
 #include "gnn.cuh"
+#include "gnn_launch.h"
 #include "launch.h"
 
 namespace lbmgnn {
@@ -194,6 +195,58 @@ __global__ void __launch_bounds__(256) channel_gnn_collide_kernel(
     for (int q = 0; q < Q; ++q) fout[q * s.ps + i.nn] = f[q];
   }
   if constexpr (TOTALS) channel_totals(f, i.on, totals, stw);
+}
+
+// ---- restriction of a refined channel --------------------------------------------
+
+// Coarse node (b, J, I) <- fine node (b, m J + (m-1)/2, m I + (m-1)/2) (odd
+// m: both lattices' walls lie halfway beyond their outer rows).  The fine
+// node's populations are pulled from the fine stored state with the walls
+// (its pre-collision state of the next step), and with u = (j + F_f/2)/rho,
+//   P = (tau_f - 1/2) w_i [3 (e_i - u) + 9 (e_i.u) e_i].F_f   (force part),
+//   G = f - f^eq - P                                          (gradient part),
+//   f*_c = f^eq + (1 - 1/tau_c) m (tau_c / tau_f) G + P.
+__global__ void __launch_bounds__(256) channel_restrict_kernel(
+    const float* __restrict__ ff, Shape fs, float* __restrict__ fc, Shape cs, int m, float tau_f,
+    const float* __restrict__ taus_f, float tau_c, const float* __restrict__ taus_c, float gx_f,
+    const float* __restrict__ gxs_f, unsigned* stw) {
+  const NodeIdx c = node_idx(cs);
+  if (!c.on) return;
+  const int o = (m - 1) / 2;
+  const int xf = m * c.x + o, yf = m * c.y + o;
+  const int64_t latf = (int64_t)c.b * fs.ny * fs.nx;
+  const int64_t nf = latf + (int64_t)yf * fs.nx + xf;
+  float f[Q];
+  channel_pull(ff, fs, nf, xf, yf, latf, f, stw);
+  const float tf = taus_f ? __ldg(taus_f + c.b) : tau_f;
+  const float tc = taus_c ? __ldg(taus_c + c.b) : tau_c;
+  const float gx = gxs_f ? __ldg(gxs_f + c.b) : gx_f;
+  const float rho = ((f[0] + (f[1] + f[3])) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8]));
+  const float jx = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
+  const float jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+  const float inv = 1.0f / rho;
+  const Moments mo{rho, (jx + 0.5f * gx) * inv, jy * inv};
+  const float usq15 = 1.5f * (mo.ux * mo.ux + mo.uy * mo.uy);
+  const float kg = (1.0f - 1.0f / tc) * (float)m * (tc / tf), kp = tf - 0.5f;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const float fe = feq_i(q, mo, usq15);
+    const float eu = float(ex(q)) * mo.ux + float(ey(q)) * mo.uy;
+    const float p = kp * wq(q) * (3.0f * (float(ex(q)) - mo.ux) + 9.0f * eu * float(ex(q))) * gx;
+    fc[q * cs.ps + c.n] = fe + kg * ((f[q] - fe) - p) + p;
+  }
+}
+
+cudaError_t launch_channel_restrict(const float* f_fine, const Shape& fs, float* f_coarse,
+                                    const Shape& cs, int m, float tau_f, const float* taus_f,
+                                    float tau_c, const float* taus_c, float gx_f,
+                                    const float* gxs_f, cudaStream_t st) {
+  unsigned* stw = status_word();
+  if (!stw) return cudaErrorInvalidDevice;
+  const int64_t N = (int64_t)cs.nb * cs.ny * cs.nx;
+  channel_restrict_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(
+      f_fine, fs, f_coarse, cs, m, tau_f, taus_f, tau_c, taus_c, gx_f, gxs_f, stw);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_channel_pull(const float* fin, float* fpre, const Shape& s, cudaStream_t st) {

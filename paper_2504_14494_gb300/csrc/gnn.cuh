@@ -515,20 +515,23 @@ struct GeoStack {
     return taus ? taus + p.b : nullptr;
   }
   __device__ __forceinline__ bool inside(const GeoPos&, int) const { return true; }
-  __device__ __forceinline__ float force_x() const { return 0.0f; }
+  __device__ __forceinline__ float force_x(const GeoPos&) const { return 0.0f; }
 };
 
 // A stack of channels (Sec. 3.1): periodic in x, walls halfway beyond the
-// first and last rows of every lattice, a body force (force_x, 0).  The
-// network's graph stops at the walls: a neighbour x + e_k exists only if its
-// row lies inside the channel.
+// first and last rows of every lattice, a body force (fx, 0), or (fxs[b], 0)
+// per lattice b when fxs is set.  The network's graph stops at the walls: a
+// neighbour x + e_k exists only if its row lies inside the channel.
 struct GeoChannel : GeoStack {
   static constexpr bool kWalls = true;
   float fx;
+  const float* fxs;
   __device__ __forceinline__ bool inside(const GeoPos& p, int dy) const {
     return (unsigned)(p.y + dy) < (unsigned)p.ny;
   }
-  __device__ __forceinline__ float force_x() const { return fx; }
+  __device__ __forceinline__ float force_x(const GeoPos& p) const {
+    return fxs ? __ldg(fxs + p.b) : fx;
+  }
 };
 
 // One lattice of a batched run: first node in the packed buffers, size and
@@ -585,7 +588,7 @@ struct GeoTable {
     return &lat[p.b].tau;
   }
   __device__ __forceinline__ bool inside(const GeoPos&, int) const { return true; }
-  __device__ __forceinline__ float force_x() const { return 0.0f; }
+  __device__ __forceinline__ float force_x(const GeoPos&) const { return 0.0f; }
 };
 
 // The dynamic shared-memory block aligned up to 1024 bytes (the SW128

@@ -109,9 +109,15 @@ __device__ __forceinline__ void st_f32x32(float* p, const float* v) {
 // Eq. 3 followed by Eq. 4: per node f_pred = f - (f - f_eq)/(tau tau_adj) +
 // s_df y_1..9, squared error against the target, and dL/dy.  The loss is the
 // mean over nodes x 9 of the whole stack.  One thread per node.
+// FORCED (the channel): a force (gx, 0) per unit volume (gxs[b] per lattice
+// when set) enters by Guo's scheme, u = (sum f e + F/2)/rho and the source
+// (1 - 1/(2t)) S with S_i = w_i [3 (e_ix - u_x) + 9 (e_i.u) e_ix] gx at the
+// network's time t; d f_pred / d t = ((f - f_eq) + S/2) / t^2.
+template <bool FORCED>
 __global__ void __launch_bounds__(256) gnn_collide_loss_kernel(
     const float* __restrict__ f_pre, const float* __restrict__ y, const float* __restrict__ tgt,
-    Shape s, float tau, const float* __restrict__ taus, const uint8_t* __restrict__ packed,
+    Shape s, float tau, const float* __restrict__ taus, float gx0,
+    const float* __restrict__ gxs, const uint8_t* __restrict__ packed,
     double* __restrict__ lossp, float* __restrict__ dy, float* __restrict__ f_pred,
     const float* __restrict__ lw, unsigned* stw) {
   if (!blob_ok(packed, stw)) {  // no loss from an invalid image: NaN
@@ -132,7 +138,12 @@ __global__ void __launch_bounds__(256) gnn_collide_loss_kernel(
   const int64_t b = nn / ((int64_t)s.nx * s.ny);
   const float t = taus ? __ldg(taus + b) : tau;
   const float wb = lw ? __ldg(lw + b) : 1.0f;  // per-instance loss weight (1: Eq. 4)
-  const Moments m = moments9(fv);
+  Moments m = moments9(fv);
+  float gx = 0.0f;
+  if constexpr (FORCED) {
+    gx = gxs ? __ldg(gxs + b) : gx0;
+    m.ux += 0.5f * gx / m.rho;
+  }
   const float usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy);
   const bool fixed_tau = variant & VAR_FIXED_TAU;
   const float sg = sigmoid_acc(yv[0]);
@@ -147,11 +158,18 @@ __global__ void __launch_bounds__(256) gnn_collide_loss_kernel(
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const float fe = feq_i(q, m, usq15);
-    const float fp = fv[q] - (fv[q] - fe) * inv + d[q];
+    float fp = fv[q] - (fv[q] - fe) * inv + d[q];
+    float dt = fv[q] - fe;  // t^2 d f_pred / d t
+    if constexpr (FORCED) {
+      const float eu = float(ex(q)) * m.ux + float(ey(q)) * m.uy;
+      const float src = wq(q) * (3.0f * (float(ex(q)) - m.ux) + 9.0f * eu * float(ex(q))) * gx;
+      fp += (1.0f - 0.5f * inv) * src;
+      dt += 0.5f * src;
+    }
     const float r = fp - __ldg(tgt + q * s.ps + nn);
     lp += (double)wb * (double)r * (double)r;
     g[q] = scale * r;  // dL/df*
-    dta += g[q] * (fv[q] - fe);
+    dta += g[q] * dt;
     if (on && f_pred) f_pred[q * s.ps + n] = fp;
   }
   // Delta f = s_df P y_1..9 with P the (symmetric) projection, or P = I
@@ -423,6 +441,11 @@ constexpr uint32_t DAB = 0, DABT = 32768, HT = 65536, WABT = 86016, CK = 102400,
 #define LBM_RB2_GROUP 4  // neighbours whose loads are in flight together
 #endif
 
+// WALLS (the channel's graph): an edge whose far node lies beyond a wall
+// (row outside [0, ny)) was left out of the forward's sum and passes no
+// gradient; its neighbour address wraps to a row inside, so loads stay in
+// range.
+template <bool WALLS>
 __global__ void __launch_bounds__(256, LBM_RB2_CTAS) gnn_round_bwd2_kernel(
     const __half* __restrict__ ab, const float* __restrict__ da,
     const float* __restrict__ dh_part, const __nv_bfloat16* __restrict__ h_in,
@@ -497,10 +520,11 @@ __global__ void __launch_bounds__(256, LBM_RB2_CTAS) gnn_round_bwd2_kernel(
             const int k = g + kk + 1;
             const __half2* c_k = ckh + (k - 1) * (HID / 2) + c0 / 2;
             const uint32_t* bw = reinterpret_cast<const uint32_t*>(bn[kk]);
+            const bool keep = !WALLS || (unsigned)(p.y + ey(k)) < (unsigned)s.ny;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               const __half2 z = __hadd2(__hadd2(u32_as_h2(aj[c]), c_k[c]), u32_as_h2(bw[c]));
-              const __half2 gp = gelu_grad2_h2(z);
+              const __half2 gp = keep ? gelu_grad2_h2(z) : __float2half2_rn(0.0f);
               S[c] = __hadd2(S[c], gp);
               if (ex(k) > 0) Sx[c] = __hadd2(Sx[c], gp);
               if (ex(k) < 0) Sx[c] = __hsub2(Sx[c], gp);
@@ -567,10 +591,12 @@ __global__ void __launch_bounds__(256, LBM_RB2_CTAS) gnn_round_bwd2_kernel(
             const __half2* c_k = ckh + (k - 1) * (HID / 2) + c0 / 2;
             const uint32_t* aw = reinterpret_cast<const uint32_t*>(ai[kk]);
             const float* dv = reinterpret_cast<const float*>(di[kk]);
+            // the edge (i, k) into this node exists if i lies inside
+            const bool keep = !WALLS || (unsigned)(p.y - ey(k)) < (unsigned)s.ny;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               const __half2 z = __hadd2(__hadd2(u32_as_h2(aw[c]), c_k[c]), u32_as_h2(bj[c]));
-              const float2 gp = __half22float2(gelu_grad2_h2(z));
+              const float2 gp = keep ? __half22float2(gelu_grad2_h2(z)) : make_float2(0.0f, 0.0f);
               gB[2 * c] = fmaf(dv[2 * c], gp.x, gB[2 * c]);
               gB[2 * c + 1] = fmaf(dv[2 * c + 1], gp.y, gB[2 * c + 1]);
             }
@@ -657,9 +683,13 @@ constexpr uint32_t U = 0, XT = 16384, YT = 49152, W2 = 69632, W2T = 77824, W1F =
 #define LBM_EB_CTAS 2  // resident CTAs per SM
 #endif
 
+// The channel's velocity feature is (sum f e + F/2)/rho with F = (fx, 0)
+// (fxs[b] per lattice when set; fx = 0 and fxs NULL elsewhere); its
+// derivative w.r.t. f_i is (e_i - u)/rho with that u.
 __global__ void __launch_bounds__(256, LBM_EB_CTAS) gnn_encode_bwd_kernel(
     const float* __restrict__ f_pre, const float* __restrict__ dh0, float* __restrict__ df,
-    float* __restrict__ G, Shape s, const uint8_t* __restrict__ packed, unsigned* stw) {
+    float* __restrict__ G, Shape s, float fx, const float* __restrict__ fxs,
+    const uint8_t* __restrict__ packed, unsigned* stw) {
   if (!blob_ok(packed, stw)) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = smem_align1024(smem_raw);
@@ -704,7 +734,9 @@ __global__ void __launch_bounds__(256, LBM_EB_CTAS) gnn_encode_bwd_kernel(
     float fv[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) fv[q] = __ldg(f_pre + q * s.ps + nn);
-    const Moments m = moments9(fv);
+    Moments m = moments9(fv);
+    if (fxs || fx != 0.0f)
+      m.ux += 0.5f * (fxs ? __ldg(fxs + nn / ((int64_t)s.nx * s.ny)) : fx) / m.rho;
     float xh[NFEAT];
 #pragma unroll
     for (int q = 0; q < Q; ++q) xh[q] = (fv[q] - nrm[q]) * isg[q];
@@ -854,8 +886,24 @@ cudaError_t launch_collide_loss(const float* f_pre, const float* y, const float*
   *nblk = (int)blocks;
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
-  gnn_collide_loss_kernel<<<blocks, 256, 0, st>>>(f_pre, y, tgt, s, tau, taus, packed, lossp, dy,
-                                                   f_pred, lw, stw);
+  gnn_collide_loss_kernel<false><<<blocks, 256, 0, st>>>(f_pre, y, tgt, s, tau, taus, 0.0f,
+                                                          nullptr, packed, lossp, dy, f_pred, lw,
+                                                          stw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collide_loss_channel(const float* f_pre, const float* y, const float* tgt,
+                                        const Shape& s, float tau, const float* taus, float gx,
+                                        const float* gxs, const uint8_t* packed, double* lossp,
+                                        int* nblk, float* dy, float* f_pred, cudaStream_t st,
+                                        const float* lw) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const unsigned blocks = (unsigned)((N + 255) / 256);
+  *nblk = (int)blocks;
+  unsigned* stw = status_word();
+  if (!stw) return cudaErrorInvalidDevice;
+  gnn_collide_loss_kernel<true><<<blocks, 256, 0, st>>>(f_pre, y, tgt, s, tau, taus, gx, gxs,
+                                                         packed, lossp, dy, f_pred, lw, stw);
   return cudaGetLastError();
 }
 
@@ -899,16 +947,17 @@ cudaError_t launch_gnn_backward(const BackwardLaunch& bl, const Shape& s, const 
     }
     {
       const uint32_t bytes = rb2::BYTES + 1024;
-      if ((e = set_smem(gnn_round_bwd2_kernel, bytes)) != cudaSuccess) return e;
-      gnn_round_bwd2_kernel<<<grad_grid(N, LBM_RB2_CTAS), 256, bytes, st>>>(abs_[r], bl.da, bl.dh[1], hs[r],
-                                                                 bl.dh[0], r, bl.G, s, packed, stw);
+      auto* kern = bl.walls ? gnn_round_bwd2_kernel<true> : gnn_round_bwd2_kernel<false>;
+      if ((e = set_smem(kern, bytes)) != cudaSuccess) return e;
+      kern<<<grad_grid(N, LBM_RB2_CTAS), 256, bytes, st>>>(abs_[r], bl.da, bl.dh[1], hs[r],
+                                                           bl.dh[0], r, bl.G, s, packed, stw);
     }
   }
   {
     const uint32_t bytes = eb::BYTES + 1024;
     if ((e = set_smem(gnn_encode_bwd_kernel, bytes)) != cudaSuccess) return e;
-    gnn_encode_bwd_kernel<<<grad_grid(N, LBM_EB_CTAS), 256, bytes, st>>>(bl.f_pre, bl.dh[0], bl.df, bl.G, s,
-                                                               packed, stw);
+    gnn_encode_bwd_kernel<<<grad_grid(N, LBM_EB_CTAS), 256, bytes, st>>>(
+        bl.f_pre, bl.dh[0], bl.df, bl.G, s, bl.fx, bl.fxs, packed, stw);
   }
   grad_reduce_kernel<<<(P::TRAINABLE + 255) / 256, 256, 0, st>>>(bl.G, GRAD_ROWS, bl.grad);
   return cudaGetLastError();

@@ -191,7 +191,8 @@ __global__ void __launch_bounds__(256, (enc_ctas<PULL, BONLY, Geo>())) gnn_encod
       for (int q = 0; q < Q; ++q) xh[q] = (fv[q] - nrm[q]) * nrm[NFEAT + q];
       xh[9] = (m.rho - nrm[9]) * nrm[NFEAT + 9];
       // channel: the force-corrected velocity (sum f e + F/2) / rho
-      const float ux = Geo::kWalls ? m.ux + 0.5f * geo.force_x() / m.rho : m.ux;
+      float ux = m.ux;
+      if constexpr (Geo::kWalls) ux += 0.5f * geo.force_x(geo.pos(base + (n < N ? n : N - 1))) / m.rho;
       xh[10] = (ux - nrm[10]) * nrm[NFEAT + 10];
       xh[11] = (m.uy - nrm[11]) * nrm[NFEAT + 11];
       xh[12] = xh[13] = xh[14] = xh[15] = 0.0f;
@@ -648,27 +649,30 @@ cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
 // The network forward of the channel (GeoChannel: graph stopped at the
 // walls, forced velocity among the features) on pre-collision populations:
 // encoder -> h0, A|B of round 0; inner round -> h1, A|B of round 1; last
-// round -> the head output y [10][N].  No activation is saved for training.
+// round -> the head output y [10][N].  For training, sv.a0, sv.a1 and sv.h2
+// (else NULL) receive the aggregated messages and the last node state.
 cudaError_t launch_gnn_forward_channel(const float* f_pre, const Shape& s, float force_x,
-                                       const uint8_t* packed, __nv_bfloat16* h0, __half* ab0,
-                                       __nv_bfloat16* h1, __half* ab1, float* y,
-                                       cudaStream_t st) {
+                                       const float* forces_x, const uint8_t* packed,
+                                       const ChannelSaved& sv, float* y, cudaStream_t st) {
   unsigned* stw = status_word();
   if (!stw) return cudaErrorInvalidDevice;
   GeoChannel geo;
   static_cast<GeoStack&>(geo) = make_geo_stack(s);
   geo.fx = force_x;
+  geo.fxs = forces_x;
   const int64_t N = (int64_t)s.nb * s.ny * s.nx;
   cudaError_t e;
-  if ((e = encode_t<false, false>(f_pre, geo, N, 2, enc::BYTES + 1024, packed, h0, ab0, stw,
+  if ((e = encode_t<false, false>(f_pre, geo, N, 2, enc::BYTES + 1024, packed, sv.h0, sv.ab0, stw,
                                   st)) != cudaSuccess)
     return e;
   const int64_t cta_tiles =
       (N + (int64_t)TILE * LBM_ROUND_GROUPS - 1) / ((int64_t)TILE * LBM_ROUND_GROUPS);
   const unsigned grid = grid_for(cta_tiles * TILE, LBM_ROUND_CTAS);
-  RoundArgs r0{h0, ab0, h1, nullptr, ab1, nullptr, nullptr, nullptr, 1.0f, nullptr, 0, nullptr};
+  RoundArgs r0{sv.h0, sv.ab0, sv.h1, sv.a0, sv.ab1, nullptr, nullptr, nullptr, 1.0f, nullptr, 0,
+               nullptr};
   if ((e = round_t<0, false>(r0, geo, grid, packed, stw, st)) != cudaSuccess) return e;
-  RoundArgs r1{h1, ab1, nullptr, nullptr, nullptr, y, nullptr, nullptr, 1.0f, nullptr, 1, nullptr};
+  RoundArgs r1{sv.h1, sv.ab1, sv.h2, sv.a1, nullptr, y, nullptr, nullptr, 1.0f, nullptr, 1,
+               nullptr};
   return round_t<2, false>(r1, geo, grid, packed, stw, st);
 }
 

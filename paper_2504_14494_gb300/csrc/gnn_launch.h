@@ -35,19 +35,37 @@ cudaError_t launch_gnn_encode(const float* f, bool pull, bool b_only, const Shap
 cudaError_t launch_gnn_round(int mode, const RoundLaunch& rl, const Shape& s,
                              const uint8_t* packed, cudaStream_t st);
 
-// Channel (walls beyond the first and last rows, force (force_x, 0)): the
-// network forward on pre-collision populations over the walled graph, no
-// activation saved: h0, h1 [N][64] BF16, ab0, ab1 [N][128] FP16, y [10][N].
+// Channel (walls beyond the first and last rows, force (force_x, 0), or
+// (forces_x[b], 0) per lattice when forces_x is set): the network forward on
+// pre-collision populations over the walled graph.  h0, h1 [N][64] BF16,
+// ab0, ab1 [N][128] FP16, y [10][N]; h2, a0, a1 [N][64] BF16: the
+// activations the backward reads, or NULL when the forward is for inference.
+struct ChannelSaved {
+  __nv_bfloat16* h0 = nullptr;
+  __half* ab0 = nullptr;
+  __nv_bfloat16* h1 = nullptr;
+  __half* ab1 = nullptr;
+  __nv_bfloat16* h2 = nullptr;
+  __nv_bfloat16* a0 = nullptr;
+  __nv_bfloat16* a1 = nullptr;
+};
 cudaError_t launch_gnn_forward_channel(const float* f_pre, const Shape& s, float force_x,
-                                       const uint8_t* packed, __nv_bfloat16* h0, __half* ab0,
-                                       __nv_bfloat16* h1, __half* ab1, float* y,
-                                       cudaStream_t st);
+                                       const float* forces_x, const uint8_t* packed,
+                                       const ChannelSaved& sv, float* y, cudaStream_t st);
 // The channel's pull with bounce-back into f_pre, and Eq. 3 with Guo's
 // source (relaxation time tau tau_adj) from the head output y.
 cudaError_t launch_channel_pull(const float* fin, float* fpre, const Shape& s, cudaStream_t st);
 cudaError_t launch_channel_gnn_collide(const float* fpre, const float* y, float* fout,
                                        const Shape& s, float tau, const float* taus, float gx,
                                        const uint8_t* packed, double* totals, cudaStream_t st);
+// Restriction of a refined channel (odd factor m) to the coarse lattice:
+// pulls the co-located fine nodes from the fine stored state (the
+// pre-collision state of the next fine step), splits off the force part of
+// the non-equilibrium populations and rescales the gradient part.
+cudaError_t launch_channel_restrict(const float* f_fine, const Shape& fs, float* f_coarse,
+                                    const Shape& cs, int m, float tau_f, const float* taus_f,
+                                    float tau_c, const float* taus_c, float gx_f,
+                                    const float* gxs_f, cudaStream_t st);
 
 // The paper's Fig. 2 network (MLP-only variant) as one fused GNN-LBM step
 // kernel (pull, features, 3 MMAs, heads, Eq. 3, store).  For any other
@@ -102,6 +120,11 @@ struct BackwardLaunch {
   float* G = nullptr;                      // FP32 [GRAD_ROWS][38922]
   float* grad = nullptr;                   // FP32 [38922]
   float* df = nullptr;                     // optional dL/df_pre [9][ps]
+  // channel: the graph stops at the walls and the velocity feature carries
+  // the force (fx, or fxs[b] per lattice)
+  bool walls = false;
+  float fx = 0.0f;
+  const float* fxs = nullptr;
 };
 
 cudaError_t launch_gnn_backward(const BackwardLaunch& bl, const Shape& s, const uint8_t* packed,
@@ -110,6 +133,13 @@ cudaError_t launch_collide_loss(const float* f_pre, const float* y, const float*
                                 const Shape& s, float tau, const float* taus,
                                 const uint8_t* packed, double* lossp, int* nblk, float* dy,
                                 float* f_pred, cudaStream_t st, const float* lw = nullptr);
+// The channel's loss: Eq. 3 with Guo's source for force (gx, 0) (gxs[b] per
+// lattice when set) at the network's relaxation time, then Eq. 4.
+cudaError_t launch_collide_loss_channel(const float* f_pre, const float* y, const float* tgt,
+                                        const Shape& s, float tau, const float* taus, float gx,
+                                        const float* gxs, const uint8_t* packed, double* lossp,
+                                        int* nblk, float* dy, float* f_pred, cudaStream_t st,
+                                        const float* lw = nullptr);
 // Per-instance loss weights (weights.cu): w_b = mean_c D_c / D_b with D_b the
 // mean squared one-step BGK residual of lattice b against its target.
 int64_t pair_weights_ws(const Shape& s);

@@ -104,6 +104,13 @@ _SIGS = {
                                                _VP, _VP, _VP, ctypes.c_int64, ctypes.c_float,
                                                ctypes.c_float, _VP, _VP, _VP, ctypes.c_size_t,
                                                _VP]),
+    "lbm_restrict_channel": (ctypes.c_int, [_VP, lbm_shape, _VP, lbm_shape, ctypes.c_int,
+                                            ctypes.c_float, _VP, ctypes.c_float, _VP,
+                                            ctypes.c_float, _VP, _VP]),
+    "gnn_train_step_channel": (ctypes.c_int, [_VP, _VP, lbm_shape, ctypes.c_float, _VP,
+                                              ctypes.c_float, _VP, _VP, _VP, _VP, _VP, _VP,
+                                              ctypes.c_int64, ctypes.c_float, ctypes.c_float, _VP,
+                                              _VP, _VP, ctypes.c_size_t, _VP]),
     "lbm_batch_plan_create": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "lbm_batch_plan_destroy": (None, [_VP]),
     "lbm_batch_nodes": (ctypes.c_int64, [_VP]),
@@ -431,6 +438,18 @@ def lbm_restrict(f_fine, fine, f_coarse, coarse, factor, tau_f, taus_f, tau_c, t
                               stream_ptr(stream)), "lbm_restrict")
 
 
+def lbm_restrict_channel(f_fine, fine, f_coarse, coarse, factor, tau_f, taus_f, tau_c, taus_c,
+                         force_x_f, forces_x_f=None, stream=None):
+    f32 = _f32()
+    check(load().lbm_restrict_channel(
+        dptr(f_fine, "f_fine", f32, _elems(fine)[2]), fine,
+        dptr(f_coarse, "f_coarse", f32, _elems(coarse)[2]), coarse, int(factor), float(tau_f),
+        dptr(taus_f, "taus_f", f32, int(fine.nb)), float(tau_c),
+        dptr(taus_c, "taus_c", f32, int(coarse.nb)), float(force_x_f),
+        dptr(forces_x_f, "forces_x_f", f32, int(fine.nb)), stream_ptr(stream)),
+        "lbm_restrict_channel")
+
+
 def gnn_loss_workspace_bytes(s):
     return load().gnn_loss_workspace_bytes(s)
 
@@ -511,6 +530,24 @@ def gnn_train_step_weighted(f_in, f_target, s, tau, taus, lat_weights, params, p
         float(wd), dptr(loss, "loss", _f64(), 1), dptr(grads, "grads", f32, nt),
         dptr(workspace, "workspace"), int(nbytes(workspace) if ws_bytes is None else ws_bytes),
         stream_ptr(stream)), "gnn_train_step_weighted")
+
+
+def gnn_train_step_channel(f_in, f_target, s, tau, taus, force_x, forces_x, lat_weights, params,
+                           packed, adam_m, adam_v, step, lr, wd, loss, grads, workspace,
+                           ws_bytes=None, stream=None):
+    _, _, fe = _elems(s)
+    nt, f32 = gnn_trainable_count(), _f32()
+    check(load().gnn_train_step_channel(
+        dptr(f_in, "f_in", f32, fe), dptr(f_target, "f_target", f32, fe), s, float(tau),
+        dptr(taus, "taus", f32, int(s.nb)), float(force_x),
+        dptr(forces_x, "forces_x", f32, int(s.nb)),
+        dptr(lat_weights, "lat_weights", f32, int(s.nb)),
+        dptr(params, "params", f32, gnn_param_count()),
+        dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
+        dptr(adam_m, "adam_m", f32, nt), dptr(adam_v, "adam_v", f32, nt), int(step), float(lr),
+        float(wd), dptr(loss, "loss", _f64(), 1), dptr(grads, "grads", f32, nt),
+        dptr(workspace, "workspace"), int(nbytes(workspace) if ws_bytes is None else ws_bytes),
+        stream_ptr(stream)), "gnn_train_step_channel")
 
 
 def gnn_train_step(f_in, f_target, s, tau, taus, params, packed, adam_m, adam_v, step, lr, wd,

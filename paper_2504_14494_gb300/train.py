@@ -222,3 +222,163 @@ class HeldOutRollout:
             L.lbm_moments(f, self.coarse, None, ux, uy, None)
             out.append((ux, uy))
         return out
+
+
+class ChannelPairBank:
+    """Training pairs for the channel network (Sec. 2.4 data for the flow of
+    Sec. 3.1), generated on the GPU through the C ABI and kept resident.
+
+    `groups` refined channels run from rest (m = 3 times finer, halfway
+    bounce-back, Guo forcing; lbm_step_channel with per-lattice tau_f and
+    the group's force F_c / m); each group holds `per_group` lattices of one
+    force with different viscosities.  Every `snapshot` coarse-step time is a
+    pair: lbm_restrict_channel of the fine state one fine step before
+    (coarse step n) and m fine steps later (n + 1).  The snapshot times are
+    fractions of the group's slowest-mode e-folding time H^2/(pi^2 nu), from
+    the start-up transient to the steady state.
+
+    Group draw (seeded): u_ref ~ U[u_range], Re_ref log-uniform in re_range,
+    nu_ref = u_ref H / Re_ref, coarse force G = 8 nu_ref u_ref / H^2; lattice
+    i of the group takes nu_i = nu_ref s_i with s_i log-uniform in
+    [1/spread, spread] (centre-line velocity u_ref / s_i, Re_ref / s_i^2).
+
+    Layout: inputs and targets [9][NB][h][nx] with plane stride NB h nx, NB =
+    groups x per_group x len(snapshots); the (group, snapshot) blocks sit in
+    a seeded random order, so that batch j (lattices batch*j ..
+    batch*(j+1)-1) mixes groups and times.  tau_c and the coarse force per
+    lattice: device FP32 [NB]."""
+
+    SNAPSHOTS = (0.02, 0.05, 0.1, 0.2, 0.35, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.5, 6.0, 8.0)
+
+    def __init__(self, device, h=32, nx=8, m=3, groups=16, per_group=8, snapshots=None,
+                 seed=0, u_range=(0.03, 0.07), re_range=(8.0, 250.0), spread=1.5):
+        import torch
+        if m % 2 == 0:
+            raise ValueError("the channel restriction needs an odd refinement factor")
+        self.dev, self.h, self.nx, self.m = device, h, nx, m
+        self.per_group = per_group
+        snaps = tuple(snapshots or self.SNAPSHOTS)
+        nblk = groups * len(snaps)
+        self.nb = nblk * per_group
+        per = h * nx
+        self.ps = self.nb * per
+        self.f_in = torch.empty(9 * self.ps, device=device)
+        self.f_tg = torch.empty(9 * self.ps, device=device)
+        rng = np.random.default_rng(seed)
+        order = rng.permutation(nblk)
+        tau_c = np.zeros(self.nb, np.float32)
+        g_c = np.zeros(self.nb, np.float32)
+        self.groups = []
+        fine = L.shape(m * nx, m * h, per_group)
+        ff = [torch.empty(9 * per_group * m * m * per, device=device) for _ in range(3)]
+        nu_max = (2.0 - 0.5) / 3.0  # keeps tau_c < 2
+        for gi in range(groups):
+            u_ref = rng.uniform(*u_range)
+            re_ref = float(np.exp(rng.uniform(np.log(re_range[0]), np.log(re_range[1]))))
+            nu_ref = u_ref * h / re_ref
+            g = 8.0 * nu_ref * u_ref / h ** 2
+            s = np.exp(rng.uniform(-np.log(spread), np.log(spread), per_group))
+            nu = np.minimum(nu_ref * s, nu_max)
+            tc = (0.5 + 3.0 * nu).astype(np.float32)
+            tf = (0.5 + m * (tc.astype(np.float64) - 0.5)).astype(np.float32)
+            tf_d = torch.from_numpy(tf).to(device)
+            tc_d = torch.from_numpy(tc).to(device)
+            efold = h * h / (np.pi ** 2 * nu_ref)
+            times = sorted({max(1, int(round(fr * efold))) for fr in snaps})
+            while len(times) < len(snaps):       # short e-folding times: distinct steps
+                times.append(times[-1] + 1)
+            self.groups.append({"u_ref": u_ref, "re_ref": re_ref, "force": g,
+                                "tau_c": tc.tolist(), "times": times})
+            L.lbm_init_tgv(ff[0], fine, 1.0, 0.0, 0.0, 0.0, False)  # rest
+            cur, done = 0, 0                     # fine steps taken
+            for k, t in enumerate(times):
+                blk = int(order[gi * len(snaps) + k])
+                lo = blk * per_group
+                tau_c[lo:lo + per_group] = tc
+                g_c[lo:lo + per_group] = g
+                coarse = L.shape(nx, h, per_group, self.ps)
+                view = slice(lo * per, None)
+                target = m * t - 1                   # fine state before coarse step t
+                cur, done = self._run(ff, cur, fine, tf_d, g / m, target - done), target
+                L.lbm_restrict_channel(ff[cur], fine, self.f_in[view], coarse, m, 0.0, tf_d, 0.0,
+                                       tc_d, g / m)
+                cur, done = self._run(ff, cur, fine, tf_d, g / m, m), done + m
+                L.lbm_restrict_channel(ff[cur], fine, self.f_tg[view], coarse, m, 0.0, tf_d, 0.0,
+                                       tc_d, g / m)
+        self.tau_c = torch.from_numpy(tau_c).to(device)
+        self.force = torch.from_numpy(g_c).to(device)
+
+    @staticmethod
+    def _run(ff, cur, fine, taus, g, steps):
+        """`steps` fine channel steps from ff[cur]; returns the index of the
+        buffer holding the result (ff[2] is the scratch of multi-step runs)."""
+        if steps <= 0:
+            return cur
+        out = 1 - cur
+        L.lbm_step_channel(ff[cur], ff[out], ff[2], fine, 0.0, taus, g, steps)
+        return out
+
+    def batch_view(self, j, batch):
+        """(f_in, f_target, shape, taus, forces) of lattices batch*j ..
+        batch*(j+1)-1: views into the bank with its plane stride."""
+        lo = j * batch
+        per = self.h * self.nx
+        s = L.shape(self.nx, self.h, batch, self.ps)
+        return (self.f_in[lo * per:], self.f_tg[lo * per:], s, self.tau_c[lo:lo + batch],
+                self.force[lo:lo + batch])
+
+
+class ChannelTrainer:
+    """AdamW training of the channel network on a ChannelPairBank (fused C
+    ABI step gnn_train_step_channel); epochs visit the bank's batches in a
+    seeded random order."""
+
+    def __init__(self, device, bank, theta=None, lr=1e-3, wd=1e-2, batch=64, seed=0):
+        import torch
+        if bank.nb % batch:
+            raise ValueError("the bank must hold a whole number of batches")
+        self.bank, self.batch = bank, batch
+        theta = inputs.xavier_params(seed) if theta is None else theta
+        self.params = torch.from_numpy(np.asarray(theta, np.float32)).to(device)
+        self.packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=device)
+        L.gnn_pack(self.params, self.packed)
+        self.m = torch.zeros(L.gnn_trainable_count(), device=device)
+        self.v = torch.zeros_like(self.m)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=device)
+        self.ws = torch.empty(L.gnn_train_workspace_bytes(bank.batch_view(0, batch)[2]),
+                              dtype=torch.uint8, device=device)
+        self.lr, self.wd = lr, wd
+        self.rng = np.random.default_rng(seed)
+        self.queue = []
+        self.step_count = 0
+
+    def step(self):
+        if not self.queue:
+            self.queue = list(self.rng.permutation(self.bank.nb // self.batch))
+        f_in, f_tg, s, taus, forces = self.bank.batch_view(int(self.queue.pop()), self.batch)
+        self.step_count += 1
+        L.gnn_train_step_channel(f_in, f_tg, s, 0.0, taus, 0.0, forces, None, self.params,
+                                 self.packed, self.m, self.v, self.step_count, self.lr, self.wd,
+                                 self.loss, None, self.ws)
+
+    def bank_loss(self, bank, params=None):
+        """Mean Eq. 4 loss of `params` (device FP32; default: the trained
+        ones) over every batch of `bank`, through the same fused step with
+        lr = 0 and scratch moments, so that no parameter changes."""
+        import torch
+        params = self.params if params is None else params
+        pk = torch.empty_like(self.packed)
+        L.gnn_pack(params, pk)
+        m, v = torch.zeros_like(self.m), torch.zeros_like(self.v)
+        loss = torch.zeros(1, dtype=torch.float64, device=self.m.device)
+        nbat = bank.nb // self.batch
+        tot = 0.0
+        for j in range(nbat):
+            f_in, f_tg, s, taus, forces = bank.batch_view(j, self.batch)
+            L.gnn_train_step_channel(f_in, f_tg, s, 0.0, taus, 0.0, forces, None, params, pk, m, v,
+                                     1, 0.0, 0.0, loss, None, self.ws)
+            tot += loss.item()
+        return tot / nbat
+
+    def theta(self):
+        return self.params.cpu().numpy().copy()

@@ -72,6 +72,28 @@ def test_host_argument_checks(lbmlib):
     assert so.lbm_step_gnn_channel(a, b, s, 0.5, None, 1e-3, pk, None, ws, need, None) == -4
     assert so.lbm_step_gnn_channel(a, a, s, 0.8, None, 1e-3, pk, None, ws, need, None) == -2
     assert so.lbm_step_gnn_channel(a, b, s, 0.8, None, 1e-3, pk, None, a + 256, need, None) == -2
+    # forced restriction of a refined channel: odd factor, sizes, force, tau, aliasing
+    fine, coarse = L.shape(24, 24), L.shape(8, 8)
+    assert so.lbm_restrict_channel(a, L.shape(16, 16), b, coarse, 2, 0.8, None, 0.7, None, 1e-4,
+                                   None, None) == -1
+    assert so.lbm_restrict_channel(a, L.shape(24, 21), b, coarse, 3, 0.8, None, 0.7, None, 1e-4,
+                                   None, None) == -3
+    assert so.lbm_restrict_channel(a, fine, b, coarse, 3, 0.8, None, 0.7, None, float("inf"),
+                                   None, None) == -1
+    assert so.lbm_restrict_channel(a, fine, b, coarse, 3, 0.8, None, 0.5, None, 1e-4, None,
+                                   None) == -4
+    assert so.lbm_restrict_channel(a, fine, a + 256, coarse, 3, 0.8, None, 0.7, None, 1e-4, None,
+                                   None) == -2
+    assert so.lbm_restrict_channel(None, fine, b, coarse, 3, 0.8, None, 0.7, None, 1e-4, None,
+                                   None) == -1
+    # channel training step: force, tau, workspace
+    tw = L.gnn_train_workspace_bytes(s)
+    prm, m_, v_, loss = 1 << 33, 1 << 34, 1 << 35, 1 << 36
+    args = lambda tau, fx, wsb: (a, b, s, tau, None, fx, None, None, prm, pk, m_, v_, 1, 1e-3,
+                                 1e-2, loss, None, ws, wsb, None)
+    assert so.gnn_train_step_channel(*args(0.8, float("nan"), tw)) == -1
+    assert so.gnn_train_step_channel(*args(0.5, 1e-4, tw)) == -4
+    assert so.gnn_train_step_channel(*args(0.8, 1e-4, tw - 1)) == -10
 
 
 def test_binding_raises_on_error(lbmlib):

@@ -65,6 +65,18 @@ def _scenario(L, dev):
         wb = torch.empty(L.gnn_backward_workspace_bytes(s), dtype=torch.uint8, device=dev)
         L.gnn_backward(din, s, pk, saved, dy, g, None, wb)
         out += [y.clone(), g.clone()]
+        # channel training: forced restriction of a 3x refined channel, and
+        # the fused step (walled edge backward, forced encoder backward)
+        ff, _ = to_dev(_state(nb, 3 * ny, 3 * nx, seed=nx + 2 * ny), dev)
+        L.lbm_restrict_channel(ff, L.shape(3 * nx, 3 * ny, nb), b, s, 3, 0.9, None, 0.6333333,
+                               None, 2e-5)
+        out.append(b.clone())
+        pc, pkc = p.clone(), pk.clone()
+        mc, vc = torch.zeros_like(g), torch.zeros_like(g)
+        wt = torch.empty(L.gnn_train_workspace_bytes(s), dtype=torch.uint8, device=dev)
+        L.gnn_train_step_channel(din, b, s, 0.75, None, 6e-5, None, None, pc, pkc, mc, vc, 1, 1e-3,
+                                 1e-2, loss, g, wt)
+        out += [loss.clone(), g.clone(), pc.clone()]
     # batched run (table geometry)
     lat = [(5, 3, 0, 0.7), (130, 2, 1, 0.8), (1, 1, 1, 0.9), (24, 16, 1, 0.65)]
     plan = L.lbm_batch_plan_create(lat)
