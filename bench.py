@@ -52,10 +52,10 @@ NCU_TRAFFIC = {
     #     python bench.py --only gnn --steps 20 --warmup 3   (one GNN-LBM step, 1024 x 1024:
     #     the MLP-only kernel returning at once, the fused encoder, 2 rounds; key files
     #     gnn_fwd.cu and gnn_mlp.cu)
-    "lbm_step_gnn": {"bytes_per_launch": 50176 + (37915392 + 204349440) + (269272064 + 213337344)
-                     + (306696192 + 25646592), "nodes": 1024 * 1024,
+    "lbm_step_gnn": {"bytes_per_launch": 50432 + (37957376 + 204766976) + (269698048 + 213554176)
+                     + (306590208 + 25459456), "nodes": 1024 * 1024,
                      "file": ["gnn_fwd.cu", "gnn_mlp.cu"],
-                     "src_sha": ["f60b456f59d6393ae43959e1f1c5d49f56088d007d374aac0545b23c1f9399fc",
+                     "src_sha": ["9d25ba2e220528efef29d6d0450ede2be182d67d0e211582c3843e5a0c9355be",
                                  "f4c35f4c20b57a0feca1e66b043ceb113a26a00364f07f524735a77ff9b9f640"]},
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #     --clock-control none -k regex:gnn_mlp_step -s 3 -c 1
