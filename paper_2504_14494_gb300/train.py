@@ -331,12 +331,19 @@ class ChannelPairBank:
 class ChannelTrainer:
     """AdamW training of the channel network on a ChannelPairBank (fused C
     ABI step gnn_train_step_channel); epochs visit the bank's batches in a
-    seeded random order."""
+    seeded random order.
 
-    def __init__(self, device, bank, theta=None, lr=1e-3, wd=1e-2, batch=64, seed=0):
+    weighting: "eq4" (the paper's loss) or "relative" (each lattice weighted
+    by mean(D) / D_b, capped at 1e4, with D_b its one-step residual under the
+    BGK channel step: the zero network's loss on that lattice alone)."""
+
+    def __init__(self, device, bank, theta=None, lr=1e-3, wd=1e-2, batch=64, seed=0,
+                 weighting="eq4"):
         import torch
         if bank.nb % batch:
             raise ValueError("the bank must hold a whole number of batches")
+        if weighting not in ("eq4", "relative"):
+            raise ValueError(f"unknown weighting {weighting!r}")
         self.bank, self.batch = bank, batch
         theta = inputs.xavier_params(seed) if theta is None else theta
         self.params = torch.from_numpy(np.asarray(theta, np.float32)).to(device)
@@ -351,13 +358,39 @@ class ChannelTrainer:
         self.rng = np.random.default_rng(seed)
         self.queue = []
         self.step_count = 0
+        self.lat_w = None
+        if weighting == "relative":
+            d = self.lattice_residuals(bank)
+            w = np.where(d * 1e4 > d.mean(), d.mean() / np.where(d > 0, d, 1.0), 1e4)
+            self.lat_w = torch.from_numpy(w.astype(np.float32)).to(device)
+
+    def lattice_residuals(self, bank):
+        """D_b of every lattice of `bank`: the zero network's Eq. 4 loss on
+        that lattice alone (the BGK channel step's one-step residual)."""
+        import torch
+        zero = torch.from_numpy(inputs.zero_params()).to(self.m.device)
+        pk = torch.empty_like(self.packed)
+        L.gnn_pack(zero, pk)
+        m, v = torch.zeros_like(self.m), torch.zeros_like(self.v)
+        loss = torch.zeros(1, dtype=torch.float64, device=self.m.device)
+        ws = torch.empty(L.gnn_train_workspace_bytes(bank.batch_view(0, 1)[2]), dtype=torch.uint8,
+                         device=self.m.device)
+        out = torch.empty(bank.nb, dtype=torch.float64, device=self.m.device)
+        for j in range(bank.nb):
+            f_in, f_tg, s, taus, forces = bank.batch_view(j, 1)
+            L.gnn_train_step_channel(f_in, f_tg, s, 0.0, taus, 0.0, forces, None, zero, pk, m, v,
+                                     1, 0.0, 0.0, loss, None, ws)
+            out[j:j + 1].copy_(loss)
+        return out.cpu().numpy()
 
     def step(self):
         if not self.queue:
             self.queue = list(self.rng.permutation(self.bank.nb // self.batch))
-        f_in, f_tg, s, taus, forces = self.bank.batch_view(int(self.queue.pop()), self.batch)
+        j = int(self.queue.pop())
+        f_in, f_tg, s, taus, forces = self.bank.batch_view(j, self.batch)
+        lw = None if self.lat_w is None else self.lat_w[j * self.batch:(j + 1) * self.batch]
         self.step_count += 1
-        L.gnn_train_step_channel(f_in, f_tg, s, 0.0, taus, 0.0, forces, None, self.params,
+        L.gnn_train_step_channel(f_in, f_tg, s, 0.0, taus, 0.0, forces, lw, self.params,
                                  self.packed, self.m, self.v, self.step_count, self.lr, self.wd,
                                  self.loss, None, self.ws)
 

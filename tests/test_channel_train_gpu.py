@@ -227,3 +227,29 @@ def test_channel_pair_bank_matches_oracle_pairs(lbmlib, cuda):
     assert (s.nx, s.ny, s.nb, s.plane_stride) == (nx, h, 4, bank.nb * h * nx)
     assert fi.data_ptr() == bank.f_in.data_ptr() + 4 * h * nx * 4
     assert np.array_equal(taus.cpu().numpy(), tau_c[4:8])
+
+
+def test_channel_relative_weights_match_oracle_residuals(lbmlib, cuda):
+    """The channel trainer's per-lattice residuals D_b (the zero network's
+    loss on each lattice alone) equal the oracle's mean squared one-step
+    residual of the BGK channel step, and its relative weights are
+    mean(D) / D_b."""
+    from paper_2504_14494_gb300.train import ChannelPairBank, ChannelTrainer
+    h, nx = 6, 2
+    bank = ChannelPairBank(cuda, h=h, nx=nx, groups=2, per_group=2, snapshots=(0.1, 1.0), seed=4,
+                           u_range=(0.03, 0.05), re_range=(5.0, 20.0))
+    tr = ChannelTrainer(cuda, bank, theta=inputs.xavier_params(0, s_df=1e-3), batch=4,
+                        weighting="relative")
+    assert lbmlib.lbm_get_status() == 0
+    f_in = from_dev(bank.f_in, (9, bank.nb, h, nx))
+    f_tg = from_dev(bank.f_tg, (9, bank.nb, h, nx))
+    tau_c = bank.tau_c.cpu().numpy().astype(np.float64)
+    force = bank.force.cpu().numpy().astype(np.float64)
+    d_ref = np.array([np.mean((channel.channel_step(f_in[:, j], tau_c[j], force[j])
+                               - f_tg[:, j]) ** 2) for j in range(bank.nb)])
+    d_gpu = tr.lattice_residuals(bank)
+    assert np.allclose(d_gpu, d_ref, rtol=5e-3, atol=0), (d_gpu, d_ref)
+    w = tr.lat_w.cpu().numpy()
+    assert np.allclose(w, d_gpu.mean() / d_gpu, rtol=1e-6)
+    tr.step()
+    assert np.isfinite(tr.loss.item()) and lbmlib.lbm_get_status() == 0
