@@ -397,7 +397,11 @@ LBM_API int gnn_backward(const float* f_pre, lbm_shape s, const void* packed, co
 LBM_API int gnn_adamw(float* params, const float* grads, float* m, float* v, int64_t step,
                       float lr, float wd, float beta1, float beta2, float eps, void* stream);
 
-/* Workspace bytes of gnn_train_step. */
+/* Workspace bytes of gnn_train_step (also gnn_train_step_weighted and
+ * gnn_train_step_channel): 1,152 bytes of saved activations, 80 bytes of
+ * head output and its gradient, 768 bytes of backward buffers per node, the
+ * pre-collision populations (9 planes of plane_stride), the per-CTA gradient
+ * partials (80 MB), the loss partials and the gradient. */
 LBM_API size_t gnn_train_workspace_bytes(lbm_shape s);
 
 /* One supervised step on nb training pairs (Sec. 2.4): f_in holds the
