@@ -23,6 +23,10 @@ Readings where the paper gives no formula:
   * tau_adj = 0.5 + sigmoid(y_0); Delta f_i = s_df * y_{1+i}.
   * Inputs are normalised x_hat = (x - mu) / sigma with a fixed (mu, sigma)
     carried with the parameters; s_df likewise.
+  * The channel's graph (Sec. 3.1 flow; ``forward(walls=True)``): periodic
+    in x, no neighbour beyond the walls past the first and last rows, so
+    those messages are left out of the sum and, in ``backward``, pass no
+    gradient; with a body force the velocity feature is (j + F/2) / rho.
   * Both sides evaluate the same network: every weight MATRIX is rounded to
     bfloat16 (round to nearest even) before use, biases and (mu, sigma, s_df)
     are used as the float32 values given.  The oracle then computes in FP64.
