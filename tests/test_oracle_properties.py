@@ -10,7 +10,15 @@ lattice size, state and relaxation time, checked on random draws.
   * the GNN-LBM step commutes with periodic translations of the lattice (the
     message passing uses only relative neighbours, Sec. 2.2);
   * the conserving projection of Delta f (this library's option) leaves no
-    component along 1, e_x, e_y and is idempotent.
+    component along 1, e_x, e_y and is idempotent;
+  * the forced channel restriction (the library's reading of Sec. 2.4 for
+    the flow of Sec. 3.1) injects rho and the time-level velocity
+    (sum f* e - F_c/2)/rho with F_c = m F_f, for any state, odd m, tau and
+    force, and without force equals the periodic restriction of the
+    collided state;
+  * the channel step (halfway bounce-back, Guo forcing) conserves the
+    domain's mass and commutes with the mirror about the centre line and
+    with shifts along the channel.
 """
 import numpy as np
 import pytest
@@ -114,3 +122,45 @@ def test_conserving_projection(seed):
     basis = np.stack([np.ones(9), e[:, 0], e[:, 1]], axis=1)
     coef, *_ = np.linalg.lstsq(basis, df - p, rcond=None)
     assert np.allclose(basis @ coef, df - p, atol=1e-12)
+
+
+@SETTINGS
+@given(nyc=sizes, nxc=sizes, m=st.sampled_from([1, 3, 5]), seed=seeds,
+       tau_c=st.floats(min_value=0.52, max_value=1.8),
+       gf=st.floats(min_value=-1e-3, max_value=1e-3))
+def test_forced_restriction_injects_moments(nyc, nxc, m, seed, tau_c, gf):
+    from oracle import channel, train
+    f = _state(m * nxc, m * nyc, seed)
+    tf = train.fine_tau(tau_c, m)
+    c = train.restrict_forced(f, m, tf, tau_c, gf)
+    o = (m - 1) // 2
+    rho_f, ux_f, uy_f = channel.moments_forced(f[:, o::m, o::m], gf)
+    rho_c, jx, jy = lbm.moments(c)
+    assert np.allclose(rho_c, rho_f, rtol=1e-13, atol=0)
+    assert np.allclose(jx - 0.5 * m * gf / rho_c, ux_f, rtol=0, atol=1e-14)
+    assert np.allclose(jy, uy_f, rtol=0, atol=1e-14)
+    if m > 1:
+        post = lbm.bgk_collide(f, tf)
+        a = train.restrict_forced(f, m, tf, tau_c, 0.0)
+        b = train.restrict(np.roll(post, (-o, -o), axis=(1, 2)), m, tf, tau_c)
+        assert np.allclose(a, b, rtol=0, atol=1e-14)
+
+
+MIRROR_Y = [0, 1, 4, 3, 2, 8, 7, 6, 5]   # e_i -> e_i with e_y negated
+
+
+@SETTINGS
+@given(ny=sizes, nx=sizes, seed=seeds, tau=st.floats(min_value=0.51, max_value=2.0),
+       gx=st.floats(min_value=-1e-3, max_value=1e-3), shift=st.integers(0, 6))
+def test_channel_step_conserves_mass_and_keeps_the_channel_symmetries(ny, nx, seed, tau, gx,
+                                                                      shift):
+    from oracle import channel
+    f = _state(nx, ny, seed)
+    g = channel.channel_step(f, tau, gx)
+    assert abs(g.sum() - f.sum()) <= 1e-12 * f.sum()
+    # mirror about the channel's centre line (walls swap places)
+    mirror = lambda a: a[MIRROR_Y, ::-1, :]
+    assert np.allclose(channel.channel_step(mirror(f), tau, gx), mirror(g), rtol=0, atol=1e-15)
+    # periodic in x
+    assert np.allclose(channel.channel_step(np.roll(f, shift, axis=2), tau, gx),
+                       np.roll(g, shift, axis=2), rtol=0, atol=1e-15)
