@@ -90,6 +90,17 @@ def stream_pull(fpost):
     return out
 
 
+def stream_pull_adjoint(g):
+    """Adjoint of ``stream_pull`` (a linear map): with out_i(x) = f_i(x - e_i)
+    periodic, <stream_pull(f), g> = <f, stream_pull_adjoint(g)> for all f, g,
+    so the adjoint pushes back: result_i(x) = g_i(x + e_i)."""
+    g = np.asarray(g, np.float64)
+    out = np.empty_like(g)
+    for i in range(Q):
+        out[i] = np.roll(g[i], shift=(-int(E[i, 1]), -int(E[i, 0])), axis=(0, 1))
+    return out
+
+
 def bgk_collide(f, tau):
     """Eq. 1 (Fig. 1 'Standard BGK Collision'): f* = f - (f - f^eq)/tau."""
     rho, ux, uy = moments(f)

@@ -25,6 +25,10 @@ Readings where the paper is silent:
     gradient part and works from the pre-collision state.
   * A training pair is (restricted state at coarse step n, at step n+1); the
     prediction is one GNN-LBM coarse step on the first element.
+  * K-step rollout loss (``rollout_loss``; an option beyond Eq. 4, which is
+    its K = 1 case): the mean of Eq. 4 over K consecutive GNN-LBM steps from
+    the restricted state against the restricted refined run, differentiated
+    through the dynamics (adjoints of Eq. 3 and of streaming).
   * The optimiser (unnamed in the paper) is AdamW with decoupled weight decay
     (Loshchilov & Hutter): beta = (0.9, 0.999), eps = 1e-8.
 """
@@ -106,6 +110,80 @@ def tgv_pair(n_c, u0, k_mult, tau_c, n_steps, m=4):
     f_in = restrict(f, m, tau_f, tau_c)
     f = lbm.bgk_run(f, tau_f, m)
     return f_in, restrict(f, m, tau_f, tau_c)
+
+
+def collide_adjoint(f_pre, y, tau, p, g):
+    """Reverse mode of Eq. 3 given g = dL/df* (9, N): returns dL/dy (N, 10)
+    and the part of dL/df_pre (9, N) that passes through the explicit f and
+    f^eq(rho(f), u(f)) of Eq. 3 (the network's own dependence on f_pre is
+    ``gnn.backward``'s d_f_pre).  With t = tau tau_adj:
+      d f*_i / d f_j = delta_ij (1 - 1/t) + (1/t) d f^eq_i / d f_j,
+      d f^eq_i / d f_j = f^eq_i / rho
+                         + w_i [3 e_i + 9 (e_i . u) e_i - 3 u] . (e_j - u),
+    the second line from Eq. 2 with rho = sum f, u = sum f e / rho."""
+    from . import gnn
+    q = lbm.Q
+    f = np.asarray(f_pre, np.float64).reshape(q, -1)
+    rho, ux, uy = lbm.moments(f)
+    feq = lbm.equilibrium(rho, ux, uy)
+    g = np.asarray(g, np.float64).reshape(q, -1)
+    tau_adj, _ = gnn.heads(y, p)
+    t = tau * tau_adj
+    dy = np.zeros_like(y)
+    dy[:, 1:] = (p["s_df"] * (gnn.conserve(g) if p["variant"] & gnn.CONSERVATIVE else g)).T
+    s = gnn.sigmoid(y[:, 0])
+    dy[:, 0] = (0.0 if p["variant"] & gnn.FIXED_TAU
+                else np.sum(g * (f - feq), axis=0) / (t * t) * tau * s * (1.0 - s))
+    a = np.sum(g * feq, axis=0) / rho                      # sum_i g_i f^eq_i / rho
+    vx = np.zeros_like(rho)
+    vy = np.zeros_like(rho)
+    for i in range(q):
+        ex, ey = lbm.E[i]
+        eu = ex * ux + ey * uy
+        vx += g[i] * lbm.W[i] * (3.0 * ex + 9.0 * eu * ex - 3.0 * ux)
+        vy += g[i] * lbm.W[i] * (3.0 * ey + 9.0 * eu * ey - 3.0 * uy)
+    df = np.empty_like(f)
+    for j in range(q):
+        ex, ey = lbm.E[j]
+        df[j] = g[j] * (1.0 - 1.0 / t) + (a + vx * (ex - ux) + vy * (ey - uy)) / t
+    return dy, df
+
+
+def rollout_loss(f0, targets, theta, tau):
+    """K-step rollout loss (this library's training option; the paper's Eq. 4
+    is the one-step case K = 1): K GNN-LBM steps (stream, network, Eq. 3)
+    from the stored state f0 (9, ny, nx), and the mean over the K steps of
+    Eq. 4 against targets[k] (the refined run's restricted state after k + 1
+    coarse steps).  theta: a parameter vector, or the dict of
+    ``gnn.unpack`` (its values used as given).  Returns (loss, packed
+    dL/dtheta (38,922), dL/df0), the
+    gradient by reverse mode through every step: the adjoint of Eq. 3
+    (``collide_adjoint``), the network's backward (``gnn.backward``, with its
+    d_f_pre) and the adjoint of streaming (``lbm.stream_pull_adjoint``)."""
+    from . import gnn
+    p = theta if isinstance(theta, dict) else gnn.unpack(theta)
+    K = len(targets)
+    f = np.asarray(f0, np.float64)
+    q, ny, nx = f.shape
+    n = f.size
+    tape = []
+    loss = 0.0
+    for k in range(K):
+        fpre = lbm.stream_pull(f)
+        y, cache = gnn.forward(fpre, p)
+        f = gnn.gnn_collide(fpre, y, tau, p)
+        r = f - np.asarray(targets[k], np.float64)
+        loss += float(np.sum(r * r)) / (n * K)
+        tape.append((fpre, y, cache, r))
+    grads = np.zeros(gnn.N_TRAINABLE)
+    gpost = np.zeros((q, ny * nx))
+    for fpre, y, cache, r in reversed(tape):
+        gpost = gpost + 2.0 * r.reshape(q, -1) / (n * K)
+        dy, dfd = collide_adjoint(fpre, y, tau, p, gpost)
+        g, dfn = gnn.backward(dy, cache, p)
+        grads += gnn.pack_grads(g)
+        gpost = lbm.stream_pull_adjoint((dfd + dfn).reshape(q, ny, nx)).reshape(q, -1)
+    return loss, grads, gpost.reshape(q, ny, nx)
 
 
 def pair_weights(f_in, f_target, taus, wmax=1.0e4):

@@ -215,3 +215,90 @@ def test_channel_pair_is_close_to_one_coarse_channel_step():
     err = np.abs(step - f_tg)[:, inner].max()
     assert err < 0.1 * np.abs(f_in - f_tg)[:, inner].max()
     assert np.abs(step - f_tg)[:, [0, ny - 1]].max() > 10 * err
+
+
+# ---- the K-step rollout loss (reverse mode through the dynamics) --------------------
+def test_stream_adjoint_is_the_transpose():
+    """<stream(f), g> = <f, stream_adjoint(g)> for random f, g (periodic
+    wrap included), and the adjoint undoes the pull."""
+    rng = np.random.default_rng(41)
+    f = rng.standard_normal((9, 5, 7))
+    g = rng.standard_normal((9, 5, 7))
+    a = float(np.sum(lbm.stream_pull(f) * g))
+    b = float(np.sum(f * lbm.stream_pull_adjoint(g)))
+    assert abs(a - b) <= 1e-12 * abs(a)
+    assert np.allclose(lbm.stream_pull_adjoint(lbm.stream_pull(f)), f, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("variant", [0, 2, 4])
+def test_collide_adjoint_matches_central_differences(variant):
+    """The explicit part of Eq. 3's reverse mode: with y held fixed,
+    <g, d f*(f_pre + h d)/dh> equals <collide_adjoint df, d>, and dL/dy
+    equals the directional derivative in y."""
+    from oracle import gnn
+    rng = np.random.default_rng(42 + variant)
+    f = lbm.tgv_init(4, 3, 1.0, 0.06, 2 * np.pi / 4, 2 * np.pi / 3)
+    f = f * (1 + 2e-2 * rng.standard_normal(f.shape))
+    p = gnn.unpack(inputs.xavier_params(3, s_df=1e-2, variant=variant))
+    y = rng.standard_normal((12, 10))
+    g = rng.standard_normal((9, 12))
+    dy, df = train.collide_adjoint(f, y, 0.7, p, g)
+    J = lambda ff, yy: float(np.sum(g * gnn.gnn_collide(ff, yy, 0.7, p).reshape(9, -1)))
+    d = rng.standard_normal(f.shape)
+    h = 1e-6
+    fd = (J(f + h * d, y) - J(f - h * d, y)) / (2 * h)
+    assert abs(fd - float(np.sum(df * d.reshape(9, -1)))) <= 1e-7 * abs(fd)
+    dd = rng.standard_normal(y.shape)
+    fd = (J(f, y + h * dd) - J(f, y - h * dd)) / (2 * h)
+    an = float(np.sum(dy * dd))
+    assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-12)
+
+
+def test_rollout_loss_one_step_is_eq4():
+    """K = 1: the rollout loss and gradient are Eq. 4's (collide_loss with
+    the network's backward)."""
+    from oracle import gnn
+    f0 = lbm.tgv_init(4, 4, 1.0, 0.05, 2 * np.pi / 4, 2 * np.pi / 4)
+    f0 = f0 * inputs.perturbation(f0.shape, 5, 1e-2)
+    tg = lbm.bgk_step(f0, 0.8) * inputs.perturbation(f0.shape, 6, 1e-3)
+    theta = inputs.xavier_params(9, s_df=1e-2, bias_scale=0.1)
+    loss, grads, _ = train.rollout_loss(f0, [tg], theta, 0.8)
+    p = gnn.unpack(theta)
+    fpre = lbm.stream_pull(f0)
+    y, cache = gnn.forward(fpre, p)
+    l1, dy, _ = gnn.collide_loss(fpre, y, 0.8, tg, p)
+    g1 = gnn.pack_grads(gnn.backward(dy, cache, p)[0])
+    assert abs(loss - l1) <= 1e-14 * l1
+    assert np.allclose(grads, g1, rtol=1e-10, atol=1e-18)
+
+
+@pytest.mark.parametrize("K", [2, 3])
+def test_rollout_gradient_matches_central_differences(K):
+    """K-step rollout: the reverse-mode gradient w.r.t. every parameter
+    tensor (directional derivatives) and w.r.t. the initial state agrees
+    with central differences of the loss in FP64."""
+    from oracle import gnn
+    rng = np.random.default_rng(50 + K)
+    f0 = lbm.tgv_init(4, 4, 1.0, 0.06, 2 * np.pi / 4, 2 * np.pi / 4)
+    f0 = f0 * (1 + 2e-2 * rng.standard_normal(f0.shape))
+    tgs = [lbm.bgk_run(f0, 0.75, k + 1) * (1 + 1e-3 * rng.standard_normal(f0.shape))
+           for k in range(K)]
+    p = gnn.unpack(inputs.xavier_params(11, s_df=1e-2, bias_scale=0.1))
+    loss, grads, df0 = train.rollout_loss(f0, tgs, p, 0.75)
+    L = lambda pp, ff: train.rollout_loss(ff, tgs, pp, 0.75)[0]
+    h = 1e-6
+    o = 0
+    for name, shape in gnn.SHAPES:
+        n = int(np.prod(shape))
+        d = rng.standard_normal(shape)
+        an = float(np.dot(grads[o:o + n], d.ravel()))
+        o += n
+        q1, q2 = dict(p), dict(p)
+        q1[name] = p[name] + h * d
+        q2[name] = p[name] - h * d
+        fd = (L(q1, f0) - L(q2, f0)) / (2 * h)
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * loss), (name, fd, an)
+    d = rng.standard_normal(f0.shape) * 1e-2
+    fd = (L(p, f0 + 1e-4 * d) - L(p, f0 - 1e-4 * d)) / 2e-4
+    an = float(np.sum(df0 * d))
+    assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
