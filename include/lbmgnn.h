@@ -443,6 +443,26 @@ LBM_API int gnn_train_step_weighted(const float* f_in, const float* f_target, lb
                                     float* grads, void* workspace, size_t ws_bytes,
                                     void* stream);
 
+/* K-step rollout training step (this library's option beyond Eq. 4, which
+ * is its K = 1 case): K GNN-LBM steps (stream, network, Eq. 3) from the
+ * stored coarse states f_in (shape s), loss = the mean over the K steps of
+ * Eq. 4 against f_targets (device: target k, the refined run's restricted
+ * state after k + 1 coarse steps, at f_targets + k * 9 * plane_stride, same
+ * layout as f_in), its gradient by reverse mode through all K steps (the
+ * adjoint of Eq. 3 including f^eq's dependence on rho and u, the network's
+ * backward with dL/df_pre, the adjoint of streaming), then AdamW and a
+ * repack as gnn_train_step.  1 <= K <= 64.  Workspace:
+ * gnn_rollout_workspace_bytes(s, K) bytes, 16-byte aligned (per step the
+ * pre- and post-collision populations, the saved activations and y: about
+ * K x 1,270 bytes per node, plus gnn_backward's workspace).  Other
+ * arguments, results and errors as gnn_train_step.  Deterministic. */
+LBM_API size_t gnn_rollout_workspace_bytes(lbm_shape s, int K);
+LBM_API int gnn_train_step_rollout(const float* f_in, const float* f_targets, int K, lbm_shape s,
+                                   float tau, const float* taus, float* params, void* packed,
+                                   float* adam_m, float* adam_v, int64_t step, float lr, float wd,
+                                   double* loss, float* grads, void* workspace, size_t ws_bytes,
+                                   void* stream);
+
 /* gnn_train_step for the channel network (Sec. 3.1 flow): the prediction is
  * one lbm_step_gnn_channel step of f_in (pull with halfway bounce-back,
  * network on the walled graph with the forced velocity feature, Eq. 3 with

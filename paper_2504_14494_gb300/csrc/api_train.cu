@@ -44,6 +44,16 @@ int64_t train_ws(const Shape& s) {
          bwd_ws(N) + up16(P::TRAINABLE * (int64_t)sizeof(float));
 }
 
+// K-step rollout: per step f_pre, f_post (9 planes of ps), saved
+// activations, y; then dy, g, dfd, dfn, the loss partials of all K steps,
+// the backward workspace and the gradient.
+int64_t rollout_ws(const Shape& s, int K) {
+  const int64_t N = nodes(s), fp = up16(9 * s.ps * (int64_t)sizeof(float));
+  return K * (2 * fp + N * 1152 + up16(N * 40)) + up16(N * 40) + 3 * fp +
+         up16(K * loss_blocks(N) * (int64_t)sizeof(double)) + bwd_ws(N) +
+         up16(P::TRAINABLE * (int64_t)sizeof(float));
+}
+
 // Carves the backward workspace.
 void carve_bwd(uint8_t* ws, int64_t N, BackwardLaunch& bl) {
   bl.G = reinterpret_cast<float*>(ws);
@@ -331,6 +341,94 @@ int lbm_restrict_channel(const float* f_fine, lbm_shape fine, float* f_coarse, l
                  cudaSuccess
              ? LBM_OK
              : LBM_ERR_CUDA;
+}
+
+size_t gnn_rollout_workspace_bytes(lbm_shape shape, int K) {
+  Shape s;
+  if (K < 1 || K > 64 || check_shape_t(shape, &s)) return 0;
+  return (size_t)rollout_ws(s, K);
+}
+
+int gnn_train_step_rollout(const float* f_in, const float* f_targets, int K, lbm_shape shape,
+                           float tau, const float* taus, float* params, void* packed,
+                           float* adam_m, float* adam_v, int64_t step, float lr, float wd,
+                           double* loss, float* grads, void* workspace, size_t ws_bytes,
+                           void* stream) {
+  LBM_TRACE("gnn_train_step_rollout");
+  Shape s;
+  if (!f_in || !f_targets || !params || !packed || !adam_m || !adam_v || !loss || step < 1 ||
+      K < 1 || K > 64)
+    return LBM_ERR_ARG;
+  if (int r = check_shape_t(shape, &s)) return r;
+  if (!taus && (!std::isfinite(tau) || !(tau > 0.5f))) return LBM_ERR_TAU;
+  if (!aligned16(packed)) return LBM_ERR_ARG;
+  const int64_t N = nodes(s);
+  if (!workspace || (int64_t)ws_bytes < rollout_ws(s, K) || !aligned16(workspace))
+    return LBM_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto* pk = static_cast<uint8_t*>(packed);
+  const int64_t fp = up16(9 * s.ps * (int64_t)sizeof(float));
+  uint8_t* w = static_cast<uint8_t*>(workspace);
+  auto take = [&w](int64_t bytes) {
+    uint8_t* p = w;
+    w += bytes;
+    return p;
+  };
+  float* fpre[64];
+  float* fpost[64];
+  void* saved[64];
+  float* y[64];
+  for (int k = 0; k < K; ++k) {
+    fpre[k] = reinterpret_cast<float*>(take(fp));
+    fpost[k] = reinterpret_cast<float*>(take(fp));
+    saved[k] = take(N * 1152);
+    y[k] = reinterpret_cast<float*>(take(up16(N * 40)));
+  }
+  float* dy = reinterpret_cast<float*>(take(up16(N * 40)));
+  float* g = reinterpret_cast<float*>(take(fp));
+  float* dfd = reinterpret_cast<float*>(take(fp));
+  float* dfn = reinterpret_cast<float*>(take(fp));
+  const int nblk = (int)loss_blocks(N);
+  auto* lossp = reinterpret_cast<double*>(take(up16(K * nblk * (int64_t)sizeof(double))));
+  uint8_t* bws = take(bwd_ws(N));
+  float* gr = grads ? grads : reinterpret_cast<float*>(take(up16(P::TRAINABLE * sizeof(float))));
+  const float* tgt[64];
+  for (int k = 0; k < K; ++k) tgt[k] = f_targets + (int64_t)k * 9 * s.ps;
+
+  // forward: K GNN-LBM steps, each with its Eq. 4 partial sums
+  const float* src = f_in;
+  for (int k = 0; k < K; ++k) {
+    if (launch_stream(src, fpre[k], s, st) != cudaSuccess) return LBM_ERR_CUDA;
+    if (int r = gnn_forward(fpre[k], shape, packed, saved[k], y[k], stream)) return r;
+    int nb = 0;
+    if (launch_collide_loss(fpre[k], y[k], tgt[k], s, tau, taus, pk, lossp + k * nblk, &nb,
+                            nullptr, fpost[k], st) != cudaSuccess)
+      return LBM_ERR_CUDA;
+    src = fpost[k];
+  }
+  if (launch_loss_finish(lossp, K * nblk, 9.0 * (double)N * K, loss, st) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  // reverse: step K first; g carries dL/df* of the step being reversed
+  const float scale = (float)(2.0 / (9.0 * (double)N * K));
+  for (int k = K - 1; k >= 0; --k) {
+    if (launch_collide_adjoint(fpre[k], y[k], fpost[k], tgt[k], k == K - 1 ? nullptr : g, s, tau,
+                               taus, pk, scale, dy, dfd, st) != cudaSuccess)
+      return LBM_ERR_CUDA;
+    BackwardLaunch bl;
+    bl.f_pre = fpre[k];
+    bl.dy = dy;
+    set_saved(saved[k], N, bl);
+    carve_bwd(bws, N, bl);
+    bl.grad = gr;
+    bl.df = k > 0 ? dfn : nullptr;
+    bl.accumulate = k != K - 1;
+    if (launch_gnn_backward(bl, s, pk, st) != cudaSuccess) return LBM_ERR_CUDA;
+    if (k > 0 && launch_stream_adjoint_sum(dfd, dfn, g, s, st) != cudaSuccess)
+      return LBM_ERR_CUDA;
+  }
+  if (int r = gnn_adamw(params, gr, adam_m, adam_v, step, lr, wd, 0.9f, 0.999f, 1e-8f, stream))
+    return r;
+  return gnn_pack(params, packed, stream);
 }
 
 size_t lbm_pair_weights_workspace_bytes(lbm_shape shape) {

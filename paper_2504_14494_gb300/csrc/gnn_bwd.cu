@@ -195,6 +195,81 @@ __global__ void __launch_bounds__(256) gnn_collide_loss_kernel(
   }
 }
 
+// Reverse mode of Eq. 3 for the K-step rollout loss, one thread per node:
+// g = g_in + scale (f_post - target) is dL/df* of this step (g_in: the
+// later steps' share, pulled back through streaming; NULL for the last
+// step); writes dL/dy as the loss kernel does and the part of dL/df_pre that
+// passes through the explicit f and f^eq(rho(f), u(f)):
+//   dfd_j = g_j (1 - 1/t) + (1/t) [sum_i g_i f^eq_i / rho
+//           + V . (e_j - u)],  V = sum_i g_i w_i (3 e_i + 9 (e_i.u) e_i - 3 u).
+__global__ void __launch_bounds__(256) gnn_collide_adjoint_kernel(
+    const float* __restrict__ f_pre, const float* __restrict__ y,
+    const float* __restrict__ f_post, const float* __restrict__ tgt,
+    const float* __restrict__ g_in, Shape s, float tau, const float* __restrict__ taus,
+    const uint8_t* __restrict__ packed, float scale, float* __restrict__ dy,
+    float* __restrict__ dfd, unsigned* stw) {
+  if (!blob_ok(packed, stw)) return;
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const float* nrm = reinterpret_cast<const float*>(packed + K::NORM);
+  const float sdf = nrm[24];
+  const int variant = variant_of(nrm);
+  float fv[Q], g[Q], gp[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    fv[q] = __ldg(f_pre + q * s.ps + n);
+    const float r = __ldg(f_post + q * s.ps + n) - __ldg(tgt + q * s.ps + n);
+    g[q] = (g_in ? __ldg(g_in + q * s.ps + n) : 0.0f) + scale * r;
+    gp[q] = g[q];
+  }
+  const float y0 = __ldg(y + n);
+  const int64_t b = n / ((int64_t)s.nx * s.ny);
+  const float t0 = taus ? __ldg(taus + b) : tau;
+  const float sg = sigmoid_acc(y0);
+  const float t = t0 * tau_adj_of(y0, variant);
+  const float inv = 1.0f / t;
+  const Moments m = moments9(fv);
+  const float usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy);
+  float dta = 0.0f, a = 0.0f, vx = 0.0f, vy = 0.0f;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const float fe = feq_i(q, m, usq15);
+    dta += g[q] * (fv[q] - fe);
+    a += g[q] * fe;
+    const float eu = float(ex(q)) * m.ux + float(ey(q)) * m.uy;
+    const float gw = g[q] * wq(q);
+    vx += gw * (3.0f * float(ex(q)) + 9.0f * eu * float(ex(q)) - 3.0f * m.ux);
+    vy += gw * (3.0f * float(ey(q)) + 9.0f * eu * float(ey(q)) - 3.0f * m.uy);
+  }
+  a /= m.rho;
+  if (variant & VAR_CONSERVATIVE) conserve9(gp);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) dy[(int64_t)(1 + q) * N + n] = sdf * gp[q];
+  dy[n] = (variant & VAR_FIXED_TAU) ? 0.0f : dta * t0 * inv * inv * sg * (1.0f - sg);
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    dfd[q * s.ps + n] = g[q] * (1.0f - inv) +
+                        inv * (a + vx * (float(ex(q)) - m.ux) + vy * (float(ey(q)) - m.uy));
+}
+
+// Adjoint of periodic pull streaming applied to a + b: out_q(x) =
+// (a + b)_q(x + e_q) within each lattice (the transpose of
+// f_q(x) = f*_q(x - e_q)).
+__global__ void __launch_bounds__(256) stream_adjoint_sum_kernel(
+    const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ out, Shape s,
+    unsigned* stw) {
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const NodeXY p = node_xy(n, s);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int64_t j = checked(node_at(p, ex(q), ey(q), s), 0, N, stw);
+    out[q * s.ps + n] = __ldg(a + q * s.ps + j) + __ldg(b + q * s.ps + j);
+  }
+}
+
 // Sum of the per-block squared errors, divided by 9 N (deterministic order).
 __global__ void loss_finish_kernel(const double* __restrict__ lossp, int nblk, double count,
                                    double* __restrict__ loss) {
@@ -851,13 +926,14 @@ __global__ void __launch_bounds__(256, LBM_EB_CTAS) gnn_encode_bwd_kernel(
 
 // ---------------------------------------------------------------------------
 // Sum of the per-CTA gradient rows in a fixed order.
+// accumulate: add to the gradient already in grad (the steps of a rollout).
 __global__ void grad_reduce_kernel(const float* __restrict__ G, int rows,
-                                   float* __restrict__ grad) {
+                                   float* __restrict__ grad, bool accumulate) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P::TRAINABLE) return;
   float acc = 0.0f;
   for (int r = 0; r < rows; ++r) acc += G[(int64_t)r * P::TRAINABLE + p];
-  grad[p] = acc;
+  grad[p] = accumulate ? grad[p] + acc : acc;
 }
 
 // AdamW (decoupled weight decay) on the trainable prefix.
@@ -904,6 +980,27 @@ cudaError_t launch_collide_loss_channel(const float* f_pre, const float* y, cons
   if (!stw) return cudaErrorInvalidDevice;
   gnn_collide_loss_kernel<true><<<blocks, 256, 0, st>>>(f_pre, y, tgt, s, tau, taus, gx, gxs,
                                                          packed, lossp, dy, f_pred, lw, stw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collide_adjoint(const float* f_pre, const float* y, const float* f_post,
+                                   const float* tgt, const float* g_in, const Shape& s, float tau,
+                                   const float* taus, const uint8_t* packed, float scale,
+                                   float* dy, float* dfd, cudaStream_t st) {
+  unsigned* stw = status_word();
+  if (!stw) return cudaErrorInvalidDevice;
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  gnn_collide_adjoint_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(
+      f_pre, y, f_post, tgt, g_in, s, tau, taus, packed, scale, dy, dfd, stw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stream_adjoint_sum(const float* a, const float* b, float* out, const Shape& s,
+                                      cudaStream_t st) {
+  unsigned* stw = status_word();
+  if (!stw) return cudaErrorInvalidDevice;
+  const int64_t N = (int64_t)s.nb * s.ny * s.nx;
+  stream_adjoint_sum_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(a, b, out, s, stw);
   return cudaGetLastError();
 }
 
@@ -959,7 +1056,8 @@ cudaError_t launch_gnn_backward(const BackwardLaunch& bl, const Shape& s, const 
     gnn_encode_bwd_kernel<<<grad_grid(N, LBM_EB_CTAS), 256, bytes, st>>>(
         bl.f_pre, bl.dh[0], bl.df, bl.G, s, bl.fx, bl.fxs, packed, stw);
   }
-  grad_reduce_kernel<<<(P::TRAINABLE + 255) / 256, 256, 0, st>>>(bl.G, GRAD_ROWS, bl.grad);
+  grad_reduce_kernel<<<(P::TRAINABLE + 255) / 256, 256, 0, st>>>(bl.G, GRAD_ROWS, bl.grad,
+                                                                   bl.accumulate);
   return cudaGetLastError();
 }
 

@@ -125,6 +125,8 @@ struct BackwardLaunch {
   bool walls = false;
   float fx = 0.0f;
   const float* fxs = nullptr;
+  // add the gradient to `grad` instead of overwriting it (rollout steps)
+  bool accumulate = false;
 };
 
 cudaError_t launch_gnn_backward(const BackwardLaunch& bl, const Shape& s, const uint8_t* packed,
@@ -147,6 +149,15 @@ cudaError_t launch_pair_weights(const float* f_in, const float* tgt, const Shape
                                 const float* taus, float* w, void* ws, cudaStream_t st);
 cudaError_t launch_loss_finish(const double* lossp, int nblk, double count, double* loss,
                                cudaStream_t st);
+// Rollout loss: reverse mode of Eq. 3 from dL/df* = g_in + scale (f_post -
+// tgt) (g_in nullable) to dL/dy [10][N] and the explicit part of dL/df_pre
+// (dfd, planes of s.ps); and the adjoint of periodic streaming of a + b.
+cudaError_t launch_collide_adjoint(const float* f_pre, const float* y, const float* f_post,
+                                   const float* tgt, const float* g_in, const Shape& s, float tau,
+                                   const float* taus, const uint8_t* packed, float scale,
+                                   float* dy, float* dfd, cudaStream_t st);
+cudaError_t launch_stream_adjoint_sum(const float* a, const float* b, float* out, const Shape& s,
+                                      cudaStream_t st);
 cudaError_t launch_adamw(float* theta, const float* g, float* m, float* v, float lr, float wd,
                          float b1, float b2, float eps, float bc1, float bc2, cudaStream_t st);
 

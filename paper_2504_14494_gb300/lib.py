@@ -104,6 +104,11 @@ _SIGS = {
                                                _VP, _VP, _VP, ctypes.c_int64, ctypes.c_float,
                                                ctypes.c_float, _VP, _VP, _VP, ctypes.c_size_t,
                                                _VP]),
+    "gnn_rollout_workspace_bytes": (ctypes.c_size_t, [lbm_shape, ctypes.c_int]),
+    "gnn_train_step_rollout": (ctypes.c_int, [_VP, _VP, ctypes.c_int, lbm_shape, ctypes.c_float,
+                                              _VP, _VP, _VP, _VP, _VP, ctypes.c_int64,
+                                              ctypes.c_float, ctypes.c_float, _VP, _VP, _VP,
+                                              ctypes.c_size_t, _VP]),
     "lbm_restrict_channel": (ctypes.c_int, [_VP, lbm_shape, _VP, lbm_shape, ctypes.c_int,
                                             ctypes.c_float, _VP, ctypes.c_float, _VP,
                                             ctypes.c_float, _VP, _VP]),
@@ -530,6 +535,26 @@ def gnn_train_step_weighted(f_in, f_target, s, tau, taus, lat_weights, params, p
         float(wd), dptr(loss, "loss", _f64(), 1), dptr(grads, "grads", f32, nt),
         dptr(workspace, "workspace"), int(nbytes(workspace) if ws_bytes is None else ws_bytes),
         stream_ptr(stream)), "gnn_train_step_weighted")
+
+
+def gnn_rollout_workspace_bytes(s, K):
+    return int(load().gnn_rollout_workspace_bytes(s, int(K)))
+
+
+def gnn_train_step_rollout(f_in, f_targets, K, s, tau, taus, params, packed, adam_m, adam_v, step,
+                           lr, wd, loss, grads, workspace, ws_bytes=None, stream=None):
+    _, _, fe = _elems(s)
+    ps = int(s.plane_stride) or int(s.nx) * int(s.ny) * int(s.nb)
+    nt, f32 = gnn_trainable_count(), _f32()
+    check(load().gnn_train_step_rollout(
+        dptr(f_in, "f_in", f32, fe), dptr(f_targets, "f_targets", f32, (int(K) - 1) * 9 * ps + fe),
+        int(K), s, float(tau), dptr(taus, "taus", f32, int(s.nb)),
+        dptr(params, "params", f32, gnn_param_count()),
+        dptr(packed, "packed", nbytes_min=gnn_packed_bytes()),
+        dptr(adam_m, "adam_m", f32, nt), dptr(adam_v, "adam_v", f32, nt), int(step), float(lr),
+        float(wd), dptr(loss, "loss", _f64(), 1), dptr(grads, "grads", f32, nt),
+        dptr(workspace, "workspace"), int(nbytes(workspace) if ws_bytes is None else ws_bytes),
+        stream_ptr(stream)), "gnn_train_step_rollout")
 
 
 def gnn_train_step_channel(f_in, f_target, s, tau, taus, force_x, forces_x, lat_weights, params,

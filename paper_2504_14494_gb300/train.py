@@ -137,6 +137,79 @@ class Trainer:
         return self.params.cpu().numpy().copy()
 
 
+class RolloutStream:
+    """K-step training windows from the refined-lattice TGV runs of a
+    PairStream: the restricted state at coarse step t and the K restricted
+    states after it, targets contiguous ([K] x 9 planes), for
+    gnn_train_step_rollout.  `episode` windows per episode of refined runs; a
+    window never spans two episodes; consecutive windows of an episode
+    overlap (a sliding window)."""
+
+    def __init__(self, device, K=4, episode=32, **pair_kw):
+        import torch
+        self.K = K
+        # episode + K - 1 pairs give episode + K states: `episode` windows
+        self.pairs = PairStream(device, episode=episode + K - 1, **pair_kw)
+        self.coarse = self.pairs.coarse
+        n = 9 * self.coarse.nx * self.coarse.ny * self.coarse.nb
+        self.ring = [torch.empty(n, device=device) for _ in range(K + 1)]
+        self.f_in = torch.empty(n, device=device)
+        self.targets = torch.empty(K * n, device=device)
+        self.count = 0
+
+    def next(self):
+        """Returns (f_in, targets, tau_c) device tensors valid until the next
+        call."""
+        K = self.K
+        while True:
+            src, dst, taus = self.pairs.next()
+            if self.pairs.t == 1:                 # a new episode began
+                self.ring[0].copy_(src)
+                self.count = 1
+            self.ring[self.count % (K + 1)].copy_(dst)
+            self.count += 1
+            if self.count >= K + 1:
+                break
+        first = self.count - (K + 1)
+        n = self.f_in.numel()
+        self.f_in.copy_(self.ring[first % (K + 1)])
+        for k in range(K):
+            self.targets[k * n:(k + 1) * n].copy_(self.ring[(first + 1 + k) % (K + 1)])
+        return self.f_in, self.targets, taus
+
+
+class RolloutTrainer:
+    """AdamW training of the network on K-step windows (RolloutStream) with
+    the rollout loss of gnn_train_step_rollout (the mean of Eq. 4 over K
+    GNN-LBM steps, differentiated through the dynamics)."""
+
+    def __init__(self, device, K=4, theta=None, lr=1e-3, wd=1e-2, seed=0, **stream_kw):
+        import torch
+        self.data = RolloutStream(device, K=K, seed=seed, **stream_kw)
+        self.K = K
+        theta = inputs.xavier_params(seed) if theta is None else theta
+        self.params = torch.from_numpy(np.asarray(theta, np.float32)).to(device)
+        self.packed = torch.empty(L.gnn_packed_bytes(), dtype=torch.uint8, device=device)
+        L.gnn_pack(self.params, self.packed)
+        self.m = torch.zeros(L.gnn_trainable_count(), device=device)
+        self.v = torch.zeros_like(self.m)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=device)
+        self.ws = torch.empty(L.gnn_rollout_workspace_bytes(self.data.coarse, K),
+                              dtype=torch.uint8, device=device)
+        self.lr, self.wd = lr, wd
+        self.step_count = 0
+
+    def step(self):
+        f_in, targets, taus = self.data.next()
+        self.step_count += 1
+        L.gnn_train_step_rollout(f_in, targets, self.K, self.data.coarse, 1.0, taus, self.params,
+                                 self.packed, self.m, self.v, self.step_count, self.lr, self.wd,
+                                 self.loss, None, self.ws)
+
+    def theta(self):
+        return self.params.cpu().numpy().copy()
+
+
 class Evaluator:
     """Eq. 4 loss of a parameter vector on pairs, without training: stream,
     network forward, Eq. 3 and the loss, all through the C ABI."""

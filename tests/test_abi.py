@@ -94,6 +94,15 @@ def test_host_argument_checks(lbmlib):
     assert so.gnn_train_step_channel(*args(0.8, float("nan"), tw)) == -1
     assert so.gnn_train_step_channel(*args(0.5, 1e-4, tw)) == -4
     assert so.gnn_train_step_channel(*args(0.8, 1e-4, tw - 1)) == -10
+    # K-step rollout training step: K range, workspace
+    assert L.gnn_rollout_workspace_bytes(s, 0) == 0 and L.gnn_rollout_workspace_bytes(s, 65) == 0
+    rw = L.gnn_rollout_workspace_bytes(s, 2)
+    assert rw > 2 * 64 * 1152
+    rargs = lambda k, wsb: (a, b, k, s, 0.8, None, prm, pk, m_, v_, 1, 1e-3, 1e-2, loss, None, ws,
+                            wsb, None)
+    assert so.gnn_train_step_rollout(*rargs(0, rw)) == -1
+    assert so.gnn_train_step_rollout(*rargs(65, rw)) == -1
+    assert so.gnn_train_step_rollout(*rargs(2, rw - 1)) == -10
 
 
 def test_binding_raises_on_error(lbmlib):
