@@ -45,3 +45,22 @@ def test_rollout_windows_are_consecutive_states_of_one_episode(monkeypatch):
                 assert np.all(f_in.numpy() == 1000.0 * e + t), (K, ep, e, t)
                 for k in range(K):
                     assert np.all(tg[k * n:(k + 1) * n].numpy() == 1000.0 * e + t + 1 + k)
+
+
+def test_channel_training_host_checks():
+    """Argument checks of the channel pair bank and trainer that run before
+    any device work: an even refinement factor, a bank that is not a whole
+    number of batches, an unknown weighting."""
+    import pytest
+
+    with pytest.raises(ValueError):
+        train.ChannelPairBank("cpu", m=2)
+
+    class _Bank:
+        nb = 10
+
+    with pytest.raises(ValueError):
+        train.ChannelTrainer("cpu", _Bank(), batch=4)
+    _Bank.nb = 8
+    with pytest.raises(ValueError):
+        train.ChannelTrainer("cpu", _Bank(), batch=4, weighting="unknown")
