@@ -54,7 +54,20 @@ static int host_part(void) {
   /* a NULL vector and an unknown variant are rejected */
   const int bad_null = gnn_params_init_xavier(NULL, 5, 1e-2f, 0);
   const int bad_variant = gnn_params_init_xavier(theta, 5, 1e-2f, 8);
-  printf("{\"param_count\": %zu, \"trainable_count\": %zu, \"packed_bytes\": %zu, "
+  /* training entry points: workspace sizes, and argument errors found on the
+   * host before any launch (an even refinement of the channel, K = 0) */
+  const lbm_shape fine = {72, 60, 2, 0};
+  const int bad_factor = lbm_restrict_channel((const float*)(uintptr_t)0x100000, fine,
+                                              (float*)(uintptr_t)0x10000000, s, 2, 0.8f, NULL,
+                                              0.7f, NULL, 1e-4f, NULL, NULL);
+  const int bad_k = gnn_train_step_rollout((const float*)(uintptr_t)0x100000,
+                                           (const float*)(uintptr_t)0x10000000, 0, s, 0.8f, NULL,
+                                           theta, (void*)(uintptr_t)0x20000000, theta, theta, 1,
+                                           1e-3f, 0.0f, (double*)(uintptr_t)0x30000000, NULL,
+                                           (void*)(uintptr_t)0x40000000, 1u << 30, NULL);
+  printf("{\"train_ws\": %zu, \"rollout_ws\": %zu, \"bad_factor\": %d, \"bad_k\": %d, ",
+         gnn_train_workspace_bytes(s), gnn_rollout_workspace_bytes(s, 3), bad_factor, bad_k);
+  printf("\"param_count\": %zu, \"trainable_count\": %zu, \"packed_bytes\": %zu, "
          "\"step_ws\": %zu, \"channel_ws\": %zu, \"host_ws\": %zu, \"saved_bytes\": %zu, "
          "\"xavier_sum\": %.17g, \"xavier_sum_abs\": %.17g, \"xavier_first\": %.9g, "
          "\"xavier_last\": %.9g, \"bad_null\": %d, \"bad_variant\": %d, "

@@ -65,6 +65,9 @@ def test_host_calls_from_c_agree_with_the_binding(consumer):
     assert got["status_ok"] == L.status_string(L.LBM_OK)
     assert got["status_tau"] == L.status_string(L.LBM_ERR_TAU)
     assert (got["abi"], got["layout"]) == L.lbm_version()
+    assert got["train_ws"] == L.gnn_train_workspace_bytes(s)
+    assert got["rollout_ws"] == L.gnn_rollout_workspace_bytes(s, 3)
+    assert got["bad_factor"] == L.LBM_ERR_ARG and got["bad_k"] == L.LBM_ERR_ARG
 
 
 @pytest.mark.gpu
