@@ -13,6 +13,11 @@
 // (gnn_fwd.cu, GeoChannel) -> channel_gnn_collide_kernel, which relaxes with
 // the network's time tau tau_adj, adds Guo's source with that same time and
 // the correction Delta f.
+//
+// Training data of the channel network (Sec. 2.4 for this flow): the
+// restriction of an m-times refined channel (odd m) that separates the
+// force part of the non-equilibrium populations from the gradient part
+// (channel_restrict_kernel).
 #include "common.cuh"
 #include "gnn.cuh"
 #include "gnn_launch.h"
