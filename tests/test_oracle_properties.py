@@ -18,7 +18,9 @@ lattice size, state and relaxation time, checked on random draws.
     collided state;
   * the channel step (halfway bounce-back, Guo forcing) conserves the
     domain's mass and commutes with the mirror about the centre line and
-    with shifts along the channel.
+    with shifts along the channel;
+  * the K-step rollout loss's reverse-mode gradient is its derivative along
+    any direction of the parameters and of the initial state.
 """
 import numpy as np
 import pytest
@@ -164,3 +166,32 @@ def test_channel_step_conserves_mass_and_keeps_the_channel_symmetries(ny, nx, se
     # periodic in x
     assert np.allclose(channel.channel_step(np.roll(f, shift, axis=2), tau, gx),
                        np.roll(g, shift, axis=2), rtol=0, atol=1e-15)
+
+
+@settings(max_examples=10, deadline=None, derandomize=True)
+@given(nx=st.integers(2, 4), ny=st.integers(2, 4), K=st.integers(1, 2), seed=seeds,
+       tau=st.floats(min_value=0.55, max_value=1.2))
+def test_rollout_gradient_is_the_derivative_of_the_rollout_loss(nx, ny, K, seed, tau):
+    """The K-step rollout loss's reverse-mode gradient (through Eq. 3, the
+    network and streaming) gives its directional derivative along a random
+    direction of all parameters and of the initial state, for any small
+    lattice, K and tau (central differences in FP64)."""
+    from oracle import train
+    rng = np.random.default_rng(seed)
+    f0 = _state(nx, ny, seed)
+    tgs = [_state(nx, ny, seed + 1 + k) for k in range(K)]
+    p = gnn.unpack(inputs.xavier_params(seed % 1000, s_df=1e-2, bias_scale=0.1))
+    loss, grads, df0 = train.rollout_loss(f0, tgs, p, tau)
+    d = {name: rng.standard_normal(shape) for name, shape in gnn.SHAPES}
+    an = float(np.dot(grads, np.concatenate([d[name].ravel() for name, _ in gnn.SHAPES])))
+    h = 1e-6
+    q1 = {k: (v + h * d[k] if k in d else v) for k, v in p.items()}
+    q2 = {k: (v - h * d[k] if k in d else v) for k, v in p.items()}
+    fd = (train.rollout_loss(f0, tgs, q1, tau)[0] - train.rollout_loss(f0, tgs, q2, tau)[0]) / (2 * h)
+    assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-9), (fd, an)
+    e = rng.standard_normal(f0.shape) * 1e-2
+    fd = (train.rollout_loss(f0 + 1e-4 * e, tgs, p, tau)[0]
+          - train.rollout_loss(f0 - 1e-4 * e, tgs, p, tau)[0]) / 2e-4
+    an = float(np.sum(df0 * e))
+    # the state step moves the loss by ~1e-9 of itself: round-off ~1e-6 of fd
+    assert abs(fd - an) <= 2e-5 * max(abs(an), 1e-12), (fd, an)
