@@ -302,3 +302,16 @@ def test_rollout_gradient_matches_central_differences(K):
     fd = (L(p, f0 + 1e-4 * d) - L(p, f0 - 1e-4 * d)) / 2e-4
     an = float(np.sum(df0 * d))
     assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+
+
+def test_restrict_forced_factor_one_is_one_channel_collision():
+    """m = 1 (tau_f = tau_c): restricting the pulled state is one collision
+    with Guo's source, (1 - 1/tau)(N - P) + P = (1 - 1/tau) N + P / tau with
+    P / tau = (1 - 1/(2 tau)) S, i.e. exactly one BGK channel step."""
+    from oracle import channel
+    rng = np.random.default_rng(61)
+    f = lbm.equilibrium(np.ones((5, 4)), np.full((5, 4), 0.03), np.zeros((5, 4)))
+    f = f * (1 + 1e-2 * rng.standard_normal(f.shape))
+    for tau, g in ((0.6, 2e-4), (1.3, -5e-4)):
+        a = train.restrict_forced(channel.stream_pull_walls(f), 1, tau, tau, g)
+        assert np.allclose(a, channel.channel_step(f, tau, g), rtol=0, atol=1e-16)
