@@ -20,7 +20,10 @@ Readings where the paper gives no scheme:
     u(y) = G/(2 nu) (y + 1/2) (ny - 1/2 - y).
   * Re = u_max H / nu with u_max = G H^2 / (8 nu).
   * Training loss of the channel network: Eq. 3 with Guo's source at the
-    network's relaxation time, then Eq. 4 (``collide_loss_channel``).
+    network's relaxation time, then Eq. 4 (``collide_loss_channel``); its
+    K-step rollout form (``rollout_loss_channel``, the library's option
+    beyond Eq. 4) differentiated through the walled pull, the forced
+    collision and the walled network.
 """
 import numpy as np
 
@@ -68,6 +71,27 @@ def stream_pull_walls(fpost):
         inside = (src_y >= 0) & (src_y < ny)
         out[i][inside] = fpost[i][src_y[inside][:, None], ((xs - ex) % nx)[None, :]]
         out[i][~inside] = fpost[OPP[i]][~inside]
+    return out
+
+
+def stream_pull_walls_adjoint(g):
+    """Adjoint of ``stream_pull_walls`` (a linear map, periodic in x with
+    halfway bounce-back): <stream_pull_walls(f), g> = <f, result> for all f.
+    A pulled value from inside sends g back to its source node; a bounced
+    value f_opp(i)(x) sends g_i(x) to population opp(i) of the same node."""
+    g = np.asarray(g, np.float64)
+    _, ny, nx = g.shape
+    out = np.zeros_like(g)
+    xs = np.arange(nx)
+    ys = np.arange(ny)
+    for i in range(lbm.Q):
+        ex, ey = lbm.E[i]
+        src_y = ys - ey
+        inside = (src_y >= 0) & (src_y < ny)
+        for y in ys[inside]:
+            np.add.at(out[i], (y - ey, (xs - ex) % nx), g[i, y])
+        for y in ys[~inside]:
+            out[OPP[i], y] += g[i, y]
     return out
 
 
@@ -142,3 +166,83 @@ def collide_loss_channel(f_pre, y, tau, target, p, gx, node_weight=None):
     s = gnn.sigmoid(y[:, 0])
     dy[:, 0] = 0.0 if p["variant"] & gnn.FIXED_TAU else dteff * tau * s * (1.0 - s)
     return loss, dy, f_pred
+
+
+def collide_adjoint_channel(f_pre, y, tau, p, gx, g):
+    """Reverse mode of the channel's Eq. 3 (Guo's source at t = tau tau_adj)
+    given g = dL/df* (9, N): returns dL/dy (N, 10) and the part of
+    dL/df_pre through the explicit f, f^eq(rho, u) and S(u), with the forced
+    u = (j + F/2)/rho (so du/df_j = (e_j - u)/rho, as without force):
+      d f*_i/d f_j = delta_ij (1 - 1/t) + (1/t) d f^eq_i/d f_j
+                     + (1 - 1/(2t)) d S_i/d f_j,
+      d S_i/d u = w_i [-3 F + 9 (e_i . F) e_i]."""
+    from . import gnn
+    q = lbm.Q
+    f = np.asarray(f_pre, np.float64).reshape(q, -1)
+    gxn = np.broadcast_to(np.asarray(gx, np.float64), f.shape[1:])
+    rho, ux, uy = moments_forced(f, gxn)
+    feq = lbm.equilibrium(rho, ux, uy)
+    src = guo_term(ux, uy, gxn)
+    g = np.asarray(g, np.float64).reshape(q, -1)
+    tau_adj, _ = gnn.heads(y, p)
+    t = tau * tau_adj
+    dy = np.zeros_like(y)
+    dy[:, 1:] = (p["s_df"] * (gnn.conserve(g) if p["variant"] & gnn.CONSERVATIVE else g)).T
+    s = gnn.sigmoid(y[:, 0])
+    dy[:, 0] = (0.0 if p["variant"] & gnn.FIXED_TAU
+                else np.sum(g * ((f - feq) + 0.5 * src), axis=0) / (t * t) * tau * s * (1.0 - s))
+    a = np.sum(g * feq, axis=0) / rho
+    vx = np.zeros_like(rho)
+    vy = np.zeros_like(rho)
+    c = 1.0 - 0.5 / t
+    for i in range(q):
+        ex, ey = lbm.E[i]
+        eu = ex * ux + ey * uy
+        ef = ex * gxn
+        vx += g[i] * lbm.W[i] * ((3.0 * ex + 9.0 * eu * ex - 3.0 * ux) / t
+                                 + c * (-3.0 * gxn + 9.0 * ef * ex) / rho)
+        vy += g[i] * lbm.W[i] * ((3.0 * ey + 9.0 * eu * ey - 3.0 * uy) / t
+                                 + c * (9.0 * ef * ey) / rho)
+    df = np.empty_like(f)
+    for j in range(q):
+        ex, ey = lbm.E[j]
+        df[j] = g[j] * (1.0 - 1.0 / t) + a / t + vx * (ex - ux) + vy * (ey - uy)
+    return dy, df
+
+
+def rollout_loss_channel(f0, targets, theta, tau, gx):
+    """The K-step rollout loss on the channel (walls, force gx): K GNN-LBM
+    channel steps from f0, the mean over the steps of Eq. 4 against
+    targets[k], and its gradient by reverse mode through the walled pull,
+    the channel collision with Guo's source and the walled network.
+    theta: a parameter vector or ``gnn.unpack``'s dict.  Returns (loss,
+    packed dL/dtheta, dL/df0)."""
+    from . import gnn
+    p = theta if isinstance(theta, dict) else gnn.unpack(theta)
+    K = len(targets)
+    f = np.asarray(f0, np.float64)
+    q, ny, nx = f.shape
+    n = f.size
+    tape = []
+    loss = 0.0
+    for k in range(K):
+        fpre = stream_pull_walls(f)
+        y, cache = gnn.forward(fpre, p, walls=True, force_x=gx)
+        tau_adj, dfc = gnn.heads(y, p)
+        teff = (tau * tau_adj).reshape(ny, nx)
+        rho, ux, uy = moments_forced(fpre, gx)
+        feq = lbm.equilibrium(rho, ux, uy)
+        f = (fpre - (fpre - feq) / teff + guo_source(ux, uy, teff, gx)
+             + dfc.reshape(q, ny, nx))
+        r = f - np.asarray(targets[k], np.float64)
+        loss += float(np.sum(r * r)) / (n * K)
+        tape.append((fpre, y, cache, r))
+    grads = np.zeros(gnn.N_TRAINABLE)
+    gpost = np.zeros((q, ny * nx))
+    for fpre, y, cache, r in reversed(tape):
+        gpost = gpost + 2.0 * r.reshape(q, -1) / (n * K)
+        dy, dfd = collide_adjoint_channel(fpre, y, tau, p, gx, gpost)
+        g, dfn = gnn.backward(dy, cache, p)
+        grads += gnn.pack_grads(g)
+        gpost = stream_pull_walls_adjoint((dfd + dfn).reshape(q, ny, nx)).reshape(q, -1)
+    return loss, grads, gpost.reshape(q, ny, nx)

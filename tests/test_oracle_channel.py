@@ -207,3 +207,98 @@ def test_channel_loss_special_cases():
     b = gnn.collide_loss(fpre, y, 0.7, target, p)
     assert abs(a[0] - b[0]) <= 1e-15 * b[0]
     assert np.allclose(a[1], b[1], rtol=1e-13, atol=1e-20)
+
+
+# ---- the channel's rollout loss (adjoints with walls and force) ----------------------
+def test_walled_stream_adjoint_is_the_transpose():
+    """<stream_pull_walls(f), g> = <f, stream_pull_walls_adjoint(g)>."""
+    rng = np.random.default_rng(71)
+    for ny, nx in ((1, 3), (4, 5), (6, 2)):
+        f = rng.standard_normal((9, ny, nx))
+        g = rng.standard_normal((9, ny, nx))
+        a = float(np.sum(channel.stream_pull_walls(f) * g))
+        b = float(np.sum(f * channel.stream_pull_walls_adjoint(g)))
+        assert abs(a - b) <= 1e-12 * max(abs(a), 1.0), (ny, nx, a, b)
+
+
+def _gnn_channel_collide(fpre, y, tau, p, gx):
+    from oracle import gnn
+    q, ny, nx = fpre.shape
+    tau_adj, dfc = gnn.heads(y, p)
+    teff = (tau * tau_adj).reshape(ny, nx)
+    rho, ux, uy = channel.moments_forced(fpre, gx)
+    feq = lbm.equilibrium(rho, ux, uy)
+    return fpre - (fpre - feq) / teff + channel.guo_source(ux, uy, teff, gx) + dfc.reshape(q, ny, nx)
+
+
+def test_channel_collide_adjoint_matches_central_differences():
+    """The explicit part of the channel collision's reverse mode (y held
+    fixed; f^eq and Guo's source through the forced velocity) and dL/dy
+    against central differences, variants 0, 2 and 4."""
+    from oracle import gnn
+    for variant in (0, 2, 4):
+        rng = np.random.default_rng(72 + variant)
+        f = _rest(3, 4) * (1 + 2e-2 * rng.standard_normal((9, 3, 4)))
+        p = gnn.unpack(_net(8, variant=variant))
+        y = rng.standard_normal((12, 10))
+        g = rng.standard_normal((9, 12))
+        gx = 3e-3
+        dy, df = channel.collide_adjoint_channel(f, y, 0.8, p, gx, g)
+        J = lambda ff, yy: float(np.sum(g * _gnn_channel_collide(ff, yy, 0.8, p, gx).reshape(9, -1)))
+        d = rng.standard_normal(f.shape)
+        h = 1e-6
+        fd = (J(f + h * d, y) - J(f - h * d, y)) / (2 * h)
+        assert abs(fd - float(np.sum(df * d.reshape(9, -1)))) <= 1e-7 * abs(fd), variant
+        dd = rng.standard_normal(y.shape)
+        fd = (J(f, y + h * dd) - J(f, y - h * dd)) / (2 * h)
+        an = float(np.sum(dy * dd))
+        assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-12), variant
+
+
+def test_channel_rollout_one_step_is_the_channel_loss():
+    """K = 1: the channel rollout loss and gradient are the channel loss
+    (Eq. 3 with Guo's source, Eq. 4) with the walled network's backward."""
+    from oracle import gnn
+    rng = np.random.default_rng(73)
+    f0 = _rest(5, 4) * (1 + 1e-2 * rng.standard_normal((9, 5, 4)))
+    tg = channel.channel_step(f0, 0.7, 2e-4) * (1 + 1e-3 * rng.standard_normal((9, 5, 4)))
+    theta = _net(9, s_df=1e-2)
+    loss, grads, _ = channel.rollout_loss_channel(f0, [tg], theta, 0.7, 2e-4)
+    p = gnn.unpack(theta)
+    fpre = channel.stream_pull_walls(f0)
+    y, cache = gnn.forward(fpre, p, walls=True, force_x=2e-4)
+    l1, dy, _ = channel.collide_loss_channel(fpre, y, 0.7, tg, p, 2e-4)
+    g1 = gnn.pack_grads(gnn.backward(dy, cache, p)[0])
+    assert abs(loss - l1) <= 1e-13 * l1
+    assert np.allclose(grads, g1, rtol=1e-9, atol=1e-18)
+
+
+def test_channel_rollout_gradient_matches_central_differences():
+    """K = 2 on a walled, forced 4 x 3 channel: the reverse-mode gradient
+    w.r.t. every parameter tensor and the initial state against central
+    differences of the loss in FP64."""
+    from oracle import gnn
+    rng = np.random.default_rng(74)
+    f0 = _rest(4, 3) * (1 + 2e-2 * rng.standard_normal((9, 4, 3)))
+    gx = 5e-4
+    tgs = [channel.channel_run(f0, 0.75, gx, k + 1) * (1 + 1e-3 * rng.standard_normal((9, 4, 3)))
+           for k in range(2)]
+    p = gnn.unpack(_net(10, s_df=1e-2))
+    loss, grads, df0 = channel.rollout_loss_channel(f0, tgs, p, 0.75, gx)
+    L = lambda pp, ff: channel.rollout_loss_channel(ff, tgs, pp, 0.75, gx)[0]
+    h = 1e-6
+    o = 0
+    for name, shape in gnn.SHAPES:
+        n = int(np.prod(shape))
+        d = rng.standard_normal(shape)
+        an = float(np.dot(grads[o:o + n], d.ravel()))
+        o += n
+        q1, q2 = dict(p), dict(p)
+        q1[name] = p[name] + h * d
+        q2[name] = p[name] - h * d
+        fd = (L(q1, f0) - L(q2, f0)) / (2 * h)
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * loss), (name, fd, an)
+    d = rng.standard_normal(f0.shape) * 1e-2
+    fd = (L(p, f0 + 1e-4 * d) - L(p, f0 - 1e-4 * d)) / 2e-4
+    an = float(np.sum(df0 * d))
+    assert abs(fd - an) <= 2e-5 * abs(an), (fd, an)
